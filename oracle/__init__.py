@@ -1,0 +1,293 @@
+"""Plain FP64 CPU oracle for the lattice core-Hamiltonian path (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  It shares no code with the CUDA library: the arithmetic lives in
+``lhf_oracle.c`` (compiled with gcc, loaded through ctypes); this module only marshals
+arguments.  See ``lhf_oracle.c`` for the passages of the paper each function follows.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lhf_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liblhf_oracle.so")
+# a test may point the wrapper at another build of the oracle source (planted-mistake checks)
+_LIB_OVERRIDE = os.environ.get("LHF_ORACLE_LIB")
+_lock = threading.Lock()
+_lib = None
+
+NOT_SPD = -3
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 (no FMA contraction) of an oracle source file into a shared library."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile lhf_oracle.c into liblhf_oracle.so (gcc, -O2, no FMA contraction)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        compile_source(_SRC, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _System(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int * 3),
+        ("b", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int * 3),
+        ("n", ctypes.c_int * 3),
+        ("n_cell", ctypes.c_int * 3),
+        ("h", ctypes.c_double * 3),
+        ("x0", ctypes.c_double * 3),
+        ("cell0", ctypes.c_double * 3),
+        ("K_sum", ctypes.c_int * 3),
+        ("M0", ctypes.c_int),
+        ("Z", ctypes.POINTER(ctypes.c_double)),
+        ("Z_cell", ctypes.POINTER(ctypes.c_double)),
+        ("a", ctypes.POINTER(ctypes.c_double)),
+        ("m0", ctypes.c_int),
+        ("kind", ctypes.POINTER(ctypes.c_int)),
+        ("alpha", ctypes.POINTER(ctypes.c_double)),
+        ("centre", ctypes.POINTER(ctypes.c_double)),
+        ("R", ctypes.c_int),
+        ("u0", ctypes.c_double),
+        ("du", ctypes.c_double),
+        ("rho", ctypes.c_double),
+    ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            S = ctypes.POINTER(_System)
+            sig = {
+                "orc_sinc_nodes": (None, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]),
+                "orc_sinc_inverse_r": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+                "orc_gauss_cell_integral": (ctypes.c_double, [ctypes.c_double] * 4),
+                "orc_basis_sample": (ctypes.c_double, [S, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "orc_potential_factor": (ctypes.c_double, [S, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "orc_potential_factors": (None, [S, ctypes.c_int, _dp]),
+                "orc_basis_samples": (None, [S, ctypes.c_int, ctypes.c_int, _dp]),
+                "orc_gram_1d": (ctypes.c_int, [S, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]),
+                "orc_core_blocks": (ctypes.c_int, [S, _dp, _dp]),
+                "orc_core_dense": (ctypes.c_int, [S, _dp, _dp]),
+                "orc_block_dft": (None, [_ip, ctypes.c_int, _dp, _dp]),
+                "orc_jacobi_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp]),
+                "orc_dense_gen_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+                "orc_herm_gen_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+                "orc_k_point_eigenvalues": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _ip]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dp)
+    if a.dtype == np.int32:
+        return a.ctypes.data_as(_ip)
+    raise TypeError(a.dtype)
+
+
+class System:
+    """ctypes view of a workload dictionary (see lhf_workloads); keeps its arrays alive."""
+
+    def __init__(self, cfg: dict):
+        self.cfg = cfg
+        self.Z = np.ascontiguousarray(cfg["Z"], dtype=np.float64)
+        self.a = np.ascontiguousarray(cfg["a"], dtype=np.float64).reshape(-1)
+        self.kind = np.ascontiguousarray(cfg["kind"], dtype=np.int32)
+        self.alpha = np.ascontiguousarray(cfg["alpha"], dtype=np.float64)
+        self.centre = np.ascontiguousarray(cfg["centre"], dtype=np.float64).reshape(-1)
+        self.Z_cell = None if cfg.get("Z_cell") is None else np.ascontiguousarray(cfg["Z_cell"], dtype=np.float64).reshape(-1)
+        s = _System()
+        for f in ("L", "periodic", "n", "n_cell", "K_sum"):
+            getattr(s, f)[:] = [int(v) for v in cfg[f]]
+        for f in ("b", "h", "x0", "cell0"):
+            getattr(s, f)[:] = [float(v) for v in cfg[f]]
+        s.M0 = len(cfg["Z"])
+        s.Z = _ptr(self.Z)
+        s.Z_cell = _ptr(self.Z_cell) if self.Z_cell is not None else ctypes.cast(None, _dp)
+        s.a = _ptr(self.a)
+        s.m0 = len(cfg["alpha"])
+        s.kind = _ptr(self.kind)
+        s.alpha = _ptr(self.alpha)
+        s.centre = _ptr(self.centre)
+        s.R = int(cfg["R"])
+        s.u0 = float(cfg["u0"])
+        s.du = float(cfg["du"])
+        s.rho = float(cfg["rho"])
+        self.s = s
+        self.m0 = s.m0
+        self.Rt = s.M0 * s.R
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _sys(cfg) -> System:
+    return cfg if isinstance(cfg, System) else System(cfg)
+
+
+# --- quadrature and 1D factors ----------------------------------------------------------------
+
+def sinc_nodes(R: int, u0: float, du: float):
+    t = np.empty(R)
+    w = np.empty(R)
+    _load().orc_sinc_nodes(R, u0, du, _ptr(t), _ptr(w))
+    return t, w
+
+
+def sinc_inverse_r(R: int, u0: float, du: float, r) -> np.ndarray:
+    lib = _load()
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    return np.array([lib.orc_sinc_inverse_r(R, u0, du, float(x)) for x in r])
+
+
+def gauss_cell_integral(t: float, lo: float, hi: float, c: float) -> float:
+    return _load().orc_gauss_cell_integral(float(t), float(lo), float(hi), float(c))
+
+
+def basis_samples(cfg, l: int, cell: int = 0) -> np.ndarray:
+    s = _sys(cfg)
+    out = np.empty((s.m0, s.cfg["n"][l]))
+    _load().orc_basis_samples(s.ref, l, cell, _ptr(out))
+    return out
+
+
+def potential_factors(cfg, l: int) -> np.ndarray:
+    """[R_tot][n_l] potential factors of direction l (periodic ones replicated per cell)."""
+    s = _sys(cfg)
+    out = np.empty((s.Rt, s.cfg["n"][l]))
+    _load().orc_potential_factors(s.ref, l, _ptr(out))
+    return out
+
+
+def gram_1d(cfg, l: int, p: int, q: int, V: np.ndarray | None = None):
+    """(C [R_tot][m0][m0], K [m0][m0], M [m0][m0]) between cell-p and cell-q copies along l."""
+    s = _sys(cfg)
+    if V is None:
+        V = potential_factors(s, l)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    C = np.empty((s.Rt, s.m0, s.m0))
+    K = np.empty((s.m0, s.m0))
+    M = np.empty((s.m0, s.m0))
+    rc = _load().orc_gram_1d(s.ref, l, p, q, _ptr(V), _ptr(C), _ptr(K), _ptr(M))
+    if rc != 0:
+        raise MemoryError(rc)
+    return C, K, M
+
+
+def rank_coefficients(cfg) -> np.ndarray:
+    s = _sys(cfg)
+    t, w = sinc_nodes(s.cfg["R"], s.cfg["u0"], s.cfg["du"])
+    return np.concatenate([z * w for z in s.cfg["Z"]])
+
+
+# --- assembled matrices -----------------------------------------------------------------------
+
+def core_blocks(cfg):
+    """First block column (H_j, S_j), shape [L0, L1, L2, m0, m0] each (periodic lattices)."""
+    s = _sys(cfg)
+    L = s.cfg["L"]
+    H = np.empty((L[0], L[1], L[2], s.m0, s.m0))
+    S = np.empty_like(H)
+    rc = _load().orc_core_blocks(s.ref, _ptr(H), _ptr(S))
+    if rc != 0:
+        raise MemoryError(rc)
+    return H, S
+
+
+def core_dense(cfg):
+    """Full N_b x N_b (H, S), index (cell, mu) with cell = (p0 L1 + p1) L2 + p2."""
+    s = _sys(cfg)
+    L = s.cfg["L"]
+    Nb = s.m0 * L[0] * L[1] * L[2]
+    H = np.empty((Nb, Nb))
+    S = np.empty((Nb, Nb))
+    rc = _load().orc_core_dense(s.ref, _ptr(H), _ptr(S))
+    if rc != 0:
+        raise MemoryError(rc)
+    return H, S
+
+
+def block_dft(A: np.ndarray) -> np.ndarray:
+    """Direct DFT of blocks A[L0, L1, L2, m, m] -> complex128 of the same shape."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    L = np.ascontiguousarray(A.shape[:3], dtype=np.int32)
+    m = A.shape[3]
+    out = np.empty(A.shape + (2,))
+    _load().orc_block_dft(_ptr(L), m, _ptr(A), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def jacobi_eigenvalues(A: np.ndarray) -> np.ndarray:
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    ev = np.empty(A.shape[0])
+    _load().orc_jacobi_eigenvalues(A.shape[0], _ptr(A), _ptr(ev))
+    return ev
+
+
+def dense_gen_eigenvalues(H: np.ndarray, S: np.ndarray) -> np.ndarray:
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    ev = np.empty(H.shape[0])
+    rc = _load().orc_dense_gen_eigenvalues(H.shape[0], _ptr(H), _ptr(S), _ptr(ev))
+    if rc != 0:
+        raise np.linalg.LinAlgError(f"overlap matrix not positive definite ({rc})")
+    return ev
+
+
+def _as_interleaved(X: np.ndarray) -> np.ndarray:
+    X = np.asarray(X)
+    out = np.empty(X.shape + (2,))
+    out[..., 0] = X.real
+    out[..., 1] = X.imag
+    return np.ascontiguousarray(out)
+
+
+def k_point_eigenvalues(Hbar: np.ndarray, Sbar: np.ndarray):
+    """Eigenvalues [K, m] (ascending) and status [K] for blocks Hbar, Sbar [..., m, m]."""
+    m = Hbar.shape[-1]
+    Hi = _as_interleaved(Hbar.reshape(-1, m, m))
+    Si = _as_interleaved(Sbar.reshape(-1, m, m))
+    K = Hi.shape[0]
+    eig = np.empty((K, m))
+    st = np.empty(K, dtype=np.int32)
+    _load().orc_k_point_eigenvalues(K, m, _ptr(Hi), _ptr(Si), _ptr(eig), _ptr(st))
+    return eig, st
+
+
+def bloch_spectrum(cfg):
+    """The whole path for a periodic lattice: blocks -> DFT -> per-k eigenvalues [K, m0]."""
+    H, S = core_blocks(cfg)
+    Hb = block_dft(H)
+    Sb = block_dft(S)
+    eig, st = k_point_eigenvalues(Hb, Sb)
+    return eig, st

@@ -1,0 +1,514 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+Every check compares the oracle with something other than itself: closed-form integrals of
+Gaussians (overlap, kinetic, Boys-function nuclear attraction), erf identities evaluated in
+high precision, brute-force 3D sums on tiny grids, dense eigen-solvers from SciPy, numpy's FFT,
+the symmetric block-circulant formula of Cor. 6.2, and invariants of the block-circulant
+structure (Lemma 4.1, Prop. 6.1).  No GPU is used.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import erf
+
+import lhf_workloads as W
+
+SINC_BOUNDS = {
+    # key: (r_min, r_max, max relative error of the exponential sum vs 1/r)
+    "periodic_8": (0.03125, 16.0, 9e-5),
+    "tube_256": (0.0109375, 362.0, 9e-5),
+    "box_64": (0.025, 186.0, 5e-5),
+    "cubic_32": (0.015625, 60.0, 3e-5),
+    "small": (0.04, 60.0, 5e-4),
+}
+
+
+def cube_system(n, h, half, Z, a, kind, alpha, centre, sinc="periodic_8"):
+    """A single open cell [-half, half]^3 with n nodes per direction."""
+    R, u0, du = W.SINC_TABLE[sinc]
+    return W.make_system(L=[1, 1, 1], b=[2 * half] * 3, periodic=[0, 0, 0], n_cell=[n] * 3,
+                         h=[h] * 3, x0=[-half] * 3, cell0=[-half] * 3, Z=Z, a=a, kind=kind,
+                         alpha=alpha, centre=centre, R=R, u0=u0, du=du)
+
+
+# ------------------------------------------------------------------------------------------
+# Sinc quadrature of the Newton kernel (eq. (3.6))
+
+@pytest.mark.parametrize("key", sorted(SINC_BOUNDS))
+def test_sinc_quadrature_approximates_inverse_r(oracle_mod, key):
+    R, u0, du = W.SINC_TABLE[key]
+    lo, hi, bound = SINC_BOUNDS[key]
+    r = np.geomspace(lo, hi, 3000)
+    err = np.abs(oracle_mod.sinc_inverse_r(R, u0, du, r) * r - 1.0)
+    assert err.max() < bound
+
+
+def test_sinc_nodes_are_the_trapezoid_rule(oracle_mod):
+    # t_q = exp(u0 + q du); interior weights 2/sqrt(pi) du t_q; the first weight carries the
+    # geometric tail sum_{k>=0} exp(-k du) of the nodes below u0.
+    t, w = oracle_mod.sinc_nodes(6, -2.0, 0.5)
+    assert np.allclose(np.log(t), -2.0 + 0.5 * np.arange(6), rtol=0, atol=1e-15)
+    tail = sum(math.exp(-k * 0.5) for k in range(200))
+    assert w[0] == pytest.approx(2 / math.sqrt(math.pi) * 0.5 * t[0] * tail, rel=1e-14)
+    assert np.allclose(w[1:], 2 / math.sqrt(math.pi) * 0.5 * t[1:], rtol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------
+# Cell integrals of one sinc term (eq. (3.5))
+
+def test_cell_integral_matches_high_precision_erf(oracle_mod):
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for t in [1e-4, 1e-3, 0.01, 0.1, 0.5, 1.0, 3.0, 10.0, 100.0, 1000.0]:
+        for width in [1e-3, 0.0219, 0.1, 1.0, 4.0]:
+            for _ in range(6):
+                c = rng.uniform(-2, 2)
+                lo = rng.uniform(-3, 3)
+                hi = lo + width
+                T, C, LO, HI = (mpmath.mpf(v) for v in (t, c, lo, hi))
+                ref = mpmath.sqrt(mpmath.pi) / (2 * T) * (mpmath.erf(T * (HI - C)) - mpmath.erf(T * (LO - C)))
+                ref = float(ref)
+                got = oracle_mod.gauss_cell_integral(t, lo, hi, c)
+                err = abs(got - ref) / (abs(ref) + 1e-22 * width)
+                worst = max(worst, err)
+    assert worst < 5e-14
+
+
+def test_cell_integrals_telescope_to_erf(oracle_mod):
+    # the cells of a grid tile [x0, x0 + n h]: their integrals sum to one erf difference
+    for t in [2e-3, 0.05, 0.7, 5.0, 60.0]:
+        x0, h, n, c = -7.3, 0.0625, 240, 0.377
+        tot = sum(oracle_mod.gauss_cell_integral(t, x0 + i * h, x0 + (i + 1) * h, c) for i in range(n))
+        ref = math.sqrt(math.pi) / (2 * t) * (erf(t * (x0 + n * h - c)) - erf(t * (x0 - c)))
+        assert tot == pytest.approx(ref, rel=2e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Separable basis (eq. (3.14)) and periodisation
+
+def test_basis_factors_unit_peak_and_moments(oracle_mod):
+    al = 0.8
+    cfg = cube_system(n=400, h=0.05, half=10.0, Z=[1.0], a=[[0, 0, 0]], kind=[0, 1, 2],
+                      alpha=[al, al, al], centre=[[0.025, 0.025, 0.025]] * 3)
+    g = oracle_mod.basis_samples(cfg, 0)           # direction x: s, px, py
+    h = 0.05
+    x = -10 + (np.arange(400) + 0.5) * h
+    # s factor: a node sits on the centre -> peak exactly 1; integral sqrt(pi/alpha)
+    assert g[0].max() == 1.0
+    assert g[0].sum() * h == pytest.approx(math.sqrt(math.pi / al), rel=1e-12)
+    # second moment of the s factor: 1/(2 alpha)
+    assert (g[0] * (x - 0.025) ** 2).sum() / g[0].sum() == pytest.approx(1 / (2 * al), rel=1e-10)
+    # p_x factor: odd about the centre, peak 1 at |d| = 1/sqrt(2 alpha), int g^2 = e sqrt(pi)/(2 sqrt(2 alpha))
+    xf = np.linspace(-3, 3, 600001)
+    assert np.max(math.sqrt(2 * al * math.e) * xf * np.exp(-al * xf ** 2)) == pytest.approx(1.0, abs=1e-9)
+    assert (g[1] ** 2).sum() * h == pytest.approx(math.e * math.sqrt(math.pi) / (2 * math.sqrt(2 * al)), rel=1e-10)
+    assert abs(g[1].sum()) < 1e-12
+    # the p_y function's x factor is the plain Gaussian
+    assert np.array_equal(g[2], g[0])
+    # truncation radius sqrt(40 / alpha)
+    cut = math.sqrt(40 / al)
+    assert np.all(g[0][np.abs(x - 0.025) > cut + 1e-12] == 0.0)
+
+
+def test_periodised_basis_integrates_over_one_period(oracle_mod):
+    # a Gaussian periodised over L b sums (trapezoid, spectrally accurate) to its full integral
+    L, b, nc = 3, 2.0, 40
+    for al in [0.05, 0.3, 2.0]:
+        cfg = W.make_system(L=[L, 1, 1], b=[b, 8, 8], periodic=[1, 0, 0], n_cell=[nc, 64, 64],
+                            h=[b / nc, 0.125, 0.125], x0=[0, -4, -4], cell0=[0, -4, -4], Z=[1.0],
+                            a=[[1.0, 0, 0]], kind=[0], alpha=[al], centre=[[0.7, 0, 0]],
+                            R=6, u0=-2.0, du=0.8)
+        for cell in range(L):
+            g = oracle_mod.basis_samples(cfg, 0, cell)[0]
+            assert g.sum() * (b / nc) == pytest.approx(math.sqrt(math.pi / al), rel=1e-11)
+            # a copy in cell j is the cell-0 copy shifted by j n_c nodes (mod n)
+            g0 = oracle_mod.basis_samples(cfg, 0, 0)[0]
+            assert np.allclose(g, np.roll(g0, cell * nc), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------------------------------------
+# Potential factors: lattice sum over a window of images (eqs. (3.9), (4.1))
+
+def _erf_window(t, lo, hi, c):
+    return math.sqrt(math.pi) / (2 * t) * (erf(t * (hi - c)) - erf(t * (lo - c)))
+
+
+def test_periodic_potential_factor_sums_the_image_window(oracle_mod):
+    for K in [5, 8]:
+        L, b, nc = 8, 2.0, 16
+        cfg = W.make_system(L=[L, 1, 1], b=[b, 8, 8], periodic=[1, 0, 0], n_cell=[nc, 32, 32],
+                            h=[b / nc, 0.25, 0.25], x0=[0, -4, -4], cell0=[0, -4, -4], Z=[1.0],
+                            a=[[0.63, 0.1, -0.2]], kind=[0], alpha=[1.0], centre=[[0.63, 0.1, -0.2]],
+                            R=12, u0=-4.0, du=0.7, K_sum=[K, 1, 1])
+        V = oracle_mod.potential_factors(cfg, 0)
+        t, _ = oracle_mod.sinc_nodes(12, -4.0, 0.7)
+        # replicated with the cell period
+        assert np.array_equal(V[:, :nc], V[:, nc:2 * nc])
+        assert np.array_equal(V[:, :nc], V[:, -nc:])
+        kmax = K // 2
+        for q in [0, 4, 8, 11]:
+            ref = 0.0
+            for k in range(-kmax, kmax + 1):
+                wk = 0.5 if (K % 2 == 0 and abs(k) == kmax) else 1.0
+                ref += wk * _erf_window(t[q], 0.0, b, 0.63 + k * b)
+            assert V[q, :nc].sum() == pytest.approx(ref, rel=1e-13)
+
+
+def test_open_potential_factors(oracle_mod):
+    # single open cell: one image; box lattice: all cells weighted by their charges
+    cfg = W.make_system(L=[4, 1, 1], b=[2.0, 8, 8], periodic=[0, 0, 0], n_cell=[20, 32, 32],
+                        n=[120, 32, 32], h=[0.1, 0.25, 0.25], x0=[-2.0, -4, -4], cell0=[0, -4, -4],
+                        Z=[1.0], Z_cell=[[1], [2], [2], [1]], a=[[0.9, 0.3, 0.1]], kind=[0],
+                        alpha=[1.0], centre=[[0.9, 0.3, 0.1]], R=10, u0=-3.0, du=0.7)
+    t, _ = oracle_mod.sinc_nodes(10, -3.0, 0.7)
+    V0 = oracle_mod.potential_factors(cfg, 0)
+    V1 = oracle_mod.potential_factors(cfg, 1)
+    for q in range(10):
+        ref = sum(z * _erf_window(t[q], -2.0, 10.0, 0.9 + k * 2.0) for k, z in enumerate([1, 2, 2, 1]))
+        assert V0[q].sum() == pytest.approx(ref, rel=1e-13)
+        assert V1[q].sum() == pytest.approx(_erf_window(t[q], -4.0, 4.0, 0.3), rel=1e-13)
+
+
+# ------------------------------------------------------------------------------------------
+# P1 forms and 1D Grams: second-order convergence to the continuum integrals (Sec. 3.4)
+
+def _pair_1d(h, al, be, A, B):
+    half = 8.0
+    n = int(round(2 * half / h))
+    return W.make_system(L=[1, 1, 1], b=[2 * half] * 3, periodic=[0, 0, 0], n_cell=[n] * 3,
+                         h=[h] * 3, x0=[-half] * 3, cell0=[-half] * 3, Z=[1.0], a=[[0.1, 0, 0]],
+                         kind=[0, 0], alpha=[al, be], centre=[[A, 0, 0], [B, 0, 0]], R=4, u0=-1.0,
+                         du=1.0)
+
+
+def test_p1_mass_and_stiffness_converge_to_gaussian_integrals(oracle_mod):
+    al, be, A, B = 0.7, 1.9, 0.31, -0.44
+    p, mu, d = al + be, al * be / (al + be), A - B
+    S_ex = math.sqrt(math.pi / p) * math.exp(-mu * d * d)
+    T_ex = 2 * al * be / p * math.sqrt(math.pi / p) * math.exp(-mu * d * d) * (1 - 2 * mu * d * d)
+    errs = []
+    for h in [0.1, 0.05, 0.025]:
+        _, K, M = oracle_mod.gram_1d(_pair_1d(h, al, be, A, B), 0, 0, 0)
+        errs.append((M[0, 1] - S_ex, K[0, 1] - T_ex))
+        assert M[0, 1] == M[1, 0] and K[0, 1] == pytest.approx(K[1, 0], rel=1e-14)
+    errs = np.abs(np.array(errs))
+    assert errs[-1, 0] < 2e-4 * S_ex and errs[-1, 1] < 2e-3 * abs(T_ex)
+    # O(h^2): halving h divides the error by ~4
+    for k in range(2):
+        assert 3.2 < errs[k, 0] / errs[k + 1, 0] < 4.8
+        assert 3.2 < errs[k, 1] / errs[k + 1, 1] < 4.8
+
+
+def test_weighted_1d_gram_converges(oracle_mod):
+    # C_r = sum_i g f v_r: v_r is the cell integral of exp(-t^2 (x - c)^2); the continuum value is
+    # the integral of a product of three Gaussians.
+    al, be, A, B, c = 0.9, 1.3, 0.2, -0.3, 0.1
+    t, _ = oracle_mod.sinc_nodes(4, -1.0, 1.0)
+    errs = []
+    for h in [0.1, 0.05, 0.025]:
+        C, _, _ = oracle_mod.gram_1d(_pair_1d(h, al, be, A, B), 0, 0, 0)
+        row = []
+        for q in range(4):
+            g2 = t[q] ** 2
+            P = al + be + g2
+            Q = al * A + be * B + g2 * c
+            Rr = al * A * A + be * B * B + g2 * c * c
+            ex = math.sqrt(math.pi / P) * math.exp(Q * Q / P - Rr)
+            row.append(C[q, 0, 1] - ex)
+            assert C[q, 0, 1] == pytest.approx(C[q, 1, 0], rel=1e-14)
+        errs.append(row)
+    errs = np.abs(np.array(errs))
+    assert np.all(errs[-1] < 1e-3)
+    assert np.all(errs[0] / errs[1] > 3.0) and np.all(errs[1] / errs[2] > 3.0)
+
+
+# ------------------------------------------------------------------------------------------
+# 3D assembly: overlap, kinetic and nuclear attraction against textbook closed forms
+
+def _boys0(x):
+    return 1.0 if x < 1e-14 else 0.5 * math.sqrt(math.pi / x) * math.erf(math.sqrt(x))
+
+
+def _ss_closed_forms(al, be, A, B, C):
+    A, B, C = map(np.asarray, (A, B, C))
+    p, mu = al + be, al * be / (al + be)
+    AB2 = float(((A - B) ** 2).sum())
+    P = (al * A + be * B) / p
+    PC2 = float(((P - C) ** 2).sum())
+    S = (math.pi / p) ** 1.5 * math.exp(-mu * AB2)
+    T = mu * (3 - 2 * mu * AB2) * S          # (1/2) int grad g . grad f
+    V = 2 * math.pi / p * math.exp(-mu * AB2) * _boys0(p * PC2)
+    return S, T, V
+
+
+def test_overlap_and_kinetic_single_cell_converge(oracle_mod):
+    # with Z = 0 the core Hamiltonian is the kinetic form alone: H = (1/2) <A_3 G, G>
+    al, be = 0.6, 1.7
+    A, B, Cn = [0.21, -0.13, 0.07], [-0.35, 0.18, 0.26], [0.04, 0.11, -0.09]
+    S_ex, T_ex, _ = _ss_closed_forms(al, be, A, B, Cn)
+    errs = []
+    for h in [0.1, 0.05]:
+        n = int(round(16 / h))
+        cfg = cube_system(n=n, h=h, half=8.0, Z=[0.0], a=[Cn], kind=[0, 0], alpha=[al, be],
+                          centre=[A, B])
+        H, S = oracle_mod.core_blocks(cfg)
+        errs.append((S[0, 0, 0, 0, 1] - S_ex, H[0, 0, 0, 0, 1] - T_ex))
+    errs = np.abs(np.array(errs))
+    assert errs[1, 0] < 1e-3 * S_ex and errs[1, 1] < 3e-3 * abs(T_ex)
+    assert 3.2 < errs[0, 0] / errs[1, 0] < 4.8 and 3.2 < errs[0, 1] / errs[1, 1] < 4.8
+
+
+def test_nuclear_attraction_s_and_p_against_boys(oracle_mod):
+    # V alone: a system whose kinetic part is removed by comparing H(Z) - H(0) ... here the
+    # nuclear part is isolated as H(Z=0) - H(Z=1) (T is independent of the nuclei).
+    al, be = 0.8, 1.4
+    A, B, Cn = [0.17, -0.11, 0.05], [-0.27, 0.22, 0.13], [0.02, 0.09, -0.12]
+    h = 0.05
+    n = int(round(16 / h))
+
+    def V_of(kind, Z):
+        cfg = cube_system(n=n, h=h, half=8.0, Z=[Z], a=[Cn], kind=kind, alpha=[al, be],
+                          centre=[A, B])
+        H, _ = oracle_mod.core_blocks(cfg)
+        return H[0, 0, 0]
+
+    Vss = V_of([0, 0], 0.0) - V_of([0, 0], 1.0)
+    Vps = V_of([1, 0], 0.0) - V_of([1, 0], 1.0)
+    _, _, Vss_ex = _ss_closed_forms(al, be, A, B, Cn)
+    assert Vss[0, 1] == pytest.approx(Vss_ex, rel=2e-3)
+    # p_x on A (unit peak) = sqrt(2 al e) (x - A_x) e^{-al |r-A|^2} = sqrt(2 al e)/(2 al) d/dA_x s
+    def vss(ax):
+        return _ss_closed_forms(al, be, [ax, A[1], A[2]], B, Cn)[2]
+
+    step = 1e-5
+    dV = (vss(A[0] + step) - vss(A[0] - step)) / (2 * step)
+    Vps_ex = math.sqrt(2 * al * math.e) / (2 * al) * dV
+    assert Vps[0, 1] == pytest.approx(Vps_ex, rel=5e-3)
+
+
+# ------------------------------------------------------------------------------------------
+# Brute force on tiny grids: full 3D sums versus the separable assembly
+
+def _tridiag(n, d, o, periodic):
+    M = np.diag(np.full(n, d)) + np.diag(np.full(n - 1, o), 1) + np.diag(np.full(n - 1, o), -1)
+    if periodic:
+        M[0, -1] = M[-1, 0] = o
+    return M
+
+
+def test_separable_assembly_equals_brute_force_3d(oracle_mod):
+    L = [3, 2, 1]
+    nc = [6, 5, 12]
+    b = [1.5, 1.25, 3.0]
+    h = [b[l] / nc[l] for l in range(3)]
+    R, u0, du = 5, -1.5, 0.9
+    cfg = W.make_system(L=L, b=b, periodic=[1, 1, 0], n_cell=nc, h=h, x0=[0, 0, -1.5],
+                        cell0=[0, 0, -1.5], Z=[1.0, 2.0], a=[[0.6, 0.5, 0.1], [1.0, 0.8, -0.4]],
+                        kind=[0, 1, 3], alpha=[1.2, 2.5, 3.1],
+                        centre=[[0.6, 0.5, 0.1], [1.0, 0.8, -0.4], [0.6, 0.5, 0.1]],
+                        R=R, u0=u0, du=du, K_sum=[3, 2, 1])
+    H, S = oracle_mod.core_dense(cfg)
+    t, w = oracle_mod.sinc_nodes(R, u0, du)
+    n = [L[l] * nc[l] for l in range(3)]
+    grids = [(np.arange(n[l]) + 0.5) * h[l] + cfg["x0"][l] for l in range(3)]
+    # basis in 3D, every cell copy, sampled directly from the analytic formula with images
+    ncell = L[0] * L[1] * L[2]
+    funcs = []
+    for P in range(ncell):
+        pc = [P // (L[1] * L[2]), (P // L[2]) % L[1], P % L[2]]
+        for mu in range(3):
+            f = np.ones(n)
+            for l in range(3):
+                x = grids[l]
+                A = cfg["centre"][mu][l] + pc[l] * b[l]
+                al = cfg["alpha"][mu]
+                cut = math.sqrt(40 / al)
+                tot = np.zeros_like(x)
+                imgs = range(-3, 4) if cfg["periodic"][l] else [0]
+                for m in imgs:
+                    d = x - A - m * L[l] * b[l]
+                    v = np.exp(-al * d * d)
+                    if cfg["kind"][mu] == 1 + l:
+                        v = v * math.sqrt(2 * al * math.e) * d
+                    v[np.abs(d) > cut] = 0.0
+                    tot += v
+                shape = [1, 1, 1]
+                shape[l] = n[l]
+                f = f * tot.reshape(shape)
+            funcs.append(f)
+    # potential cell integrals in 3D: sum over nuclei, sinc terms and the full 3D image window
+    pot = np.zeros(n)
+    for nu, (Z, a) in enumerate(zip(cfg["Z"], cfg["a"])):
+        for q in range(R):
+            for k0 in range(-1, 2):
+                for k1 in (-1, 0, 1):
+                    w1 = 0.5 if abs(k1) == 1 else 1.0
+                    fac = []
+                    for l, k in ((0, k0), (1, k1), (2, 0)):
+                        lo = (np.arange(n[l]) % nc[l]) * h[l] + cfg["cell0"][l] if cfg["periodic"][l] \
+                            else np.arange(n[l]) * h[l] + cfg["x0"][l]
+                        c = a[l] + k * b[l]
+                        fac.append(math.sqrt(math.pi) / (2 * t[q]) *
+                                   (erf(t[q] * (lo + h[l] - c)) - erf(t[q] * (lo - c))))
+                    pot += Z * w[q] * w1 * np.einsum("i,j,k->ijk", *fac)
+    A1 = [_tridiag(n[l], 2.0 / h[l], -1.0 / h[l], cfg["periodic"][l]) for l in range(3)]
+    S1 = [_tridiag(n[l], 4 * h[l] / 6, h[l] / 6, cfg["periodic"][l]) for l in range(3)]
+
+    def apply(ops, X):
+        Y = np.einsum("ia,ajk->ijk", ops[0], X)
+        Y = np.einsum("jb,ibk->ijk", ops[1], Y)
+        return np.einsum("kc,ijc->ijk", ops[2], Y)
+
+    Nb = len(funcs)
+    Hb = np.zeros((Nb, Nb))
+    Sb = np.zeros((Nb, Nb))
+    for J, f in enumerate(funcs):
+        Af = apply([A1[0], S1[1], S1[2]], f) + apply([S1[0], A1[1], S1[2]], f) + apply([S1[0], S1[1], A1[2]], f)
+        Sf = apply(S1, f)
+        for I, g in enumerate(funcs):
+            Hb[I, J] = 0.5 * (g * Af).sum() - (g * f * pot).sum()
+            Sb[I, J] = (g * Sf).sum()
+    assert np.abs(H - Hb).max() <= 1e-12 * np.abs(Hb).max()
+    assert np.abs(S - Sb).max() <= 1e-12 * np.abs(Sb).max()
+
+
+# ------------------------------------------------------------------------------------------
+# Block-circulant structure (Lemma 4.1), the block DFT (Prop. 6.1) and the spectrum
+
+def small_tube(L=6, seed=21, nc=16, K_sum=None, alpha_lo=0.3):
+    return W.tube(L, seed=seed, n_c=nc, n_perp=32, half_width=5.0, M0=2, m0_s=2, m0_pshell=1,
+                  lo=alpha_lo, hi=8.0, K_sum=K_sum)
+
+
+def test_dense_matrix_is_block_circulant_and_symmetric(oracle_mod):
+    cfg = small_tube()
+    H, S = oracle_mod.core_dense(cfg)
+    Hj, Sj = oracle_mod.core_blocks(cfg)
+    L, m0 = cfg["L"][0], len(cfg["alpha"])
+    scale = np.abs(H).max()
+    for P in range(L):
+        for Q in range(L):
+            blk = H[P * m0:(P + 1) * m0, Q * m0:(Q + 1) * m0]
+            assert np.abs(blk - Hj[(P - Q) % L, 0, 0]).max() <= 1e-12 * scale
+            sblk = S[P * m0:(P + 1) * m0, Q * m0:(Q + 1) * m0]
+            assert np.abs(sblk - Sj[(P - Q) % L, 0, 0]).max() <= 1e-12 * np.abs(S).max()
+    assert np.abs(H - H.T).max() <= 1e-12 * scale
+    assert np.abs(S - S.T).max() <= 1e-13 * np.abs(S).max()
+    # symmetric BC: A_{L-j} = A_j^T
+    for j in range(1, L):
+        assert np.abs(Hj[L - j, 0, 0] - Hj[j, 0, 0].T).max() <= 1e-12 * scale
+
+
+def test_block_dft_matches_numpy_fft_and_symmetric_formula(oracle_mod):
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((6, 4, 3, 5, 5))
+    Ab = oracle_mod.block_dft(A)
+    ref = np.fft.fftn(A, axes=(0, 1, 2))
+    assert np.abs(Ab - ref).max() < 1e-12
+    # Cor. 6.2: for A_{L-k} = A_k^T the DFT is A_0 + sum_{k<L/2}(w^{kj} A_k + conj(w)^{kj} A_k^T) + (-1)^j A_{L/2}
+    L = 8
+    B = rng.standard_normal((L, 1, 1, 4, 4))
+    B[0, 0, 0] = B[0, 0, 0] + B[0, 0, 0].T
+    B[L // 2, 0, 0] = B[L // 2, 0, 0] + B[L // 2, 0, 0].T
+    for k in range(1, L // 2):
+        B[L - k, 0, 0] = B[k, 0, 0].T
+    Bb = oracle_mod.block_dft(B)
+    w = np.exp(-2j * np.pi / L)
+    for j in range(L):
+        tj = B[0, 0, 0] + (-1) ** j * B[L // 2, 0, 0]
+        for k in range(1, L // 2):
+            tj = tj + w ** (k * j) * B[k, 0, 0] + np.conj(w) ** (k * j) * B[k, 0, 0].T
+        assert np.abs(Bb[j, 0, 0] - tj).max() < 1e-12
+        assert np.abs(Bb[j, 0, 0] - Bb[j, 0, 0].conj().T).max() < 1e-12   # Hermitian
+        assert np.abs(Bb[(L - j) % L, 0, 0] - Bb[j, 0, 0].conj()).max() < 1e-12
+
+
+def eig_tolerance(Hb, Sb, lam, floor=1e-10, c=64.0):
+    """First-order perturbation bound for a backward-stable solver of H u = lambda S u:
+    |d lambda| <= c eps (||H|| + |lambda| ||S||) ||u||^2 with u S-normalised."""
+    eps = np.finfo(float).eps
+    _, U = sla.eigh(Hb, Sb)
+    u2 = (np.abs(U) ** 2).sum(axis=0)
+    nH = np.linalg.norm(Hb, 2)
+    nS = np.linalg.norm(Sb, 2)
+    return np.maximum(floor, c * eps * (nH + np.abs(lam) * nS) * u2)
+
+
+def test_k_point_eigenvalues_match_scipy(oracle_mod):
+    cfg = small_tube(L=8, seed=5, alpha_lo=0.1)
+    H, S = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(H), oracle_mod.block_dft(S)
+    eig, st = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    assert np.all(st == 0)
+    for k in range(8):
+        ref = sla.eigh(Hb[k, 0, 0], Sb[k, 0, 0], eigvals_only=True)
+        tol = eig_tolerance(Hb[k, 0, 0], Sb[k, 0, 0], ref)
+        assert np.all(np.abs(eig[k] - ref) <= tol)
+
+
+def test_spectrum_is_union_of_k_point_spectra(oracle_mod):
+    # Prop. 6.1, eq. (6.7): the dense generalized spectrum equals the union over kappa
+    cfg = small_tube(L=6, seed=8)
+    H, S = oracle_mod.core_dense(cfg)
+    dense = sla.eigh(H, S, eigvals_only=True)
+    own = oracle_mod.dense_gen_eigenvalues(H, S)
+    eig, _ = oracle_mod.bloch_spectrum(cfg)
+    union = np.sort(eig.ravel())
+    assert np.abs(union - dense).max() < 1e-9
+    assert np.abs(own - dense).max() < 1e-9
+
+
+def test_m0_one_closed_form_and_trace(oracle_mod):
+    rng = np.random.default_rng(11)
+    Hb = rng.standard_normal((5, 1, 1)) + 0j
+    Sb = rng.uniform(0.5, 2.0, (5, 1, 1)) + 0j
+    eig, _ = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    assert np.allclose(eig[:, 0], (Hb / Sb).real.ravel(), rtol=1e-14)
+    # trace identity sum lambda = tr(S^-1 H) on a random Hermitian pencil
+    m = 6
+    X = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    Hh = X + X.conj().T
+    Y = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    Sh = Y @ Y.conj().T + m * np.eye(m)
+    eig, _ = oracle_mod.k_point_eigenvalues(Hh[None], Sh[None])
+    assert eig.sum() == pytest.approx(np.trace(np.linalg.solve(Sh, Hh)).real, rel=1e-12)
+    # non-SPD overlap is reported, not solved
+    eig, st = oracle_mod.k_point_eigenvalues(Hh[None], -Sh[None])
+    assert st[0] == -3 and np.all(np.isnan(eig))
+
+
+def test_jacobi_against_numpy(oracle_mod):
+    rng = np.random.default_rng(2)
+    for n in [1, 2, 7, 20]:
+        X = rng.standard_normal((n, n))
+        A = X + X.T
+        assert np.abs(oracle_mod.jacobi_eigenvalues(A) - np.linalg.eigvalsh(A)).max() < 1e-12 * max(1, np.abs(A).max())
+
+
+def test_k_sampling_consistency_L_vs_2L(oracle_mod):
+    # with the same image window and no self-overlap across the supercell, system L at kappa
+    # and system 2L at 2 kappa have the same Bloch blocks, hence the same eigenvalues
+    base = dict(n_c=12, n_perp=24, half_width=4.0, M0=1, m0_s=2, m0_pshell=1, lo=1.6, hi=6.0, b=2.8)
+    c4 = W.tube(4, seed=31, K_sum=4, **base)
+    c8 = W.tube(8, seed=31, K_sum=4, **base)
+    e4, _ = oracle_mod.bloch_spectrum(c4)
+    e8, _ = oracle_mod.bloch_spectrum(c8)
+    assert np.abs(e4 - e8[::2]).max() < 1e-11
+
+
+def test_single_cell_periodic_equals_open(oracle_mod):
+    # L = 1, one image, tight functions that never reach the cell boundary: the periodic and the
+    # open assemblies coincide
+    common = dict(L=[1, 1, 1], b=[6.0, 6.0, 6.0], n_cell=[48, 48, 48], h=[0.125] * 3,
+                  x0=[-3.0] * 3, cell0=[-3.0] * 3, Z=[1.0], a=[[0.1, 0.2, -0.1]], kind=[0, 2],
+                  alpha=[5.0, 7.0], centre=[[0.1, 0.2, -0.1], [-0.2, 0.1, 0.3]], R=10, u0=-3.0,
+                  du=0.7, K_sum=[1, 1, 1])
+    Hp, Sp = oracle_mod.core_blocks(W.make_system(periodic=[1, 1, 1], **common))
+    Ho, So = oracle_mod.core_blocks(W.make_system(periodic=[0, 0, 0], **common))
+    assert np.abs(Hp - Ho).max() < 1e-13 * np.abs(Ho).max()
+    assert np.abs(Sp - So).max() < 1e-14 * np.abs(So).max()
