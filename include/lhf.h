@@ -1,0 +1,213 @@
+/*
+ * lhf.h -- C ABI of the GB300 lattice core-Hamiltonian library (liblhf.so).
+ *
+ * Method: Khoromskaia & Khoromskij, "Tensor numerical approach to linearized Hartree-Fock
+ * equation for lattice-type and periodic systems" (arXiv:1408.3839).  The library assembles the
+ * Galerkin matrices of the core Hamiltonian h = -1/2 Laplacian - v_c (eqs. (3.1), (3.4)) and of
+ * the overlap in a lattice-translated separable Gaussian basis, block-diagonalises the
+ * block-circulant matrices of a periodic lattice by a DFT along the lattice indices (Lemma 2.2,
+ * Prop. 6.1) and solves the small generalized Hermitian eigenproblems at every k-point
+ * (eq. (4.7)).  Every step runs in this library's CUDA kernels on one GPU; there is no CPU path.
+ *
+ * Conventions common to all calls
+ *   - Units are atomic (bohr, Hartree).  Directions l = 0, 1, 2.
+ *   - Device pointers are caller-owned CUDA device memory; host pointers are plain host memory.
+ *     The library never frees caller memory.  It owns only its context and internal workspace.
+ *   - Calls are asynchronous on the context's CUDA stream (set at creation or by
+ *     lhf_set_stream).  Arguments are validated on the host before any launch; an invalid
+ *     argument returns LHF_ERR_ARG and launches nothing.  Conditions found on the device (a
+ *     k-point overlap block that is not positive definite) are reported per k-point through
+ *     k_status and summarised by the next lhf_sync.
+ *   - No call throws; every call returns an lhf_status.  lhf_last_error gives a message for the
+ *     last failing call on that context.
+ *   - Matrices are row-major FP64.  Complex arrays are interleaved (re, im) FP64.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef LHF_H
+#define LHF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LHF_MAX_M0 32     /* basis functions per cell */
+#define LHF_MAX_NUCLEI 8  /* nuclei per cell */
+#define LHF_MAX_R 64      /* sinc-quadrature terms */
+
+typedef enum {
+    LHF_OK = 0,
+    LHF_ERR_ARG = -1,         /* invalid argument or descriptor; nothing was launched */
+    LHF_ERR_CUDA = -2,        /* a CUDA runtime call failed (message in lhf_last_error) */
+    LHF_ERR_NOT_SPD = -3,     /* an overlap block was not positive definite (see k_status) */
+    LHF_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+    LHF_ERR_UNSUPPORTED = -5, /* valid input outside what this build supports */
+    LHF_ERR_STATE = -6,       /* call order violated (e.g. assemble before setup) */
+    LHF_ERR_NOMEM = -7        /* workspace allocation failed */
+} lhf_status;
+
+/* Arithmetic of the weighted Gram contractions (steps a3-a4).  Everything else (potential
+ * factors, rank sum, DFT, eigensolves) is FP64 in both modes.
+ *   LHF_FP64:   FP64 CUDA-core contraction.
+ *   LHF_MIXED:  tensor-core contraction (tcgen05) on BF16 slices of the FP64 operands with
+ *               exact FP32 accumulation per slice pair, recombined in FP64. */
+typedef enum { LHF_FP64 = 0, LHF_MIXED = 1 } lhf_precision;
+
+typedef struct lhf_ctx lhf_ctx;
+
+/* Lattice (Sec. 3.2, Sec. 4.1).  L[l] cells of side b[l] per direction; periodic[l] = 1 makes
+ * direction l block-circulant (supercell of L[l] cells, basis periodised over L[l] b[l]).
+ * M0 nuclei per cell with charges Z[nu] > 0 at positions a[3 nu + l] (coordinates of the copy in
+ * lattice cell 0).  K_sum[l] = number of lattice images in the periodic potential sum of
+ * direction l (images k = -floor(K/2) .. floor(K/2), weight 1/2 on |k| = K/2 for even K; the sum
+ * is evaluated in cell 0 and replicated, eq. (4.1)).  Open directions ignore K_sum.  Z_cell
+ * (optional, NULL otherwise) gives per-cell charges Z_cell[k M0 + nu] of an open box whose only
+ * lattice direction is l = 0 (eq. (3.8)).  Host pointers; copied during setup. */
+typedef struct {
+    int L[3];
+    double b[3];
+    int periodic[3];
+    int K_sum[3];
+    int M0;
+    const double *Z;
+    const double *a;
+    const double *Z_cell;
+} lhf_lattice_desc;
+
+/* Separable Gaussian basis of one cell (eq. (3.14)): m0 functions; kind[mu] = 0 (s) or 1 + d
+ * (p along direction d); exponent alpha[mu] > 0; centre[3 mu + l] (cell-0 coordinates).  1D
+ * factors: exp(-alpha d^2), or sqrt(2 alpha e) d exp(-alpha d^2) along a p function's own
+ * direction (unit peak); each factor is cut to zero where |d| > sqrt(rho / alpha).  The copy
+ * in lattice cell k is shifted by k b.  Host pointers; copied during setup. */
+typedef struct {
+    int m0;
+    const int *kind;
+    const double *alpha;
+    const double *centre;
+    double rho;
+} lhf_basis_desc;
+
+/* Tensor grid and potential quadrature (Sec. 3.2, Sec. 3.4).  Nodes x_i = x0[l] + (i + 1/2) h[l],
+ * i = 0 .. n[l]-1, serve both as P1 nodes (kinetic, overlap) and as centres of the cells of the
+ * piecewise-constant potential.  In a lattice direction (periodic, or open with L > 1) lattice
+ * cell k spans [cell0 + k b, cell0 + (k+1) b) and holds n_cell[l] = b / h nodes; a periodic
+ * direction requires n[l] = L[l] n_cell[l] and x0[l] = cell0[l].  A single-cell open
+ * direction uses n_cell[l] = n[l].  Newton kernel: R sinc terms, t_q = exp(u0 + q du),
+ * w_q = 2/sqrt(pi) du t_q, with w_0 divided by (1 - exp(-du)) (the nodes below u0 folded into
+ * the first one), eq. (3.6). */
+typedef struct {
+    int n[3];
+    int n_cell[3];
+    double h[3];
+    double x0[3];
+    double cell0[3];
+    int R;
+    double u0;
+    double du;
+} lhf_grid_desc;
+
+typedef struct {
+    lhf_lattice_desc lattice;
+    lhf_basis_desc basis;
+    lhf_grid_desc grid;
+} lhf_system_desc;
+
+/* Sizes of the current system (after the three setup calls). */
+typedef struct {
+    int m0;             /* basis functions per cell */
+    int n_blocks;       /* L0 L1 L2: blocks of the first block column (periodic) */
+    int n_kpoints;      /* = n_blocks; eigenvalue rows */
+    int n_basis;        /* N_b = m0 L0 L1 L2 */
+    int rank;           /* R_tot = M0 R rank terms of the potential */
+    int window[3];      /* blocks computed per direction (overlap window, <= L) */
+    int n_potential[3]; /* length of each direction's potential factor (n_cell periodic, else n) */
+    int periodic;       /* 1 if every direction with L > 1 is periodic */
+} lhf_sizes;
+
+/* Context creation.  device: CUDA ordinal; stream: a cudaStream_t (NULL = default stream).
+ * *out receives the context (NULL on failure). */
+lhf_status lhf_create(lhf_ctx **out, int device, void *stream);
+void lhf_destroy(lhf_ctx *ctx);
+const char *lhf_last_error(const lhf_ctx *ctx);
+lhf_status lhf_set_stream(lhf_ctx *ctx, void *stream);
+/* Wait for the context stream; returns LHF_ERR_NOT_SPD if any k-point since the last sync
+ * reported a non-positive-definite overlap, LHF_ERR_CUDA on a CUDA error. */
+lhf_status lhf_sync(lhf_ctx *ctx);
+
+/* Setup of the current system (Sec. 3.2-3.4 define its parts).  Each call validates its
+ * descriptor and keeps a copy; the three together define the problem. */
+lhf_status lhf_lattice_setup(lhf_ctx *ctx, const lhf_lattice_desc *lattice);
+lhf_status lhf_basis_setup(lhf_ctx *ctx, const lhf_basis_desc *basis);
+lhf_status lhf_grid_setup(lhf_ctx *ctx, const lhf_grid_desc *grid);
+lhf_status lhf_query_sizes(lhf_ctx *ctx, lhf_sizes *out);
+
+/* Core Hamiltonian and overlap (eqs. (3.4), (3.10); Lemma 4.1 eqs. (4.2), (4.5), (4.6)).
+ * Periodic lattice: H, S receive the first block column A_j[mu][nu] = <g_{mu,j}, H g_{nu,0}>,
+ * layout [L0][L1][L2][m0][m0] (j = (j0, j1, j2)); blocks outside the overlap window are exact
+ * zeros.  Open box (periodic = 0 in a lattice direction): H, S receive the full [N_b][N_b]
+ * matrices, index (cell, mu).  Device pointers of n_blocks m0^2 (periodic) or N_b^2 doubles. */
+lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *ctx, lhf_precision precision, double *H, double *S);
+
+/* Block DFT along the lattice indices (Prop. 6.1 eq. (6.6), Lemma 2.2 eq. (2.1)):
+ * Xbar_kappa = sum_j omega^{kappa . j} X_j, omega_l = exp(-2 pi i / L_l), for X = H, S given
+ * as first block columns [L0][L1][L2][m0][m0] (device).  Hbar, Sbar: device, complex
+ * interleaved [L0][L1][L2][m0][m0][2].  Periodic lattices only. */
+lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, double *Hbar,
+                             double *Sbar);
+
+/* Generalized Hermitian eigenproblems Hbar_kappa u = lambda Sbar_kappa u at every k-point
+ * (eq. (4.7); spectrum = union over kappa, eq. (6.7)).  Inputs as produced by
+ * lhf_circulant_fft (device).  eig: device [n_kpoints][m0], ascending per k-point.  k_status:
+ * device [n_kpoints] (may be NULL): 0 or LHF_ERR_NOT_SPD; eigenvalues of such a k-point are NaN. */
+lhf_status lhf_k_point_eigensolve(lhf_ctx *ctx, const double *Hbar, const double *Sbar,
+                                  double *eig, int *k_status);
+
+/* Generalized symmetric-definite eigenvalues of dense N x N matrices (open box, Table 4.1's
+ * full eigensolver): H x = lambda S x.  Device pointers; eig [N] ascending. */
+lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, int N, double *eig);
+
+/* Batched Bloch spectra: for every system s of an array of nsys periodic lattices, the whole
+ * path (basis and potential factors, Grams, rank sum, block DFT, k-point eigensolves) in one
+ * pass of batched launches.  eig: device, systems concatenated, system s at offset
+ * sum_{t<s} n_kpoints(t) m0(t).  k_status: device (may be NULL), concatenated likewise.
+ * Scratch memory is the context's workspace (grown on demand). */
+lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
+                             lhf_precision precision, double *eig, int *k_status);
+
+/* Same as lhf_bloch_spectra with a HOST output buffer: the call copies the eigenvalues back
+ * and returns after the stream has finished (synchronising). */
+lhf_status lhf_bloch_spectra_host(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
+                                  lhf_precision precision, double *eig_host, int *k_status_host);
+
+/* Stage outputs of the current system, for verification (same kernels as the full path).
+ * lhf_basis_factors: 1D basis samples of direction l for the cell-0 copies, [m0][n_l]
+ * (periodic directions periodised), eq. (3.14).
+ * lhf_potential_factors: 1D potential factors of direction l, [R_tot][n_potential_l], rank
+ * r = nu R + q, eqs. (3.5), (3.9), (4.1).
+ * lhf_gram_factors: per-direction factors for the window blocks j = jlo .. jlo+J-1 (mod L),
+ * [J][R_tot + 2][m0][m0]: slots r < R_tot hold the weighted Grams sum_i g_{mu,j} v_r g_{nu,0},
+ * slot R_tot the P1 stiffness form, slot R_tot + 1 the P1 mass form (Lemma 3.1 proof, Sec. 3.4).
+ * *jlo receives the first displacement of the window (host int, may be NULL). */
+lhf_status lhf_basis_factors(lhf_ctx *ctx, int l, double *G);
+lhf_status lhf_potential_factors(lhf_ctx *ctx, int l, double *V);
+lhf_status lhf_gram_factors(lhf_ctx *ctx, lhf_precision precision, int l, double *C, int *jlo);
+
+/* Live stage timing.  With profiling enabled, every launch of the path is bracketed by CUDA
+ * events recorded on the context stream (no synchronisation is added).  lhf_stage_times waits
+ * for the stream, adds the elapsed times of all launches recorded since the previous call into
+ * ms[stage] and their count into launches[stage] (arrays of LHF_NUM_STAGES, host), and clears
+ * the record.  Stages: 0 basis samples (a1), 1 potential factors (a2), 2 Gram factors (a3-a4),
+ * 3 rank sum (a5), 4 block DFT (a7), 5 k-point eigensolve (a8), 6 window zero fill (a6),
+ * 7 descriptor upload. */
+#define LHF_NUM_STAGES 8
+lhf_status lhf_set_profiling(lhf_ctx *ctx, int enable);
+lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
+
+/* Work counters of the k-point eigensolver since the previous call (synchronising; host
+ * outputs): total Jacobi sweeps and number of matrices solved (one per conjugate pair of
+ * k-points).  Reset by the call. */
+lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *sweeps, unsigned long long *matrices);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LHF_H */

@@ -1,0 +1,172 @@
+// k_dft.cu -- step a7: DFT of the first block column along the lattice indices, FP64 complex.
+//
+// Xbar_kappa = sum_j omega^{kappa . j} X_j, omega_l = exp(-2 pi i / L_l)  (Prop. 6.1 eq. (6.6);
+// Lemma 2.2 eq. (2.1): the multilevel transform F_L = F_L0 x F_L1 x F_L2 applied to every entry
+// (mu, nu) of the folded block column).  The three levels are separable, so the transform runs
+// as one pass per lattice dimension with L_d > 1 (d = 2, 1, 0); the first pass of a system
+// reads the real blocks, later passes work in place on the complex output.
+//
+// A CTA owns a tile of TW consecutive inner indices (entries (mu, nu) and the faster lattice
+// dimensions) for all L_d positions of one outer index: global loads and stores are rows of TW
+// contiguous values.  The tile is transformed in shared memory: an iterative radix-2 FFT when
+// L_d is a power of two, otherwise the direct O(L_d^2) sum.  Twiddles come from a per-CTA table
+// built with sincospi (correctly-rounded arguments).
+#include "lhf_internal.cuh"
+
+namespace lhf {
+namespace {
+
+constexpr int kDftThreads = 256;
+
+__host__ __device__ inline int tile_width(int Ld) {
+  int tw = 16;
+  while (tw > 1 && (size_t)Ld * tw * 2 > 8192) tw >>= 1;  // <= 128 KB of complex data
+  return tw;
+}
+
+__device__ inline unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+
+__global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restrict__ sysv, int d) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  const int L0 = s.d[0].L, L1 = s.d[1].L, L2 = s.d[2].L;
+  const int Ls[3] = {L0, L1, L2};
+  const bool all_one = (L0 == 1 && L1 == 1 && L2 == 1);
+  if (!(Ls[d] > 1 || (d == 0 && all_one))) return;
+  // first pass of this system reads the real blocks
+  int first = 0;
+  for (int q = 2; q >= 0; --q)
+    if (Ls[q] > 1) {
+      first = q;
+      break;
+    }
+  const bool real_in = (d == first);
+  const int Ld = Ls[d];
+  const int mm = s.m0 * s.m0;
+  int64_t inner = mm;
+  for (int q = d + 1; q < 3; ++q) inner *= Ls[q];
+  int64_t outer = 1;
+  for (int q = 0; q < d; ++q) outer *= Ls[q];
+  const int TW = tile_width(Ld);
+  const int64_t tiles_inner = (inner + TW - 1) / TW;
+  const int64_t tile = blockIdx.x;
+  if (tile >= outer * tiles_inner) return;
+  const int64_t o = tile / tiles_inner;
+  const int64_t i0 = (tile - o * tiles_inner) * TW;
+  const int tw_valid = (int)((inner - i0) < TW ? (inner - i0) : TW);
+
+  const double *Xr = blockIdx.z == 0 ? s.H : s.S;
+  double *Xc = blockIdx.z == 0 ? s.Hbar : s.Sbar;
+
+  extern __shared__ double sm[];
+  double2 *x = reinterpret_cast<double2 *>(sm);  // [Ld][TW]
+  double2 *tab = x + (size_t)Ld * TW;            // [Ld] omega^m
+  const int tid = threadIdx.x;
+  for (int m = tid; m < Ld; m += kDftThreads) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)Ld, &sn, &cs);
+    tab[m] = make_double2(cs, -sn);
+  }
+  const bool pow2 = (Ld & (Ld - 1)) == 0;
+  const int bits = pow2 ? __ffs(Ld) - 1 : 0;
+  for (int k = tid; k < Ld * TW; k += kDftThreads) {
+    const int j = k / TW, t = k - j * TW;
+    double2 v = make_double2(0.0, 0.0);
+    if (t < tw_valid) {
+      const int64_t idx = (o * Ld + j) * inner + i0 + t;
+      if (real_in)
+        v.x = Xr[idx];
+      else
+        v = reinterpret_cast<const double2 *>(Xc)[idx];
+    }
+    const int pos = (pow2 && bits > 0) ? (int)bitrev((unsigned)j, bits) : j;
+    x[pos * TW + t] = v;
+  }
+  __syncthreads();
+  if (pow2) {
+    for (int hs = 1; hs < Ld; hs <<= 1) {
+      const int stride = Ld / (2 * hs);
+      const int nb = (Ld / 2) * TW;
+      for (int k = tid; k < nb; k += kDftThreads) {
+        const int t = k % TW, b = k / TW;
+        const int kk = b % hs;
+        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
+        const double2 w = tab[kk * stride];
+        const double2 u = x[top * TW + t], v = x[bot * TW + t];
+        const double2 wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
+        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
+        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
+      }
+      __syncthreads();
+    }
+    for (int k = tid; k < Ld * TW; k += kDftThreads) {
+      const int kap = k / TW, t = k - kap * TW;
+      if (t < tw_valid) {
+        const int64_t idx = (o * Ld + kap) * inner + i0 + t;
+        reinterpret_cast<double2 *>(Xc)[idx] = x[kap * TW + t];
+      }
+    }
+  } else {
+    for (int k = tid; k < Ld * TW; k += kDftThreads) {
+      const int kap = k / TW, t = k - kap * TW;
+      if (t >= tw_valid) continue;
+      double re = 0.0, im = 0.0;
+      int m = 0;  // (kap * j) mod Ld, advanced incrementally
+      for (int j = 0; j < Ld; ++j) {
+        const double2 w = tab[m], v = x[j * TW + t];
+        re += w.x * v.x - w.y * v.y;
+        im += w.x * v.y + w.y * v.x;
+        m += kap;
+        if (m >= Ld) m -= Ld;
+      }
+      const int64_t idx = (o * Ld + kap) * inner + i0 + t;
+      reinterpret_cast<double2 *>(Xc)[idx] = make_double2(re, im);
+    }
+  }
+}
+
+}  // namespace
+
+// host_L: [nsys][3] lattice sizes (host copy) used to size the grid of each pass.
+cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int /*max_lines*/,
+                       cudaStream_t st) {
+  if (nsys <= 0) return cudaSuccess;
+  for (int d = 2; d >= 0; --d) {
+    int64_t max_tiles = 0;
+    int max_Ld = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const int *L = host_L + 4 * s;  // L0, L1, L2, m0
+      const bool all_one = (L[0] == 1 && L[1] == 1 && L[2] == 1);
+      if (!(L[d] > 1 || (d == 0 && all_one))) continue;
+      int64_t inner = (int64_t)L[3] * L[3];
+      for (int q = d + 1; q < 3; ++q) inner *= L[q];
+      int64_t outer = 1;
+      for (int q = 0; q < d; ++q) outer *= L[q];
+      const int TW = tile_width(L[d]);
+      const int64_t tiles = outer * ((inner + TW - 1) / TW);
+      if (tiles > max_tiles) max_tiles = tiles;
+      if (L[d] > max_Ld) max_Ld = L[d];
+    }
+    if (max_tiles == 0) continue;
+    // shared memory: the largest Ld fixes both TW and the table
+    size_t smem = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const int *L = host_L + 4 * s;
+      const int Ld = L[d];
+      const size_t need = sizeof(double2) * ((size_t)Ld * tile_width(Ld) + Ld);
+      if (need > smem) smem = need;
+    }
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_dft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)max_tiles, nsys, 2);
+    k_dft_pass<<<grid, kDftThreads, smem, st>>>(sys, d);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace lhf

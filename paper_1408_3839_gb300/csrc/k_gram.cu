@@ -1,0 +1,168 @@
+// k_gram.cu -- steps a3 + a4 in FP64: per-direction weighted 1D Grams and P1 forms.
+//
+// For direction l, window block j (displacement), row function mu and column function nu
+// (eq. (3.10) and the proof of Lemma 3.1; Sec. 3.4 for the P1 matrices):
+//   C_r[j][mu][nu] = sum_i g_{mu,j}(i) v_r(i) g_{nu,0}(i)            r < R_tot
+//   K[j][mu][nu]   = g_{mu,j}^T A g_{nu,0},  A = (1/h) tridiag(-1, 2, -1)
+//   M[j][mu][nu]   = g_{mu,j}^T S g_{nu,0},  S = (h/6) tridiag(1, 4, 1)
+// with g_{mu,j}(i) = g_mu(i - j n_c) (the copy in cell j).  In a periodic direction v_r has the
+// period n_c of one cell (the potential is replicated from cell 0, eq. (4.1)), so the sum over
+// the grid folds onto the n_c nodes of one cell:
+//   C_r[j][mu][nu] = sum_c v_r(c) Q_j[mu][nu](c),  Q_j[mu][nu](c) = sum_p g_{mu,j}(c + p n_c) g_nu(c + p n_c)
+// -- the same sum regrouped, exact up to rounding.  The second step is a dense contraction over
+// c of the R_tot potential rows with the m0^2 folded products (a GEMM with K = n_c).
+//
+// One CTA per (system, direction, window block, mu): phase 1 forms Q[nu][c] for all nu in
+// shared memory (only the cells where both supports can be nonzero are visited) together with
+// the P1 sums; phase 2 contracts with the R_tot potential rows.  Deterministic (fixed-order
+// reductions, no atomics).
+#include "lhf_internal.cuh"
+
+namespace lhf {
+namespace {
+
+constexpr int kGramThreads = 256;
+
+struct GramItem {
+  int l, jw, mu;
+};
+
+__device__ __forceinline__ bool decode_gram(const SysDev &s, int b, GramItem &it) {
+  for (int l = 0; l < 3; ++l) {
+    const int cnt = s.d[l].J * s.m0;
+    if (b < cnt) {
+      it.l = l;
+      it.jw = b / s.m0;
+      it.mu = b - it.jw * s.m0;
+      return true;
+    }
+    b -= cnt;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  GramItem it;
+  if (!decode_gram(s, blockIdx.x, it)) return;
+  const DirDev &D = s.d[it.l];
+  const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, L = D.L;
+  const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
+  extern __shared__ double sm[];
+  double *Q = sm;               // [m0][ld]
+  double *E = Q + m0 * ld;      // [m0][ld]  P1 cross terms per node
+  double *red = E + m0 * ld;    // [m0][2]   Dsum, Esum per nu
+  const double *G = s.ws + D.offG;
+  const int mu = it.mu;
+  const int j = D.jlo + it.jw;
+  const double *f = G + (int64_t)mu * n;
+  const int tid = threadIdx.x;
+
+  // support of the shifted row function (cells), tested modulo L
+  const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
+  const int mspan = mhi - mlo;
+  const bool periodic = D.periodic != 0;
+
+  // ---- phase 1: Q[nu][c], E[nu][c] -----------------------------------------------------
+  const int items = m0 * nv;
+  for (int p0 = tid; p0 < items; p0 += kGramThreads) {
+    const int nu = p0 / nv;
+    const int c = p0 - nu * nv;
+    const double *g = G + (int64_t)nu * n;
+    double q = 0.0, e = 0.0;
+    if (periodic) {
+      const int plo = s.cell_lo[it.l][nu];
+      int phi = s.cell_hi[it.l][nu];
+      if (phi > plo + L - 1) phi = plo + L - 1;
+      for (int p = plo; p <= phi; ++p) {
+        if (mspan < L - 1 && wrap(p - mlo, L) > mspan) continue;  // row support absent
+        const int iv = wrap(c + p * nc, n);
+        const int iu = wrap(iv - j * nc, n);
+        const int iv1 = (iv + 1 == n) ? 0 : iv + 1;
+        const int iu1 = (iu + 1 == n) ? 0 : iu + 1;
+        const double fi = f[iu], gi = g[iv];
+        q += fi * gi;
+        e += fi * g[iv1] + f[iu1] * gi;
+      }
+    } else {
+      // single open cell: nodes c = 0..n-1, Dirichlet ends (no wrap)
+      const double fi = f[c], gi = g[c];
+      q = fi * gi;
+      if (c + 1 < n) e = fi * g[c + 1] + f[c + 1] * gi;
+    }
+    Q[nu * ld + c] = q;
+    E[nu * ld + c] = e;
+  }
+  __syncthreads();
+
+  // P1 sums per nu: warp w reduces rows nu = w, w + 8, ... in a fixed order
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
+    double dq = 0.0, de = 0.0;
+    for (int c = lane; c < nv; c += 32) {
+      dq += Q[nu * ld + c];
+      de += E[nu * ld + c];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dq += __shfl_xor_sync(0xffffffffu, dq, o);
+      de += __shfl_xor_sync(0xffffffffu, de, o);
+    }
+    if (lane == 0) {
+      red[2 * nu] = dq;
+      red[2 * nu + 1] = de;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: C_r[nu] = sum_c V[r][c] Q[nu][c] ------------------------------------------
+  const int Rt = s.Rt;
+  const int mm = m0 * m0;
+  double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
+  const double *V = s.ws + D.offV;
+  const int outs = Rt * m0;
+  for (int o = tid; o < outs; o += kGramThreads) {
+    const int r = o / m0;
+    const int nu = o - r * m0;
+    const double *vr = V + (int64_t)r * nv;
+    const double *qn = Q + nu * ld;
+    double acc0 = 0.0, acc1 = 0.0;
+    int c = 0;
+    for (; c + 1 < nv; c += 2) {
+      acc0 += __ldg(vr + c) * qn[c];
+      acc1 += __ldg(vr + c + 1) * qn[c + 1];
+    }
+    if (c < nv) acc0 += __ldg(vr + c) * qn[c];
+    Cout[(int64_t)r * mm + nu] = acc0 + acc1;
+  }
+  if (tid < m0) {
+    const double dq = red[2 * tid], de = red[2 * tid + 1];
+    Cout[(int64_t)Rt * mm + tid] = (2.0 * dq - de) / D.h;
+    Cout[(int64_t)(Rt + 1) * mm + tid] = (4.0 * dq + de) * D.h / 6.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
+                             int max_nv, cudaStream_t st) {
+  if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  dim3 grid(max_blocks, nsys);
+  k_gram_fp64<<<grid, kGramThreads, smem, st>>>(sys);
+  return cudaGetLastError();
+}
+
+}  // namespace lhf

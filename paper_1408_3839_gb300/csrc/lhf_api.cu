@@ -1,0 +1,873 @@
+// lhf_api.cu -- the C ABI of liblhf: descriptor validation, per-system layout (overlap window,
+// workspace offsets), workspace management and the launch sequence of the path
+//   a1 basis -> a2 potential -> a3/a4 Grams -> a5 rank sum (+ a6 zero fill) -> a7 DFT -> a8 eig.
+// Host code only prepares descriptors and launches; every arithmetic step of the path runs in
+// the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lhf_internal.cuh"
+
+using lhf::DirDev;
+using lhf::SysDev;
+
+namespace {
+
+struct HostSystem {
+  int L[3] = {1, 1, 1};
+  double b[3] = {1, 1, 1};
+  int periodic[3] = {0, 0, 0};
+  int K[3] = {1, 1, 1};
+  int M0 = 0;
+  std::vector<double> Z, a, zcell;
+  int m0 = 0;
+  std::vector<int> kind;
+  std::vector<double> alpha, centre;
+  double rho = 40.0;
+  int n[3] = {1, 1, 1}, nc[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1}, x0[3] = {0, 0, 0}, cell0[3] = {0, 0, 0};
+  int R = 0;
+  double u0 = 0, du = 0;
+};
+
+// Sizes of the per-system workspace regions (doubles) and launch extents.
+struct Plan {
+  SysDev sd;
+  size_t ws = 0;       // doubles of G, V, C
+  size_t blocks_doubles = 0;  // nblocks * m0^2
+  int basis_items = 0, pot_items = 0, gram_blocks = 0, rank_items = 0;
+  int nv_max = 0;
+};
+
+constexpr size_t kAlign = 32;  // doubles (256 bytes)
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool finite(double x) { return isfinite(x) != 0; }
+
+}  // namespace
+
+struct lhf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  bool has_lat = false, has_basis = false, has_grid = false;
+  HostSystem cur;
+  double *ws = nullptr;
+  size_t ws_cap = 0;  // doubles
+  SysDev *d_sys = nullptr;
+  size_t d_sys_cap = 0;
+  SysDev *h_sys = nullptr;  // pinned staging
+  size_t h_sys_cap = 0;
+  cudaEvent_t upload_done = nullptr;
+  unsigned *d_flags = nullptr;
+  unsigned long long *d_counters = nullptr;  // [0] Jacobi sweeps, [1] matrices solved
+  double *d_zcell = nullptr;
+  size_t zcell_cap = 0;
+  double *d_out = nullptr;  // device staging of lhf_bloch_spectra_host
+  size_t out_cap = 0;
+  std::vector<int> host_L;
+  // live stage timing
+  bool prof = false;
+  struct Mark {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  Mark open_mark{-1, nullptr, nullptr};
+
+  cudaEvent_t take_event() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  void begin(int stage) {
+    if (!prof) return;
+    open_mark = {stage, take_event(), take_event()};
+    if (open_mark.a) cudaEventRecord(open_mark.a, stream);
+  }
+  void end() {
+    if (!prof || open_mark.stage < 0) return;
+    if (open_mark.b) cudaEventRecord(open_mark.b, stream);
+    if (open_mark.a && open_mark.b) marks.push_back(open_mark);
+    open_mark = {-1, nullptr, nullptr};
+  }
+
+  lhf_status fail(lhf_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return st;
+  }
+  lhf_status cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LHF_OK;
+    return fail(LHF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// validation
+
+lhf_status check_lattice(lhf_ctx *c, const lhf_lattice_desc *d) {
+  if (!d) return c->fail(LHF_ERR_ARG, "lattice descriptor is NULL");
+  for (int l = 0; l < 3; ++l) {
+    if (d->L[l] < 1 || d->L[l] > 4096) return c->fail(LHF_ERR_ARG, "L[%d] = %d outside [1, 4096]", l, d->L[l]);
+    if (!(d->b[l] > 0) || !finite(d->b[l])) return c->fail(LHF_ERR_ARG, "b[%d] must be positive", l);
+    if (d->periodic[l] != 0 && d->periodic[l] != 1) return c->fail(LHF_ERR_ARG, "periodic[%d] must be 0 or 1", l);
+    if (d->periodic[l] && (d->K_sum[l] < 1 || d->K_sum[l] > 1 << 20))
+      return c->fail(LHF_ERR_ARG, "K_sum[%d] = %d must be >= 1", l, d->K_sum[l]);
+  }
+  if (d->M0 < 1 || d->M0 > LHF_MAX_NUCLEI) return c->fail(LHF_ERR_ARG, "M0 = %d outside [1, %d]", d->M0, LHF_MAX_NUCLEI);
+  if (!d->Z || !d->a) return c->fail(LHF_ERR_ARG, "Z and a must be given");
+  for (int nu = 0; nu < d->M0; ++nu) {
+    if (!(d->Z[nu] > 0) || !finite(d->Z[nu])) return c->fail(LHF_ERR_ARG, "Z[%d] must be positive", nu);
+    for (int l = 0; l < 3; ++l)
+      if (!finite(d->a[3 * nu + l])) return c->fail(LHF_ERR_ARG, "a[%d][%d] not finite", nu, l);
+  }
+  if (d->Z_cell) {
+    if (d->L[1] != 1 || d->L[2] != 1 || d->periodic[0])
+      return c->fail(LHF_ERR_UNSUPPORTED, "per-cell charges need an open box with lattice direction 0 only");
+    for (int k = 0; k < d->L[0] * d->M0; ++k)
+      if (!(d->Z_cell[k] >= 0) || !finite(d->Z_cell[k])) return c->fail(LHF_ERR_ARG, "Z_cell[%d] must be >= 0", k);
+  }
+  return LHF_OK;
+}
+
+lhf_status check_basis(lhf_ctx *c, const lhf_basis_desc *d) {
+  if (!d) return c->fail(LHF_ERR_ARG, "basis descriptor is NULL");
+  if (d->m0 < 1 || d->m0 > LHF_MAX_M0) return c->fail(LHF_ERR_ARG, "m0 = %d outside [1, %d]", d->m0, LHF_MAX_M0);
+  if (!d->kind || !d->alpha || !d->centre) return c->fail(LHF_ERR_ARG, "kind, alpha and centre must be given");
+  if (!(d->rho > 0) || !finite(d->rho)) return c->fail(LHF_ERR_ARG, "rho must be positive");
+  for (int mu = 0; mu < d->m0; ++mu) {
+    if (d->kind[mu] < 0 || d->kind[mu] > 3) return c->fail(LHF_ERR_ARG, "kind[%d] = %d outside [0, 3]", mu, d->kind[mu]);
+    if (!(d->alpha[mu] > 0) || !finite(d->alpha[mu])) return c->fail(LHF_ERR_ARG, "alpha[%d] must be positive", mu);
+    for (int l = 0; l < 3; ++l)
+      if (!finite(d->centre[3 * mu + l])) return c->fail(LHF_ERR_ARG, "centre[%d][%d] not finite", mu, l);
+  }
+  return LHF_OK;
+}
+
+lhf_status check_grid(lhf_ctx *c, const lhf_grid_desc *d) {
+  if (!d) return c->fail(LHF_ERR_ARG, "grid descriptor is NULL");
+  for (int l = 0; l < 3; ++l) {
+    if (d->n[l] < 1 || d->n[l] > (1 << 24)) return c->fail(LHF_ERR_ARG, "n[%d] = %d invalid", l, d->n[l]);
+    if (d->n_cell[l] < 1) return c->fail(LHF_ERR_ARG, "n_cell[%d] = %d invalid", l, d->n_cell[l]);
+    if (!(d->h[l] > 0) || !finite(d->h[l])) return c->fail(LHF_ERR_ARG, "h[%d] must be positive", l);
+    if (!finite(d->x0[l]) || !finite(d->cell0[l])) return c->fail(LHF_ERR_ARG, "x0/cell0[%d] not finite", l);
+  }
+  if (d->R < 1 || d->R > LHF_MAX_R) return c->fail(LHF_ERR_ARG, "R = %d outside [1, %d]", d->R, LHF_MAX_R);
+  if (!(d->du > 0) || !finite(d->du) || !finite(d->u0)) return c->fail(LHF_ERR_ARG, "sinc parameters invalid");
+  return LHF_OK;
+}
+
+void copy_lattice(HostSystem &s, const lhf_lattice_desc *d) {
+  for (int l = 0; l < 3; ++l) {
+    s.L[l] = d->L[l];
+    s.b[l] = d->b[l];
+    s.periodic[l] = d->periodic[l];
+    s.K[l] = d->periodic[l] ? d->K_sum[l] : 1;
+  }
+  s.M0 = d->M0;
+  s.Z.assign(d->Z, d->Z + d->M0);
+  s.a.assign(d->a, d->a + 3 * d->M0);
+  if (d->Z_cell)
+    s.zcell.assign(d->Z_cell, d->Z_cell + (size_t)d->L[0] * d->M0);
+  else
+    s.zcell.clear();
+}
+
+void copy_basis(HostSystem &s, const lhf_basis_desc *d) {
+  s.m0 = d->m0;
+  s.kind.assign(d->kind, d->kind + d->m0);
+  s.alpha.assign(d->alpha, d->alpha + d->m0);
+  s.centre.assign(d->centre, d->centre + 3 * d->m0);
+  s.rho = d->rho;
+}
+
+void copy_grid(HostSystem &s, const lhf_grid_desc *d) {
+  for (int l = 0; l < 3; ++l) {
+    s.n[l] = d->n[l];
+    s.nc[l] = d->n_cell[l];
+    s.h[l] = d->h[l];
+    s.x0[l] = d->x0[l];
+    s.cell0[l] = d->cell0[l];
+  }
+  s.R = d->R;
+  s.u0 = d->u0;
+  s.du = d->du;
+}
+
+// Consistency of the three parts; fills the plan (descriptor, window, workspace sizes).
+lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
+  SysDev &sd = P.sd;
+  memset(&sd, 0, sizeof sd);
+  if (s.M0 * s.R > lhf::kMaxRt) return c->fail(LHF_ERR_ARG, "M0 R = %d exceeds %d", s.M0 * s.R, lhf::kMaxRt);
+  int open_lattice = 0;
+  for (int l = 0; l < 3; ++l) {
+    const bool lat = s.L[l] > 1 || s.periodic[l];
+    if (s.periodic[l]) {
+      if ((long long)s.L[l] * s.nc[l] != s.n[l])
+        return c->fail(LHF_ERR_ARG, "direction %d: n = %d must equal L n_cell = %d", l, s.n[l], s.L[l] * s.nc[l]);
+      if (fabs(s.nc[l] * s.h[l] - s.b[l]) > 1e-9 * s.b[l])
+        return c->fail(LHF_ERR_ARG, "direction %d: n_cell h = %.17g must equal b = %.17g", l, s.nc[l] * s.h[l], s.b[l]);
+      if (fabs(s.x0[l] - s.cell0[l]) > 1e-12 * s.b[l])
+        return c->fail(LHF_ERR_ARG, "direction %d: periodic grid must start at cell0", l);
+    } else if (lat) {
+      open_lattice |= 1 << l;
+      if (fabs(s.nc[l] * s.h[l] - s.b[l]) > 1e-9 * s.b[l])
+        return c->fail(LHF_ERR_ARG, "direction %d: n_cell h must equal b", l);
+    }
+  }
+  if (open_lattice) {
+    return c->fail(LHF_ERR_UNSUPPORTED, "open boxes with L > 1 are not supported by this build");
+  }
+  if (!s.zcell.empty()) return c->fail(LHF_ERR_UNSUPPORTED, "per-cell charges need an open box");
+
+  const int m0 = s.m0, Rt = s.M0 * s.R, mm = m0 * m0;
+  sd.m0 = m0;
+  sd.M0 = s.M0;
+  sd.R = s.R;
+  sd.Rt = Rt;
+  sd.box = 0;
+  for (int mu = 0; mu < m0; ++mu) {
+    sd.kind[mu] = s.kind[mu];
+    sd.alpha[mu] = s.alpha[mu];
+    for (int l = 0; l < 3; ++l) sd.centre[mu][l] = s.centre[3 * mu + l];
+    sd.cut[mu] = sqrt(s.rho / s.alpha[mu]);
+    sd.pnorm[mu] = sqrt(2.0 * s.alpha[mu] * exp(1.0));
+  }
+  for (int nu = 0; nu < s.M0; ++nu) {
+    sd.Z[nu] = s.Z[nu];
+    for (int l = 0; l < 3; ++l) sd.a[nu][l] = s.a[3 * nu + l];
+  }
+  // sinc nodes and weights (eq. (3.6)): t_q = exp(u0 + q du), w_q = 2/sqrt(pi) du t_q, the
+  // nodes below u0 folded into w_0 (geometric tail)
+  double w[lhf::kMaxR];
+  for (int q = 0; q < s.R; ++q) {
+    sd.t[q] = exp(s.u0 + q * s.du);
+    w[q] = 2.0 / sqrt(M_PI) * s.du * sd.t[q];
+  }
+  w[0] = w[0] / (1.0 - exp(-s.du));
+  for (int nu = 0; nu < s.M0; ++nu)
+    for (int q = 0; q < s.R; ++q) sd.c[nu * s.R + q] = s.Z[nu] * w[q];
+
+  size_t off = 0;
+  P.basis_items = P.pot_items = P.gram_blocks = 0;
+  P.nv_max = 0;
+  sd.nwin = 1;
+  sd.nblocks = 1;
+  for (int l = 0; l < 3; ++l) {
+    DirDev &D = sd.d[l];
+    D.L = s.L[l];
+    D.n = s.n[l];
+    D.periodic = s.periodic[l];
+    D.lattice = (s.L[l] > 1 || s.periodic[l]) ? 1 : 0;
+    D.nc = D.lattice ? s.nc[l] : s.n[l];
+    D.nv = D.periodic ? D.nc : D.n;
+    D.K = s.K[l];
+    D.h = s.h[l];
+    D.x0 = s.x0[l];
+    D.cell0 = s.cell0[l];
+    D.b = s.b[l];
+    // support cells of each cell-0 basis copy, dilated by one node for the P1 cross terms
+    for (int mu = 0; mu < m0; ++mu) {
+      if (D.lattice) {
+        const double A = s.centre[3 * mu + l], cut = sd.cut[mu];
+        sd.cell_lo[l][mu] = (int)floor((A - cut - D.h - D.cell0) / D.b);
+        sd.cell_hi[l][mu] = (int)floor((A + cut + D.h - D.cell0) / D.b);
+      } else {
+        sd.cell_lo[l][mu] = sd.cell_hi[l][mu] = 0;
+      }
+    }
+    // overlap window of displacements j: blocks outside are exact zeros
+    if (D.periodic) {
+      int jmin = 1 << 30, jmax = -(1 << 30);
+      for (int mu = 0; mu < m0; ++mu)
+        for (int nu = 0; nu < m0; ++nu) {
+          jmin = std::min(jmin, sd.cell_lo[l][nu] - sd.cell_hi[l][mu]);
+          jmax = std::max(jmax, sd.cell_hi[l][nu] - sd.cell_lo[l][mu]);
+        }
+      if ((long long)jmax - jmin + 1 >= D.L) {
+        D.jlo = 0;
+        D.J = D.L;
+      } else {
+        D.jlo = jmin;
+        D.J = jmax - jmin + 1;
+      }
+    } else {
+      D.jlo = 0;
+      D.J = 1;
+    }
+    sd.nwin *= D.J;
+    sd.nblocks *= D.L;
+    P.basis_items += m0 * D.n;
+    P.pot_items += Rt * D.nv;
+    P.gram_blocks += D.J * m0;
+    P.nv_max = std::max(P.nv_max, D.nv);
+  }
+  for (int l = 0; l < 3; ++l) {
+    sd.d[l].offG = (int64_t)off;
+    off = align_up(off + (size_t)m0 * sd.d[l].n);
+  }
+  for (int l = 0; l < 3; ++l) {
+    sd.d[l].offV = (int64_t)off;
+    off = align_up(off + (size_t)Rt * sd.d[l].nv);
+  }
+  for (int l = 0; l < 3; ++l) {
+    sd.d[l].offC = (int64_t)off;
+    off = align_up(off + (size_t)sd.d[l].J * (Rt + 2) * mm);
+  }
+  P.ws = off;
+  P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
+  P.rank_items = sd.nwin * mm;
+  if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
+  return LHF_OK;
+}
+
+lhf_status current_plan(lhf_ctx *c, Plan &P) {
+  if (!c->has_lat || !c->has_basis || !c->has_grid)
+    return c->fail(LHF_ERR_STATE, "lattice, basis and grid setup must precede this call");
+  return make_plan(c, c->cur, P);
+}
+
+lhf_status ensure_ws(lhf_ctx *c, size_t doubles) {
+  if (doubles <= c->ws_cap) return LHF_OK;
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  if (c->ws) cudaFree(c->ws);
+  c->ws = nullptr;
+  c->ws_cap = 0;
+  size_t want = std::max(doubles, c->ws_cap + c->ws_cap / 4);
+  cudaError_t e = cudaMalloc(&c->ws, want * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&c->ws, doubles * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return c->fail(LHF_ERR_NOMEM, "workspace of %zu bytes: %s", doubles * sizeof(double), cudaGetErrorString(e));
+    }
+    want = doubles;
+  }
+  c->ws_cap = want;
+  return LHF_OK;
+}
+
+// Copy nsys descriptors to the device through the pinned staging buffer.
+lhf_status upload(lhf_ctx *c, const std::vector<SysDev> &v) {
+  const size_t n = v.size();
+  lhf_status st;
+  if (c->upload_done) {
+    st = c->cuda(cudaEventSynchronize(c->upload_done), "cudaEventSynchronize");
+    if (st != LHF_OK) return st;
+  }
+  if (n > c->h_sys_cap) {
+    if (c->h_sys) cudaFreeHost(c->h_sys);
+    c->h_sys = nullptr;
+    st = c->cuda(cudaMallocHost(&c->h_sys, n * sizeof(SysDev)), "cudaMallocHost");
+    if (st != LHF_OK) return st;
+    c->h_sys_cap = n;
+  }
+  if (n > c->d_sys_cap) {
+    st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (st != LHF_OK) return st;
+    if (c->d_sys) cudaFree(c->d_sys);
+    c->d_sys = nullptr;
+    st = c->cuda(cudaMalloc(&c->d_sys, n * sizeof(SysDev)), "cudaMalloc");
+    if (st != LHF_OK) return st;
+    c->d_sys_cap = n;
+  }
+  memcpy(c->h_sys, v.data(), n * sizeof(SysDev));
+  c->begin(7);
+  st = c->cuda(cudaMemcpyAsync(c->d_sys, c->h_sys, n * sizeof(SysDev), cudaMemcpyHostToDevice, c->stream),
+               "cudaMemcpyAsync");
+  c->end();
+  if (st != LHF_OK) return st;
+  return c->cuda(cudaEventRecord(c->upload_done, c->stream), "cudaEventRecord");
+}
+
+int max_of(const std::vector<Plan> &ps, int Plan::*f) {
+  int m = 0;
+  for (const Plan &p : ps) m = std::max(m, p.*f);
+  return m;
+}
+
+// Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
+lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
+  const int nsys = (int)ps.size();
+  // a6: blocks outside the window are exact zeros
+  for (const Plan &p : ps)
+    if (p.sd.nwin < p.sd.nblocks) {
+      const size_t bytes = (size_t)p.sd.nblocks * p.sd.m0 * p.sd.m0 * sizeof(double);
+      c->begin(6);
+      lhf_status st = c->cuda(cudaMemsetAsync(p.sd.H, 0, bytes, c->stream), "cudaMemsetAsync");
+      if (st != LHF_OK) return st;
+      st = c->cuda(cudaMemsetAsync(p.sd.S, 0, bytes, c->stream), "cudaMemsetAsync");
+      c->end();
+      if (st != LHF_OK) return st;
+    }
+  lhf_status st;
+  c->begin(0);
+  st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(1);
+  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  int max_m0 = 0;
+  for (const Plan &p : ps) max_m0 = std::max(max_m0, p.sd.m0);
+  c->begin(2);
+  st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
+                                     max_of(ps, &Plan::nv_max), c->stream),
+               "Gram kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(3);
+  st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, &Plan::rank_items), c->stream), "rank-sum kernel");
+  c->end();
+  return st;
+}
+
+lhf_status run_dft(lhf_ctx *c, const std::vector<Plan> &ps) {
+  c->host_L.resize(4 * ps.size());
+  for (size_t i = 0; i < ps.size(); ++i) {
+    for (int l = 0; l < 3; ++l) c->host_L[4 * i + l] = ps[i].sd.d[l].L;
+    c->host_L[4 * i + 3] = ps[i].sd.m0;
+  }
+  c->begin(4);
+  lhf_status st = c->cuda(lhf::launch_dft(c->d_sys, (int)ps.size(), c->host_L.data(), 0, c->stream), "DFT kernel");
+  c->end();
+  return st;
+}
+
+lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
+  int max_k = 0, max_m0 = 0;
+  for (const Plan &p : ps) {
+    max_k = std::max(max_k, p.sd.nblocks);
+    max_m0 = std::max(max_m0, p.sd.m0);
+  }
+  c->begin(5);
+  lhf_status st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream), "eigen kernel");
+  c->end();
+  return st;
+}
+
+lhf_status system_from_desc(lhf_ctx *c, const lhf_system_desc *d, HostSystem &s) {
+  lhf_status st = check_lattice(c, &d->lattice);
+  if (st != LHF_OK) return st;
+  st = check_basis(c, &d->basis);
+  if (st != LHF_OK) return st;
+  st = check_grid(c, &d->grid);
+  if (st != LHF_OK) return st;
+  copy_lattice(s, &d->lattice);
+  copy_basis(s, &d->basis);
+  copy_grid(s, &d->grid);
+  return LHF_OK;
+}
+
+// Plan one system with workspace at ws_base and internal H, S, Hbar, Sbar after its factors.
+size_t internal_doubles(const Plan &p) { return p.ws + 6 * p.blocks_doubles; }
+
+void place_internal(Plan &p, double *base) {
+  p.sd.ws = base;
+  double *blk = base + p.ws;
+  p.sd.H = blk;
+  p.sd.S = blk + p.blocks_doubles;
+  p.sd.Hbar = blk + 2 * p.blocks_doubles;
+  p.sd.Sbar = blk + 4 * p.blocks_doubles;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+
+extern "C" {
+
+lhf_status lhf_create(lhf_ctx **out, int device, void *stream) {
+  if (!out) return LHF_ERR_ARG;
+  *out = nullptr;
+  lhf_ctx *c = new (std::nothrow) lhf_ctx();
+  if (!c) return LHF_ERR_NOMEM;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return LHF_ERR_CUDA;
+  }
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaSetDevice(device) != cudaSuccess || cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->upload_done) cudaEventDestroy(c->upload_done);
+    if (c->d_flags) cudaFree(c->d_flags);
+    if (c->d_counters) cudaFree(c->d_counters);
+    delete c;
+    return LHF_ERR_CUDA;
+  }
+  *out = c;
+  return LHF_OK;
+}
+
+void lhf_destroy(lhf_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->d_sys) cudaFree(c->d_sys);
+  if (c->h_sys) cudaFreeHost(c->h_sys);
+  if (c->d_flags) cudaFree(c->d_flags);
+  if (c->d_counters) cudaFree(c->d_counters);
+  if (c->d_zcell) cudaFree(c->d_zcell);
+  if (c->d_out) cudaFree(c->d_out);
+  if (c->upload_done) cudaEventDestroy(c->upload_done);
+  for (auto &m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+lhf_status lhf_eig_counters(lhf_ctx *c, unsigned long long *sweeps, unsigned long long *matrices) {
+  if (!c || !sweeps || !matrices) return LHF_ERR_ARG;
+  unsigned long long h[2] = {0, 0};
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  st = c->cuda(cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (st != LHF_OK) return st;
+  st = c->cuda(cudaMemset(c->d_counters, 0, sizeof h), "cudaMemset");
+  *sweeps = h[0];
+  *matrices = h[1];
+  return st;
+}
+
+lhf_status lhf_set_profiling(lhf_ctx *c, int enable) {
+  if (!c) return LHF_ERR_ARG;
+  c->prof = enable != 0;
+  return LHF_OK;
+}
+
+lhf_status lhf_stage_times(lhf_ctx *c, double *ms, int *launches) {
+  if (!c || !ms || !launches) return LHF_ERR_ARG;
+  for (int i = 0; i < LHF_NUM_STAGES; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  for (auto &m : c->marks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess && m.stage >= 0 && m.stage < LHF_NUM_STAGES) {
+      ms[m.stage] += t;
+      launches[m.stage] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->marks.clear();
+  return LHF_OK;
+}
+
+const char *lhf_last_error(const lhf_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+lhf_status lhf_set_stream(lhf_ctx *c, void *stream) {
+  if (!c) return LHF_ERR_ARG;
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  c->stream = (cudaStream_t)stream;
+  return LHF_OK;
+}
+
+lhf_status lhf_sync(lhf_ctx *c) {
+  if (!c) return LHF_ERR_ARG;
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  unsigned flags = 0;
+  st = c->cuda(cudaMemcpy(&flags, c->d_flags, sizeof flags, cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (st != LHF_OK) return st;
+  st = c->cuda(cudaMemset(c->d_flags, 0, sizeof(unsigned)), "cudaMemset");
+  if (st != LHF_OK) return st;
+  if (flags & lhf::kFlagNotSpd) return c->fail(LHF_ERR_NOT_SPD, "an overlap block was not positive definite");
+  return LHF_OK;
+}
+
+lhf_status lhf_lattice_setup(lhf_ctx *c, const lhf_lattice_desc *d) {
+  if (!c) return LHF_ERR_ARG;
+  lhf_status st = check_lattice(c, d);
+  if (st != LHF_OK) return st;
+  copy_lattice(c->cur, d);
+  c->has_lat = true;
+  return LHF_OK;
+}
+
+lhf_status lhf_basis_setup(lhf_ctx *c, const lhf_basis_desc *d) {
+  if (!c) return LHF_ERR_ARG;
+  lhf_status st = check_basis(c, d);
+  if (st != LHF_OK) return st;
+  copy_basis(c->cur, d);
+  c->has_basis = true;
+  return LHF_OK;
+}
+
+lhf_status lhf_grid_setup(lhf_ctx *c, const lhf_grid_desc *d) {
+  if (!c) return LHF_ERR_ARG;
+  lhf_status st = check_grid(c, d);
+  if (st != LHF_OK) return st;
+  copy_grid(c->cur, d);
+  c->has_grid = true;
+  return LHF_OK;
+}
+
+lhf_status lhf_query_sizes(lhf_ctx *c, lhf_sizes *out) {
+  if (!c || !out) return LHF_ERR_ARG;
+  Plan P;
+  lhf_status st = current_plan(c, P);
+  if (st != LHF_OK) return st;
+  memset(out, 0, sizeof *out);
+  out->m0 = P.sd.m0;
+  out->n_blocks = P.sd.nblocks;
+  out->n_kpoints = P.sd.nblocks;
+  out->n_basis = P.sd.m0 * P.sd.nblocks;
+  out->rank = P.sd.Rt;
+  out->periodic = P.sd.box ? 0 : 1;
+  for (int l = 0; l < 3; ++l) {
+    out->window[l] = P.sd.d[l].J;
+    out->n_potential[l] = P.sd.d[l].nv;
+  }
+  return LHF_OK;
+}
+
+static lhf_status check_precision(lhf_ctx *c, lhf_precision p) {
+  if (p == LHF_FP64) return LHF_OK;
+  if (p == LHF_MIXED) return c->fail(LHF_ERR_UNSUPPORTED, "mixed precision is not available in this build");
+  return c->fail(LHF_ERR_ARG, "unknown precision %d", (int)p);
+}
+
+lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *c, lhf_precision prec, double *H, double *S) {
+  if (!c) return LHF_ERR_ARG;
+  if (!H || !S) return c->fail(LHF_ERR_ARG, "H and S must be device pointers");
+  lhf_status st = check_precision(c, prec);
+  if (st != LHF_OK) return st;
+  std::vector<Plan> ps(1);
+  st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  ps[0].sd.ws = c->ws;
+  ps[0].sd.H = H;
+  ps[0].sd.S = S;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  return run_assembly(c, ps);
+}
+
+lhf_status lhf_circulant_fft(lhf_ctx *c, const double *H, const double *S, double *Hbar, double *Sbar) {
+  if (!c) return LHF_ERR_ARG;
+  if (!H || !S || !Hbar || !Sbar) return c->fail(LHF_ERR_ARG, "all four pointers are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  ps[0].sd.H = const_cast<double *>(H);
+  ps[0].sd.S = const_cast<double *>(S);
+  ps[0].sd.Hbar = Hbar;
+  ps[0].sd.Sbar = Sbar;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  return run_dft(c, ps);
+}
+
+lhf_status lhf_k_point_eigensolve(lhf_ctx *c, const double *Hbar, const double *Sbar, double *eig, int *kstat) {
+  if (!c) return LHF_ERR_ARG;
+  if (!Hbar || !Sbar || !eig) return c->fail(LHF_ERR_ARG, "Hbar, Sbar and eig are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  ps[0].sd.Hbar = const_cast<double *>(Hbar);
+  ps[0].sd.Sbar = const_cast<double *>(Sbar);
+  ps[0].sd.eig = eig;
+  ps[0].sd.kstat = kstat;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  return run_eig(c, ps);
+}
+
+lhf_status lhf_dense_eigensolve(lhf_ctx *c, const double *H, const double *S, int N, double *eig) {
+  if (!c) return LHF_ERR_ARG;
+  (void)H;
+  (void)S;
+  (void)N;
+  (void)eig;
+  return c->fail(LHF_ERR_UNSUPPORTED, "dense eigensolver not available in this build");
+}
+
+lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,
+                             double *eig, int *kstat) {
+  if (!c) return LHF_ERR_ARG;
+  if (nsys < 1 || !systems || !eig) return c->fail(LHF_ERR_ARG, "nsys >= 1, systems and eig are required");
+  lhf_status st = check_precision(c, prec);
+  if (st != LHF_OK) return st;
+  std::vector<Plan> ps(nsys);
+  size_t total = 0;
+  for (int i = 0; i < nsys; ++i) {
+    HostSystem hs;
+    st = system_from_desc(c, &systems[i], hs);
+    if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
+    st = make_plan(c, hs, ps[i]);
+    if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
+    total += internal_doubles(ps[i]);
+  }
+  st = ensure_ws(c, total);
+  if (st != LHF_OK) return st;
+  size_t base = 0, eoff = 0, koff = 0;
+  std::vector<SysDev> sds(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    place_internal(ps[i], c->ws + base);
+    base += internal_doubles(ps[i]);
+    ps[i].sd.eig = eig + eoff;                  // [n_kpoints][m0] per system
+    ps[i].sd.kstat = kstat ? kstat + koff : nullptr;  // [n_kpoints] per system
+    eoff += (size_t)ps[i].sd.nblocks * ps[i].sd.m0;
+    koff += ps[i].sd.nblocks;
+    sds[i] = ps[i].sd;
+  }
+  st = upload(c, sds);
+  if (st != LHF_OK) return st;
+  st = run_assembly(c, ps);
+  if (st != LHF_OK) return st;
+  st = run_dft(c, ps);
+  if (st != LHF_OK) return st;
+  return run_eig(c, ps);
+}
+
+lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,
+                                  double *eig_host, int *kstat_host) {
+  if (!c) return LHF_ERR_ARG;
+  if (nsys < 1 || !systems || !eig_host) return c->fail(LHF_ERR_ARG, "nsys >= 1, systems and eig_host are required");
+  // count outputs first
+  size_t neig = 0, nk = 0;
+  for (int i = 0; i < nsys; ++i) {
+    HostSystem hs;
+    lhf_status st = system_from_desc(c, &systems[i], hs);
+    if (st != LHF_OK) return st;
+    Plan p;
+    st = make_plan(c, hs, p);
+    if (st != LHF_OK) return st;
+    neig += (size_t)p.sd.nblocks * p.sd.m0;
+    nk += p.sd.nblocks;
+  }
+  const size_t need = align_up(neig) + (nk + 1) / 2 + 1;
+  if (need > c->out_cap) {
+    lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (st != LHF_OK) return st;
+    if (c->d_out) cudaFree(c->d_out);
+    c->d_out = nullptr;
+    c->out_cap = 0;
+    st = c->cuda(cudaMalloc(&c->d_out, need * sizeof(double)), "cudaMalloc");
+    if (st != LHF_OK) return st;
+    c->out_cap = need;
+  }
+  double *d_out = c->d_out;
+  int *d_k = reinterpret_cast<int *>(d_out + align_up(neig));
+  lhf_status st = lhf_bloch_spectra(c, nsys, systems, prec, d_out, d_k);
+  if (st != LHF_OK) return st;
+  st = c->cuda(cudaMemcpyAsync(eig_host, d_out, neig * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (st != LHF_OK) return st;
+  if (kstat_host) {
+    st = c->cuda(cudaMemcpyAsync(kstat_host, d_k, nk * sizeof(int), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (st != LHF_OK) return st;
+  }
+  return c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+lhf_status lhf_basis_factors(lhf_ctx *c, int l, double *G) {
+  if (!c) return LHF_ERR_ARG;
+  if (l < 0 || l > 2 || !G) return c->fail(LHF_ERR_ARG, "direction 0..2 and an output pointer are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  ps[0].sd.ws = c->ws;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
+  if (st != LHF_OK) return st;
+  const DirDev &D = ps[0].sd.d[l];
+  return c->cuda(cudaMemcpyAsync(G, c->ws + D.offG, sizeof(double) * (size_t)ps[0].sd.m0 * D.n,
+                                 cudaMemcpyDeviceToDevice, c->stream),
+                 "cudaMemcpyAsync");
+}
+
+lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
+  if (!c) return LHF_ERR_ARG;
+  if (l < 0 || l > 2 || !V) return c->fail(LHF_ERR_ARG, "direction 0..2 and an output pointer are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  ps[0].sd.ws = c->ws;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
+  if (st != LHF_OK) return st;
+  const DirDev &D = ps[0].sd.d[l];
+  return c->cuda(cudaMemcpyAsync(V, c->ws + D.offV, sizeof(double) * (size_t)ps[0].sd.Rt * D.nv,
+                                 cudaMemcpyDeviceToDevice, c->stream),
+                 "cudaMemcpyAsync");
+}
+
+lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, int *jlo) {
+  if (!c) return LHF_ERR_ARG;
+  if (l < 0 || l > 2 || !C) return c->fail(LHF_ERR_ARG, "direction 0..2 and an output pointer are required");
+  lhf_status st = check_precision(c, prec);
+  if (st != LHF_OK) return st;
+  std::vector<Plan> ps(1);
+  st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  ps[0].sd.ws = c->ws;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
+  if (st != LHF_OK) return st;
+  st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
+  if (st != LHF_OK) return st;
+  st = c->cuda(lhf::launch_gram_fp64(c->d_sys, 1, ps[0].gram_blocks, ps[0].sd.m0, ps[0].nv_max, c->stream),
+               "Gram kernel");
+  if (st != LHF_OK) return st;
+  const DirDev &D = ps[0].sd.d[l];
+  if (jlo) *jlo = D.jlo;
+  const size_t mm = (size_t)ps[0].sd.m0 * ps[0].sd.m0;
+  return c->cuda(cudaMemcpyAsync(C, c->ws + D.offC, sizeof(double) * (size_t)D.J * (ps[0].sd.Rt + 2) * mm,
+                                 cudaMemcpyDeviceToDevice, c->stream),
+                 "cudaMemcpyAsync");
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// lhf_internal.cuh -- device-side system descriptors and kernel entry points of liblhf.
+//
+// Every kernel works on a batch of systems: blockIdx.y (or the decoded work item) selects the
+// system, whose descriptor SysDev lives in device memory.  One system is a batch of one.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lhf.h"
+
+namespace lhf {
+
+constexpr int kMaxM0 = LHF_MAX_M0;
+constexpr int kMaxNuc = LHF_MAX_NUCLEI;
+constexpr int kMaxR = LHF_MAX_R;
+constexpr int kMaxRt = kMaxNuc * kMaxR;
+
+// One direction of one system.
+struct DirDev {
+  int L;          // cells
+  int n;          // grid nodes
+  int nc;         // nodes per lattice cell (n for a single-cell open direction)
+  int nv;         // potential factor length: nc (periodic, replicated per cell) or n
+  int periodic;   // block-circulant direction
+  int lattice;    // L > 1 or periodic: basis copies shifted by k b
+  int K;          // periodic image window
+  int J;          // window blocks computed (<= L)
+  int jlo;        // first displacement of the window (may be negative; blocks taken mod L)
+  int pad_;
+  double h, x0, cell0, b;
+  int64_t offG;   // basis samples [m0][n]          (doubles, from SysDev::ws)
+  int64_t offV;   // potential factors [Rt][nv]
+  int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
+};
+
+struct SysDev {
+  DirDev d[3];
+  int m0, M0, R, Rt;
+  int nblocks;     // L0 L1 L2
+  int nwin;        // J0 J1 J2
+  int box;         // open lattice direction 0 (dense matrices)
+  int nkhalf;      // k-points solved (the rest are complex conjugates)
+  int kind[kMaxM0];
+  double alpha[kMaxM0];
+  double centre[kMaxM0][3];
+  double cut[kMaxM0];     // truncation radius sqrt(rho / alpha)
+  double pnorm[kMaxM0];   // sqrt(2 alpha e)
+  int cell_lo[3][kMaxM0]; // support cells of the cell-0 copy (unwrapped, dilated by one node)
+  int cell_hi[3][kMaxM0];
+  double Z[kMaxNuc];
+  double a[kMaxNuc][3];
+  double t[kMaxR];        // sinc nodes
+  double c[kMaxRt];       // rank coefficients Z_nu w_q, r = nu R + q
+  double *ws;             // workspace of this system
+  double *H, *S;          // first block column [L0][L1][L2][m0][m0] (or dense [Nb][Nb])
+  double *Hbar, *Sbar;    // complex [L0][L1][L2][m0][m0][2]
+  double *eig;            // [nblocks][m0]
+  int *kstat;             // [nblocks] or null
+  const double *zcell;    // box charges [L0][M0] (device) or null
+};
+
+// Per-launch status word written by kernels (atomicOr of flag bits).
+enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u };
+
+// ---- kernel launchers (each returns the launch error) ------------------------------------
+cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+cudaError_t launch_potential(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
+                             int max_nv, cudaStream_t st);
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int max_lines,
+                       cudaStream_t st);
+cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                       unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *eig,
+                             double *work, unsigned *flags, cudaStream_t st);
+size_t dense_eig_workspace_doubles(int N);
+
+}  // namespace lhf

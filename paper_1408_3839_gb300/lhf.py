@@ -1,0 +1,303 @@
+"""Thin ctypes binding of liblhf.so (include/lhf.h).  Argument marshalling only: every step of
+the path runs in the library's CUDA kernels.  Device buffers are passed as torch CUDA tensors
+(or raw integer device pointers); the library never allocates them.  Loading fails loudly when
+the library is missing: there is no fallback."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "liblhf.so"
+
+LHF_OK = 0
+LHF_ERR_ARG = -1
+LHF_ERR_CUDA = -2
+LHF_ERR_NOT_SPD = -3
+LHF_ERR_TIMEOUT = -4
+LHF_ERR_UNSUPPORTED = -5
+LHF_ERR_STATE = -6
+LHF_ERR_NOMEM = -7
+
+FP64 = 0
+MIXED = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class lhf_lattice_desc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 3), ("b", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3),
+                ("K_sum", ctypes.c_int * 3), ("M0", ctypes.c_int), ("Z", _dp), ("a", _dp),
+                ("Z_cell", _dp)]
+
+
+class lhf_basis_desc(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_int), ("kind", _ip), ("alpha", _dp), ("centre", _dp),
+                ("rho", ctypes.c_double)]
+
+
+class lhf_grid_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("n_cell", ctypes.c_int * 3), ("h", ctypes.c_double * 3),
+                ("x0", ctypes.c_double * 3), ("cell0", ctypes.c_double * 3), ("R", ctypes.c_int),
+                ("u0", ctypes.c_double), ("du", ctypes.c_double)]
+
+
+class lhf_system_desc(ctypes.Structure):
+    _fields_ = [("lattice", lhf_lattice_desc), ("basis", lhf_basis_desc), ("grid", lhf_grid_desc)]
+
+
+class lhf_sizes(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_int), ("n_blocks", ctypes.c_int), ("n_kpoints", ctypes.c_int),
+                ("n_basis", ctypes.c_int), ("rank", ctypes.c_int), ("window", ctypes.c_int * 3),
+                ("n_potential", ctypes.c_int * 3), ("periodic", ctypes.c_int)]
+
+
+class LhfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"liblhf status {status}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(HERE, _LIB_NAME)
+
+
+def load():
+    """Load liblhf.so (built by paper_1408_3839_gb300.build).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run `python -m paper_1408_3839_gb300.build` "
+                               "(the CUDA library is required; there is no CPU path)")
+        lib = ctypes.CDLL(path)
+        ctx = ctypes.c_void_p
+        S = ctypes.POINTER(lhf_system_desc)
+        st = ctypes.c_int
+        sig = {
+            "lhf_create": (st, [ctypes.POINTER(ctx), ctypes.c_int, ctypes.c_void_p]),
+            "lhf_destroy": (None, [ctx]),
+            "lhf_last_error": (ctypes.c_char_p, [ctx]),
+            "lhf_set_stream": (st, [ctx, ctypes.c_void_p]),
+            "lhf_sync": (st, [ctx]),
+            "lhf_lattice_setup": (st, [ctx, ctypes.POINTER(lhf_lattice_desc)]),
+            "lhf_basis_setup": (st, [ctx, ctypes.POINTER(lhf_basis_desc)]),
+            "lhf_grid_setup": (st, [ctx, ctypes.POINTER(lhf_grid_desc)]),
+            "lhf_query_sizes": (st, [ctx, ctypes.POINTER(lhf_sizes)]),
+            "lhf_assemble_core_hamiltonian": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lhf_circulant_fft": (st, [ctx] + [ctypes.c_void_p] * 4),
+            "lhf_k_point_eigensolve": (st, [ctx] + [ctypes.c_void_p] * 4),
+            "lhf_dense_eigensolve": (st, [ctx, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+            "lhf_bloch_spectra": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lhf_bloch_spectra_host": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lhf_basis_factors": (st, [ctx, ctypes.c_int, ctypes.c_void_p]),
+            "lhf_potential_factors": (st, [ctx, ctypes.c_int, ctypes.c_void_p]),
+            "lhf_gram_factors": (st, [ctx, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _ip]),
+            "lhf_set_profiling": (st, [ctx, ctypes.c_int]),
+            "lhf_stage_times": (st, [ctx, _dp, _ip]),
+            "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(x) -> int | None:
+    """Device pointer of a torch tensor (or an int pointer); None stays NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"expected a device tensor or pointer, got {type(x)}")
+
+
+class _Desc:
+    """ctypes descriptors built from a workload dictionary; keeps the host arrays alive."""
+
+    def __init__(self, cfg: dict):
+        self.Z = np.ascontiguousarray(cfg["Z"], dtype=np.float64)
+        self.a = np.ascontiguousarray(cfg["a"], dtype=np.float64).reshape(-1)
+        self.Z_cell = (None if cfg.get("Z_cell") is None
+                       else np.ascontiguousarray(cfg["Z_cell"], dtype=np.float64).reshape(-1))
+        self.kind = np.ascontiguousarray(cfg["kind"], dtype=np.int32)
+        self.alpha = np.ascontiguousarray(cfg["alpha"], dtype=np.float64)
+        self.centre = np.ascontiguousarray(cfg["centre"], dtype=np.float64).reshape(-1)
+        lat = lhf_lattice_desc()
+        lat.L[:] = cfg["L"]
+        lat.b[:] = cfg["b"]
+        lat.periodic[:] = cfg["periodic"]
+        lat.K_sum[:] = cfg["K_sum"]
+        lat.M0 = len(cfg["Z"])
+        lat.Z = self.Z.ctypes.data_as(_dp)
+        lat.a = self.a.ctypes.data_as(_dp)
+        lat.Z_cell = self.Z_cell.ctypes.data_as(_dp) if self.Z_cell is not None else ctypes.cast(None, _dp)
+        bas = lhf_basis_desc()
+        bas.m0 = len(cfg["alpha"])
+        bas.kind = self.kind.ctypes.data_as(_ip)
+        bas.alpha = self.alpha.ctypes.data_as(_dp)
+        bas.centre = self.centre.ctypes.data_as(_dp)
+        bas.rho = float(cfg["rho"])
+        grd = lhf_grid_desc()
+        grd.n[:] = cfg["n"]
+        grd.n_cell[:] = cfg["n_cell"]
+        grd.h[:] = cfg["h"]
+        grd.x0[:] = cfg["x0"]
+        grd.cell0[:] = cfg["cell0"]
+        grd.R = int(cfg["R"])
+        grd.u0 = float(cfg["u0"])
+        grd.du = float(cfg["du"])
+        self.lattice, self.basis, self.grid = lat, bas, grd
+        self.system = lhf_system_desc(lat, bas, grd)
+
+
+class Context:
+    """One lhf_ctx on one device and stream (torch.cuda stream or raw cudaStream_t)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        self._h = ctypes.c_void_p()
+        raw = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = self.lib.lhf_create(ctypes.byref(self._h), int(device), raw)
+        if st != LHF_OK:
+            raise LhfError(st, "lhf_create failed")
+        self._keep = []
+
+    def _check(self, st: int):
+        if st != LHF_OK:
+            msg = self.lib.lhf_last_error(self._h)
+            raise LhfError(st, msg.decode() if msg else "")
+        return st
+
+    def close(self):
+        if self._h:
+            self.lib.lhf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- setup -----------------------------------------------------------------------------
+    def set_stream(self, stream):
+        raw = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self._check(self.lib.lhf_set_stream(self._h, raw))
+
+    def lattice_setup(self, cfg: dict):
+        d = _Desc(cfg)
+        self._check(self.lib.lhf_lattice_setup(self._h, ctypes.byref(d.lattice)))
+
+    def basis_setup(self, cfg: dict):
+        d = _Desc(cfg)
+        self._check(self.lib.lhf_basis_setup(self._h, ctypes.byref(d.basis)))
+
+    def grid_setup(self, cfg: dict):
+        d = _Desc(cfg)
+        self._check(self.lib.lhf_grid_setup(self._h, ctypes.byref(d.grid)))
+
+    def setup(self, cfg: dict):
+        """lattice_setup + basis_setup + grid_setup of one workload dictionary."""
+        self.lattice_setup(cfg)
+        self.basis_setup(cfg)
+        self.grid_setup(cfg)
+
+    def query_sizes(self) -> dict:
+        out = lhf_sizes()
+        self._check(self.lib.lhf_query_sizes(self._h, ctypes.byref(out)))
+        return {"m0": out.m0, "n_blocks": out.n_blocks, "n_kpoints": out.n_kpoints,
+                "n_basis": out.n_basis, "rank": out.rank, "window": list(out.window),
+                "n_potential": list(out.n_potential), "periodic": out.periodic}
+
+    def sync(self):
+        self._check(self.lib.lhf_sync(self._h))
+
+    # -- path --------------------------------------------------------------------------------
+    def assemble_core_hamiltonian(self, H, S, precision: int = FP64):
+        self._check(self.lib.lhf_assemble_core_hamiltonian(self._h, precision, _ptr(H), _ptr(S)))
+
+    def circulant_fft(self, H, S, Hbar, Sbar):
+        self._check(self.lib.lhf_circulant_fft(self._h, _ptr(H), _ptr(S), _ptr(Hbar), _ptr(Sbar)))
+
+    def k_point_eigensolve(self, Hbar, Sbar, eig, k_status=None):
+        self._check(self.lib.lhf_k_point_eigensolve(self._h, _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(k_status)))
+
+    def dense_eigensolve(self, H, S, N: int, eig):
+        self._check(self.lib.lhf_dense_eigensolve(self._h, _ptr(H), _ptr(S), int(N), _ptr(eig)))
+
+    @staticmethod
+    def _systems(cfgs):
+        descs = [_Desc(c) for c in cfgs]
+        arr = (lhf_system_desc * len(descs))(*[d.system for d in descs])
+        return descs, arr
+
+    def bloch_spectra(self, cfgs, eig, k_status=None, precision: int = FP64):
+        descs, arr = self._systems(cfgs)
+        self._check(self.lib.lhf_bloch_spectra(self._h, len(descs), arr, precision, _ptr(eig), _ptr(k_status)))
+
+    def bloch_spectra_host(self, cfgs, eig_host: np.ndarray, k_status_host: np.ndarray | None = None,
+                           precision: int = FP64):
+        assert eig_host.dtype == np.float64 and eig_host.flags["C_CONTIGUOUS"]
+        descs, arr = self._systems(cfgs)
+        kp = None
+        if k_status_host is not None:
+            assert k_status_host.dtype == np.int32 and k_status_host.flags["C_CONTIGUOUS"]
+            kp = k_status_host.ctypes.data
+        self._check(self.lib.lhf_bloch_spectra_host(self._h, len(descs), arr, precision,
+                                                    eig_host.ctypes.data, kp))
+
+    # -- live stage timing -------------------------------------------------------------------
+    STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "zero_fill", "upload")
+
+    def set_profiling(self, enable: bool):
+        self._check(self.lib.lhf_set_profiling(self._h, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, launches)} for launches recorded since the previous call."""
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        self._check(self.lib.lhf_stage_times(self._h, ms, cnt))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
+
+    def eig_counters(self) -> tuple[int, int]:
+        """(Jacobi sweeps, matrices solved) since the previous call."""
+        a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        self._check(self.lib.lhf_eig_counters(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    # -- stage outputs -----------------------------------------------------------------------
+    def basis_factors(self, l: int, G):
+        self._check(self.lib.lhf_basis_factors(self._h, int(l), _ptr(G)))
+
+    def potential_factors(self, l: int, V):
+        self._check(self.lib.lhf_potential_factors(self._h, int(l), _ptr(V)))
+
+    def gram_factors(self, l: int, C, precision: int = FP64) -> int:
+        jlo = ctypes.c_int(0)
+        self._check(self.lib.lhf_gram_factors(self._h, precision, int(l), _ptr(C), ctypes.byref(jlo)))
+        return jlo.value

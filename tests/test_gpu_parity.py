@@ -1,0 +1,304 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, stage by stage and end
+to end, on seeded synthetic lattices (the workloads of lhf_workloads and edge cases).
+
+Tolerances (see tests/_numerics.py): blocks 1e-12 of the block max; eigenvalues 1e-10 Ha, widened
+only by the first-order perturbation bound where the k-point overlap is nearly singular."""
+
+import numpy as np
+import pytest
+
+import lhf_workloads as W
+from tests._numerics import block_rel_err, check_eigenvalues
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lhf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1408_3839_gb300 import build, lhf as B
+
+    build.build()
+    return B
+
+
+@pytest.fixture(scope="module")
+def ctx(lhf):
+    c = lhf.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def dev(shape, dtype=torch.float64):
+    return torch.empty(shape, dtype=dtype, device="cuda")
+
+
+def gpu_blocks(ctx, cfg, precision=0):
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0 = sz["m0"]
+    L = cfg["L"]
+    H = dev((L[0], L[1], L[2], m0, m0))
+    S = dev((L[0], L[1], L[2], m0, m0))
+    ctx.assemble_core_hamiltonian(H, S, precision)
+    ctx.sync()
+    return H.cpu().numpy(), S.cpu().numpy()
+
+
+def small_tube(L=16, seed=11, **kw):
+    base = dict(n_c=32, n_perp=64, half_width=8.0, M0=2, m0_s=4, m0_pshell=4, lo=0.04, hi=30.0)
+    base.update(kw)
+    return W.tube(L, seed=seed, **base)
+
+
+CASES = {
+    "periodic_8": lambda: W.periodic_8(),
+    "tube_16_m16": lambda: small_tube(16, seed=11),
+    "tube_12_odd_window": lambda: small_tube(12, seed=12, lo=0.3, K_sum=7),
+    "tube_24_windowed": lambda: small_tube(24, seed=13, lo=0.5, hi=20.0, n_c=24),
+    "tube_9_m5_odd": lambda: W.tube(9, seed=14, n_c=20, n_perp=48, half_width=6.0, M0=1, m0_s=2,
+                                    m0_pshell=1, lo=0.2, hi=9.0),
+    "cubic_3x2x2": lambda: W.cubic_32(seed=15, L=3, n_c=10),
+}
+
+
+# ---------------------------------------------------------------------------------------------
+# stage parity
+
+@pytest.mark.parametrize("name", ["periodic_8", "tube_16_m16", "cubic_3x2x2"])
+def test_basis_and_potential_factors(ctx, oracle_mod, name):
+    cfg = CASES[name]()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    for l in range(3):
+        G = dev((sz["m0"], cfg["n"][l]))
+        ctx.basis_factors(l, G)
+        ref = oracle_mod.basis_samples(cfg, l, 0)
+        assert np.abs(G.cpu().numpy() - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max())
+        nv = sz["n_potential"][l]
+        V = dev((sz["rank"], nv))
+        ctx.potential_factors(l, V)
+        vref = oracle_mod.potential_factors(cfg, l)[:, :nv]
+        got = V.cpu().numpy()
+        rel = np.abs(got - vref).max(axis=1) / np.abs(vref).max(axis=1)
+        assert rel.max() <= 1e-13, (l, rel.max())
+
+
+@pytest.mark.parametrize("name", ["periodic_8", "tube_16_m16", "tube_24_windowed", "cubic_3x2x2"])
+def test_gram_factors(ctx, oracle_mod, name):
+    cfg = CASES[name]()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0, Rt = sz["m0"], sz["rank"]
+    for l in range(3):
+        J = sz["window"][l]
+        C = dev((J, Rt + 2, m0, m0))
+        jlo = ctx.gram_factors(l, C)
+        C = C.cpu().numpy()
+        V = oracle_mod.potential_factors(cfg, l)
+        L = cfg["L"][l]
+        for jw in range(J):
+            j = (jlo + jw) % L
+            Cr, K, M = oracle_mod.gram_1d(cfg, l, j, 0, V)
+            for r in range(Rt):
+                den = max(np.abs(Cr[r]).max(), 1e-300)
+                assert np.abs(C[jw, r] - Cr[r]).max() <= 1e-12 * den or np.abs(Cr[r]).max() == 0
+            assert np.abs(C[jw, Rt] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300)
+            assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_core_hamiltonian_blocks(ctx, oracle_mod, name):
+    cfg = CASES[name]()
+    H, S = gpu_blocks(ctx, cfg)
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    m0 = H.shape[-1]
+    assert block_rel_err(H, Hr, m0) <= 1e-12
+    assert block_rel_err(S, Sr, m0) <= 1e-12
+    # blocks outside the overlap window are exact zeros on both sides
+    zr = np.abs(Hr).reshape(-1, m0 * m0).max(axis=1) == 0
+    assert np.all(np.abs(H).reshape(-1, m0 * m0)[zr] == 0)
+
+
+@pytest.mark.parametrize("name", ["periodic_8", "tube_16_m16", "tube_12_odd_window", "tube_9_m5_odd",
+                                  "cubic_3x2x2"])
+def test_block_dft_and_eigensolve(ctx, oracle_mod, name):
+    cfg = CASES[name]()
+    H, S = gpu_blocks(ctx, cfg)
+    Hd = torch.from_numpy(H).cuda()
+    Sd = torch.from_numpy(S).cuda()
+    m0 = H.shape[-1]
+    Hb = dev(H.shape + (2,))
+    Sb = dev(S.shape + (2,))
+    ctx.circulant_fft(Hd, Sd, Hb, Sb)
+    Hb_ref = oracle_mod.block_dft(H)
+    Sb_ref = oracle_mod.block_dft(S)
+    Hbg = Hb.cpu().numpy()
+    Sbg = Sb.cpu().numpy()
+    Hbg = Hbg[..., 0] + 1j * Hbg[..., 1]
+    Sbg = Sbg[..., 0] + 1j * Sbg[..., 1]
+    scale_h = np.abs(H).max()
+    assert np.abs(Hbg - Hb_ref).max() <= 1e-12 * scale_h * np.sqrt(H.shape[0] * H.shape[1] * H.shape[2])
+    assert np.abs(Sbg - Sb_ref).max() <= 1e-12 * np.abs(S).max() * np.sqrt(S.shape[0] * S.shape[1] * S.shape[2])
+    K = H.shape[0] * H.shape[1] * H.shape[2]
+    eig = dev((K, m0))
+    ks = dev((K,), torch.int32)
+    ctx.k_point_eigensolve(Hb, Sb, eig, ks)
+    ctx.sync()
+    assert np.all(ks.cpu().numpy() == 0)
+    ref, st = oracle_mod.k_point_eigenvalues(Hb_ref, Sb_ref)
+    assert np.all(st == 0)
+    worst, ratio = check_eigenvalues(eig.cpu().numpy(), ref, Hb_ref, Sb_ref)
+    assert ratio <= 1.0, (worst, ratio)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_bloch_spectrum_end_to_end(ctx, oracle_mod, name):
+    cfg = CASES[name]()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    eig = dev((sz["n_kpoints"], sz["m0"]))
+    ks = dev((sz["n_kpoints"],), torch.int32)
+    ctx.bloch_spectra([cfg], eig, ks)
+    ctx.sync()
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, _ = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    worst, ratio = check_eigenvalues(eig.cpu().numpy(), ref, Hb, Sb)
+    assert ratio <= 1.0, (worst, ratio)
+
+
+# ---------------------------------------------------------------------------------------------
+# batching, determinism, edge cases and errors
+
+def test_batch_equals_single_runs_bitwise(ctx):
+    cfgs = [CASES["tube_16_m16"](), CASES["periodic_8"](), CASES["tube_9_m5_odd"](), CASES["cubic_3x2x2"]()]
+    sizes = []
+    for c in cfgs:
+        ctx.setup(c)
+        s = ctx.query_sizes()
+        sizes.append(s["n_kpoints"] * s["m0"])
+    eig = dev((sum(sizes),))
+    ctx.bloch_spectra(cfgs, eig)
+    ctx.sync()
+    batch = eig.cpu().numpy()
+    off = 0
+    for c, n in zip(cfgs, sizes):
+        single = dev((n,))
+        ctx.bloch_spectra([c], single)
+        ctx.sync()
+        assert np.array_equal(single.cpu().numpy(), batch[off:off + n])
+        off += n
+    again = dev((sum(sizes),))
+    ctx.bloch_spectra(cfgs, again)
+    ctx.sync()
+    assert np.array_equal(again.cpu().numpy(), batch)  # deterministic
+
+
+def test_host_entry_point_matches_device_entry_point(ctx):
+    cfgs = [CASES["tube_16_m16"](), CASES["tube_9_m5_odd"]()]
+    n = 0
+    for c in cfgs:
+        ctx.setup(c)
+        s = ctx.query_sizes()
+        n += s["n_kpoints"] * s["m0"]
+    host = np.empty(n)
+    ks = np.empty(16 + 9, dtype=np.int32)
+    ctx.bloch_spectra_host(cfgs, host, ks)
+    eig = dev((n,))
+    ctx.bloch_spectra(cfgs, eig)
+    ctx.sync()
+    assert np.array_equal(eig.cpu().numpy(), host)
+    assert np.all(ks == 0)
+
+
+def test_single_cell_lattice(ctx, oracle_mod):
+    cfg = W.make_system(L=[1, 1, 1], b=[6.0, 6.0, 6.0], periodic=[0, 0, 0], n_cell=[48, 48, 48],
+                        h=[0.125] * 3, x0=[-3.0] * 3, cell0=[-3.0] * 3, Z=[1.0], a=[[0.1, 0.2, -0.1]],
+                        kind=[0, 2, 0], alpha=[1.0, 2.0, 0.4], centre=[[0.1, 0.2, -0.1]] * 3, R=10,
+                        u0=-3.0, du=0.7)
+    H, S = gpu_blocks(ctx, cfg)
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    assert block_rel_err(H, Hr, 3) <= 1e-12 and block_rel_err(S, Sr, 3) <= 1e-12
+    ctx.setup(cfg)
+    eig = dev((1, 3))
+    ctx.bloch_spectra([cfg], eig)
+    ctx.sync()
+    ref, _ = oracle_mod.bloch_spectrum(cfg)
+    assert np.abs(eig.cpu().numpy() - ref).max() <= 1e-10
+
+
+def test_m0_one(ctx, oracle_mod):
+    cfg = W.make_system(L=[5, 1, 1], b=[2.0, 8.0, 8.0], periodic=[1, 0, 0], n_cell=[16, 32, 32],
+                        h=[0.125, 0.25, 0.25], x0=[0, -4, -4], cell0=[0, -4, -4], Z=[1.0],
+                        a=[[1.0, 0.1, 0.0]], kind=[0], alpha=[0.7], centre=[[1.0, 0.1, 0.0]], R=10,
+                        u0=-3.0, du=0.7)
+    ctx.setup(cfg)
+    eig = dev((5, 1))
+    ctx.bloch_spectra([cfg], eig)
+    ctx.sync()
+    ref, _ = oracle_mod.bloch_spectrum(cfg)
+    assert np.abs(eig.cpu().numpy() - ref).max() <= 1e-10
+
+
+def test_not_positive_definite_overlap_is_reported(ctx, lhf):
+    cfg = CASES["tube_9_m5_odd"]()
+    ctx.setup(cfg)
+    m0 = 5
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((9, 1, 1, m0, m0, 2))
+    Hb = torch.from_numpy(X).cuda()
+    Sb = torch.from_numpy(-np.abs(X)).cuda()   # negative diagonal: not positive definite
+    eig = dev((9, m0))
+    ks = dev((9,), torch.int32)
+    ctx.k_point_eigensolve(Hb, Sb, eig, ks)
+    with pytest.raises(lhf.LhfError) as ei:
+        ctx.sync()
+    assert ei.value.status == lhf.LHF_ERR_NOT_SPD
+    assert np.all(ks.cpu().numpy() == lhf.LHF_ERR_NOT_SPD)
+    assert np.all(np.isnan(eig.cpu().numpy()))
+    ctx.sync()  # the flag is cleared by the sync that reported it
+
+
+def test_invalid_descriptors_are_rejected(ctx, lhf):
+    cfg = dict(CASES["tube_9_m5_odd"]())
+    bad = dict(cfg, n=[cfg["n"][0] + 1] + cfg["n"][1:])  # periodic n != L n_cell
+    ctx.setup(bad)
+    with pytest.raises(lhf.LhfError) as ei:
+        ctx.query_sizes()
+    assert ei.value.status == lhf.LHF_ERR_ARG
+    with pytest.raises(lhf.LhfError):
+        ctx.lattice_setup(dict(cfg, Z=[-1.0]))
+    with pytest.raises(lhf.LhfError):
+        ctx.basis_setup(dict(cfg, alpha=[0.0] + cfg["alpha"][1:]))
+    ctx.setup(cfg)
+    ctx.query_sizes()
+
+
+@pytest.mark.slow
+def test_tube_256_full_size_blocks_and_spectrum(ctx, oracle_mod):
+    """The benchmark workload at full size (n1 = 32768, m0 = 16, R_tot = 64, L = 256)."""
+    cfg = W.tube_256()
+    H, S = gpu_blocks(ctx, cfg)
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    assert block_rel_err(H, Hr, 16) <= 1e-12
+    assert block_rel_err(S, Sr, 16) <= 1e-12
+    ctx.setup(cfg)
+    eig = dev((256, 16))
+    ctx.bloch_spectra([cfg], eig)
+    ctx.sync()
+    Hb, Sb = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, _ = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    worst, ratio = check_eigenvalues(eig.cpu().numpy(), ref, Hb, Sb)
+    assert ratio <= 1.0, (worst, ratio)
