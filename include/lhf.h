@@ -156,8 +156,22 @@ lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, dou
 
 /* Generalized Hermitian eigenproblems Hbar_kappa u = lambda Sbar_kappa u at every k-point
  * (eq. (4.7); spectrum = union over kappa, eq. (6.7)).  Inputs as produced by
- * lhf_circulant_fft (device).  eig: device [n_kpoints][m0], ascending per k-point.  k_status:
- * device [n_kpoints] (may be NULL): 0 or LHF_ERR_NOT_SPD; eigenvalues of such a k-point are NaN. */
+ * lhf_circulant_fft (device): blocks of a real lattice matrix, so that Xbar at -kappa is the
+ * complex conjugate of Xbar at kappa; one k-point of each conjugate pair is solved and its
+ * eigenvalues are written to both.  eig: device [n_kpoints][m0], ascending per k-point.
+ * FP64 data cannot represent a Bloch function whose overlap diagonal cancels to rounding level:
+ * with s0_i = mean over kappa of Re Sbar_ii (the cell-periodic norm of basis function i),
+ * function i is removed at kappa when Re Sbar_ii(kappa) <= LHF_DROP_TOL s0_i; the remaining
+ * pencil is diagonally scaled, reduced (Cholesky) and solved by Jacobi; removed slots hold
+ * +INFINITY (sorted last).  k_status: device [n_kpoints] (may be NULL): the number of removed
+ * functions (>= 0), or LHF_ERR_NOT_SPD when the reduced overlap is not positive definite (the
+ * eigenvalues of such a k-point are NaN). */
+#define LHF_DROP_TOL 1e-9
+/* The kept pencil is scaled to unit overlap diagonal; where the scaled overlap is nearly
+ * singular (a Cholesky pivot below 1e-5) the k-point is solved by canonical orthogonalisation,
+ * dropping the overlap eigen-directions below LHF_LINDEP_TOL (their slots also hold +INFINITY
+ * and are counted in k_status). */
+#define LHF_LINDEP_TOL 1e-8
 lhf_status lhf_k_point_eigensolve(lhf_ctx *ctx, const double *Hbar, const double *Sbar,
                                   double *eig, int *k_status);
 
@@ -168,7 +182,8 @@ lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, 
 /* Batched Bloch spectra: for every system s of an array of nsys periodic lattices, the whole
  * path (basis and potential factors, Grams, rank sum, block DFT, k-point eigensolves) in one
  * pass of batched launches.  eig: device, systems concatenated, system s at offset
- * sum_{t<s} n_kpoints(t) m0(t).  k_status: device (may be NULL), concatenated likewise.
+ * sum_{t<s} n_kpoints(t) m0(t), conventions of lhf_k_point_eigensolve.  k_status: device (may
+ * be NULL), concatenated likewise.
  * Scratch memory is the context's workspace (grown on demand). */
 lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
                              lhf_precision precision, double *eig, int *k_status);

@@ -24,6 +24,12 @@ _lock = threading.Lock()
 _lib = None
 
 NOT_SPD = -3
+# a Bloch function is removed at a k-point when its overlap diagonal is below this fraction of
+# its cell-periodic norm (numerically absent in FP64; see orc_k_point_eigenvalues)
+DROP_TOL = 1e-9
+# canonical orthogonalisation: directions of the diagonally scaled overlap with eigenvalue below
+# this threshold are dropped (near-linear dependence)
+LINDEP_TOL = 1e-8
 
 
 def compile_source(src: str, out: str) -> str:
@@ -95,7 +101,7 @@ def _load():
                 "orc_jacobi_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp]),
                 "orc_dense_gen_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
                 "orc_herm_gen_eigenvalues": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
-                "orc_k_point_eigenvalues": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _ip]),
+                "orc_k_point_eigenvalues": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _ip]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -272,15 +278,17 @@ def _as_interleaved(X: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(out)
 
 
-def k_point_eigenvalues(Hbar: np.ndarray, Sbar: np.ndarray):
-    """Eigenvalues [K, m] (ascending) and status [K] for blocks Hbar, Sbar [..., m, m]."""
+def k_point_eigenvalues(Hbar: np.ndarray, Sbar: np.ndarray, tau: float = DROP_TOL,
+                        tau2: float = LINDEP_TOL):
+    """Eigenvalues [K, m] (ascending, removed slots +inf) and status [K] (number of removed
+    Bloch functions, or NOT_SPD) for blocks Hbar, Sbar [..., m, m] of all k-points."""
     m = Hbar.shape[-1]
     Hi = _as_interleaved(Hbar.reshape(-1, m, m))
     Si = _as_interleaved(Sbar.reshape(-1, m, m))
     K = Hi.shape[0]
     eig = np.empty((K, m))
     st = np.empty(K, dtype=np.int32)
-    _load().orc_k_point_eigenvalues(K, m, _ptr(Hi), _ptr(Si), _ptr(eig), _ptr(st))
+    _load().orc_k_point_eigenvalues(K, m, _ptr(Hi), _ptr(Si), float(tau), float(tau2), _ptr(eig), _ptr(st))
     return eig, st
 
 

@@ -611,6 +611,43 @@ int orc_jacobi_eigenvalues(int n, double *A, double *eig)
     return sweep;
 }
 
+/* Cyclic-by-row Jacobi with accumulated rotations: on return A is (numerically) diagonal,
+ * diag(A) holds the eigenvalues and the columns of V (n x n, initialised here) the eigenvectors,
+ * in matching order.                                                                         */
+static void jacobi_vectors(int n, double *A, double *V)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[(size_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (size_t e = 0; e < (size_t)n * n; ++e) fro += A[e] * A[e];
+    double tol2 = 1e-30 * fro;
+    for (int sweep = 0; sweep < 100 && off_norm2(n, A) > tol2; ++sweep)
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+}
+
 /* Generalized symmetric-definite eigenvalues H x = lambda S x (dense real, ascending):
  * Cholesky S = G G^T, C = G^{-1} H G^{-T}, cyclic Jacobi on C.                            */
 int orc_dense_gen_eigenvalues(int n, const double *H, const double *S, double *eig)
@@ -634,6 +671,22 @@ int orc_dense_gen_eigenvalues(int n, const double *H, const double *S, double *e
     return rc;
 }
 
+/* Real symmetric embedding [[Re X, -Im X], [Im X, Re X]] (2m x 2m) of a Hermitian m x m
+ * matrix X given as interleaved (re, im); every eigenvalue of X appears twice.             */
+static void embed(int m, const double *X, double *Xe)
+{
+    int n = 2 * m;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            size_t e = (size_t)i * m + j;
+            double xr = X[2 * e], xi = X[2 * e + 1];
+            Xe[(size_t)i * n + j] = xr;
+            Xe[(size_t)i * n + j + m] = -xi;
+            Xe[(size_t)(i + m) * n + j] = xi;
+            Xe[(size_t)(i + m) * n + j + m] = xr;
+        }
+}
+
 /* Eigenvalues of one Hermitian generalized problem Hbar u = lambda Sbar u (eq. (4.7)) through
  * the real symmetric embedding [[Re X, -Im X], [Im X, Re X]] of both m x m blocks: each
  * eigenvalue of the 2m x 2m real pencil appears twice; every other one is returned.        */
@@ -649,19 +702,8 @@ int orc_herm_gen_eigenvalues(int m, const double *Hbar, const double *Sbar, doub
         free(ev);
         return ORC_ERR_NOMEM;
     }
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) {
-            size_t e = (size_t)i * m + j;
-            double hr = Hbar[2 * e], hi = Hbar[2 * e + 1], sr = Sbar[2 * e], si = Sbar[2 * e + 1];
-            He[(size_t)i * n + j] = hr;
-            He[(size_t)i * n + j + m] = -hi;
-            He[(size_t)(i + m) * n + j] = hi;
-            He[(size_t)(i + m) * n + j + m] = hr;
-            Se[(size_t)i * n + j] = sr;
-            Se[(size_t)i * n + j + m] = -si;
-            Se[(size_t)(i + m) * n + j] = si;
-            Se[(size_t)(i + m) * n + j + m] = sr;
-        }
+    embed(m, Hbar, He);
+    embed(m, Sbar, Se);
     int rc = orc_dense_gen_eigenvalues(n, He, Se, ev);
     if (rc == ORC_OK)
         for (int i = 0; i < m; ++i) eig[i] = ev[2 * i];
@@ -671,20 +713,151 @@ int orc_herm_gen_eigenvalues(int m, const double *Hbar, const double *Sbar, doub
     return rc;
 }
 
-/* Per-k-point eigenvalues for K blocks (Prop. 6.1, eq. (6.7); eq. (4.7)).  status[k] = 0 or
- * ORC_ERR_NOT_SPD.  Returns the number of failed k-points.                                  */
-int orc_k_point_eigenvalues(int K, int m, const double *Hbar, const double *Sbar, double *eig,
-                            int *status)
+/* Canonical orthogonalisation (Loewdin) of one Hermitian pencil given as m x m complex blocks:
+ * eigen-decompose the real embedding of S, keep the directions with eigenvalue >= tau2,
+ * X = V_kept diag(sigma)^{-1/2}, and solve the standard problem X^T H X.  Each complex
+ * eigenvalue appears twice in the embedding, so the kept directions come in pairs.  eig[0..]
+ * receives the kept eigenvalues (ascending); *removed the number of complex directions
+ * dropped.                                                                                   */
+static int canonical_eigenvalues(int m, const double *Hbar, const double *Sbar, double tau2,
+                                 double *eig, int *removed)
+{
+    int n = 2 * m;
+    size_t nn = (size_t)n * n;
+    double *He = (double *)malloc(sizeof(double) * nn), *Se = (double *)malloc(sizeof(double) * nn);
+    double *V = (double *)malloc(sizeof(double) * nn), *X = (double *)malloc(sizeof(double) * nn);
+    double *W = (double *)malloc(sizeof(double) * nn), *ev = (double *)malloc(sizeof(double) * n);
+    int *kept = (int *)malloc(sizeof(int) * n);
+    if (!He || !Se || !V || !X || !W || !ev || !kept) {
+        free(He);
+        free(Se);
+        free(V);
+        free(X);
+        free(W);
+        free(ev);
+        free(kept);
+        return ORC_ERR_NOMEM;
+    }
+    embed(m, Hbar, He);
+    embed(m, Sbar, Se);
+    jacobi_vectors(n, Se, V);
+    int nk = 0;
+    for (int i = 0; i < n; ++i)
+        if (Se[(size_t)i * n + i] >= tau2) kept[nk++] = i;
+    if (nk & 1) { /* a pair split by rounding at the threshold: drop its kept member */
+        int lo = 0;
+        for (int a = 1; a < nk; ++a)
+            if (Se[(size_t)kept[a] * n + kept[a]] < Se[(size_t)kept[lo] * n + kept[lo]]) lo = a;
+        for (int a = lo; a < nk - 1; ++a) kept[a] = kept[a + 1];
+        --nk;
+    }
+    /* X = V_kept diag(sigma)^{-1/2}  (n x nk) */
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < nk; ++a)
+            X[(size_t)i * nk + a] = V[(size_t)i * n + kept[a]] / sqrt(Se[(size_t)kept[a] * n + kept[a]]);
+    /* W = He X (n x nk); C = X^T W (nk x nk) stored in V */
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < nk; ++a) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += He[(size_t)i * n + k] * X[(size_t)k * nk + a];
+            W[(size_t)i * nk + a] = v;
+        }
+    for (int a = 0; a < nk; ++a)
+        for (int b = 0; b < nk; ++b) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += X[(size_t)k * nk + a] * W[(size_t)k * nk + b];
+            V[(size_t)a * nk + b] = v;
+        }
+    for (int a = 0; a < nk; ++a)
+        for (int b = a + 1; b < nk; ++b) {
+            double v = 0.5 * (V[(size_t)a * nk + b] + V[(size_t)b * nk + a]);
+            V[(size_t)a * nk + b] = v;
+            V[(size_t)b * nk + a] = v;
+        }
+    if (nk > 0) orc_jacobi_eigenvalues(nk, V, ev);
+    for (int i = 0; i < nk / 2; ++i) eig[i] = ev[2 * i];
+    *removed = m - nk / 2;
+    free(He);
+    free(Se);
+    free(V);
+    free(X);
+    free(W);
+    free(ev);
+    free(kept);
+    return ORC_OK;
+}
+
+/* Per-k-point eigenvalues for K blocks (Prop. 6.1, eq. (6.7); eq. (4.7)).
+ * Reading for FP64 data: a Bloch function whose overlap diagonal cancels to rounding level is
+ * numerically absent.  With s0_i = mean over kappa of Re Sbar_ii (= S_0,ii, the cell-periodic
+ * norm of basis function i), function i is removed at kappa when Re Sbar_ii(kappa) <= tau s0_i.
+ * The remaining pencil is scaled by D = diag(Sbar)^{-1/2} on both sides (a congruence: same
+ * eigenvalues) and solved by canonical orthogonalisation with threshold tau2 on the scaled
+ * overlap (directions of near-linear dependence dropped); removed slots hold +INFINITY (sorted
+ * last).  status[k] = number of removed directions (>= 0), or ORC_ERR_NOT_SPD when the input
+ * has no positive norms.  Returns the number of k-points reported as not positive definite. */
+int orc_k_point_eigenvalues(int K, int m, const double *Hbar, const double *Sbar, double tau,
+                            double tau2, double *eig, int *status)
 {
     int bad = 0;
     size_t mm2 = 2 * (size_t)m * m;
-    for (int k = 0; k < K; ++k) {
-        int rc = orc_herm_gen_eigenvalues(m, Hbar + k * mm2, Sbar + k * mm2, eig + (size_t)k * m);
-        status[k] = rc;
+    double *s0 = (double *)calloc((size_t)m, sizeof(double));
+    double *Hr = (double *)malloc(sizeof(double) * mm2), *Sr = (double *)malloc(sizeof(double) * mm2);
+    double *ev = (double *)malloc(sizeof(double) * (size_t)m);
+    int *keep = (int *)malloc(sizeof(int) * (size_t)m);
+    if (!s0 || !Hr || !Sr || !ev || !keep) {
+        free(s0);
+        free(Hr);
+        free(Sr);
+        free(ev);
+        free(keep);
+        return -1;
+    }
+    for (int k = 0; k < K; ++k)
+        for (int i = 0; i < m; ++i) s0[i] += Sbar[k * mm2 + 2 * ((size_t)i * m + i)];
+    int valid = 1;
+    for (int i = 0; i < m; ++i) {
+        s0[i] /= K;
+        if (!(s0[i] > 0.0)) valid = 0; /* not an overlap matrix: no positive norm */
+    }
+    for (int k = 0; k < K && !valid; ++k) {
+        status[k] = ORC_ERR_NOT_SPD;
+        for (int i = 0; i < m; ++i) eig[(size_t)k * m + i] = NAN;
+    }
+    if (!valid) bad = K;
+    for (int k = 0; k < K && valid; ++k) {
+        const double *Hk = Hbar + k * mm2, *Sk = Sbar + k * mm2;
+        int mr = 0;
+        for (int i = 0; i < m; ++i)
+            if (Sk[2 * ((size_t)i * m + i)] > tau * s0[i]) keep[mr++] = i;
+        for (int a = 0; a < mr; ++a)
+            for (int b = 0; b < mr; ++b) {
+                size_t e = (size_t)keep[a] * m + keep[b];
+                double da = 1.0 / sqrt(Sk[2 * ((size_t)keep[a] * m + keep[a])]);
+                double db = 1.0 / sqrt(Sk[2 * ((size_t)keep[b] * m + keep[b])]);
+                size_t f = (size_t)a * mr + b;
+                Hr[2 * f] = Hk[2 * e] * da * db;
+                Hr[2 * f + 1] = Hk[2 * e + 1] * da * db;
+                Sr[2 * f] = Sk[2 * e] * da * db;
+                Sr[2 * f + 1] = Sk[2 * e + 1] * da * db;
+            }
+        int removed2 = 0;
+        int rc = mr > 0 ? canonical_eigenvalues(mr, Hr, Sr, tau2, ev, &removed2) : ORC_OK;
         if (rc != ORC_OK) {
             ++bad;
+            status[k] = rc;
             for (int i = 0; i < m; ++i) eig[(size_t)k * m + i] = NAN;
+            continue;
         }
+        int nkept = mr - removed2;
+        status[k] = m - nkept;
+        for (int i = 0; i < nkept; ++i) eig[(size_t)k * m + i] = ev[i];
+        for (int i = nkept; i < m; ++i) eig[(size_t)k * m + i] = INFINITY;
     }
+    free(s0);
+    free(Hr);
+    free(Sr);
+    free(ev);
+    free(keep);
     return bad;
 }

@@ -48,8 +48,10 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
   if (D.periodic) {
     const double P = D.L * D.b;
     const double d0 = x - A;
-    const int mlo = (int)floor((d0 - cut) / P) - 1;
-    const int mhi = (int)ceil((d0 + cut) / P) + 1;
+    // images m with |d0 - m P| <= cut (the bracket is widened by one on each side; the cut
+    // test inside gto_factor decides)
+    const int mlo = (int)floor((d0 - cut) * D.invP) - 1;
+    const int mhi = (int)ceil((d0 + cut) * D.invP) + 1;
     for (int m = mlo; m <= mhi; ++m) g += gto_factor(d0 - m * P, al, cut, pdir, pn);
   } else {
     g = gto_factor(x - A, al, cut, pdir, pn);
@@ -61,13 +63,21 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
 // of the Gaussian about the cell centre; H_n are the physicists' Hermite polynomials, whose
 // recurrence H_{n+1} = 2 m H_n - 2 n H_{n-1} gives the derivatives).  Used for narrow cells
 // where the erf difference would cancel.
+__constant__ double kRecip[64] = {
+    1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,  1.0 / 9,  1.0 / 10, 1.0 / 11,
+    1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22,
+    1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32, 1.0 / 33,
+    1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44,
+    1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55,
+    1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63, 1.0 / 64};
+
 __device__ double gauss_cell_series(double m, double d) {
   double hm1 = 1.0, h0 = 2.0 * m;   // H_0, H_1
   double p = d;                     // d^(n+1) / (n+1)!  for n = 0
   double sum = 2.0 * p;             // k = 0 term: H_0 * 2 d
   int small = 0;                    // consecutive negligible terms (a Hermite root may zero one)
   for (int n = 1; n < 60; ++n) {
-    p = p * d / (n + 1);
+    p = p * d * kRecip[n];  // d^(n+1) / (n+1)!
     if (!(n & 1)) {
       double term = 2.0 * h0 * p;
       sum += term;
@@ -120,9 +130,37 @@ __global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sy
     double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
     int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
     int khi = (khi_f > kmax) ? kmax : (int)khi_f;
-    for (int k = klo; k <= khi; ++k) {
-      const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
-      v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+    const double delta = t * D.h, sb = t * D.b;
+    if (delta <= 1e-3 && sb <= 0.1) {
+      // Wide Gaussian: with m_k = t (x_mid - c0 - k b), the cell integral is
+      // h exp(-m_k^2) [1 + (2 m^2 - 1) delta^2 / 12 + (4 m^4 - 12 m^2 + 3) delta^4 / 480] up to
+      // O(delta^6) (the Taylor series about the cell centre), and exp(-m_k^2) follows k by
+      // exp(-m_{k+1}^2) = exp(-m_k^2) R_k, R_{k+1} = R_k exp(-2 s^2), s = t b, restarted from exp
+      // every 8 images so that the product's rounding stays within 32 ulp.
+      const double xm = 0.5 * (lo + hi);
+      const double d2 = delta * delta, c2 = d2 * (1.0 / 12.0), c4 = d2 * d2 * (1.0 / 480.0);
+      const double Q = exp(-2.0 * sb * sb);
+      for (int k0 = klo; k0 <= khi; k0 += 8) {
+        double mk = t * (xm - c0 - k0 * D.b);
+        double e = exp(-mk * mk);
+        double R = exp(2.0 * mk * sb - sb * sb);
+        const int kend = min(k0 + 8, khi + 1);
+        for (int k = k0; k < kend; ++k) {
+          const double m2 = mk * mk;
+          const double corr = 1.0 + (2.0 * m2 - 1.0) * c2 + ((4.0 * m2 - 12.0) * m2 + 3.0) * c4;
+          const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
+          v += wk * e * corr;
+          e *= R;
+          R *= Q;
+          mk = t * (xm - c0 - (k + 1) * D.b);
+        }
+      }
+      v *= D.h;
+    } else {
+      for (int k = klo; k <= khi; ++k) {
+        const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
+        v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+      }
     }
   } else {
     const double lo = D.x0 + i * D.h, hi = lo + D.h;

@@ -39,7 +39,8 @@ struct HostSystem {
 // Sizes of the per-system workspace regions (doubles) and launch extents.
 struct Plan {
   SysDev sd;
-  size_t ws = 0;       // doubles of G, V, C
+  size_t ws = 0;       // doubles of G, V, C and the overlap norms s0
+  size_t s0_off = 0;   // offset of s0 [m0]
   size_t blocks_doubles = 0;  // nblocks * m0^2
   int basis_items = 0, pot_items = 0, gram_blocks = 0, rank_items = 0;
   int nv_max = 0;
@@ -66,7 +67,7 @@ struct lhf_ctx {
   size_t h_sys_cap = 0;
   cudaEvent_t upload_done = nullptr;
   unsigned *d_flags = nullptr;
-  unsigned long long *d_counters = nullptr;  // [0] Jacobi sweeps, [1] matrices solved
+  unsigned long long *d_counters = nullptr;  // [0] Jacobi sweeps, [1] matrices, [2] canonical route
   double *d_zcell = nullptr;
   size_t zcell_cap = 0;
   double *d_out = nullptr;  // device staging of lhf_bloch_spectra_host
@@ -288,6 +289,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
     D.x0 = s.x0[l];
     D.cell0 = s.cell0[l];
     D.b = s.b[l];
+    D.invP = 1.0 / (s.L[l] * s.b[l]);
     // support cells of each cell-0 basis copy, dilated by one node for the P1 cross terms
     for (int mu = 0; mu < m0; ++mu) {
       if (D.lattice) {
@@ -336,6 +338,8 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
     sd.d[l].offC = (int64_t)off;
     off = align_up(off + (size_t)sd.d[l].J * (Rt + 2) * mm);
   }
+  P.s0_off = off;
+  off = align_up(off + (size_t)m0);
   P.ws = off;
   P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
   P.rank_items = sd.nwin * mm;
@@ -466,7 +470,10 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
     max_m0 = std::max(max_m0, p.sd.m0);
   }
   c->begin(5);
-  lhf_status st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream), "eigen kernel");
+  lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
+  if (st == LHF_OK)
+    st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream),
+                 "eigen kernel");
   c->end();
   return st;
 }
@@ -489,6 +496,7 @@ size_t internal_doubles(const Plan &p) { return p.ws + 6 * p.blocks_doubles; }
 
 void place_internal(Plan &p, double *base) {
   p.sd.ws = base;
+  p.sd.s0 = base + p.s0_off;
   double *blk = base + p.ws;
   p.sd.H = blk;
   p.sd.S = blk + p.blocks_doubles;
@@ -519,8 +527,8 @@ lhf_status lhf_create(lhf_ctx **out, int device, void *stream) {
   if (cudaSetDevice(device) != cudaSuccess || cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->d_counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(c->d_counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     if (c->upload_done) cudaEventDestroy(c->upload_done);
     if (c->d_flags) cudaFree(c->d_flags);
@@ -554,7 +562,7 @@ void lhf_destroy(lhf_ctx *c) {
 
 lhf_status lhf_eig_counters(lhf_ctx *c, unsigned long long *sweeps, unsigned long long *matrices) {
   if (!c || !sweeps || !matrices) return LHF_ERR_ARG;
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (st != LHF_OK) return st;
   st = c->cuda(cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost), "cudaMemcpy");
@@ -708,6 +716,10 @@ lhf_status lhf_k_point_eigensolve(lhf_ctx *c, const double *Hbar, const double *
   std::vector<Plan> ps(1);
   lhf_status st = current_plan(c, ps[0]);
   if (st != LHF_OK) return st;
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  ps[0].sd.ws = c->ws;
+  ps[0].sd.s0 = c->ws + ps[0].s0_off;
   ps[0].sd.Hbar = const_cast<double *>(Hbar);
   ps[0].sd.Sbar = const_cast<double *>(Sbar);
   ps[0].sd.eig = eig;

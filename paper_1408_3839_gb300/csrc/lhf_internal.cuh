@@ -15,6 +15,14 @@ constexpr int kMaxM0 = LHF_MAX_M0;
 constexpr int kMaxNuc = LHF_MAX_NUCLEI;
 constexpr int kMaxR = LHF_MAX_R;
 constexpr int kMaxRt = kMaxNuc * kMaxR;
+// A Bloch function is numerically absent at a k-point when Re Sbar_ii <= kDropTol * s0_i.
+constexpr double kDropTol = LHF_DROP_TOL;
+// Canonical orthogonalisation drops directions of the scaled overlap below kLindepTol.  The
+// Cholesky route is taken only when every scaled pivot is at least kCholTol: the smallest
+// overlap eigenvalue never exceeds the smallest pivot, and with no eigenvalue below kLindepTol
+// both routes solve the same pencil.
+constexpr double kLindepTol = LHF_LINDEP_TOL;
+constexpr double kCholTol = 1e-5;
 
 // One direction of one system.
 struct DirDev {
@@ -29,6 +37,7 @@ struct DirDev {
   int jlo;        // first displacement of the window (may be negative; blocks taken mod L)
   int pad_;
   double h, x0, cell0, b;
+  double invP;     // 1 / (L b): supercell period of a periodic direction
   int64_t offG;   // basis samples [m0][n]          (doubles, from SysDev::ws)
   int64_t offV;   // potential factors [Rt][nv]
   int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
@@ -57,6 +66,7 @@ struct SysDev {
   double *Hbar, *Sbar;    // complex [L0][L1][L2][m0][m0][2]
   double *eig;            // [nblocks][m0]
   int *kstat;             // [nblocks] or null
+  double *s0;             // [m0] mean over k-points of Re Sbar_ii (cell-periodic norms)
   const double *zcell;    // box charges [L0][M0] (device) or null
 };
 
@@ -73,6 +83,7 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int max_l
                        cudaStream_t st);
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
 cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *eig,
                              double *work, unsigned *flags, cudaStream_t st);

@@ -21,7 +21,9 @@ MUTANTS = {
     "image_shift_sign": ("double c = c0 + k * s->b[l];\n            double dmin", "double c = c0 - 2 * k * s->b[l];\n            double dmin"),
     "p_factor_direction": ("if (s->kind[mu] == 1 + l)", "if (s->kind[mu] == 2 - l)"),
     "dft_sign": ("double ph = -2.0 * ORC_PI *", "double ph = -1.0 * ORC_PI *"),
-    "embedding_transpose": ("He[(size_t)i * n + j + m] = -hi;", "He[(size_t)i * n + j + m] = hi;"),
+    "embedding_transpose": ("Xe[(size_t)i * n + j + m] = -xi;", "Xe[(size_t)i * n + j + m] = xi;"),
+    "lindep_scale": ("X[(size_t)i * nk + a] = V[(size_t)i * n + kept[a]] / sqrt(", "X[(size_t)i * nk + a] = V[(size_t)i * n + kept[a]] * sqrt("),
+    "drop_rule": ("if (Sk[2 * ((size_t)i * m + i)] > tau * s0[i]) keep[mr++] = i;", "keep[mr++] = i;"),
     "first_weight_tail": ("w[0] = w[0] / (1.0 - exp(-du));", "w[0] = w[0];"),
     "cell_shift": ("double A = s->centre[3 * mu + l] + cell * s->b[l];", "double A = s->centre[3 * mu + l] - cell * s->b[l];"),
 }

@@ -439,6 +439,27 @@ def eig_tolerance(Hb, Sb, lam, floor=1e-10, c=64.0):
     return np.maximum(floor, c * eps * (nH + np.abs(lam) * nS) * u2)
 
 
+def test_numerically_absent_bloch_functions_are_removed(oracle_mod):
+    # tube with a diffuse p_x function: its Bloch sum at kappa = 0 cancels to ~1e-13 of its norm
+    cfg = W.tube(16, seed=11, n_c=32, n_perp=64, half_width=8.0)
+    H, S = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(H), oracle_mod.block_dft(S)
+    eig, st = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    m0 = H.shape[-1]
+    s0 = np.real(np.einsum("kii->i", Sb.reshape(-1, m0, m0))) / 16
+    ratio = np.real(np.einsum("kii->ki", Sb.reshape(-1, m0, m0))) / s0
+    removed = ratio <= oracle_mod.DROP_TOL
+    assert removed.sum() >= 1 and np.all(st == removed.sum(axis=1))
+    for k in range(16):
+        keep = np.where(~removed[k])[0]
+        ref = sla.eigh(Hb[k, 0, 0][np.ix_(keep, keep)], Sb[k, 0, 0][np.ix_(keep, keep)], eigvals_only=True)
+        assert np.all(np.isinf(eig[k, len(keep):]))
+        assert np.abs(eig[k, :len(keep)] - ref).max() < 1e-6 * max(1.0, np.abs(ref).max())
+    # well-conditioned lattice: nothing removed
+    e8, st8 = oracle_mod.bloch_spectrum(W.periodic_8())
+    assert np.all(st8 == 0) and np.all(np.isfinite(e8))
+
+
 def test_k_point_eigenvalues_match_scipy(oracle_mod):
     cfg = small_tube(L=8, seed=5, alpha_lo=0.1)
     H, S = oracle_mod.core_blocks(cfg)
@@ -477,9 +498,22 @@ def test_m0_one_closed_form_and_trace(oracle_mod):
     Sh = Y @ Y.conj().T + m * np.eye(m)
     eig, _ = oracle_mod.k_point_eigenvalues(Hh[None], Sh[None])
     assert eig.sum() == pytest.approx(np.trace(np.linalg.solve(Sh, Hh)).real, rel=1e-12)
-    # non-SPD overlap is reported, not solved
+    # an overlap without positive norms is reported, not solved
     eig, st = oracle_mod.k_point_eigenvalues(Hh[None], -Sh[None])
     assert st[0] == -3 and np.all(np.isnan(eig))
+    # an exactly rank-deficient Galerkin pair S = B B^H, H = B M B^H (rank r; a function that
+    # vanishes has no energy either): the nullity is dropped and the kept eigenvalues are those
+    # of the pencil restricted to range(S) (orthonormal basis from QR)
+    r = 4
+    Bm = rng.standard_normal((m, r)) + 1j * rng.standard_normal((m, r))
+    Mm = rng.standard_normal((r, r)) + 1j * rng.standard_normal((r, r))
+    Sdef = Bm @ Bm.conj().T
+    Hdef = Bm @ (Mm + Mm.conj().T) @ Bm.conj().T
+    eig, st = oracle_mod.k_point_eigenvalues(Hdef[None], Sdef[None])
+    Q, _ = np.linalg.qr(Bm)
+    ref = sla.eigh(Q.conj().T @ Hdef @ Q, Q.conj().T @ Sdef @ Q, eigvals_only=True)
+    assert st[0] == m - r and np.all(np.isinf(eig[0, r:]))
+    assert np.abs(eig[0, :r] - ref).max() < 1e-8 * max(1.0, np.abs(ref).max())
 
 
 def test_jacobi_against_numpy(oracle_mod):
