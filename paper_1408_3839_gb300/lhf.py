@@ -107,6 +107,7 @@ def load():
             "lhf_set_profiling": (st, [ctx, ctypes.c_int]),
             "lhf_stage_times": (st, [ctx, _dp, _ip]),
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
+            "lhf_k_point_eigensolve_noalloc": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int] + [ctypes.c_void_p] * 5),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -301,3 +302,14 @@ class Context:
         jlo = ctypes.c_int(0)
         self._check(self.lib.lhf_gram_factors(self._h, precision, int(l), _ptr(C), ctypes.byref(jlo)))
         return jlo.value
+
+
+def k_point_eigensolve_noalloc(L, m0: int, Hbar, Sbar, eig, k_status=None, stream=None):
+    """lhf_k_point_eigensolve_noalloc: the k-point eigensolve without a context or any device
+    allocation (its scratch is a static device array inside the library)."""
+    lib = load()
+    Larr = (ctypes.c_int * 3)(*[int(v) for v in L])
+    raw = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = lib.lhf_k_point_eigensolve_noalloc(Larr, int(m0), _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(k_status), raw)
+    if st != LHF_OK:
+        raise LhfError(st, "lhf_k_point_eigensolve_noalloc failed")
