@@ -46,30 +46,21 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-__global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv) {
-  const SysDev &s = sysv[blockIdx.y];
-  if (s.box) return;
-  GramItem it;
-  if (!decode_gram(s, blockIdx.x, it)) return;
+// Phase 1 for one CTA: Q[nu][c] and the P1 cross terms E[nu][c] in shared memory, their row
+// sums in red[2 nu], and the P1 stiffness/mass slots of C written out.
+__device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, double *E, double *red) {
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, L = D.L;
-  const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
-  extern __shared__ double sm[];
-  double *Q = sm;               // [m0][ld]
-  double *E = Q + m0 * ld;      // [m0][ld]  P1 cross terms per node
-  double *red = E + m0 * ld;    // [m0][2]   Dsum, Esum per nu
+  const int ld = nv + 1;
   const double *G = s.ws + D.offG;
   const int mu = it.mu;
   const int j = D.jlo + it.jw;
   const double *f = G + (int64_t)mu * n;
   const int tid = threadIdx.x;
-
   // support of the shifted row function (cells), tested modulo L
   const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
   const int mspan = mhi - mlo;
   const bool periodic = D.periodic != 0;
-
-  // ---- phase 1: Q[nu][c], E[nu][c] -----------------------------------------------------
   const int items = m0 * nv;
   for (int p0 = tid; p0 < items; p0 += kGramThreads) {
     const int nu = p0 / nv;
@@ -100,7 +91,6 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
     E[nu * ld + c] = e;
   }
   __syncthreads();
-
   // P1 sums per nu: warp w reduces rows nu = w, w + 8, ... in a fixed order
   const int warp = tid >> 5, lane = tid & 31;
   for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
@@ -119,14 +109,37 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
     }
   }
   __syncthreads();
+  const int Rt = s.Rt, mm = m0 * m0;
+  double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
+  if (tid < m0) {
+    const double dq = red[2 * tid], de = red[2 * tid + 1];
+    Cout[(int64_t)Rt * mm + tid] = (2.0 * dq - de) / D.h;
+    Cout[(int64_t)(Rt + 1) * mm + tid] = (4.0 * dq + de) * D.h / 6.0;
+  }
+}
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  GramItem it;
+  if (!decode_gram(s, blockIdx.x, it)) return;
+  const DirDev &D = s.d[it.l];
+  const int m0 = s.m0, nv = D.nv;
+  const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
+  extern __shared__ double sm[];
+  double *Q = sm;               // [m0][ld]
+  double *E = Q + m0 * ld;      // [m0][ld]  P1 cross terms per node
+  double *red = E + m0 * ld;    // [m0][2]   Dsum, Esum per nu
+  gram_phase1(s, it, Q, E, red);
 
   // ---- phase 2: C_r[nu] = sum_c V[r][c] Q[nu][c] ------------------------------------------
   const int Rt = s.Rt;
   const int mm = m0 * m0;
+  const int mu = it.mu;
   double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
   const double *V = s.ws + D.offV;
   const int outs = Rt * m0;
-  for (int o = tid; o < outs; o += kGramThreads) {
+  for (int o = threadIdx.x; o < outs; o += kGramThreads) {
     const int r = o / m0;
     const int nu = o - r * m0;
     const double *vr = V + (int64_t)r * nv;
@@ -140,10 +153,121 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
     if (c < nv) acc0 += __ldg(vr + c) * qn[c];
     Cout[(int64_t)r * mm + nu] = acc0 + acc1;
   }
-  if (tid < m0) {
-    const double dq = red[2 * tid], de = red[2 * tid + 1];
-    Cout[(int64_t)Rt * mm + tid] = (2.0 * dq - de) / D.h;
-    Cout[(int64_t)(Rt + 1) * mm + tid] = (4.0 * dq + de) * D.h / 6.0;
+}
+
+// ---- tensor-core route: exact digit slices of the FP64 operands -------------------------
+//
+// A row x[c] (c < nv) with max|x| = f 2^e, 1/2 <= f < 1, becomes the 62-bit fixed-point integers
+// X[c] = rint(x[c] 2^(62-e)) and then 7 balanced base-2^7 digits
+//   X = a_0 2^55 + a_1 2^48 + ... + a_6 2^13 + r,  a_0 in [-128, 128], a_k in [-64, 64], |r| <= 2^12,
+// so x[c] = 2^e (sum_k a_k 2^(-7(k+1)) + O(2^-50)).  Every digit is an integer of at most 8
+// significant bits, exact in BF16; products of two digits are exact in FP32 and sums of up to
+// 2^24 / 2^14 of them accumulate exactly.  Digit plane k of a row block goes to
+// planes + k * rows * Kpad + row * Kpad + c (BF16, Kpad >= nv, zero padded).
+__device__ __forceinline__ void digits7(double x, int e, int *a) {
+  long long X = llrint(ldexp(x, 62 - e));
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) {
+    const int sh = 55 - 7 * k;
+    const long long d = (X + (1ll << (sh - 1))) >> sh;
+    X -= d << sh;
+    a[k] = (int)d;
+  }
+}
+
+__device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v| <= 256
+  return (unsigned short)(__float_as_uint((float)v) >> 16);
+}
+
+__device__ __forceinline__ int scale_exponent(double mx) {
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  return e;
+}
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  GramItem it;
+  if (!decode_gram(s, blockIdx.x, it)) return;
+  const DirDev &D = s.d[it.l];
+  const int m0 = s.m0, nv = D.nv, Kp = D.Kpad;
+  const int ld = nv + 1;
+  extern __shared__ double sm[];
+  double *Q = sm;
+  double *E = Q + m0 * ld;
+  double *red = E + m0 * ld;
+  __shared__ int rexp[kMaxM0];
+  gram_phase1(s, it, Q, E, red);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
+    double mx = 0.0;
+    for (int c = lane; c < nv; c += 32) mx = fmax(mx, fabs(Q[nu * ld + c]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) rexp[nu] = scale_exponent(mx);
+  }
+  __syncthreads();
+  const int64_t rows = (int64_t)D.J * m0 * m0;
+  const int64_t row0 = ((int64_t)it.jw * m0 + it.mu) * m0;
+  unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
+  int *rowexp = reinterpret_cast<int *>(s.ws + D.offRE);
+  if (tid < m0) rowexp[row0 + tid] = rexp[tid];
+  const int items = m0 * Kp;
+  for (int p0 = tid; p0 < items; p0 += kGramThreads) {
+    const int nu = p0 / Kp, c = p0 - nu * Kp;
+    int a[kSlices];
+    if (c < nv) {
+      digits7(Q[nu * ld + c], rexp[nu], a);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSlices; ++k) a[k] = 0;
+    }
+    const int64_t at = (row0 + nu) * Kp + c;
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k) planes[k * rows * Kp + at] = bf16_of_int(a[k]);
+  }
+}
+
+// Digit planes of the potential factors: one CTA per (system, direction, rank term r).
+__global__ void __launch_bounds__(kGramThreads) k_vslice(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  int b = blockIdx.x, l = 0;
+  for (; l < 3; ++l) {
+    if (b < s.Rt) break;
+    b -= s.Rt;
+  }
+  if (l == 3) return;
+  const DirDev &D = s.d[l];
+  const int r = b, nv = D.nv, Kp = D.Kpad, Rt = s.Rt;
+  const double *v = s.ws + D.offV + (int64_t)r * nv;
+  __shared__ double part[kGramThreads / 32];
+  __shared__ int e_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double mx = 0.0;
+  for (int c = tid; c < nv; c += kGramThreads) mx = fmax(mx, fabs(v[c]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) part[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < kGramThreads / 32; ++w) m = fmax(m, part[w]);
+    e_sh = scale_exponent(m);
+    reinterpret_cast<int *>(s.ws + D.offCE)[r] = e_sh;
+  }
+  __syncthreads();
+  const int e = e_sh;
+  unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offB);
+  for (int c = tid; c < Kp; c += kGramThreads) {
+    int a[kSlices];
+    if (c < nv) {
+      digits7(v[c], e, a);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kSlices; ++k) a[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k) planes[((int64_t)k * Rt + r) * Kp + c] = bf16_of_int(a[k]);
   }
 }
 
@@ -153,15 +277,29 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
                              int max_nv, cudaStream_t st) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   dim3 grid(max_blocks, nsys);
   k_gram_fp64<<<grid, kGramThreads, smem, st>>>(sys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
+                               int max_rt3, cudaStream_t st) {
+  if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_gram_slice<<<dim3(max_blocks, nsys), kGramThreads, smem, st>>>(sys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_vslice<<<dim3(max_rt3, nsys), kGramThreads, 0, st>>>(sys);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,318 @@
+// k_gram_tc.cu -- step a3 on the tensor cores (LHF_MIXED): the weighted 1D Gram contraction
+// C_r[row] = sum_c V_r(c) Q_row(c) of the folded products Q (rows = (window block, mu, nu))
+// with the potential factors V, from the exact base-2^7 digit planes written by k_gram_slice /
+// k_vslice (k_gram.cu).
+//
+// With row = 2^e_row sum_a alpha_a 2^(-7(a+1)) and V_r = 2^e_r sum_b beta_b 2^(-7(b+1)) (digits
+// alpha, beta integers with |.| <= 128), the contraction is
+//   C_r[row] = 2^(e_row + e_r) sum_s 2^(-7(s+2)) D_s,   D_s = sum_c sum_{a+b=s} alpha_a(c) beta_b(c),
+// the splitting of Ozaki et al. ("Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication", 2012) with the 28 digit pairs a + b <= 6 kept
+// (relative truncation ~2^-48 of sum |Q| |V|).  Each D_s is an integer below 2^24 for K <= 448, so
+// BF16 x BF16 products accumulated in FP32 are exact; the recombination is exact in 64-bit
+// integers (two partial sums) and rounded once to FP64.
+//
+// One CTA of 128 threads per (system, direction, 128-row tile, 64-column tile):
+//   * TMA (cp.async.bulk.tensor.2d, 128-byte swizzle, no multicast) brings, per 64-wide K chunk,
+//     the 7 digit planes of the A tile (7 x 128 x 64 BF16) and of the B tile (7 x 64 x 64) into
+//     shared memory (168 KB, one stage);
+//   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 64, K = 16) for every
+//     pair (a, b) into the TMEM accumulator of its diagonal s = a + b (7 x 64 columns of the
+//     512 allocated), then tcgen05.commit to an mbarrier;
+//   * the 4 warps read their 32 TMEM lanes back with tcgen05.ld (32x32b), recombine the 7
+//     diagonals and store the FP64 results in the layout of the FP64 route.
+// Every mbarrier wait is bounded (~1 s of clock cycles); on time-out the CTA sets kFlagTimeout,
+// waits (bounded) for its outstanding operations, frees its TMEM and returns.
+#include <cuda.h>
+#include <mutex>
+#include <string.h>
+
+#include <vector>
+
+#include "lhf_internal.cuh"
+
+namespace lhf {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kTileN = 64;
+constexpr int kChunkK = 64;  // one 128-byte swizzle atom of BF16
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kABytes = kTileM * kChunkK * 2;  // 16 KB per digit plane
+constexpr uint32_t kBBytes = kTileN * kChunkK * 2;  // 8 KB per digit plane
+constexpr uint32_t kStageBytes = kSlices * (kABytes + kBBytes);
+constexpr size_t kSmemBytes = kStageBytes + 1024;  // + alignment slack for the 1024-byte swizzle base
+constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
+
+struct TcJob {
+  int sys, l, row0, n0;
+};
+
+struct TcArgs {  // per (system, direction)
+  CUtensorMap mapA;
+  CUtensorMap mapB;
+  double *C;
+  const int *rowexp;
+  const int *colexp;
+  int rows, Kpad, Rt, m0;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+
+// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (start >> 4 in bits 0-13, leading offset 16 B (unused) in 16-29, stride 1024 B
+// in 32-45, descriptor version 1 in 46-48, swizzle mode 2 = 128B in 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restrict__ jobs,
+                                                           const TcArgs *__restrict__ args, unsigned *flags) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int ok_sh;
+  unsigned char *tiles =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sA = smem_u32(tiles), sB = sA + kSlices * kABytes;
+  const TcJob job = jobs[blockIdx.x];
+  const TcArgs &P = args[job.sys * 3 + job.l];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_load)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ok_sh = 1;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const uint32_t bl = smem_u32(&bar_load), bm = smem_u32(&bar_mma);
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapB)) : "memory");
+    const int nchunks = P.Kpad / kChunkK;
+    uint32_t phase = 0;
+    bool ok = true, mma_pending = false;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl), "r"(kStageBytes) : "memory");
+      for (int a = 0; a < kSlices; ++a)
+        tma_load_2d(sA + a * kABytes, &P.mapA, ch * kChunkK, a * P.rows + job.row0, bl);
+      for (int b = 0; b < kSlices; ++b)
+        tma_load_2d(sB + b * kBBytes, &P.mapB, ch * kChunkK, b * P.Rt + job.n0, bl);
+      if (!mbar_wait(bl, phase)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int s = 0; s < kSlices; ++s)
+        for (int a = 0; a <= s; ++a) {
+          const int b = s - a;
+          for (int kk = 0; kk < kChunkK / 16; ++kk) {
+            const uint64_t ad = sw128_desc(sA + a * kABytes + kk * 32);
+            const uint64_t bd = sw128_desc(sB + b * kBBytes + kk * 32);
+            mma_bf16(tmem + (uint32_t)(s * kTileN), ad, bd, (ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bm)
+                   : "memory");
+      mma_pending = true;
+      if (!mbar_wait(bm, phase)) {
+        ok = false;
+        break;
+      }
+      mma_pending = false;
+      phase ^= 1u;
+    }
+    if (!ok) {
+      atomicOr(flags, kFlagTimeout);
+      ok_sh = 0;
+      if (mma_pending) mbar_wait(bm, phase);  // bounded: give in-flight MMAs a chance to drain
+    }
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (ok_sh) {
+    const int row = job.row0 + warp * 32 + lane;
+    const int mm = P.m0 * P.m0;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int er = row < P.rows ? P.rowexp[row] : 0;
+    double *Crow = P.C + (int64_t)(row / mm) * (P.Rt + 2) * mm + (row % mm);
+    for (int cc = 0; cc < kTileN / 16; ++cc) {
+      uint32_t v[kSlices][16];
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) tmem_ld16(tmem + lane_base + (uint32_t)(s * kTileN + cc * 16), v[s]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < P.rows) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int n = job.n0 + cc * 16 + t;
+          if (n >= P.Rt) continue;
+          long long d[kSlices];
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2ll_rn(__uint_as_float(v[s][t]));
+          const long long hi = (d[0] << 14) + (d[1] << 7) + d[2];
+          const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
+          const int E = er + P.colexp[n];
+          const double val = ldexp((double)hi, E - 28) + ldexp((double)lo, E - 56);
+          Crow[(int64_t)n * mm] = val;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+bool encode_planes(CUtensorMap *map, void *base, int K, int rows_total, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows_total};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys) {
+  size_t jobs = 0;
+  for (int i = 0; i < nsys; ++i)
+    for (int l = 0; l < 3; ++l) {
+      const DirDev &D = host_sys[i].d[l];
+      const size_t rows = (size_t)D.J * host_sys[i].m0 * host_sys[i].m0;
+      jobs += ((rows + kTileM - 1) / kTileM) * ((host_sys[i].Rt + kTileN - 1) / kTileN);
+    }
+  return (size_t)nsys * 3 * sizeof(TcArgs) + jobs * sizeof(TcJob) + 256;
+}
+
+cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
+                                unsigned *flags, cudaStream_t st) {
+  std::vector<TcArgs> args((size_t)nsys * 3);
+  std::vector<TcJob> jobs;
+  memset(args.data(), 0, args.size() * sizeof(TcArgs));
+  for (int i = 0; i < nsys; ++i) {
+    const SysDev &s = host_sys[i];
+    for (int l = 0; l < 3; ++l) {
+      const DirDev &D = s.d[l];
+      const int rows = D.J * s.m0 * s.m0;
+      if (D.Kpad % kChunkK != 0 || D.Kpad > 448 || rows < 1) return cudaErrorNotSupported;
+      TcArgs &a = args[(size_t)i * 3 + l];
+      if (!encode_planes(&a.mapA, s.ws + D.offA, D.Kpad, kSlices * rows, kTileM) ||
+          !encode_planes(&a.mapB, s.ws + D.offB, D.Kpad, kSlices * s.Rt, kTileN))
+        return cudaErrorInvalidValue;
+      a.C = s.ws + D.offC;
+      a.rowexp = reinterpret_cast<const int *>(s.ws + D.offRE);
+      a.colexp = reinterpret_cast<const int *>(s.ws + D.offCE);
+      a.rows = rows;
+      a.Kpad = D.Kpad;
+      a.Rt = s.Rt;
+      a.m0 = s.m0;
+      for (int r0 = 0; r0 < rows; r0 += kTileM)
+        for (int n0 = 0; n0 < s.Rt; n0 += kTileN) jobs.push_back({i, l, r0, n0});
+    }
+  }
+  const size_t abytes = args.size() * sizeof(TcArgs);
+  const size_t need = abytes + jobs.size() * sizeof(TcJob);
+  if (need > dev_bytes) return cudaErrorMemoryAllocation;
+  unsigned char *d = static_cast<unsigned char *>(dev_buf);
+  // pageable sources: each copy is staged before cudaMemcpyAsync returns
+  cudaError_t e = cudaMemcpyAsync(d, args.data(), abytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d + abytes, jobs.data(), jobs.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  k_gram_tc<<<(unsigned)jobs.size(), kTcThreads, kSmemBytes, st>>>(
+      reinterpret_cast<const TcJob *>(d + abytes), reinterpret_cast<const TcArgs *>(d), flags);
+  return cudaGetLastError();
+}
+
+}  // namespace lhf

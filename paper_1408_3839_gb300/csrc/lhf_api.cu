@@ -41,6 +41,7 @@ struct Plan {
   SysDev sd;
   size_t ws = 0;       // doubles of G, V, C and the overlap norms s0
   size_t s0_off = 0;   // offset of s0 [m0]
+  bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
   int basis_items = 0, pot_items = 0, gram_blocks = 0, rank_items = 0;
   int nv_max = 0;
@@ -72,6 +73,8 @@ struct lhf_ctx {
   size_t zcell_cap = 0;
   double *d_out = nullptr;  // device staging of lhf_bloch_spectra_host
   size_t out_cap = 0;
+  void *tc_buf = nullptr;   // tensor maps and job list of the tensor-core Gram
+  size_t tc_cap = 0;
   std::vector<int> host_L;
   // live stage timing
   bool prof = false;
@@ -218,7 +221,7 @@ void copy_grid(HostSystem &s, const lhf_grid_desc *d) {
 }
 
 // Consistency of the three parts; fills the plan (descriptor, window, workspace sizes).
-lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
+lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = false) {
   SysDev &sd = P.sd;
   memset(&sd, 0, sizeof sd);
   if (s.M0 * s.R > lhf::kMaxRt) return c->fail(LHF_ERR_ARG, "M0 R = %d exceeds %d", s.M0 * s.R, lhf::kMaxRt);
@@ -340,6 +343,23 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
   }
   P.s0_off = off;
   off = align_up(off + (size_t)m0);
+  for (int l = 0; l < 3; ++l) {
+    DirDev &D = sd.d[l];
+    D.Kpad = (D.nv + 63) / 64 * 64;
+    if (mixed) {
+      const size_t rows = (size_t)D.J * mm;
+      D.offA = (int64_t)off;
+      off = align_up(off + (lhf::kSlices * rows * D.Kpad * 2 + 7) / 8);
+      D.offB = (int64_t)off;
+      off = align_up(off + (lhf::kSlices * (size_t)Rt * D.Kpad * 2 + 7) / 8);
+      D.offRE = (int64_t)off;
+      off = align_up(off + (rows * 4 + 7) / 8);
+      D.offCE = (int64_t)off;
+      off = align_up(off + ((size_t)Rt * 4 + 7) / 8);
+      if (D.Kpad > 448) return c->fail(LHF_ERR_UNSUPPORTED, "mixed precision: direction %d has %d nodes per contraction (limit 448)", l, D.nv);
+    }
+  }
+  P.mixed = mixed;
   P.ws = off;
   P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
   P.rank_items = sd.nwin * mm;
@@ -347,10 +367,10 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P) {
   return LHF_OK;
 }
 
-lhf_status current_plan(lhf_ctx *c, Plan &P) {
+lhf_status current_plan(lhf_ctx *c, Plan &P, bool mixed = false) {
   if (!c->has_lat || !c->has_basis || !c->has_grid)
     return c->fail(LHF_ERR_STATE, "lattice, basis and grid setup must precede this call");
-  return make_plan(c, c->cur, P);
+  return make_plan(c, c->cur, P, mixed);
 }
 
 lhf_status ensure_ws(lhf_ctx *c, size_t doubles) {
@@ -414,6 +434,40 @@ int max_of(const std::vector<Plan> &ps, int Plan::*f) {
   return m;
 }
 
+// a3 + a4 for the uploaded systems: FP64 contraction, or digit planes + tensor cores.
+lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
+  const int nsys = (int)ps.size();
+  int max_m0 = 0, max_rt = 0;
+  for (const Plan &p : ps) {
+    max_m0 = std::max(max_m0, p.sd.m0);
+    max_rt = std::max(max_rt, p.sd.Rt);
+  }
+  if (!ps[0].mixed)
+    return c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
+                                         max_of(ps, &Plan::nv_max), c->stream),
+                   "Gram kernel");
+  lhf_status st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
+                                                  max_of(ps, &Plan::nv_max), 3 * max_rt, c->stream),
+                          "digit-plane kernels");
+  if (st != LHF_OK) return st;
+  std::vector<SysDev> host(nsys);
+  for (int i = 0; i < nsys; ++i) host[i] = ps[i].sd;
+  const size_t need = lhf::gram_tc_args_bytes(host.data(), nsys);
+  if (need > c->tc_cap) {
+    st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (st != LHF_OK) return st;
+    if (c->tc_buf) cudaFree(c->tc_buf);
+    c->tc_buf = nullptr;
+    c->tc_cap = 0;
+    st = c->cuda(cudaMalloc(&c->tc_buf, need), "cudaMalloc");
+    if (st != LHF_OK) return st;
+    c->tc_cap = need;
+  }
+  cudaError_t e = lhf::launch_gram_tc_impl(host.data(), nsys, c->tc_buf, c->tc_cap, c->d_flags, c->stream);
+  if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "shape outside the tensor-core kernel's limits");
+  return c->cuda(e, "tensor-core Gram kernel");
+}
+
 // Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
 lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
@@ -437,12 +491,8 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
   c->end();
   if (st != LHF_OK) return st;
-  int max_m0 = 0;
-  for (const Plan &p : ps) max_m0 = std::max(max_m0, p.sd.m0);
   c->begin(2);
-  st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
-                                     max_of(ps, &Plan::nv_max), c->stream),
-               "Gram kernel");
+  st = run_gram(c, ps);
   c->end();
   if (st != LHF_OK) return st;
   c->begin(3);
@@ -551,6 +601,7 @@ void lhf_destroy(lhf_ctx *c) {
   if (c->d_counters) cudaFree(c->d_counters);
   if (c->d_zcell) cudaFree(c->d_zcell);
   if (c->d_out) cudaFree(c->d_out);
+  if (c->tc_buf) cudaFree(c->tc_buf);
   if (c->upload_done) cudaEventDestroy(c->upload_done);
   for (auto &m : c->marks) {
     cudaEventDestroy(m.a);
@@ -621,6 +672,7 @@ lhf_status lhf_sync(lhf_ctx *c) {
   if (st != LHF_OK) return st;
   st = c->cuda(cudaMemset(c->d_flags, 0, sizeof(unsigned)), "cudaMemset");
   if (st != LHF_OK) return st;
+  if (flags & lhf::kFlagTimeout) return c->fail(LHF_ERR_TIMEOUT, "a bounded wait of the tensor-core Gram kernel gave up");
   if (flags & lhf::kFlagNotSpd) return c->fail(LHF_ERR_NOT_SPD, "an overlap block was not positive definite");
   return LHF_OK;
 }
@@ -672,8 +724,7 @@ lhf_status lhf_query_sizes(lhf_ctx *c, lhf_sizes *out) {
 }
 
 static lhf_status check_precision(lhf_ctx *c, lhf_precision p) {
-  if (p == LHF_FP64) return LHF_OK;
-  if (p == LHF_MIXED) return c->fail(LHF_ERR_UNSUPPORTED, "mixed precision is not available in this build");
+  if (p == LHF_FP64 || p == LHF_MIXED) return LHF_OK;
   return c->fail(LHF_ERR_ARG, "unknown precision %d", (int)p);
 }
 
@@ -683,7 +734,7 @@ lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *c, lhf_precision prec, double 
   lhf_status st = check_precision(c, prec);
   if (st != LHF_OK) return st;
   std::vector<Plan> ps(1);
-  st = current_plan(c, ps[0]);
+  st = current_plan(c, ps[0], prec == LHF_MIXED);
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
@@ -750,7 +801,7 @@ lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *system
     HostSystem hs;
     st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
-    st = make_plan(c, hs, ps[i]);
+    st = make_plan(c, hs, ps[i], prec == LHF_MIXED);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
     total += internal_doubles(ps[i]);
   }
@@ -797,6 +848,7 @@ lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *s
     lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     if (st != LHF_OK) return st;
     if (c->d_out) cudaFree(c->d_out);
+  if (c->tc_buf) cudaFree(c->tc_buf);
     c->d_out = nullptr;
     c->out_cap = 0;
     st = c->cuda(cudaMalloc(&c->d_out, need * sizeof(double)), "cudaMalloc");
@@ -860,7 +912,7 @@ lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, in
   lhf_status st = check_precision(c, prec);
   if (st != LHF_OK) return st;
   std::vector<Plan> ps(1);
-  st = current_plan(c, ps[0]);
+  st = current_plan(c, ps[0], prec == LHF_MIXED);
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
@@ -871,8 +923,7 @@ lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, in
   if (st != LHF_OK) return st;
   st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
   if (st != LHF_OK) return st;
-  st = c->cuda(lhf::launch_gram_fp64(c->d_sys, 1, ps[0].gram_blocks, ps[0].sd.m0, ps[0].nv_max, c->stream),
-               "Gram kernel");
+  st = run_gram(c, ps);
   if (st != LHF_OK) return st;
   const DirDev &D = ps[0].sd.d[l];
   if (jlo) *jlo = D.jlo;

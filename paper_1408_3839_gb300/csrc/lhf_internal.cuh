@@ -15,6 +15,7 @@ constexpr int kMaxM0 = LHF_MAX_M0;
 constexpr int kMaxNuc = LHF_MAX_NUCLEI;
 constexpr int kMaxR = LHF_MAX_R;
 constexpr int kMaxRt = kMaxNuc * kMaxR;
+constexpr int kSlices = 7;  // base-2^7 digit slices per FP64 operand on the tensor-core route
 // A Bloch function is numerically absent at a k-point when Re Sbar_ii <= kDropTol * s0_i.
 constexpr double kDropTol = LHF_DROP_TOL;
 // Canonical orthogonalisation drops directions of the scaled overlap below kLindepTol.  The
@@ -41,6 +42,13 @@ struct DirDev {
   int64_t offG;   // basis samples [m0][n]          (doubles, from SysDev::ws)
   int64_t offV;   // potential factors [Rt][nv]
   int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
+  // tensor-core route (LHF_MIXED): digit planes and scale exponents
+  int Kpad;       // nv rounded up to a multiple of 64
+  int pad2_;
+  int64_t offA;   // BF16 [kSlices][J m0 m0][Kpad] digit planes of the folded products
+  int64_t offB;   // BF16 [kSlices][Rt][Kpad] digit planes of the potential factors
+  int64_t offRE;  // int [J m0 m0] row scale exponents
+  int64_t offCE;  // int [Rt] potential-row scale exponents
 };
 
 struct SysDev {
@@ -71,13 +79,22 @@ struct SysDev {
 };
 
 // Per-launch status word written by kernels (atomicOr of flag bits).
-enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u };
+enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
 
 // ---- kernel launchers (each returns the launch error) ------------------------------------
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
                              int max_nv, cudaStream_t st);
+cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
+                               int max_rt3, cudaStream_t st);
+// Tensor-core contraction of the digit planes (tcgen05), one job per (system, direction, 128-row
+// tile, 64-column tile).  host_sys: host copies of the descriptors (device workspace pointers).
+// dev_buf (dev_bytes >= gram_tc_args_bytes) receives the tensor maps and the job list.  Returns
+// cudaErrorNotSupported for shapes outside the kernel's limits (K padded above 448).
+size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys);
+cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
+                                unsigned *flags, cudaStream_t st);
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int max_lines,
                        cudaStream_t st);

@@ -337,3 +337,76 @@ def test_tube_256_full_size_blocks_and_spectrum(ctx, oracle_mod):
     assert np.array_equal(ks.cpu().numpy(), st)
     worst, ratio = check_eigenvalues(eig.cpu().numpy(), ref, Hb, Sb, Hr, Sr, status=st)
     assert ratio <= 1.0, (worst, ratio)
+
+
+# ---------------------------------------------------------------------------------------------
+# tensor-core route (LHF_MIXED): exact base-2^7 digit planes on tcgen05, ~2^-48 truncation
+
+MIXED_CASES = ["periodic_8", "tube_16_m16", "tube_24_windowed", "tube_9_m5_odd", "cubic_3"]
+
+
+@pytest.mark.parametrize("name", MIXED_CASES)
+def test_mixed_gram_factors(ctx, oracle_mod, lhf, name):
+    cfg = CASES[name]()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0, Rt = sz["m0"], sz["rank"]
+    for l in range(3):
+        J = sz["window"][l]
+        C = dev((J, Rt + 2, m0, m0))
+        jlo = ctx.gram_factors(l, C, lhf.MIXED)
+        ctx.sync()
+        C = C.cpu().numpy()
+        V = oracle_mod.potential_factors(cfg, l)
+        for jw in range(J):
+            j = (jlo + jw) % cfg["L"][l]
+            Cr, K, M = oracle_mod.gram_1d(cfg, l, j, 0, V)
+            big = np.abs(Cr).max()
+            for r in range(Rt):
+                # truncation of the 7-digit splitting: ~2^-48 of sum |Q| |V| <= of the row's scale
+                assert np.abs(C[jw, r] - Cr[r]).max() <= 1e-12 * np.abs(Cr[r]).max() + 1e-40 * big
+            assert np.abs(C[jw, Rt] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300)
+            assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", MIXED_CASES)
+def test_mixed_blocks_and_spectrum(ctx, oracle_mod, lhf, name):
+    cfg = CASES[name]()
+    H, S = gpu_blocks(ctx, cfg, lhf.MIXED)
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    m0 = H.shape[-1]
+    assert block_rel_err(H, Hr, m0) <= 1e-12
+    assert block_rel_err(S, Sr, m0) <= 1e-12
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    eig = dev((sz["n_kpoints"], sz["m0"]))
+    ks = dev((sz["n_kpoints"],), torch.int32)
+    ctx.bloch_spectra([cfg], eig, ks, lhf.MIXED)
+    ctx.sync()
+    Hb, Sb = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, st = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    assert np.array_equal(ks.cpu().numpy(), st)
+    worst, ratio = check_eigenvalues(eig.cpu().numpy(), ref, Hb, Sb, Hr, Sr, status=st)
+    assert ratio <= 1.0, (worst, ratio)
+
+
+def test_mixed_batch_equals_single_and_is_deterministic(ctx, lhf):
+    cfgs = [CASES["tube_16_m16"](), CASES["periodic_8"](), CASES["cubic_3"]()]
+    sizes = []
+    for c in cfgs:
+        ctx.setup(c)
+        s = ctx.query_sizes()
+        sizes.append(s["n_kpoints"] * s["m0"])
+    eig = dev((sum(sizes),))
+    ctx.bloch_spectra(cfgs, eig, None, lhf.MIXED)
+    again = dev((sum(sizes),))
+    ctx.bloch_spectra(cfgs, again, None, lhf.MIXED)
+    ctx.sync()
+    assert np.array_equal(eig.cpu().numpy(), again.cpu().numpy())
+    off = 0
+    for c, n in zip(cfgs, sizes):
+        single = dev((n,))
+        ctx.bloch_spectra([c], single, None, lhf.MIXED)
+        ctx.sync()
+        assert np.array_equal(single.cpu().numpy(), eig.cpu().numpy()[off:off + n])
+        off += n
