@@ -274,7 +274,7 @@ size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys) {
 }
 
 cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
-                                unsigned *flags, cudaStream_t st) {
+                                void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st) {
   std::vector<TcArgs> args((size_t)nsys * 3);
   std::vector<TcJob> jobs;
   memset(args.data(), 0, args.size() * sizeof(TcArgs));
@@ -301,12 +301,12 @@ cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf,
   }
   const size_t abytes = args.size() * sizeof(TcArgs);
   const size_t need = abytes + jobs.size() * sizeof(TcJob);
-  if (need > dev_bytes) return cudaErrorMemoryAllocation;
+  if (need > dev_bytes || need > host_bytes) return cudaErrorMemoryAllocation;
   unsigned char *d = static_cast<unsigned char *>(dev_buf);
-  // pageable sources: each copy is staged before cudaMemcpyAsync returns
-  cudaError_t e = cudaMemcpyAsync(d, args.data(), abytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(d + abytes, jobs.data(), jobs.size() * sizeof(TcJob), cudaMemcpyHostToDevice, st);
+  unsigned char *h = static_cast<unsigned char *>(host_buf);  // pinned, owned by the caller
+  memcpy(h, args.data(), abytes);
+  memcpy(h + abytes, jobs.data(), jobs.size() * sizeof(TcJob));
+  cudaError_t e = cudaMemcpyAsync(d, h, need, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;

@@ -73,8 +73,10 @@ struct lhf_ctx {
   size_t zcell_cap = 0;
   double *d_out = nullptr;  // device staging of lhf_bloch_spectra_host
   size_t out_cap = 0;
-  void *tc_buf = nullptr;   // tensor maps and job list of the tensor-core Gram
+  void *tc_buf = nullptr;   // tensor maps and job list of the tensor-core Gram (device)
+  void *tc_host = nullptr;  // their pinned staging copy
   size_t tc_cap = 0;
+  cudaEvent_t tc_copied = nullptr;  // the staging copy has been consumed
   std::vector<int> host_L;
   // live stage timing
   bool prof = false;
@@ -453,19 +455,29 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
   std::vector<SysDev> host(nsys);
   for (int i = 0; i < nsys; ++i) host[i] = ps[i].sd;
   const size_t need = lhf::gram_tc_args_bytes(host.data(), nsys);
+  // the pinned staging buffer of the previous launch must have been copied out
+  st = c->cuda(cudaEventSynchronize(c->tc_copied), "cudaEventSynchronize");
+  if (st != LHF_OK) return st;
   if (need > c->tc_cap) {
     st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     if (st != LHF_OK) return st;
     if (c->tc_buf) cudaFree(c->tc_buf);
     c->tc_buf = nullptr;
+    if (c->tc_host) cudaFreeHost(c->tc_host);
+    c->tc_host = nullptr;
     c->tc_cap = 0;
     st = c->cuda(cudaMalloc(&c->tc_buf, need), "cudaMalloc");
     if (st != LHF_OK) return st;
+    st = c->cuda(cudaMallocHost(&c->tc_host, need), "cudaMallocHost");
+    if (st != LHF_OK) return st;
     c->tc_cap = need;
   }
-  cudaError_t e = lhf::launch_gram_tc_impl(host.data(), nsys, c->tc_buf, c->tc_cap, c->d_flags, c->stream);
+  cudaError_t e = lhf::launch_gram_tc_impl(host.data(), nsys, c->tc_buf, c->tc_cap, c->tc_host, c->tc_cap,
+                                           c->d_flags, c->stream);
   if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "shape outside the tensor-core kernel's limits");
-  return c->cuda(e, "tensor-core Gram kernel");
+  st = c->cuda(e, "tensor-core Gram kernel");
+  if (st != LHF_OK) return st;
+  return c->cuda(cudaEventRecord(c->tc_copied, c->stream), "cudaEventRecord");
 }
 
 // Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
@@ -575,12 +587,14 @@ lhf_status lhf_create(lhf_ctx **out, int device, void *stream) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   if (cudaSetDevice(device) != cudaSuccess || cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->tc_copied, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(c->d_counters, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     if (c->upload_done) cudaEventDestroy(c->upload_done);
+    if (c->tc_copied) cudaEventDestroy(c->tc_copied);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_counters) cudaFree(c->d_counters);
     delete c;
@@ -602,7 +616,9 @@ void lhf_destroy(lhf_ctx *c) {
   if (c->d_zcell) cudaFree(c->d_zcell);
   if (c->d_out) cudaFree(c->d_out);
   if (c->tc_buf) cudaFree(c->tc_buf);
+  if (c->tc_host) cudaFreeHost(c->tc_host);
   if (c->upload_done) cudaEventDestroy(c->upload_done);
+  if (c->tc_copied) cudaEventDestroy(c->tc_copied);
   for (auto &m : c->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -848,7 +864,6 @@ lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *s
     lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     if (st != LHF_OK) return st;
     if (c->d_out) cudaFree(c->d_out);
-  if (c->tc_buf) cudaFree(c->tc_buf);
     c->d_out = nullptr;
     c->out_cap = 0;
     st = c->cuda(cudaMalloc(&c->d_out, need * sizeof(double)), "cudaMalloc");

@@ -90,11 +90,12 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
                                int max_rt3, cudaStream_t st);
 // Tensor-core contraction of the digit planes (tcgen05), one job per (system, direction, 128-row
 // tile, 64-column tile).  host_sys: host copies of the descriptors (device workspace pointers).
-// dev_buf (dev_bytes >= gram_tc_args_bytes) receives the tensor maps and the job list.  Returns
+// dev_buf (dev_bytes >= gram_tc_args_bytes) receives the tensor maps and the job list through the
+// pinned host_buf, which must stay untouched until the copy has executed.  Returns
 // cudaErrorNotSupported for shapes outside the kernel's limits (K padded above 448).
 size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys);
 cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
-                                unsigned *flags, cudaStream_t st);
+                                void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st);
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int max_lines,
                        cudaStream_t st);

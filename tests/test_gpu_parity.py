@@ -358,13 +358,21 @@ def test_mixed_gram_factors(ctx, oracle_mod, lhf, name):
         ctx.sync()
         C = C.cpu().numpy()
         V = oracle_mod.potential_factors(cfg, l)
+        nv = sz["n_potential"][l]
+        vsum = np.abs(V[:, :nv]).sum(axis=1)          # sum_c |V_r(c)| on the folded domain
+        g0 = oracle_mod.basis_samples(cfg, l, 0)
         for jw in range(J):
             j = (jlo + jw) % cfg["L"][l]
             Cr, K, M = oracle_mod.gram_1d(cfg, l, j, 0, V)
-            big = np.abs(Cr).max()
+            # folded products Q[mu][nu](c) (sum over the cells of the products of the samples)
+            gj = oracle_mod.basis_samples(cfg, l, j)
+            P = gj[:, None, :] * g0[None, :, :]
+            Q = P.reshape(m0, m0, -1, nv).sum(axis=2) if cfg["periodic"][l] else P
+            qmax = np.abs(Q).max(axis=2)
             for r in range(Rt):
-                # truncation of the 7-digit splitting: ~2^-48 of sum |Q| |V| <= of the row's scale
-                assert np.abs(C[jw, r] - Cr[r]).max() <= 1e-12 * np.abs(Cr[r]).max() + 1e-40 * big
+                # digit truncation: below 2^-46 of max_c |Q_row| sum_c |V_r| for every row
+                bound = 1e-12 * np.abs(Cr[r]).max() + 2.0 ** -46 * qmax * vsum[r]
+                assert np.all(np.abs(C[jw, r] - Cr[r]) <= bound + 1e-300)
             assert np.abs(C[jw, Rt] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300)
             assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300)
 
@@ -410,3 +418,36 @@ def test_mixed_batch_equals_single_and_is_deterministic(ctx, lhf):
         ctx.sync()
         assert np.array_equal(single.cpu().numpy(), eig.cpu().numpy()[off:off + n])
         off += n
+
+
+@pytest.mark.slow
+def test_mixed_gram_factors_full_size_tube_256(ctx, lhf):
+    """The digit-plane route at the benchmark size, against the FP64 route on the GPU."""
+    cfg = W.tube_256()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0, Rt = sz["m0"], sz["rank"]
+    for l in range(3):
+        J = sz["window"][l]
+        C64 = dev((J, Rt + 2, m0, m0))
+        Cmx = dev((J, Rt + 2, m0, m0))
+        ctx.gram_factors(l, C64, lhf.FP64)
+        ctx.gram_factors(l, Cmx, lhf.MIXED)
+        ctx.sync()
+        a, b = C64.cpu().numpy(), Cmx.cpu().numpy()
+        # P1 slots are FP64 on both routes; rank slots within 1e-11 of their own scale or, for
+        # tail slots (digit truncation is relative to the row's scale), 1e-14 of the block's
+        # largest slot
+        assert np.array_equal(a[:, Rt:], b[:, Rt:])
+        scale = np.abs(a[:, :Rt]).max(axis=(2, 3), keepdims=True)
+        block = np.abs(a[:, :Rt]).max(axis=(1, 2, 3), keepdims=True)
+        assert np.all(np.abs(a[:, :Rt] - b[:, :Rt]) <= 1e-11 * scale + 1e-14 * block)
+    H64 = dev((256, 1, 1, m0, m0))
+    S64 = dev((256, 1, 1, m0, m0))
+    Hmx = dev((256, 1, 1, m0, m0))
+    Smx = dev((256, 1, 1, m0, m0))
+    ctx.assemble_core_hamiltonian(H64, S64, lhf.FP64)
+    ctx.assemble_core_hamiltonian(Hmx, Smx, lhf.MIXED)
+    ctx.sync()
+    assert block_rel_err(Hmx.cpu().numpy(), H64.cpu().numpy(), m0) <= 1e-12
+    assert np.array_equal(Smx.cpu().numpy(), S64.cpu().numpy())
