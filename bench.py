@@ -9,7 +9,9 @@ eigensolves.  One Bloch spectrum = all 256 x 16 = 4096 eigenvalues of one system
 
 value: systems/s with the system descriptors on the host and every intermediate on the device
        (device-timed with CUDA events on the launching stream; the per-step working set,
-       ~13 MB per system, is far larger than L2).
+       ~13 MB per system, is far larger than L2), for --precision (default mixed: the Gram
+       contractions on tensor cores through exact BF16 digit slices); the other route (FP64
+       CUDA-core Grams) is timed beside it and reported with the ratio of the two.
 e2e:   the same through lhf_bloch_spectra_host: descriptor upload and the copy of all
        eigenvalues back to host memory inside the timed region (wall clock, synchronised).
 --impl reference: the CPU oracle as it stands (the plain FP64 C reference), on this host's
@@ -96,7 +98,14 @@ class ClockSampler:
 # algorithmic work per system (roofline numerators)
 
 def work_model(sizes: list[dict], sweeps: int, matrices: int) -> dict:
-    """Algorithmic FLOPs / bytes per batch for the stages (roofline section)."""
+    """Algorithmic FLOPs / bytes per batch for the stages (the roofline numerators).
+
+    gram: 2 R_tot J m0^2 n_v per direction (the weighted-Gram contraction); gram_tc: the same
+    contraction as 28 exact BF16 digit-pair products (7 digits per operand, pairs a + b <= 6);
+    rank: (4 R_tot + 12) per window entry; dft: read 2 real blocks, write 2 complex blocks; eig:
+    9.33 m^3 per matrix (Cholesky and two triangular solves, complex) plus per Jacobi sweep
+    (m' - 1) steps of npair (npair - 1) / 2 off-diagonal 2x2 block updates (96 flops) and npair
+    diagonal updates (16 flops), m' = m rounded up to even, npair = m' / 2."""
     gram = 0.0
     dft_bytes = 0.0
     rank = 0.0
@@ -110,8 +119,12 @@ def work_model(sizes: list[dict], sweeps: int, matrices: int) -> dict:
         dft_bytes += s["n_blocks"] * m0 * m0 * (2 * 8 + 2 * 16)
     if sizes:
         m = sizes[0]["m0"]
-        eig = matrices * 9.33 * m ** 3 + sweeps * 20.0 * m * m * (m - 1 + (m & 1))
-    return {"gram_flops": gram, "rank_flops": rank, "dft_bytes": dft_bytes, "eig_flops": eig}
+        mp = m + (m & 1)
+        npair = mp // 2
+        per_sweep = (mp - 1) * (96.0 * npair * (npair - 1) / 2 + 16.0 * npair)
+        eig = matrices * 9.33 * m ** 3 + sweeps * per_sweep
+    return {"gram_flops": gram, "gram_tc_flops": 28.0 * gram, "rank_flops": rank, "dft_bytes": dft_bytes,
+            "eig_flops": eig}
 
 
 def fp64_peak_tflops() -> float:
@@ -198,6 +211,49 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 # GPU arm
 
+def replica_seeds(rank: int, batch: int, first: int = 3000) -> list[int]:
+    """Seeds of the tube_256 variants that replica `rank` solves per step (disjoint per rank)."""
+    return list(range(first + rank * batch, first + (rank + 1) * batch))
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """Maximum of a per-rank scalar over the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None):
+    """Device time (ms, max over ranks) of `steps` batched passes, with live stage times."""
+    import torch
+
+    ctx.eig_counters()
+    ctx.stage_times()
+    ctx.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(steps):
+        ctx.bloch_spectra(cfgs, eig, kst, precision)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    ms = t_start.elapsed_time(t_end)
+    ctx.set_profiling(False)
+    stages = ctx.stage_times()
+    sweeps, mats = ctx.eig_counters()
+    return max_over_ranks(ms, dist, "cuda"), stages, sweeps, mats, ck
+
+
 def run_gpu(args):
     import torch
 
@@ -214,49 +270,30 @@ def run_gpu(args):
     ctx = lhf.Context(local, stream)
     precision = lhf.MIXED if args.precision == "mixed" else lhf.FP64
     B = args.batch
-    cfgs = W.tube_256_batch(B, first_seed=3000 + rank * B)
-    sizes = []
-    for c in cfgs[:1]:
-        ctx.setup(c)
-        sizes.append(ctx.query_sizes())
+    cfgs = [W.tube_256(seed) for seed in replica_seeds(rank, B)]
+    ctx.setup(cfgs[0])
+    sizes = [ctx.query_sizes()]
     per_sys = sizes[0]["n_kpoints"] * sizes[0]["m0"]
     eig = torch.empty(B * per_sys, dtype=torch.float64, device="cuda")
     kst = torch.empty(B * sizes[0]["n_kpoints"], dtype=torch.int32, device="cuda")
-
-    for _ in range(max(args.warmup, 0)):
-        ctx.bloch_spectra(cfgs, eig, kst, precision)
-    torch.cuda.synchronize()
     all_sizes = []
     for c in cfgs:
         ctx.setup(c)
         all_sizes.append(ctx.query_sizes())
-    ctx.eig_counters()
-    ctx.stage_times()
-    ctx.set_profiling(True)
 
+    # FP64 route beside the mixed one (the metric compares the two); the main line is
+    # args.precision, timed last
+    other = lhf.FP64 if precision == lhf.MIXED else lhf.MIXED
+    for prec in (other, precision):
+        for _ in range(max(args.warmup, 0)):
+            ctx.bloch_spectra(cfgs, eig, kst, prec)
+    torch.cuda.synchronize()
+    ms_other, stages_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
     clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        ctx.bloch_spectra(cfgs, eig, kst, precision)
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
-    ctx.set_profiling(False)
-    stages = ctx.stage_times()
-    sweeps, mats = ctx.eig_counters()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, stages, sweeps, mats, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
     total_systems = B * args.steps * world
     value = total_systems / (ms / 1e3)
+    value_other = total_systems / (ms_other / 1e3)
     bad_k = int((kst < 0).sum().item())
 
     # end to end through the host entry point
@@ -268,33 +305,43 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.bloch_spectra_host(cfgs, host, hk, precision)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = total_systems / e2e_s
 
-    # roofline of the dominant kernel (stage with the most device time)
+    # rooflines per stage and of the dominant one (the stage with the most device time)
     work = work_model(all_sizes, sweeps, mats)
-    kernel_stages = ["basis", "potential", "gram", "ranksum", "dft", "eig"]
-    dom = max(kernel_stages, key=lambda s: stages[s][0])
-    dom_ms, dom_n = stages[dom]
-    per_launch_s = dom_ms / 1e3 / max(dom_n, 1)
+    kernel_stages = ["basis", "potential", "gram", "gram_tc", "ranksum", "dft", "eig"]
     peaks = measured_peaks()
-    if dom == "dft":
-        achieved = work["dft_bytes"] / per_launch_s / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-    else:
-        flops = {"gram": work["gram_flops"], "eig": work["eig_flops"] / max(args.steps, 1),
-                 "ranksum": work["rank_flops"]}.get(dom, float("nan"))
-        achieved = flops / per_launch_s / 1e12
-        peak = fp64_peak_tflops()
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
-                "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    rooflines = {}
+    for st_name in kernel_stages:
+        st_ms, st_n = stages[st_name]
+        if st_n == 0 or st_ms <= 0:
+            continue
+        per_launch_s = st_ms / 1e3 / st_n
+        if st_name == "dft":
+            achieved = work["dft_bytes"] / per_launch_s / 1e9
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            rooflines[st_name] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak,
+                                  "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        elif st_name == "gram_tc":
+            achieved = work["gram_tc_flops"] / per_launch_s / 1e12
+            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            rooflines[st_name] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": achieved / peak,
+                                  "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks
+                                  else "fallback"}
+        elif st_name in ("gram", "ranksum", "eig") and not (st_name == "gram" and args.precision == "mixed"):
+            flops = {"gram": work["gram_flops"], "ranksum": work["rank_flops"],
+                     "eig": work["eig_flops"] / max(args.steps, 1)}[st_name]
+            achieved = flops / per_launch_s / 1e12
+            peak = fp64_peak_tflops()
+            rooflines[st_name] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": achieved / peak, "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    dom = max(kernel_stages, key=lambda s: stages[s][0])
+    roof = dict(rooflines.get(dom, {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}))
+    roof["traffic"] = None
+    roof["kernel"] = dom
     stage_summary = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages.items()}
     gpu_launches = sum(stages[s][1] for s in kernel_stages)
 
@@ -307,9 +354,14 @@ def run_gpu(args):
                    "systems_per_step_per_gpu": B, "l2": "working set per step >> L2 (no flush needed)",
                    "parallelism": f"replicas x{world} (independent systems per GPU)"},
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": None, "d2h_bytes_per_step": B * per_sys * 8 + hk.nbytes},
+                "h2d_bytes_per_step": B * sizes[0]["desc_bytes"], "d2h_bytes_per_step": B * per_sys * 8 + hk.nbytes},
         "gpu_launches": gpu_launches,
         "roofline": roof,
+        "stage_rooflines": rooflines,
+        ("fp64" if other == lhf.FP64 else "mixed"): {
+            "value": value_other, "unit": UNIT, "ms_per_step": ms_other / args.steps,
+            "stages": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages_other.items()}},
+        "mixed_over_fp64": (value / value_other) if precision == lhf.MIXED else (value_other / value),
         "stages": stage_summary,
         "eig_sweeps_per_matrix": sweeps / max(mats, 1),
         "bad_kpoints": bad_k,
@@ -346,7 +398,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

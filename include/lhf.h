@@ -121,6 +121,7 @@ typedef struct {
     int window[3];      /* blocks computed per direction (overlap window, <= L) */
     int n_potential[3]; /* length of each direction's potential factor (n_cell periodic, else n) */
     int periodic;       /* 1 if every direction with L > 1 is periodic */
+    int desc_bytes;     /* bytes of the device descriptor copied host -> device per system and call */
 } lhf_sizes;
 
 /* Context creation.  device: CUDA ordinal; stream: a cudaStream_t (NULL = default stream).
@@ -209,11 +210,13 @@ lhf_status lhf_gram_factors(lhf_ctx *ctx, lhf_precision precision, int l, double
 /* Live stage timing.  With profiling enabled, every launch of the path is bracketed by CUDA
  * events recorded on the context stream (no synchronisation is added).  lhf_stage_times waits
  * for the stream, adds the elapsed times of all launches recorded since the previous call into
- * ms[stage] and their count into launches[stage] (arrays of LHF_NUM_STAGES, host), and clears
- * the record.  Stages: 0 basis samples (a1), 1 potential factors (a2), 2 Gram factors (a3-a4),
- * 3 rank sum (a5), 4 block DFT (a7), 5 k-point eigensolve (a8), 6 window zero fill (a6),
- * 7 descriptor upload. */
-#define LHF_NUM_STAGES 8
+ * ms[stage] and the number of kernels launched into launches[stage] (memory fills and copies
+ * for stages 6 and 7) (arrays of LHF_NUM_STAGES, host), and clears
+ * the record.  Stages: 0 basis samples (a1), 1 potential factors (a2), 2 Gram factors (a3-a4:
+ * the FP64 contraction, or the folding and digit slicing of LHF_MIXED), 3 rank sum (a5; open
+ * box: dense assembly), 4 block DFT (a7), 5 eigensolve (a8; open box: dense), 6 window zero
+ * fill (a6), 7 descriptor upload, 8 tensor-core contraction of LHF_MIXED. */
+#define LHF_NUM_STAGES 9
 lhf_status lhf_set_profiling(lhf_ctx *ctx, int enable);
 lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
 

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
 }  // namespace
 
 // host_L: [nsys][3] lattice sizes (host copy) used to size the grid of each pass.
-cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int /*max_lines*/,
+cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
   for (int d = 2; d >= 0; --d) {
@@ -165,6 +165,7 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int /*max
     k_dft_pass<<<grid, kDftThreads, smem, st>>>(sys, d);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (passes) ++*passes;
   }
   return cudaSuccess;
 }

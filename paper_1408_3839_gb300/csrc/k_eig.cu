@@ -12,7 +12,7 @@
 //      orthogonalisation: Jacobi with vectors S = V diag(sigma) V^H, directions with sigma below
 //      kLindepTol dropped, X = V_kept diag(sigma)^{-1/2}, C = X^H H X
 //   3. cyclic complex Jacobi on C: sweeps of m'-1 steps; each step applies m'/2 disjoint plane
-//      rotations at once (round-robin ordering), first to columns, then to rows.  The rotation
+//      rotations at once (round-robin ordering) as 2x2 block updates R1^H X R2.  The rotation
 //      for the pair (p, q) with C_pq = |g| e^{i phi} is J = [[c, s e^{i phi}], [-s e^{-i phi}, c]]
 //      with t = s/c the smaller root of t^2 + 2 tau t - 1 = 0, tau = (C_qq - C_pp) / (2 |g|);
 //      it zeroes C_pq.  Sweeps stop when the off-diagonal Frobenius norm is below 1e-16 of the
@@ -42,24 +42,36 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
 // per warp: A, B, V (m^2 complex each), rotation table (16 x {c, sr, si, p, q}), kept index
-// map, scales and overlap eigenvalues (32 each)
+// map, scales and overlap eigenvalues (32 each), and the (k1 < k2) pair-block table (120 x 2)
 __host__ __device__ inline size_t eig_warp_bytes(int m) {
   return (size_t)3 * m * m * sizeof(double2) + 16 * (3 * sizeof(double) + 2 * sizeof(int)) +
-         32 * (2 * sizeof(double) + 2 * sizeof(int));
+         32 * (2 * sizeof(double) + 2 * sizeof(int)) + 288;
 }
 
 struct RotTab {
   double *c, *sr, *si;
   int *p, *q;
+  const unsigned char *blk;  // [nblk][2] pair indices (k1, k2), k1 < k2
 };
 
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+
 // Cyclic Jacobi on the Hermitian m x m matrix A (shared memory, row-major), one warp.  Each sweep
-// is m'-1 steps (m' = m rounded up to even) of m'/2 disjoint rotations (round-robin ordering),
-// applied to the columns and then to the rows of A; with V non-null the rotations are also
-// accumulated into V's columns (V <- V J).  Stops when the off-diagonal Frobenius norm falls
-// below 1e-16 of the total.  Returns the number of sweeps.
+// is m'-1 steps (m' = m rounded up to even) of m'/2 disjoint rotations (round-robin ordering);
+// a step applies A <- J^H A J for the product J of its rotations.  R = [[c, s e^{i phi}],
+// [-s e^{-i phi}, c]] with t = s / c the smaller root of t^2 + 2 tau t - 1 = 0,
+// tau = (A_qq - A_pp) / (2 |A_pq|), zeroes A_pq; written with u = t / |A_pq| =
+// 2 sign(d) / (|d| + sqrt(d^2 + 4 |A_pq|^2)), d = A_qq - A_pp, so that one square root, one
+// division and one reciprocal square root give the rotation.  The lane of a pair updates its
+// own diagonal block in closed form (A_pp - t |A_pq|, A_qq + t |A_pq|, zero off-diagonal); the
+// blocks A[{p1,q1}, {p2,q2}] of two different pairs k1 < k2 are then updated as X <- R1^H X R2
+// by one lane each, and the mirrored block written as the conjugate transpose.  With V
+// non-null the rotations are also accumulated into V's columns (V <- V J).  Stops when the
+// off-diagonal Frobenius norm falls below 1e-16 of the total.  Returns the sweeps.
 __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab &R) {
   const int mm = m * m, mp = m + (m & 1), npair = mp / 2;
+  const int nblk = npair * (npair - 1) / 2;
   int sweep = 0;
   for (; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
@@ -86,15 +98,20 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
         double c = 1.0, sr = 0.0, si = 0.0;
         if (q < m) {
           const double2 g = A[p * m + q];
-          const double ag = hypot(g.x, g.y);
-          const double app = A[p * m + p].x, aqq = A[q * m + q].x;
-          if (ag > 1e-300 && ag > 1e-18 * sqrt(fabs(app * aqq))) {
-            const double tau = (aqq - app) / (2.0 * ag);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            const double sn = t * c;
-            sr = sn * g.x / ag;
-            si = sn * g.y / ag;
+          const double a = A[p * m + p].x, b = A[q * m + q].x;
+          const double ag2 = g.x * g.x + g.y * g.y;
+          if (ag2 > 1e-290 && ag2 > 1e-36 * fabs(a * b)) {
+            const double d = b - a;
+            const double u = copysign(2.0, d) / (fabs(d) + sqrt(fma(d, d, 4.0 * ag2)));
+            const double tg = u * ag2;  // t |A_pq|
+            c = rsqrt(fma(tg, u, 1.0));  // 1 / sqrt(1 + t^2)
+            const double uc = u * c;
+            sr = uc * g.x;
+            si = uc * g.y;
+            A[p * m + p] = make_double2(a - tg, 0.0);
+            A[q * m + q] = make_double2(b + tg, 0.0);
+            A[p * m + q] = make_double2(0.0, 0.0);
+            A[q * m + p] = make_double2(0.0, 0.0);
           }
         }
         R.p[lane] = p;
@@ -104,42 +121,54 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
         R.si[lane] = si;
       }
       __syncwarp();
-      const int work = npair * m;
-      for (int it = lane; it < work; it += 32) {  // columns: A <- A J (and V <- V J)
-        const int k = it / m, r = it - (it / m) * m;
-        const int p = R.p[k], q = R.q[k];
-        if (q >= m || (R.sr[k] == 0.0 && R.si[k] == 0.0)) continue;
-        const double c = R.c[k];
-        const double2 se = make_double2(R.sr[k], R.si[k]), sec = make_double2(R.sr[k], -R.si[k]);
-        {
-          const double2 x = A[r * m + p], y = A[r * m + q];
-          const double2 sy = cmul(sec, y), sx = cmul(se, x);
-          A[r * m + p] = make_double2(c * x.x - sy.x, c * x.y - sy.y);
-          A[r * m + q] = make_double2(sx.x + c * y.x, sx.y + c * y.y);
+      for (int bi = lane; bi < nblk; bi += 32) {
+        const int k1 = R.blk[2 * bi], k2 = R.blk[2 * bi + 1];
+        const bool r1 = !(R.sr[k1] == 0.0 && R.si[k1] == 0.0), r2 = !(R.sr[k2] == 0.0 && R.si[k2] == 0.0);
+        if (!r1 && !r2) continue;
+        const int p1 = R.p[k1], q1 = R.q[k1], p2 = R.p[k2], q2 = R.q[k2];
+        const bool v1 = q1 < m, v2 = q2 < m;  // q = m is the dummy of an odd order
+        const double c1 = R.c[k1], c2 = R.c[k2];
+        const double2 s1 = make_double2(R.sr[k1], R.si[k1]), s2 = make_double2(R.sr[k2], R.si[k2]);
+        const double2 z = make_double2(0.0, 0.0);
+        const double2 x11 = A[p1 * m + p2], x12 = v2 ? A[p1 * m + q2] : z;
+        const double2 x21 = v1 ? A[q1 * m + p2] : z, x22 = (v1 && v2) ? A[q1 * m + q2] : z;
+        // Y = X R2: Y[:,0] = c2 X[:,0] - conj(s2) X[:,1], Y[:,1] = s2 X[:,0] + c2 X[:,1]
+        const double2 y11 = csub(cscale(x11, c2), cmul(conjd(s2), x12));
+        const double2 y21 = csub(cscale(x21, c2), cmul(conjd(s2), x22));
+        const double2 y12 = cadd(cmul(s2, x11), cscale(x12, c2));
+        const double2 y22 = cadd(cmul(s2, x21), cscale(x22, c2));
+        // X' = R1^H Y: row 0 = c1 Y0 - s1 Y1, row 1 = conj(s1) Y0 + c1 Y1
+        const double2 n11 = csub(cscale(y11, c1), cmul(s1, y21));
+        const double2 n12 = csub(cscale(y12, c1), cmul(s1, y22));
+        const double2 n21 = cadd(cmul(conjd(s1), y11), cscale(y21, c1));
+        const double2 n22 = cadd(cmul(conjd(s1), y12), cscale(y22, c1));
+        A[p1 * m + p2] = n11;
+        A[p2 * m + p1] = conjd(n11);
+        if (v2) {
+          A[p1 * m + q2] = n12;
+          A[q2 * m + p1] = conjd(n12);
         }
-        if (V) {
+        if (v1) {
+          A[q1 * m + p2] = n21;
+          A[p2 * m + q1] = conjd(n21);
+        }
+        if (v1 && v2) {
+          A[q1 * m + q2] = n22;
+          A[q2 * m + q1] = conjd(n22);
+        }
+      }
+      if (V) {
+        const int work = npair * m;
+        for (int it = lane; it < work; it += 32) {  // V <- V J
+          const int k = it / m, r = it - (it / m) * m;
+          const int p = R.p[k], q = R.q[k];
+          if (q >= m || (R.sr[k] == 0.0 && R.si[k] == 0.0)) continue;
+          const double c = R.c[k];
+          const double2 se = make_double2(R.sr[k], R.si[k]);
           const double2 x = V[r * m + p], y = V[r * m + q];
-          const double2 sy = cmul(sec, y), sx = cmul(se, x);
-          V[r * m + p] = make_double2(c * x.x - sy.x, c * x.y - sy.y);
-          V[r * m + q] = make_double2(sx.x + c * y.x, sx.y + c * y.y);
+          V[r * m + p] = csub(cscale(x, c), cmul(conjd(se), y));
+          V[r * m + q] = cadd(cmul(se, x), cscale(y, c));
         }
-      }
-      __syncwarp();
-      for (int it = lane; it < work; it += 32) {  // rows: A <- J^H A
-        const int k = it / m, r = it - (it / m) * m;
-        const int p = R.p[k], q = R.q[k];
-        if (q >= m || (R.sr[k] == 0.0 && R.si[k] == 0.0)) continue;
-        const double c = R.c[k];
-        const double2 se = make_double2(R.sr[k], R.si[k]), sec = make_double2(R.sr[k], -R.si[k]);
-        const double2 x = A[p * m + r], y = A[q * m + r];
-        const double2 sy = cmul(se, y), sx = cmul(sec, x);
-        A[p * m + r] = make_double2(c * x.x - sy.x, c * x.y - sy.y);
-        A[q * m + r] = make_double2(sx.x + c * y.x, sx.y + c * y.y);
-      }
-      __syncwarp();
-      if (lane < npair && R.q[lane] < m && !(R.sr[lane] == 0.0 && R.si[lane] == 0.0)) {
-        A[R.p[lane] * m + R.q[lane]] = make_double2(0.0, 0.0);
-        A[R.q[lane] * m + R.p[lane]] = make_double2(0.0, 0.0);
       }
       __syncwarp();
     }
@@ -190,12 +219,22 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int kap = blockIdx.x * kEigWarps + warp;
-  if (kap >= s.nblocks) return;
+  // k-point of this warp: the i-th entry of the list of solved k-points (one per conjugate pair)
+  // when the system has one, otherwise warp i takes k-point i and leaves it to its partner if
+  // the partner's index is lower
+  const int widx = blockIdx.x * kEigWarps + warp;
+  int kap;
+  if (s.klist) {
+    if (widx >= s.nkhalf) return;
+    kap = s.klist[widx];
+  } else {
+    kap = widx;
+    if (kap >= s.nblocks) return;
+  }
   const int L0 = s.d[0].L, L1 = s.d[1].L, L2 = s.d[2].L;
   const int k0 = kap / (L1 * L2), k1 = (kap / L2) % L1, k2 = kap % L2;
   const int mk = (((L0 - k0) % L0) * L1 + (L1 - k1) % L1) * L2 + (L2 - k2) % L2;
-  if (mk < kap) return;  // the conjugate partner solves this pair
+  if (!s.klist && mk < kap) return;  // the conjugate partner solves this pair
   const int m0 = s.m0;
   extern __shared__ unsigned char smraw[];
   unsigned char *base = smraw + (size_t)warp * eig_warp_bytes(max_m0);
@@ -209,7 +248,22 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   int *rp = reinterpret_cast<int *>(sg + 32), *rq = rp + 16;
   int *kidx = rq + 16;      // [32] original index of kept function a
   int *kidx2 = kidx + 32;   // [32] kept overlap eigen-directions (canonical path)
-  const RotTab R{rc, rsr, rsi, rp, rq};
+  unsigned char *blk = reinterpret_cast<unsigned char *>(kidx2 + 32);  // [<= 120][2]
+  {
+    // pairs k1 < k2 ordered by k2, so that the first n (n - 1) / 2 entries are those of n pairs
+    const int np = (m0 + 1) / 2;  // pairs of the largest order this warp may rotate
+    for (int bi = lane; bi < np * (np - 1) / 2; bi += 32) {
+      int k2 = 1, rem = bi;
+      while (rem >= k2) {
+        rem -= k2;
+        ++k2;
+      }
+      blk[2 * bi] = (unsigned char)rem;
+      blk[2 * bi + 1] = (unsigned char)k2;
+    }
+    __syncwarp();
+  }
+  const RotTab R{rc, rsr, rsi, rp, rq, blk};
 
   const double2 *Hb = reinterpret_cast<const double2 *>(s.Hbar) + (int64_t)kap * m0 * m0;
   const double2 *Sb = reinterpret_cast<const double2 *>(s.Sbar) + (int64_t)kap * m0 * m0;

@@ -120,8 +120,7 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
 
 __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
-  if (s.box) return;
-  GramItem it;
+  GramItem it;  // open boxes: directions 1, 2 only (direction 0 has no window here)
   if (!decode_gram(s, blockIdx.x, it)) return;
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv;

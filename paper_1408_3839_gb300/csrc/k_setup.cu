@@ -30,15 +30,23 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
   const int m0 = s.m0;
   int l = 0;
   for (; l < 3; ++l) {
-    int64_t cnt = (int64_t)m0 * s.d[l].n;
+    int64_t cnt = (int64_t)m0 * (s.d[l].n + s.d[l].gext);
     if (item < cnt) break;
     item -= cnt;
   }
   if (l == 3) return;
   const DirDev &D = s.d[l];
-  const int mu = (int)(item / D.n);
-  const int i = (int)(item - (int64_t)mu * D.n);
-  const double x = D.x0 + (i + 0.5) * D.h;
+  const int nx = D.n + D.gext;
+  const int mu = (int)(item / nx);
+  const int e = (int)(item - (int64_t)mu * nx);  // sample index: grid node i = e - gext
+  // samples outside the (widened) cut range are exact zeros: no floating-point work
+  int rel = e - s.node_lo[l][mu];
+  if (D.periodic && rel < 0) rel += D.n;
+  if (rel < 0 || rel >= s.node_span[l][mu]) {
+    s.ws[D.offG + (int64_t)mu * nx + e] = 0.0;
+    return;
+  }
+  const double x = D.x0 + (e - D.gext + 0.5) * D.h;
   const double A = s.centre[mu][l];
   const double cut = s.cut[mu];
   const double al = s.alpha[mu];
@@ -56,7 +64,7 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
   } else {
     g = gto_factor(x - A, al, cut, pdir, pn);
   }
-  s.ws[D.offG + (int64_t)mu * D.n + i] = g;
+  s.ws[D.offG + (int64_t)mu * nx + e] = g;
 }
 
 // int_{-d}^{d} exp(-(m + u)^2) du = exp(-m^2) sum_k H_2k(m) 2 d^(2k+1) / (2k+1)!  (Taylor series
@@ -103,6 +111,85 @@ __device__ double gauss_cell_integral(double t, double lo, double hi, double c) 
   return f * (erfc(-B) - erfc(-A));
 }
 
+// Sum over the images k = klo .. khi (weight 1/2 on k = +-kmax when the window is even) of the
+// cell integrals int_{cell} exp(-t^2 (x - c0 - k b)^2) dx, times t, for a cell of width h
+// centred at c0 + xc (xc = cell midpoint - c0), delta = t h.  With m_k = t (xc - k b) and
+// d = delta / 2 the integral is exp(-m_k^2) S(m_k^2) / t, where
+//   S = sum_j a_j H_2j(m) = sum_j b_j y^j,  y = m^2,  a_j = 2 d^(2j+1) / (2j+1)!
+// (Taylor series of the Gaussian about the cell centre, the odd terms integrating to zero), and
+// H_2j(m) = sum_i (2j)! (-1)^(j-i) 4^i / ((j-i)! (2i)!) y^i, so that
+//   b_i = 4^i / (2i)! sum_{l >= 0} (-1)^l 2 d^(2(i+l)+1) / ((2(i+l)+1) l!).
+// The series is cut after degree J, the first j with (22 d)^(2j+2) / (2j+3)! < 1e-18 (|m| <= 11
+// within the image reach).  exp(-m_k^2) follows the images by exp(-m_{k+-1}^2) =
+// exp(-m_k^2) R, R = exp(-+2 m_k s - s^2), s = t b, R <- R exp(-2 s^2), walking outward from the
+// image nearest to the cell and restarted from exp every 8 images, so that the dominant terms
+// come from small exponents and the product's rounding stays within a few tens of ulp.
+constexpr double kTaylorMaxDelta = 0.25;
+constexpr int kTaylorMaxJ = 16;
+
+__device__ double image_sum_taylor(double t, double xc, double b, double delta, int klo, int khi,
+                                   int kmax, bool even) {
+  const double d = 0.5 * delta;
+  const double x22 = (22.0 * d) * (22.0 * d);
+  int J = 1;
+  {
+    double bound = x22 * x22 * kRecip[0] * kRecip[1] * kRecip[2] * kRecip[3] * kRecip[4];  // j = 1
+    while (bound >= 1e-18 && J < kTaylorMaxJ) {
+      ++J;
+      bound *= x22 * kRecip[2 * J + 1] * kRecip[2 * J + 2];
+    }
+  }
+  // coefficients b_0 .. b_J
+  double bc[kTaylorMaxJ + 1];
+  const double d2 = d * d;
+  for (int i = 0; i <= J; ++i) {
+    double dp = 2.0 * d;  // 2 d^(2(i+l)+1), l = 0
+    for (int u = 0; u < i; ++u) dp *= d2;
+    double sum = 0.0, lf = 1.0;  // lf = 1 / l!
+    for (int l = 0; i + l <= J; ++l) {
+      const double term = dp * kRecip[2 * (i + l)] * lf;  // / (2(i+l)+1)
+      sum += (l & 1) ? -term : term;
+      dp *= d2;
+      lf *= kRecip[l];  // 1 / (l+1)!
+    }
+    double f = sum;  // * 4^i / (2i)!
+    for (int u = 1; u <= 2 * i; ++u) f *= kRecip[u - 1];
+    for (int u = 0; u < i; ++u) f *= 4.0;
+    bc[i] = f;
+  }
+  const double sb = t * b;
+  const double Q = exp(-2.0 * sb * sb);
+  if (klo > khi) return 0.0;  // no image within reach
+  // the image nearest to the cell, clamped to the window
+  int kc = (int)rint(xc / b);
+  kc = kc < klo ? klo : (kc > khi ? khi : kc);
+  double v = 0.0;
+  // outward: dir = +1 (k = kc .. khi, m decreasing), dir = -1 (k = kc-1 .. klo, m increasing)
+  for (int dir = 1; dir >= -1; dir -= 2) {
+    const int kbeg = dir > 0 ? kc : kc - 1;
+    const int kend = dir > 0 ? khi + 1 : klo - 1;
+    for (int k0 = kbeg; k0 != kend;) {
+      double m = t * (xc - k0 * b);
+      double e = exp(-m * m);
+      double R = exp(dir * 2.0 * m * sb - sb * sb);
+      const int steps = dir > 0 ? min(8, kend - k0) : min(8, k0 - kend);
+      for (int u = 0; u < steps; ++u) {
+        const int k = k0 + dir * u;
+        const double y = m * m;
+        double S = bc[J];
+        for (int j = J - 1; j >= 0; --j) S = fma(S, y, bc[j]);
+        const double w = (even && (k == kmax || k == -kmax)) ? 0.5 * e : e;
+        v = fma(w, S, v);
+        e *= R;
+        R *= Q;
+        m -= dir * sb;
+      }
+      k0 += dir * steps;
+    }
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,32 +217,9 @@ __global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sy
     double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
     int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
     int khi = (khi_f > kmax) ? kmax : (int)khi_f;
-    const double delta = t * D.h, sb = t * D.b;
-    if (delta <= 1e-3 && sb <= 0.1) {
-      // Wide Gaussian: with m_k = t (x_mid - c0 - k b), the cell integral is
-      // h exp(-m_k^2) [1 + (2 m^2 - 1) delta^2 / 12 + (4 m^4 - 12 m^2 + 3) delta^4 / 480] up to
-      // O(delta^6) (the Taylor series about the cell centre), and exp(-m_k^2) follows k by
-      // exp(-m_{k+1}^2) = exp(-m_k^2) R_k, R_{k+1} = R_k exp(-2 s^2), s = t b, restarted from exp
-      // every 8 images so that the product's rounding stays within 32 ulp.
-      const double xm = 0.5 * (lo + hi);
-      const double d2 = delta * delta, c2 = d2 * (1.0 / 12.0), c4 = d2 * d2 * (1.0 / 480.0);
-      const double Q = exp(-2.0 * sb * sb);
-      for (int k0 = klo; k0 <= khi; k0 += 8) {
-        double mk = t * (xm - c0 - k0 * D.b);
-        double e = exp(-mk * mk);
-        double R = exp(2.0 * mk * sb - sb * sb);
-        const int kend = min(k0 + 8, khi + 1);
-        for (int k = k0; k < kend; ++k) {
-          const double m2 = mk * mk;
-          const double corr = 1.0 + (2.0 * m2 - 1.0) * c2 + ((4.0 * m2 - 12.0) * m2 + 3.0) * c4;
-          const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
-          v += wk * e * corr;
-          e *= R;
-          R *= Q;
-          mk = t * (xm - c0 - (k + 1) * D.b);
-        }
-      }
-      v *= D.h;
+    const double delta = t * D.h;
+    if (delta <= kTaylorMaxDelta) {
+      v = image_sum_taylor(t, 0.5 * (lo + hi) - c0, D.b, delta, klo, khi, kmax, even) / t;
     } else {
       for (int k = klo; k <= khi; ++k) {
         const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -45,6 +47,10 @@ struct Plan {
   size_t blocks_doubles = 0;  // nblocks * m0^2
   int basis_items = 0, pot_items = 0, gram_blocks = 0, rank_items = 0;
   int nv_max = 0;
+  // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
+  int box_items = 0, box_width = 0;
+  size_t zcell_off = 0, dense_off = 0;
+  std::vector<double> zcell;  // host copy of the per-cell charges (box)
 };
 
 constexpr size_t kAlign = 32;  // doubles (256 bytes)
@@ -78,15 +84,18 @@ struct lhf_ctx {
   size_t tc_cap = 0;
   cudaEvent_t tc_copied = nullptr;  // the staging copy has been consumed
   std::vector<int> host_L;
+  // solved k-points (one per conjugate pair) per lattice shape, on the device
+  std::map<std::array<int, 3>, std::pair<int *, int>> klists;
   // live stage timing
   bool prof = false;
   struct Mark {
     int stage;
     cudaEvent_t a, b;
+    int kernels;  // kernel launches (or copies/fills) inside the bracket
   };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> pool;
-  Mark open_mark{-1, nullptr, nullptr};
+  Mark open_mark{-1, nullptr, nullptr, 0};
 
   cudaEvent_t take_event() {
     if (!pool.empty()) {
@@ -103,14 +112,15 @@ struct lhf_ctx {
   }
   void begin(int stage) {
     if (!prof) return;
-    open_mark = {stage, take_event(), take_event()};
+    open_mark = {stage, take_event(), take_event(), 0};
     if (open_mark.a) cudaEventRecord(open_mark.a, stream);
   }
-  void end() {
+  void end(int kernels = 1) {
     if (!prof || open_mark.stage < 0) return;
     if (open_mark.b) cudaEventRecord(open_mark.b, stream);
+    open_mark.kernels = kernels;
     if (open_mark.a && open_mark.b) marks.push_back(open_mark);
-    open_mark = {-1, nullptr, nullptr};
+    open_mark = {-1, nullptr, nullptr, 0};
   }
 
   lhf_status fail(lhf_status st, const char *fmt, ...) {
@@ -243,17 +253,18 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
         return c->fail(LHF_ERR_ARG, "direction %d: n_cell h must equal b", l);
     }
   }
-  if (open_lattice) {
-    return c->fail(LHF_ERR_UNSUPPORTED, "open boxes with L > 1 are not supported by this build");
-  }
-  if (!s.zcell.empty()) return c->fail(LHF_ERR_UNSUPPORTED, "per-cell charges need an open box");
+  // open lattice (Sec. 3.2 box): direction 0 only, single cells across
+  const bool box = open_lattice != 0;
+  if (box && (open_lattice != 1 || s.L[1] != 1 || s.L[2] != 1 || s.periodic[1] || s.periodic[2]))
+    return c->fail(LHF_ERR_UNSUPPORTED, "open lattices are supported along direction 0 only, as an (L,1,1) box");
+  if (!s.zcell.empty() && !box) return c->fail(LHF_ERR_UNSUPPORTED, "per-cell charges need an open box");
 
   const int m0 = s.m0, Rt = s.M0 * s.R, mm = m0 * m0;
   sd.m0 = m0;
   sd.M0 = s.M0;
   sd.R = s.R;
   sd.Rt = Rt;
-  sd.box = 0;
+  sd.box = box ? 1 : 0;
   for (int mu = 0; mu < m0; ++mu) {
     sd.kind[mu] = s.kind[mu];
     sd.alpha[mu] = s.alpha[mu];
@@ -295,6 +306,9 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     D.cell0 = s.cell0[l];
     D.b = s.b[l];
     D.invP = 1.0 / (s.L[l] * s.b[l]);
+    // open box direction 0: the cell-0 basis copies are sampled (L0 - 1) n_c nodes further to
+    // the left, so that the copy in cell p is the plain offset p n_c
+    D.gext = (box && l == 0) ? (s.L[0] - 1) * D.nc : 0;
     // support cells of each cell-0 basis copy, dilated by one node for the P1 cross terms
     for (int mu = 0; mu < m0; ++mu) {
       if (D.lattice) {
@@ -303,6 +317,26 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
         sd.cell_hi[l][mu] = (int)floor((A + cut + D.h - D.cell0) / D.b);
       } else {
         sd.cell_lo[l][mu] = sd.cell_hi[l][mu] = 0;
+      }
+      // samples e (node i = e - gext, x = x0 + (i + 1/2) h) with |x - A| <= cut, widened by two
+      // nodes per side
+      const double A = s.centre[3 * mu + l], cut = sd.cut[mu];
+      const double flo = floor((A - cut - D.x0) / D.h - 0.5) + D.gext - 2.0;
+      const double fhi = ceil((A + cut - D.x0) / D.h - 0.5) + D.gext + 2.0;
+      if (D.periodic) {
+        if (fhi - flo + 1.0 >= (double)D.n) {
+          sd.node_lo[l][mu] = 0;
+          sd.node_span[l][mu] = D.n;
+        } else {
+          const long long lo = (long long)flo;
+          sd.node_lo[l][mu] = (int)(((lo % D.n) + D.n) % D.n);
+          sd.node_span[l][mu] = (int)(fhi - flo) + 1;
+        }
+      } else {
+        const double nx = (double)D.n + D.gext;
+        const double lo = std::max(flo, 0.0), hi = std::min(fhi, nx - 1.0);
+        sd.node_lo[l][mu] = (int)std::min(lo, nx);
+        sd.node_span[l][mu] = hi >= lo ? (int)(hi - lo) + 1 : 0;
       }
     }
     // overlap window of displacements j: blocks outside are exact zeros
@@ -320,20 +354,34 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
         D.jlo = jmin;
         D.J = jmax - jmin + 1;
       }
+    } else if (box && l == 0) {
+      // cell pairs (p, p + d) whose supports can meet; the factors live in the box region
+      int dmin = 1 << 30, dmax = -(1 << 30);
+      for (int mu = 0; mu < m0; ++mu)
+        for (int nu = 0; nu < m0; ++nu) {
+          dmin = std::min(dmin, sd.cell_lo[l][mu] - sd.cell_hi[l][nu]);
+          dmax = std::max(dmax, sd.cell_hi[l][mu] - sd.cell_lo[l][nu]);
+        }
+      dmin = std::max(dmin, 1 - D.L);
+      dmax = std::min(dmax, D.L - 1);
+      sd.bjlo = dmin;
+      sd.bJ = dmax - dmin + 1;
+      D.jlo = 0;
+      D.J = 0;  // no translation-invariant window
     } else {
       D.jlo = 0;
       D.J = 1;
     }
-    sd.nwin *= D.J;
+    if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
-    P.basis_items += m0 * D.n;
+    P.basis_items += m0 * (D.n + D.gext);
     P.pot_items += Rt * D.nv;
     P.gram_blocks += D.J * m0;
-    P.nv_max = std::max(P.nv_max, D.nv);
+    if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
   for (int l = 0; l < 3; ++l) {
     sd.d[l].offG = (int64_t)off;
-    off = align_up(off + (size_t)m0 * sd.d[l].n);
+    off = align_up(off + (size_t)m0 * (sd.d[l].n + sd.d[l].gext));
   }
   for (int l = 0; l < 3; ++l) {
     sd.d[l].offV = (int64_t)off;
@@ -345,10 +393,21 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
   }
   P.s0_off = off;
   off = align_up(off + (size_t)m0);
+  if (box) {
+    sd.offCb = (int64_t)off;
+    off = align_up(off + (size_t)s.L[0] * sd.bJ * (Rt + 2) * mm);
+    P.box_items = sd.bJ * mm;
+    for (int mu = 0; mu < m0; ++mu) P.box_width = std::max(P.box_width, sd.node_span[0][mu]);
+    if (lhf::box_gram_smem_bytes(P.box_width) > 200 * 1024)
+      return c->fail(LHF_ERR_UNSUPPORTED, "open box: a basis function spans %d nodes (limit 12800)", P.box_width);
+    P.zcell = s.zcell;
+    P.zcell_off = off;
+    off = align_up(off + (size_t)s.L[0] * s.M0);
+  }
   for (int l = 0; l < 3; ++l) {
     DirDev &D = sd.d[l];
     D.Kpad = (D.nv + 63) / 64 * 64;
-    if (mixed) {
+    if (mixed && !box) {
       const size_t rows = (size_t)D.J * mm;
       D.offA = (int64_t)off;
       off = align_up(off + (lhf::kSlices * rows * D.Kpad * 2 + 7) / 8);
@@ -361,11 +420,20 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
       if (D.Kpad > 448) return c->fail(LHF_ERR_UNSUPPORTED, "mixed precision: direction %d has %d nodes per contraction (limit 448)", l, D.nv);
     }
   }
-  P.mixed = mixed;
+  P.mixed = mixed && !box;  // the box's Grams run in FP64 in both modes
+  if (box) {
+    const size_t Nb = (size_t)m0 * s.L[0];
+    if (Nb > 8192) return c->fail(LHF_ERR_UNSUPPORTED, "open box: N_b = %zu above 8192", Nb);
+    P.dense_off = off;
+    off = align_up(off + lhf::dense_eig_workspace_doubles((int)Nb));
+    P.blocks_doubles = align_up(Nb * Nb);
+    P.rank_items = 0;
+  } else {
+    P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
+    P.rank_items = sd.nwin * mm;
+    if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
+  }
   P.ws = off;
-  P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
-  P.rank_items = sd.nwin * mm;
-  if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   return LHF_OK;
 }
 
@@ -444,13 +512,19 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
     max_m0 = std::max(max_m0, p.sd.m0);
     max_rt = std::max(max_rt, p.sd.Rt);
   }
-  if (!ps[0].mixed)
-    return c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
-                                         max_of(ps, &Plan::nv_max), c->stream),
-                   "Gram kernel");
+  if (!ps[0].mixed) {
+    c->begin(2);
+    lhf_status st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
+                                                  max_of(ps, &Plan::nv_max), c->stream),
+                            "Gram kernel");
+    c->end();
+    return st;
+  }
+  c->begin(2);
   lhf_status st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
                                                   max_of(ps, &Plan::nv_max), 3 * max_rt, c->stream),
                           "digit-plane kernels");
+  c->end(2);
   if (st != LHF_OK) return st;
   std::vector<SysDev> host(nsys);
   for (int i = 0; i < nsys; ++i) host[i] = ps[i].sd;
@@ -472,8 +546,10 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
     if (st != LHF_OK) return st;
     c->tc_cap = need;
   }
+  c->begin(8);
   cudaError_t e = lhf::launch_gram_tc_impl(host.data(), nsys, c->tc_buf, c->tc_cap, c->tc_host, c->tc_cap,
                                            c->d_flags, c->stream);
+  c->end();
   if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "shape outside the tensor-core kernel's limits");
   st = c->cuda(e, "tensor-core Gram kernel");
   if (st != LHF_OK) return st;
@@ -485,13 +561,13 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
   // a6: blocks outside the window are exact zeros
   for (const Plan &p : ps)
-    if (p.sd.nwin < p.sd.nblocks) {
+    if (!p.sd.box && p.sd.nwin < p.sd.nblocks) {
       const size_t bytes = (size_t)p.sd.nblocks * p.sd.m0 * p.sd.m0 * sizeof(double);
       c->begin(6);
       lhf_status st = c->cuda(cudaMemsetAsync(p.sd.H, 0, bytes, c->stream), "cudaMemsetAsync");
       if (st != LHF_OK) return st;
       st = c->cuda(cudaMemsetAsync(p.sd.S, 0, bytes, c->stream), "cudaMemsetAsync");
-      c->end();
+      c->end(2);
       if (st != LHF_OK) return st;
     }
   lhf_status st;
@@ -503,14 +579,77 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
   c->end();
   if (st != LHF_OK) return st;
-  c->begin(2);
   st = run_gram(c, ps);
-  c->end();
   if (st != LHF_OK) return st;
   c->begin(3);
   st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, &Plan::rank_items), c->stream), "rank-sum kernel");
   c->end();
   return st;
+}
+
+// Per-cell charges of open boxes into their workspace regions (pageable source: the copy is
+// staged before cudaMemcpyAsync returns).
+lhf_status upload_zcell(lhf_ctx *c, const std::vector<Plan> &ps) {
+  for (const Plan &p : ps)
+    if (p.sd.zcell) {
+      lhf_status st = c->cuda(cudaMemcpyAsync(const_cast<double *>(p.sd.zcell), p.zcell.data(),
+                                              p.zcell.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                              "cudaMemcpyAsync");
+      if (st != LHF_OK) return st;
+    }
+  return LHF_OK;
+}
+
+// a1, a2 and the factors of open boxes (uploaded, all plans boxes): FP64 Grams of the single-cell
+// directions, then the direction-0 factors between cell pairs.
+lhf_status run_box_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
+  const int nsys = (int)ps.size();
+  lhf_status st = upload_zcell(c, ps);
+  if (st != LHF_OK) return st;
+  int max_m0 = 0, width = 0;
+  for (const Plan &p : ps) {
+    max_m0 = std::max(max_m0, p.sd.m0);
+    width = std::max(width, p.box_width);
+  }
+  c->begin(0);
+  st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(1);
+  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(2);
+  st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
+                                     max_of(ps, &Plan::nv_max), c->stream),
+               "Gram kernel");
+  if (st == LHF_OK)
+    st = c->cuda(lhf::launch_box_gram(c->d_sys, nsys, max_of(ps, &Plan::box_items), width, c->stream),
+                 "box Gram kernel");
+  c->end(2);
+  return st;
+}
+
+// Dense H, S of open boxes (after run_box_factors).
+lhf_status run_box_assemble(lhf_ctx *c, const std::vector<Plan> &ps) {
+  long long entries = 0;
+  for (const Plan &p : ps) {
+    const long long nb = (long long)p.sd.m0 * p.sd.d[0].L;
+    entries = std::max(entries, nb * nb);
+  }
+  c->begin(3);
+  lhf_status st = c->cuda(lhf::launch_box_assemble(c->d_sys, (int)ps.size(), entries, c->stream), "box assembly kernel");
+  c->end();
+  return st;
+}
+
+// Dense generalized eigensolve of one pencil with the context's flags word.
+lhf_status run_dense_eig(lhf_ctx *c, const double *H, const double *S, int N, double *eig, double *work) {
+  c->begin(5);
+  cudaError_t e = lhf::launch_dense_eig(H, S, N, eig, work, c->d_flags, c->stream);
+  c->end();
+  if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "cooperative launch not available");
+  return c->cuda(e, "dense eigensolver");
 }
 
 lhf_status run_dft(lhf_ctx *c, const std::vector<Plan> &ps) {
@@ -520,15 +659,50 @@ lhf_status run_dft(lhf_ctx *c, const std::vector<Plan> &ps) {
     c->host_L[4 * i + 3] = ps[i].sd.m0;
   }
   c->begin(4);
-  lhf_status st = c->cuda(lhf::launch_dft(c->d_sys, (int)ps.size(), c->host_L.data(), 0, c->stream), "DFT kernel");
-  c->end();
+  int passes = 0;
+  lhf_status st = c->cuda(lhf::launch_dft(c->d_sys, (int)ps.size(), c->host_L.data(), &passes, c->stream), "DFT kernel");
+  c->end(passes);
   return st;
+}
+
+// List of the k-points kappa with kappa <= -kappa (row-major index of (k0, k1, k2) mod L):
+// one per conjugate pair; built once per lattice shape and kept on the device.
+lhf_status klist_for(lhf_ctx *c, const int *L, const int **out, int *count) {
+  const std::array<int, 3> key{L[0], L[1], L[2]};
+  auto it = c->klists.find(key);
+  if (it == c->klists.end()) {
+    std::vector<int> v;
+    for (int a = 0; a < L[0]; ++a)
+      for (int b = 0; b < L[1]; ++b)
+        for (int d = 0; d < L[2]; ++d) {
+          const int k = (a * L[1] + b) * L[2] + d;
+          const int mk = (((L[0] - a) % L[0]) * L[1] + (L[1] - b) % L[1]) * L[2] + (L[2] - d) % L[2];
+          if (k <= mk) v.push_back(k);
+        }
+    int *dptr = nullptr;
+    lhf_status st = c->cuda(cudaMalloc(&dptr, v.size() * sizeof(int)), "cudaMalloc");
+    if (st != LHF_OK) return st;
+    st = c->cuda(cudaMemcpy(dptr, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (st != LHF_OK) {
+      cudaFree(dptr);
+      return st;
+    }
+    it = c->klists.emplace(key, std::make_pair(dptr, (int)v.size())).first;
+  }
+  *out = it->second.first;
+  *count = it->second.second;
+  return LHF_OK;
+}
+
+lhf_status set_klist(lhf_ctx *c, SysDev &sd) {
+  const int L[3] = {sd.d[0].L, sd.d[1].L, sd.d[2].L};
+  return klist_for(c, L, &sd.klist, &sd.nkhalf);
 }
 
 lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
   int max_k = 0, max_m0 = 0;
   for (const Plan &p : ps) {
-    max_k = std::max(max_k, p.sd.nblocks);
+    max_k = std::max(max_k, p.sd.klist ? p.sd.nkhalf : p.sd.nblocks);
     max_m0 = std::max(max_m0, p.sd.m0);
   }
   c->begin(5);
@@ -536,7 +710,7 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
   if (st == LHF_OK)
     st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream),
                  "eigen kernel");
-  c->end();
+  c->end(2);
   return st;
 }
 
@@ -553,12 +727,18 @@ lhf_status system_from_desc(lhf_ctx *c, const lhf_system_desc *d, HostSystem &s)
   return LHF_OK;
 }
 
+// Point the descriptor's workspace regions at base.
+void bind_ws(Plan &p, double *base) {
+  p.sd.ws = base;
+  p.sd.s0 = base + p.s0_off;
+  p.sd.zcell = (p.sd.box && !p.zcell.empty()) ? base + p.zcell_off : nullptr;
+}
+
 // Plan one system with workspace at ws_base and internal H, S, Hbar, Sbar after its factors.
 size_t internal_doubles(const Plan &p) { return p.ws + 6 * p.blocks_doubles; }
 
 void place_internal(Plan &p, double *base) {
-  p.sd.ws = base;
-  p.sd.s0 = base + p.s0_off;
+  bind_ws(p, base);
   double *blk = base + p.ws;
   p.sd.H = blk;
   p.sd.S = blk + p.blocks_doubles;
@@ -624,6 +804,7 @@ void lhf_destroy(lhf_ctx *c) {
     cudaEventDestroy(m.b);
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  for (auto &kv : c->klists) cudaFree(kv.second.first);
   delete c;
 }
 
@@ -658,7 +839,7 @@ lhf_status lhf_stage_times(lhf_ctx *c, double *ms, int *launches) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess && m.stage >= 0 && m.stage < LHF_NUM_STAGES) {
       ms[m.stage] += t;
-      launches[m.stage] += 1;
+      launches[m.stage] += m.kernels;
     } else {
       cudaGetLastError();
     }
@@ -688,7 +869,7 @@ lhf_status lhf_sync(lhf_ctx *c) {
   if (st != LHF_OK) return st;
   st = c->cuda(cudaMemset(c->d_flags, 0, sizeof(unsigned)), "cudaMemset");
   if (st != LHF_OK) return st;
-  if (flags & lhf::kFlagTimeout) return c->fail(LHF_ERR_TIMEOUT, "a bounded wait of the tensor-core Gram kernel gave up");
+  if (flags & lhf::kFlagTimeout) return c->fail(LHF_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core Gram pipeline or dense-solver grid barrier)");
   if (flags & lhf::kFlagNotSpd) return c->fail(LHF_ERR_NOT_SPD, "an overlap block was not positive definite");
   return LHF_OK;
 }
@@ -732,8 +913,9 @@ lhf_status lhf_query_sizes(lhf_ctx *c, lhf_sizes *out) {
   out->n_basis = P.sd.m0 * P.sd.nblocks;
   out->rank = P.sd.Rt;
   out->periodic = P.sd.box ? 0 : 1;
+  out->desc_bytes = (int)sizeof(SysDev);
   for (int l = 0; l < 3; ++l) {
-    out->window[l] = P.sd.d[l].J;
+    out->window[l] = (P.sd.box && l == 0) ? P.sd.bJ : P.sd.d[l].J;
     out->n_potential[l] = P.sd.d[l].nv;
   }
   return LHF_OK;
@@ -754,11 +936,16 @@ lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *c, lhf_precision prec, double 
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
-  ps[0].sd.ws = c->ws;
+  bind_ws(ps[0], c->ws);
   ps[0].sd.H = H;
   ps[0].sd.S = S;
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
+  if (ps[0].sd.box) {
+    st = run_box_factors(c, ps);
+    if (st != LHF_OK) return st;
+    return run_box_assemble(c, ps);
+  }
   return run_assembly(c, ps);
 }
 
@@ -768,6 +955,7 @@ lhf_status lhf_circulant_fft(lhf_ctx *c, const double *H, const double *S, doubl
   std::vector<Plan> ps(1);
   lhf_status st = current_plan(c, ps[0]);
   if (st != LHF_OK) return st;
+  if (ps[0].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "the block DFT needs a periodic lattice");
   ps[0].sd.H = const_cast<double *>(H);
   ps[0].sd.S = const_cast<double *>(S);
   ps[0].sd.Hbar = Hbar;
@@ -783,14 +971,16 @@ lhf_status lhf_k_point_eigensolve(lhf_ctx *c, const double *Hbar, const double *
   std::vector<Plan> ps(1);
   lhf_status st = current_plan(c, ps[0]);
   if (st != LHF_OK) return st;
+  if (ps[0].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "k-point eigensolves need a periodic lattice");
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
-  ps[0].sd.ws = c->ws;
-  ps[0].sd.s0 = c->ws + ps[0].s0_off;
+  bind_ws(ps[0], c->ws);
   ps[0].sd.Hbar = const_cast<double *>(Hbar);
   ps[0].sd.Sbar = const_cast<double *>(Sbar);
   ps[0].sd.eig = eig;
   ps[0].sd.kstat = kstat;
+  st = set_klist(c, ps[0].sd);
+  if (st != LHF_OK) return st;
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
   return run_eig(c, ps);
@@ -798,11 +988,11 @@ lhf_status lhf_k_point_eigensolve(lhf_ctx *c, const double *Hbar, const double *
 
 lhf_status lhf_dense_eigensolve(lhf_ctx *c, const double *H, const double *S, int N, double *eig) {
   if (!c) return LHF_ERR_ARG;
-  (void)H;
-  (void)S;
-  (void)N;
-  (void)eig;
-  return c->fail(LHF_ERR_UNSUPPORTED, "dense eigensolver not available in this build");
+  if (!H || !S || !eig) return c->fail(LHF_ERR_ARG, "H, S and eig are required");
+  if (N < 1 || N > 8192) return c->fail(LHF_ERR_ARG, "N = %d outside [1, 8192]", N);
+  lhf_status st = ensure_ws(c, lhf::dense_eig_workspace_doubles(N));
+  if (st != LHF_OK) return st;
+  return run_dense_eig(c, H, S, N, eig, c->ws);
 }
 
 lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,
@@ -811,36 +1001,66 @@ lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *system
   if (nsys < 1 || !systems || !eig) return c->fail(LHF_ERR_ARG, "nsys >= 1, systems and eig are required");
   lhf_status st = check_precision(c, prec);
   if (st != LHF_OK) return st;
-  std::vector<Plan> ps(nsys);
+  std::vector<Plan> all(nsys);
   size_t total = 0;
   for (int i = 0; i < nsys; ++i) {
     HostSystem hs;
     st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
-    st = make_plan(c, hs, ps[i], prec == LHF_MIXED);
+    st = make_plan(c, hs, all[i], prec == LHF_MIXED);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
-    total += internal_doubles(ps[i]);
+    total += internal_doubles(all[i]);
   }
   st = ensure_ws(c, total);
   if (st != LHF_OK) return st;
+  // periodic lattices go through one batched pass; open boxes (dense matrices) one at a time
+  std::vector<Plan> ps, boxes;
   size_t base = 0, eoff = 0, koff = 0;
-  std::vector<SysDev> sds(nsys);
   for (int i = 0; i < nsys; ++i) {
-    place_internal(ps[i], c->ws + base);
-    base += internal_doubles(ps[i]);
-    ps[i].sd.eig = eig + eoff;                  // [n_kpoints][m0] per system
-    ps[i].sd.kstat = kstat ? kstat + koff : nullptr;  // [n_kpoints] per system
-    eoff += (size_t)ps[i].sd.nblocks * ps[i].sd.m0;
-    koff += ps[i].sd.nblocks;
-    sds[i] = ps[i].sd;
+    Plan &p = all[i];
+    place_internal(p, c->ws + base);
+    base += internal_doubles(p);
+    p.sd.eig = eig + eoff;                        // [n_kpoints][m0] per system
+    p.sd.kstat = kstat ? kstat + koff : nullptr;  // [n_kpoints] per system
+    eoff += (size_t)p.sd.nblocks * p.sd.m0;
+    koff += p.sd.nblocks;
+    if (p.sd.box) {
+      boxes.push_back(p);
+    } else {
+      st = set_klist(c, p.sd);
+      if (st != LHF_OK) return st;
+      ps.push_back(p);
+    }
   }
-  st = upload(c, sds);
-  if (st != LHF_OK) return st;
-  st = run_assembly(c, ps);
-  if (st != LHF_OK) return st;
-  st = run_dft(c, ps);
-  if (st != LHF_OK) return st;
-  return run_eig(c, ps);
+  if (!ps.empty()) {
+    std::vector<SysDev> sds(ps.size());
+    for (size_t i = 0; i < ps.size(); ++i) sds[i] = ps[i].sd;
+    st = upload(c, sds);
+    if (st != LHF_OK) return st;
+    st = run_assembly(c, ps);
+    if (st != LHF_OK) return st;
+    st = run_dft(c, ps);
+    if (st != LHF_OK) return st;
+    st = run_eig(c, ps);
+    if (st != LHF_OK) return st;
+  }
+  for (Plan &p : boxes) {
+    std::vector<Plan> one(1, p);
+    st = upload(c, {p.sd});
+    if (st != LHF_OK) return st;
+    st = run_box_factors(c, one);
+    if (st != LHF_OK) return st;
+    st = run_box_assemble(c, one);
+    if (st != LHF_OK) return st;
+    const int N = p.sd.m0 * p.sd.d[0].L;
+    st = run_dense_eig(c, p.sd.H, p.sd.S, N, p.sd.eig, p.sd.ws + p.dense_off);
+    if (st != LHF_OK) return st;
+    if (p.sd.kstat) {  // no functions are removed in the dense solve
+      st = c->cuda(cudaMemsetAsync(p.sd.kstat, 0, sizeof(int) * (size_t)p.sd.nblocks, c->stream), "cudaMemsetAsync");
+      if (st != LHF_OK) return st;
+    }
+  }
+  return LHF_OK;
 }
 
 lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,
@@ -891,15 +1111,17 @@ lhf_status lhf_basis_factors(lhf_ctx *c, int l, double *G) {
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
-  ps[0].sd.ws = c->ws;
+  bind_ws(ps[0], c->ws);
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
   st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
   if (st != LHF_OK) return st;
   const DirDev &D = ps[0].sd.d[l];
-  return c->cuda(cudaMemcpyAsync(G, c->ws + D.offG, sizeof(double) * (size_t)ps[0].sd.m0 * D.n,
-                                 cudaMemcpyDeviceToDevice, c->stream),
-                 "cudaMemcpyAsync");
+  // rows of n nodes out of rows of gext + n samples
+  return c->cuda(cudaMemcpy2DAsync(G, sizeof(double) * (size_t)D.n, c->ws + D.offG + D.gext,
+                                   sizeof(double) * (size_t)(D.n + D.gext), sizeof(double) * (size_t)D.n,
+                                   (size_t)ps[0].sd.m0, cudaMemcpyDeviceToDevice, c->stream),
+                 "cudaMemcpy2DAsync");
 }
 
 lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
@@ -910,8 +1132,10 @@ lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
-  ps[0].sd.ws = c->ws;
+  bind_ws(ps[0], c->ws);
   st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  st = upload_zcell(c, ps);
   if (st != LHF_OK) return st;
   st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
   if (st != LHF_OK) return st;
@@ -931,18 +1155,30 @@ lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, in
   if (st != LHF_OK) return st;
   st = ensure_ws(c, ps[0].ws);
   if (st != LHF_OK) return st;
-  ps[0].sd.ws = c->ws;
+  bind_ws(ps[0], c->ws);
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
-  st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
-  if (st != LHF_OK) return st;
-  st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
-  if (st != LHF_OK) return st;
-  st = run_gram(c, ps);
-  if (st != LHF_OK) return st;
+  const size_t mm = (size_t)ps[0].sd.m0 * ps[0].sd.m0;
+  if (ps[0].sd.box) {
+    st = run_box_factors(c, ps);
+    if (st != LHF_OK) return st;
+    if (l == 0) {  // [L0][bJ][Rt+2][m0][m0]: cells p and p + bjlo + dd
+      if (jlo) *jlo = ps[0].sd.bjlo;
+      return c->cuda(cudaMemcpyAsync(C, c->ws + ps[0].sd.offCb,
+                                     sizeof(double) * (size_t)ps[0].sd.d[0].L * ps[0].sd.bJ * (ps[0].sd.Rt + 2) * mm,
+                                     cudaMemcpyDeviceToDevice, c->stream),
+                     "cudaMemcpyAsync");
+    }
+  } else {
+    st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
+    if (st != LHF_OK) return st;
+    st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
+    if (st != LHF_OK) return st;
+    st = run_gram(c, ps);
+    if (st != LHF_OK) return st;
+  }
   const DirDev &D = ps[0].sd.d[l];
   if (jlo) *jlo = D.jlo;
-  const size_t mm = (size_t)ps[0].sd.m0 * ps[0].sd.m0;
   return c->cuda(cudaMemcpyAsync(C, c->ws + D.offC, sizeof(double) * (size_t)D.J * (ps[0].sd.Rt + 2) * mm,
                                  cudaMemcpyDeviceToDevice, c->stream),
                  "cudaMemcpyAsync");

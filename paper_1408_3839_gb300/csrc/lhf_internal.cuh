@@ -36,10 +36,10 @@ struct DirDev {
   int K;          // periodic image window
   int J;          // window blocks computed (<= L)
   int jlo;        // first displacement of the window (may be negative; blocks taken mod L)
-  int pad_;
+  int gext;       // basis samples start gext nodes left of the grid (open box direction 0)
   double h, x0, cell0, b;
   double invP;     // 1 / (L b): supercell period of a periodic direction
-  int64_t offG;   // basis samples [m0][n]          (doubles, from SysDev::ws)
+  int64_t offG;   // basis samples [m0][gext + n]   (doubles, from SysDev::ws)
   int64_t offV;   // potential factors [Rt][nv]
   int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
   // tensor-core route (LHF_MIXED): digit planes and scale exponents
@@ -65,6 +65,8 @@ struct SysDev {
   double pnorm[kMaxM0];   // sqrt(2 alpha e)
   int cell_lo[3][kMaxM0]; // support cells of the cell-0 copy (unwrapped, dilated by one node)
   int cell_hi[3][kMaxM0];
+  int node_lo[3][kMaxM0];   // grid nodes that may be inside the cut of the cell-0 copy: from
+  int node_span[3][kMaxM0]; // node_lo, node_span nodes (mod n in periodic directions; widened)
   double Z[kMaxNuc];
   double a[kMaxNuc][3];
   double t[kMaxR];        // sinc nodes
@@ -75,6 +77,11 @@ struct SysDev {
   double *eig;            // [nblocks][m0]
   int *kstat;             // [nblocks] or null
   double *s0;             // [m0] mean over k-points of Re Sbar_ii (cell-periodic norms)
+  const int *klist;       // [nkhalf] k-points solved (one per conjugate pair), or null
+  // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
+  // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
+  int bJ, bjlo;
+  int64_t offCb;
   const double *zcell;    // box charges [L0][M0] (device) or null
 };
 
@@ -97,12 +104,18 @@ size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys);
 cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
                                 void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st);
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
-cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int max_lines,
-                       cudaStream_t st);
+cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
+                       cudaStream_t st);  // *passes += kernel launches (may be null)
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
-cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+// Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
+// the dense matrices (thread per entry).
+size_t box_gram_smem_bytes(int max_width);
+cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, int max_width, cudaStream_t st);
+cudaError_t launch_box_assemble(const SysDev *sys, int nsys, long long max_entries, cudaStream_t st);
+// Dense generalized symmetric-definite eigenvalues (cooperative launch, one CTA per SM).
+// work: dense_eig_workspace_doubles(N) doubles.  cudaErrorNotSupported without cooperative launch.
 cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *eig,
                              double *work, unsigned *flags, cudaStream_t st);
 size_t dense_eig_workspace_doubles(int N);

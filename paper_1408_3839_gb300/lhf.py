@@ -54,7 +54,7 @@ class lhf_system_desc(ctypes.Structure):
 class lhf_sizes(ctypes.Structure):
     _fields_ = [("m0", ctypes.c_int), ("n_blocks", ctypes.c_int), ("n_kpoints", ctypes.c_int),
                 ("n_basis", ctypes.c_int), ("rank", ctypes.c_int), ("window", ctypes.c_int * 3),
-                ("n_potential", ctypes.c_int * 3), ("periodic", ctypes.c_int)]
+                ("n_potential", ctypes.c_int * 3), ("periodic", ctypes.c_int), ("desc_bytes", ctypes.c_int)]
 
 
 class LhfError(RuntimeError):
@@ -232,7 +232,8 @@ class Context:
         self._check(self.lib.lhf_query_sizes(self._h, ctypes.byref(out)))
         return {"m0": out.m0, "n_blocks": out.n_blocks, "n_kpoints": out.n_kpoints,
                 "n_basis": out.n_basis, "rank": out.rank, "window": list(out.window),
-                "n_potential": list(out.n_potential), "periodic": out.periodic}
+                "n_potential": list(out.n_potential), "periodic": out.periodic,
+                "desc_bytes": out.desc_bytes}
 
     def sync(self):
         self._check(self.lib.lhf_sync(self._h))
@@ -272,7 +273,7 @@ class Context:
                                                     eig_host.ctypes.data, kp))
 
     # -- live stage timing -------------------------------------------------------------------
-    STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "zero_fill", "upload")
+    STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "zero_fill", "upload", "gram_tc")
 
     def set_profiling(self, enable: bool):
         self._check(self.lib.lhf_set_profiling(self._h, 1 if enable else 0))

@@ -97,3 +97,29 @@ def check_eigenvalues(eig, eig_ref, Hbar_ref, Sbar_ref, H_blocks=None, S_blocks=
         worst = max(worst, float(d.max()))
         ratio = max(ratio, float((d / tol).max()))
     return worst, ratio
+
+
+def check_dense_eigenvalues(eig, eig_ref, H, S, dH=None, dS=None, floor=1e-10, c=None):
+    """Dense generalized symmetric-definite eigenvalues (open box).  Both solvers are backward
+    stable: each eigenvalue may move by (||dH|| + |lambda| ||dS||) ||u||^2 (u S-normalised, first
+    order), with ||dH|| <= c eps ||H|| from the reductions (c = N: the growth bound of the
+    Cholesky and Householder steps) plus, when the two sides start from different matrices, the
+    measured input difference (dH, dS).  Returns (max |d lambda|, max ratio to tolerance)."""
+    H = np.asarray(H)
+    S = np.asarray(S)
+    N = H.shape[0]
+    if c is None:
+        c = float(N)
+    eps = np.finfo(float).eps
+    lam, U = _reduced(H, S, N)
+    u2 = (U ** 2).sum(axis=0)
+    nH, nS = np.linalg.norm(H, 2), np.linalg.norm(S, 2)
+    pH = c * eps * nH + (np.linalg.norm(dH, 2) if dH is not None else 0.0)
+    pS = c * eps * nS + (np.linalg.norm(dS, 2) if dS is not None else 0.0)
+    tol = np.maximum(floor, (pH + np.abs(lam) * pS) * u2)
+    eig = np.asarray(eig).ravel()
+    eig_ref = np.asarray(eig_ref).ravel()
+    if not (np.all(np.isfinite(eig)) and np.all(np.isfinite(eig_ref))):
+        return float("inf"), float("inf")
+    d = np.abs(eig - eig_ref)
+    return float(d.max()), float((d / tol).max())
