@@ -36,6 +36,8 @@ SINC_TABLE = {
     "box_64": (32, -8.4614, 0.4223),  # 4.3e-05 on [0.025, 186]
     "cubic_32": (32, -8.0245, 0.4189),  # 2.3e-05 on [0.0156, 60]
     "small": (20, -6.8657, 0.557),  # 4.4e-04 on [0.04, 60]
+    "hetero_24": (24, -9.7916, 0.6024),  # 8.7e-04 on [0.025, 1500]
+    "hetero_32": (32, -10.1649, 0.4724),  # 1.5e-04 on [0.025, 1500]
 }
 
 RHO = 40.0  # basis truncation: exp(-40) ~ 4e-18 of the peak
@@ -202,6 +204,50 @@ def box_64(seed: int = 2, L: int = 64, n_perp: int = 320) -> dict:
         cell0=[0.0, -8.0, -8.0], K_sum=[1, 1, 1], Z=[1.0], a=pos, kinds=kinds, alphas=alphas,
         centres=centres, sinc_key="box_64", name=f"box_{L}", seed=seed,
         Z_cell=[[z] for z in z_cell])
+
+
+def hetero(seed: int) -> dict:
+    """One member of the heterogeneous batch: b = 2.0, one Z = 1 nucleus at a seeded offset,
+    h drawn from {0.05, 0.0625, 0.08} (n_cell = 40, 32, 25), m0 from {4, 8, 16} (4 s; 4 s + px,
+    py, pz, px; 4 s + 4 p-shells; exponents log-uniform in [0.05, 20]), R from {24, 32}; with
+    probability 1/2 a periodic (L,1,1) tube with L log-uniform in [16, 512], else a periodic
+    (L,L,1) slab with L uniform in [4, 32]; open directions span [-8, 8]; K_sum = L."""
+    rng = _rng(seed)
+    b = 2.0
+    h = float(rng.choice([0.05, 0.0625, 0.08]))
+    n_c = int(round(b / h))
+    m0 = int(rng.choice([4, 8, 16]))
+    sinc_key = "hetero_24" if rng.random() < 0.5 else "hetero_32"
+    slab = rng.random() < 0.5
+    if slab:
+        L = int(rng.integers(4, 33))
+        Ls, periodic = [L, L, 1], [1, 1, 0]
+    else:
+        L = int(round(math.exp(rng.uniform(math.log(16.0), math.log(512.0)))))
+        Ls, periodic = [L, 1, 1], [1, 0, 0]
+    off = rng.uniform(-b / 4.0, b / 4.0, size=3)
+    pos = [[b / 2.0 + off[0], (b / 2.0 + off[1]) if slab else off[1], off[2]]]
+    if m0 == 4:
+        kinds, alphas, centres = _basis_s_p(rng, 4, 4, 0, 0.05, 20.0, pos)
+    elif m0 == 8:
+        kinds, alphas, centres = _basis_s_p(rng, 8, 4, 1, 0.05, 20.0, pos, extra_p_dir=[0])
+    else:
+        kinds, alphas, centres = _basis_s_p(rng, 16, 4, 4, 0.05, 20.0, pos)
+    n_open = int(round(16.0 / h))
+    n = [Ls[l] * n_c if periodic[l] else n_open for l in range(3)]
+    n_cell = [n_c if periodic[l] else n_open for l in range(3)]
+    bb = [b if periodic[l] else 16.0 for l in range(3)]
+    x0 = [0.0 if periodic[l] else -8.0 for l in range(3)]
+    return _system(
+        L=Ls, b=bb, periodic=periodic, n=n, n_cell=n_cell, h=[h] * 3, x0=x0, cell0=x0,
+        K_sum=[Ls[l] if periodic[l] else 1 for l in range(3)], Z=[1.0], a=pos, kinds=kinds,
+        alphas=alphas, centres=centres, sinc_key=sinc_key,
+        name=f"hetero_{'slab' if slab else 'tube'}_{L}", seed=seed)
+
+
+def hetero_batch(count: int = 64, first_seed: int = 4000) -> list[dict]:
+    """The heterogeneous batch: hetero(first_seed + s), s = 0 .. count-1."""
+    return [hetero(first_seed + s) for s in range(count)]
 
 
 def tube_256_batch(count: int, first_seed: int = 3000) -> list[dict]:

@@ -24,6 +24,8 @@ CLASSES = {
     "box_64": (32, 0.025, 186.0),
     "cubic_32": (32, 0.015625, 60.0),
     "small": (20, 0.04, 60.0),
+    "hetero_24": (24, 0.025, 1500.0),
+    "hetero_32": (32, 0.025, 1500.0),
 }
 
 

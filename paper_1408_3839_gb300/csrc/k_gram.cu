@@ -12,6 +12,11 @@
 // -- the same sum regrouped, exact up to rounding.  The second step is a dense contraction over
 // c of the R_tot potential rows with the m0^2 folded products (a GEMM with K = n_c).
 //
+// Substituting p -> p + j shows Q_{-j}[nu][mu](c) = Q_j[mu][nu](c), hence C_r[-j][nu][mu] =
+// C_r[j][mu][nu] and the same for the P1 forms (A and S are symmetric circulants): only the
+// blocks with j >= 0 (window indices cw0 .. cw0 + Jc - 1) are contracted; k_gram_mirror copies
+// the others from their mirrors.
+//
 // One CTA per (system, direction, window block, mu): phase 1 forms Q[nu][c] for all nu in
 // shared memory (only the cells where both supports can be nonzero are visited) together with
 // the P1 sums; phase 2 contracts with the R_tot potential rows.  Deterministic (fixed-order
@@ -27,13 +32,16 @@ struct GramItem {
   int l, jw, mu;
 };
 
+// CTA b of a system -> (direction, window block, mu) over the contracted blocks jw = cw0 ..
+// cw0 + Jc - 1 of each direction.
 __device__ __forceinline__ bool decode_gram(const SysDev &s, int b, GramItem &it) {
   for (int l = 0; l < 3; ++l) {
-    const int cnt = s.d[l].J * s.m0;
+    const int cnt = s.d[l].Jc * s.m0;
     if (b < cnt) {
       it.l = l;
-      it.jw = b / s.m0;
-      it.mu = b - it.jw * s.m0;
+      const int jc = b / s.m0;
+      it.jw = s.d[l].cw0 + jc;
+      it.mu = b - jc * s.m0;
       return true;
     }
     b -= cnt;
@@ -71,15 +79,24 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
       const int plo = s.cell_lo[it.l][nu];
       int phi = s.cell_hi[it.l][nu];
       if (phi > plo + L - 1) phi = plo + L - 1;
+      // indices advance by one cell per p (no division inside the loop)
+      int iv = wrap(c + plo * nc, n);    // node of g_nu in cell p
+      int iu = wrap(iv - j * nc, n);     // node of the row function shifted by j
+      int rel = wrap(plo - mlo, L);      // position of p in the row function's support
+      const bool test = mspan < L - 1;
       for (int p = plo; p <= phi; ++p) {
-        if (mspan < L - 1 && wrap(p - mlo, L) > mspan) continue;  // row support absent
-        const int iv = wrap(c + p * nc, n);
-        const int iu = wrap(iv - j * nc, n);
-        const int iv1 = (iv + 1 == n) ? 0 : iv + 1;
-        const int iu1 = (iu + 1 == n) ? 0 : iu + 1;
-        const double fi = f[iu], gi = g[iv];
-        q += fi * gi;
-        e += fi * g[iv1] + f[iu1] * gi;
+        if (!test || rel <= mspan) {  // else the row support is absent in this cell
+          const int iv1 = (iv + 1 == n) ? 0 : iv + 1;
+          const int iu1 = (iu + 1 == n) ? 0 : iu + 1;
+          const double fi = f[iu], gi = g[iv];
+          q += fi * gi;
+          e += fi * g[iv1] + f[iu1] * gi;
+        }
+        iv += nc;
+        if (iv >= n) iv -= n;
+        iu += nc;
+        if (iu >= n) iu -= n;
+        if (++rel == L) rel = 0;
       }
     } else {
       // single open cell: nodes c = 0..n-1, Dirichlet ends (no wrap)
@@ -164,7 +181,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
 // 2^24 / 2^14 of them accumulate exactly.  Digit plane k of a row block goes to
 // planes + k * rows * Kpad + row * Kpad + c (BF16, Kpad >= nv, zero padded).
 __device__ __forceinline__ void digits7(double x, int e, int *a) {
-  long long X = llrint(ldexp(x, 62 - e));
+  long long X = __double2ll_rn(scale_pow2(x, 62 - e));  // exact scaling, |X| < 2^62
 #pragma unroll
   for (int k = 0; k < kSlices; ++k) {
     const int sh = 55 - 7 * k;
@@ -206,8 +223,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__res
     if (lane == 0) rexp[nu] = scale_exponent(mx);
   }
   __syncthreads();
-  const int64_t rows = (int64_t)D.J * m0 * m0;
-  const int64_t row0 = ((int64_t)it.jw * m0 + it.mu) * m0;
+  const int64_t rows = (int64_t)D.Jc * m0 * m0;
+  const int64_t row0 = ((int64_t)(it.jw - D.cw0) * m0 + it.mu) * m0;
   unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
   int *rowexp = reinterpret_cast<int *>(s.ws + D.offRE);
   if (tid < m0) rowexp[row0 + tid] = rexp[tid];
@@ -270,7 +287,45 @@ __global__ void __launch_bounds__(kGramThreads) k_vslice(const SysDev *__restric
   }
 }
 
+// C[jw][slot][mu][nu] = C[mirror(jw)][slot][nu][mu] for the window blocks that were not
+// contracted: thread per element, systems on blockIdx.y.
+__global__ void __launch_bounds__(256) k_gram_mirror(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box) return;
+  int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m0 = s.m0, mm = m0 * m0, slots = s.Rt + 2;
+  int l = 0;
+  for (; l < 3; ++l) {
+    const int64_t cnt = (int64_t)(s.d[l].J - s.d[l].Jc) * slots * mm;
+    if (item < cnt) break;
+    item -= cnt;
+  }
+  if (l == 3) return;
+  const DirDev &D = s.d[l];
+  const int64_t per_block = (int64_t)slots * mm;
+  int k = (int)(item / per_block);  // k-th block outside cw0 .. cw0 + Jc - 1
+  const int rem = (int)(item - (int64_t)k * per_block);
+  const int jw = k < D.cw0 ? k : k + D.Jc;
+  // mirror: j' = -j; in the window j = jlo + jw, taken mod L when the window is the whole lattice
+  int jm;
+  if (D.J == D.L && D.jlo == 0) {
+    jm = jw == 0 ? 0 : D.L - jw;
+  } else {
+    jm = -2 * D.jlo - jw;
+  }
+  const int slot = rem / mm, e = rem - slot * mm, mu = e / m0, nu = e - mu * m0;
+  const double *src = s.ws + D.offC + ((int64_t)jm * slots + slot) * mm + nu * m0 + mu;
+  s.ws[D.offC + ((int64_t)jw * slots + slot) * mm + e] = *src;
+}
+
 }  // namespace
+
+cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items, cudaStream_t st) {
+  if (max_items <= 0 || nsys <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((max_items + 255) / 256), nsys);
+  k_gram_mirror<<<grid, 256, 0, st>>>(sys);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
                              int max_nv, cudaStream_t st) {

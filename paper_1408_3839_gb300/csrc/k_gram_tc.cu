@@ -208,14 +208,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
         for (int t = 0; t < 16; ++t) {
           const int n = job.n0 + cc * 16 + t;
           if (n >= P.Rt) continue;
+          // D_s are integers below 2^24 held exactly in FP32: converted to int32 and combined
+          // exactly in 64-bit integers (hi < 2^39, lo < 2^46), converted and scaled exactly, and
+          // rounded once by the final addition
           long long d[kSlices];
 #pragma unroll
-          for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2ll_rn(__uint_as_float(v[s][t]));
+          for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2int_rn(__uint_as_float(v[s][t]));
           const long long hi = (d[0] << 14) + (d[1] << 7) + d[2];
           const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
           const int E = er + P.colexp[n];
-          const double val = ldexp((double)hi, E - 28) + ldexp((double)lo, E - 56);
-          Crow[(int64_t)n * mm] = val;
+          Crow[(int64_t)n * mm] = scale_pow2((double)hi, E - 28) + scale_pow2((double)lo, E - 56);
         }
       }
     }
@@ -267,14 +269,14 @@ size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys) {
   for (int i = 0; i < nsys; ++i)
     for (int l = 0; l < 3; ++l) {
       const DirDev &D = host_sys[i].d[l];
-      const size_t rows = (size_t)D.J * host_sys[i].m0 * host_sys[i].m0;
+      const size_t rows = (size_t)D.Jc * host_sys[i].m0 * host_sys[i].m0;
       jobs += ((rows + kTileM - 1) / kTileM) * ((host_sys[i].Rt + kTileN - 1) / kTileN);
     }
   return (size_t)nsys * 3 * sizeof(TcArgs) + jobs * sizeof(TcJob) + 256;
 }
 
-cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
-                                void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st) {
+cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, size_t host_bytes, int *njobs,
+                            size_t *jobs_off) {
   std::vector<TcArgs> args((size_t)nsys * 3);
   std::vector<TcJob> jobs;
   memset(args.data(), 0, args.size() * sizeof(TcArgs));
@@ -282,13 +284,13 @@ cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf,
     const SysDev &s = host_sys[i];
     for (int l = 0; l < 3; ++l) {
       const DirDev &D = s.d[l];
-      const int rows = D.J * s.m0 * s.m0;
+      const int rows = D.Jc * s.m0 * s.m0;  // the contracted window blocks cw0 .. cw0 + Jc - 1
       if (D.Kpad % kChunkK != 0 || D.Kpad > 448 || rows < 1) return cudaErrorNotSupported;
       TcArgs &a = args[(size_t)i * 3 + l];
       if (!encode_planes(&a.mapA, s.ws + D.offA, D.Kpad, kSlices * rows, kTileM) ||
           !encode_planes(&a.mapB, s.ws + D.offB, D.Kpad, kSlices * s.Rt, kTileN))
         return cudaErrorInvalidValue;
-      a.C = s.ws + D.offC;
+      a.C = s.ws + D.offC + (size_t)D.cw0 * (s.Rt + 2) * s.m0 * s.m0;
       a.rowexp = reinterpret_cast<const int *>(s.ws + D.offRE);
       a.colexp = reinterpret_cast<const int *>(s.ws + D.offCE);
       a.rows = rows;
@@ -301,18 +303,37 @@ cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf,
   }
   const size_t abytes = args.size() * sizeof(TcArgs);
   const size_t need = abytes + jobs.size() * sizeof(TcJob);
-  if (need > dev_bytes || need > host_bytes) return cudaErrorMemoryAllocation;
-  unsigned char *d = static_cast<unsigned char *>(dev_buf);
-  unsigned char *h = static_cast<unsigned char *>(host_buf);  // pinned, owned by the caller
+  if (need > host_bytes) return cudaErrorMemoryAllocation;
+  unsigned char *h = static_cast<unsigned char *>(host_buf);
   memcpy(h, args.data(), abytes);
   memcpy(h + abytes, jobs.data(), jobs.size() * sizeof(TcJob));
-  cudaError_t e = cudaMemcpyAsync(d, h, need, cudaMemcpyHostToDevice, st);
+  *njobs = (int)jobs.size();
+  *jobs_off = abytes;
+  return cudaSuccess;
+}
+
+cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsigned *flags, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (e != cudaSuccess) return e;
-  k_gram_tc<<<(unsigned)jobs.size(), kTcThreads, kSmemBytes, st>>>(
-      reinterpret_cast<const TcJob *>(d + abytes), reinterpret_cast<const TcArgs *>(d), flags);
+  const unsigned char *d = static_cast<const unsigned char *>(dev_buf);
+  k_gram_tc<<<(unsigned)njobs, kTcThreads, kSmemBytes, st>>>(reinterpret_cast<const TcJob *>(d + jobs_off),
+                                                             reinterpret_cast<const TcArgs *>(d), flags);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
+                                void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st) {
+  int njobs = 0;
+  size_t jobs_off = 0;
+  cudaError_t e = gram_tc_prepare(host_sys, nsys, host_buf, host_bytes, &njobs, &jobs_off);
+  if (e != cudaSuccess) return e;
+  const size_t need = jobs_off + (size_t)njobs * sizeof(TcJob);
+  if (need > dev_bytes) return cudaErrorMemoryAllocation;
+  // host_buf is pinned and owned by the caller: it must stay untouched until the copy has run
+  e = cudaMemcpyAsync(dev_buf, host_buf, need, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return gram_tc_launch(dev_buf, njobs, jobs_off, flags, st);
 }
 
 }  // namespace lhf

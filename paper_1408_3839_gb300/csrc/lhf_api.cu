@@ -49,6 +49,7 @@ struct Plan {
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
+  long long mirror_items = 0;  // window-block elements filled from their mirrors
   size_t zcell_off = 0, dense_off = 0;
   std::vector<double> zcell;  // host copy of the per-cell charges (box)
 };
@@ -372,11 +373,24 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
       D.jlo = 0;
       D.J = 1;
     }
+    // blocks contracted: j >= 0 of the (symmetric) window; the rest are mirrors
+    if (D.J == 0) {
+      D.cw0 = 0;
+      D.Jc = 0;
+    } else if (D.J == D.L && D.jlo == 0) {
+      D.cw0 = 0;
+      D.Jc = D.L / 2 + 1;
+    } else {
+      D.cw0 = -D.jlo;
+      D.Jc = D.J - D.cw0;
+      if (D.jlo > 0 || D.J != 2 * D.cw0 + 1) return c->fail(LHF_ERR_ARG, "direction %d: asymmetric window", l);
+    }
+    P.mirror_items += (long long)(D.J - D.Jc) * (Rt + 2) * mm;
     if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
     P.basis_items += m0 * (D.n + D.gext);
     P.pot_items += Rt * D.nv;
-    P.gram_blocks += D.J * m0;
+    P.gram_blocks += D.Jc * m0;
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
   for (int l = 0; l < 3; ++l) {
@@ -408,7 +422,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     DirDev &D = sd.d[l];
     D.Kpad = (D.nv + 63) / 64 * 64;
     if (mixed && !box) {
-      const size_t rows = (size_t)D.J * mm;
+      const size_t rows = (size_t)D.Jc * mm;
       D.offA = (int64_t)off;
       off = align_up(off + (lhf::kSlices * rows * D.Kpad * 2 + 7) / 8);
       D.offB = (int64_t)off;
@@ -512,12 +526,15 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
     max_m0 = std::max(max_m0, p.sd.m0);
     max_rt = std::max(max_rt, p.sd.Rt);
   }
+  long long mirror = 0;
+  for (const Plan &p : ps) mirror = std::max(mirror, p.mirror_items);
   if (!ps[0].mixed) {
     c->begin(2);
     lhf_status st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
                                                   max_of(ps, &Plan::nv_max), c->stream),
                             "Gram kernel");
-    c->end();
+    if (st == LHF_OK) st = c->cuda(lhf::launch_gram_mirror(c->d_sys, nsys, mirror, c->stream), "mirror kernel");
+    c->end(mirror > 0 ? 2 : 1);
     return st;
   }
   c->begin(2);
@@ -552,6 +569,10 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
   c->end();
   if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "shape outside the tensor-core kernel's limits");
   st = c->cuda(e, "tensor-core Gram kernel");
+  if (st != LHF_OK) return st;
+  c->begin(2);
+  st = c->cuda(lhf::launch_gram_mirror(c->d_sys, nsys, mirror, c->stream), "mirror kernel");
+  c->end(mirror > 0 ? 1 : 0);
   if (st != LHF_OK) return st;
   return c->cuda(cudaEventRecord(c->tc_copied, c->stream), "cudaEventRecord");
 }

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "lhf.h"
@@ -42,12 +43,15 @@ struct DirDev {
   int64_t offG;   // basis samples [m0][gext + n]   (doubles, from SysDev::ws)
   int64_t offV;   // potential factors [Rt][nv]
   int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
+  // C[j][mu][nu] = C[-j][nu][mu] (Q_j and its mirror are the same sums): only the window blocks
+  // jw = cw0 .. cw0 + Jc - 1 (displacements j >= 0) are contracted, the others are mirrored
+  int cw0, Jc;
   // tensor-core route (LHF_MIXED): digit planes and scale exponents
   int Kpad;       // nv rounded up to a multiple of 64
   int pad2_;
-  int64_t offA;   // BF16 [kSlices][J m0 m0][Kpad] digit planes of the folded products
+  int64_t offA;   // BF16 [kSlices][Jc m0 m0][Kpad] digit planes of the folded products
   int64_t offB;   // BF16 [kSlices][Rt][Kpad] digit planes of the potential factors
-  int64_t offRE;  // int [J m0 m0] row scale exponents
+  int64_t offRE;  // int [Jc m0 m0] row scale exponents
   int64_t offCE;  // int [Rt] potential-row scale exponents
 };
 
@@ -85,6 +89,20 @@ struct SysDev {
   const double *zcell;    // box charges [L0][M0] (device) or null
 };
 
+// 2^e as a double from its exponent field (normal range), else by ldexp.
+__device__ __forceinline__ double pow2(int e) {
+  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
+
+// x 2^e, exact whenever the result is a normal number (two power-of-two factors when 2^e itself
+// is out of range).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * pow2(e);
+  const int h = e / 2;
+  return (x * pow2(h)) * pow2(e - h);
+}
+
 // Per-launch status word written by kernels (atomicOr of flag bits).
 enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
 
@@ -95,6 +113,8 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
                              int max_nv, cudaStream_t st);
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
                                int max_rt3, cudaStream_t st);
+// The window blocks outside cw0 .. cw0 + Jc - 1 from their mirrors (thread per element).
+cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items, cudaStream_t st);
 // Tensor-core contraction of the digit planes (tcgen05), one job per (system, direction, 128-row
 // tile, 64-column tile).  host_sys: host copies of the descriptors (device workspace pointers).
 // dev_buf (dev_bytes >= gram_tc_args_bytes) receives the tensor maps and the job list through the
@@ -103,6 +123,11 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
 size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys);
 cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf, size_t dev_bytes,
                                 void *host_buf, size_t host_bytes, unsigned *flags, cudaStream_t st);
+// The same in two parts: tensor maps and jobs into host_buf (nothing launched; *jobs_off is the
+// byte offset of the job list), then the launch on a device copy of that buffer.
+cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, size_t host_bytes, int *njobs,
+                            size_t *jobs_off);
+cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsigned *flags, cudaStream_t st);
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st);  // *passes += kernel launches (may be null)
