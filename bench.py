@@ -97,15 +97,16 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 # algorithmic work per system (roofline numerators)
 
-def work_model(sizes: list[dict], sweeps: int, matrices: int) -> dict:
+def work_model(sizes: list[dict], rotations: int, matrices: int) -> dict:
     """Algorithmic FLOPs / bytes per batch for the stages (the roofline numerators).
 
-    gram: 2 R_tot J m0^2 n_v per direction (the weighted-Gram contraction); gram_tc: the same
-    contraction as 28 exact BF16 digit-pair products (7 digits per operand, pairs a + b <= 6);
-    rank: (4 R_tot + 12) per window entry; dft: read 2 real blocks, write 2 complex blocks; eig:
-    9.33 m^3 per matrix (Cholesky and two triangular solves, complex) plus per Jacobi sweep
-    (m' - 1) steps of npair (npair - 1) / 2 off-diagonal 2x2 block updates (96 flops) and npair
-    diagonal updates (16 flops), m' = m rounded up to even, npair = m' / 2."""
+    gram: 2 R_tot J m0^2 n_v per direction (the weighted-Gram contraction, counted over the whole
+    window although the mirrored half is copied); gram_tc: the same contraction as 28 exact BF16
+    digit-pair products (7 digits per operand, pairs a + b <= 6); rank: (4 R_tot + 12) per window
+    entry; dft: read 2 real blocks, write 2 complex blocks; eig: per solved matrix 9.33 m^3
+    (Cholesky and two triangular solves, complex) + 8 m^3 (Householder reduction to tridiagonal
+    form: per column a complex matrix-vector product and a rank-2 update of the trailing block),
+    plus 20 flops per QR rotation of the tridiagonal stage."""
     gram = 0.0
     dft_bytes = 0.0
     rank = 0.0
@@ -119,10 +120,7 @@ def work_model(sizes: list[dict], sweeps: int, matrices: int) -> dict:
         dft_bytes += s["n_blocks"] * m0 * m0 * (2 * 8 + 2 * 16)
     if sizes:
         m = sizes[0]["m0"]
-        mp = m + (m & 1)
-        npair = mp // 2
-        per_sweep = (mp - 1) * (96.0 * npair * (npair - 1) / 2 + 16.0 * npair)
-        eig = matrices * 9.33 * m ** 3 + sweeps * per_sweep
+        eig = matrices * 17.33 * m ** 3 + rotations * 20.0
     return {"gram_flops": gram, "gram_tc_flops": 28.0 * gram, "rank_flops": rank, "dft_bytes": dft_bytes,
             "eig_flops": eig}
 
@@ -250,8 +248,100 @@ def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None
     ms = t_start.elapsed_time(t_end)
     ctx.set_profiling(False)
     stages = ctx.stage_times()
-    sweeps, mats = ctx.eig_counters()
-    return max_over_ranks(ms, dist, "cuda"), stages, sweeps, mats, ck
+    rotations, mats = ctx.eig_counters()
+    return max_over_ranks(ms, dist, "cuda"), stages, rotations, mats, ck
+
+
+def _device_time_ms(fn, steps, stream):
+    import torch
+
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_extras(ctx, lhf, stream, steps: int, warmup: int) -> dict:
+    """The other workloads of the path, each timed on the device (not part of the headline):
+    the heterogeneous batch of 64 tubes and slabs as one captured CUDA graph (mixed route), the
+    open (64,1,1) box (dense matrices and dense eigensolve, FP64) and the periodic (32,32,32)
+    cube (three-level block DFT, 16 385 k-point solves; mixed route)."""
+    import torch
+
+    out = {}
+    # heterogeneous batch through a graph
+    try:
+        cfgs = W.hetero_batch()
+        ne = nk = 0
+        for c in cfgs:
+            ctx.setup(c)
+            sz = ctx.query_sizes()
+            ne += sz["n_kpoints"] * sz["m0"]
+            nk += sz["n_kpoints"]
+        eig = torch.empty(ne, dtype=torch.float64, device="cuda")
+        ks = torch.empty(nk, dtype=torch.int32, device="cuda")
+        g = ctx.graph_create(cfgs, eig, ks, lhf.MIXED)
+        for _ in range(warmup):
+            g.launch()
+        ms_graph = _device_time_ms(g.launch, steps, stream)
+        for _ in range(warmup):
+            ctx.bloch_spectra(cfgs, eig, ks, lhf.MIXED)
+        ms_direct = _device_time_ms(lambda: ctx.bloch_spectra(cfgs, eig, ks, lhf.MIXED), steps, stream)
+        g.close()
+        out["hetero_64"] = {
+            "workload": "64 seeded tubes (L in [16, 512]) and slabs (L x L, L in [4, 32]), m0 in {4, 8, 16}, "
+                        "h in {0.05, 0.0625, 0.08}, R in {24, 32}, b = 2.0; mixed route",
+            "graph": {"value": len(cfgs) * steps / (ms_graph / 1e3), "unit": UNIT, "ms_per_step": ms_graph / steps},
+            "direct": {"value": len(cfgs) * steps / (ms_direct / 1e3), "unit": UNIT, "ms_per_step": ms_direct / steps},
+            "eigenvalues_per_step": ne, "bad_kpoints": int((ks < 0).sum().item())}
+    except Exception as e:  # reported, not hidden
+        out["hetero_64"] = {"error": str(e)}
+    # open box (64,1,1)
+    try:
+        box = W.box_64()
+        ctx.setup(box)
+        N = ctx.query_sizes()["n_basis"]
+        eig = torch.empty(N, dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            ctx.bloch_spectra([box], eig)
+        ctx.stage_times()
+        ctx.set_profiling(True)
+        ms = _device_time_ms(lambda: ctx.bloch_spectra([box], eig), steps, stream)
+        ctx.set_profiling(False)
+        st = ctx.stage_times()
+        out["box_64"] = {
+            "workload": "open (64,1,1) box, N_b = 512, n1 = 3712, n2 = n3 = 320, R = 32, FP64",
+            "value": steps / (ms / 1e3), "unit": "spectra/s", "ms_per_step": ms / steps,
+            "stages_ms": {k: v[0] / steps for k, v in st.items() if v[1]}}
+    except Exception as e:
+        out["box_64"] = {"error": str(e)}
+    # periodic cube (32,32,32)
+    try:
+        cube = W.cubic_32()
+        ctx.setup(cube)
+        sz = ctx.query_sizes()
+        eig = torch.empty(sz["n_kpoints"] * sz["m0"], dtype=torch.float64, device="cuda")
+        ks = torch.empty(sz["n_kpoints"], dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            ctx.bloch_spectra([cube], eig, ks, lhf.MIXED)
+        ctx.stage_times()
+        ctx.set_profiling(True)
+        ms = _device_time_ms(lambda: ctx.bloch_spectra([cube], eig, ks, lhf.MIXED), steps, stream)
+        ctx.set_profiling(False)
+        st = ctx.stage_times()
+        out["cubic_32"] = {
+            "workload": "periodic (32,32,32), b = 2.0, m0 = 16, n_cell = 64 per direction, R = 32, mixed route",
+            "value": steps / (ms / 1e3), "unit": "spectra/s", "ms_per_step": ms / steps,
+            "kpoints": sz["n_kpoints"], "removed_slots": int(ks.clamp(min=0).sum().item()),
+            "stages_ms": {k: v[0] / steps for k, v in st.items() if v[1]}}
+    except Exception as e:
+        out["cubic_32"] = {"error": str(e)}
+    return out
 
 
 def run_gpu(args):
@@ -290,7 +380,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms_other, stages_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
     clocks = ClockSampler(local)
-    ms, stages, sweeps, mats, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
+    ms, stages, rotations, mats, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
     total_systems = B * args.steps * world
     value = total_systems / (ms / 1e3)
     value_other = total_systems / (ms_other / 1e3)
@@ -309,7 +399,7 @@ def run_gpu(args):
     e2e_value = total_systems / e2e_s
 
     # rooflines per stage and of the dominant one (the stage with the most device time)
-    work = work_model(all_sizes, sweeps, mats)
+    work = work_model(all_sizes, rotations, mats)
     kernel_stages = ["basis", "potential", "gram", "gram_tc", "ranksum", "dft", "eig"]
     peaks = measured_peaks()
     rooflines = {}
@@ -363,10 +453,12 @@ def run_gpu(args):
             "stages": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages_other.items()}},
         "mixed_over_fp64": (value / value_other) if precision == lhf.MIXED else (value_other / value),
         "stages": stage_summary,
-        "eig_sweeps_per_matrix": sweeps / max(mats, 1),
+        "eig_qr_rotations_per_matrix": rotations / max(mats, 1),
         "bad_kpoints": bad_k,
         "clocks": ck,
     }
+    if rank == 0 and not args.no_extras:
+        line["extra"] = run_extras(ctx, lhf, stream, max(args.steps // 2, 2), 2)
     if rank == 0 and not args.no_cpu_baseline:
         from tests._numerics import check_eigenvalues
 
@@ -400,6 +492,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads (box, cube, batch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -160,16 +160,19 @@ lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, dou
  * lhf_circulant_fft (device): blocks of a real lattice matrix, so that Xbar at -kappa is the
  * complex conjugate of Xbar at kappa; one k-point of each conjugate pair is solved and its
  * eigenvalues are written to both.  eig: device [n_kpoints][m0], ascending per k-point.
- * FP64 data cannot represent a Bloch function whose overlap diagonal cancels to rounding level:
- * with s0_i = mean over kappa of Re Sbar_ii (the cell-periodic norm of basis function i),
- * function i is removed at kappa when Re Sbar_ii(kappa) <= LHF_DROP_TOL s0_i; the remaining
- * pencil is diagonally scaled, reduced (Cholesky) and solved by Jacobi; removed slots hold
+ * FP64 data resolve a Bloch function whose overlap diagonal has cancelled to a fraction r of
+ * its cell-periodic norm only to about eps / r relative: with s0_i = mean over kappa of
+ * Re Sbar_ii, function i is removed at kappa when Re Sbar_ii(kappa) <= LHF_DROP_TOL s0_i (at
+ * 1e-6 its scaled overlap row is still good to ~2e-10, far below LHF_LINDEP_TOL); the remaining
+ * pencil is diagonally scaled, reduced (Cholesky), brought to real tridiagonal form by
+ * Householder reflections and solved by the implicit QR iteration; removed slots hold
  * +INFINITY (sorted last).  k_status: device [n_kpoints] (may be NULL): the number of removed
  * functions (>= 0), or LHF_ERR_NOT_SPD when the reduced overlap is not positive definite (the
  * eigenvalues of such a k-point are NaN). */
-#define LHF_DROP_TOL 1e-9
-/* The kept pencil is scaled to unit overlap diagonal; where the scaled overlap is nearly
- * singular (a Cholesky pivot below 1e-5) the k-point is solved by canonical orthogonalisation,
+#define LHF_DROP_TOL 1e-6
+/* The kept pencil is scaled to unit overlap diagonal; where the scaled overlap may be nearly
+ * singular (a Cholesky pivot below 1e-5, or trace(S~^-1) above 1 / LHF_LINDEP_TOL) the k-point
+ * is solved by canonical orthogonalisation,
  * dropping the overlap eigen-directions below LHF_LINDEP_TOL (their slots also hold +INFINITY
  * and are counted in k_status). */
 #define LHF_LINDEP_TOL 1e-8
@@ -188,6 +191,18 @@ lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, 
  * Scratch memory is the context's workspace (grown on demand). */
 lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
                              lhf_precision precision, double *eig, int *k_status);
+
+/* The batched path of lhf_bloch_spectra captured once into a CUDA graph and replayed by
+ * lhf_graph_launch on the context stream (one graph launch instead of a dozen kernel launches
+ * and no host work per replay).  The graph owns its workspace and descriptors; every replay
+ * recomputes the same systems into the same eig / k_status device buffers (which must outlive
+ * the graph).  Periodic lattices only (LHF_ERR_UNSUPPORTED for open boxes).  The graph must be
+ * destroyed before its context; lhf_graph_destroy waits for the context stream. */
+typedef struct lhf_graph lhf_graph;
+lhf_status lhf_graph_create(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems, lhf_precision precision,
+                            double *eig, int *k_status, lhf_graph **out);
+lhf_status lhf_graph_launch(lhf_graph *graph);
+void lhf_graph_destroy(lhf_graph *graph);
 
 /* Same as lhf_bloch_spectra with a HOST output buffer: the call copies the eigenvalues back
  * and returns after the stream has finished (synchronising). */
@@ -214,16 +229,17 @@ lhf_status lhf_gram_factors(lhf_ctx *ctx, lhf_precision precision, int l, double
  * for stages 6 and 7) (arrays of LHF_NUM_STAGES, host), and clears
  * the record.  Stages: 0 basis samples (a1), 1 potential factors (a2), 2 Gram factors (a3-a4:
  * the FP64 contraction, or the folding and digit slicing of LHF_MIXED), 3 rank sum (a5; open
- * box: dense assembly), 4 block DFT (a7), 5 eigensolve (a8; open box: dense), 6 window zero
- * fill (a6), 7 descriptor upload, 8 tensor-core contraction of LHF_MIXED. */
+ * box: dense assembly; the zero blocks outside the overlap window, a6, are written by the same
+ * kernel), 4 block DFT (a7), 5 eigensolve (a8; open box: dense), 6 unused, 7 descriptor upload,
+ * 8 tensor-core contraction of LHF_MIXED. */
 #define LHF_NUM_STAGES 9
 lhf_status lhf_set_profiling(lhf_ctx *ctx, int enable);
 lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
 
 /* Work counters of the k-point eigensolver since the previous call (synchronising; host
- * outputs): total Jacobi sweeps and number of matrices solved (one per conjugate pair of
- * k-points).  Reset by the call. */
-lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *sweeps, unsigned long long *matrices);
+ * outputs): total QR rotations of the tridiagonal eigenvalue stage and number of matrices solved
+ * (one per conjugate pair of k-points).  Reset by the call. */
+lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *rotations, unsigned long long *matrices);
 
 /* Allocation-free variant of lhf_k_point_eigensolve (the paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory -- code inside CUDA stream capture,

@@ -26,7 +26,7 @@ _lib = None
 NOT_SPD = -3
 # a Bloch function is removed at a k-point when its overlap diagonal is below this fraction of
 # its cell-periodic norm (numerically absent in FP64; see orc_k_point_eigenvalues)
-DROP_TOL = 1e-9
+DROP_TOL = 1e-6
 # canonical orthogonalisation: directions of the diagonally scaled overlap with eigenvalue below
 # this threshold are dropped (near-linear dependence)
 LINDEP_TOL = 1e-8

@@ -841,6 +841,23 @@ int orc_k_point_eigenvalues(int K, int m, const double *Hbar, const double *Sbar
                 Sr[2 * f] = Sk[2 * e] * da * db;
                 Sr[2 * f + 1] = Sk[2 * e + 1] * da * db;
             }
+        /* the blocks are Hermitian (eq. (4.7)) up to the rounding of the transform: the pencil
+         * solved is their Hermitian part (X + X^H) / 2 */
+        for (int a = 0; a < mr; ++a)
+            for (int b = a; b < mr; ++b) {
+                size_t f = (size_t)a * mr + b, g = (size_t)b * mr + a;
+                double hr = 0.5 * (Hr[2 * f] + Hr[2 * g]), hi = 0.5 * (Hr[2 * f + 1] - Hr[2 * g + 1]);
+                double sr = 0.5 * (Sr[2 * f] + Sr[2 * g]), si = 0.5 * (Sr[2 * f + 1] - Sr[2 * g + 1]);
+                if (a == b) hi = si = 0.0;
+                Hr[2 * f] = hr;
+                Hr[2 * f + 1] = hi;
+                Hr[2 * g] = hr;
+                Hr[2 * g + 1] = -hi;
+                Sr[2 * f] = sr;
+                Sr[2 * f + 1] = si;
+                Sr[2 * g] = sr;
+                Sr[2 * g + 1] = -si;
+            }
         int removed2 = 0;
         int rc = mr > 0 ? canonical_eigenvalues(mr, Hr, Sr, tau2, ev, &removed2) : ORC_OK;
         if (rc != ORC_OK) {

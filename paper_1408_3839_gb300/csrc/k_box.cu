@@ -64,7 +64,10 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_gram(const SysDev *__restri
   const double *V = s.ws + D.offV;  // [Rt][n]
   double *Cb = s.ws + s.offCb;
   const int outs = L0 * slots;
-  for (int o = tid; o < outs; o += kBoxThreads) {
+  const int warp = tid >> 5, lane = tid & 31;
+  // one warp per output (cell p, slot), lanes over the nodes (coalesced potential rows), a fixed
+  // shuffle tree for the sum
+  for (int o = warp; o < outs; o += kBoxThreads / 32) {
     const int p = o / slots, slot = o - p * slots;
     if (p + d < 0 || p + d >= L0) continue;  // column cell outside the box: never read
     // grid nodes i = i' + p n_c in [0, n): i' in [-p n_c, n - p n_c)
@@ -72,17 +75,21 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_gram(const SysDev *__restri
     double acc = 0.0;
     if (slot < Rt) {
       const double *vr = V + (int64_t)slot * n + p * nc;
-      for (int ip = lo; ip < hi; ++ip) acc += P[ip - ia] * __ldg(vr + ip);
+      for (int ip = lo + lane; ip < hi; ip += 32) acc += P[ip - ia] * __ldg(vr + ip);
     } else {
-      // P1 forms, node by node in ascending order: diagonal terms over i in [0, n), cross terms
-      // over i in [0, n - 1) (the stiffness sum cancels to O(h^2) of its terms, so it is formed
-      // per node rather than from two large partial sums)
+      // P1 forms node by node: diagonal terms over i in [0, n), cross terms over i in [0, n - 1)
+      // (the stiffness sum cancels to O(h^2) of its terms, so each node's 2 f g - cross is formed
+      // before summing rather than two large partial sums)
       const int hx = min(ib, n - 1 - p * nc);
       const double wd = (slot == Rt) ? 2.0 : 4.0, wx = (slot == Rt) ? -1.0 : 1.0;
-      for (int ip = lo; ip < hi; ++ip) acc += wd * P[ip - ia] + (ip < hx ? wx * X[ip - ia] : 0.0);
-      acc = (slot == Rt) ? acc / D.h : acc * D.h / 6.0;
+      for (int ip = lo + lane; ip < hi; ip += 32) acc += wd * P[ip - ia] + (ip < hx ? wx * X[ip - ia] : 0.0);
     }
-    Cb[(((int64_t)p * s.bJ + dd) * slots + slot) * mm + e] = acc;
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      if (slot == Rt) acc /= D.h;
+      else if (slot == Rt + 1) acc *= D.h / 6.0;
+      Cb[(((int64_t)p * s.bJ + dd) * slots + slot) * mm + e] = acc;
+    }
   }
 }
 

@@ -54,14 +54,17 @@ __device__ bool grid_barrier(GridBar *bar, unsigned nblocks, unsigned *flags, in
     } else {
       const long long t0 = clock64();
       unsigned spins = 0;
-      while (atomicAdd(&bar->gen, 0u) == g) {
-        if ((++spins & 255u) == 0 && (clock64() - t0 > 2000000000ll || atomicAdd(&bar->abort, 0u))) {
+      // poll with plain volatile loads (atomics on the word would contend with the arrivals)
+      const volatile unsigned *gen = &bar->gen;
+      const volatile unsigned *abort_word = &bar->abort;
+      while (*gen == g) {
+        if ((++spins & 255u) == 0 && (clock64() - t0 > 2000000000ll || *abort_word)) {
           atomicOr(flags, kFlagTimeout);
           atomicExch(&bar->abort, 1u);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
     if (atomicAdd(&bar->abort, 0u)) ok = 0;
@@ -107,16 +110,30 @@ __device__ void rows_times_inv_lt(double *X, const double *Lt, const double *ld,
   }
 }
 
-// Number of eigenvalues of T = tridiag(e, d, e) below sigma (negative LDL^T pivots).
-__device__ int sturm_count(const double *td, const double *te2, int N, double sigma, double pivmin) {
+// Number of eigenvalues of T = tridiag(e, d, e) below sigma: the sign changes of the Sturm
+// sequence of leading principal minors p_i = (d_i - sigma) p_(i-1) - e_(i-1)^2 p_(i-2), p_0 = 1
+// (a sign change where p_i / p_(i-1) < 0, the LDL^T pivot of T - sigma I), without divisions; the
+// pair (p_(i-1), p_i) is rescaled by an exact power of two when it leaves [2^-500, 2^500], and an
+// exact zero takes the sign that counts it (the pivot -0 of the LDL^T form).
+__device__ int sturm_count(const double *td, const double *te2, int N, double sigma) {
   int cnt = 0;
-  double q = __ldcg(td) - sigma;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += q < 0.0;
+  double p0 = 1.0, p1 = __ldcg(td) - sigma;
+  if (p1 == 0.0) p1 = -1e-300;
+  cnt += p1 < 0.0;
   for (int i = 1; i < N; ++i) {
-    q = (__ldcg(td + i) - sigma) - __ldcg(te2 + i - 1) / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    double p2 = fma(__ldcg(td + i) - sigma, p1, -__ldcg(te2 + i - 1) * p0);
+    if (p2 == 0.0) p2 = p1 > 0.0 ? -1e-300 : 1e-300;
+    cnt += (p2 < 0.0) != (p1 < 0.0);
+    p0 = p1;
+    p1 = p2;
+    const double a = fabs(p1);
+    if (a > 0x1p500) {
+      p0 *= 0x1p-500;
+      p1 *= 0x1p-500;
+    } else if (a < 0x1p-500 && fabs(p0) < 0x1p-500) {
+      p0 *= 0x1p500;
+      p1 *= 0x1p500;
+    }
   }
   return cnt;
 }
@@ -221,13 +238,16 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
     }
     __syncthreads();
     if (tau != 0.0) {
-      for (int i = blockIdx.x; i < N; i += G) {  // p = tau C v, own rows
+      // p = tau C v on the own rows, one warp per row (shuffle reduction, no block barrier)
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int q = warp; blockIdx.x + (int64_t)q * G < N; q += kDenseThreads / 32) {
+        const int i = blockIdx.x + q * G;
         if (i <= k) continue;
         const double *row = C + (int64_t)i * N;
         double acc = 0.0;
-        for (int j = k + 1 + tid; j < N; j += kDenseThreads) acc += row[j] * vec[j];
-        acc = block_sum(acc, red);
-        if (tid == 0) pv[i] = tau * acc;
+        for (int j = k + 1 + lane; j < N; j += 32) acc += row[j] * vec[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) pv[i] = tau * acc;
       }
     }
     if (!grid_barrier(bar, G, flags, &ok_sh)) return;
@@ -303,7 +323,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
     for (int rd = 0; rd < kSturmRounds; ++rd) {
       const double step = (hi - lo) / (kSturmLanes + 1);
       const double sg = lo + (gl + 1) * step;
-      const bool above = live && sturm_count(td, te2, N, sg, pivmin) > t;  // lambda_t < sg
+      const bool above = live && sturm_count(td, te2, N, sg) > t;  // lambda_t < sg
       const unsigned bal = __ballot_sync(0xffffffffu, above) & gmask;
       // first lane (of the group) whose sigma has lambda_t below it
       const int first = bal ? __ffs(bal) - 1 - (tid & 31) / kSturmLanes * kSturmLanes : kSturmLanes;

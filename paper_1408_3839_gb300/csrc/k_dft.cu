@@ -55,26 +55,68 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   const int64_t i0 = (tile - o * tiles_inner) * TW;
   const int tw_valid = (int)((inner - i0) < TW ? (inner - i0) : TW);
 
+  const bool pow2 = (Ld & (Ld - 1)) == 0;
+  // real first pass of a power-of-two length: H and S in one complex transform of
+  // z = H + i sigma S (sigma a power of two balancing the tile's magnitudes), unpacked as
+  // Hbar_k = (Z_k + conj Z_-k) / 2, Sbar_k = (Z_k - conj Z_-k) / (2 i sigma); the z = 1 CTAs idle
+  const bool packed = real_in && pow2;
+  if (packed && blockIdx.z == 1) return;
   const double *Xr = blockIdx.z == 0 ? s.H : s.S;
   double *Xc = blockIdx.z == 0 ? s.Hbar : s.Sbar;
 
   extern __shared__ double sm[];
   double2 *x = reinterpret_cast<double2 *>(sm);  // [Ld][TW]
   double2 *tab = x + (size_t)Ld * TW;            // [Ld] omega^m
+  __shared__ double red[2 * (kDftThreads / 32)];
   const int tid = threadIdx.x;
   for (int m = tid; m < Ld; m += kDftThreads) {
     double sn, cs;
     sincospi(2.0 * (double)m / (double)Ld, &sn, &cs);
     tab[m] = make_double2(cs, -sn);
   }
-  const bool pow2 = (Ld & (Ld - 1)) == 0;
   const int bits = pow2 ? __ffs(Ld) - 1 : 0;
+  int sig_e = 0;  // sigma = 2^sig_e
+  if (packed) {
+    double mh = 0.0, ms = 0.0;
+    for (int k = tid; k < Ld * TW; k += kDftThreads) {
+      const int j = k / TW, t = k - j * TW;
+      if (t < tw_valid) {
+        const int64_t idx = (o * Ld + j) * inner + i0 + t;
+        mh = fmax(mh, fabs(s.H[idx]));
+        ms = fmax(ms, fabs(s.S[idx]));
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, off));
+      ms = fmax(ms, __shfl_xor_sync(0xffffffffu, ms, off));
+    }
+    if ((tid & 31) == 0) {
+      red[2 * (tid >> 5)] = mh;
+      red[2 * (tid >> 5) + 1] = ms;
+    }
+    __syncthreads();
+    mh = red[0];
+    ms = red[1];
+    for (int w = 1; w < kDftThreads / 32; ++w) {
+      mh = fmax(mh, red[2 * w]);
+      ms = fmax(ms, red[2 * w + 1]);
+    }
+    if (mh > 0.0 && ms > 0.0) {
+      int eh = 0, es = 0;
+      frexp(mh, &eh);
+      frexp(ms, &es);
+      sig_e = eh - es;
+    }
+  }
+  const double sig = pow2_scale(sig_e);
   for (int k = tid; k < Ld * TW; k += kDftThreads) {
     const int j = k / TW, t = k - j * TW;
     double2 v = make_double2(0.0, 0.0);
     if (t < tw_valid) {
       const int64_t idx = (o * Ld + j) * inner + i0 + t;
-      if (real_in)
+      if (packed)
+        v = make_double2(s.H[idx], sig * s.S[idx]);
+      else if (real_in)
         v.x = Xr[idx];
       else
         v = reinterpret_cast<const double2 *>(Xc)[idx];
@@ -99,11 +141,26 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
       }
       __syncthreads();
     }
-    for (int k = tid; k < Ld * TW; k += kDftThreads) {
-      const int kap = k / TW, t = k - kap * TW;
-      if (t < tw_valid) {
-        const int64_t idx = (o * Ld + kap) * inner + i0 + t;
-        reinterpret_cast<double2 *>(Xc)[idx] = x[kap * TW + t];
+    if (packed) {
+      const double hs2 = 0.5 / sig;
+      for (int k = tid; k < Ld * TW; k += kDftThreads) {
+        const int kap = k / TW, t = k - kap * TW;
+        if (t < tw_valid) {
+          const int kn = kap == 0 ? 0 : Ld - kap;
+          const double2 z = x[kap * TW + t], zc = x[kn * TW + t];  // Z_k, Z_-k
+          const int64_t idx = (o * Ld + kap) * inner + i0 + t;
+          reinterpret_cast<double2 *>(s.Hbar)[idx] = make_double2(0.5 * (z.x + zc.x), 0.5 * (z.y - zc.y));
+          // (Z_k - conj Z_-k) / (2 i sigma)
+          reinterpret_cast<double2 *>(s.Sbar)[idx] = make_double2(hs2 * (z.y + zc.y), -hs2 * (z.x - zc.x));
+        }
+      }
+    } else {
+      for (int k = tid; k < Ld * TW; k += kDftThreads) {
+        const int kap = k / TW, t = k - kap * TW;
+        if (t < tw_valid) {
+          const int64_t idx = (o * Ld + kap) * inner + i0 + t;
+          reinterpret_cast<double2 *>(Xc)[idx] = x[kap * TW + t];
+        }
       }
     }
   } else {

@@ -42,11 +42,14 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
 // per warp: A, B, V (m^2 complex each), rotation table (16 x {c, sr, si, p, q}), kept index
-// map, scales and overlap eigenvalues (32 each), and the (k1 < k2) pair-block table (120 x 2)
-__host__ __device__ inline size_t eig_warp_bytes(int m) {
+// map, scales and overlap eigenvalues (32 each), the (k1 < k2) pair-block table (120 x 2) and the
+// Householder vectors (2 x 32 complex)
+__host__ __device__ inline size_t eig_warp_core_bytes(int m) {
   return (size_t)3 * m * m * sizeof(double2) + 16 * (3 * sizeof(double) + 2 * sizeof(int)) +
          32 * (2 * sizeof(double) + 2 * sizeof(int)) + 288;
 }
+// + 64 complex of Householder scratch (v and w)
+__host__ __device__ inline size_t eig_warp_bytes(int m) { return eig_warp_core_bytes(m) + 64 * sizeof(double2); }
 
 struct RotTab {
   double *c, *sr, *si;
@@ -176,6 +179,126 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
   return sweep;
 }
 
+// Householder reduction of the Hermitian m x m matrix A (shared memory, destroyed) to a real
+// symmetric tridiagonal matrix with the same eigenvalues, one warp.  Column k: x = A[k+1:, k],
+// alpha = -e^{i arg x0} |x|, v = x - alpha e1, H = I - tau v v^H with tau = 1 / (|x|^2 + |x| |x0|);
+// A <- H A H as p = tau A v, w = p - (tau/2)(v^H p) v, A <- A - v w^H - w v^H on the trailing
+// block.  The off-diagonal alpha_k is replaced by |alpha_k| (a diagonal unitary similarity).
+// td[0..m), te[0..m-1) receive the diagonal and off-diagonal.  vw: 2 x 32 complex scratch.
+__device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, double *td, double *te) {
+  double2 *vec = vw, *wv = vw + 32;
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n = m - k - 1;
+    double2 xi = make_double2(0.0, 0.0);
+    if (lane < n) xi = A[(k + 1 + lane) * m + k];
+    double part = xi.x * xi.x + xi.y * xi.y;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double sig = part;
+    const double2 x0 = A[(k + 1) * m + k];
+    const double akk = A[k * m + k].x;
+    if (!(sig > 0.0)) {  // column already reduced
+      if (lane == 0) {
+        td[k] = akk;
+        te[k] = 0.0;
+      }
+      continue;
+    }
+    const double nrm = sqrt(sig), ax0 = hypot(x0.x, x0.y);
+    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    const double tau = 1.0 / (sig + nrm * ax0);
+    if (lane < n) vec[lane] = lane == 0 ? make_double2(x0.x + ph.x * nrm, x0.y + ph.y * nrm) : xi;
+    __syncwarp();
+    // p = tau B v on rows i < n of the trailing block B = A[k+1:, k+1:]
+    double2 pi = make_double2(0.0, 0.0);
+    if (lane < n) {
+      const double2 *row = A + (k + 1 + lane) * m + (k + 1);
+      for (int j = 0; j < n; ++j) {
+        const double2 b = row[j], v = vec[j];
+        pi.x += b.x * v.x - b.y * v.y;
+        pi.y += b.x * v.y + b.y * v.x;
+      }
+      pi = cscale(pi, tau);
+    }
+    // K = (tau / 2) Re(v^H p)
+    double kp = 0.0;
+    if (lane < n) kp = vec[lane].x * pi.x + vec[lane].y * pi.y;
+    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+    const double Kf = 0.5 * tau * kp;
+    if (lane < n) wv[lane] = make_double2(pi.x - Kf * vec[lane].x, pi.y - Kf * vec[lane].y);
+    __syncwarp();
+    for (int e = lane; e < n * n; e += 32) {
+      const int i = e / n, j = e - (e / n) * n;
+      const double2 vi = vec[i], wi = wv[i], vj = vec[j], wj = wv[j];
+      double2 &a = A[(k + 1 + i) * m + (k + 1 + j)];
+      // a -= v_i conj(w_j) + w_i conj(v_j)
+      a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
+      a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+    }
+    if (lane == 0) {
+      td[k] = akk;
+      te[k] = nrm;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (m >= 2) {
+      td[m - 2] = A[(m - 2) * m + (m - 2)].x;
+      const double2 b = A[(m - 1) * m + (m - 2)];
+      te[m - 2] = hypot(b.x, b.y);
+    }
+    td[m - 1] = A[(m - 1) * m + (m - 1)].x;
+  }
+  __syncwarp();
+}
+
+// Eigenvalues of the symmetric tridiagonal matrix (d[0..n), e[0..n-1)) by the implicit QR
+// iteration with Wilkinson shifts (one thread; d and e are overwritten, the eigenvalues are
+// left unsorted in d).  A block [l, h] is split where |e_i| <= eps (|d_i| + |d_i+1|); each sweep
+// chases the bulge of the rotation chosen from the shifted first column.  Returns the number of
+// rotations, or -1 if some eigenvalue did not converge within 30 n sweeps.
+__device__ int tridiag_qr(double *d, double *e, int n) {
+  const double eps = 2.220446049250313e-16;
+  int rot = 0, sweeps = 0;
+  int h = n - 1;
+  while (h > 0) {
+    if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) {
+      e[h - 1] = 0.0;
+      --h;
+      continue;
+    }
+    if (++sweeps > 30 * n) return -1;
+    int l = h - 1;
+    while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
+    // Wilkinson shift from the trailing 2 x 2 block
+    const double dd = 0.5 * (d[h - 1] - d[h]), bb = e[h - 1];
+    const double r0 = hypot(dd, bb);
+    const double mu = d[h] - bb * bb / (dd + (dd >= 0.0 ? r0 : -r0));
+    double x = d[l] - mu, z = e[l], bulge = 0.0;
+    for (int k = l; k < h; ++k) {
+      const double r = hypot(x, z);
+      double c = 1.0, sn = 0.0;
+      if (r > 0.0) {
+        c = x / r;
+        sn = -z / r;
+      }
+      if (k > l) e[k - 1] = r;
+      const double ak = d[k], ak1 = d[k + 1], bk = e[k];
+      const double cc = c * c, ss = sn * sn, cs = c * sn;
+      d[k] = cc * ak - 2.0 * cs * bk + ss * ak1;
+      d[k + 1] = ss * ak + 2.0 * cs * bk + cc * ak1;
+      e[k] = cs * (ak - ak1) + (cc - ss) * bk;
+      if (k + 1 < h) {
+        bulge = -sn * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
+        z = bulge;
+      }
+      ++rot;
+    }
+  }
+  return rot;
+}
+
 // Hermitian part of a matrix that is Hermitian up to rounding.
 __device__ void hermitian_part(double2 *A, int m, int lane) {
   for (int e = lane; e < m * m; e += 32) {
@@ -287,55 +410,83 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
     dsc[a] = 1.0 / sqrt(dii);
   }
   __syncwarp();
+  double hf2 = 0.0;  // ||H~||_F^2
   for (int e = lane; e < m * m; e += 32) {
     const int a = e / m, b = e - (e / m) * m;
     const int ia = kidx[a], ib = kidx[b];
     const double sc = dsc[a] * dsc[b];
     A[e] = cscale(Hb[ia * m0 + ib], sc);
     B[e] = cscale(Sb[ia * m0 + ib], sc);
+    hf2 += A[e].x * A[e].x + A[e].y * A[e].y;
   }
+  for (int o = 16; o > 0; o >>= 1) hf2 += __shfl_xor_sync(0xffffffffu, hf2, o);
   __syncwarp();
+  // the blocks are Hermitian up to the rounding of the transform: solve their Hermitian parts
+  hermitian_part(A, m, lane);
+  hermitian_part(B, m, lane);
 
-  // 1. Cholesky of the scaled overlap (lower triangle, in place in B); a pivot below kCholTol
-  //    sends the k-point to canonical orthogonalisation
+  // 1. Cholesky of the scaled overlap (lower triangle, in place in B), right-looking: column j
+  //    is scaled by its pivot, then the trailing lower triangle is updated by every lane (no
+  //    serial sums); a pivot below kCholTol sends the k-point to canonical orthogonalisation
   bool chol = ok;
   for (int j = 0; chol && j < m; ++j) {
-    if (lane == 0) {
-      double d = B[j * m + j].x;
-      for (int k = 0; k < j; ++k) {
-        const double2 v = B[j * m + k];
-        d -= v.x * v.x + v.y * v.y;
-      }
-      B[j * m + j] = make_double2(d >= kCholTol ? sqrt(d) : -1.0, 0.0);
-    }
-    __syncwarp();
-    const double dj = B[j * m + j].x;
-    if (!(dj > 0.0)) {
+    const double d = B[j * m + j].x;
+    if (!(d >= kCholTol)) {  // warp-uniform: every lane reads the same pivot
       chol = false;
       break;
     }
-    const double inv = 1.0 / dj;
-    for (int i = j + 1 + lane; i < m; i += 32) {
-      double2 v = B[i * m + j];
-      for (int k = 0; k < j; ++k) v = csub(v, cmulc(B[i * m + k], B[j * m + k]));
-      B[i * m + j] = cscale(v, inv);
+    const double ljj = sqrt(d), inv = 1.0 / ljj;
+    __syncwarp();
+    for (int i = j + 1 + lane; i < m; i += 32) B[i * m + j] = cscale(B[i * m + j], inv);
+    __syncwarp();
+    if (lane == 0) B[j * m + j] = make_double2(ljj, 0.0);
+    // B[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i < m: the n (n + 1) / 2 entries of the
+    // trailing lower triangle, n = m - j - 1, row by row
+    const int n = m - j - 1;
+    for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+      int i = (int)((sqrt(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // row of the t-th entry
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int k = t - i * (i + 1) / 2;
+      const int ri = j + 1 + i, rk = j + 1 + k;
+      B[ri * m + rk] = csub(B[ri * m + rk], cmulc(B[ri * m + j], B[rk * m + j]));
     }
     __syncwarp();
   }
 
   int sweeps = 0;
   if (ok && chol) {
-    // 2. C = L^{-1} H L^{-H}
+    // 2. C = L^{-1} H L^{-H}.  The first pass also solves L Z = I in the columns m .. 2m-1 (the
+    //    lanes a warp leaves idle when m <= 16): trace(S~^{-1}) = ||Z||_F^2 >= 1 / lambda_min, so
+    //    1 / ||Z||_F^2 >= kLindepTol proves that no overlap direction falls below kLindepTol and
+    //    the Cholesky route solves the same pencil as canonical orthogonalisation; otherwise the
+    //    k-point goes to the canonical route.
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = e / m, j = e - (e / m) * m;
+      V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
-      for (int c = lane; c < m; c += 32) {
+      const int ncol = pass == 0 ? 2 * m : m;
+      for (int cc = lane; cc < ncol; cc += 32) {
+        double2 *X = cc < m ? A : V;
+        const int c = cc < m ? cc : cc - m;
         for (int i = 0; i < m; ++i) {
-          double2 v = A[i * m + c];
-          for (int k = 0; k < i; ++k) v = csub(v, cmul(B[i * m + k], A[k * m + c]));
-          A[i * m + c] = cscale(v, 1.0 / B[i * m + i].x);
+          double2 v = X[i * m + c];
+          for (int k = 0; k < i; ++k) v = csub(v, cmul(B[i * m + k], X[k * m + c]));
+          X[i * m + c] = cscale(v, 1.0 / B[i * m + i].x);
         }
       }
       __syncwarp();
-      if (pass == 0) {  // A <- A^H
+      if (pass == 0) {
+        double tr = 0.0;
+        for (int e = lane; e < m * m; e += 32) tr += V[e].x * V[e].x + V[e].y * V[e].y;
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (!(tr * kLindepTol <= 1.0)) {  // a direction may lie below kLindepTol
+          chol = false;
+          break;
+        }
+        // A <- A^H
         for (int e = lane; e < m * m; e += 32) {
           const int i = e / m, j = e - (e / m) * m;
           if (i < j) {
@@ -349,8 +500,18 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
         __syncwarp();
       }
     }
-    hermitian_part(A, m, lane);
-  } else if (ok) {
+    if (chol) {
+      hermitian_part(A, m, lane);
+    } else {  // the scaled H again for the canonical route
+      for (int e = lane; e < m * m; e += 32) {
+        const int a = e / m, b = e - (e / m) * m;
+        A[e] = cscale(Hb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
+      }
+      __syncwarp();
+      hermitian_part(A, m, lane);
+    }
+  }
+  if (ok && !chol) {
     // 2'. canonical orthogonalisation: S~ = V diag(sigma) V^H, keep sigma >= kLindepTol,
     //     X = V_kept diag(sigma)^{-1/2}, C = X^H H~ X
     for (int e = lane; e < m * m; e += 32) {
@@ -401,11 +562,54 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
     hermitian_part(A, m, lane);
   }
 
+  bool tri = s.tri != nullptr;
+  if (tri && ok) {
+    // The tridiagonal route (Householder + QR) is accurate to ~m eps ||C|| absolute for every
+    // eigenvalue; Jacobi keeps the accuracy of the small eigenvalues of graded matrices (nearly
+    // singular overlaps, nearly cancelled Bloch functions with large scaled entries), so such
+    // k-points stay on Jacobi: tridiagonal only if ||C||_F <= 2 ||H~||_F
+    double cf2 = 0.0;
+    for (int e = lane; e < m * m; e += 32) cf2 += A[e].x * A[e].x + A[e].y * A[e].y;
+    for (int o = 16; o > 0; o >>= 1) cf2 += __shfl_xor_sync(0xffffffffu, cf2, o);
+    // and only if its absolute error stays below half the 1e-10 Ha floor: m eps ||C||_F <= 5e-11
+    const double cmax = 5e-11 / (m * 2.220446049250313e-16);
+    if (!(cf2 <= 4.0 * hf2) || !(cf2 <= cmax * cmax)) {
+      tri = false;
+      if (lane == 0) s.tri[(int64_t)widx * (2 * m0 + 1)] = -2.0;  // solved here
+    }
+  }
+  if (tri) {
+    // 3'. tridiagonal route: Householder reduction here, the tridiagonal eigenvalues by
+    //     k_tridiag_eig (one thread per matrix); slot widx = [m | d[m0] | e[m0]]
+    double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
+    if (ok && m > 0)
+      householder_tridiag(A, m, lane, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+                          slot + 1 + m0);
+    if (lane == 0) {
+      slot[0] = ok ? (double)m : -1.0;
+      if (counters && ok) {
+        atomicAdd(counters + 1, 1ull);
+        if (!chol) atomicAdd(counters + 2, 1ull);
+      }
+      const int st = ok ? m0 - m : (int)LHF_ERR_NOT_SPD;
+      if (s.kstat) {
+        s.kstat[kap] = st;
+        s.kstat[mk] = st;
+      }
+      if (!ok) atomicOr(flags, kFlagNotSpd);
+    }
+    if (!ok && lane < m0) {
+      s.eig[(int64_t)kap * m0 + lane] = NAN;
+      s.eig[(int64_t)mk * m0 + lane] = NAN;
+    }
+    return;
+  }
+
   if (ok) {
     // 3. cyclic Jacobi on C
     sweeps += jacobi_herm(A, nullptr, m, lane, R);
     if (lane == 0 && counters) {
-      atomicAdd(counters, (unsigned long long)sweeps);
+      if (!s.tri) atomicAdd(counters, (unsigned long long)sweeps);  // tridiagonal mode counts QR rotations
       atomicAdd(counters + 1, 1ull);
       if (!chol) atomicAdd(counters + 2, 1ull);
     }
@@ -434,6 +638,51 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   }
 }
 
+// Eigenvalues of the tridiagonal matrices left by k_eig: one thread per solved k-point; sorted
+// ascending and written to the k-point and its conjugate partner, removed slots +inf.
+__global__ void __launch_bounds__(128) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
+                                                     unsigned long long *counters) {
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box || !s.tri) return;
+  const int widx = blockIdx.x * blockDim.x + threadIdx.x;
+  int kap;
+  if (s.klist) {
+    if (widx >= s.nkhalf) return;
+    kap = s.klist[widx];
+  } else {
+    return;
+  }
+  const int m0 = s.m0;
+  const double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
+  const int m = (int)slot[0];
+  if (m < 0) return;  // -1: not positive definite (NaN written by k_eig); -2: solved by k_eig
+  const int L0 = s.d[0].L, L1 = s.d[1].L, L2 = s.d[2].L;
+  const int k0 = kap / (L1 * L2), k1 = (kap / L2) % L1, k2 = kap % L2;
+  const int mk = (((L0 - k0) % L0) * L1 + (L1 - k1) % L1) * L2 + (L2 - k2) % L2;
+  double d[kMaxM0], e[kMaxM0];
+  for (int i = 0; i < m; ++i) d[i] = slot[1 + i];
+  for (int i = 0; i + 1 < m; ++i) e[i] = slot[1 + m0 + i];
+  const int rot = m > 0 ? tridiag_qr(d, e, m) : 0;
+  if (rot < 0) atomicOr(flags, kFlagNotSpd);
+  if (counters && rot > 0) atomicAdd(counters, (unsigned long long)rot);
+  // insertion sort (m <= 32)
+  for (int i = 1; i < m; ++i) {
+    const double v = d[i];
+    int j = i - 1;
+    while (j >= 0 && d[j] > v) {
+      d[j + 1] = d[j];
+      --j;
+    }
+    d[j + 1] = v;
+  }
+  double *out = s.eig + (int64_t)kap * m0, *out2 = s.eig + (int64_t)mk * m0;
+  for (int i = 0; i < m0; ++i) {
+    const double v = rot < 0 ? NAN : (i < m ? d[i] : INFINITY);
+    out[i] = v;
+    out2[i] = v;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
@@ -443,7 +692,7 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
 }
 
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                       unsigned long long *counters, cudaStream_t st) {
+                       unsigned long long *counters, cudaStream_t st, bool tri) {
   if (max_k <= 0 || nsys <= 0) return cudaSuccess;
   const size_t smem = kEigWarps * eig_warp_bytes(max_m0);
   if (smem > 48 * 1024) {
@@ -452,6 +701,9 @@ cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsig
   }
   dim3 grid((max_k + kEigWarps - 1) / kEigWarps, nsys);
   k_eig<<<grid, kEigWarps * 32, smem, st>>>(sys, flags, counters, max_m0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !tri) return e;
+  k_tridiag_eig<<<dim3((max_k + 127) / 128, nsys), 128, 0, st>>>(sys, flags, counters);
   return cudaGetLastError();
 }
 

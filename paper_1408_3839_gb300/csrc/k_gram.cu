@@ -54,16 +54,22 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// Phase 1 for one CTA: Q[nu][c] and the P1 cross terms E[nu][c] in shared memory, their row
-// sums in red[2 nu], and the P1 stiffness/mass slots of C written out.
+// Phase 1 for one CTA: Q[nu][c] and the difference products E[nu][c] = sum_p D_i(g_mu,j) D_i(g_nu)
+// in shared memory, their row sums in red[2 nu], and the P1 stiffness/mass slots of C written
+// out.  With D_i(f) = f_i - f_(i+1) (periodic wrap; open: f_(-1) = f_n = 0),
+//   g^T A f = (1/h) sum_i D_i(f) D_i(g),   g^T S f = h sum_i f_i g_i - (h/6) sum_i D_i(f) D_i(g),
+// the same sums as (1/h) sum (2 f_i g_i - f_i g_(i+1) - f_(i+1) g_i) and (h/6) sum (4 f_i g_i +
+// cross terms) regrouped: no cancellation in the stiffness sum and two products per node.
 __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, double *E, double *red) {
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, L = D.L;
   const int ld = nv + 1;
   const double *G = s.ws + D.offG;
+  const double *Dg = s.ws + D.offD;
   const int mu = it.mu;
   const int j = D.jlo + it.jw;
   const double *f = G + (int64_t)mu * n;
+  const double *df = Dg + (int64_t)mu * n;
   const int tid = threadIdx.x;
   // support of the shifted row function (cells), tested modulo L
   const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
@@ -74,6 +80,7 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
     const int nu = p0 / nv;
     const int c = p0 - nu * nv;
     const double *g = G + (int64_t)nu * n;
+    const double *dg = Dg + (int64_t)nu * n;
     double q = 0.0, e = 0.0;
     if (periodic) {
       const int plo = s.cell_lo[it.l][nu];
@@ -86,11 +93,8 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
       const bool test = mspan < L - 1;
       for (int p = plo; p <= phi; ++p) {
         if (!test || rel <= mspan) {  // else the row support is absent in this cell
-          const int iv1 = (iv + 1 == n) ? 0 : iv + 1;
-          const int iu1 = (iu + 1 == n) ? 0 : iu + 1;
-          const double fi = f[iu], gi = g[iv];
-          q += fi * gi;
-          e += fi * g[iv1] + f[iu1] * gi;
+          q += f[iu] * g[iv];
+          e += df[iu] * dg[iv];
         }
         iv += nc;
         if (iv >= n) iv -= n;
@@ -99,10 +103,10 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
         if (++rel == L) rel = 0;
       }
     } else {
-      // single open cell: nodes c = 0..n-1, Dirichlet ends (no wrap)
-      const double fi = f[c], gi = g[c];
-      q = fi * gi;
-      if (c + 1 < n) e = fi * g[c + 1] + f[c + 1] * gi;
+      // single open cell: nodes c = 0..n-1, Dirichlet ends (the virtual node -1 adds f_0 g_0)
+      q = f[c] * g[c];
+      e = df[c] * dg[c];
+      if (c == 0) e += f[0] * g[0];
     }
     Q[nu * ld + c] = q;
     E[nu * ld + c] = e;
@@ -130,8 +134,8 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
   double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
   if (tid < m0) {
     const double dq = red[2 * tid], de = red[2 * tid + 1];
-    Cout[(int64_t)Rt * mm + tid] = (2.0 * dq - de) / D.h;
-    Cout[(int64_t)(Rt + 1) * mm + tid] = (4.0 * dq + de) * D.h / 6.0;
+    Cout[(int64_t)Rt * mm + tid] = de / D.h;
+    Cout[(int64_t)(Rt + 1) * mm + tid] = D.h * dq - de * D.h / 6.0;
   }
 }
 
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
   const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
   extern __shared__ double sm[];
   double *Q = sm;               // [m0][ld]
-  double *E = Q + m0 * ld;      // [m0][ld]  P1 cross terms per node
+  double *E = Q + m0 * ld;      // [m0][ld]  difference products per node (P1 forms)
   double *red = E + m0 * ld;    // [m0][2]   Dsum, Esum per nu
   gram_phase1(s, it, Q, E, red);
 

@@ -6,10 +6,10 @@
 //   T_j = K0 M1 M2 + M0 K1 M2 + M0 M1 K2        (P1 Laplacian, rank 3)
 //   V_j = sum_r c_r C0_r C1_r C2_r              (nuclear attraction, rank R_tot)
 //   H_j = T_j / 2 - V_j
-// written to block (j0 mod L0, j1 mod L1, j2 mod L2) of the first block column.  Blocks
-// outside the window are zero-filled by the host before the launch (step a6).
-// Thread per (block, entry): consecutive threads read consecutive entries of each factor slot
-// (coalesced); the loop over r streams the three directions' factors.
+// written to block (j0 mod L0, j1 mod L1, j2 mod L2) of the first block column; blocks outside
+// the window are written as exact zeros by the same kernel (step a6).
+// Thread per (block of the first block column, entry): consecutive threads read consecutive
+// entries of each factor slot (coalesced); the loop over r streams the three directions' factors.
 #include "lhf_internal.cuh"
 
 namespace lhf {
@@ -20,21 +20,25 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
   if (s.box) return;
   const int m0 = s.m0, mm = m0 * m0, Rt = s.Rt;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= (int64_t)s.nwin * mm) return;
-  const int w = (int)(item / mm);
-  const int e = (int)(item - (int64_t)w * mm);
-  const int J1 = s.d[1].J, J2 = s.d[2].J;
-  const int jw0 = w / (J1 * J2);
-  const int jw1 = (w / J2) % J1;
-  const int jw2 = w % J2;
-  const int jw[3] = {jw0, jw1, jw2};
+  if (item >= (int64_t)s.nblocks * mm) return;
+  const int64_t blk = item / mm;
+  const int e = (int)(item - blk * mm);
+  const int L1 = s.d[1].L, L2 = s.d[2].L;
+  const int jj[3] = {(int)(blk / ((int64_t)L1 * L2)), (int)((blk / L2) % L1), (int)(blk % L2)};
+  // window index of each direction's displacement; outside the window the block is zero (a6)
   const double *F[3];
-  int jj[3];
+  bool inside = true;
   for (int l = 0; l < 3; ++l) {
     const DirDev &D = s.d[l];
-    F[l] = s.ws + D.offC + (int64_t)jw[l] * (Rt + 2) * mm + e;
-    int j = (D.jlo + jw[l]) % D.L;
-    jj[l] = j < 0 ? j + D.L : j;
+    int jw = (jj[l] - D.jlo) % D.L;
+    if (jw < 0) jw += D.L;
+    if (jw >= D.J) inside = false;
+    F[l] = s.ws + D.offC + (int64_t)(inside ? jw : 0) * (Rt + 2) * mm + e;
+  }
+  if (!inside) {
+    s.H[item] = 0.0;
+    s.S[item] = 0.0;
+    return;
   }
   double v = 0.0;
   for (int r = 0; r < Rt; ++r) {
@@ -46,9 +50,8 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
   const double M0 = F[0][om], M1 = F[1][om], M2 = F[2][om];
   const double S = M0 * M1 * M2;
   const double T = K0 * M1 * M2 + M0 * K1 * M2 + M0 * M1 * K2;
-  const int64_t blk = ((int64_t)jj[0] * s.d[1].L + jj[1]) * s.d[2].L + jj[2];
-  s.H[blk * mm + e] = 0.5 * T - v;
-  s.S[blk * mm + e] = S;
+  s.H[item] = 0.5 * T - v;
+  s.S[item] = S;
 }
 
 }  // namespace

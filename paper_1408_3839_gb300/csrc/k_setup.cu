@@ -67,6 +67,30 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
   s.ws[D.offG + (int64_t)mu * nx + e] = g;
 }
 
+// Forward differences D_i = g_i - g_(i+1) of the samples (periodic directions wrap; open ones
+// take g_n = 0): the P1 stiffness form is sum_i D_i(f) D_i(g) / h with no cancellation, and the
+// mass form follows from it (k_gram.cu).  Not formed for the extended samples of an open box.
+__global__ void __launch_bounds__(256) k_basis_diff(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m0 = s.m0;
+  int l = 0;
+  for (; l < 3; ++l) {
+    int64_t cnt = (int64_t)m0 * (s.d[l].n + s.d[l].gext);
+    if (item < cnt) break;
+    item -= cnt;
+  }
+  if (l == 3) return;
+  const DirDev &D = s.d[l];
+  if (D.offD < 0) return;
+  const int n = D.n;
+  if (item >= (int64_t)m0 * n) return;
+  const int mu = (int)(item / n), i = (int)(item - (int64_t)mu * n);
+  const double *g = s.ws + D.offG + (int64_t)mu * n;
+  const double next = i + 1 < n ? g[i + 1] : (D.periodic ? g[0] : 0.0);
+  s.ws[D.offD + (int64_t)mu * n + i] = g[i] - next;
+}
+
 // int_{-d}^{d} exp(-(m + u)^2) du = exp(-m^2) sum_k H_2k(m) 2 d^(2k+1) / (2k+1)!  (Taylor series
 // of the Gaussian about the cell centre; H_n are the physicists' Hermite polynomials, whose
 // recurrence H_{n+1} = 2 m H_n - 2 n H_{n-1} gives the derivatives).  Used for narrow cells
@@ -349,6 +373,9 @@ cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_
   if (max_items <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid((max_items + 255) / 256, nsys);
   k_basis<<<grid, 256, 0, st>>>(sys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_basis_diff<<<grid, 256, 0, st>>>(sys);
   return cudaGetLastError();
 }
 

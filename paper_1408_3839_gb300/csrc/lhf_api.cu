@@ -51,6 +51,7 @@ struct Plan {
   int box_items = 0, box_width = 0;
   long long mirror_items = 0;  // window-block elements filled from their mirrors
   size_t zcell_off = 0, dense_off = 0;
+  size_t tri_off = 0;  // tridiagonal scratch of the k-point solves (periodic)
   std::vector<double> zcell;  // host copy of the per-cell charges (box)
 };
 
@@ -84,6 +85,10 @@ struct lhf_ctx {
   void *tc_host = nullptr;  // their pinned staging copy
   size_t tc_cap = 0;
   cudaEvent_t tc_copied = nullptr;  // the staging copy has been consumed
+  // while a graph is captured: its prepared tensor-core argument buffer (device)
+  const void *graph_tc = nullptr;
+  int graph_tc_jobs = 0;
+  size_t graph_tc_off = 0;
   std::vector<int> host_L;
   // solved k-points (one per conjugate pair) per lattice shape, on the device
   std::map<std::array<int, 3>, std::pair<int *, int>> klists;
@@ -137,6 +142,18 @@ struct lhf_ctx {
     if (e == cudaSuccess) return LHF_OK;
     return fail(LHF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   }
+};
+
+struct lhf_graph {
+  lhf_ctx *ctx = nullptr;
+  double *ws = nullptr;        // the graph's own workspace (factors and internal blocks)
+  SysDev *d_sys = nullptr;     // its descriptors
+  void *tc_dev = nullptr;      // tensor-core maps and jobs (LHF_MIXED)
+  int tc_jobs = 0;
+  size_t tc_off = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nsys = 0;
 };
 
 namespace {
@@ -396,6 +413,12 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
   for (int l = 0; l < 3; ++l) {
     sd.d[l].offG = (int64_t)off;
     off = align_up(off + (size_t)m0 * (sd.d[l].n + sd.d[l].gext));
+    if (sd.d[l].gext == 0 && sd.d[l].J > 0) {  // differences for the P1 forms of the Gram kernels
+      sd.d[l].offD = (int64_t)off;
+      off = align_up(off + (size_t)m0 * sd.d[l].n);
+    } else {
+      sd.d[l].offD = -1;
+    }
   }
   for (int l = 0; l < 3; ++l) {
     sd.d[l].offV = (int64_t)off;
@@ -443,8 +466,10 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.blocks_doubles = align_up(Nb * Nb);
     P.rank_items = 0;
   } else {
+    P.tri_off = off;  // one slot per k-point bounds the solved ones
+    off = align_up(off + (size_t)sd.nblocks * (2 * m0 + 1));
     P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
-    P.rank_items = sd.nwin * mm;
+    P.rank_items = sd.nblocks * mm;  // window blocks and the zeros outside
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
   P.ws = off;
@@ -543,6 +568,17 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
                           "digit-plane kernels");
   c->end(2);
   if (st != LHF_OK) return st;
+  if (c->graph_tc) {  // capture: the arguments were prepared and copied before the capture
+    c->begin(8);
+    st = c->cuda(lhf::gram_tc_launch(c->graph_tc, c->graph_tc_jobs, c->graph_tc_off, c->d_flags, c->stream),
+                 "tensor-core Gram kernel");
+    c->end();
+    if (st != LHF_OK) return st;
+    c->begin(2);
+    st = c->cuda(lhf::launch_gram_mirror(c->d_sys, nsys, mirror, c->stream), "mirror kernel");
+    c->end(mirror > 0 ? 1 : 0);
+    return st;
+  }
   std::vector<SysDev> host(nsys);
   for (int i = 0; i < nsys; ++i) host[i] = ps[i].sd;
   const size_t need = lhf::gram_tc_args_bytes(host.data(), nsys);
@@ -580,21 +616,10 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
 // Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
 lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
-  // a6: blocks outside the window are exact zeros
-  for (const Plan &p : ps)
-    if (!p.sd.box && p.sd.nwin < p.sd.nblocks) {
-      const size_t bytes = (size_t)p.sd.nblocks * p.sd.m0 * p.sd.m0 * sizeof(double);
-      c->begin(6);
-      lhf_status st = c->cuda(cudaMemsetAsync(p.sd.H, 0, bytes, c->stream), "cudaMemsetAsync");
-      if (st != LHF_OK) return st;
-      st = c->cuda(cudaMemsetAsync(p.sd.S, 0, bytes, c->stream), "cudaMemsetAsync");
-      c->end(2);
-      if (st != LHF_OK) return st;
-    }
-  lhf_status st;
+  lhf_status st;  // (a6, the zero blocks outside the window, is written by the rank-sum kernel)
   c->begin(0);
   st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
-  c->end();
+  c->end(2);
   if (st != LHF_OK) return st;
   c->begin(1);
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
@@ -634,7 +659,7 @@ lhf_status run_box_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
   }
   c->begin(0);
   st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
-  c->end();
+  c->end(2);
   if (st != LHF_OK) return st;
   c->begin(1);
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
@@ -729,9 +754,10 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
   c->begin(5);
   lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
   if (st == LHF_OK)
-    st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream),
+    st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream,
+                                 true),
                  "eigen kernel");
-  c->end(2);
+  c->end(3);
   return st;
 }
 
@@ -753,6 +779,7 @@ void bind_ws(Plan &p, double *base) {
   p.sd.ws = base;
   p.sd.s0 = base + p.s0_off;
   p.sd.zcell = (p.sd.box && !p.zcell.empty()) ? base + p.zcell_off : nullptr;
+  p.sd.tri = p.sd.box ? nullptr : base + p.tri_off;
 }
 
 // Plan one system with workspace at ws_base and internal H, S, Hbar, Sbar after its factors.
@@ -1082,6 +1109,122 @@ lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *system
     }
   }
   return LHF_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// CUDA graph of the batched path
+
+lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,
+                            double *eig, int *kstat, lhf_graph **out) {
+  if (!c) return LHF_ERR_ARG;
+  if (!out) return c->fail(LHF_ERR_ARG, "out is required");
+  *out = nullptr;
+  if (nsys < 1 || !systems || !eig) return c->fail(LHF_ERR_ARG, "nsys >= 1, systems and eig are required");
+  lhf_status st = check_precision(c, prec);
+  if (st != LHF_OK) return st;
+  std::vector<Plan> ps(nsys);
+  size_t total = 0;
+  for (int i = 0; i < nsys; ++i) {
+    HostSystem hs;
+    st = system_from_desc(c, &systems[i], hs);
+    if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
+    st = make_plan(c, hs, ps[i], prec == LHF_MIXED);
+    if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
+    if (ps[i].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "system %d: open boxes are not captured in graphs", i);
+    total += internal_doubles(ps[i]);
+  }
+  lhf_graph *g = new (std::nothrow) lhf_graph();
+  if (!g) return c->fail(LHF_ERR_NOMEM, "graph");
+  g->ctx = c;
+  auto cleanup = [&](lhf_status s) {
+    lhf_graph_destroy(g);
+    return s;
+  };
+  if (cudaMalloc(&g->ws, total * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(c->fail(LHF_ERR_NOMEM, "graph workspace of %zu bytes", total * sizeof(double)));
+  }
+  size_t base = 0, eoff = 0, koff = 0;
+  std::vector<SysDev> sds(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    place_internal(ps[i], g->ws + base);
+    base += internal_doubles(ps[i]);
+    st = set_klist(c, ps[i].sd);
+    if (st != LHF_OK) return cleanup(st);
+    ps[i].sd.eig = eig + eoff;
+    ps[i].sd.kstat = kstat ? kstat + koff : nullptr;
+    eoff += (size_t)ps[i].sd.nblocks * ps[i].sd.m0;
+    koff += ps[i].sd.nblocks;
+    sds[i] = ps[i].sd;
+  }
+  st = c->cuda(cudaMalloc(&g->d_sys, nsys * sizeof(SysDev)), "cudaMalloc");
+  if (st != LHF_OK) return cleanup(st);
+  st = c->cuda(cudaMemcpy(g->d_sys, sds.data(), nsys * sizeof(SysDev), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st != LHF_OK) return cleanup(st);
+  if (ps[0].mixed) {
+    std::vector<unsigned char> hbuf(lhf::gram_tc_args_bytes(sds.data(), nsys));
+    cudaError_t e = lhf::gram_tc_prepare(sds.data(), nsys, hbuf.data(), hbuf.size(), &g->tc_jobs, &g->tc_off);
+    if (e == cudaErrorNotSupported) return cleanup(c->fail(LHF_ERR_UNSUPPORTED, "shape outside the tensor-core kernel's limits"));
+    st = c->cuda(e, "tensor-core preparation");
+    if (st != LHF_OK) return cleanup(st);
+    st = c->cuda(cudaMalloc(&g->tc_dev, hbuf.size()), "cudaMalloc");
+    if (st != LHF_OK) return cleanup(st);
+    st = c->cuda(cudaMemcpy(g->tc_dev, hbuf.data(), hbuf.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (st != LHF_OK) return cleanup(st);
+  }
+  // capture on a private stream (the legacy default stream cannot be captured)
+  cudaStream_t cs = nullptr;
+  st = c->cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (st != LHF_OK) return cleanup(st);
+  SysDev *saved_sys = c->d_sys;
+  cudaStream_t saved_stream = c->stream;
+  const bool saved_prof = c->prof;
+  c->d_sys = g->d_sys;
+  c->stream = cs;
+  c->prof = false;
+  c->graph_tc = g->tc_dev;
+  c->graph_tc_jobs = g->tc_jobs;
+  c->graph_tc_off = g->tc_off;
+  lhf_status run = c->cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (run == LHF_OK) {
+    run = run_assembly(c, ps);
+    if (run == LHF_OK) run = run_dft(c, ps);
+    if (run == LHF_OK) run = run_eig(c, ps);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (run == LHF_OK) run = c->cuda(e, "cudaStreamEndCapture");
+    g->graph = graph;
+  }
+  c->d_sys = saved_sys;
+  c->stream = saved_stream;
+  c->prof = saved_prof;
+  c->graph_tc = nullptr;
+  c->graph_tc_jobs = 0;
+  c->graph_tc_off = 0;
+  cudaStreamDestroy(cs);
+  if (run != LHF_OK) return cleanup(run);
+  st = c->cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");
+  if (st != LHF_OK) return cleanup(st);
+  g->nsys = nsys;
+  *out = g;
+  return LHF_OK;
+}
+
+lhf_status lhf_graph_launch(lhf_graph *g) {
+  if (!g || !g->exec) return LHF_ERR_ARG;
+  return g->ctx->cuda(cudaGraphLaunch(g->exec, g->ctx->stream), "cudaGraphLaunch");
+}
+
+void lhf_graph_destroy(lhf_graph *g) {
+  if (!g) return;
+  if (g->ctx) cudaStreamSynchronize(g->ctx->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->tc_dev) cudaFree(g->tc_dev);
+  if (g->d_sys) cudaFree(g->d_sys);
+  if (g->ws) cudaFree(g->ws);
+  cudaGetLastError();
+  delete g;
 }
 
 lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,

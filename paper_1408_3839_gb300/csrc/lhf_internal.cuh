@@ -41,6 +41,7 @@ struct DirDev {
   double h, x0, cell0, b;
   double invP;     // 1 / (L b): supercell period of a periodic direction
   int64_t offG;   // basis samples [m0][gext + n]   (doubles, from SysDev::ws)
+  int64_t offD;   // forward differences g_i - g_(i+1) [m0][n] (periodic wrap; open: g_n = 0), or -1
   int64_t offV;   // potential factors [Rt][nv]
   int64_t offC;   // Gram factors [J][Rt+2][m0][m0]
   // C[j][mu][nu] = C[-j][nu][mu] (Q_j and its mirror are the same sums): only the window blocks
@@ -82,6 +83,7 @@ struct SysDev {
   int *kstat;             // [nblocks] or null
   double *s0;             // [m0] mean over k-points of Re Sbar_ii (cell-periodic norms)
   const int *klist;       // [nkhalf] k-points solved (one per conjugate pair), or null
+  double *tri;            // [nkhalf][2 m0 + 1] tridiagonal of each solved k-point, or null (Jacobi)
   // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
@@ -94,6 +96,9 @@ __device__ __forceinline__ double pow2(int e) {
   if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
   return ldexp(1.0, e);
 }
+
+// 2^e for |e| <= 2046 as a double (0 or inf beyond the representable range).
+__device__ __forceinline__ double pow2_scale(int e) { return ldexp(1.0, e); }
 
 // x 2^e, exact whenever the result is a normal number (two power-of-two factors when 2^e itself
 // is out of range).
@@ -131,8 +136,10 @@ cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsi
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st);  // *passes += kernel launches (may be null)
+// k-point eigensolves; tri: systems carry a tridiagonal scratch (SysDev::tri), and the
+// tridiagonal eigenvalues are taken by a second kernel (else Jacobi inside k_eig).
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                       unsigned long long *counters, cudaStream_t st);
+                       unsigned long long *counters, cudaStream_t st, bool tri);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
 // Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
 // the dense matrices (thread per entry).

@@ -81,7 +81,7 @@ extern "C" lhf_status lhf_k_point_eigensolve_noalloc(const int *L, int m0, const
   if (cudaMemcpyAsync(dsys, &sd, sizeof sd, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess ||
       lhf::launch_overlap_norms(dsys, 1, st) != cudaSuccess ||
-      lhf::launch_eig(dsys, 1, (int)nblocks, m0, flags, nullptr, st) != cudaSuccess) {
+      lhf::launch_eig(dsys, 1, (int)nblocks, m0, flags, nullptr, st, false) != cudaSuccess) {
     cudaGetLastError();
     return LHF_ERR_CUDA;
   }

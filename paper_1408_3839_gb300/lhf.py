@@ -108,6 +108,10 @@ def load():
             "lhf_stage_times": (st, [ctx, _dp, _ip]),
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
             "lhf_k_point_eigensolve_noalloc": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int] + [ctypes.c_void_p] * 5),
+            "lhf_graph_create": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+            "lhf_graph_launch": (st, [ctypes.c_void_p]),
+            "lhf_graph_destroy": (None, [ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -272,8 +276,16 @@ class Context:
         self._check(self.lib.lhf_bloch_spectra_host(self._h, len(descs), arr, precision,
                                                     eig_host.ctypes.data, kp))
 
+    def graph_create(self, cfgs, eig, k_status=None, precision: int = FP64) -> "Graph":
+        """lhf_graph_create: the batched path captured once into a CUDA graph."""
+        descs, arr = self._systems(cfgs)
+        h = ctypes.c_void_p()
+        self._check(self.lib.lhf_graph_create(self._h, len(descs), arr, precision, _ptr(eig), _ptr(k_status),
+                                              ctypes.byref(h)))
+        return Graph(self, h, (eig, k_status))
+
     # -- live stage timing -------------------------------------------------------------------
-    STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "zero_fill", "upload", "gram_tc")
+    STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "unused", "upload", "gram_tc")
 
     def set_profiling(self, enable: bool):
         self._check(self.lib.lhf_set_profiling(self._h, 1 if enable else 0))
@@ -287,7 +299,7 @@ class Context:
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
 
     def eig_counters(self) -> tuple[int, int]:
-        """(Jacobi sweeps, matrices solved) since the previous call."""
+        """(QR rotations of the tridiagonal stage, matrices solved) since the previous call."""
         a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
         self._check(self.lib.lhf_eig_counters(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
@@ -303,6 +315,29 @@ class Context:
         jlo = ctypes.c_int(0)
         self._check(self.lib.lhf_gram_factors(self._h, precision, int(l), _ptr(C), ctypes.byref(jlo)))
         return jlo.value
+
+
+class Graph:
+    """A captured batched path (lhf_graph): launch() replays it on the context stream."""
+
+    def __init__(self, ctx: Context, handle, keep):
+        self._ctx = ctx
+        self._h = handle
+        self._keep = keep  # the output buffers the graph writes
+
+    def launch(self):
+        self._ctx._check(self._ctx.lib.lhf_graph_launch(self._h))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._ctx.lib.lhf_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def k_point_eigensolve_noalloc(L, m0: int, Hbar, Sbar, eig, k_status=None, stream=None):

@@ -17,7 +17,7 @@ steps.  ||u||^2 is large only where the kept overlap is nearly singular.
 import numpy as np
 import scipy.linalg as sla
 
-DROP_TOL = 1e-9
+DROP_TOL = 1e-6
 
 
 def block_rel_err(X, Xref, m0):
