@@ -275,11 +275,15 @@ __device__ int tridiag_qr(double *d, double *e, int n) {
     const double mu = d[h] - bb * bb / (dd + (dd >= 0.0 ? r0 : -r0));
     double x = d[l] - mu, z = e[l], bulge = 0.0;
     for (int k = l; k < h; ++k) {
-      const double r = hypot(x, z);
-      double c = 1.0, sn = 0.0;
-      if (r > 0.0) {
-        c = x / r;
-        sn = -z / r;
+      // Givens rotation from one reciprocal square root (|x|, |z| stay far inside the FP64 range:
+      // they are entries of the scaled reduced matrix)
+      const double r2 = fma(x, x, z * z);
+      double c = 1.0, sn = 0.0, r = 0.0;
+      if (r2 > 0.0) {
+        const double ri = rsqrt(r2);
+        c = x * ri;
+        sn = -z * ri;
+        r = r2 * ri;
       }
       if (k > l) e[k - 1] = r;
       const double ak = d[k], ak1 = d[k + 1], bk = e[k];
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
 
 // Eigenvalues of the tridiagonal matrices left by k_eig: one thread per solved k-point; sorted
 // ascending and written to the k-point and its conjugate partner, removed slots +inf.
-__global__ void __launch_bounds__(128) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
+__global__ void __launch_bounds__(32) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
                                                      unsigned long long *counters) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box || !s.tri) return;
@@ -703,7 +707,8 @@ cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsig
   k_eig<<<grid, kEigWarps * 32, smem, st>>>(sys, flags, counters, max_m0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !tri) return e;
-  k_tridiag_eig<<<dim3((max_k + 127) / 128, nsys), 128, 0, st>>>(sys, flags, counters);
+  // one thread per matrix; warp-sized blocks spread the (latency-bound) iterations over all SMs
+  k_tridiag_eig<<<dim3((max_k + 31) / 32, nsys), 32, 0, st>>>(sys, flags, counters);
   return cudaGetLastError();
 }
 

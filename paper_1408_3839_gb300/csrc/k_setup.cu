@@ -24,6 +24,34 @@ __device__ __forceinline__ double gto_factor(double d, double alpha, double cut,
   return g;
 }
 
+// Sample e (node i = e - gext) of the cell-0 copy of mu in direction l; exact zero outside the
+// widened cut range without floating-point work.
+__device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
+  const DirDev &D = s.d[l];
+  int rel = e - s.node_lo[l][mu];
+  if (D.periodic && rel < 0) rel += D.n;
+  if (rel < 0 || rel >= s.node_span[l][mu]) return 0.0;
+  const double x = D.x0 + (e - D.gext + 0.5) * D.h;
+  const double A = s.centre[mu][l];
+  const double cut = s.cut[mu];
+  const double al = s.alpha[mu];
+  const bool pdir = (s.kind[mu] == 1 + l);
+  const double pn = s.pnorm[mu];
+  if (!D.periodic) return gto_factor(x - A, al, cut, pdir, pn);
+  const double P = D.L * D.b;
+  const double d0 = x - A;
+  // images m with |d0 - m P| <= cut (the bracket is widened by one on each side; the cut test
+  // inside gto_factor decides)
+  const int mlo = (int)floor((d0 - cut) * D.invP) - 1;
+  const int mhi = (int)ceil((d0 + cut) * D.invP) + 1;
+  double g = 0.0;
+  for (int m = mlo; m <= mhi; ++m) g += gto_factor(d0 - m * P, al, cut, pdir, pn);
+  return g;
+}
+
+// Samples and their forward differences D_e = g_e - g_(e+1) (periodic directions wrap; open
+// ones take g_n = 0; not formed for the extended samples of an open box): the neighbour's
+// sample comes from the next lane, or is evaluated where the next lane holds another row.
 __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,61 +62,27 @@ __global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) 
     if (item < cnt) break;
     item -= cnt;
   }
-  if (l == 3) return;
-  const DirDev &D = s.d[l];
-  const int nx = D.n + D.gext;
-  const int mu = (int)(item / nx);
-  const int e = (int)(item - (int64_t)mu * nx);  // sample index: grid node i = e - gext
-  // samples outside the (widened) cut range are exact zeros: no floating-point work
-  int rel = e - s.node_lo[l][mu];
-  if (D.periodic && rel < 0) rel += D.n;
-  if (rel < 0 || rel >= s.node_span[l][mu]) {
-    s.ws[D.offG + (int64_t)mu * nx + e] = 0.0;
-    return;
-  }
-  const double x = D.x0 + (e - D.gext + 0.5) * D.h;
-  const double A = s.centre[mu][l];
-  const double cut = s.cut[mu];
-  const double al = s.alpha[mu];
-  const bool pdir = (s.kind[mu] == 1 + l);
-  const double pn = s.pnorm[mu];
+  const bool valid = l < 3;
+  int mu = 0, e = 0, nx = 1;
   double g = 0.0;
-  if (D.periodic) {
-    const double P = D.L * D.b;
-    const double d0 = x - A;
-    // images m with |d0 - m P| <= cut (the bracket is widened by one on each side; the cut
-    // test inside gto_factor decides)
-    const int mlo = (int)floor((d0 - cut) * D.invP) - 1;
-    const int mhi = (int)ceil((d0 + cut) * D.invP) + 1;
-    for (int m = mlo; m <= mhi; ++m) g += gto_factor(d0 - m * P, al, cut, pdir, pn);
-  } else {
-    g = gto_factor(x - A, al, cut, pdir, pn);
+  if (valid) {
+    nx = s.d[l].n + s.d[l].gext;
+    mu = (int)(item / nx);
+    e = (int)(item - (int64_t)mu * nx);
+    g = basis_sample(s, l, mu, e);
   }
-  s.ws[D.offG + (int64_t)mu * nx + e] = g;
-}
-
-// Forward differences D_i = g_i - g_(i+1) of the samples (periodic directions wrap; open ones
-// take g_n = 0): the P1 stiffness form is sum_i D_i(f) D_i(g) / h with no cancellation, and the
-// mass form follows from it (k_gram.cu).  Not formed for the extended samples of an open box.
-__global__ void __launch_bounds__(256) k_basis_diff(const SysDev *__restrict__ sysv) {
-  const SysDev &s = sysv[blockIdx.y];
-  int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int m0 = s.m0;
-  int l = 0;
-  for (; l < 3; ++l) {
-    int64_t cnt = (int64_t)m0 * (s.d[l].n + s.d[l].gext);
-    if (item < cnt) break;
-    item -= cnt;
-  }
-  if (l == 3) return;
+  // the whole warp takes part in the shuffle
+  double gn = __shfl_down_sync(0xffffffffu, g, 1);
+  if (!valid) return;
   const DirDev &D = s.d[l];
+  s.ws[D.offG + (int64_t)mu * nx + e] = g;
   if (D.offD < 0) return;
-  const int n = D.n;
-  if (item >= (int64_t)m0 * n) return;
-  const int mu = (int)(item / n), i = (int)(item - (int64_t)mu * n);
-  const double *g = s.ws + D.offG + (int64_t)mu * n;
-  const double next = i + 1 < n ? g[i + 1] : (D.periodic ? g[0] : 0.0);
-  s.ws[D.offD + (int64_t)mu * n + i] = g[i] - next;
+  const int lane = threadIdx.x & 31;
+  if (e + 1 == D.n)
+    gn = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
+  else if (lane == 31)
+    gn = basis_sample(s, l, mu, e + 1);
+  s.ws[D.offD + (int64_t)mu * D.n + e] = g - gn;
 }
 
 // int_{-d}^{d} exp(-(m + u)^2) du = exp(-m^2) sum_k H_2k(m) 2 d^(2k+1) / (2k+1)!  (Taylor series
@@ -373,9 +367,6 @@ cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_
   if (max_items <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid((max_items + 255) / 256, nsys);
   k_basis<<<grid, 256, 0, st>>>(sys);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_basis_diff<<<grid, 256, 0, st>>>(sys);
   return cudaGetLastError();
 }
 

@@ -619,7 +619,7 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   lhf_status st;  // (a6, the zero blocks outside the window, is written by the rank-sum kernel)
   c->begin(0);
   st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
-  c->end(2);
+  c->end();
   if (st != LHF_OK) return st;
   c->begin(1);
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
@@ -659,7 +659,7 @@ lhf_status run_box_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
   }
   c->begin(0);
   st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
-  c->end(2);
+  c->end();
   if (st != LHF_OK) return st;
   c->begin(1);
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
