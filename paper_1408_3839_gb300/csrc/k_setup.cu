@@ -308,6 +308,31 @@ __device__ double image_sum_taylor(double t, double xc, double b, double delta, 
   return v;
 }
 
+// Image sums whose window holds every image within reach (the images beyond the window lie
+// beyond exp(-100) of the nearest one): the lattice sum of the Gaussian is periodic in x and its
+// Fourier series (Poisson summation) integrates over the cell in closed form,
+//   sum_k int_cell exp(-t^2 (x - c0 - k b)^2) dx
+//     = sqrt(pi) / (t b) [h + sum_{n>=1} exp(-pi^2 n^2 / s^2) (2 b / (pi n)) cos(2 pi n (x_m - c0) / b)
+//                             sin(pi n h / b)],   s = t b, x_m the cell midpoint,
+// cut after the first n with exp(-pi^2 n^2 / s^2) below 1e-20 (n > 2.16 s): a few terms where
+// the direct sum would take ~20 / s images.
+constexpr double kPoissonMaxS = 1.5;
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ double image_sum_poisson(double t, double lo, double hi, double c0, double b) {
+  const double s = t * b, h = hi - lo, xm = 0.5 * (lo + hi);
+  const int N = (int)ceil(2.16 * s) + 1;
+  double acc = h;
+  for (int n = 1; n <= N; ++n) {
+    const double g = exp(-(kPi * n / s) * (kPi * n / s));
+    if (g == 0.0) break;
+    const double cs = cospi(2.0 * n * (xm - c0) / b);
+    const double sn = sinpi(n * h / b);
+    acc = fma(g * (2.0 * b / (kPi * n)) * cs, sn, acc);
+  }
+  return 1.7724538509055160273 / (t * b) * acc;  // sqrt(pi) / (t b)
+}
+
 __global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -336,7 +361,10 @@ __global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sy
     int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
     int khi = (khi_f > kmax) ? kmax : (int)khi_f;
     const double delta = t * D.h;
-    if (delta <= kTaylorMaxDelta) {
+    const double sb = t * D.b;
+    if (sb < kPoissonMaxS && klo > -kmax && khi < kmax) {
+      v = image_sum_poisson(t, lo, hi, c0, D.b);
+    } else if (delta <= kTaylorMaxDelta) {
       v = image_sum_taylor(t, 0.5 * (lo + hi) - c0, D.b, delta, klo, khi, kmax, even) / t;
     } else {
       for (int k = klo; k <= khi; ++k) {
