@@ -183,8 +183,10 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
 // symmetric tridiagonal matrix with the same eigenvalues, one warp.  Column k: x = A[k+1:, k],
 // alpha = -e^{i arg x0} |x|, v = x - alpha e1, H = I - tau v v^H with tau = 1 / (|x|^2 + |x| |x0|);
 // A <- H A H as p = tau A v, w = p - (tau/2)(v^H p) v, A <- A - v w^H - w v^H on the trailing
-// block.  The off-diagonal alpha_k is replaced by |alpha_k| (a diagonal unitary similarity).
-// td[0..m), te[0..m-1) receive the diagonal and off-diagonal.  vw: 2 x 32 complex scratch.
+// block.  Only the lower triangle of the trailing block is kept (the upper one is its conjugate);
+// the matrix-vector product takes two lanes per row.  The off-diagonal alpha_k is replaced by
+// |alpha_k| (a diagonal unitary similarity).  td[0..m), te[0..m-1) receive the diagonal and
+// off-diagonal.  vw: 2 x 32 complex scratch.
 __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, double *td, double *te) {
   double2 *vec = vw, *wv = vw + 32;
   for (int k = 0; k + 2 < m; ++k) {
@@ -208,29 +210,43 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
     const double tau = 1.0 / (sig + nrm * ax0);
     if (lane < n) vec[lane] = lane == 0 ? make_double2(x0.x + ph.x * nrm, x0.y + ph.y * nrm) : xi;
     __syncwarp();
-    // p = tau B v on rows i < n of the trailing block B = A[k+1:, k+1:]
-    double2 pi = make_double2(0.0, 0.0);
-    if (lane < n) {
-      const double2 *row = A + (k + 1 + lane) * m + (k + 1);
-      for (int j = 0; j < n; ++j) {
-        const double2 b = row[j], v = vec[j];
-        pi.x += b.x * v.x - b.y * v.y;
-        pi.y += b.x * v.y + b.y * v.x;
+    // p = tau B v, B = A[k+1:, k+1:] from its lower triangle, two lanes per row
+    const double2 *Bt = A + (k + 1) * m + (k + 1);
+    double kp = 0.0;
+    for (int r0 = 0; r0 < n; r0 += 16) {
+      const int r = r0 + (lane >> 1);
+      double2 pi = make_double2(0.0, 0.0);
+      if (r < n) {
+        for (int j = lane & 1; j < n; j += 2) {
+          double2 b = j <= r ? Bt[r * m + j] : Bt[j * m + r];
+          if (j > r) b.y = -b.y;
+          const double2 v = vec[j];
+          pi.x += b.x * v.x - b.y * v.y;
+          pi.y += b.x * v.y + b.y * v.x;
+        }
       }
-      pi = cscale(pi, tau);
+      pi.x += __shfl_xor_sync(0xffffffffu, pi.x, 1);
+      pi.y += __shfl_xor_sync(0xffffffffu, pi.y, 1);
+      if (r < n && (lane & 1) == 0) {
+        pi = cscale(pi, tau);
+        wv[r] = pi;
+        kp += vec[r].x * pi.x + vec[r].y * pi.y;  // Re(conj(v_r) p_r)
+      }
     }
     // K = (tau / 2) Re(v^H p)
-    double kp = 0.0;
-    if (lane < n) kp = vec[lane].x * pi.x + vec[lane].y * pi.y;
     for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
     const double Kf = 0.5 * tau * kp;
-    if (lane < n) wv[lane] = make_double2(pi.x - Kf * vec[lane].x, pi.y - Kf * vec[lane].y);
     __syncwarp();
-    for (int e = lane; e < n * n; e += 32) {
-      const int i = e / n, j = e - (e / n) * n;
+    if (lane < n) wv[lane] = make_double2(wv[lane].x - Kf * vec[lane].x, wv[lane].y - Kf * vec[lane].y);
+    __syncwarp();
+    // lower triangle (i >= j) of the trailing block: a -= v_i conj(w_j) + w_i conj(v_j)
+    for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+      int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int j = t - i * (i + 1) / 2;
       const double2 vi = vec[i], wi = wv[i], vj = vec[j], wj = wv[j];
       double2 &a = A[(k + 1 + i) * m + (k + 1 + j)];
-      // a -= v_i conj(w_j) + w_i conj(v_j)
       a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
       a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
     }
@@ -469,16 +485,34 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       const int i = e / m, j = e - (e / m) * m;
       V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
+    for (int i = lane; i < m; i += 32) sg[i] = 1.0 / B[i * m + i].x;  // 1 / L_ii
     __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
+      // forward substitution per column; with 16 columns or fewer two lanes share a column
+      // (even and odd k of each inner sum, combined by a shuffle)
       const int ncol = pass == 0 ? 2 * m : m;
-      for (int cc = lane; cc < ncol; cc += 32) {
+      const int q = ncol <= 16 ? 2 : 1;
+      for (int cc0 = 0; cc0 < ncol; cc0 += 32 / q) {
+        const int cc = cc0 + lane / q, part = lane % q;
+        const bool act = cc < ncol;
         double2 *X = cc < m ? A : V;
-        const int c = cc < m ? cc : cc - m;
+        const int c = act ? (cc < m ? cc : cc - m) : 0;
+        double2 z[kMaxM0];
         for (int i = 0; i < m; ++i) {
-          double2 v = X[i * m + c];
-          for (int k = 0; k < i; ++k) v = csub(v, cmul(B[i * m + k], X[k * m + c]));
-          X[i * m + c] = cscale(v, 1.0 / B[i * m + i].x);
+          double2 acc = make_double2(0.0, 0.0);
+          if (act)
+            for (int k = part; k < i; k += q) {
+              const double2 t = cmul(B[i * m + k], z[k]);
+              acc.x += t.x;
+              acc.y += t.y;
+            }
+          if (q == 2) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+          }
+          const double2 xi = act ? X[i * m + c] : make_double2(0.0, 0.0);
+          z[i] = cscale(csub(xi, acc), sg[i]);
+          if (act && part == 0) X[i * m + c] = z[i];
         }
       }
       __syncwarp();
