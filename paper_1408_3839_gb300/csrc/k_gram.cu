@@ -49,6 +49,9 @@ __device__ __forceinline__ bool decode_gram(const SysDev &s, int b, GramItem &it
   return false;
 }
 
+// floor(a / b) for b > 0
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
@@ -86,21 +89,32 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
       const int plo = s.cell_lo[it.l][nu];
       int phi = s.cell_hi[it.l][nu];
       if (phi > plo + L - 1) phi = plo + L - 1;
-      // indices advance by one cell per p (no division inside the loop)
-      int iv = wrap(c + plo * nc, n);    // node of g_nu in cell p
-      int iu = wrap(iv - j * nc, n);     // node of the row function shifted by j
-      int rel = wrap(plo - mlo, L);      // position of p in the row function's support
-      const bool test = mspan < L - 1;
-      for (int p = plo; p <= phi; ++p) {
-        if (!test || rel <= mspan) {  // else the row support is absent in this cell
+      // cells p of g_nu's support where the shifted row function is present: [plo, phi] meets the
+      // row support [mlo, mhi] modulo L.  Unless the row support covers every residue its images
+      // [mlo + kL, mhi + kL] are disjoint, and [plo, phi] (at most L cells) meets at most two of
+      // them, k0 (the first that ends at or after plo) and k0 + 1.  Visited in increasing p.
+      int seg_lo[2] = {plo, 1}, seg_hi[2] = {phi, 0};
+      if (mspan < L - 1) {
+        const int k0 = floor_div(plo - mhi + L - 1, L);
+        seg_lo[0] = max(plo, mlo + k0 * L);
+        seg_hi[0] = min(phi, mhi + k0 * L);
+        seg_lo[1] = max(plo, mlo + (k0 + 1) * L);
+        seg_hi[1] = min(phi, mhi + (k0 + 1) * L);
+      }
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        if (seg_lo[sg] > seg_hi[sg]) continue;
+        // indices advance by one cell per p (no division inside the loop)
+        int iv = wrap(c + seg_lo[sg] * nc, n);  // node of g_nu in cell p
+        int iu = wrap(iv - j * nc, n);          // node of the row function shifted by j
+        for (int p = seg_lo[sg]; p <= seg_hi[sg]; ++p) {
           q += f[iu] * g[iv];
           e += df[iu] * dg[iv];
+          iv += nc;
+          if (iv >= n) iv -= n;
+          iu += nc;
+          if (iu >= n) iu -= n;
         }
-        iv += nc;
-        if (iv >= n) iv -= n;
-        iu += nc;
-        if (iu >= n) iu -= n;
-        if (++rel == L) rel = 0;
       }
     } else {
       // single open cell: nodes c = 0..n-1, Dirichlet ends (the virtual node -1 adds f_0 g_0)
@@ -184,8 +198,32 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
 // significant bits, exact in BF16; products of two digits are exact in FP32 and sums of up to
 // 2^24 / 2^14 of them accumulate exactly.  Digit plane k of a row block goes to
 // planes + k * rows * Kpad + row * Kpad + c (BF16, Kpad >= nv, zero padded).
+//
+// X is formed from the bit fields of x with integer arithmetic only (the FP64 pipe of this GPU
+// runs at a small fraction of the integer rate): |x| = M 2^(ex - 1075) with M the 53-bit
+// significand, so X = M 2^(ex - 1013 - e), a left shift by at most 9 bits (|x| < 2^e) or a right
+// shift rounded to nearest, ties to even.
+__device__ __forceinline__ long long fixed62(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int bex = (int)((u >> 52) & 0x7ff);
+  const unsigned long long M = (u & ((1ull << 52) - 1)) | (bex ? (1ull << 52) : 0ull);
+  const int sh = (bex ? bex : 1) - 1013 - e;
+  unsigned long long X;
+  if (sh >= 0) {
+    X = M << sh;
+  } else if (sh > -64) {
+    const int r = -sh;
+    X = M >> r;
+    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (X & 1ull))) ++X;
+  } else {
+    X = 0;
+  }
+  return (u >> 63) ? -(long long)X : (long long)X;
+}
+
 __device__ __forceinline__ void digits7(double x, int e, int *a) {
-  long long X = __double2ll_rn(scale_pow2(x, 62 - e));  // exact scaling, |X| < 2^62
+  long long X = fixed62(x, e);  // |X| <= 2^62
 #pragma unroll
   for (int k = 0; k < kSlices; ++k) {
     const int sh = 55 - 7 * k;
@@ -199,10 +237,16 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v|
   return (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
-__device__ __forceinline__ int scale_exponent(double mx) {
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  return e;
+// Magnitude key of x: the high word without the sign.  Keys order like |x| up to the low word,
+// and the largest key of a row carries the largest biased exponent.
+__device__ __forceinline__ unsigned mag_key(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+
+// e with max |x| < 2^e over a row from its largest magnitude key: frexp's exponent of the largest
+// element (f 2^e, 1/2 <= f < 1) when it is normal, 0 when every element is below 2^-1022 (those
+// round to zero digits).
+__device__ __forceinline__ int scale_exponent_key(unsigned key) {
+  const int bex = (int)(key >> 20);
+  return bex ? bex - 1022 : 0;
 }
 
 __global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__restrict__ sysv) {
@@ -221,10 +265,10 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__res
   gram_phase1(s, it, Q, E, red);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
-    double mx = 0.0;
-    for (int c = lane; c < nv; c += 32) mx = fmax(mx, fabs(Q[nu * ld + c]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) rexp[nu] = scale_exponent(mx);
+    unsigned mx = 0;
+    for (int c = lane; c < nv; c += 32) mx = max(mx, mag_key(Q[nu * ld + c]));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) rexp[nu] = scale_exponent_key(mx);
   }
   __syncthreads();
   const int64_t rows = (int64_t)D.Jc * m0 * m0;
@@ -232,19 +276,21 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__res
   unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
   int *rowexp = reinterpret_cast<int *>(s.ws + D.offRE);
   if (tid < m0) rowexp[row0 + tid] = rexp[tid];
-  const int items = m0 * Kp;
+  // two adjacent columns per thread (Kp is even): one 32-bit store per digit plane
+  const int half = Kp >> 1;
+  const int items = m0 * half;
   for (int p0 = tid; p0 < items; p0 += kGramThreads) {
-    const int nu = p0 / Kp, c = p0 - nu * Kp;
-    int a[kSlices];
-    if (c < nv) {
-      digits7(Q[nu * ld + c], rexp[nu], a);
-    } else {
+    const int nu = p0 / half, c = 2 * (p0 - nu * half);
+    int a[kSlices], b[kSlices];
 #pragma unroll
-      for (int k = 0; k < kSlices; ++k) a[k] = 0;
-    }
+    for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0;
+    if (c < nv) digits7(Q[nu * ld + c], rexp[nu], a);
+    if (c + 1 < nv) digits7(Q[nu * ld + c + 1], rexp[nu], b);
     const int64_t at = (row0 + nu) * Kp + c;
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) planes[k * rows * Kp + at] = bf16_of_int(a[k]);
+    for (int k = 0; k < kSlices; ++k)
+      *reinterpret_cast<unsigned *>(planes + k * rows * Kp + at) =
+          (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
   }
 }
 
@@ -261,33 +307,33 @@ __global__ void __launch_bounds__(kGramThreads) k_vslice(const SysDev *__restric
   const DirDev &D = s.d[l];
   const int r = b, nv = D.nv, Kp = D.Kpad, Rt = s.Rt;
   const double *v = s.ws + D.offV + (int64_t)r * nv;
-  __shared__ double part[kGramThreads / 32];
+  __shared__ unsigned part[kGramThreads / 32];
   __shared__ int e_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  double mx = 0.0;
-  for (int c = tid; c < nv; c += kGramThreads) mx = fmax(mx, fabs(v[c]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  unsigned mx = 0;
+  for (int c = tid; c < nv; c += kGramThreads) mx = max(mx, mag_key(v[c]));
+  mx = __reduce_max_sync(0xffffffffu, mx);
   if (lane == 0) part[warp] = mx;
   __syncthreads();
   if (tid == 0) {
-    double m = 0.0;
-    for (int w = 0; w < kGramThreads / 32; ++w) m = fmax(m, part[w]);
-    e_sh = scale_exponent(m);
+    unsigned m = 0;
+    for (int w = 0; w < kGramThreads / 32; ++w) m = max(m, part[w]);
+    e_sh = scale_exponent_key(m);
     reinterpret_cast<int *>(s.ws + D.offCE)[r] = e_sh;
   }
   __syncthreads();
   const int e = e_sh;
   unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offB);
-  for (int c = tid; c < Kp; c += kGramThreads) {
-    int a[kSlices];
-    if (c < nv) {
-      digits7(v[c], e, a);
-    } else {
+  for (int c = 2 * tid; c < Kp; c += 2 * kGramThreads) {
+    int a[kSlices], b[kSlices];
 #pragma unroll
-      for (int k = 0; k < kSlices; ++k) a[k] = 0;
-    }
+    for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0;
+    if (c < nv) digits7(v[c], e, a);
+    if (c + 1 < nv) digits7(v[c + 1], e, b);
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) planes[((int64_t)k * Rt + r) * Kp + c] = bf16_of_int(a[k]);
+    for (int k = 0; k < kSlices; ++k)
+      *reinterpret_cast<unsigned *>(planes + ((int64_t)k * Rt + r) * Kp + c) =
+          (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
   }
 }
 

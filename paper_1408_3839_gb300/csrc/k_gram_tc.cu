@@ -9,8 +9,9 @@
 // the splitting of Ozaki et al. ("Error-free transformations of matrix multiplication by using
 // fast routines of matrix multiplication", 2012) with the 28 digit pairs a + b <= 6 kept
 // (relative truncation ~2^-48 of sum |Q| |V|).  Each D_s is an integer below 2^24 for K <= 448, so
-// BF16 x BF16 products accumulated in FP32 are exact; the recombination is exact in 64-bit
-// integers (two partial sums) and rounded once to FP64.
+// BF16 x BF16 products accumulated in FP32 are exact; the recombination runs in 64-bit integers
+// (its one rounding, 2^-53 of the scale, is far below the truncation of the dropped pairs) and is
+// converted to FP64 once.
 //
 // One CTA of 128 threads per (system, direction, 128-row tile, 64-column tile):
 //   * TMA (cp.async.bulk.tensor.2d, 128-byte swizzle, no multicast) brings, per 64-wide K chunk,
@@ -208,16 +209,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
         for (int t = 0; t < 16; ++t) {
           const int n = job.n0 + cc * 16 + t;
           if (n >= P.Rt) continue;
-          // D_s are integers below 2^24 held exactly in FP32: converted to int32 and combined
-          // exactly in 64-bit integers (hi < 2^39, lo < 2^46), converted and scaled exactly, and
-          // rounded once by the final addition
+          // D_s are integers below 2^24 held exactly in FP32: converted to int32 and combined in
+          // 64-bit integers, hi < 2^39 (weights 2^-14 .. 2^-28) and lo < 2^46 (2^-35 .. 2^-56),
+          // then T = hi 2^24 + round(lo / 16) (< 2^63; the rounding, 2^-53 of the scale 2^E, is far
+          // below the 2^-48 truncation of the dropped digit pairs) converted and scaled once
           long long d[kSlices];
 #pragma unroll
           for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2int_rn(__uint_as_float(v[s][t]));
           const long long hi = (d[0] << 14) + (d[1] << 7) + d[2];
           const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
+          const long long T = (hi << 24) + ((lo + 8) >> 4);
           const int E = er + P.colexp[n];
-          Crow[(int64_t)n * mm] = scale_pow2((double)hi, E - 28) + scale_pow2((double)lo, E - 56);
+          Crow[(int64_t)n * mm] = scale_pow2((double)T, E - 52);
         }
       }
     }

@@ -129,60 +129,88 @@ __device__ double gauss_cell_integral(double t, double lo, double hi, double c) 
   return f * (erfc(-B) - erfc(-A));
 }
 
+// Cell integrals by Taylor series about the cell centre.  For a cell of width h centred at
+// distance xc from a Gaussian exp(-t^2 x^2), m = t xc, delta = t h and d = delta / 2:
+//   int_cell exp(-t^2 x^2) dx = exp(-m^2) S(m^2) / t,
+//   S = sum_j a_j H_2j(m) = sum_j b_j y^j,  y = m^2,  a_j = 2 d^(2j+1) / (2j+1)!
+// (the odd terms integrate to zero; H_n are the physicists' Hermite polynomials), and with
+// H_2j(m) = sum_i (2j)! (-1)^(j-i) 4^i / ((j-i)! (2i)!) y^i
+//   b_i = 4^i / (2i)! sum_{l >= 0} (-1)^l 2 d^(2(i+l)+1) / ((2(i+l)+1) l!).
+// The series is cut after degree J, the first j with (22 d)^(2j+2) / (2j+3)! < 1e-18 (|m| <= 11
+// within the reach of a Gaussian).  The b_i depend on t and h only: one set per potential row.
+constexpr double kTaylorMaxDelta = 0.25;
+constexpr int kTaylorMaxJ = 16;
+
+__device__ int taylor_degree(double d) {
+  const double x22 = (22.0 * d) * (22.0 * d);
+  int J = 1;
+  double bound = x22 * x22 * kRecip[0] * kRecip[1] * kRecip[2] * kRecip[3] * kRecip[4];  // j = 1
+  while (bound >= 1e-18 && J < kTaylorMaxJ) {
+    ++J;
+    bound *= x22 * kRecip[2 * J + 1] * kRecip[2 * J + 2];
+  }
+  return J;
+}
+
+__device__ double taylor_coef(int i, int J, double d) {
+  const double d2 = d * d;
+  double dp = 2.0 * d;  // 2 d^(2(i+l)+1), l = 0
+  for (int u = 0; u < i; ++u) dp *= d2;
+  double sum = 0.0, lf = 1.0;  // lf = 1 / l!
+  for (int l = 0; i + l <= J; ++l) {
+    const double term = dp * kRecip[2 * (i + l)] * lf;  // / (2(i+l)+1)
+    sum += (l & 1) ? -term : term;
+    dp *= d2;
+    lf *= kRecip[l];  // 1 / (l+1)!
+  }
+  double f = sum;  // * 4^i / (2i)!
+  for (int u = 1; u <= 2 * i; ++u) f *= kRecip[u - 1];
+  for (int u = 0; u < i; ++u) f *= 4.0;
+  return f;
+}
+
+__device__ __forceinline__ double taylor_S(const double *bc, int J, double y) {
+  double S = bc[J];
+  for (int j = J - 1; j >= 0; --j) S = fma(S, y, bc[j]);
+  return S;
+}
+
 // Wide Gaussians (s = t b <= 0.1) over many images: the image sum is a trapezoidal rule of
-// phi(k) = psi(m0 - k s), psi(m) = exp(-m^2) S(m^2) (the Taylor form above), and the
-// Euler-Maclaurin formula gives it in closed form:
+// phi(k) = psi(m0 - k s), psi(m) = exp(-m^2) S(m^2), and the Euler-Maclaurin formula gives it in
+// closed form:
 //   sum_{k=a..c} w_k phi(k) = (1/s) int_{m_c}^{m_a} psi + sum_{j=1..7} B_2j/(2j)! s^(2j-1)
 //                              (psi^(2j-1)(m_a) - psi^(2j-1)(m_c)) + (w_a - 1/2) phi(a) + (w_c - 1/2) phi(c)
 // with m_a = m0 - a s, m_c = m0 - c s.  The integral is sum_j b_j (G_2j(m_a) - G_2j(m_c)),
-// G_0 = (sqrt(pi)/2) erf, G_2j = (2j-1)/2 G_2j-2 - m^(2j-1) exp(-m^2) / 2; the derivatives are
-// psi^(n) = exp(-m^2) sum_i C(n,i) (-1)^(n-i) H_(n-i)(m) d^i S(m^2)/dm^i (Leibniz, physicists'
-// Hermite polynomials).  The remainder after 7 terms is below 1e-17 of the sum for s <= 0.1
-// (the terms fall like (s / 2 pi)^(2j) sqrt((2j)!)), and S has degree <= 2 kEmJ.
+// G_0 = (sqrt(pi)/2) erf, G_2j = (2j-1)/2 G_2j-2 - m^(2j-1) exp(-m^2) / 2.  The derivatives are
+// psi^(n) = exp(-m^2) P_n(m) with P_0(m) = S(m^2) and P_(n+1) = P_n' - 2 m P_n, so the whole
+// correction is exp(-m^2) C(m) at each end, C = sum_j B_2j/(2j)! s^(2j-1) P_(2j-1): a polynomial
+// of degree <= 2 kEmJ + 2 kEmP - 1 whose coefficients depend on the row (t, h, b) only.  The
+// remainder after 7 terms is below 1e-17 of the sum for s <= 0.1 (the terms fall like
+// (s / 2 pi)^(2j) sqrt((2j)!)), and S has degree <= 2 kEmJ.
 constexpr int kEmJ = 3;
 constexpr int kEmP = 7;
+constexpr int kEmDeg = 2 * kEmJ + 2 * kEmP - 1;
 constexpr double kEmMaxS = 0.1;
 __constant__ double kEmB[kEmP] = {1.0 / 12.0,         -1.0 / 720.0,     1.0 / 30240.0,
                                   -1.0 / 1209600.0,   1.0 / 47900160.0, -691.0 / 1307674368000.0,
                                   1.0 / 74724249600.0};
 
-// exp(m^2) psi^(2j-1)(m) for j = 1..kEmP into out[j], exp(m^2) psi(m) into out[0].
-__device__ void em_endpoint(double m, const double *bc, int J, double *out) {
-  double a[2 * kEmJ + 1];
-#pragma unroll
-  for (int k = 0; k <= 2 * kEmJ; ++k) a[k] = ((k & 1) == 0 && k / 2 <= J) ? bc[k / 2] : 0.0;
-  double Q[2 * kEmJ + 1];  // d^i/dm^i of sum_k a_k m^k
-#pragma unroll
-  for (int i = 0; i <= 2 * kEmJ; ++i) {
-    double acc = 0.0;
-#pragma unroll
-    for (int k = 2 * kEmJ; k >= i; --k) {
-      double fall = 1.0;
-#pragma unroll
-      for (int u = 0; u < i; ++u) fall *= (double)(k - u);
-      acc = fma(acc, m, a[k] * fall);
+// Coefficients of C (C[k] of m^k, k <= kEmDeg) by one warp, lane k holding the coefficient of
+// m^k of P_n (J <= kEmJ).
+__device__ void em_poly_warp(const double *bc, int J, double s, double *C) {
+  const int k = threadIdx.x & 31;
+  double P = ((k & 1) == 0 && k / 2 <= J) ? bc[k / 2] : 0.0;
+  double acc = 0.0, sp = s;  // s^(2j-1)
+  for (int n = 0; n < 2 * kEmP - 1; ++n) {
+    const double up = __shfl_down_sync(0xffffffffu, P, 1);  // coefficient of m^(k+1)
+    const double dn = __shfl_up_sync(0xffffffffu, P, 1);    // coefficient of m^(k-1)
+    P = (double)(k + 1) * (k < 31 ? up : 0.0) - 2.0 * (k > 0 ? dn : 0.0);
+    if (((n + 1) & 1) != 0) {
+      acc = fma(kEmB[n / 2] * sp, P, acc);  // j = (n + 2) / 2
+      sp *= s * s;
     }
-    Q[i] = acc;
   }
-  double H[2 * kEmP];
-  H[0] = 1.0;
-  H[1] = 2.0 * m;
-#pragma unroll
-  for (int k = 1; k + 1 < 2 * kEmP; ++k) H[k + 1] = 2.0 * m * H[k] - 2.0 * k * H[k - 1];
-  out[0] = Q[0];
-#pragma unroll
-  for (int j = 1; j <= kEmP; ++j) {
-    const int n = 2 * j - 1;
-    double acc = 0.0;
-    double binom = 1.0;  // C(n, i)
-#pragma unroll
-    for (int i = 0; i <= 2 * kEmJ && i <= n; ++i) {
-      const double term = binom * H[n - i] * Q[i];
-      acc += ((n - i) & 1) ? -term : term;
-      binom = binom * (double)(n - i) / (double)(i + 1);
-    }
-    out[j] = acc;
-  }
+  if (k <= kEmDeg) C[k] = acc;
 }
 
 // (sqrt(pi)/2) (erf(x) - erf(y)) for x >= y, without cancellation when both are far out on one
@@ -194,8 +222,8 @@ __device__ double half_sqrtpi_erf_diff(double x, double y) {
   return f * (erf(x) - erf(y));
 }
 
-__device__ double image_sum_em(double t, double xc, double b, const double *bc, int J, int klo, int khi,
-                               int kmax, bool even) {
+__device__ double image_sum_em(double t, double xc, double b, const double *bc, int J, const double *C,
+                               int klo, int khi, int kmax, bool even) {
   const double s = t * b, m0 = t * xc;
   const double ma = m0 - klo * s, mc = m0 - khi * s;
   const double ea = exp(-ma * ma), ec = exp(-mc * mc);
@@ -213,71 +241,30 @@ __device__ double image_sum_em(double t, double xc, double b, const double *bc, 
     pc *= mc * mc;
   }
   integ /= s;
-  double oa[kEmP + 1], oc[kEmP + 1];
-  em_endpoint(ma, bc, J, oa);
-  em_endpoint(mc, bc, J, oc);
-  double corr = 0.0, sp = s;
+  double ca = C[kEmDeg], cc = C[kEmDeg];
 #pragma unroll
-  for (int j = 1; j <= kEmP; ++j) {
-    corr = fma(kEmB[j - 1] * sp, ea * oa[j] - ec * oc[j], corr);
-    sp *= s * s;
+  for (int k = kEmDeg - 1; k >= 0; --k) {
+    ca = fma(ca, ma, C[k]);
+    cc = fma(cc, mc, C[k]);
   }
   const double wa = (even && (klo == kmax || klo == -kmax)) ? 0.5 : 1.0;
   const double wc = (even && (khi == kmax || khi == -kmax)) ? 0.5 : 1.0;
-  return integ + corr + (wa - 0.5) * ea * oa[0] + (wc - 0.5) * ec * oc[0];
+  return integ + (ea * ca - ec * cc) + (wa - 0.5) * ea * taylor_S(bc, J, ma * ma) +
+         (wc - 0.5) * ec * taylor_S(bc, J, mc * mc);
 }
 
-// Sum over the images k = klo .. khi (weight 1/2 on k = +-kmax when the window is even) of the
-// cell integrals int_{cell} exp(-t^2 (x - c0 - k b)^2) dx, times t, for a cell of width h
-// centred at c0 + xc (xc = cell midpoint - c0), delta = t h.  With m_k = t (xc - k b) and
-// d = delta / 2 the integral is exp(-m_k^2) S(m_k^2) / t, where
-//   S = sum_j a_j H_2j(m) = sum_j b_j y^j,  y = m^2,  a_j = 2 d^(2j+1) / (2j+1)!
-// (Taylor series of the Gaussian about the cell centre, the odd terms integrating to zero), and
-// H_2j(m) = sum_i (2j)! (-1)^(j-i) 4^i / ((j-i)! (2i)!) y^i, so that
-//   b_i = 4^i / (2i)! sum_{l >= 0} (-1)^l 2 d^(2(i+l)+1) / ((2(i+l)+1) l!).
-// The series is cut after degree J, the first j with (22 d)^(2j+2) / (2j+3)! < 1e-18 (|m| <= 11
-// within the image reach).  exp(-m_k^2) follows the images by exp(-m_{k+-1}^2) =
-// exp(-m_k^2) R, R = exp(-+2 m_k s - s^2), s = t b, R <- R exp(-2 s^2), walking outward from the
-// image nearest to the cell and restarted from exp every 8 images, so that the dominant terms
-// come from small exponents and the product's rounding stays within a few tens of ulp.
-constexpr double kTaylorMaxDelta = 0.25;
-constexpr int kTaylorMaxJ = 16;
-
-__device__ double image_sum_taylor(double t, double xc, double b, double delta, int klo, int khi,
+// Sum over the images k = klo .. khi (weight 1/2 on k = +-kmax when the window is even) of
+// t int_{cell} exp(-t^2 (x - c0 - k b)^2) dx for a narrow cell (delta <= kTaylorMaxDelta) centred
+// at c0 + xc: sum_k w_k exp(-m_k^2) S(m_k^2), m_k = t (xc - k b).  exp(-m_k^2) follows the images
+// by exp(-m_{k+-1}^2) = exp(-m_k^2) R, R = exp(-+2 m_k s - s^2), s = t b, R <- R exp(-2 s^2),
+// walking outward from the image nearest to the cell and restarted from exp every 8 images, so
+// that the dominant terms come from small exponents and the product's rounding stays within a
+// few tens of ulp.
+__device__ double image_sum_taylor(double t, double xc, double b, const double *bc, int J, int klo, int khi,
                                    int kmax, bool even) {
-  const double d = 0.5 * delta;
-  const double x22 = (22.0 * d) * (22.0 * d);
-  int J = 1;
-  {
-    double bound = x22 * x22 * kRecip[0] * kRecip[1] * kRecip[2] * kRecip[3] * kRecip[4];  // j = 1
-    while (bound >= 1e-18 && J < kTaylorMaxJ) {
-      ++J;
-      bound *= x22 * kRecip[2 * J + 1] * kRecip[2 * J + 2];
-    }
-  }
-  // coefficients b_0 .. b_J
-  double bc[kTaylorMaxJ + 1];
-  const double d2 = d * d;
-  for (int i = 0; i <= J; ++i) {
-    double dp = 2.0 * d;  // 2 d^(2(i+l)+1), l = 0
-    for (int u = 0; u < i; ++u) dp *= d2;
-    double sum = 0.0, lf = 1.0;  // lf = 1 / l!
-    for (int l = 0; i + l <= J; ++l) {
-      const double term = dp * kRecip[2 * (i + l)] * lf;  // / (2(i+l)+1)
-      sum += (l & 1) ? -term : term;
-      dp *= d2;
-      lf *= kRecip[l];  // 1 / (l+1)!
-    }
-    double f = sum;  // * 4^i / (2i)!
-    for (int u = 1; u <= 2 * i; ++u) f *= kRecip[u - 1];
-    for (int u = 0; u < i; ++u) f *= 4.0;
-    bc[i] = f;
-  }
-  const double sb = t * b;
-  if (sb <= kEmMaxS && J <= kEmJ && khi - klo >= 16)
-    return image_sum_em(t, xc, b, bc, J, klo, khi, kmax, even);
-  const double Q = exp(-2.0 * sb * sb);
   if (klo > khi) return 0.0;  // no image within reach
+  const double sb = t * b;
+  const double Q = exp(-2.0 * sb * sb);
   // the image nearest to the cell, clamped to the window
   int kc = (int)rint(xc / b);
   kc = kc < klo ? klo : (kc > khi ? khi : kc);
@@ -293,9 +280,7 @@ __device__ double image_sum_taylor(double t, double xc, double b, double delta, 
       const int steps = dir > 0 ? min(8, kend - k0) : min(8, k0 - kend);
       for (int u = 0; u < steps; ++u) {
         const int k = k0 + dir * u;
-        const double y = m * m;
-        double S = bc[J];
-        for (int j = J - 1; j >= 0; --j) S = fma(S, y, bc[j]);
+        const double S = taylor_S(bc, J, m * m);
         const double w = (even && (k == kmax || k == -kmax)) ? 0.5 * e : e;
         v = fma(w, S, v);
         e *= R;
@@ -315,78 +300,108 @@ __device__ double image_sum_taylor(double t, double xc, double b, double delta, 
 //     = sqrt(pi) / (t b) [h + sum_{n>=1} exp(-pi^2 n^2 / s^2) (2 b / (pi n)) cos(2 pi n (x_m - c0) / b)
 //                             sin(pi n h / b)],   s = t b, x_m the cell midpoint,
 // cut after the first n with exp(-pi^2 n^2 / s^2) below 1e-20 (n > 2.16 s): a few terms where
-// the direct sum would take ~20 / s images.
+// the direct sum would take ~20 / s images.  The weights of the cosines depend on the row only;
+// cos(n theta) follows from cos(theta) by the Chebyshev recurrence (terms n >= 2 carry weights
+// below exp(-4 pi^2 / s^2) < 3e-8, far below the recurrence's rounding growth).
 constexpr double kPoissonMaxS = 1.5;
+constexpr int kPoissonMaxN = 5;  // ceil(2.16 s) + 1 for s < 1.5
 constexpr double kPi = 3.14159265358979323846;
 
-__device__ double image_sum_poisson(double t, double lo, double hi, double c0, double b) {
-  const double s = t * b, h = hi - lo, xm = 0.5 * (lo + hi);
-  const int N = (int)ceil(2.16 * s) + 1;
-  double acc = h;
+__device__ double poisson_weight(int n, double s, double h, double b) {
+  const double g = exp(-(kPi * n / s) * (kPi * n / s));
+  if (g == 0.0) return 0.0;
+  return g * (2.0 * b / (kPi * n)) * sinpi(n * h / b);
+}
+
+__device__ double image_sum_poisson(double t, double lo, double hi, double c0, double b, const double *pw, int N) {
+  const double h = hi - lo, xm = 0.5 * (lo + hi);
+  const double c1 = cospi(2.0 * (xm - c0) / b);
+  double acc = h, cm = 1.0, cn = c1;  // cos((n-1) theta), cos(n theta)
   for (int n = 1; n <= N; ++n) {
-    const double g = exp(-(kPi * n / s) * (kPi * n / s));
-    if (g == 0.0) break;
-    const double cs = cospi(2.0 * n * (xm - c0) / b);
-    const double sn = sinpi(n * h / b);
-    acc = fma(g * (2.0 * b / (kPi * n)) * cs, sn, acc);
+    acc = fma(pw[n], cn, acc);
+    const double nx = 2.0 * c1 * cn - cm;
+    cm = cn;
+    cn = nx;
   }
   return 1.7724538509055160273 / (t * b) * acc;  // sqrt(pi) / (t b)
 }
 
-__global__ void __launch_bounds__(256) k_potential(const SysDev *__restrict__ sysv) {
+// One CTA per (system, direction, rank term r = (nucleus nu, sinc node q)): the row constants
+// (series coefficients, Euler-Maclaurin polynomial, Poisson weights) in shared memory, then a
+// thread per cell i of the row.  Cells farther than 10 / t from every image within the window
+// get exactly zero (their integrals are below exp(-100) of the nearest image's).
+constexpr int kPotThreads = 128;
+
+__global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
-  int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int Rt = s.Rt;
-  int l = 0;
-  for (; l < 3; ++l) {
-    int64_t cnt = (int64_t)Rt * s.d[l].nv;
-    if (item < cnt) break;
-    item -= cnt;
-  }
-  if (l == 3) return;
+  if ((int)blockIdx.x >= 3 * Rt) return;
+  const int l = blockIdx.x / Rt, r = blockIdx.x - l * Rt;
   const DirDev &D = s.d[l];
-  const int r = (int)(item / D.nv);
-  const int i = (int)(item - (int64_t)r * D.nv);
   const int nu = r / s.R, q = r - nu * s.R;
   const double t = s.t[q];
   const double c0 = s.a[nu][l];
-  double v = 0.0;
-  // images farther than 10/t from the cell contribute below exp(-100) of the nearest one
   const double reach = 10.0 / t;
-  if (D.periodic) {
-    const double lo = D.cell0 + i * D.h, hi = lo + D.h;
-    const int kmax = D.K / 2;
-    const bool even = (D.K % 2) == 0;
-    double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
-    int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
-    int khi = (khi_f > kmax) ? kmax : (int)khi_f;
-    const double delta = t * D.h;
-    const double sb = t * D.b;
-    if (sb < kPoissonMaxS && klo > -kmax && khi < kmax) {
-      v = image_sum_poisson(t, lo, hi, c0, D.b);
-    } else if (delta <= kTaylorMaxDelta) {
-      v = image_sum_taylor(t, 0.5 * (lo + hi) - c0, D.b, delta, klo, khi, kmax, even) / t;
+  const double delta = t * D.h, sb = t * D.b;
+  const bool taylor = delta <= kTaylorMaxDelta;
+  const int J = taylor ? taylor_degree(0.5 * delta) : 0;
+  const bool em_row = D.periodic && taylor && sb <= kEmMaxS && J <= kEmJ;
+  const bool poisson_row = D.periodic && sb < kPoissonMaxS;
+  const int NP = poisson_row ? min((int)ceil(2.16 * sb) + 1, kPoissonMaxN) : 0;
+  __shared__ double bc[kTaylorMaxJ + 1];
+  __shared__ double emc[kEmDeg + 1];
+  __shared__ double pw[kPoissonMaxN + 1];
+  const int tid = threadIdx.x;
+  if (taylor && tid <= J) bc[tid] = taylor_coef(tid, J, 0.5 * delta);
+  if (tid >= 32 && tid - 32 < NP) pw[tid - 31] = poisson_weight(tid - 31, sb, D.h, D.b);
+  __syncthreads();
+  if (em_row && tid < 32) em_poly_warp(bc, J, sb, emc);
+  __syncthreads();
+
+  double *out = s.ws + D.offV + (int64_t)r * D.nv;
+  for (int i = tid; i < D.nv; i += kPotThreads) {
+    double v = 0.0;
+    if (D.periodic) {
+      const double lo = D.cell0 + i * D.h, hi = lo + D.h;
+      const int kmax = D.K / 2;
+      const bool even = (D.K % 2) == 0;
+      const double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
+      const int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
+      const int khi = (khi_f > kmax) ? kmax : (int)khi_f;
+      const double xc = 0.5 * (lo + hi) - c0;
+      if (poisson_row && klo > -kmax && khi < kmax) {
+        v = image_sum_poisson(t, lo, hi, c0, D.b, pw, NP);
+      } else if (em_row && khi - klo >= 16) {
+        v = image_sum_em(t, xc, D.b, bc, J, emc, klo, khi, kmax, even) / t;
+      } else if (taylor) {
+        v = image_sum_taylor(t, xc, D.b, bc, J, klo, khi, kmax, even) / t;
+      } else {
+        for (int k = klo; k <= khi; ++k) {
+          const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
+          v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+        }
+      }
     } else {
-      for (int k = klo; k <= khi; ++k) {
-        const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
-        v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+      const double lo = D.x0 + i * D.h, hi = lo + D.h;
+      if (D.lattice) {
+        const double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
+        const int klo = (klo_f < 0.0) ? 0 : (int)klo_f;
+        const int khi = (khi_f > D.L - 1) ? D.L - 1 : (int)khi_f;
+        for (int k = klo; k <= khi; ++k) {
+          const double wk = s.zcell ? s.zcell[k * s.M0 + nu] / s.Z[nu] : 1.0;
+          v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+        }
+      } else if (lo - reach <= c0 && c0 <= hi + reach) {
+        if (taylor) {
+          const double m = t * (0.5 * (lo + hi) - c0), y = m * m;
+          v = exp(-y) * taylor_S(bc, J, y) / t;
+        } else {
+          v = gauss_cell_integral(t, lo, hi, c0);
+        }
       }
     }
-  } else {
-    const double lo = D.x0 + i * D.h, hi = lo + D.h;
-    if (D.lattice) {
-      double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
-      int klo = (klo_f < 0.0) ? 0 : (int)klo_f;
-      int khi = (khi_f > D.L - 1) ? D.L - 1 : (int)khi_f;
-      for (int k = klo; k <= khi; ++k) {
-        const double wk = s.zcell ? s.zcell[k * s.M0 + nu] / s.Z[nu] : 1.0;
-        v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
-      }
-    } else {
-      v = gauss_cell_integral(t, lo, hi, c0);
-    }
+    out[i] = v;
   }
-  s.ws[D.offV + (int64_t)r * D.nv + i] = v;
 }
 
 }  // namespace
@@ -398,10 +413,10 @@ cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_potential(const SysDev *sys, int nsys, int max_items, cudaStream_t st) {
-  if (max_items <= 0 || nsys <= 0) return cudaSuccess;
-  dim3 grid((max_items + 255) / 256, nsys);
-  k_potential<<<grid, 256, 0, st>>>(sys);
+cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st) {
+  if (max_rows <= 0 || nsys <= 0) return cudaSuccess;
+  dim3 grid(max_rows, nsys);
+  k_potential<<<grid, kPotThreads, 0, st>>>(sys);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ struct Plan {
   size_t s0_off = 0;   // offset of s0 [m0]
   bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
-  int basis_items = 0, pot_items = 0, gram_blocks = 0, rank_items = 0;
+  int basis_items = 0, pot_rows = 0, gram_blocks = 0, rank_items = 0;
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
@@ -306,7 +306,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     for (int q = 0; q < s.R; ++q) sd.c[nu * s.R + q] = s.Z[nu] * w[q];
 
   size_t off = 0;
-  P.basis_items = P.pot_items = P.gram_blocks = 0;
+  P.basis_items = P.pot_rows = P.gram_blocks = 0;
   P.nv_max = 0;
   sd.nwin = 1;
   sd.nblocks = 1;
@@ -406,7 +406,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
     P.basis_items += m0 * (D.n + D.gext);
-    P.pot_items += Rt * D.nv;
+    P.pot_rows += Rt;  // one CTA per (direction, rank term) row
     P.gram_blocks += D.Jc * m0;
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
@@ -622,7 +622,7 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   c->end();
   if (st != LHF_OK) return st;
   c->begin(1);
-  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
+  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
   c->end();
   if (st != LHF_OK) return st;
   st = run_gram(c, ps);
@@ -662,7 +662,7 @@ lhf_status run_box_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
   c->end();
   if (st != LHF_OK) return st;
   c->begin(1);
-  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_items), c->stream), "potential kernel");
+  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
   c->end();
   if (st != LHF_OK) return st;
   c->begin(2);
@@ -1301,7 +1301,7 @@ lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
   if (st != LHF_OK) return st;
   st = upload_zcell(c, ps);
   if (st != LHF_OK) return st;
-  st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
+  st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_rows, c->stream), "potential kernel");
   if (st != LHF_OK) return st;
   const DirDev &D = ps[0].sd.d[l];
   return c->cuda(cudaMemcpyAsync(V, c->ws + D.offV, sizeof(double) * (size_t)ps[0].sd.Rt * D.nv,
@@ -1336,7 +1336,7 @@ lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, in
   } else {
     st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
     if (st != LHF_OK) return st;
-    st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_items, c->stream), "potential kernel");
+    st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_rows, c->stream), "potential kernel");
     if (st != LHF_OK) return st;
     st = run_gram(c, ps);
     if (st != LHF_OK) return st;

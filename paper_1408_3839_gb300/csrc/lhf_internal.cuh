@@ -113,7 +113,8 @@ enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
 
 // ---- kernel launchers (each returns the launch error) ------------------------------------
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
-cudaError_t launch_potential(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+// One CTA per (direction, rank term) row: max_rows = 3 R_tot over the batch.
+cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
                              int max_nv, cudaStream_t st);
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
