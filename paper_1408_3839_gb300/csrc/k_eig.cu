@@ -40,6 +40,21 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) {
   return make_double2(a.x - b.x, a.y - b.y);
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc + a b and acc - a conj(b) as four FMAs each
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 cfms_conj(double2 a, double2 b, double2 acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.y, b.x, acc.y);
+  acc.y = fma(a.x, b.y, acc.y);
+  return acc;
+}
 
 // per warp: A, B, V (m^2 complex each), rotation table (16 x {c, sr, si, p, q}), kept index
 // map, scales and overlap eigenvalues (32 each), the (k1 < k2) pair-block table (120 x 2) and the
@@ -205,9 +220,13 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
       }
       continue;
     }
-    const double nrm = sqrt(sig), ax0 = hypot(x0.x, x0.y);
-    const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-    const double tau = 1.0 / (sig + nrm * ax0);
+    // |x| and |x0| from reciprocal square roots (the scaled entries are far inside the FP64
+    // range), e^{i arg x0} = x0 / |x0|
+    const double nrm = sig * rsqrt(sig);
+    const double a2 = fma(x0.x, x0.x, x0.y * x0.y);
+    const double ra = a2 > 0.0 ? rsqrt(a2) : 0.0, ax0 = a2 * ra;
+    const double2 ph = a2 > 0.0 ? make_double2(x0.x * ra, x0.y * ra) : make_double2(1.0, 0.0);
+    const double tau = 1.0 / fma(nrm, ax0, sig);
     if (lane < n) vec[lane] = lane == 0 ? make_double2(x0.x + ph.x * nrm, x0.y + ph.y * nrm) : xi;
     __syncwarp();
     // p = tau B v, B = A[k+1:, k+1:] from its lower triangle, two lanes per row
@@ -220,9 +239,7 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
         for (int j = lane & 1; j < n; j += 2) {
           double2 b = j <= r ? Bt[r * m + j] : Bt[j * m + r];
           if (j > r) b.y = -b.y;
-          const double2 v = vec[j];
-          pi.x += b.x * v.x - b.y * v.y;
-          pi.y += b.x * v.y + b.y * v.x;
+          pi = cfma(b, vec[j], pi);
         }
       }
       pi.x += __shfl_xor_sync(0xffffffffu, pi.x, 1);
@@ -247,8 +264,7 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
       const int j = t - i * (i + 1) / 2;
       const double2 vi = vec[i], wi = wv[i], vj = vec[j], wj = wv[j];
       double2 &a = A[(k + 1 + i) * m + (k + 1 + j)];
-      a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
-      a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+      a = cfms_conj(wi, vj, cfms_conj(vi, wj, a));
     }
     if (lane == 0) {
       td[k] = akk;
@@ -455,11 +471,14 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       chol = false;
       break;
     }
-    const double ljj = sqrt(d), inv = 1.0 / ljj;
+    const double inv = rsqrt(d), ljj = d * inv;  // 1 / L_jj and L_jj
     __syncwarp();
     for (int i = j + 1 + lane; i < m; i += 32) B[i * m + j] = cscale(B[i * m + j], inv);
     __syncwarp();
-    if (lane == 0) B[j * m + j] = make_double2(ljj, 0.0);
+    if (lane == 0) {
+      B[j * m + j] = make_double2(ljj, 0.0);
+      sg[j] = inv;
+    }
     // B[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i < m: the n (n + 1) / 2 entries of the
     // trailing lower triangle, n = m - j - 1, row by row
     const int n = m - j - 1;
@@ -469,7 +488,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       while (i * (i + 1) / 2 > t) --i;
       const int k = t - i * (i + 1) / 2;
       const int ri = j + 1 + i, rk = j + 1 + k;
-      B[ri * m + rk] = csub(B[ri * m + rk], cmulc(B[ri * m + j], B[rk * m + j]));
+      B[ri * m + rk] = cfms_conj(B[ri * m + j], B[rk * m + j], B[ri * m + rk]);
     }
     __syncwarp();
   }
@@ -485,8 +504,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       const int i = e / m, j = e - (e / m) * m;
       V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
     }
-    for (int i = lane; i < m; i += 32) sg[i] = 1.0 / B[i * m + i].x;  // 1 / L_ii
-    __syncwarp();
+    __syncwarp();  // sg[i] = 1 / L_ii from the factorisation
     for (int pass = 0; pass < 2; ++pass) {
       // forward substitution per column; with 16 columns or fewer two lanes share a column
       // (even and odd k of each inner sum, combined by a shuffle)
@@ -501,11 +519,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
         for (int i = 0; i < m; ++i) {
           double2 acc = make_double2(0.0, 0.0);
           if (act)
-            for (int k = part; k < i; k += q) {
-              const double2 t = cmul(B[i * m + k], z[k]);
-              acc.x += t.x;
-              acc.y += t.y;
-            }
+            for (int k = part; k < i; k += q) acc = cfma(B[i * m + k], z[k], acc);
           if (q == 2) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
