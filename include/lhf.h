@@ -165,7 +165,8 @@ lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, dou
  * Re Sbar_ii, function i is removed at kappa when Re Sbar_ii(kappa) <= LHF_DROP_TOL s0_i (at
  * 1e-6 its scaled overlap row is still good to ~2e-10, far below LHF_LINDEP_TOL); the remaining
  * pencil is diagonally scaled, reduced (Cholesky), brought to real tridiagonal form by
- * Householder reflections and solved by the implicit QR iteration; removed slots hold
+ * Householder reflections, and each eigenvalue of the tridiagonal matrix is isolated by Sturm
+ * bisection and refined by Newton's iteration on its characteristic polynomial; removed slots hold
  * +INFINITY (sorted last).  k_status: device [n_kpoints] (may be NULL): the number of removed
  * functions (>= 0), or LHF_ERR_NOT_SPD when the reduced overlap is not positive definite (the
  * eigenvalues of such a k-point are NaN). */
@@ -237,9 +238,11 @@ lhf_status lhf_set_profiling(lhf_ctx *ctx, int enable);
 lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
 
 /* Work counters of the k-point eigensolver since the previous call (synchronising; host
- * outputs): total QR rotations of the tridiagonal eigenvalue stage and number of matrices solved
- * (one per conjugate pair of k-points).  Reset by the call. */
-lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *rotations, unsigned long long *matrices);
+ * outputs): total FP64 characteristic-polynomial passes of the tridiagonal eigenvalue stage (one
+ * pass: the order-m recurrence for the leading minors and their derivatives at one point; k-points
+ * solved by Jacobi instead add their sweeps) and number of matrices solved (one per conjugate pair
+ * of k-points).  Reset by the call. */
+lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned long long *matrices);
 
 /* Allocation-free variant of lhf_k_point_eigensolve (the paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory -- code inside CUDA stream capture,

@@ -283,58 +283,6 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
   __syncwarp();
 }
 
-// Eigenvalues of the symmetric tridiagonal matrix (d[0..n), e[0..n-1)) by the implicit QR
-// iteration with Wilkinson shifts (one thread; d and e are overwritten, the eigenvalues are
-// left unsorted in d).  A block [l, h] is split where |e_i| <= eps (|d_i| + |d_i+1|); each sweep
-// chases the bulge of the rotation chosen from the shifted first column.  Returns the number of
-// rotations, or -1 if some eigenvalue did not converge within 30 n sweeps.
-__device__ int tridiag_qr(double *d, double *e, int n) {
-  const double eps = 2.220446049250313e-16;
-  int rot = 0, sweeps = 0;
-  int h = n - 1;
-  while (h > 0) {
-    if (fabs(e[h - 1]) <= eps * (fabs(d[h - 1]) + fabs(d[h]))) {
-      e[h - 1] = 0.0;
-      --h;
-      continue;
-    }
-    if (++sweeps > 30 * n) return -1;
-    int l = h - 1;
-    while (l > 0 && fabs(e[l - 1]) > eps * (fabs(d[l - 1]) + fabs(d[l]))) --l;
-    // Wilkinson shift from the trailing 2 x 2 block
-    const double dd = 0.5 * (d[h - 1] - d[h]), bb = e[h - 1];
-    const double r0 = hypot(dd, bb);
-    const double mu = d[h] - bb * bb / (dd + (dd >= 0.0 ? r0 : -r0));
-    double x = d[l] - mu, z = e[l], bulge = 0.0;
-    for (int k = l; k < h; ++k) {
-      // Givens rotation from one reciprocal square root (|x|, |z| stay far inside the FP64 range:
-      // they are entries of the scaled reduced matrix)
-      const double r2 = fma(x, x, z * z);
-      double c = 1.0, sn = 0.0, r = 0.0;
-      if (r2 > 0.0) {
-        const double ri = rsqrt(r2);
-        c = x * ri;
-        sn = -z * ri;
-        r = r2 * ri;
-      }
-      if (k > l) e[k - 1] = r;
-      const double ak = d[k], ak1 = d[k + 1], bk = e[k];
-      const double cc = c * c, ss = sn * sn, cs = c * sn;
-      d[k] = cc * ak - 2.0 * cs * bk + ss * ak1;
-      d[k + 1] = ss * ak + 2.0 * cs * bk + cc * ak1;
-      e[k] = cs * (ak - ak1) + (cc - ss) * bk;
-      if (k + 1 < h) {
-        bulge = -sn * e[k + 1];
-        e[k + 1] = c * e[k + 1];
-        x = e[k];
-        z = bulge;
-      }
-      ++rot;
-    }
-  }
-  return rot;
-}
-
 // Hermitian part of a matrix that is Hermitian up to rounding.
 __device__ void hermitian_part(double2 *A, int m, int lane) {
   for (int e = lane; e < m * m; e += 32) {
@@ -690,48 +638,246 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   }
 }
 
-// Eigenvalues of the tridiagonal matrices left by k_eig: one thread per solved k-point; sorted
-// ascending and written to the k-point and its conjugate partner, removed slots +inf.
-__global__ void __launch_bounds__(32) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
-                                                     unsigned long long *counters) {
-  const SysDev &s = sysv[blockIdx.y];
-  if (s.box || !s.tri) return;
-  const int widx = blockIdx.x * blockDim.x + threadIdx.x;
-  int kap;
-  if (s.klist) {
-    if (widx >= s.nkhalf) return;
-    kap = s.klist[widx];
-  } else {
-    return;
+// Eigenvalues of the real symmetric tridiagonal matrices left by k_eig (diagonal d, off-diagonal
+// e, order m): G lanes per matrix, lane i finds the i-th smallest eigenvalue, so that the results
+// come out sorted and every lane runs the same short recurrence (a one-thread QR iteration per
+// matrix is a long serial chain that leaves the GPU idle).
+//   * Scaling: T / 2^s with 2^s >= max(|d|, |e|) (exact); the eigenvalues lie in the Gershgorin
+//     interval [lo, hi] of the scaled matrix, |lo|, |hi| <= 3 + 2^-20.
+//   * Sturm counts: the number of eigenvalues below x is the number of negative pivots of
+//     T - x I = L D L^T, r_0 = d_0 - x, r_j = (d_j - x) - e_(j-1)^2 / r_(j-1) (Sylvester's law of
+//     inertia).  In FP32 the computed count is the exact count of a matrix within
+//     eta ~ 6 eps_32 max|T| < 2^-19 of T (rounding of the recurrence as backward perturbations
+//     of the entries), so count32(y) lies between #(lambda < y - eta) and #(lambda < y + eta).
+//   * FP32 bisection: 24 halvings of [lo, hi] give [a, b] with count32(a) <= i < count32(b);
+//     with delta = 2^-17 > eta, count32(a - 2 delta) = i and count32(b + 2 delta) = i + 1 prove
+//     that [A, B] = [a - delta, b + delta] holds lambda_i alone, at least delta - eta from either
+//     end, and that det(T - x I) has the sign (-1)^i at A.
+//   * FP64 Newton's iteration on q_m(x) = det(T - x I) from the leading-minor recurrence
+//     q_j = (d_j - x) q_(j-1) - e_(j-1)^2 q_(j-2) and its derivative, kept inside the bracket
+//     (bisecting when a step leaves it), stopped once a step is below 2^-40 (with the other
+//     eigenvalues at least delta - eta away, the quadratic error of the last step is far below
+//     the rounding of q_m).
+//   * Otherwise (a cluster closer than 2 delta, or no convergence in 12 steps) bisection on FP64
+//     minor counts until lambda_i is alone in the bracket (then Newton again) or the bracket is
+//     two adjacent doubles.
+// counters[0] accumulates the FP64 recurrence passes (one pass: m steps).
+constexpr int kTriThreads = 128;
+constexpr int kTriMax = kMaxM0;
+
+// q_m(x) = det(T - x I) and its derivative (dn, e2: scaled diagonal and squared off-diagonal,
+// |entries| <= 1, |x| <= 4: no overflow; the minors are rescaled by 2^400 every fourth step when
+// they have fallen below 2^-400, which leaves the ratio q / q' and the signs unchanged).
+__device__ __forceinline__ void tri_det(const double *dn, const double *e2, int m, double x, double &q_out,
+                                        double &dq_out) {
+  double qm1 = 1.0, q = dn[0] - x, dqm1 = 0.0, dq = -1.0;
+  for (int j = 1; j < m; ++j) {
+    const double t = dn[j] - x, b = e2[j - 1];
+    const double qn = fma(t, q, -b * qm1);
+    const double dqn = fma(t, dq, fma(-b, dqm1, -q));
+    qm1 = q;
+    q = qn;
+    dqm1 = dq;
+    dq = dqn;
+    if ((j & 3) == 3 && fabs(q) < 0x1p-400) {
+      q *= 0x1p400;
+      qm1 *= 0x1p400;
+      dq *= 0x1p400;
+      dqm1 *= 0x1p400;
+    }
   }
+  q_out = q;
+  dq_out = dq;
+}
+
+// Eigenvalues below x from the signs of the FP64 leading minors (an exact zero minor takes the
+// sign opposite to its predecessor; a minor below 2^-400 is rescaled with its predecessor by
+// 2^400).  Signs and the range test read the bit patterns (integer operations).
+__device__ int tri_count64(const double *dn, const double *e2, int m, double x) {
+  double qm1 = 1.0, q = dn[0] - x;
+  if (q == 0.0) q = -1e-290;
+  int neg = __double_as_longlong(q) < 0 ? 1 : 0;
+  int c = neg;
+  for (int j = 1; j < m; ++j) {
+    double qn = fma(dn[j] - x, q, -e2[j - 1] * qm1);
+    if (((__double_as_longlong(qn) >> 52) & 0x7ff) < 1023 - 400) {  // |qn| < 2^-400
+      if (qn == 0.0) {
+        qn = neg ? 1e-290 : -1e-290;
+      } else {
+        qn *= 0x1p400;
+        q *= 0x1p400;
+      }
+    }
+    const int nn = __double_as_longlong(qn) < 0 ? 1 : 0;
+    c += nn ^ neg;
+    neg = nn;
+    qm1 = q;
+    q = qn;
+  }
+  return c;
+}
+
+// Newton's iteration on q_m inside [A, B], which holds lambda_i alone (sign of q_m at A:
+// (-1)^i), from x0; bisects when a step leaves the bracket.  True with *x once a step is below
+// tol (or q_m vanishes), false after 12 steps.  The error after a step dx is about
+// |q''/(2 q')| dx^2 ~ dx^2 / gap: tol = 2^-40 needs a gap of at least ~2^-18 to the other
+// eigenvalues, tol = 2^-50 serves any gap.
+__device__ bool tri_newton(const double *dn, const double *e2, int m, int i, double A, double B, double x0,
+                           double tol, double *x, int *passes) {
+  const bool negA = (i & 1) != 0;
+  double xc = x0;
+  for (int it = 0; it < 12; ++it) {
+    double q, dq;
+    tri_det(dn, e2, m, xc, q, dq);
+    ++*passes;
+    if (q == 0.0) {
+      *x = xc;
+      return true;
+    }
+    if ((q < 0.0) == negA)
+      A = xc;
+    else
+      B = xc;
+    const double dx = dq != 0.0 ? q / dq : INFINITY;
+    const double xn = xc - dx;
+    if (fabs(dx) <= tol) {
+      *x = fmin(fmax(xn, A), B);
+      return true;
+    }
+    xc = (xn > A && xn < B) ? xn : 0.5 * (A + B);
+  }
+  return false;
+}
+
+// Negative pivots of the FP32 L D L^T factorisation of T - x I (an exact zero pivot is taken as
+// a tiny negative one).
+__device__ int tri_count32(const float *df, const float *e2f, int m, float x) {
+  float r = df[0] - x;
+  if (r == 0.0f) r = -1e-30f;
+  int c = r < 0.0f ? 1 : 0;
+  for (int j = 1; j < m; ++j) {
+    r = (df[j] - x) - __fdividef(e2f[j - 1], r);
+    if (r == 0.0f) r = -1e-30f;
+    c += r < 0.0f ? 1 : 0;
+  }
+  return c;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kTriThreads) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
+                                                              unsigned long long *counters) {
+  (void)flags;
+  const SysDev &s = sysv[blockIdx.y];
+  if (s.box || !s.tri || !s.klist) return;
+  const int gi = threadIdx.x / G, i = threadIdx.x % G;  // group (matrix) in the CTA, eigenvalue index
+  const int widx = blockIdx.x * (kTriThreads / G) + gi;
+  if (widx >= s.nkhalf) return;  // uniform over the group
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const int m0 = s.m0;
   const double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
   const int m = (int)slot[0];
   if (m < 0) return;  // -1: not positive definite (NaN written by k_eig); -2: solved by k_eig
+  __shared__ double dsh[kTriThreads / G][kTriMax], esh[kTriThreads / G][kTriMax];
+  __shared__ float dfs[kTriThreads / G][kTriMax], efs[kTriThreads / G][kTriMax];
+  double *dn = dsh[gi], *e2 = esh[gi];
+  float *df = dfs[gi], *e2f = efs[gi];
+  // scale 2^ex >= max |entries|
+  const double di = i < m ? slot[1 + i] : 0.0;
+  const double ei = i + 1 < m ? slot[1 + m0 + i] : 0.0;
+  double mx = fmax(fabs(di), fabs(ei));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(gmask, mx, o));
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  const double dni = scale_pow2(di, -ex), eni = scale_pow2(ei, -ex);
+  if (i < m) {
+    dn[i] = dni;
+    e2[i] = eni * eni;
+    df[i] = (float)dni;
+    e2f[i] = (float)(eni * eni);
+  }
+  // Gershgorin interval of the scaled matrix
+  const double eprev = __shfl_up_sync(gmask, eni, 1, G);
+  const double rad = fabs(eni) + (i > 0 ? fabs(eprev) : 0.0);
+  double lo = i < m ? dni - rad : 1e300, hi = i < m ? dni + rad : -1e300;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(gmask, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(gmask, hi, o));
+  }
+  lo -= 0x1p-20;
+  hi += 0x1p-20;
+  __syncwarp(gmask);
+  double x = INFINITY;
+  int passes = 0;
+  if (i < m) {
+    // FP32 bisection on the pivot counts
+    float a = (float)lo, b = (float)hi;
+    for (int it = 0; it < 24; ++it) {
+      const float mid = 0.5f * (a + b);
+      if (tri_count32(df, e2f, m, mid) <= i)
+        a = mid;
+      else
+        b = mid;
+    }
+    const double delta = 0x1p-17;
+    bool done = false;
+    if (tri_count32(df, e2f, m, (float)((double)a - 2.0 * delta)) == i &&
+        tri_count32(df, e2f, m, (float)((double)b + 2.0 * delta)) == i + 1)
+      done = tri_newton(dn, e2, m, i, (double)a - delta, (double)b + delta, 0.5 * ((double)a + (double)b), 0x1p-40,
+                        &x, &passes);
+    if (!done) {
+      // a cluster: bisection on FP64 minor counts, count(A) <= i < count(B), from the FP32
+      // bracket when the FP64 counts confirm it, until lambda_i is alone in [A, B] (then
+      // Newton) or the bracket is two adjacent doubles
+      double A = (double)a - 2.0 * delta, B = (double)b + 2.0 * delta;
+      int cA = tri_count64(dn, e2, m, A), cB = tri_count64(dn, e2, m, B);
+      passes += 2;
+      if (cA > i) {
+        A = lo;
+        cA = 0;
+      }
+      if (cB <= i) {
+        B = hi;
+        cB = m;
+      }
+      bool newton_tried = false;
+      for (int it = 0; it < 120; ++it) {
+        if (!newton_tried && cA == i && cB == i + 1) {
+          newton_tried = true;
+          if (tri_newton(dn, e2, m, i, A, B, 0.5 * (A + B), 0x1p-50, &x, &passes)) {
+            done = true;
+            break;
+          }
+        }
+        const double mid = 0.5 * (A + B);
+        if (!(mid > A && mid < B)) break;
+        const int c = tri_count64(dn, e2, m, mid);
+        ++passes;
+        if (c <= i) {
+          A = mid;
+          cA = c;
+        } else {
+          B = mid;
+          cB = c;
+        }
+      }
+      if (!done) x = 0.5 * (A + B);
+    }
+    x = scale_pow2(x, ex);
+  }
+  const int kap = s.klist[widx];
   const int L0 = s.d[0].L, L1 = s.d[1].L, L2 = s.d[2].L;
   const int k0 = kap / (L1 * L2), k1 = (kap / L2) % L1, k2 = kap % L2;
   const int mk = (((L0 - k0) % L0) * L1 + (L1 - k1) % L1) * L2 + (L2 - k2) % L2;
-  double d[kMaxM0], e[kMaxM0];
-  for (int i = 0; i < m; ++i) d[i] = slot[1 + i];
-  for (int i = 0; i + 1 < m; ++i) e[i] = slot[1 + m0 + i];
-  const int rot = m > 0 ? tridiag_qr(d, e, m) : 0;
-  if (rot < 0) atomicOr(flags, kFlagNotSpd);
-  if (counters && rot > 0) atomicAdd(counters, (unsigned long long)rot);
-  // insertion sort (m <= 32)
-  for (int i = 1; i < m; ++i) {
-    const double v = d[i];
-    int j = i - 1;
-    while (j >= 0 && d[j] > v) {
-      d[j + 1] = d[j];
-      --j;
-    }
-    d[j + 1] = v;
+  if (i < m0) {
+    s.eig[(int64_t)kap * m0 + i] = x;  // +inf in the removed slots i >= m
+    s.eig[(int64_t)mk * m0 + i] = x;
   }
-  double *out = s.eig + (int64_t)kap * m0, *out2 = s.eig + (int64_t)mk * m0;
-  for (int i = 0; i < m0; ++i) {
-    const double v = rot < 0 ? NAN : (i < m ? d[i] : INFINITY);
-    out[i] = v;
-    out2[i] = v;
+  if (counters) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) passes += __shfl_xor_sync(gmask, passes, o);
+    if (i == 0) atomicAdd(counters, (unsigned long long)passes);
   }
 }
 
@@ -755,8 +901,13 @@ cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsig
   k_eig<<<grid, kEigWarps * 32, smem, st>>>(sys, flags, counters, max_m0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !tri) return e;
-  // one thread per matrix; warp-sized blocks spread the (latency-bound) iterations over all SMs
-  k_tridiag_eig<<<dim3((max_k + 31) / 32, nsys), 32, 0, st>>>(sys, flags, counters);
+  // G lanes per matrix (one per eigenvalue): 16 when every order fits, else 32
+  if (max_m0 <= 16)
+    k_tridiag_eig<16><<<dim3((max_k + kTriThreads / 16 - 1) / (kTriThreads / 16), nsys), kTriThreads, 0, st>>>(
+        sys, flags, counters);
+  else
+    k_tridiag_eig<32><<<dim3((max_k + kTriThreads / 32 - 1) / (kTriThreads / 32), nsys), kTriThreads, 0, st>>>(
+        sys, flags, counters);
   return cudaGetLastError();
 }
 

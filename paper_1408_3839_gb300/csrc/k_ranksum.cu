@@ -8,58 +8,107 @@
 //   H_j = T_j / 2 - V_j
 // written to block (j0 mod L0, j1 mod L1, j2 mod L2) of the first block column; blocks outside
 // the window are written as exact zeros by the same kernel (step a6).
-// Thread per (block of the first block column, entry): consecutive threads read consecutive
-// entries of each factor slot (coalesced); the loop over r streams the three directions' factors.
+//
+// A thread takes one entry (mu, nu) of kRankGroup consecutive direction-0 window blocks with the
+// same (j1, j2): the weights w_r = c_r C1_r C2_r are formed once and each block costs one FMA
+// per rank term.  Factor blocks outside the contracted half of a window are read from their
+// mirrors, C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
+// Consecutive threads take consecutive entries: the factor slots are read coalesced.
 #include "lhf_internal.cuh"
 
 namespace lhf {
 namespace {
 
-__global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv) {
+constexpr int kRankGroup = 8;
+
+// Window block jw of direction D, entry e = (mu, nu): pointer to slot 0 of that entry (slots are
+// mm doubles apart).
+__device__ __forceinline__ const double *factor_entry(const SysDev &s, const DirDev &D, int jw, int mu, int nu) {
+  const int m0 = s.m0, mm = m0 * m0, slots = s.Rt + 2;
+  if (jw >= D.cw0 && jw < D.cw0 + D.Jc) return s.ws + D.offC + (int64_t)jw * slots * mm + mu * m0 + nu;
+  int jm;  // mirror: j -> -j (mod L when the window is the whole lattice)
+  if (D.J == D.L && D.jlo == 0)
+    jm = jw == 0 ? 0 : D.L - jw;
+  else
+    jm = -2 * D.jlo - jw;
+  return s.ws + D.offC + (int64_t)jm * slots * mm + nu * m0 + mu;
+}
+
+__device__ __forceinline__ int wrap_block(int j, int L) {
+  j %= L;
+  return j < 0 ? j + L : j;
+}
+
+__global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv, int compute_ctas) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   const int m0 = s.m0, mm = m0 * m0, Rt = s.Rt;
+  const DirDev &D0 = s.d[0], &D1 = s.d[1], &D2 = s.d[2];
+  if ((int)blockIdx.x >= compute_ctas) {
+    // zeros outside the window (a6): thread per (block, entry)
+    const int64_t item = (int64_t)(blockIdx.x - compute_ctas) * blockDim.x + threadIdx.x;
+    if (item >= (int64_t)s.nblocks * mm) return;
+    const int64_t blk = item / mm;
+    const int jj[3] = {(int)(blk / ((int64_t)D1.L * D2.L)), (int)((blk / D2.L) % D1.L), (int)(blk % D2.L)};
+    for (int l = 0; l < 3; ++l)
+      if (wrap_block(jj[l] - s.d[l].jlo, s.d[l].L) >= s.d[l].J) {
+        s.H[item] = 0.0;
+        s.S[item] = 0.0;
+        return;
+      }
+    return;  // inside the window: written by the compute threads
+  }
+  const int groups = (D0.J + kRankGroup - 1) / kRankGroup;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= (int64_t)s.nblocks * mm) return;
-  const int64_t blk = item / mm;
-  const int e = (int)(item - blk * mm);
-  const int L1 = s.d[1].L, L2 = s.d[2].L;
-  const int jj[3] = {(int)(blk / ((int64_t)L1 * L2)), (int)((blk / L2) % L1), (int)(blk % L2)};
-  // window index of each direction's displacement; outside the window the block is zero (a6)
-  const double *F[3];
-  bool inside = true;
-  for (int l = 0; l < 3; ++l) {
-    const DirDev &D = s.d[l];
-    int jw = (jj[l] - D.jlo) % D.L;
-    if (jw < 0) jw += D.L;
-    if (jw >= D.J) inside = false;
-    F[l] = s.ws + D.offC + (int64_t)(inside ? jw : 0) * (Rt + 2) * mm + e;
-  }
-  if (!inside) {
-    s.H[item] = 0.0;
-    s.S[item] = 0.0;
-    return;
-  }
-  double v = 0.0;
+  if (item >= (int64_t)D1.J * D2.J * groups * mm) return;
+  const int e = (int)(item % mm);
+  int64_t rest = item / mm;
+  const int g = (int)(rest % groups);
+  rest /= groups;
+  const int jw2 = (int)(rest % D2.J), jw1 = (int)(rest / D2.J);
+  const int mu = e / m0, nu = e - mu * m0;
+  const double *F1 = factor_entry(s, D1, jw1, mu, nu);
+  const double *F2 = factor_entry(s, D2, jw2, mu, nu);
+  const double *F0[kRankGroup];
+  const int jw0_0 = g * kRankGroup;
+  const int nb = min(kRankGroup, D0.J - jw0_0);
+#pragma unroll
+  for (int b = 0; b < kRankGroup; ++b) F0[b] = factor_entry(s, D0, jw0_0 + (b < nb ? b : 0), mu, nu);
+  double acc[kRankGroup];
+#pragma unroll
+  for (int b = 0; b < kRankGroup; ++b) acc[b] = 0.0;
   for (int r = 0; r < Rt; ++r) {
     const int64_t o = (int64_t)r * mm;
-    v += s.c[r] * F[0][o] * F[1][o] * F[2][o];
+    const double w = s.c[r] * F1[o] * F2[o];
+#pragma unroll
+    for (int b = 0; b < kRankGroup; ++b) acc[b] = fma(w, F0[b][o], acc[b]);
   }
   const int64_t ok = (int64_t)Rt * mm, om = (int64_t)(Rt + 1) * mm;
-  const double K0 = F[0][ok], K1 = F[1][ok], K2 = F[2][ok];
-  const double M0 = F[0][om], M1 = F[1][om], M2 = F[2][om];
-  const double S = M0 * M1 * M2;
-  const double T = K0 * M1 * M2 + M0 * K1 * M2 + M0 * M1 * K2;
-  s.H[item] = 0.5 * T - v;
-  s.S[item] = S;
+  const double K1 = F1[ok], K2 = F2[ok], M1 = F1[om], M2 = F2[om];
+  const double P = M1 * M2, Q = K1 * M2 + M1 * K2;
+  const int64_t col = ((int64_t)wrap_block(D1.jlo + jw1, D1.L)) * D2.L + wrap_block(D2.jlo + jw2, D2.L);
+#pragma unroll
+  for (int b = 0; b < kRankGroup; ++b) {
+    if (b >= nb) break;
+    const double K0 = F0[b][ok], M0 = F0[b][om];
+    const int64_t blk = (int64_t)wrap_block(D0.jlo + jw0_0 + b, D0.L) * D1.L * D2.L + col;
+    s.H[blk * mm + e] = 0.5 * (K0 * P + M0 * Q) - acc[b];
+    s.S[blk * mm + e] = M0 * P;
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_items, cudaStream_t st) {
+int ranksum_compute_items(const SysDev &s) {
+  const int groups = (s.d[0].J + kRankGroup - 1) / kRankGroup;
+  return s.d[1].J * s.d[2].J * groups * s.m0 * s.m0;
+}
+
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_items, cudaStream_t st) {
   if (max_items <= 0 || nsys <= 0) return cudaSuccess;
-  dim3 grid((max_items + 255) / 256, nsys);
-  k_ranksum<<<grid, 256, 0, st>>>(sys);
+  const int compute_ctas = (max_compute_items + 255) / 256;
+  dim3 grid(compute_ctas + (max_items + 255) / 256, nsys);
+  k_ranksum<<<grid, 256, 0, st>>>(sys, compute_ctas);
   return cudaGetLastError();
 }
 

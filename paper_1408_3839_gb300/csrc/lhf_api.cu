@@ -45,7 +45,7 @@ struct Plan {
   size_t s0_off = 0;   // offset of s0 [m0]
   bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
-  int basis_items = 0, pot_rows = 0, gram_blocks = 0, rank_items = 0;
+  int basis_items = 0, pot_rows = 0, gram_blocks = 0, rank_items = 0, rank_compute = 0;
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
@@ -469,7 +469,8 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.tri_off = off;  // one slot per k-point bounds the solved ones
     off = align_up(off + (size_t)sd.nblocks * (2 * m0 + 1));
     P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
-    P.rank_items = sd.nblocks * mm;  // window blocks and the zeros outside
+    P.rank_items = sd.nblocks * mm;  // zeros outside the window
+    P.rank_compute = lhf::ranksum_compute_items(sd);
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
   P.ws = off;
@@ -543,8 +544,10 @@ int max_of(const std::vector<Plan> &ps, int Plan::*f) {
   return m;
 }
 
-// a3 + a4 for the uploaded systems: FP64 contraction, or digit planes + tensor cores.
-lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
+// a3 + a4 for the uploaded systems: FP64 contraction, or digit planes + tensor cores.  The
+// window blocks with j < 0 are filled from their mirrors only with_mirror (the rank-sum kernel
+// reads the mirrors itself).
+lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
   const int nsys = (int)ps.size();
   int max_m0 = 0, max_rt = 0;
   for (const Plan &p : ps) {
@@ -552,7 +555,8 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
     max_rt = std::max(max_rt, p.sd.Rt);
   }
   long long mirror = 0;
-  for (const Plan &p : ps) mirror = std::max(mirror, p.mirror_items);
+  if (with_mirror)
+    for (const Plan &p : ps) mirror = std::max(mirror, p.mirror_items);
   if (!ps[0].mixed) {
     c->begin(2);
     lhf_status st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
@@ -625,10 +629,12 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
   c->end();
   if (st != LHF_OK) return st;
-  st = run_gram(c, ps);
+  st = run_gram(c, ps, false);
   if (st != LHF_OK) return st;
   c->begin(3);
-  st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, &Plan::rank_items), c->stream), "rank-sum kernel");
+  st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, &Plan::rank_compute), max_of(ps, &Plan::rank_items),
+                                   c->stream),
+               "rank-sum kernel");
   c->end();
   return st;
 }
@@ -856,15 +862,15 @@ void lhf_destroy(lhf_ctx *c) {
   delete c;
 }
 
-lhf_status lhf_eig_counters(lhf_ctx *c, unsigned long long *sweeps, unsigned long long *matrices) {
-  if (!c || !sweeps || !matrices) return LHF_ERR_ARG;
+lhf_status lhf_eig_counters(lhf_ctx *c, unsigned long long *passes, unsigned long long *matrices) {
+  if (!c || !passes || !matrices) return LHF_ERR_ARG;
   unsigned long long h[3] = {0, 0, 0};
   lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (st != LHF_OK) return st;
   st = c->cuda(cudaMemcpy(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost), "cudaMemcpy");
   if (st != LHF_OK) return st;
   st = c->cuda(cudaMemset(c->d_counters, 0, sizeof h), "cudaMemset");
-  *sweeps = h[0];
+  *passes = h[0];
   *matrices = h[1];
   return st;
 }
@@ -1338,7 +1344,7 @@ lhf_status lhf_gram_factors(lhf_ctx *c, lhf_precision prec, int l, double *C, in
     if (st != LHF_OK) return st;
     st = c->cuda(lhf::launch_potential(c->d_sys, 1, ps[0].pot_rows, c->stream), "potential kernel");
     if (st != LHF_OK) return st;
-    st = run_gram(c, ps);
+    st = run_gram(c, ps, true);
     if (st != LHF_OK) return st;
   }
   const DirDev &D = ps[0].sd.d[l];

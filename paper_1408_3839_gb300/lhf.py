@@ -299,7 +299,7 @@ class Context:
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
 
     def eig_counters(self) -> tuple[int, int]:
-        """(QR rotations of the tridiagonal stage, matrices solved) since the previous call."""
+        """(FP64 polynomial passes of the tridiagonal stage, matrices solved) since the previous call."""
         a, b = ctypes.c_ulonglong(), ctypes.c_ulonglong()
         self._check(self.lib.lhf_eig_counters(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
