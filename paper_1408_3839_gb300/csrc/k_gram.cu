@@ -126,21 +126,19 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
     E[nu * ld + c] = e;
   }
   __syncthreads();
-  // P1 sums per nu: warp w reduces rows nu = w, w + 8, ... in a fixed order
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
-    double dq = 0.0, de = 0.0;
-    for (int c = lane; c < nv; c += 32) {
-      dq += Q[nu * ld + c];
-      de += E[nu * ld + c];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      dq += __shfl_xor_sync(0xffffffffu, dq, o);
-      de += __shfl_xor_sync(0xffffffffu, de, o);
-    }
-    if (lane == 0) {
-      red[2 * nu] = dq;
-      red[2 * nu + 1] = de;
+  // P1 sums per nu: red[2 nu] = sum_c Q[nu][c], red[2 nu + 1] = sum_c E[nu][c], each by a group
+  // of 8 lanes (strided partial sums, then a fixed 3-level shuffle tree)
+  {
+    const int sub = tid & 7, lane = tid & 31;
+    const unsigned gmask = 0xffu << (lane & 24);
+    for (int sidx = tid >> 3; sidx < 2 * m0; sidx += kGramThreads / 8) {
+      const double *row = ((sidx & 1) ? E : Q) + (sidx >> 1) * ld;
+      double acc = 0.0;
+      for (int c = sub; c < nv; c += 8) acc += row[c];
+      acc += __shfl_xor_sync(gmask, acc, 4);
+      acc += __shfl_xor_sync(gmask, acc, 2);
+      acc += __shfl_xor_sync(gmask, acc, 1);
+      if (sub == 0) red[sidx] = acc;
     }
   }
   __syncthreads();

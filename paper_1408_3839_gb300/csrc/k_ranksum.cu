@@ -19,7 +19,7 @@
 namespace lhf {
 namespace {
 
-constexpr int kRankGroup = 8;
+constexpr int kRankGroup = 4;
 
 // Window block jw of direction D, entry e = (mu, nu): pointer to slot 0 of that entry (slots are
 // mm doubles apart).
@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
   double acc[kRankGroup];
 #pragma unroll
   for (int b = 0; b < kRankGroup; ++b) acc[b] = 0.0;
+  // unrolled: the loads of four rank terms are in flight together
+#pragma unroll 4
   for (int r = 0; r < Rt; ++r) {
     const int64_t o = (int64_t)r * mm;
     const double w = s.c[r] * F1[o] * F2[o];
