@@ -8,7 +8,11 @@
 //
 // A CTA owns a tile of TW consecutive inner indices (entries (mu, nu) and the faster lattice
 // dimensions) for all L_d positions of one outer index: global loads and stores are rows of TW
-// contiguous values.  The tile is transformed in shared memory: an iterative radix-2 FFT when
+// contiguous values.  The blocks of a real lattice matrix satisfy H_-j = H_j^T, so every
+// transformed block is Hermitian, Hbar_kappa[nu][mu] = conj(Hbar_kappa[mu][nu]) (the same holds
+// for S): the last pass transforms only the entries mu <= nu and writes the others as their
+// conjugates (earlier passes of a multi-dimensional lattice still relate entries of different
+// outer indices and transform every entry).  The tile is transformed in shared memory: an iterative radix-2 FFT when
 // L_d is a power of two, otherwise the direct O(L_d^2) sum.  Twiddles come from a per-CTA table
 // built with sincospi (correctly-rounded arguments).
 #include "lhf_internal.cuh"
@@ -41,19 +45,49 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
       break;
     }
   const bool real_in = (d == first);
+  int last = 0;  // the final pass: the lowest dimension with L_d > 1 (0 for a single block)
+  for (int q = 0; q < 3; ++q)
+    if (Ls[q] > 1) {
+      last = q;
+      break;
+    }
+  const bool upper = (d == last);
   const int Ld = Ls[d];
-  const int mm = s.m0 * s.m0;
-  int64_t inner = mm;
-  for (int q = d + 1; q < 3; ++q) inner *= Ls[q];
+  const int m0 = s.m0, mm = m0 * m0, nup = upper ? m0 * (m0 + 1) / 2 : mm;
+  int64_t nlat = 1;  // faster lattice positions
+  for (int q = d + 1; q < 3; ++q) nlat *= Ls[q];
+  const int64_t inner = nlat * mm;       // stride of one position along dimension d
+  const int64_t items = nlat * nup;      // inner items transformed
   int64_t outer = 1;
   for (int q = 0; q < d; ++q) outer *= Ls[q];
   const int TW = tile_width(Ld);
-  const int64_t tiles_inner = (inner + TW - 1) / TW;
+  const int64_t tiles_inner = (items + TW - 1) / TW;
   const int64_t tile = blockIdx.x;
   if (tile >= outer * tiles_inner) return;
   const int64_t o = tile / tiles_inner;
   const int64_t i0 = (tile - o * tiles_inner) * TW;
-  const int tw_valid = (int)((inner - i0) < TW ? (inner - i0) : TW);
+  const int tw_valid = (int)((items - i0) < TW ? (items - i0) : TW);
+  // inner offsets of this tile's items (and of their transposed entries), kept by thread t < TW
+  __shared__ int64_t off_sh[16], offT_sh[16];
+  if ((int)threadIdx.x < TW) {
+    const int t = threadIdx.x;
+    int64_t u = i0 + t < items ? i0 + t : 0;
+    const int64_t lat = u / nup;
+    int r = (int)(u - lat * nup), mu = 0, nu = 0;
+    if (upper) {
+      while (r >= m0 - mu) {  // row mu holds nu = mu .. m0 - 1
+        r -= m0 - mu;
+        ++mu;
+      }
+      nu = mu + r;
+    } else {
+      mu = r / m0;
+      nu = r - mu * m0;
+    }
+    off_sh[t] = lat * mm + mu * m0 + nu;
+    offT_sh[t] = (upper && mu != nu) ? lat * mm + nu * m0 + mu : -1;
+  }
+  __syncthreads();
 
   const bool pow2 = (Ld & (Ld - 1)) == 0;
   // real first pass of a power-of-two length: H and S in one complex transform of
@@ -81,7 +115,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
     for (int k = tid; k < Ld * TW; k += kDftThreads) {
       const int j = k / TW, t = k - j * TW;
       if (t < tw_valid) {
-        const int64_t idx = (o * Ld + j) * inner + i0 + t;
+        const int64_t idx = (o * Ld + j) * inner + off_sh[t];
         mh = fmax(mh, fabs(s.H[idx]));
         ms = fmax(ms, fabs(s.S[idx]));
       }
@@ -113,7 +147,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
     const int j = k / TW, t = k - j * TW;
     double2 v = make_double2(0.0, 0.0);
     if (t < tw_valid) {
-      const int64_t idx = (o * Ld + j) * inner + i0 + t;
+      const int64_t idx = (o * Ld + j) * inner + off_sh[t];
       if (packed)
         v = make_double2(s.H[idx], sig * s.S[idx]);
       else if (real_in)
@@ -148,18 +182,26 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
         if (t < tw_valid) {
           const int kn = kap == 0 ? 0 : Ld - kap;
           const double2 z = x[kap * TW + t], zc = x[kn * TW + t];  // Z_k, Z_-k
-          const int64_t idx = (o * Ld + kap) * inner + i0 + t;
-          reinterpret_cast<double2 *>(s.Hbar)[idx] = make_double2(0.5 * (z.x + zc.x), 0.5 * (z.y - zc.y));
+          const int64_t base = (o * Ld + kap) * inner;
+          const double2 h = make_double2(0.5 * (z.x + zc.x), 0.5 * (z.y - zc.y));
           // (Z_k - conj Z_-k) / (2 i sigma)
-          reinterpret_cast<double2 *>(s.Sbar)[idx] = make_double2(hs2 * (z.y + zc.y), -hs2 * (z.x - zc.x));
+          const double2 sv = make_double2(hs2 * (z.y + zc.y), -hs2 * (z.x - zc.x));
+          reinterpret_cast<double2 *>(s.Hbar)[base + off_sh[t]] = h;
+          reinterpret_cast<double2 *>(s.Sbar)[base + off_sh[t]] = sv;
+          if (offT_sh[t] >= 0) {
+            reinterpret_cast<double2 *>(s.Hbar)[base + offT_sh[t]] = make_double2(h.x, -h.y);
+            reinterpret_cast<double2 *>(s.Sbar)[base + offT_sh[t]] = make_double2(sv.x, -sv.y);
+          }
         }
       }
     } else {
       for (int k = tid; k < Ld * TW; k += kDftThreads) {
         const int kap = k / TW, t = k - kap * TW;
         if (t < tw_valid) {
-          const int64_t idx = (o * Ld + kap) * inner + i0 + t;
-          reinterpret_cast<double2 *>(Xc)[idx] = x[kap * TW + t];
+          const int64_t base = (o * Ld + kap) * inner;
+          const double2 v = x[kap * TW + t];
+          reinterpret_cast<double2 *>(Xc)[base + off_sh[t]] = v;
+          if (offT_sh[t] >= 0) reinterpret_cast<double2 *>(Xc)[base + offT_sh[t]] = make_double2(v.x, -v.y);
         }
       }
     }
@@ -176,8 +218,9 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
         m += kap;
         if (m >= Ld) m -= Ld;
       }
-      const int64_t idx = (o * Ld + kap) * inner + i0 + t;
-      reinterpret_cast<double2 *>(Xc)[idx] = make_double2(re, im);
+      const int64_t base = (o * Ld + kap) * inner;
+      reinterpret_cast<double2 *>(Xc)[base + off_sh[t]] = make_double2(re, im);
+      if (offT_sh[t] >= 0) reinterpret_cast<double2 *>(Xc)[base + offT_sh[t]] = make_double2(re, -im);
     }
   }
 }
@@ -195,12 +238,18 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
       const int *L = host_L + 4 * s;  // L0, L1, L2, m0
       const bool all_one = (L[0] == 1 && L[1] == 1 && L[2] == 1);
       if (!(L[d] > 1 || (d == 0 && all_one))) continue;
-      int64_t inner = (int64_t)L[3] * L[3];
-      for (int q = d + 1; q < 3; ++q) inner *= L[q];
+      int last = 0;
+      for (int q = 0; q < 3; ++q)
+        if (L[q] > 1) {
+          last = q;
+          break;
+        }
+      int64_t items = (d == last) ? (int64_t)L[3] * (L[3] + 1) / 2 : (int64_t)L[3] * L[3];
+      for (int q = d + 1; q < 3; ++q) items *= L[q];
       int64_t outer = 1;
       for (int q = 0; q < d; ++q) outer *= L[q];
       const int TW = tile_width(L[d]);
-      const int64_t tiles = outer * ((inner + TW - 1) / TW);
+      const int64_t tiles = outer * ((items + TW - 1) / TW);
       if (tiles > max_tiles) max_tiles = tiles;
       if (L[d] > max_Ld) max_Ld = L[d];
     }

@@ -50,39 +50,46 @@ __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
 }
 
 // Samples and their forward differences D_e = g_e - g_(e+1) (periodic directions wrap; open
-// ones take g_n = 0; not formed for the extended samples of an open box): the neighbour's
-// sample comes from the next lane, or is evaluated where the next lane holds another row.
-__global__ void __launch_bounds__(256) k_basis(const SysDev *__restrict__ sysv) {
+// ones take g_n = 0; not formed for the extended samples of an open box): one CTA per (system,
+// direction, function mu).  In a periodic lattice direction only the nodes of the support cells
+// cell_lo .. cell_hi of the cell-0 copy (mod L, at most L cells) are written -- the Gram kernels
+// read nothing else, and every node outside them lies beyond the cut (zero sample); other
+// directions write the whole row.  The neighbour's sample comes from the next lane, or is
+// evaluated where the next lane holds no node of the window.
+constexpr int kBasisThreads = 256;
+
+__global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
-  int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int m0 = s.m0;
-  int l = 0;
-  for (; l < 3; ++l) {
-    int64_t cnt = (int64_t)m0 * (s.d[l].n + s.d[l].gext);
-    if (item < cnt) break;
-    item -= cnt;
-  }
-  const bool valid = l < 3;
-  int mu = 0, e = 0, nx = 1;
-  double g = 0.0;
-  if (valid) {
-    nx = s.d[l].n + s.d[l].gext;
-    mu = (int)(item / nx);
-    e = (int)(item - (int64_t)mu * nx);
-    g = basis_sample(s, l, mu, e);
-  }
-  // the whole warp takes part in the shuffle
-  double gn = __shfl_down_sync(0xffffffffu, g, 1);
-  if (!valid) return;
+  if ((int)blockIdx.x >= 3 * m0) return;
+  const int l = blockIdx.x / m0, mu = blockIdx.x - l * m0;
   const DirDev &D = s.d[l];
-  s.ws[D.offG + (int64_t)mu * nx + e] = g;
-  if (D.offD < 0) return;
+  const int nx = D.n + D.gext;
+  int start = 0, count = nx;
+  if (D.periodic) {
+    const int cells = min(s.cell_hi[l][mu] - s.cell_lo[l][mu] + 1, D.L);
+    count = min(D.n, cells * D.nc);
+    start = (s.cell_lo[l][mu] % D.L) * D.nc;
+    if (start < 0) start += D.n;
+  }
   const int lane = threadIdx.x & 31;
-  if (e + 1 == D.n)
-    gn = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
-  else if (lane == 31)
-    gn = basis_sample(s, l, mu, e + 1);
-  s.ws[D.offD + (int64_t)mu * D.n + e] = g - gn;
+  for (int k0 = threadIdx.x & ~31; k0 < count; k0 += kBasisThreads) {
+    const int k = k0 + lane;
+    const bool valid = k < count;
+    int e = start + k;
+    if (e >= nx) e -= nx;  // periodic wrap (start < n = nx there)
+    const double g = valid ? basis_sample(s, l, mu, e) : 0.0;
+    // the whole warp takes part in the shuffle
+    double gn = __shfl_down_sync(0xffffffffu, g, 1);
+    if (!valid) continue;
+    s.ws[D.offG + (int64_t)mu * nx + e] = g;
+    if (D.offD < 0) continue;
+    if (e + 1 == D.n)
+      gn = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
+    else if (lane == 31 || k + 1 == count)
+      gn = basis_sample(s, l, mu, e + 1);
+    s.ws[D.offD + (int64_t)mu * D.n + e] = g - gn;
+  }
 }
 
 // int_{-d}^{d} exp(-(m + u)^2) du = exp(-m^2) sum_k H_2k(m) 2 d^(2k+1) / (2k+1)!  (Taylor series
@@ -406,10 +413,10 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
 
 }  // namespace
 
-cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_t st) {
-  if (max_items <= 0 || nsys <= 0) return cudaSuccess;
-  dim3 grid((max_items + 255) / 256, nsys);
-  k_basis<<<grid, 256, 0, st>>>(sys);
+cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st) {
+  if (max_rows <= 0 || nsys <= 0) return cudaSuccess;
+  dim3 grid(max_rows, nsys);
+  k_basis<<<grid, kBasisThreads, 0, st>>>(sys);
   return cudaGetLastError();
 }
 

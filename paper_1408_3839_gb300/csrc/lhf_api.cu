@@ -45,7 +45,7 @@ struct Plan {
   size_t s0_off = 0;   // offset of s0 [m0]
   bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
-  int basis_items = 0, pot_rows = 0, gram_blocks = 0, rank_items = 0, rank_compute = 0;
+  int basis_items = 0 /* rows */, pot_rows = 0, gram_blocks = 0, rank_items = 0, rank_compute = 0;
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
@@ -405,7 +405,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.mirror_items += (long long)(D.J - D.Jc) * (Rt + 2) * mm;
     if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
-    P.basis_items += m0 * (D.n + D.gext);
+    P.basis_items += m0;  // one CTA per (direction, function) row
     P.pot_rows += Rt;  // one CTA per (direction, rank term) row
     P.gram_blocks += D.Jc * m0;
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
@@ -1284,9 +1284,13 @@ lhf_status lhf_basis_factors(lhf_ctx *c, int l, double *G) {
   bind_ws(ps[0], c->ws);
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
+  const DirDev &D = ps[0].sd.d[l];
+  // the basis kernel writes only the support windows of periodic rows: the rest are zeros
+  st = c->cuda(cudaMemsetAsync(c->ws + D.offG, 0, sizeof(double) * (size_t)ps[0].sd.m0 * (D.n + D.gext), c->stream),
+               "cudaMemsetAsync");
+  if (st != LHF_OK) return st;
   st = c->cuda(lhf::launch_basis(c->d_sys, 1, ps[0].basis_items, c->stream), "basis kernel");
   if (st != LHF_OK) return st;
-  const DirDev &D = ps[0].sd.d[l];
   // rows of n nodes out of rows of gext + n samples
   return c->cuda(cudaMemcpy2DAsync(G, sizeof(double) * (size_t)D.n, c->ws + D.offG + D.gext,
                                    sizeof(double) * (size_t)(D.n + D.gext), sizeof(double) * (size_t)D.n,

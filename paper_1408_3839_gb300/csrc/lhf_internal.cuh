@@ -112,7 +112,9 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
 
 // ---- kernel launchers (each returns the launch error) ------------------------------------
-cudaError_t launch_basis(const SysDev *sys, int nsys, int max_items, cudaStream_t st);
+// One CTA per (direction, function) row: max_rows = 3 m0 over the batch.  Periodic lattice
+// directions write only the support-cell window of each row (see k_basis).
+cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 // One CTA per (direction, rank term) row: max_rows = 3 R_tot over the batch.
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
