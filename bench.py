@@ -51,7 +51,9 @@ def dist_env():
 # clocks during the timed region
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 50 ms; only the samples whose timestamps fall inside the timed
+    region (host wall clock around the synchronised region) are summarised."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -59,6 +61,7 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -66,13 +69,24 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # wait for the first sample so that the timed region is covered from its start
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -81,49 +95,108 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+            if len(parts) >= 10:
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                except Exception:
+                    ts = None
+                rows.append((ts, parts[1:]))
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = [r for ts, r in rows if ts is not None and self.t0 is not None and self.t0 - 0.05 <= ts <= self.t1 + 0.05]
+        use = inside if inside else [r for _, r in rows]
+        sm = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in use if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in use for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(use),
+                "samples_in_timed_region": len(inside)}
 
 
 # ----------------------------------------------------------------------------------------------
 # algorithmic work per system (roofline numerators)
 
-def work_model(sizes: list[dict], passes: int, matrices: int) -> dict:
-    """Algorithmic FLOPs / bytes per batch for the stages (the roofline numerators).
+def _jc(s: dict, l: int) -> int:
+    """Window blocks of direction l that are contracted (j >= 0); the others are mirrors."""
+    J, L = s["window"][l], s["L"][l]
+    if J == 0:
+        return 0
+    return L // 2 + 1 if J == L else (J + 1) // 2
 
-    gram: 2 R_tot J m0^2 n_v per direction (the weighted-Gram contraction, counted over the whole
-    window although the mirrored half is copied); gram_tc: the same contraction as 28 exact BF16
-    digit-pair products (7 digits per operand, pairs a + b <= 6); rank: (4 R_tot + 12) per window
-    entry; dft: read 2 real blocks, write 2 complex blocks; eig: per solved matrix 9.33 m^3
-    (Cholesky and two triangular solves, complex) + 8 m^3 (Householder reduction to tridiagonal
-    form: per column a complex matrix-vector product and a rank-2 update of the trailing block),
-    plus 8 m flops per FP64 characteristic-polynomial pass of the tridiagonal stage (the
-    minors and their derivatives; its FP32 bisection is not counted)."""
-    gram = 0.0
-    dft_bytes = 0.0
-    rank = 0.0
-    eig = 0.0
+
+def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
+    """Algorithmic work of one step (a batch of systems) per kernel: the roofline numerators.
+
+    k_gram_fp64: 2 R_tot m0^2 n_v per contracted window block (blocks j >= 0; the j < 0 blocks are
+    mirrors), per direction.  k_gram_tc: the same contraction issued as 28 BF16 digit-pair
+    products per FP64 product (7 digits per operand, pairs a + b <= 6), over K padded to a
+    multiple of 64 (tensor-pipe work; "algorithmic_flops" keeps the FP64 count).  k_gram_slice:
+    bytes of the digit planes and exponents it writes.  k_ranksum: (4 R_tot + 12) per window
+    entry.  k_dft_pass: read 2 real blocks, write 2 complex blocks per lattice block, per level.
+    k_eig: per solved matrix 9.33 m^3 (Cholesky and two triangular solves, complex) + 8 m^3
+    (Householder reduction to real tridiagonal form).  k_tridiag_eig: 8 m flops per FP64
+    characteristic-polynomial pass (the minors and their derivatives; its FP32 bisection is not
+    counted).  `passes` and `matrices` are per step."""
+    gram = tc = tc_alg = slice_bytes = rank = dft_bytes = 0.0
+    levels = 0
     for s in sizes:
         m0, Rt = s["m0"], s["rank"]
         for l in range(3):
-            gram += 2.0 * Rt * s["window"][l] * m0 * m0 * s["n_potential"][l]
+            jc = _jc(s, l)
+            nv = s["n_potential"][l]
+            kpad = (nv + 63) // 64 * 64
+            gram += 2.0 * Rt * jc * m0 * m0 * nv
+            tc += 28.0 * 2.0 * Rt * jc * m0 * m0 * kpad
+            slice_bytes += 7 * 2.0 * jc * m0 * m0 * kpad + 4.0 * jc * m0 * m0
         nwin = s["window"][0] * s["window"][1] * s["window"][2]
         rank += nwin * m0 * m0 * (4.0 * Rt + 12.0)
         dft_bytes += s["n_blocks"] * m0 * m0 * (2 * 8 + 2 * 16)
-    if sizes:
-        m = sizes[0]["m0"]
-        eig = matrices * 17.33 * m ** 3 + passes * 8.0 * m
-    return {"gram_flops": gram, "gram_tc_flops": 28.0 * gram, "rank_flops": rank, "dft_bytes": dft_bytes,
-            "eig_flops": eig}
+        levels = max(levels, sum(1 for l in range(3) if s["L"][l] > 1))
+    m = sizes[0]["m0"] if sizes else 0
+    return {
+        "k_gram_fp64": {"bound": "alu", "work": gram},
+        "k_gram_tc": {"bound": "tensor", "work": tc, "algorithmic_flops": gram},
+        "k_gram_slice": {"bound": "hbm", "work": slice_bytes},
+        "k_ranksum": {"bound": "alu", "work": rank},
+        "k_dft_pass": {"bound": "hbm", "work": dft_bytes, "launches_per_step": max(levels, 1)},
+        "k_eig": {"bound": "alu", "work": matrices * 17.33 * m ** 3},
+        "k_tridiag_eig": {"bound": "alu", "work": passes * 8.0 * m},
+    }
+
+
+# DRAM traffic per system of the bench workload, from one ncu capture of the kernel (sum of
+# dram__bytes_read.sum and dram__bytes_write.sum over the captured launch, divided by the systems
+# it processed; traffic grows in proportion to the systems of a batch).  Valid only while the
+# kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
+# time; any other hash reports null.
+TRAFFIC = {
+    # ncu --set full of the tube_256 workload at 16 systems (profiles/tube_256_kernels_batch16.md)
+    "k_eig": {"src": "k_eig.cu", "sha": "e3648d26e1bda79e", "bytes_per_system": (17.008896e6 + 0.028160e6) / 16},
+    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "afc3622104ae4eef", "bytes_per_system": (180.74752e6 + 26.00704e6) / 16},
+    "k_gram_slice": {"src": "k_gram.cu", "sha": "41d7660d9b5eb076", "bytes_per_system": (6.277376e6 + 112.187648e6) / 16},
+    "k_ranksum": {"src": "k_ranksum.cu", "sha": "2c6c387596456151", "bytes_per_system": (46.152704e6 + 5.535232e6) / 16},
+}
+
+
+def _src_sha(fname: str) -> str:
+    import hashlib
+
+    p = os.path.join(ROOT, "paper_1408_3839_gb300", "csrc", fname)
+    try:
+        return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return ""
+
+
+def kernel_traffic(kernel: str, systems: int):
+    t = TRAFFIC.get(kernel)
+    if not t or _src_sha(t["src"]) != t["sha"]:
+        return None
+    return t["bytes_per_system"] * systems
 
 
 def fp64_peak_tflops() -> float:
@@ -158,8 +231,14 @@ def _oracle_one(seed: int, keep: bool = False):
     return dt, eig, st
 
 
+def _oracle_task(args):
+    seed, keep = args
+    return _oracle_one(seed, keep)
+
+
 def cpu_baseline(seed: int, procs: int = 1):
-    """Time the oracle on `procs` systems in parallel (spawned workers, one system each)."""
+    """Time the oracle on `procs` systems at once, one system per spawned single-threaded process
+    (seeds seed .. seed + procs - 1); the first system also returns its matrices."""
     import multiprocessing as mp
 
     import oracle
@@ -171,18 +250,27 @@ def cpu_baseline(seed: int, procs: int = 1):
         return {"wall": time.perf_counter() - t0, "systems": 1, "cores": 1, "eig": [eig], "status": [st],
                 "mats": mats}
     ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_one, [seed + i for i in range(procs)])
-    wall = time.perf_counter() - t0
-    return {"wall": wall, "systems": procs, "cores": procs, "eig": [r[1] for r in res]}
+        pool.map(int, range(procs))  # workers started before the clock
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_task, [(seed + i, i == 0) for i in range(procs)])
+        wall = time.perf_counter() - t0
+    return {"wall": wall, "systems": procs, "cores": procs, "eig": [r[1] for r in res],
+            "status": [r[2] for r in res], "mats": res[0][3]}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    cores = min(os.cpu_count() or 1, 16)
+    cores = min(host_cores(), 16)
     for _ in range(args.warmup):
         cpu_baseline(3000, cores)
     t0 = time.perf_counter()
@@ -226,18 +314,24 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
-def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None):
-    """Device time (ms, max over ranks) of `steps` batched passes, with live stage times."""
+def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None, profile=False):
+    """Device time (ms, max over ranks) of `steps` batched passes.  With profile, every stage and
+    every kernel launch is also bracketed by CUDA events on the launching stream (live stage and
+    kernel times; the extra event records cost a few percent of the step, so the headline
+    number is taken from a pass without them)."""
     import torch
 
     ctx.eig_counters()
     ctx.stage_times()
-    ctx.set_profiling(True)
+    ctx.kernel_times()
+    ctx.set_profiling(profile)
+    if clocks:
+        clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     if clocks:
-        clocks.start()
+        clocks.mark_start()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -245,12 +339,15 @@ def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None
         ctx.bloch_spectra(cfgs, eig, kst, precision)
     t_end.record(stream)
     torch.cuda.synchronize()
+    if clocks:
+        clocks.mark_end()
     ck = clocks.stop() if clocks else None
     ms = t_start.elapsed_time(t_end)
     ctx.set_profiling(False)
     stages = ctx.stage_times()
+    kernels = ctx.kernel_times()
     passes, mats = ctx.eig_counters()
-    return max_over_ranks(ms, dist, "cuda"), stages, passes, mats, ck
+    return max_over_ranks(ms, dist, "cuda"), stages, kernels, passes, mats, ck
 
 
 def _device_time_ms(fn, steps, stream):
@@ -370,7 +467,7 @@ def run_gpu(args):
     all_sizes = []
     for c in cfgs:
         ctx.setup(c)
-        all_sizes.append(ctx.query_sizes())
+        all_sizes.append(dict(ctx.query_sizes(), L=list(c["L"])))
 
     # FP64 route beside the mixed one (the metric compares the two); the main line is
     # args.precision, timed last
@@ -379,9 +476,14 @@ def run_gpu(args):
         for _ in range(max(args.warmup, 0)):
             ctx.bloch_spectra(cfgs, eig, kst, prec)
     torch.cuda.synchronize()
-    ms_other, stages_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
+    ms_other, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
+    _, stages_other, kernels_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist,
+                                                          profile=True)
     clocks = ClockSampler(local)
-    ms, stages, passes, mats, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
+    ms, _, _, _, _, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
+    # the same steps again with live stage and kernel timing (the rooflines' denominators)
+    ms_prof, stages, kernels, passes, mats, _ = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream,
+                                                            dist, profile=True)
     total_systems = B * args.steps * world
     value = total_systems / (ms / 1e3)
     value_other = total_systems / (ms_other / 1e3)
@@ -399,42 +501,44 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e_value = total_systems / e2e_s
 
-    # rooflines per stage and of the dominant one (the stage with the most device time)
-    work = work_model(all_sizes, passes, mats)
-    kernel_stages = ["basis", "potential", "gram", "gram_tc", "ranksum", "dft", "eig"]
+    # rooflines per kernel, and of the dominant kernel (the most device time in the timed region)
+    work = kernel_work(all_sizes, passes / max(args.steps, 1), mats / max(args.steps, 1))
     peaks = measured_peaks()
+    fp64_peak = fp64_peak_tflops()
     rooflines = {}
-    for st_name in kernel_stages:
-        st_ms, st_n = stages[st_name]
-        if st_n == 0 or st_ms <= 0:
+    for kname, (k_ms, k_n) in kernels.items():
+        if k_n == 0 or k_ms <= 0 or kname not in work:
             continue
-        per_launch_s = st_ms / 1e3 / st_n
-        if st_name == "dft":
-            achieved = work["dft_bytes"] / per_launch_s / 1e9
-            peak = float(peaks.get("hbm_gbs", 6800.0))
-            rooflines[st_name] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                  "frac": achieved / peak,
-                                  "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-        elif st_name == "gram_tc":
-            achieved = work["gram_tc_flops"] / per_launch_s / 1e12
-            peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            rooflines[st_name] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": achieved / peak,
-                                  "peak_source": "measured bf16 sustained" if "bf16_tflops_sustained" in peaks
-                                  else "fallback"}
-        elif st_name in ("gram", "ranksum", "eig") and not (st_name == "gram" and args.precision == "mixed"):
-            flops = {"gram": work["gram_flops"], "ranksum": work["rank_flops"],
-                     "eig": work["eig_flops"] / max(args.steps, 1)}[st_name]
-            achieved = flops / per_launch_s / 1e12
-            peak = fp64_peak_tflops()
-            rooflines[st_name] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": achieved / peak, "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
-    dom = max(kernel_stages, key=lambda s: stages[s][0])
+        w = work[kname]
+        per_launch_s = k_ms / 1e3 / k_n
+        per_launch_work = w["work"] / w.get("launches_per_step", 1)
+        if w["bound"] == "hbm":
+            achieved = per_launch_work / per_launch_s / 1e9
+            peak, unit = float(peaks.get("hbm_gbs", 6800.0)), "GB/s"
+            src = "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback"
+        elif w["bound"] == "tensor":
+            achieved = per_launch_work / per_launch_s / 1e12
+            peak, unit = float(peaks.get("bf16_tflops_sustained", 1700.0)), "TFLOP/s"
+            src = "measured bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "fallback"
+        else:
+            achieved = per_launch_work / per_launch_s / 1e12
+            peak, unit = fp64_peak, "TFLOP/s"
+            src = "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
+        r = {"bound": w["bound"], "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+             "peak_source": src, "launches": k_n, "ms_per_launch": k_ms / k_n}
+        if "algorithmic_flops" in w:
+            r["algorithmic_tflops"] = w["algorithmic_flops"] / per_launch_s / 1e12
+        rooflines[kname] = r
+    dom = max(kernels, key=lambda k: kernels[k][0])
     roof = dict(rooflines.get(dom, {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}))
-    roof["traffic"] = None
     roof["kernel"] = dom
+    roof["traffic"] = kernel_traffic(dom, B)
+    roof["algorithmic_per_launch"] = work.get(dom, {}).get("work")
     stage_summary = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages.items()}
-    gpu_launches = sum(stages[s][1] for s in kernel_stages)
+    kernel_summary = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                          "share": v[0] / max(sum(x[0] for x in kernels.values()), 1e-30)}
+                      for k, v in kernels.items() if v[1]}
+    gpu_launches = sum(v[1] for v in kernels.values())
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -448,12 +552,16 @@ def run_gpu(args):
                 "h2d_bytes_per_step": B * sizes[0]["desc_bytes"], "d2h_bytes_per_step": B * per_sys * 8 + hk.nbytes},
         "gpu_launches": gpu_launches,
         "roofline": roof,
-        "stage_rooflines": rooflines,
+        "kernel_rooflines": rooflines,
+        "kernels": kernel_summary,
         ("fp64" if other == lhf.FP64 else "mixed"): {
             "value": value_other, "unit": UNIT, "ms_per_step": ms_other / args.steps,
-            "stages": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages_other.items()}},
+            "stages": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages_other.items()},
+            "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                        for k, v in kernels_other.items() if v[1]}},
         "mixed_over_fp64": (value / value_other) if precision == lhf.MIXED else (value_other / value),
         "stages": stage_summary,
+        "profiled_ms_per_step": ms_prof / args.steps,
         "eig_tridiag_passes_per_matrix": passes / max(mats, 1),
         "bad_kpoints": bad_k,
         "clocks": ck,
@@ -463,7 +571,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         from tests._numerics import check_eigenvalues
 
-        cb = cpu_baseline(3000, 1)
+        cb = cpu_baseline(3000, min(host_cores(), 16))
         ref = cb["eig"][0]
         got = eig[:per_sys].cpu().numpy().reshape(ref.shape)
         H, S, Hb, Sb = cb["mats"]
@@ -475,7 +583,9 @@ def run_gpu(args):
             "median_abs_ha": float(np.median(np.abs(got[fin] - ref[fin]))),
             "k_status_match": bool(np.array_equal(kst[:ref.shape[0]].cpu().numpy(), cb["status"][0]))}
         line["cpu_baseline"] = {"value": cb["systems"] / cb["wall"], "unit": UNIT, "cores": cb["cores"],
-                                "kind": "oracle", "sample": "1 tube_256 system (seed 3000), single process"}
+                                "kind": "oracle", "wall_s": cb["wall"],
+                                "sample": f"{cb['systems']} tube_256 systems (seeds 3000..{2999 + cb['systems']}), "
+                                          "one per single-threaded process, all at once"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -487,7 +597,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--batch", type=int, default=64)

@@ -237,6 +237,33 @@ lhf_status lhf_gram_factors(lhf_ctx *ctx, lhf_precision precision, int l, double
 lhf_status lhf_set_profiling(lhf_ctx *ctx, int enable);
 lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
 
+/* Live per-kernel timing (same switch as the stage timing): with profiling enabled every kernel
+ * launch of the path is bracketed by its own pair of CUDA events on the context stream.
+ * lhf_kernel_times waits for the stream, adds the elapsed time of every launch recorded since
+ * the previous call into ms[kernel] and the launch count into launches[kernel] (host arrays of
+ * LHF_NUM_KERNELS), and clears the record.  lhf_kernel_name gives the kernel's name (static
+ * string; NULL outside 0 .. LHF_NUM_KERNELS - 1). */
+enum {
+    LHF_K_BASIS = 0,         /* a1 basis samples and differences */
+    LHF_K_POTENTIAL = 1,     /* a2 potential factors */
+    LHF_K_GRAM_FP64 = 2,     /* a3-a4 FP64 weighted Grams */
+    LHF_K_GRAM_SLICE = 3,    /* a3-a4 folded products and their digit planes (LHF_MIXED) */
+    LHF_K_VSLICE = 4,        /* digit planes of the potential factors (LHF_MIXED) */
+    LHF_K_GRAM_TC = 5,       /* tensor-core contraction of the digit planes (LHF_MIXED) */
+    LHF_K_GRAM_MIRROR = 6,   /* window blocks j < 0 from their mirrors */
+    LHF_K_RANKSUM = 7,       /* a5 Hadamard products and rank sum, a6 zero blocks */
+    LHF_K_DFT = 8,           /* a7 block DFT, one launch per lattice level */
+    LHF_K_OVERLAP_NORMS = 9, /* a8 cell-periodic overlap norms s0 */
+    LHF_K_EIG = 10,          /* a8 removal, scaling, reduction, Householder tridiagonalisation */
+    LHF_K_TRIDIAG_EIG = 11,  /* a8 tridiagonal eigenvalues */
+    LHF_K_BOX_GRAM = 12,     /* a9 direction-0 factors between cell pairs */
+    LHF_K_BOX_ASSEMBLE = 13, /* a9 dense H, S */
+    LHF_K_DENSE_EIG = 14,    /* a9 dense generalized eigensolve */
+    LHF_NUM_KERNELS = 15
+};
+lhf_status lhf_kernel_times(lhf_ctx *ctx, double *ms, int *launches);
+const char *lhf_kernel_name(int kernel);
+
 /* Work counters of the k-point eigensolver since the previous call (synchronising; host
  * outputs): total FP64 characteristic-polynomial passes of the tridiagonal eigenvalue stage (one
  * pass: the order-m recurrence for the leading minors and their derivatives at one point; k-points

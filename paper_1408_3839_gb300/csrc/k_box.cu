@@ -137,14 +137,18 @@ cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, int max_
     cudaError_t e = cudaFuncSetAttribute(k_box_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  kmark(LHF_K_BOX_GRAM, 1, st);
   k_box_gram<<<dim3(max_items, nsys), kBoxThreads, smem, st>>>(sys);
+  kmark(LHF_K_BOX_GRAM, 0, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_box_assemble(const SysDev *sys, int nsys, long long max_entries, cudaStream_t st) {
   if (max_entries <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid((unsigned)((max_entries + 255) / 256), nsys);
+  kmark(LHF_K_BOX_ASSEMBLE, 1, st);
   k_box_assemble<<<grid, 256, 0, st>>>(sys);
+  kmark(LHF_K_BOX_ASSEMBLE, 0, st);
   return cudaGetLastError();
 }
 

@@ -361,7 +361,10 @@ cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *ei
   GridBar *bar = reinterpret_cast<GridBar *>(work + 3 * (size_t)N * N + 5 * (size_t)N);
   if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st)) != cudaSuccess) return e;
   void *args[] = {(void *)&H, (void *)&S, (void *)&N, (void *)&eig, (void *)&work, (void *)&bar, (void *)&flags};
-  return cudaLaunchCooperativeKernel((const void *)k_dense_eig, dim3(G), dim3(kDenseThreads), args, smem, st);
+  kmark(LHF_K_DENSE_EIG, 1, st);
+  e = cudaLaunchCooperativeKernel((const void *)k_dense_eig, dim3(G), dim3(kDenseThreads), args, smem, st);
+  kmark(LHF_K_DENSE_EIG, 0, st);
+  return e;
 }
 
 }  // namespace lhf

@@ -268,7 +268,9 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
       if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)max_tiles, nsys, 2);
+    kmark(LHF_K_DFT, 1, st);
     k_dft_pass<<<grid, kDftThreads, smem, st>>>(sys, d);
+    kmark(LHF_K_DFT, 0, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (passes) ++*passes;

@@ -885,7 +885,9 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag_eig(const SysDev *__res
 
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
+  kmark(LHF_K_OVERLAP_NORMS, 1, st);
   k_overlap_norms<<<dim3(1, nsys), 256, 0, st>>>(sys);
+  kmark(LHF_K_OVERLAP_NORMS, 0, st);
   return cudaGetLastError();
 }
 
@@ -898,16 +900,20 @@ cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsig
     if (e != cudaSuccess) return e;
   }
   dim3 grid((max_k + kEigWarps - 1) / kEigWarps, nsys);
+  kmark(LHF_K_EIG, 1, st);
   k_eig<<<grid, kEigWarps * 32, smem, st>>>(sys, flags, counters, max_m0);
+  kmark(LHF_K_EIG, 0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !tri) return e;
   // G lanes per matrix (one per eigenvalue): 16 when every order fits, else 32
+  kmark(LHF_K_TRIDIAG_EIG, 1, st);
   if (max_m0 <= 16)
     k_tridiag_eig<16><<<dim3((max_k + kTriThreads / 16 - 1) / (kTriThreads / 16), nsys), kTriThreads, 0, st>>>(
         sys, flags, counters);
   else
     k_tridiag_eig<32><<<dim3((max_k + kTriThreads / 32 - 1) / (kTriThreads / 32), nsys), kTriThreads, 0, st>>>(
         sys, flags, counters);
+  kmark(LHF_K_TRIDIAG_EIG, 0, st);
   return cudaGetLastError();
 }
 

@@ -371,7 +371,9 @@ __global__ void __launch_bounds__(256) k_gram_mirror(const SysDev *__restrict__ 
 cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items, cudaStream_t st) {
   if (max_items <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid((unsigned)((max_items + 255) / 256), nsys);
+  kmark(LHF_K_GRAM_MIRROR, 1, st);
   k_gram_mirror<<<grid, 256, 0, st>>>(sys);
+  kmark(LHF_K_GRAM_MIRROR, 0, st);
   return cudaGetLastError();
 }
 
@@ -385,7 +387,9 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
     if (e != cudaSuccess) return e;
   }
   dim3 grid(max_blocks, nsys);
+  kmark(LHF_K_GRAM_FP64, 1, st);
   k_gram_fp64<<<grid, kGramThreads, smem, st>>>(sys);
+  kmark(LHF_K_GRAM_FP64, 0, st);
   return cudaGetLastError();
 }
 
@@ -398,10 +402,14 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
+  kmark(LHF_K_GRAM_SLICE, 1, st);
   k_gram_slice<<<dim3(max_blocks, nsys), kGramThreads, smem, st>>>(sys);
+  kmark(LHF_K_GRAM_SLICE, 0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  kmark(LHF_K_VSLICE, 1, st);
   k_vslice<<<dim3(max_rt3, nsys), kGramThreads, 0, st>>>(sys);
+  kmark(LHF_K_VSLICE, 0, st);
   return cudaGetLastError();
 }
 

@@ -320,8 +320,10 @@ cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsi
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   const unsigned char *d = static_cast<const unsigned char *>(dev_buf);
+  kmark(LHF_K_GRAM_TC, 1, st);
   k_gram_tc<<<(unsigned)njobs, kTcThreads, kSmemBytes, st>>>(reinterpret_cast<const TcJob *>(d + jobs_off),
                                                              reinterpret_cast<const TcArgs *>(d), flags);
+  kmark(LHF_K_GRAM_TC, 0, st);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,9 @@ cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, i
   if (max_items <= 0 || nsys <= 0) return cudaSuccess;
   const int compute_ctas = (max_compute_items + 255) / 256;
   dim3 grid(compute_ctas + (max_items + 255) / 256, nsys);
+  kmark(LHF_K_RANKSUM, 1, st);
   k_ranksum<<<grid, 256, 0, st>>>(sys, compute_ctas);
+  kmark(LHF_K_RANKSUM, 0, st);
   return cudaGetLastError();
 }
 

@@ -416,14 +416,18 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st) {
   if (max_rows <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid(max_rows, nsys);
+  kmark(LHF_K_BASIS, 1, st);
   k_basis<<<grid, kBasisThreads, 0, st>>>(sys);
+  kmark(LHF_K_BASIS, 0, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st) {
   if (max_rows <= 0 || nsys <= 0) return cudaSuccess;
   dim3 grid(max_rows, nsys);
+  kmark(LHF_K_POTENTIAL, 1, st);
   k_potential<<<grid, kPotThreads, 0, st>>>(sys);
+  kmark(LHF_K_POTENTIAL, 0, st);
   return cudaGetLastError();
 }
 

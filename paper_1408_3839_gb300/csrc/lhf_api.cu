@@ -19,6 +19,10 @@
 using lhf::DirDev;
 using lhf::SysDev;
 
+namespace lhf {
+thread_local KernelClock kclock = {nullptr, nullptr};
+}
+
 namespace {
 
 struct HostSystem {
@@ -102,6 +106,21 @@ struct lhf_ctx {
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> pool;
   Mark open_mark{-1, nullptr, nullptr, 0};
+  // per-kernel marks (Mark::stage holds the kernel id, Mark::kernels = 1)
+  std::vector<Mark> kmarks;
+  Mark open_kmark{-1, nullptr, nullptr, 0};
+
+  static void kernel_mark(void *owner, int kernel, int begin, cudaStream_t st) {
+    lhf_ctx *c = static_cast<lhf_ctx *>(owner);
+    if (begin) {
+      c->open_kmark = {kernel, c->take_event(), c->take_event(), 1};
+      if (c->open_kmark.a) cudaEventRecord(c->open_kmark.a, st);
+    } else if (c->open_kmark.stage == kernel) {
+      if (c->open_kmark.b) cudaEventRecord(c->open_kmark.b, st);
+      if (c->open_kmark.a && c->open_kmark.b) c->kmarks.push_back(c->open_kmark);
+      c->open_kmark = {-1, nullptr, nullptr, 0};
+    }
+  }
 
   cudaEvent_t take_event() {
     if (!pool.empty()) {
@@ -120,8 +139,10 @@ struct lhf_ctx {
     if (!prof) return;
     open_mark = {stage, take_event(), take_event(), 0};
     if (open_mark.a) cudaEventRecord(open_mark.a, stream);
+    lhf::kclock = {this, &lhf_ctx::kernel_mark};
   }
   void end(int kernels = 1) {
+    lhf::kclock = {nullptr, nullptr};
     if (!prof || open_mark.stage < 0) return;
     if (open_mark.b) cudaEventRecord(open_mark.b, stream);
     open_mark.kernels = kernels;
@@ -857,6 +878,10 @@ void lhf_destroy(lhf_ctx *c) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
   }
+  for (auto &m : c->kmarks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   for (auto &kv : c->klists) cudaFree(kv.second.first);
   delete c;
@@ -902,6 +927,37 @@ lhf_status lhf_stage_times(lhf_ctx *c, double *ms, int *launches) {
   }
   c->marks.clear();
   return LHF_OK;
+}
+
+lhf_status lhf_kernel_times(lhf_ctx *c, double *ms, int *launches) {
+  if (!c || !ms || !launches) return LHF_ERR_ARG;
+  for (int i = 0; i < LHF_NUM_KERNELS; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  for (auto &m : c->kmarks) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess && m.stage >= 0 && m.stage < LHF_NUM_KERNELS) {
+      ms[m.stage] += t;
+      launches[m.stage] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(m.a);
+    c->pool.push_back(m.b);
+  }
+  c->kmarks.clear();
+  return LHF_OK;
+}
+
+const char *lhf_kernel_name(int kernel) {
+  static const char *const names[LHF_NUM_KERNELS] = {
+      "k_basis",   "k_potential",     "k_gram_fp64", "k_gram_slice",      "k_vslice",
+      "k_gram_tc", "k_gram_mirror",   "k_ranksum",   "k_dft_pass",        "k_overlap_norms",
+      "k_eig",     "k_tridiag_eig",   "k_box_gram",  "k_box_assemble",    "k_dense_eig"};
+  return kernel >= 0 && kernel < LHF_NUM_KERNELS ? names[kernel] : nullptr;
 }
 
 const char *lhf_last_error(const lhf_ctx *c) { return c ? c->err.c_str() : "null context"; }

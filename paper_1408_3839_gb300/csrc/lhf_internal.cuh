@@ -111,6 +111,18 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 // Per-launch status word written by kernels (atomicOr of flag bits).
 enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
 
+// Per-kernel timing hook: while a context with profiling enabled is launching, kclock.mark is
+// set and every launcher brackets each of its kernel launches with kmark(kernel, 1 / 0, st)
+// (kernel = LHF_K_*).  Unset (the default) the calls do nothing.
+struct KernelClock {
+  void *owner;
+  void (*mark)(void *owner, int kernel, int begin, cudaStream_t st);
+};
+extern thread_local KernelClock kclock;
+inline void kmark(int kernel, int begin, cudaStream_t st) {
+  if (kclock.mark) kclock.mark(kclock.owner, kernel, begin, st);
+}
+
 // ---- kernel launchers (each returns the launch error) ------------------------------------
 // One CTA per (direction, function) row: max_rows = 3 m0 over the batch.  Periodic lattice
 // directions write only the support-cell window of each row (see k_basis).

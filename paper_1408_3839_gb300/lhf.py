@@ -106,6 +106,8 @@ def load():
             "lhf_gram_factors": (st, [ctx, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _ip]),
             "lhf_set_profiling": (st, [ctx, ctypes.c_int]),
             "lhf_stage_times": (st, [ctx, _dp, _ip]),
+            "lhf_kernel_times": (st, [ctx, _dp, _ip]),
+            "lhf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
             "lhf_k_point_eigensolve_noalloc": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int] + [ctypes.c_void_p] * 5),
             "lhf_graph_create": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -297,6 +299,16 @@ class Context:
         cnt = (ctypes.c_int * n)()
         self._check(self.lib.lhf_stage_times(self._h, ms, cnt))
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
+
+    NUM_KERNELS = 15
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (total ms, launches)} for kernel launches recorded since the previous call."""
+        n = self.NUM_KERNELS
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        self._check(self.lib.lhf_kernel_times(self._h, ms, cnt))
+        return {self.lib.lhf_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
 
     def eig_counters(self) -> tuple[int, int]:
         """(FP64 polynomial passes of the tridiagonal stage, matrices solved) since the previous call."""

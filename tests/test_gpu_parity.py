@@ -211,6 +211,35 @@ def test_batch_equals_single_runs_bitwise(ctx):
     assert np.array_equal(again.cpu().numpy(), batch)  # deterministic
 
 
+def test_live_kernel_times_count_every_launch(ctx, lhf):
+    """Per-kernel timing brackets each launch of the path: one pass of a 1D tube launches each
+    kernel of its route once (the DFT once per lattice level), and the kernel times fit inside
+    the stage times that bracket them."""
+    cfg = CASES["tube_16_m16"]()
+    ctx.setup(cfg)
+    s = ctx.query_sizes()
+    eig = dev((s["n_kpoints"] * s["m0"],))
+    for precision, route in ((lhf.FP64, ["k_gram_fp64"]), (lhf.MIXED, ["k_gram_slice", "k_vslice", "k_gram_tc"])):
+        ctx.bloch_spectra([cfg], eig, None, precision)  # warm-up: workspace growth outside the record
+        ctx.sync()
+        ctx.stage_times()
+        ctx.kernel_times()
+        ctx.set_profiling(True)
+        ctx.bloch_spectra([cfg], eig, None, precision)
+        ctx.set_profiling(False)
+        kt = ctx.kernel_times()
+        st = ctx.stage_times()
+        expect = ["k_basis", "k_potential", "k_ranksum", "k_dft_pass", "k_overlap_norms", "k_eig",
+                  "k_tridiag_eig"] + route
+        for k, (ms, n) in kt.items():
+            assert n == (1 if k in expect else 0), (k, n)
+            assert ms >= 0.0
+        total_k = sum(v[0] for v in kt.values())
+        total_s = sum(v[0] for v in st.values())
+        assert 0.0 < total_k <= total_s * 1.01 + 0.01
+        assert ctx.kernel_times()["k_eig"] == (0.0, 0)  # cleared by the previous call
+
+
 def test_host_entry_point_matches_device_entry_point(ctx):
     cfgs = [CASES["tube_16_m16"](), CASES["tube_9_m5_odd"]()]
     n = 0
