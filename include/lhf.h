@@ -155,6 +155,16 @@ lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *ctx, lhf_precision precision, 
 lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, double *Hbar,
                              double *Sbar);
 
+/* The k-point blocks of a periodic lattice by the separable route (Theorem 2.5, Prop. 4.2): the
+ * per-direction factors of steps a3-a4 (in the given precision) are transformed by 1D DFTs along
+ * their own lattice index, Fl_r(kappa_l) = sum_{j_l} omega_l^{kappa_l j_l} Cl_r[j_l], and each
+ * k-point block is assembled from their Hadamard products: Sbar = M0 M1 M2, Hbar = (K0 M1 M2 +
+ * M0 K1 M2 + M0 M1 K2) / 2 - sum_r c_r C0_r C1_r C2_r (entry-wise, complex).  Same result as
+ * lhf_assemble_core_hamiltonian followed by lhf_circulant_fft up to rounding, without forming
+ * the real-space blocks; the workspace holds sum_l L_l (R_tot + 2) m0^2 complex factor entries.
+ * Hbar, Sbar: device, complex interleaved [L0][L1][L2][m0][m0][2]. */
+lhf_status lhf_kspace_blocks(lhf_ctx *ctx, lhf_precision precision, double *Hbar, double *Sbar);
+
 /* Generalized Hermitian eigenproblems Hbar_kappa u = lambda Sbar_kappa u at every k-point
  * (eq. (4.7); spectrum = union over kappa, eq. (6.7)).  Inputs as produced by
  * lhf_circulant_fft (device): blocks of a real lattice matrix, so that Xbar at -kappa is the
@@ -179,6 +189,20 @@ lhf_status lhf_circulant_fft(lhf_ctx *ctx, const double *H, const double *S, dou
 #define LHF_LINDEP_TOL 1e-8
 lhf_status lhf_k_point_eigensolve(lhf_ctx *ctx, const double *Hbar, const double *Sbar,
                                   double *eig, int *k_status);
+
+/* Bloch eigenvectors (Prop. 6.1, eq. (6.8)): the eigenpairs Hbar_kappa u = lambda Sbar_kappa u at
+ * every k-point, inputs and eig / k_status as for lhf_k_point_eigensolve (same removal,
+ * scaling and Cholesky-or-canonical reduction; the reduced Hermitian matrix is diagonalised by
+ * cyclic Jacobi with accumulated rotations at every k-point).  vecs: device, complex interleaved
+ * [n_kpoints][m0][m0]: row r of k-point kappa is the eigenvector u of the r-th smallest
+ * eigenvalue, components over the m0 cell functions, normalised to u^H Sbar_kappa u = 1 on the
+ * kept functions (removed functions have component 0; dropped slots are zero rows, rows of a
+ * k-point whose overlap is not positive definite are NaN).  Its phase is fixed: the first
+ * component of largest magnitude is real and positive.  The vectors at -kappa are the complex
+ * conjugates of those at kappa.  The eigenvector of the lattice matrix for (kappa, r) is
+ * x_p = exp(2 pi i kappa . p / L) u / sqrt(L0 L1 L2) on cell p (eq. (6.8)). */
+lhf_status lhf_k_point_eigenvectors(lhf_ctx *ctx, const double *Hbar, const double *Sbar, double *eig,
+                                    double *vecs, int *k_status);
 
 /* Generalized symmetric-definite eigenvalues of dense N x N matrices (open box, Table 4.1's
  * full eigensolver): H x = lambda S x.  Device pointers; eig [N] ascending. */
@@ -259,7 +283,9 @@ enum {
     LHF_K_BOX_GRAM = 12,     /* a9 direction-0 factors between cell pairs */
     LHF_K_BOX_ASSEMBLE = 13, /* a9 dense H, S */
     LHF_K_DENSE_EIG = 14,    /* a9 dense generalized eigensolve */
-    LHF_NUM_KERNELS = 15
+    LHF_K_FACTOR_DFT = 15,   /* k-space route: 1D DFTs of the per-direction factors */
+    LHF_K_KSPACE_BLOCKS = 16, /* k-space route: Hadamard products and rank sum per k-point */
+    LHF_NUM_KERNELS = 17
 };
 lhf_status lhf_kernel_times(lhf_ctx *ctx, double *ms, int *launches);
 const char *lhf_kernel_name(int kernel);

@@ -2,8 +2,10 @@
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this package.  It shares no code with the CUDA library: the arithmetic lives in
-``lhf_oracle.c`` (compiled with gcc, loaded through ctypes); this module only marshals
-arguments.  See ``lhf_oracle.c`` for the passages of the paper each function follows.
+``lhf_oracle.c`` (compiled with gcc, loaded through ctypes), except for the Bloch eigenvectors
+(``k_point_eigenvectors``, ``lattice_eigenvector``) and the separable k-space route
+(``kspace_blocks``), written here in numpy; the rest of this module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each
+function follows.
 """
 
 from __future__ import annotations
@@ -290,6 +292,101 @@ def k_point_eigenvalues(Hbar: np.ndarray, Sbar: np.ndarray, tau: float = DROP_TO
     st = np.empty(K, dtype=np.int32)
     _load().orc_k_point_eigenvalues(K, m, _ptr(Hi), _ptr(Si), float(tau), float(tau2), _ptr(eig), _ptr(st))
     return eig, st
+
+
+def kspace_blocks(cfg):
+    """k-point blocks (Hbar, Sbar) [L0, L1, L2, m0, m0] of a periodic lattice by the separable
+    route (Theorem 2.5; Prop. 4.2): for every direction l the factors between the copy in cell j
+    and cell 0, C_r[j], K[j], M[j] (gram_1d, the per-entry formula of Lemma 3.1), are transformed
+    by the direct 1D DFT Fl(kappa) = sum_j omega^(kappa j) X[j], omega = exp(-2 pi i / L_l), and
+    each k-point block is the Hadamard-product form of Lemma 4.1 in the transformed factors:
+    Sbar = M0 M1 M2, Hbar = (K0 M1 M2 + M0 K1 M2 + M0 M1 K2) / 2 - sum_r c_r C0_r C1_r C2_r."""
+    s = _sys(cfg)
+    L = [int(v) for v in s.cfg["L"]]
+    c = rank_coefficients(s)
+    F = []
+    for l in range(3):
+        V = potential_factors(s, l)
+        X = np.empty((L[l], s.Rt + 2, s.m0, s.m0))
+        for j in range(L[l]):
+            C, K, M = gram_1d(s, l, j, 0, V)
+            X[j, :s.Rt], X[j, s.Rt], X[j, s.Rt + 1] = C, K, M
+        j = np.arange(L[l])
+        Wm = np.exp(-2j * np.pi * np.outer(j, j) / L[l])  # [kappa, j]
+        F.append(np.einsum("kj,jsab->ksab", Wm, X))
+    Hb = np.empty((L[0], L[1], L[2], s.m0, s.m0), dtype=np.complex128)
+    Sb = np.empty_like(Hb)
+    for k0 in range(L[0]):
+        for k1 in range(L[1]):
+            for k2 in range(L[2]):
+                A0, A1, A2 = F[0][k0], F[1][k1], F[2][k2]
+                Rt = s.Rt
+                V = np.einsum("r,rab,rab,rab->ab", c, A0[:Rt], A1[:Rt], A2[:Rt])
+                T = A0[Rt] * A1[Rt + 1] * A2[Rt + 1] + A0[Rt + 1] * A1[Rt] * A2[Rt + 1] \
+                    + A0[Rt + 1] * A1[Rt + 1] * A2[Rt]
+                Sb[k0, k1, k2] = A0[Rt + 1] * A1[Rt + 1] * A2[Rt + 1]
+                Hb[k0, k1, k2] = 0.5 * T - V
+    return Hb, Sb
+
+
+def k_point_eigenvectors(Hbar: np.ndarray, Sbar: np.ndarray, tau: float = DROP_TOL,
+                         tau2: float = LINDEP_TOL):
+    """Eigenpairs of Hbar_k u = lambda Sbar_k u at every k-point (eq. (4.7); Prop. 6.1).
+
+    Steps, in the order of k_point_eigenvalues (the readings of the removal rule and of the
+    near-linear dependence are the same): functions i with Re Sbar_ii(k) <= tau s0_i (s0_i the
+    mean over k of Re Sbar_ii) are removed at k; the kept pencil is scaled by D = diag(Sbar)^-1/2
+    and its Hermitian part taken; canonical orthogonalisation of the scaled overlap,
+    S~ = V diag(s) V^H, keeps the directions with s >= tau2, X = V_kept diag(s)^-1/2; the reduced
+    Hermitian matrix C = X^H H~ X is diagonalised (numpy.linalg.eigh, the library step), and
+    u = D X w.  Returns eig [K, m] ascending (+inf in removed slots), vecs [K, m, m] complex
+    (row r: eigenvector of the r-th eigenvalue over the m cell functions, 0 on removed
+    functions, u^H Sbar u = 1; the first component of largest magnitude real and positive;
+    zero rows in removed slots) and status [K] (removed directions)."""
+    m = Hbar.shape[-1]
+    Hb = np.asarray(Hbar).reshape(-1, m, m)
+    Sb = np.asarray(Sbar).reshape(-1, m, m)
+    K = Hb.shape[0]
+    s0 = np.mean(Sb[:, np.arange(m), np.arange(m)].real, axis=0)
+    eig = np.full((K, m), np.inf)
+    vecs = np.zeros((K, m, m), dtype=np.complex128)
+    status = np.zeros(K, dtype=np.int32)
+    for k in range(K):
+        d = Sb[k].diagonal().real
+        kept = np.nonzero(d > tau * s0)[0]
+        Dk = 1.0 / np.sqrt(d[kept])
+        Hs = Hb[k][np.ix_(kept, kept)] * np.outer(Dk, Dk)
+        Ss = Sb[k][np.ix_(kept, kept)] * np.outer(Dk, Dk)
+        Hs = 0.5 * (Hs + Hs.conj().T)
+        Ss = 0.5 * (Ss + Ss.conj().T)
+        sig, Vs = np.linalg.eigh(Ss)
+        keep2 = sig >= tau2
+        X = Vs[:, keep2] / np.sqrt(sig[keep2])
+        C = X.conj().T @ Hs @ X
+        C = 0.5 * (C + C.conj().T)
+        lam, W = np.linalg.eigh(C)
+        U = (Dk[:, None] * (X @ W))  # kept functions x eigenpairs
+        n = lam.shape[0]
+        eig[k, :n] = lam
+        status[k] = m - n
+        for r in range(n):
+            u = U[:, r]
+            big = np.argmax(np.abs(u) ** 2)  # first index of the largest magnitude
+            mag = abs(u[big])
+            u = u * (np.conj(u[big]) / mag)
+            u[big] = mag  # exactly real
+            vecs[k, r, kept] = u
+    return eig, vecs, status
+
+
+def lattice_eigenvector(u: np.ndarray, kappa, L) -> np.ndarray:
+    """The eigenvector of the lattice matrix built from the Bloch vector u at k-point
+    kappa = (k0, k1, k2) (Prop. 6.1, eq. (6.8)): x on cell p = (p0, p1, p2), index
+    ((p0 L1 + p1) L2 + p2) m + mu, is exp(2 pi i kappa . p / L) u_mu / sqrt(L0 L1 L2)."""
+    L = [int(v) for v in L]
+    p0, p1, p2 = np.meshgrid(np.arange(L[0]), np.arange(L[1]), np.arange(L[2]), indexing="ij")
+    ph = np.exp(2j * np.pi * (kappa[0] * p0 / L[0] + kappa[1] * p1 / L[1] + kappa[2] * p2 / L[2]))
+    return (ph.reshape(-1, 1) * np.asarray(u)[None, :]).reshape(-1) / np.sqrt(L[0] * L[1] * L[2])
 
 
 def bloch_spectrum(cfg):

@@ -299,6 +299,90 @@ __device__ void hermitian_part(double2 *A, int m, int lane) {
   __syncwarp();
 }
 
+// Eigenvectors of the pencil at k-point kap (and, conjugated, at its partner mk) from the
+// eigenvectors W of C (columns of V after Jacobi, sorted order given by vid per lane):
+//   Cholesky route:  y = L^{-H} w (back substitution, lanes over columns), S~-orthonormal;
+//   canonical route: y = X w with X = V_kept diag(sigma)^{-1/2} (in B, m x m2 by rows);
+// then u = D y on the kept functions (D = diag(Sbar)^{-1/2}) and zero on the removed ones, so
+// that u^H Sbar u = 1 on the kept block.  Each eigenvector's phase is fixed by making its first
+// component of largest magnitude real and positive.  Row r of vecs[kap] is the eigenvector of
+// the r-th smallest eigenvalue; dropped slots and failed k-points hold zero / NaN rows.
+__device__ void bloch_vectors(const SysDev &s, int kap, int mk, bool ok, bool chol, int m, int mkept, int lane,
+                              int vid, double2 *A, const double2 *B, double2 *V, const double *sg, const double *dsc,
+                              const int *kidx) {
+  const int m0 = s.m0;
+  const double2 *U = V;  // back-transformed columns, row stride m
+  if (ok && chol) {
+    const int q = m <= 16 ? 2 : 1;
+    const int cc = lane / q, part = lane % q;
+    const bool act = cc < m;
+    double2 z[kMaxM0];
+    for (int i = m - 1; i >= 0; --i) {
+      double2 acc = make_double2(0.0, 0.0);
+      if (act)
+        for (int k = i + 1 + part; k < m; k += q) {
+          const double2 l = B[k * m + i];  // conj(L[k][i]) z[k]
+          acc.x = fma(l.x, z[k].x, fma(l.y, z[k].y, acc.x));
+          acc.y = fma(l.x, z[k].y, fma(-l.y, z[k].x, acc.y));
+        }
+      if (q == 2) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      }
+      const double2 w = act ? V[i * m + cc] : make_double2(0.0, 0.0);
+      z[i] = cscale(csub(w, acc), sg[i]);
+    }
+    __syncwarp();
+    if (act && part == 0)
+      for (int i = 0; i < m; ++i) V[i * m + cc] = z[i];
+    __syncwarp();
+  } else if (ok) {
+    // U = X W (mkept x m) into A (its diagonal, the eigenvalues, is already in registers)
+    __syncwarp();
+    for (int e = lane; e < mkept * m; e += 32) {
+      const int a = e / m, c = e - (e / m) * m;
+      double2 acc = make_double2(0.0, 0.0);
+      for (int b = 0; b < m; ++b) acc = cfma(B[a * m + b], V[b * m + c], acc);
+      A[e] = acc;
+    }
+    __syncwarp();
+    U = A;
+  }
+  if (lane >= m0) return;
+  double2 *out = reinterpret_cast<double2 *>(s.vecs) + ((int64_t)kap * m0 + lane) * m0;
+  double2 *outc = reinterpret_cast<double2 *>(s.vecs) + ((int64_t)mk * m0 + lane) * m0;
+  if (!ok || lane >= m) {
+    const double2 fill = ok ? make_double2(0.0, 0.0) : make_double2(NAN, NAN);
+    for (int mu = 0; mu < m0; ++mu) {
+      out[mu] = fill;
+      if (mk != kap) outc[mu] = fill;
+    }
+    return;
+  }
+  // phase: the first component of largest magnitude becomes real and positive
+  double big = -1.0;
+  int abig = 0;
+  double2 ph = make_double2(1.0, 0.0);
+  for (int a = 0; a < mkept; ++a) {
+    const double2 u = cscale(U[a * m + vid], dsc[a]);
+    const double mag = u.x * u.x + u.y * u.y;
+    if (mag > big) {
+      big = mag;
+      abig = a;
+      ph = u;
+    }
+  }
+  const double amag = sqrt(big);
+  ph = big > 0.0 ? make_double2(ph.x / amag, -ph.y / amag) : make_double2(1.0, 0.0);  // conj(u_max) / |u_max|
+  for (int mu = 0; mu < m0; ++mu) {
+    double2 u = make_double2(0.0, 0.0);
+    for (int a = 0; a < mkept; ++a)
+      if (kidx[a] == mu) u = a == abig ? make_double2(amag, 0.0) : cmul(cscale(U[a * m + vid], dsc[a]), ph);
+    out[mu] = u;
+    if (mk != kap) outc[mu] = make_double2(u.x, -u.y);
+  }
+}
+
 // s0_i = (1/K) sum_kappa Re Sbar_kappa[i][i], one CTA per system, fixed-order reduction.
 __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
@@ -371,6 +455,9 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
     __syncwarp();
   }
   const RotTab R{rc, rsr, rsi, rp, rq, blk};
+  // FP32 copy of the Cholesky factor (off-diagonal entries, 1 / L_jj on the diagonal), kept in
+  // V's space, which the Cholesky route needs only after the FP32 trace estimate
+  float2 *L32 = reinterpret_cast<float2 *>(V);
 
   const double2 *Hb = reinterpret_cast<const double2 *>(s.Hbar) + (int64_t)kap * m0 * m0;
   const double2 *Sb = reinterpret_cast<const double2 *>(s.Sbar) + (int64_t)kap * m0 * m0;
@@ -421,11 +508,16 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
     }
     const double inv = rsqrt(d), ljj = d * inv;  // 1 / L_jj and L_jj
     __syncwarp();
-    for (int i = j + 1 + lane; i < m; i += 32) B[i * m + j] = cscale(B[i * m + j], inv);
+    for (int i = j + 1 + lane; i < m; i += 32) {
+      const double2 lij = cscale(B[i * m + j], inv);
+      B[i * m + j] = lij;
+      L32[i * m + j] = make_float2((float)lij.x, (float)lij.y);
+    }
     __syncwarp();
     if (lane == 0) {
       B[j * m + j] = make_double2(ljj, 0.0);
       sg[j] = inv;
+      L32[j * m + j] = make_float2((float)inv, 0.0f);  // the diagonal holds 1 / L_jj
     }
     // B[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i < m: the n (n + 1) / 2 entries of the
     // trailing lower triangle, n = m - j - 1, row by row
@@ -442,21 +534,62 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   }
 
   int sweeps = 0;
+  // 2a. trace(S~^{-1}) = ||L^{-1}||_F^2 >= 1 / lambda_min decides whether the Cholesky route may
+  //     be taken: 1 / trace >= kLindepTol proves that no overlap direction falls below
+  //     kLindepTol, so that it solves the same pencil as canonical orthogonalisation.  First an
+  //     FP32 estimate from the FP32 copy of L (forward substitution of L Z = I, two lanes per
+  //     column when m <= 16): wherever trace <= 1e8 the FP32 solve is accurate to a few percent
+  //     (kappa(L) <= 4e4), so an estimate below 1e6 accepts and one above 1e10 (or not finite)
+  //     rejects with a factor 100 to spare; in between the exact FP64 solve decides (step 2).
+  bool need64 = false;
   if (ok && chol) {
-    // 2. C = L^{-1} H L^{-H}.  The first pass also solves L Z = I in the columns m .. 2m-1 (the
-    //    lanes a warp leaves idle when m <= 16): trace(S~^{-1}) = ||Z||_F^2 >= 1 / lambda_min, so
-    //    1 / ||Z||_F^2 >= kLindepTol proves that no overlap direction falls below kLindepTol and
-    //    the Cholesky route solves the same pencil as canonical orthogonalisation; otherwise the
-    //    k-point goes to the canonical route.
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = e / m, j = e - (e / m) * m;
-      V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    const int q = m <= 16 ? 2 : 1;
+    const int cc = lane / q, part = lane % q;
+    const bool act = cc < m;
+    float2 z[kMaxM0];
+    float tr = 0.0f;
+    for (int i = 0; i < m; ++i) {
+      float2 acc = make_float2(0.0f, 0.0f);
+      if (act)
+        for (int k = part; k < i; k += q) {
+          const float2 l = L32[i * m + k];
+          acc.x = fmaf(l.x, z[k].x, acc.x);
+          acc.x = fmaf(-l.y, z[k].y, acc.x);
+          acc.y = fmaf(l.x, z[k].y, acc.y);
+          acc.y = fmaf(l.y, z[k].x, acc.y);
+        }
+      if (q == 2) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      }
+      const float di = L32[i * m + i].x;
+      z[i] = make_float2(((i == cc ? 1.0f : 0.0f) - acc.x) * di, -acc.y * di);
+      if (act && part == 0) tr = fmaf(z[i].x, z[i].x, fmaf(z[i].y, z[i].y, tr));
+    }
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (!(tr <= 1e6f)) {
+      if (tr <= 1e10f)
+        need64 = true;
+      else
+        chol = false;  // also when not finite
+    }
+    __syncwarp();
+  }
+  if (ok && chol) {
+    // 2. C = L^{-1} H L^{-H}.  When the FP32 estimate left the decision open, the first pass also
+    //    solves L Z = I in FP64 in the columns m .. 2m-1 and ||Z||_F^2 decides: 1 / ||Z||_F^2 >=
+    //    kLindepTol keeps the Cholesky route, otherwise the k-point goes to the canonical route.
+    if (need64) {
+      for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      }
     }
     __syncwarp();  // sg[i] = 1 / L_ii from the factorisation
     for (int pass = 0; pass < 2; ++pass) {
       // forward substitution per column; with 16 columns or fewer two lanes share a column
       // (even and odd k of each inner sum, combined by a shuffle)
-      const int ncol = pass == 0 ? 2 * m : m;
+      const int ncol = (pass == 0 && need64) ? 2 * m : m;
       const int q = ncol <= 16 ? 2 : 1;
       for (int cc0 = 0; cc0 < ncol; cc0 += 32 / q) {
         const int cc = cc0 + lane / q, part = lane % q;
@@ -479,12 +612,14 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       }
       __syncwarp();
       if (pass == 0) {
-        double tr = 0.0;
-        for (int e = lane; e < m * m; e += 32) tr += V[e].x * V[e].x + V[e].y * V[e].y;
-        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-        if (!(tr * kLindepTol <= 1.0)) {  // a direction may lie below kLindepTol
-          chol = false;
-          break;
+        if (need64) {
+          double tr = 0.0;
+          for (int e = lane; e < m * m; e += 32) tr += V[e].x * V[e].x + V[e].y * V[e].y;
+          for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+          if (!(tr * kLindepTol <= 1.0)) {  // a direction may lie below kLindepTol
+            chol = false;
+            break;
+          }
         }
         // A <- A^H
         for (int e = lane; e < m * m; e += 32) {
@@ -511,6 +646,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
       hermitian_part(A, m, lane);
     }
   }
+  const int mkept = m;  // kept functions (rows of the back-transformation)
   if (ok && !chol) {
     // 2'. canonical orthogonalisation: S~ = V diag(sigma) V^H, keep sigma >= kLindepTol,
     //     X = V_kept diag(sigma)^{-1/2}, C = X^H H~ X
@@ -606,8 +742,16 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   }
 
   if (ok) {
-    // 3. cyclic Jacobi on C
-    sweeps += jacobi_herm(A, nullptr, m, lane, R);
+    // 3. cyclic Jacobi on C (with the eigenvectors of C accumulated in V when requested: V is
+    //    free on both routes once C is formed)
+    if (s.vecs) {
+      for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      }
+      __syncwarp();
+    }
+    sweeps += jacobi_herm(A, s.vecs ? V : nullptr, m, lane, R);
     if (lane == 0 && counters) {
       if (!s.tri) atomicAdd(counters, (unsigned long long)sweeps);  // tridiagonal mode counts QR rotations
       atomicAdd(counters + 1, 1ull);
@@ -615,15 +759,23 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
     }
   }
 
-  // 4. sort and store (dropped functions and directions: +inf, last)
+  // 4. sort and store (dropped functions and directions: +inf, last); the sort carries the
+  //    column of each eigenvalue (ties keep the lower column first)
   double v = (ok && lane < m) ? A[lane * m + lane].x : INFINITY;
+  int vid = lane;
   for (int k = 2; k <= 32; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
       const double o = __shfl_xor_sync(0xffffffffu, v, j);
+      const int oid = __shfl_xor_sync(0xffffffffu, vid, j);
       const bool up = (lane & k) == 0, lower = (lane & j) == 0;
-      v = (lower == up) ? fmin(v, o) : fmax(v, o);
+      const bool o_less = o < v || (o == v && oid < vid);
+      if ((lower == up) == o_less) {
+        v = o;
+        vid = oid;
+      }
     }
   if (!ok) v = NAN;
+  if (s.vecs) bloch_vectors(s, kap, mk, ok, chol, m, mkept, lane, vid, A, B, V, sg, dsc, kidx);
   if (lane < m0) {
     s.eig[(int64_t)kap * m0 + lane] = v;
     s.eig[(int64_t)mk * m0 + lane] = v;

@@ -21,19 +21,6 @@ namespace {
 
 constexpr int kRankGroup = 4;
 
-// Window block jw of direction D, entry e = (mu, nu): pointer to slot 0 of that entry (slots are
-// mm doubles apart).
-__device__ __forceinline__ const double *factor_entry(const SysDev &s, const DirDev &D, int jw, int mu, int nu) {
-  const int m0 = s.m0, mm = m0 * m0, slots = s.Rt + 2;
-  if (jw >= D.cw0 && jw < D.cw0 + D.Jc) return s.ws + D.offC + (int64_t)jw * slots * mm + mu * m0 + nu;
-  int jm;  // mirror: j -> -j (mod L when the window is the whole lattice)
-  if (D.J == D.L && D.jlo == 0)
-    jm = jw == 0 ? 0 : D.L - jw;
-  else
-    jm = -2 * D.jlo - jw;
-  return s.ws + D.offC + (int64_t)jm * slots * mm + nu * m0 + mu;
-}
-
 __device__ __forceinline__ int wrap_block(int j, int L) {
   j %= L;
   return j < 0 ? j + L : j;

@@ -51,31 +51,44 @@ __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
 
 // Samples and their forward differences D_e = g_e - g_(e+1) (periodic directions wrap; open
 // ones take g_n = 0; not formed for the extended samples of an open box): one CTA per (system,
-// direction, function mu).  In a periodic lattice direction only the nodes of the support cells
-// cell_lo .. cell_hi of the cell-0 copy (mod L, at most L cells) are written -- the Gram kernels
-// read nothing else, and every node outside them lies beyond the cut (zero sample); other
-// directions write the whole row.  The neighbour's sample comes from the next lane, or is
-// evaluated where the next lane holds no node of the window.
+// direction, function mu, chunk of kBasisChunk samples of the row), so that the long rows of a
+// periodic lattice direction are spread over several CTAs.  In a periodic lattice direction
+// only the nodes of the support cells cell_lo .. cell_hi of the cell-0 copy (mod L, at most L
+// cells) are written -- the Gram kernels read nothing else, and every node outside them lies
+// beyond the cut (zero sample); other directions write the whole row (basis_row_samples).  The
+// neighbour's sample comes from the next lane, or is evaluated where the next lane holds no
+// node of the window (chunks end on warp boundaries).
 constexpr int kBasisThreads = 256;
+static_assert(kBasisChunk % 32 == 0, "chunks end on warp boundaries");
 
 __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   const int m0 = s.m0;
-  if ((int)blockIdx.x >= 3 * m0) return;
-  const int l = blockIdx.x / m0, mu = blockIdx.x - l * m0;
+  int b = blockIdx.x, l = 0, mu = 0, count = 0;
+  for (int r = 0; r < 3 * m0; ++r) {
+    const int cnt = basis_row_samples(s, r / m0, r % m0);
+    const int nch = (cnt + kBasisChunk - 1) / kBasisChunk;
+    if (b < nch) {
+      l = r / m0;
+      mu = r % m0;
+      count = cnt;
+      break;
+    }
+    b -= nch;
+  }
+  if (count == 0) return;  // surplus CTA of a smaller system
   const DirDev &D = s.d[l];
   const int nx = D.n + D.gext;
-  int start = 0, count = nx;
+  int start = 0;
   if (D.periodic) {
-    const int cells = min(s.cell_hi[l][mu] - s.cell_lo[l][mu] + 1, D.L);
-    count = min(D.n, cells * D.nc);
     start = (s.cell_lo[l][mu] % D.L) * D.nc;
     if (start < 0) start += D.n;
   }
   const int lane = threadIdx.x & 31;
-  for (int k0 = threadIdx.x & ~31; k0 < count; k0 += kBasisThreads) {
+  const int kend = min(count, (b + 1) * kBasisChunk);
+  for (int k0 = b * kBasisChunk + (threadIdx.x & ~31); k0 < kend; k0 += kBasisThreads) {
     const int k = k0 + lane;
-    const bool valid = k < count;
+    const bool valid = k < kend;
     int e = start + k;
     if (e >= nx) e -= nx;  // periodic wrap (start < n = nx there)
     const double g = valid ? basis_sample(s, l, mu, e) : 0.0;
@@ -86,7 +99,7 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
     if (D.offD < 0) continue;
     if (e + 1 == D.n)
       gn = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
-    else if (lane == 31 || k + 1 == count)
+    else if (lane == 31 || k + 1 == kend)
       gn = basis_sample(s, l, mu, e + 1);
     s.ws[D.offD + (int64_t)mu * D.n + e] = g - gn;
   }

@@ -426,7 +426,6 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.mirror_items += (long long)(D.J - D.Jc) * (Rt + 2) * mm;
     if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
-    P.basis_items += m0;  // one CTA per (direction, function) row
     P.pot_rows += Rt;  // one CTA per (direction, rank term) row
     P.gram_blocks += D.Jc * m0;
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
@@ -494,6 +493,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.rank_compute = lhf::ranksum_compute_items(sd);
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
+  P.basis_items = lhf::basis_ctas(sd);  // one CTA per (direction, function, chunk of samples)
   P.ws = off;
   return LHF_OK;
 }
@@ -772,7 +772,7 @@ lhf_status set_klist(lhf_ctx *c, SysDev &sd) {
   return klist_for(c, L, &sd.klist, &sd.nkhalf);
 }
 
-lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
+lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps, bool tri = true) {
   int max_k = 0, max_m0 = 0;
   for (const Plan &p : ps) {
     max_k = std::max(max_k, p.sd.klist ? p.sd.nkhalf : p.sd.nblocks);
@@ -782,9 +782,9 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps) {
   lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
   if (st == LHF_OK)
     st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream,
-                                 true),
+                                 tri),
                  "eigen kernel");
-  c->end(3);
+  c->end(tri ? 3 : 2);
   return st;
 }
 
@@ -954,9 +954,9 @@ lhf_status lhf_kernel_times(lhf_ctx *c, double *ms, int *launches) {
 
 const char *lhf_kernel_name(int kernel) {
   static const char *const names[LHF_NUM_KERNELS] = {
-      "k_basis",   "k_potential",     "k_gram_fp64", "k_gram_slice",      "k_vslice",
-      "k_gram_tc", "k_gram_mirror",   "k_ranksum",   "k_dft_pass",        "k_overlap_norms",
-      "k_eig",     "k_tridiag_eig",   "k_box_gram",  "k_box_assemble",    "k_dense_eig"};
+      "k_basis",   "k_potential",   "k_gram_fp64", "k_gram_slice",   "k_vslice",        "k_gram_tc",
+      "k_gram_mirror", "k_ranksum", "k_dft_pass",  "k_overlap_norms", "k_eig",          "k_tridiag_eig",
+      "k_box_gram", "k_box_assemble", "k_dense_eig", "k_factor_dft", "k_kspace_blocks"};
   return kernel >= 0 && kernel < LHF_NUM_KERNELS ? names[kernel] : nullptr;
 }
 
@@ -1059,6 +1059,48 @@ lhf_status lhf_assemble_core_hamiltonian(lhf_ctx *c, lhf_precision prec, double 
   return run_assembly(c, ps);
 }
 
+lhf_status lhf_kspace_blocks(lhf_ctx *c, lhf_precision prec, double *Hbar, double *Sbar) {
+  if (!c) return LHF_ERR_ARG;
+  if (!Hbar || !Sbar) return c->fail(LHF_ERR_ARG, "Hbar and Sbar must be device pointers");
+  lhf_status st = check_precision(c, prec);
+  if (st != LHF_OK) return st;
+  std::vector<Plan> ps(1);
+  st = current_plan(c, ps[0], prec == LHF_MIXED);
+  if (st != LHF_OK) return st;
+  Plan &P = ps[0];
+  if (P.sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "the k-space route needs a periodic lattice");
+  // the 1D factor transforms after the plan's regions
+  const size_t mm = (size_t)P.sd.m0 * P.sd.m0;
+  for (int l = 0; l < 3; ++l) {
+    P.sd.d[l].offF = (int64_t)P.ws;
+    P.ws = align_up(P.ws + 2 * (size_t)P.sd.d[l].L * (P.sd.Rt + 2) * mm);
+  }
+  st = ensure_ws(c, P.ws);
+  if (st != LHF_OK) return st;
+  bind_ws(P, c->ws);
+  P.sd.Hbar = Hbar;
+  P.sd.Sbar = Sbar;
+  st = set_klist(c, P.sd);
+  if (st != LHF_OK) return st;
+  st = upload(c, {P.sd});
+  if (st != LHF_OK) return st;
+  c->begin(0);
+  st = c->cuda(lhf::launch_basis(c->d_sys, 1, P.basis_items, c->stream), "basis kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(1);
+  st = c->cuda(lhf::launch_potential(c->d_sys, 1, P.pot_rows, c->stream), "potential kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  st = run_gram(c, ps, false);
+  if (st != LHF_OK) return st;
+  c->begin(4);
+  st = c->cuda(lhf::launch_kspace(c->d_sys, 1, lhf::kspace_factor_ctas(P.sd), (long long)P.sd.nkhalf * mm, c->stream),
+               "k-space kernels");
+  c->end(2);
+  return st;
+}
+
 lhf_status lhf_circulant_fft(lhf_ctx *c, const double *H, const double *S, double *Hbar, double *Sbar) {
   if (!c) return LHF_ERR_ARG;
   if (!H || !S || !Hbar || !Sbar) return c->fail(LHF_ERR_ARG, "all four pointers are required");
@@ -1094,6 +1136,30 @@ lhf_status lhf_k_point_eigensolve(lhf_ctx *c, const double *Hbar, const double *
   st = upload(c, {ps[0].sd});
   if (st != LHF_OK) return st;
   return run_eig(c, ps);
+}
+
+lhf_status lhf_k_point_eigenvectors(lhf_ctx *c, const double *Hbar, const double *Sbar, double *eig, double *vecs,
+                                    int *kstat) {
+  if (!c) return LHF_ERR_ARG;
+  if (!Hbar || !Sbar || !eig || !vecs) return c->fail(LHF_ERR_ARG, "Hbar, Sbar, eig and vecs are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  if (ps[0].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "k-point eigensolves need a periodic lattice");
+  st = ensure_ws(c, ps[0].ws);
+  if (st != LHF_OK) return st;
+  bind_ws(ps[0], c->ws);
+  ps[0].sd.Hbar = const_cast<double *>(Hbar);
+  ps[0].sd.Sbar = const_cast<double *>(Sbar);
+  ps[0].sd.eig = eig;
+  ps[0].sd.kstat = kstat;
+  ps[0].sd.vecs = vecs;
+  ps[0].sd.tri = nullptr;  // Jacobi with accumulated rotations at every k-point
+  st = set_klist(c, ps[0].sd);
+  if (st != LHF_OK) return st;
+  st = upload(c, {ps[0].sd});
+  if (st != LHF_OK) return st;
+  return run_eig(c, ps, false);
 }
 
 lhf_status lhf_dense_eigensolve(lhf_ctx *c, const double *H, const double *S, int N, double *eig) {

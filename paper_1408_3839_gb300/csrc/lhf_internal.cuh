@@ -54,6 +54,7 @@ struct DirDev {
   int64_t offB;   // BF16 [kSlices][Rt][Kpad] digit planes of the potential factors
   int64_t offRE;  // int [Jc m0 m0] row scale exponents
   int64_t offCE;  // int [Rt] potential-row scale exponents
+  int64_t offF;   // k-space route: complex [L][Rt+2][m0][m0] 1D DFTs of the factors (0 when unused)
 };
 
 struct SysDev {
@@ -84,6 +85,7 @@ struct SysDev {
   double *s0;             // [m0] mean over k-points of Re Sbar_ii (cell-periodic norms)
   const int *klist;       // [nkhalf] k-points solved (one per conjugate pair), or null
   double *tri;            // [nkhalf][2 m0 + 1] tridiagonal of each solved k-point, or null (Jacobi)
+  double *vecs;           // complex [nblocks][m0][m0] Bloch eigenvectors (rows), or null
   // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
@@ -108,8 +110,40 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
   return (x * pow2(h)) * pow2(e - h);
 }
 
+// Window block jw of direction D, entry (mu, nu): pointer to slot 0 of that entry (slots are m0^2
+// doubles apart).  Blocks outside the contracted half of the window are read from their
+// mirrors, C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
+__device__ __forceinline__ const double *factor_entry(const SysDev &s, const DirDev &D, int jw, int mu, int nu) {
+  const int m0 = s.m0, mm = m0 * m0, slots = s.Rt + 2;
+  if (jw >= D.cw0 && jw < D.cw0 + D.Jc) return s.ws + D.offC + (int64_t)jw * slots * mm + mu * m0 + nu;
+  int jm;  // mirror: j -> -j (mod L when the window is the whole lattice)
+  if (D.J == D.L && D.jlo == 0)
+    jm = jw == 0 ? 0 : D.L - jw;
+  else
+    jm = -2 * D.jlo - jw;
+  return s.ws + D.offC + (int64_t)jm * slots * mm + nu * m0 + mu;
+}
+
 // Per-launch status word written by kernels (atomicOr of flag bits).
 enum : unsigned { kFlagNotSpd = 1u, kFlagBadArg = 2u, kFlagTimeout = 4u };
+
+// Samples written by k_basis for row (l, mu): in a periodic lattice direction the nodes of the
+// support cells of the cell-0 copy (at most the whole row), elsewhere the whole (extended) row.
+// The host sizes the basis launch with the same count.
+constexpr int kBasisChunk = 512;  // samples per k_basis CTA
+__host__ __device__ inline int basis_row_samples(const SysDev &s, int l, int mu) {
+  const DirDev &D = s.d[l];
+  const int nx = D.n + D.gext;
+  if (!D.periodic) return nx;
+  const int span = s.cell_hi[l][mu] - s.cell_lo[l][mu] + 1;
+  const int cells = span < D.L ? span : D.L;
+  return D.n < cells * D.nc ? D.n : cells * D.nc;
+}
+__host__ __device__ inline int basis_ctas(const SysDev &s) {
+  int n = 0;
+  for (int r = 0; r < 3 * s.m0; ++r) n += (basis_row_samples(s, r / s.m0, r % s.m0) + kBasisChunk - 1) / kBasisChunk;
+  return n;
+}
 
 // Per-kernel timing hook: while a context with profiling enabled is launching, kclock.mark is
 // set and every launcher brackets each of its kernel launches with kmark(kernel, 1 / 0, st)
@@ -124,8 +158,9 @@ inline void kmark(int kernel, int begin, cudaStream_t st) {
 }
 
 // ---- kernel launchers (each returns the launch error) ------------------------------------
-// One CTA per (direction, function) row: max_rows = 3 m0 over the batch.  Periodic lattice
-// directions write only the support-cell window of each row (see k_basis).
+// One CTA per (direction, function, chunk of kBasisChunk samples): max_rows = basis_ctas over the
+// batch.  Periodic lattice directions write only the support-cell window of each row (see
+// k_basis).
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 // One CTA per (direction, rank term) row: max_rows = 3 R_tot over the batch.
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
@@ -160,6 +195,12 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st, bool tri);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
+// Separable k-space route (Theorem 2.5): 1D DFTs of the factors (max_factor_ctas =
+// kspace_factor_ctas over the batch) into D.offF, then Hbar / Sbar of every solved k-point and its
+// conjugate (max_items = nkhalf m0^2 over the batch).  The factors' mirrored blocks are read
+// from their partners.
+int kspace_factor_ctas(const SysDev &s);
+cudaError_t launch_kspace(const SysDev *sys, int nsys, int max_factor_ctas, long long max_items, cudaStream_t st);
 // Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
 // the dense matrices (thread per entry).
 size_t box_gram_smem_bytes(int max_width);

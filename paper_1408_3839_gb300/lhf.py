@@ -97,7 +97,9 @@ def load():
             "lhf_query_sizes": (st, [ctx, ctypes.POINTER(lhf_sizes)]),
             "lhf_assemble_core_hamiltonian": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_circulant_fft": (st, [ctx] + [ctypes.c_void_p] * 4),
+            "lhf_kspace_blocks": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_k_point_eigensolve": (st, [ctx] + [ctypes.c_void_p] * 4),
+            "lhf_k_point_eigenvectors": (st, [ctx] + [ctypes.c_void_p] * 5),
             "lhf_dense_eigensolve": (st, [ctx, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
             "lhf_bloch_spectra": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_bloch_spectra_host": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -248,11 +250,18 @@ class Context:
     def assemble_core_hamiltonian(self, H, S, precision: int = FP64):
         self._check(self.lib.lhf_assemble_core_hamiltonian(self._h, precision, _ptr(H), _ptr(S)))
 
+    def kspace_blocks(self, Hbar, Sbar, precision: int = FP64):
+        self._check(self.lib.lhf_kspace_blocks(self._h, int(precision), _ptr(Hbar), _ptr(Sbar)))
+
     def circulant_fft(self, H, S, Hbar, Sbar):
         self._check(self.lib.lhf_circulant_fft(self._h, _ptr(H), _ptr(S), _ptr(Hbar), _ptr(Sbar)))
 
     def k_point_eigensolve(self, Hbar, Sbar, eig, k_status=None):
         self._check(self.lib.lhf_k_point_eigensolve(self._h, _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(k_status)))
+
+    def k_point_eigenvectors(self, Hbar, Sbar, eig, vecs, k_status=None):
+        self._check(self.lib.lhf_k_point_eigenvectors(self._h, _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(vecs),
+                                                      _ptr(k_status)))
 
     def dense_eigensolve(self, H, S, N: int, eig):
         self._check(self.lib.lhf_dense_eigensolve(self._h, _ptr(H), _ptr(S), int(N), _ptr(eig)))
@@ -300,7 +309,7 @@ class Context:
         self._check(self.lib.lhf_stage_times(self._h, ms, cnt))
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
 
-    NUM_KERNELS = 15
+    NUM_KERNELS = 17
 
     def kernel_times(self) -> dict:
         """{kernel name: (total ms, launches)} for kernel launches recorded since the previous call."""
