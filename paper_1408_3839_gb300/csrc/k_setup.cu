@@ -29,7 +29,8 @@ __device__ __forceinline__ double gto_factor(double d, double alpha, double cut,
 __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
   const DirDev &D = s.d[l];
   int rel = e - s.node_lo[l][mu];
-  if (D.periodic && rel < 0) rel += D.n;
+  const int wrapped = (D.periodic && rel < 0) ? 1 : 0;
+  if (wrapped) rel += D.n;
   if (rel < 0 || rel >= s.node_span[l][mu]) return 0.0;
   const double x = D.x0 + (e - D.gext + 0.5) * D.h;
   const double A = s.centre[mu][l];
@@ -40,6 +41,13 @@ __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
   if (!D.periodic) return gto_factor(x - A, al, cut, pdir, pn);
   const double P = D.L * D.b;
   const double d0 = x - A;
+  if (s.node_span[l][mu] < D.n) {
+    // the window is shorter than the period: the one image within the cut is the one that puts
+    // node e at its unwrapped index (node_lo + node_wrap n) + rel, image m = -(node_wrap + wrapped)
+    // (the others contribute exact zeros to the sum below)
+    const int m = -(s.node_wrap[l][mu] + wrapped);
+    return gto_factor(d0 - m * P, al, cut, pdir, pn);
+  }
   // images m with |d0 - m P| <= cut (the bracket is widened by one on each side; the cut test
   // inside gto_factor decides)
   const int mlo = (int)floor((d0 - cut) * D.invP) - 1;

@@ -370,6 +370,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
           const long long lo = (long long)flo;
           sd.node_lo[l][mu] = (int)(((lo % D.n) + D.n) % D.n);
           sd.node_span[l][mu] = (int)(fhi - flo) + 1;
+          sd.node_wrap[l][mu] = (int)((lo - sd.node_lo[l][mu]) / D.n);
         }
       } else {
         const double nx = (double)D.n + D.gext;

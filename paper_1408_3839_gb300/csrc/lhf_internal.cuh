@@ -73,6 +73,7 @@ struct SysDev {
   int cell_hi[3][kMaxM0];
   int node_lo[3][kMaxM0];   // grid nodes that may be inside the cut of the cell-0 copy: from
   int node_span[3][kMaxM0]; // node_lo, node_span nodes (mod n in periodic directions; widened)
+  int node_wrap[3][kMaxM0]; // periodic, node_span < n: the unwrapped first node is node_lo + node_wrap n
   double Z[kMaxNuc];
   double a[kMaxNuc][3];
   double t[kMaxR];        // sinc nodes
