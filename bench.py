@@ -551,6 +551,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": B * sizes[0]["desc_bytes"], "d2h_bytes_per_step": B * per_sys * 8 + hk.nbytes},
         "gpu_launches": gpu_launches,
+        "launch_shapes": ctx.launch_shapes(),
         "roofline": roof,
         "kernel_rooflines": rooflines,
         "kernels": kernel_summary,

@@ -247,6 +247,17 @@ lhf_status lhf_basis_factors(lhf_ctx *ctx, int l, double *G);
 lhf_status lhf_potential_factors(lhf_ctx *ctx, int l, double *V);
 lhf_status lhf_gram_factors(lhf_ctx *ctx, lhf_precision precision, int l, double *C, int *jlo);
 
+/* Launch-shape autotuner (enabled by default).  The first time a context solves the k-points of
+ * a batch class -- (m0, route, log2 of the number of solved matrices) -- it times each candidate
+ * launch shape of the eigensolver kernels (k-points per CTA of the reduction kernel: 1, 2, 4, 8;
+ * threads per CTA of the tridiagonal kernel: 32 .. 256) once on that batch, synchronising the
+ * stream, and keeps the fastest for the class.  The shape changes no result (every k-point is
+ * solved by the same code in any shape).  Graph capture uses the shapes tuned before it (else
+ * the defaults 4 and 128): tune a class with one direct call before capturing it.
+ * lhf_launch_shapes reports the shapes of the last k-point solve (host outputs). */
+lhf_status lhf_set_autotune(lhf_ctx *ctx, int enable);
+lhf_status lhf_launch_shapes(lhf_ctx *ctx, int *eig_warps, int *tri_threads);
+
 /* Live stage timing.  With profiling enabled, every launch of the path is bracketed by CUDA
  * events recorded on the context stream (no synchronisation is added).  lhf_stage_times waits
  * for the stream, adds the elapsed times of all launches recorded since the previous call into

@@ -28,7 +28,7 @@
 namespace lhf {
 namespace {
 
-constexpr int kEigWarps = 4;
+constexpr int kEigMaxWarps = 8;  // warps (k-points) per CTA: blockDim.x / 32, set by the launcher
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict_
   }
 }
 
-__global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict__ sysv,
+__global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restrict__ sysv,
                                                         unsigned *flags, unsigned long long *counters,
                                                         int max_m0) {
   const SysDev &s = sysv[blockIdx.y];
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
   // k-point of this warp: the i-th entry of the list of solved k-points (one per conjugate pair)
   // when the system has one, otherwise warp i takes k-point i and leaves it to its partner if
   // the partner's index is lower
-  const int widx = blockIdx.x * kEigWarps + warp;
+  const int widx = blockIdx.x * (int)(blockDim.x >> 5) + warp;
   int kap;
   if (s.klist) {
     if (widx >= s.nkhalf) return;
@@ -814,7 +814,7 @@ __global__ void __launch_bounds__(kEigWarps * 32) k_eig(const SysDev *__restrict
 //     minor counts until lambda_i is alone in the bracket (then Newton again) or the bracket is
 //     two adjacent doubles.
 // counters[0] accumulates the FP64 recurrence passes (one pass: m steps).
-constexpr int kTriThreads = 128;
+constexpr int kTriMaxThreads = 256;  // threads per CTA: blockDim.x (a multiple of G), set by the launcher
 constexpr int kTriMax = kMaxM0;
 
 // q_m(x) = det(T - x I) and its derivative (dn, e2: scaled diagonal and squared off-diagonal,
@@ -916,21 +916,21 @@ __device__ int tri_count32(const float *df, const float *e2f, int m, float x) {
 }
 
 template <int G>
-__global__ void __launch_bounds__(kTriThreads) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
+__global__ void __launch_bounds__(kTriMaxThreads) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
                                                               unsigned long long *counters) {
   (void)flags;
   const SysDev &s = sysv[blockIdx.y];
   if (s.box || !s.tri || !s.klist) return;
   const int gi = threadIdx.x / G, i = threadIdx.x % G;  // group (matrix) in the CTA, eigenvalue index
-  const int widx = blockIdx.x * (kTriThreads / G) + gi;
+  const int widx = blockIdx.x * (int)(blockDim.x / G) + gi;
   if (widx >= s.nkhalf) return;  // uniform over the group
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const int m0 = s.m0;
   const double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
   const int m = (int)slot[0];
   if (m < 0) return;  // -1: not positive definite (NaN written by k_eig); -2: solved by k_eig
-  __shared__ double dsh[kTriThreads / G][kTriMax], esh[kTriThreads / G][kTriMax];
-  __shared__ float dfs[kTriThreads / G][kTriMax], efs[kTriThreads / G][kTriMax];
+  __shared__ double dsh[kTriMaxThreads / G][kTriMax], esh[kTriMaxThreads / G][kTriMax];
+  __shared__ float dfs[kTriMaxThreads / G][kTriMax], efs[kTriMaxThreads / G][kTriMax];
   double *dn = dsh[gi], *e2 = esh[gi];
   float *df = dfs[gi], *e2f = efs[gi];
   // scale 2^ex >= max |entries|
@@ -1043,30 +1043,49 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                       unsigned long long *counters, cudaStream_t st, bool tri) {
+int eig_max_warps(int max_m0) {
+  int w = kEigMaxWarps;
+  while (w > 1 && (size_t)w * eig_warp_bytes(max_m0) > 227 * 1024) --w;
+  return w;
+}
+
+cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                              unsigned long long *counters, cudaStream_t st, int warps) {
   if (max_k <= 0 || nsys <= 0) return cudaSuccess;
-  const size_t smem = kEigWarps * eig_warp_bytes(max_m0);
+  if (warps < 1 || warps > kEigMaxWarps) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)warps * eig_warp_bytes(max_m0);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((max_k + kEigWarps - 1) / kEigWarps, nsys);
+  dim3 grid((max_k + warps - 1) / warps, nsys);
   kmark(LHF_K_EIG, 1, st);
-  k_eig<<<grid, kEigWarps * 32, smem, st>>>(sys, flags, counters, max_m0);
+  k_eig<<<grid, warps * 32, smem, st>>>(sys, flags, counters, max_m0);
   kmark(LHF_K_EIG, 0, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !tri) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                           unsigned long long *counters, cudaStream_t st, int threads) {
+  if (max_k <= 0 || nsys <= 0) return cudaSuccess;
   // G lanes per matrix (one per eigenvalue): 16 when every order fits, else 32
+  const int G = max_m0 <= 16 ? 16 : 32;
+  if (threads < G || threads > kTriMaxThreads || threads % G != 0) return cudaErrorInvalidValue;
+  const int per = threads / G;
   kmark(LHF_K_TRIDIAG_EIG, 1, st);
-  if (max_m0 <= 16)
-    k_tridiag_eig<16><<<dim3((max_k + kTriThreads / 16 - 1) / (kTriThreads / 16), nsys), kTriThreads, 0, st>>>(
-        sys, flags, counters);
+  if (G == 16)
+    k_tridiag_eig<16><<<dim3((max_k + per - 1) / per, nsys), threads, 0, st>>>(sys, flags, counters);
   else
-    k_tridiag_eig<32><<<dim3((max_k + kTriThreads / 32 - 1) / (kTriThreads / 32), nsys), kTriThreads, 0, st>>>(
-        sys, flags, counters);
+    k_tridiag_eig<32><<<dim3((max_k + per - 1) / per, nsys), threads, 0, st>>>(sys, flags, counters);
   kmark(LHF_K_TRIDIAG_EIG, 0, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                       unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps, int tri_threads) {
+  cudaError_t e = launch_eig_reduce(sys, nsys, max_k, max_m0, flags, counters, st, eig_warps);
+  if (e != cudaSuccess || !tri) return e;
+  return launch_tridiag(sys, nsys, max_k, max_m0, flags, counters, st, tri_threads);
 }
 
 }  // namespace lhf

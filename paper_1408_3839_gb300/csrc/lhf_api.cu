@@ -96,6 +96,13 @@ struct lhf_ctx {
   std::vector<int> host_L;
   // solved k-points (one per conjugate pair) per lattice shape, on the device
   std::map<std::array<int, 3>, std::pair<int *, int>> klists;
+  // launch-shape autotuner of the k-point eigensolver: per (m0, tridiagonal route, log2 of the
+  // solved matrices) the fastest k_eig warps per CTA and tridiagonal threads per CTA, timed on
+  // the first batch of that class (outside graph capture); results do not depend on the shape
+  bool autotune = true;
+  bool capturing = false;
+  std::map<std::array<int, 3>, std::array<int, 2>> eig_tune;
+  int last_eig_warps = 4, last_tri_threads = 128;
   // live stage timing
   bool prof = false;
   struct Mark {
@@ -773,17 +780,86 @@ lhf_status set_klist(lhf_ctx *c, SysDev &sd) {
   return klist_for(c, L, &sd.klist, &sd.nkhalf);
 }
 
+// Times each candidate launch shape of k_eig (warps per CTA) and, on the tridiagonal route, of
+// k_tridiag_eig (threads per CTA) once on the uploaded batch (the overlap norms already
+// launched); both kernels rewrite the same outputs, so the trial runs leave no trace beyond
+// the time they take.  Returns the fastest pair.
+lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, std::array<int, 2> *best) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  lhf_status st = c->cuda(cudaEventCreate(&a), "cudaEventCreate");
+  if (st == LHF_OK) st = c->cuda(cudaEventCreate(&b), "cudaEventCreate");
+  auto timed = [&](auto launch, float *ms) -> lhf_status {
+    lhf_status s2 = c->cuda(cudaEventRecord(a, c->stream), "cudaEventRecord");
+    if (s2 == LHF_OK) s2 = c->cuda(launch(), "eigen kernel (tuning)");
+    if (s2 == LHF_OK) s2 = c->cuda(cudaEventRecord(b, c->stream), "cudaEventRecord");
+    if (s2 == LHF_OK) s2 = c->cuda(cudaEventSynchronize(b), "cudaEventSynchronize");
+    if (s2 == LHF_OK) s2 = c->cuda(cudaEventElapsedTime(ms, a, b), "cudaEventElapsedTime");
+    return s2;
+  };
+  (*best)[0] = 4;
+  (*best)[1] = 128;
+  float tbest = 1e30f, t = 0.f;
+  const int wmax = lhf::eig_max_warps(max_m0);
+  // a first run at the default shape warms the caches (and its output feeds the tridiagonal trials)
+  if (st == LHF_OK)
+    st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream,
+                                                   std::min(4, wmax)); },
+               &t);
+  for (int w : {1, 2, 4, 8}) {
+    if (st != LHF_OK || w > wmax) break;
+    st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream, w); },
+               &t);
+    if (st == LHF_OK && t < tbest) {
+      tbest = t;
+      (*best)[0] = w;
+    }
+  }
+  if (tri) {
+    tbest = 1e30f;
+    const int G = max_m0 <= 16 ? 16 : 32;
+    for (int th : {32, 64, 128, 256}) {
+      if (st != LHF_OK) break;
+      if (th < G) continue;
+      st = timed([&] { return lhf::launch_tridiag(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream, th); },
+                 &t);
+      if (st == LHF_OK && t < tbest) {
+        tbest = t;
+        (*best)[1] = th;
+      }
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  return st;
+}
+
 lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps, bool tri = true) {
   int max_k = 0, max_m0 = 0;
+  long long total = 0;
   for (const Plan &p : ps) {
-    max_k = std::max(max_k, p.sd.klist ? p.sd.nkhalf : p.sd.nblocks);
+    const int k = p.sd.klist ? p.sd.nkhalf : p.sd.nblocks;
+    max_k = std::max(max_k, k);
     max_m0 = std::max(max_m0, p.sd.m0);
+    total += k;
   }
+  int lg = 0;
+  while ((1ll << (lg + 1)) <= total) ++lg;
+  const std::array<int, 3> key{max_m0, tri ? 1 : 0, lg};
+  std::array<int, 2> shape{std::min(4, lhf::eig_max_warps(max_m0)), 128};
   c->begin(5);
   lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
+  auto it = c->eig_tune.find(key);
+  if (it != c->eig_tune.end()) {
+    shape = it->second;
+  } else if (st == LHF_OK && c->autotune && !c->capturing) {
+    st = tune_eig(c, (int)ps.size(), max_k, max_m0, tri, &shape);
+    if (st == LHF_OK) c->eig_tune[key] = shape;
+  }
+  c->last_eig_warps = shape[0];
+  c->last_tri_threads = shape[1];
   if (st == LHF_OK)
     st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream,
-                                 tri),
+                                 tri, shape[0], shape[1]),
                  "eigen kernel");
   c->end(tri ? 3 : 2);
   return st;
@@ -899,6 +975,19 @@ lhf_status lhf_eig_counters(lhf_ctx *c, unsigned long long *passes, unsigned lon
   *passes = h[0];
   *matrices = h[1];
   return st;
+}
+
+lhf_status lhf_set_autotune(lhf_ctx *c, int enable) {
+  if (!c) return LHF_ERR_ARG;
+  c->autotune = enable != 0;
+  return LHF_OK;
+}
+
+lhf_status lhf_launch_shapes(lhf_ctx *c, int *eig_warps, int *tri_threads) {
+  if (!c || !eig_warps || !tri_threads) return LHF_ERR_ARG;
+  *eig_warps = c->last_eig_warps;
+  *tri_threads = c->last_tri_threads;
+  return LHF_OK;
 }
 
 lhf_status lhf_set_profiling(lhf_ctx *c, int enable) {
@@ -1314,6 +1403,7 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
   c->graph_tc = g->tc_dev;
   c->graph_tc_jobs = g->tc_jobs;
   c->graph_tc_off = g->tc_off;
+  c->capturing = true;  // no autotuning (it synchronises) inside the capture
   lhf_status run = c->cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   if (run == LHF_OK) {
     run = run_assembly(c, ps);
@@ -1330,6 +1420,7 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
   c->graph_tc = nullptr;
   c->graph_tc_jobs = 0;
   c->graph_tc_off = 0;
+  c->capturing = false;
   cudaStreamDestroy(cs);
   if (run != LHF_OK) return cleanup(run);
   st = c->cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "cudaGraphInstantiate");

@@ -193,8 +193,17 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
                        cudaStream_t st);  // *passes += kernel launches (may be null)
 // k-point eigensolves; tri: systems carry a tridiagonal scratch (SysDev::tri), and the
 // tridiagonal eigenvalues are taken by a second kernel (else Jacobi inside k_eig).
+// eig_warps: k-points (warps) per CTA of k_eig, 1 .. 8; tri_threads: threads per CTA of the
+// tridiagonal kernel (a multiple of its 16 or 32 lanes per matrix, at most 256).  The two
+// kernels alone (launch_eig_reduce, launch_tridiag) serve the launch-shape autotuner.
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                       unsigned long long *counters, cudaStream_t st, bool tri);
+                       unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps = 4,
+                       int tri_threads = 128);
+cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                              unsigned long long *counters, cudaStream_t st, int warps);
+int eig_max_warps(int max_m0);  // most k_eig warps per CTA whose shared memory fits an SM
+cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                           unsigned long long *counters, cudaStream_t st, int threads);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
 // Separable k-space route (Theorem 2.5): 1D DFTs of the factors (max_factor_ctas =
 // kspace_factor_ctas over the batch) into D.offF, then Hbar / Sbar of every solved k-point and its

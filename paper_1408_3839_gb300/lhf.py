@@ -107,6 +107,8 @@ def load():
             "lhf_potential_factors": (st, [ctx, ctypes.c_int, ctypes.c_void_p]),
             "lhf_gram_factors": (st, [ctx, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _ip]),
             "lhf_set_profiling": (st, [ctx, ctypes.c_int]),
+            "lhf_set_autotune": (st, [ctx, ctypes.c_int]),
+            "lhf_launch_shapes": (st, [ctx, _ip, _ip]),
             "lhf_stage_times": (st, [ctx, _dp, _ip]),
             "lhf_kernel_times": (st, [ctx, _dp, _ip]),
             "lhf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -297,6 +299,15 @@ class Context:
 
     # -- live stage timing -------------------------------------------------------------------
     STAGES = ("basis", "potential", "gram", "ranksum", "dft", "eig", "unused", "upload", "gram_tc")
+
+    def set_autotune(self, enable: bool):
+        self._check(self.lib.lhf_set_autotune(self._h, 1 if enable else 0))
+
+    def launch_shapes(self) -> dict:
+        """Launch shapes of the last k-point solve: k_eig warps per CTA, tridiagonal threads per CTA."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lhf_launch_shapes(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return {"eig_warps": a.value, "tri_threads": b.value}
 
     def set_profiling(self, enable: bool):
         self._check(self.lib.lhf_set_profiling(self._h, 1 if enable else 0))

@@ -240,6 +240,32 @@ def test_live_kernel_times_count_every_launch(ctx, lhf):
         assert ctx.kernel_times()["k_eig"] == (0.0, 0)  # cleared by the previous call
 
 
+def test_autotuned_launch_shapes_change_no_result(lhf):
+    """The eigensolver's launch shapes (tuned on the first batch of a class, or the defaults with
+    the autotuner off) leave every eigenvalue bit for bit the same."""
+    cfgs = [CASES["tube_16_m16"](), CASES["cubic_3"](), CASES["tube_9_m5_odd"]()]
+    out = []
+    for tune in (False, True):
+        c = lhf.Context(0)
+        c.set_autotune(tune)
+        n = 0
+        for cf in cfgs:
+            c.setup(cf)
+            s = c.query_sizes()
+            n += s["n_kpoints"] * s["m0"]
+        eig = dev((n,))
+        c.bloch_spectra(cfgs, eig, None, lhf.MIXED)
+        c.bloch_spectra(cfgs, eig, None, lhf.MIXED)  # the second call uses the tuned shapes
+        c.sync()
+        shapes = c.launch_shapes()
+        assert 1 <= shapes["eig_warps"] <= 8 and shapes["tri_threads"] in (32, 64, 128, 256)
+        if not tune:
+            assert shapes == {"eig_warps": 4, "tri_threads": 128}
+        out.append(eig.cpu().numpy())
+        c.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_host_entry_point_matches_device_entry_point(ctx):
     cfgs = [CASES["tube_16_m16"](), CASES["tube_9_m5_odd"]()]
     n = 0
