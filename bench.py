@@ -137,8 +137,10 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
     multiple of 64 (tensor-pipe work; "algorithmic_flops" keeps the FP64 count).  k_gram_slice:
     bytes of the digit planes and exponents it writes.  k_ranksum: (4 R_tot + 12) per window
     entry.  k_dft_pass: read 2 real blocks, write 2 complex blocks per lattice block, per level.
-    k_eig: per solved matrix 9.33 m^3 (Cholesky and two triangular solves, complex) + 8 m^3
-    (Householder reduction to real tridiagonal form).  k_tridiag_eig: 8 m flops per FP64
+    k_eig: per solved matrix 9.33 m^3 (Cholesky m^3/6 and two triangular solves m^3/2 each, in
+    complex multiply-adds of 8 flops) + 5.33 m^3 (Householder reduction to real tridiagonal form:
+    per column a Hermitian matrix-vector product and a rank-2 update of the lower triangle, 2 n^2
+    complex multiply-adds for a trailing block of order n).  k_tridiag_eig: 8 m flops per FP64
     characteristic-polynomial pass (the minors and their derivatives; its FP32 bisection is not
     counted).  `passes` and `matrices` are per step."""
     gram = tc = tc_alg = slice_bytes = rank = dft_bytes = 0.0
@@ -163,7 +165,7 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
         "k_gram_slice": {"bound": "hbm", "work": slice_bytes},
         "k_ranksum": {"bound": "alu", "work": rank},
         "k_dft_pass": {"bound": "hbm", "work": dft_bytes, "launches_per_step": max(levels, 1)},
-        "k_eig": {"bound": "alu", "work": matrices * 17.33 * m ** 3},
+        "k_eig": {"bound": "alu", "work": matrices * (28.0 / 3.0 + 16.0 / 3.0) * m ** 3},
         "k_tridiag_eig": {"bound": "alu", "work": passes * 8.0 * m},
     }
 
