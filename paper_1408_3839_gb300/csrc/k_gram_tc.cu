@@ -13,15 +13,16 @@
 // (its one rounding, 2^-53 of the scale, is far below the truncation of the dropped pairs) and is
 // converted to FP64 once.
 //
-// One CTA of 128 threads per (system, direction, 128-row tile, 64-column tile):
+// One CTA of 256 threads per (system, direction, 128-row tile, 64-column tile):
 //   * TMA (cp.async.bulk.tensor.2d, 128-byte swizzle, no multicast) brings, per 64-wide K chunk,
 //     the 7 digit planes of the A tile (7 x 128 x 64 BF16) and of the B tile (7 x 64 x 64) into
 //     shared memory (168 KB, one stage);
 //   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 64, K = 16) for every
 //     pair (a, b) into the TMEM accumulator of its diagonal s = a + b (7 x 64 columns of the
 //     512 allocated), then tcgen05.commit to an mbarrier;
-//   * the 4 warps read their 32 TMEM lanes back with tcgen05.ld (32x32b), recombine the 7
-//     diagonals and store the FP64 results in the layout of the FP64 route.
+//   * the 8 warps read the accumulators back with tcgen05.ld (32x32b; warp w reads TMEM lanes
+//     32 (w % 4) .. + 31, warps w and w + 4 half of the columns each), recombine the 7 diagonals
+//     and store the FP64 results in the layout of the FP64 route.
 // Every mbarrier wait is bounded (~1 s of clock cycles); on time-out the CTA sets kFlagTimeout,
 // waits (bounded) for its outstanding operations, frees its TMEM and returns.
 #include <cuda.h>
@@ -35,7 +36,7 @@
 namespace lhf {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 read TMEM lane quadrant w % 4, half the columns each
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
 constexpr int kChunkK = 64;  // one 128-byte swizzle atom of BF16
@@ -194,12 +195,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (ok_sh) {
-    const int row = job.row0 + warp * 32 + lane;
+    const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad .. 32 quad + 31; column half
+    const int row = job.row0 + quad * 32 + lane;
     const int mm = P.m0 * P.m0;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     const int er = row < P.rows ? P.rowexp[row] : 0;
     double *Crow = P.C + (int64_t)(row / mm) * (P.Rt + 2) * mm + (row % mm);
-    for (int cc = 0; cc < kTileN / 16; ++cc) {
+    for (int cc = half * (kTileN / 32); cc < (half + 1) * (kTileN / 32); ++cc) {
       uint32_t v[kSlices][16];
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) tmem_ld16(tmem + lane_base + (uint32_t)(s * kTileN + cc * 16), v[s]);
