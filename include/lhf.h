@@ -204,6 +204,17 @@ lhf_status lhf_k_point_eigensolve(lhf_ctx *ctx, const double *Hbar, const double
 lhf_status lhf_k_point_eigenvectors(lhf_ctx *ctx, const double *Hbar, const double *Sbar, double *eig,
                                     double *vecs, int *k_status);
 
+/* Bloch orbitals on the grid (eq. (6.8) expanded in the basis, eq. (3.14)): for k-point kappa
+ * (host [3], 0 <= kappa_l < L_l) and Bloch vectors coef (device, complex [norb][m0], e.g. rows of
+ * lhf_k_point_eigenvectors), the values on the grid window lo[l] .. lo[l] + cnt[l] - 1 (host [3])
+ * of psi(x) = (L0 L1 L2)^{-1/2} sum_p exp(2 pi i kappa . p / L) sum_mu coef_mu phi_mu(x - p b),
+ * summed over all lattice cells p, in the rank-m0 separable form
+ * sum_mu coef_mu prod_l Bl_mu(i_l) with Bl_mu(i) = sum_p exp(2 pi i kappa_l p / L_l) g_mu^l(i - p n_c).
+ * out: device, complex interleaved [norb][cnt0][cnt1][cnt2].  Periodic lattices only.  With
+ * coef S-normalised the orbital has unit norm in the P1 mass inner product of the grid. */
+lhf_status lhf_bloch_orbitals(lhf_ctx *ctx, const int *kappa, int norb, const double *coef, const int *lo,
+                              const int *cnt, double *out);
+
 /* Generalized symmetric-definite eigenvalues of dense N x N matrices (open box, Table 4.1's
  * full eigensolver): H x = lambda S x.  Device pointers; eig [N] ascending. */
 lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, int N, double *eig);

@@ -3,8 +3,9 @@
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this package.  It shares no code with the CUDA library: the arithmetic lives in
 ``lhf_oracle.c`` (compiled with gcc, loaded through ctypes), except for the Bloch eigenvectors
-(``k_point_eigenvectors``, ``lattice_eigenvector``) and the separable k-space route
-(``kspace_blocks``), written here in numpy; the rest of this module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each
+(``k_point_eigenvectors``, ``lattice_eigenvector``), the Bloch orbitals on the grid
+(``bloch_orbital``, ``p1_mass_matrix``) and the separable k-space route (``kspace_blocks``),
+written here in numpy; the rest of this module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each
 function follows.
 """
 
@@ -387,6 +388,34 @@ def lattice_eigenvector(u: np.ndarray, kappa, L) -> np.ndarray:
     p0, p1, p2 = np.meshgrid(np.arange(L[0]), np.arange(L[1]), np.arange(L[2]), indexing="ij")
     ph = np.exp(2j * np.pi * (kappa[0] * p0 / L[0] + kappa[1] * p1 / L[1] + kappa[2] * p2 / L[2]))
     return (ph.reshape(-1, 1) * np.asarray(u)[None, :]).reshape(-1) / np.sqrt(L[0] * L[1] * L[2])
+
+
+def bloch_orbital(cfg, kappa, u, lo, cnt) -> np.ndarray:
+    """Values of the Bloch orbital psi(x) = N^-1/2 sum_p exp(2 pi i kappa . p / L) sum_mu u_mu
+    phi_mu(x - p b) (eq. (6.8) expanded in the basis, eq. (3.14)) on the grid window
+    lo[l] .. lo[l] + cnt[l] - 1, complex [cnt0, cnt1, cnt2]: the sum over every lattice cell p
+    of the translated (periodised) basis functions, each a product of its 1D samples."""
+    s = _sys(cfg)
+    L = [int(v) for v in s.cfg["L"]]
+    win = []
+    for l in range(3):
+        win.append(np.stack([basis_samples(s, l, p)[:, lo[l]:lo[l] + cnt[l]] for p in range(L[l])]))
+    u = np.asarray(u, dtype=np.complex128)
+    psi = np.zeros(tuple(int(c) for c in cnt), dtype=np.complex128)
+    for p0 in range(L[0]):
+        for p1 in range(L[1]):
+            for p2 in range(L[2]):
+                ph = np.exp(2j * np.pi * (kappa[0] * p0 / L[0] + kappa[1] * p1 / L[1] + kappa[2] * p2 / L[2]))
+                psi += ph * np.einsum("m,mi,mj,mk->ijk", u, win[0][p0], win[1][p1], win[2][p2], optimize=True)
+    return psi / np.sqrt(L[0] * L[1] * L[2])
+
+
+def p1_mass_matrix(n: int, h: float, periodic: bool) -> np.ndarray:
+    """The 1D P1 mass matrix (h / 6) tridiag(1, 4, 1) (Sec. 3.4), circulant when periodic."""
+    M = np.diag(np.full(n, 4.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    if periodic and n > 2:
+        M[0, -1] = M[-1, 0] = 1.0
+    return M * (h / 6.0)
 
 
 def bloch_spectrum(cfg):

@@ -1512,6 +1512,47 @@ lhf_status lhf_basis_factors(lhf_ctx *c, int l, double *G) {
                  "cudaMemcpy2DAsync");
 }
 
+lhf_status lhf_bloch_orbitals(lhf_ctx *c, const int *kappa, int norb, const double *coef, const int *lo,
+                              const int *cnt, double *out) {
+  if (!c) return LHF_ERR_ARG;
+  if (!kappa || !coef || !lo || !cnt || !out || norb < 1)
+    return c->fail(LHF_ERR_ARG, "kappa, coef, lo, cnt, out and norb >= 1 are required");
+  std::vector<Plan> ps(1);
+  lhf_status st = current_plan(c, ps[0]);
+  if (st != LHF_OK) return st;
+  Plan &P = ps[0];
+  if (P.sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "Bloch orbitals need a periodic lattice");
+  int maxcnt = 0, maxL = 1;
+  long long npts = 1;
+  for (int l = 0; l < 3; ++l) {
+    const DirDev &D = P.sd.d[l];
+    if (kappa[l] < 0 || kappa[l] >= D.L) return c->fail(LHF_ERR_ARG, "kappa[%d] = %d outside [0, %d)", l, kappa[l], D.L);
+    if (lo[l] < 0 || cnt[l] < 1 || (long long)lo[l] + cnt[l] > D.n)
+      return c->fail(LHF_ERR_ARG, "direction %d: nodes [%d, %d + %d) outside [0, %d)", l, lo[l], lo[l], cnt[l], D.n);
+    maxcnt = std::max(maxcnt, cnt[l]);
+    maxL = std::max(maxL, D.L);
+    npts *= cnt[l];
+  }
+  if (npts * norb > (1ll << 31)) return c->fail(LHF_ERR_ARG, "too many output values");
+  const size_t boff = P.ws;
+  st = ensure_ws(c, boff + align_up((size_t)6 * P.sd.m0 * maxcnt));
+  if (st != LHF_OK) return st;
+  bind_ws(P, c->ws);
+  st = upload(c, {P.sd});
+  if (st != LHF_OK) return st;
+  for (int l = 0; l < 3; ++l) {  // rows zero outside the support windows the basis kernel writes
+    const DirDev &D = P.sd.d[l];
+    st = c->cuda(cudaMemsetAsync(c->ws + D.offG, 0, sizeof(double) * (size_t)P.sd.m0 * (D.n + D.gext), c->stream),
+                 "cudaMemsetAsync");
+    if (st != LHF_OK) return st;
+  }
+  st = c->cuda(lhf::launch_basis(c->d_sys, 1, P.basis_items, c->stream), "basis kernel");
+  if (st != LHF_OK) return st;
+  return c->cuda(lhf::launch_orbitals(c->d_sys, kappa, lo, cnt, norb, coef, c->ws + boff, out, P.sd.m0, maxL,
+                                      c->stream),
+                 "orbital kernels");
+}
+
 lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
   if (!c) return LHF_ERR_ARG;
   if (l < 0 || l > 2 || !V) return c->fail(LHF_ERR_ARG, "direction 0..2 and an output pointer are required");

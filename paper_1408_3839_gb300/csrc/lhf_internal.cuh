@@ -211,6 +211,12 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
 // from their partners.
 int kspace_factor_ctas(const SysDev &s);
 cudaError_t launch_kspace(const SysDev *sys, int nsys, int max_factor_ctas, long long max_items, cudaStream_t st);
+// Bloch orbitals on a window of the grid: kappa, lo, cnt host [3]; coef device complex
+// [norb][m0]; B device scratch of 6 m0 max(cnt) doubles; out device complex [norb][cnt0][cnt1]
+// [cnt2].  The basis samples of the (single) system must be in its workspace, zero outside the
+// support windows.  maxL: the largest L_l.
+cudaError_t launch_orbitals(const SysDev *sys, const int *kappa, const int *lo, const int *cnt, int norb,
+                            const double *coef, double *B, double *out, int m0, int maxL, cudaStream_t st);
 // Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
 // the dense matrices (thread per entry).
 size_t box_gram_smem_bytes(int max_width);

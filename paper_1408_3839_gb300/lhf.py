@@ -98,6 +98,7 @@ def load():
             "lhf_assemble_core_hamiltonian": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_circulant_fft": (st, [ctx] + [ctypes.c_void_p] * 4),
             "lhf_kspace_blocks": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+            "lhf_bloch_orbitals": (st, [ctx, _ip, ctypes.c_int, ctypes.c_void_p, _ip, _ip, ctypes.c_void_p]),
             "lhf_k_point_eigensolve": (st, [ctx] + [ctypes.c_void_p] * 4),
             "lhf_k_point_eigenvectors": (st, [ctx] + [ctypes.c_void_p] * 5),
             "lhf_dense_eigensolve": (st, [ctx, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -251,6 +252,14 @@ class Context:
     # -- path --------------------------------------------------------------------------------
     def assemble_core_hamiltonian(self, H, S, precision: int = FP64):
         self._check(self.lib.lhf_assemble_core_hamiltonian(self._h, precision, _ptr(H), _ptr(S)))
+
+    def bloch_orbitals(self, kappa, coef, lo, cnt, out):
+        """lhf_bloch_orbitals: coef device complex [norb][m0][2]; out device [norb][cnt0][cnt1][cnt2][2]."""
+        k = (ctypes.c_int * 3)(*[int(v) for v in kappa])
+        a = (ctypes.c_int * 3)(*[int(v) for v in lo])
+        b = (ctypes.c_int * 3)(*[int(v) for v in cnt])
+        norb = int(coef.shape[0]) if hasattr(coef, "shape") else 1
+        self._check(self.lib.lhf_bloch_orbitals(self._h, k, norb, _ptr(coef), a, b, _ptr(out)))
 
     def kspace_blocks(self, Hbar, Sbar, precision: int = FP64):
         self._check(self.lib.lhf_kspace_blocks(self._h, int(precision), _ptr(Hbar), _ptr(Sbar)))

@@ -227,3 +227,42 @@ def test_full_size_tube_256_eigenvectors(ctx, oracle_mod, lhf):
     v = vecs.cpu().numpy()
     compare_with_oracle(eig.cpu().numpy(), v[..., 0] + 1j * v[..., 1], ks.cpu().numpy(), oracle_mod,
                         hb[..., 0] + 1j * hb[..., 1], sb[..., 0] + 1j * sb[..., 1])
+
+
+@pytest.mark.parametrize("name,kappas,lo,cnt", [
+    ("tube_9_m5_odd", [(0, 0, 0), (2, 0, 0), (4, 0, 0)], (0, 0, 0), None),
+    ("cubic_3", [(1, 0, 2), (0, 0, 0)], (3, 5, 7), (20, 9, 11)),
+    ("tube_256", [(5, 0, 0), (128, 0, 0)], (1000, 100, 120), (200, 8, 8)),
+])
+def test_bloch_orbitals_on_the_grid(ctx, oracle_mod, name, kappas, lo, cnt):
+    cfg = W.tube_256(3000) if name == "tube_256" else CASES[name]()
+    ctx.setup(cfg)
+    Hj, Sj = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(Hj), oracle_mod.block_dft(Sj)
+    eig, vecs, ks = gpu_vectors(ctx, Hb, Sb)
+    cnt = tuple(cfg["n"]) if cnt is None else cnt
+    Lt = cfg["L"]
+    for kap in kappas:
+        k = np.ravel_multi_index(kap, Lt)
+        rows = vecs[k, :3]
+        coef = torch.from_numpy(np.ascontiguousarray(np.stack([rows.real, rows.imag], -1))).cuda()
+        out = torch.empty((3,) + tuple(cnt) + (2,), dtype=torch.float64, device="cuda")
+        ctx.bloch_orbitals(kap, coef, lo, cnt, out)
+        ctx.sync()
+        got = out.cpu().numpy()
+        got = got[..., 0] + 1j * got[..., 1]
+        for r in range(3):
+            ref = oracle_mod.bloch_orbital(cfg, kap, rows[r], lo, cnt)
+            assert np.abs(got[r] - ref).max() <= 1e-12 * np.abs(ref).max(), (kap, r)
+
+
+def test_bloch_orbitals_reject_bad_windows(ctx, lhf):
+    cfg = CASES["tube_9_m5_odd"]()
+    ctx.setup(cfg)
+    coef = torch.zeros((1, 5, 2), dtype=torch.float64, device="cuda")
+    out = torch.empty((1, 4, 4, 4, 2), dtype=torch.float64, device="cuda")
+    for kap, lo, cnt in [((9, 0, 0), (0, 0, 0), (4, 4, 4)), ((0, 0, 0), (178, 0, 0), (4, 4, 4)),
+                         ((0, 0, 0), (0, 0, 0), (0, 4, 4))]:
+        with pytest.raises(lhf.LhfError) as ei:
+            ctx.bloch_orbitals(kap, coef, lo, cnt, out)
+        assert ei.value.status == lhf.LHF_ERR_ARG

@@ -103,3 +103,28 @@ def test_removed_functions_have_zero_components(oracle_mod):
     _, st_ref = oracle_mod.k_point_eigenvalues(Hb, Sb)
     assert st[1] == 1 and np.array_equal(st, st_ref)
     assert np.all(vecs[1, :, 2] == 0) and np.all(vecs[1, 3] == 0) and np.isinf(eig[1, 3])
+
+
+def test_bloch_orbital_is_normalised_and_bloch_periodic(oracle_mod):
+    # the orbital of an S-normalised Bloch vector has unit norm in the P1 mass inner product of the
+    # whole grid (the Galerkin overlap that Sbar transforms), and psi(x + b) = exp(2 pi i kappa / L) psi(x)
+    cfg = W.tube(9, seed=14, n_c=20, n_perp=48, half_width=6.0, M0=1, m0_s=2, m0_pshell=1, lo=0.2, hi=9.0)
+    Hj, Sj = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(Hj), oracle_mod.block_dft(Sj)
+    eig, vecs, st = oracle_mod.k_point_eigenvectors(Hb, Sb)
+    n, h, L = cfg["n"], cfg["h"], cfg["L"]
+    M = [oracle_mod.p1_mass_matrix(n[l], h[l], bool(cfg["periodic"][l])) for l in range(3)]
+    for k, r in [(0, 0), (2, 1), (4, 3)]:
+        psi = oracle_mod.bloch_orbital(cfg, (k, 0, 0), vecs[k, r], (0, 0, 0), n)
+        Mpsi = np.einsum("ai,ijk->ajk", M[0], psi)
+        Mpsi = np.einsum("bj,ajk->abk", M[1], Mpsi)
+        Mpsi = np.einsum("ck,abk->abc", M[2], Mpsi)
+        norm = np.vdot(psi, Mpsi)
+        assert abs(norm - 1.0) < 1e-10, (k, r, norm)
+        # two different eigenvectors of one k-point are orthogonal in the same inner product
+        phi = oracle_mod.bloch_orbital(cfg, (k, 0, 0), vecs[k, r + 1], (0, 0, 0), n)
+        assert abs(np.vdot(phi, Mpsi)) < 1e-10
+        # Bloch periodicity along the lattice direction
+        nc = cfg["n_cell"][0]
+        ph = np.exp(2j * np.pi * k / L[0])
+        assert np.abs(psi[nc:] - ph * psi[:-nc]).max() < 1e-12 * np.abs(psi).max()
