@@ -180,6 +180,72 @@ class _Desc:
         self.system = lhf_system_desc(lat, bas, grd)
 
 
+def _np_dtype(ct) -> np.dtype:
+    """numpy structured dtype with the exact layout of a ctypes structure (pointers as uint64)."""
+    names, formats, offsets = [], [], []
+    for fname, ftype in ct._fields_:
+        if hasattr(ftype, "_fields_"):
+            fmt = _np_dtype(ftype)
+        elif hasattr(ftype, "_length_"):
+            fmt = (np.float64 if ftype._type_ is ctypes.c_double else np.int32, (ftype._length_,))
+        elif ftype is ctypes.c_double:
+            fmt = np.float64
+        elif ftype is ctypes.c_int:
+            fmt = np.int32
+        else:  # pointers
+            fmt = np.uint64
+        names.append(fname)
+        formats.append(fmt)
+        offsets.append(getattr(ct, fname).offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(ct)})
+
+
+_SYSTEM_DTYPE = None
+
+
+class _Batch:
+    """An array of lhf_system_desc for many workload dictionaries, filled column by column in one
+    numpy structured array (its per-system host arrays packed into two buffers it keeps alive)."""
+
+    def __init__(self, cfgs):
+        global _SYSTEM_DTYPE
+        if _SYSTEM_DTYPE is None:
+            _SYSTEM_DTYPE = _np_dtype(lhf_system_desc)
+        n = len(cfgs)
+        arr = np.zeros(n, dtype=_SYSTEM_DTYPE)
+        lat, bas, grd = arr["lattice"], arr["basis"], arr["grid"]
+        for fld in ("L", "b", "periodic", "K_sum"):
+            lat[fld] = [c[fld] for c in cfgs]
+        lat["M0"] = [len(c["Z"]) for c in cfgs]
+        m0 = np.array([len(c["alpha"]) for c in cfgs], dtype=np.int64)
+        bas["m0"] = m0
+        bas["rho"] = [c["rho"] for c in cfgs]
+        for fld in ("n", "n_cell", "h", "x0", "cell0", "R", "u0", "du"):
+            grd[fld] = [c[fld] for c in cfgs]
+        # doubles per system: Z, a (flattened), alpha, centre (flattened), Z_cell (flattened, optional)
+        parts = []
+        for c in cfgs:
+            zc = c.get("Z_cell")
+            parts += [c["Z"], [v for r in c["a"] for v in r], c["alpha"], [v for r in c["centre"] for v in r],
+                      [] if zc is None else [v for r in zc for v in r]]
+        lens = np.array([len(p) for p in parts], dtype=np.int64).reshape(n, 5)
+        self.dbuf = np.array([v for p in parts for v in p], dtype=np.float64)
+        self.ibuf = np.array([v for c in cfgs for v in c["kind"]], dtype=np.int32)
+        start = np.concatenate([[0], np.cumsum(lens.ravel())[:-1]]).reshape(n, 5)
+        addr = (start * 8 + self.dbuf.ctypes.data).astype(np.uint64)
+        lat["Z"] = addr[:, 0]
+        lat["a"] = addr[:, 1]
+        bas["alpha"] = addr[:, 2]
+        bas["centre"] = addr[:, 3]
+        lat["Z_cell"] = np.where(lens[:, 4] > 0, addr[:, 4], 0).astype(np.uint64)
+        bas["kind"] = (np.concatenate([[0], np.cumsum(m0)[:-1]]) * 4 + self.ibuf.ctypes.data).astype(np.uint64)
+        self.arr = arr
+        self.count = n
+
+    def ptr(self):
+        return self.arr.ctypes.data_as(ctypes.POINTER(lhf_system_desc))
+
+
 class Context:
     """One lhf_ctx on one device and stream (torch.cuda stream or raw cudaStream_t)."""
 
@@ -279,30 +345,30 @@ class Context:
 
     @staticmethod
     def _systems(cfgs):
-        descs = [_Desc(c) for c in cfgs]
-        arr = (lhf_system_desc * len(descs))(*[d.system for d in descs])
-        return descs, arr
+        """(keep-alive object, pointer to the lhf_system_desc array) for a list of workloads."""
+        batch = _Batch(cfgs)
+        return batch, batch.ptr()
 
     def bloch_spectra(self, cfgs, eig, k_status=None, precision: int = FP64):
-        descs, arr = self._systems(cfgs)
-        self._check(self.lib.lhf_bloch_spectra(self._h, len(descs), arr, precision, _ptr(eig), _ptr(k_status)))
+        batch, arr = self._systems(cfgs)
+        self._check(self.lib.lhf_bloch_spectra(self._h, batch.count, arr, precision, _ptr(eig), _ptr(k_status)))
 
     def bloch_spectra_host(self, cfgs, eig_host: np.ndarray, k_status_host: np.ndarray | None = None,
                            precision: int = FP64):
         assert eig_host.dtype == np.float64 and eig_host.flags["C_CONTIGUOUS"]
-        descs, arr = self._systems(cfgs)
+        batch, arr = self._systems(cfgs)
         kp = None
         if k_status_host is not None:
             assert k_status_host.dtype == np.int32 and k_status_host.flags["C_CONTIGUOUS"]
             kp = k_status_host.ctypes.data
-        self._check(self.lib.lhf_bloch_spectra_host(self._h, len(descs), arr, precision,
+        self._check(self.lib.lhf_bloch_spectra_host(self._h, batch.count, arr, precision,
                                                     eig_host.ctypes.data, kp))
 
     def graph_create(self, cfgs, eig, k_status=None, precision: int = FP64) -> "Graph":
         """lhf_graph_create: the batched path captured once into a CUDA graph."""
-        descs, arr = self._systems(cfgs)
+        batch, arr = self._systems(cfgs)
         h = ctypes.c_void_p()
-        self._check(self.lib.lhf_graph_create(self._h, len(descs), arr, precision, _ptr(eig), _ptr(k_status),
+        self._check(self.lib.lhf_graph_create(self._h, batch.count, arr, precision, _ptr(eig), _ptr(k_status),
                                               ctypes.byref(h)))
         return Graph(self, h, (eig, k_status))
 

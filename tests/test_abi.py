@@ -52,3 +52,32 @@ def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(B, "HERE", str(tmp_path))
     with pytest.raises(RuntimeError, match="no CPU path"):
         B.load()
+
+
+def test_batched_descriptors_match_single_descriptors():
+    """The vectorised descriptor array (binding) carries the same values as the per-system ctypes
+    descriptors: scalar fields byte for byte, and the pointed-to host arrays element for element."""
+    import numpy as np
+
+    import lhf_workloads as W
+    import paper_1408_3839_gb300.lhf as B
+
+    cfgs = [W.tube_256(3000), W.box_64(L=4, n_perp=64), W.cubic_32(seed=15, L=3, n_c=10), W.periodic_8()]
+    batch = B._Batch(cfgs)
+    arr = ctypes.cast(batch.ptr(), ctypes.POINTER(B.lhf_system_desc * len(cfgs))).contents
+    for cfg, got in zip(cfgs, arr):
+        ref = B._Desc(cfg).system
+        assert bytes(got.grid) == bytes(ref.grid)
+        for f in ("L", "b", "periodic", "K_sum"):
+            assert list(getattr(got.lattice, f)) == list(getattr(ref.lattice, f))
+        assert got.lattice.M0 == ref.lattice.M0 and got.basis.m0 == ref.basis.m0 and got.basis.rho == ref.basis.rho
+        M0, m0 = ref.lattice.M0, ref.basis.m0
+        for name, n in (("Z", M0), ("a", 3 * M0)):
+            assert [getattr(got.lattice, name)[i] for i in range(n)] == [getattr(ref.lattice, name)[i] for i in range(n)]
+        for name, n in (("kind", m0), ("alpha", m0), ("centre", 3 * m0)):
+            assert [getattr(got.basis, name)[i] for i in range(n)] == [getattr(ref.basis, name)[i] for i in range(n)]
+        if cfg.get("Z_cell") is None:
+            assert not bool(got.lattice.Z_cell)
+        else:
+            n = len(cfg["Z_cell"]) * M0
+            assert [got.lattice.Z_cell[i] for i in range(n)] == list(np.ravel(cfg["Z_cell"]))
