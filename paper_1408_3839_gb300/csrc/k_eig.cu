@@ -56,6 +56,31 @@ __device__ __forceinline__ double2 cfms_conj(double2 a, double2 b, double2 acc) 
   return acc;
 }
 
+// The lanes that solve one matrix: G = 32 (a whole warp) or G = 16 (half a warp, two matrices
+// per warp, used when every order is at most 16: the scalar steps of a factorisation -- pivots,
+// norms, reciprocals -- then cost one FP64 warp instruction per two matrices).  Every
+// collective (shuffle, ballot, vote, syncwarp) runs over the group's own lanes only, so the two
+// groups of a warp may follow different paths.
+template <int G>
+struct Grp {
+  unsigned mask;  // the group's lanes within the warp
+  int lane;       // lane within the group
+  int base;       // first warp lane of the group
+  __device__ Grp() {
+    const int wl = (int)(threadIdx.x & 31);
+    base = wl & ~(G - 1);
+    lane = wl - base;
+    mask = G == 32 ? 0xffffffffu : (0xffffu << base);
+  }
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+  __device__ __forceinline__ double sum(double v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+  }
+  __device__ __forceinline__ unsigned ballot(bool p) const { return __ballot_sync(mask, p) >> base; }
+};
+
 // per warp: A, B, V (m^2 complex each), rotation table (16 x {c, sr, si, p, q}), kept index
 // map, scales and overlap eigenvalues (32 each), the (k1 < k2) pair-block table (120 x 2) and the
 // Householder vectors (2 x 32 complex)
@@ -87,20 +112,22 @@ __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -
 // by one lane each, and the mirrored block written as the conjugate transpose.  With V
 // non-null the rotations are also accumulated into V's columns (V <- V J).  Stops when the
 // off-diagonal Frobenius norm falls below 1e-16 of the total.  Returns the sweeps.
-__device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab &R) {
+template <int G>
+__device__ int jacobi_herm(double2 *A, double2 *V, int m, const Grp<G> &g, const RotTab &R) {
+  const int lane = g.lane;
   const int mm = m * m, mp = m + (m & 1), npair = mp / 2;
   const int nblk = npair * (npair - 1) / 2;
   int sweep = 0;
   for (; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
-    for (int e = lane; e < mm; e += 32) {
+    for (int e = lane; e < mm; e += G) {
       const double v = A[e].x * A[e].x + A[e].y * A[e].y;
       tot += v;
       if (e / m != e - (e / m) * m) off += v;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(g.mask, off, o);
+      tot += __shfl_xor_sync(g.mask, tot, o);
     }
     if (off <= 1e-32 * tot) break;
     for (int step = 0; step < mp - 1; ++step) {
@@ -138,8 +165,8 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
         R.sr[lane] = sr;
         R.si[lane] = si;
       }
-      __syncwarp();
-      for (int bi = lane; bi < nblk; bi += 32) {
+      g.sync();
+      for (int bi = lane; bi < nblk; bi += G) {
         const int k1 = R.blk[2 * bi], k2 = R.blk[2 * bi + 1];
         const bool r1 = !(R.sr[k1] == 0.0 && R.si[k1] == 0.0), r2 = !(R.sr[k2] == 0.0 && R.si[k2] == 0.0);
         if (!r1 && !r2) continue;
@@ -177,7 +204,7 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
       }
       if (V) {
         const int work = npair * m;
-        for (int it = lane; it < work; it += 32) {  // V <- V J
+        for (int it = lane; it < work; it += G) {  // V <- V J
           const int k = it / m, r = it - (it / m) * m;
           const int p = R.p[k], q = R.q[k];
           if (q >= m || (R.sr[k] == 0.0 && R.si[k] == 0.0)) continue;
@@ -188,7 +215,7 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
           V[r * m + q] = cadd(cmul(se, x), cscale(y, c));
         }
       }
-      __syncwarp();
+      g.sync();
     }
   }
   return sweep;
@@ -202,14 +229,16 @@ __device__ int jacobi_herm(double2 *A, double2 *V, int m, int lane, const RotTab
 // the matrix-vector product takes two lanes per row.  The off-diagonal alpha_k is replaced by
 // |alpha_k| (a diagonal unitary similarity).  td[0..m), te[0..m-1) receive the diagonal and
 // off-diagonal.  vw: 2 x 32 complex scratch.
-__device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, double *td, double *te) {
+template <int G>
+__device__ void householder_tridiag(double2 *A, int m, const Grp<G> &g, double2 *vw, double *td, double *te) {
+  const int lane = g.lane;
   double2 *vec = vw, *wv = vw + 32;
   for (int k = 0; k + 2 < m; ++k) {
     const int n = m - k - 1;
     double2 xi = make_double2(0.0, 0.0);
     if (lane < n) xi = A[(k + 1 + lane) * m + k];
     double part = xi.x * xi.x + xi.y * xi.y;
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(g.mask, part, o);
     const double sig = part;
     const double2 x0 = A[(k + 1) * m + k];
     const double akk = A[k * m + k].x;
@@ -228,36 +257,39 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
     const double2 ph = a2 > 0.0 ? make_double2(x0.x * ra, x0.y * ra) : make_double2(1.0, 0.0);
     const double tau = 1.0 / fma(nrm, ax0, sig);
     if (lane < n) vec[lane] = lane == 0 ? make_double2(x0.x + ph.x * nrm, x0.y + ph.y * nrm) : xi;
-    __syncwarp();
-    // p = tau B v, B = A[k+1:, k+1:] from its lower triangle, two lanes per row
+    g.sync();
+    // p = tau B v, B = A[k+1:, k+1:] from its lower triangle, RL = G / 16 lanes per row
+    constexpr int RL = G / 16;
     const double2 *Bt = A + (k + 1) * m + (k + 1);
     double kp = 0.0;
     for (int r0 = 0; r0 < n; r0 += 16) {
-      const int r = r0 + (lane >> 1);
+      const int r = r0 + lane / RL;
       double2 pi = make_double2(0.0, 0.0);
       if (r < n) {
-        for (int j = lane & 1; j < n; j += 2) {
+        for (int j = lane % RL; j < n; j += RL) {
           double2 b = j <= r ? Bt[r * m + j] : Bt[j * m + r];
           if (j > r) b.y = -b.y;
           pi = cfma(b, vec[j], pi);
         }
       }
-      pi.x += __shfl_xor_sync(0xffffffffu, pi.x, 1);
-      pi.y += __shfl_xor_sync(0xffffffffu, pi.y, 1);
-      if (r < n && (lane & 1) == 0) {
+      if (RL == 2) {
+        pi.x += __shfl_xor_sync(g.mask, pi.x, 1);
+        pi.y += __shfl_xor_sync(g.mask, pi.y, 1);
+      }
+      if (r < n && lane % RL == 0) {
         pi = cscale(pi, tau);
         wv[r] = pi;
         kp += vec[r].x * pi.x + vec[r].y * pi.y;  // Re(conj(v_r) p_r)
       }
     }
     // K = (tau / 2) Re(v^H p)
-    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+    for (int o = G / 2; o > 0; o >>= 1) kp += __shfl_xor_sync(g.mask, kp, o);
     const double Kf = 0.5 * tau * kp;
-    __syncwarp();
+    g.sync();
     if (lane < n) wv[lane] = make_double2(wv[lane].x - Kf * vec[lane].x, wv[lane].y - Kf * vec[lane].y);
-    __syncwarp();
+    g.sync();
     // lower triangle (i >= j) of the trailing block: a -= v_i conj(w_j) + w_i conj(v_j)
-    for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+    for (int t = lane; t < n * (n + 1) / 2; t += G) {
       int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= t) ++i;
       while (i * (i + 1) / 2 > t) --i;
@@ -270,7 +302,7 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
       td[k] = akk;
       te[k] = nrm;
     }
-    __syncwarp();
+    g.sync();
   }
   if (lane == 0) {
     if (m >= 2) {
@@ -280,12 +312,14 @@ __device__ void householder_tridiag(double2 *A, int m, int lane, double2 *vw, do
     }
     td[m - 1] = A[(m - 1) * m + (m - 1)].x;
   }
-  __syncwarp();
+  g.sync();
 }
 
 // Hermitian part of a matrix that is Hermitian up to rounding.
-__device__ void hermitian_part(double2 *A, int m, int lane) {
-  for (int e = lane; e < m * m; e += 32) {
+template <int G>
+__device__ void hermitian_part(double2 *A, int m, const Grp<G> &g) {
+  const int lane = g.lane;
+  for (int e = lane; e < m * m; e += G) {
     const int i = e / m, j = e - (e / m) * m;
     if (i < j) {
       const double2 x = A[i * m + j], y = A[j * m + i];
@@ -296,7 +330,7 @@ __device__ void hermitian_part(double2 *A, int m, int lane) {
       A[e].y = 0.0;
     }
   }
-  __syncwarp();
+  g.sync();
 }
 
 // Eigenvectors of the pencil at k-point kap (and, conjugated, at its partner mk) from the
@@ -307,13 +341,15 @@ __device__ void hermitian_part(double2 *A, int m, int lane) {
 // that u^H Sbar u = 1 on the kept block.  Each eigenvector's phase is fixed by making its first
 // component of largest magnitude real and positive.  Row r of vecs[kap] is the eigenvector of
 // the r-th smallest eigenvalue; dropped slots and failed k-points hold zero / NaN rows.
-__device__ void bloch_vectors(const SysDev &s, int kap, int mk, bool ok, bool chol, int m, int mkept, int lane,
+template <int G>
+__device__ void bloch_vectors(const SysDev &s, int kap, int mk, bool ok, bool chol, int m, int mkept, const Grp<G> &g,
                               int vid, double2 *A, const double2 *B, double2 *V, const double *sg, const double *dsc,
                               const int *kidx) {
+  const int lane = g.lane;
   const int m0 = s.m0;
   const double2 *U = V;  // back-transformed columns, row stride m
   if (ok && chol) {
-    const int q = m <= 16 ? 2 : 1;
+    const int q = (G == 32 && m <= 16) ? 2 : 1;
     const int cc = lane / q, part = lane % q;
     const bool act = cc < m;
     double2 z[kMaxM0];
@@ -326,26 +362,26 @@ __device__ void bloch_vectors(const SysDev &s, int kap, int mk, bool ok, bool ch
           acc.y = fma(l.x, z[k].y, fma(-l.y, z[k].x, acc.y));
         }
       if (q == 2) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+        acc.x += __shfl_xor_sync(g.mask, acc.x, 1);
+        acc.y += __shfl_xor_sync(g.mask, acc.y, 1);
       }
       const double2 w = act ? V[i * m + cc] : make_double2(0.0, 0.0);
       z[i] = cscale(csub(w, acc), sg[i]);
     }
-    __syncwarp();
+    g.sync();
     if (act && part == 0)
       for (int i = 0; i < m; ++i) V[i * m + cc] = z[i];
-    __syncwarp();
+    g.sync();
   } else if (ok) {
     // U = X W (mkept x m) into A (its diagonal, the eigenvalues, is already in registers)
-    __syncwarp();
-    for (int e = lane; e < mkept * m; e += 32) {
+    g.sync();
+    for (int e = lane; e < mkept * m; e += G) {
       const int a = e / m, c = e - (e / m) * m;
       double2 acc = make_double2(0.0, 0.0);
       for (int b = 0; b < m; ++b) acc = cfma(B[a * m + b], V[b * m + c], acc);
       A[e] = acc;
     }
-    __syncwarp();
+    g.sync();
     U = A;
   }
   if (lane >= m0) return;
@@ -404,16 +440,20 @@ __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict_
   }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restrict__ sysv,
                                                         unsigned *flags, unsigned long long *counters,
                                                         int max_m0) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // k-point of this warp: the i-th entry of the list of solved k-points (one per conjugate pair)
-  // when the system has one, otherwise warp i takes k-point i and leaves it to its partner if
-  // the partner's index is lower
-  const int widx = blockIdx.x * (int)(blockDim.x >> 5) + warp;
+  const Grp<G> g;
+  const int lane = g.lane;
+  // matrix slot of this group in the CTA (32 / G groups per warp)
+  const int slotm = (int)(threadIdx.x >> 5) * (32 / G) + (int)((threadIdx.x & 31) / G);
+  // k-point of this group: the i-th entry of the list of solved k-points (one per conjugate
+  // pair) when the system has one, otherwise group i takes k-point i and leaves it to its
+  // partner if the partner's index is lower
+  const int widx = blockIdx.x * (int)((blockDim.x >> 5) * (32 / G)) + slotm;
   int kap;
   if (s.klist) {
     if (widx >= s.nkhalf) return;
@@ -428,7 +468,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   if (!s.klist && mk < kap) return;  // the conjugate partner solves this pair
   const int m0 = s.m0;
   extern __shared__ unsigned char smraw[];
-  unsigned char *base = smraw + (size_t)warp * eig_warp_bytes(max_m0);
+  unsigned char *base = smraw + (size_t)slotm * eig_warp_bytes(max_m0);
   double2 *A = reinterpret_cast<double2 *>(base);
   double2 *B = A + max_m0 * max_m0;
   double2 *V = B + max_m0 * max_m0;
@@ -443,7 +483,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   {
     // pairs k1 < k2 ordered by k2, so that the first n (n - 1) / 2 entries are those of n pairs
     const int np = (m0 + 1) / 2;  // pairs of the largest order this warp may rotate
-    for (int bi = lane; bi < np * (np - 1) / 2; bi += 32) {
+    for (int bi = lane; bi < np * (np - 1) / 2; bi += G) {
       int k2 = 1, rem = bi;
       while (rem >= k2) {
         rem -= k2;
@@ -452,7 +492,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       blk[2 * bi] = (unsigned char)rem;
       blk[2 * bi + 1] = (unsigned char)k2;
     }
-    __syncwarp();
+    g.sync();
   }
   const RotTab R{rc, rsr, rsi, rp, rq, blk};
   // FP32 copy of the Cholesky factor (off-diagonal entries, 1 / L_jj on the diagonal), kept in
@@ -472,17 +512,17 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     if (!(norm > 0.0)) ok = false;
     keep = dii > kDropTol * norm;
   }
-  ok = __all_sync(0xffffffffu, ok);
-  const unsigned kmask = __ballot_sync(0xffffffffu, keep);
+  ok = __all_sync(g.mask, ok);
+  const unsigned kmask = g.ballot(keep);
   int m = __popc(kmask);
   if (keep) {
     const int a = __popc(kmask & ((1u << lane) - 1u));
     kidx[a] = lane;
     dsc[a] = 1.0 / sqrt(dii);
   }
-  __syncwarp();
+  g.sync();
   double hf2 = 0.0;  // ||H~||_F^2
-  for (int e = lane; e < m * m; e += 32) {
+  for (int e = lane; e < m * m; e += G) {
     const int a = e / m, b = e - (e / m) * m;
     const int ia = kidx[a], ib = kidx[b];
     const double sc = dsc[a] * dsc[b];
@@ -490,11 +530,11 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     B[e] = cscale(Sb[ia * m0 + ib], sc);
     hf2 += A[e].x * A[e].x + A[e].y * A[e].y;
   }
-  for (int o = 16; o > 0; o >>= 1) hf2 += __shfl_xor_sync(0xffffffffu, hf2, o);
-  __syncwarp();
+  for (int o = G / 2; o > 0; o >>= 1) hf2 += __shfl_xor_sync(g.mask, hf2, o);
+  g.sync();
   // the blocks are Hermitian up to the rounding of the transform: solve their Hermitian parts
-  hermitian_part(A, m, lane);
-  hermitian_part(B, m, lane);
+  hermitian_part(A, m, g);
+  hermitian_part(B, m, g);
 
   // 1. Cholesky of the scaled overlap (lower triangle, in place in B), right-looking: column j
   //    is scaled by its pivot, then the trailing lower triangle is updated by every lane (no
@@ -507,13 +547,13 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       break;
     }
     const double inv = rsqrt(d), ljj = d * inv;  // 1 / L_jj and L_jj
-    __syncwarp();
-    for (int i = j + 1 + lane; i < m; i += 32) {
+    g.sync();
+    for (int i = j + 1 + lane; i < m; i += G) {
       const double2 lij = cscale(B[i * m + j], inv);
       B[i * m + j] = lij;
       L32[i * m + j] = make_float2((float)lij.x, (float)lij.y);
     }
-    __syncwarp();
+    g.sync();
     if (lane == 0) {
       B[j * m + j] = make_double2(ljj, 0.0);
       sg[j] = inv;
@@ -522,7 +562,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     // B[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i < m: the n (n + 1) / 2 entries of the
     // trailing lower triangle, n = m - j - 1, row by row
     const int n = m - j - 1;
-    for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+    for (int t = lane; t < n * (n + 1) / 2; t += G) {
       int i = (int)((sqrt(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // row of the t-th entry
       while ((i + 1) * (i + 2) / 2 <= t) ++i;
       while (i * (i + 1) / 2 > t) --i;
@@ -530,7 +570,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       const int ri = j + 1 + i, rk = j + 1 + k;
       B[ri * m + rk] = cfms_conj(B[ri * m + j], B[rk * m + j], B[ri * m + rk]);
     }
-    __syncwarp();
+    g.sync();
   }
 
   int sweeps = 0;
@@ -543,7 +583,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   //     rejects with a factor 100 to spare; in between the exact FP64 solve decides (step 2).
   bool need64 = false;
   if (ok && chol) {
-    const int q = m <= 16 ? 2 : 1;
+    const int q = (G == 32 && m <= 16) ? 2 : 1;
     const int cc = lane / q, part = lane % q;
     const bool act = cc < m;
     float2 z[kMaxM0];
@@ -559,39 +599,39 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
           acc.y = fmaf(l.y, z[k].x, acc.y);
         }
       if (q == 2) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+        acc.x += __shfl_xor_sync(g.mask, acc.x, 1);
+        acc.y += __shfl_xor_sync(g.mask, acc.y, 1);
       }
       const float di = L32[i * m + i].x;
       z[i] = make_float2(((i == cc ? 1.0f : 0.0f) - acc.x) * di, -acc.y * di);
       if (act && part == 0) tr = fmaf(z[i].x, z[i].x, fmaf(z[i].y, z[i].y, tr));
     }
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    for (int o = G / 2; o > 0; o >>= 1) tr += __shfl_xor_sync(g.mask, tr, o);
     if (!(tr <= 1e6f)) {
       if (tr <= 1e10f)
         need64 = true;
       else
         chol = false;  // also when not finite
     }
-    __syncwarp();
+    g.sync();
   }
   if (ok && chol) {
     // 2. C = L^{-1} H L^{-H}.  When the FP32 estimate left the decision open, the first pass also
     //    solves L Z = I in FP64 in the columns m .. 2m-1 and ||Z||_F^2 decides: 1 / ||Z||_F^2 >=
     //    kLindepTol keeps the Cholesky route, otherwise the k-point goes to the canonical route.
     if (need64) {
-      for (int e = lane; e < m * m; e += 32) {
+      for (int e = lane; e < m * m; e += G) {
         const int i = e / m, j = e - (e / m) * m;
         V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
       }
     }
-    __syncwarp();  // sg[i] = 1 / L_ii from the factorisation
+    g.sync();  // sg[i] = 1 / L_ii from the factorisation
     for (int pass = 0; pass < 2; ++pass) {
       // forward substitution per column; with 16 columns or fewer two lanes share a column
       // (even and odd k of each inner sum, combined by a shuffle)
       const int ncol = (pass == 0 && need64) ? 2 * m : m;
-      const int q = ncol <= 16 ? 2 : 1;
-      for (int cc0 = 0; cc0 < ncol; cc0 += 32 / q) {
+      const int q = (G == 32 && ncol <= 16) ? 2 : 1;
+      for (int cc0 = 0; cc0 < ncol; cc0 += G / q) {
         const int cc = cc0 + lane / q, part = lane % q;
         const bool act = cc < ncol;
         double2 *X = cc < m ? A : V;
@@ -602,27 +642,27 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
           if (act)
             for (int k = part; k < i; k += q) acc = cfma(B[i * m + k], z[k], acc);
           if (q == 2) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+            acc.x += __shfl_xor_sync(g.mask, acc.x, 1);
+            acc.y += __shfl_xor_sync(g.mask, acc.y, 1);
           }
           const double2 xi = act ? X[i * m + c] : make_double2(0.0, 0.0);
           z[i] = cscale(csub(xi, acc), sg[i]);
           if (act && part == 0) X[i * m + c] = z[i];
         }
       }
-      __syncwarp();
+      g.sync();
       if (pass == 0) {
         if (need64) {
           double tr = 0.0;
-          for (int e = lane; e < m * m; e += 32) tr += V[e].x * V[e].x + V[e].y * V[e].y;
-          for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+          for (int e = lane; e < m * m; e += G) tr += V[e].x * V[e].x + V[e].y * V[e].y;
+          for (int o = G / 2; o > 0; o >>= 1) tr += __shfl_xor_sync(g.mask, tr, o);
           if (!(tr * kLindepTol <= 1.0)) {  // a direction may lie below kLindepTol
             chol = false;
             break;
           }
         }
         // A <- A^H
-        for (int e = lane; e < m * m; e += 32) {
+        for (int e = lane; e < m * m; e += G) {
           const int i = e / m, j = e - (e / m) * m;
           if (i < j) {
             const double2 x = A[i * m + j], y = A[j * m + i];
@@ -632,47 +672,47 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
             A[e].y = -A[e].y;
           }
         }
-        __syncwarp();
+        g.sync();
       }
     }
     if (chol) {
-      hermitian_part(A, m, lane);
+      hermitian_part(A, m, g);
     } else {  // the scaled H again for the canonical route
-      for (int e = lane; e < m * m; e += 32) {
+      for (int e = lane; e < m * m; e += G) {
         const int a = e / m, b = e - (e / m) * m;
         A[e] = cscale(Hb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
       }
-      __syncwarp();
-      hermitian_part(A, m, lane);
+      g.sync();
+      hermitian_part(A, m, g);
     }
   }
   const int mkept = m;  // kept functions (rows of the back-transformation)
   if (ok && !chol) {
     // 2'. canonical orthogonalisation: S~ = V diag(sigma) V^H, keep sigma >= kLindepTol,
     //     X = V_kept diag(sigma)^{-1/2}, C = X^H H~ X
-    for (int e = lane; e < m * m; e += 32) {
+    for (int e = lane; e < m * m; e += G) {
       const int a = e / m, b = e - (e / m) * m;
       B[e] = cscale(Sb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
       V[e] = make_double2(a == b ? 1.0 : 0.0, 0.0);
     }
-    __syncwarp();
-    hermitian_part(B, m, lane);
-    sweeps += jacobi_herm(B, V, m, lane, R);
+    g.sync();
+    hermitian_part(B, m, g);
+    sweeps += jacobi_herm(B, V, m, g, R);
     const bool kp = lane < m && B[lane * m + lane].x >= kLindepTol;
-    const unsigned m2mask = __ballot_sync(0xffffffffu, kp);
+    const unsigned m2mask = g.ballot(kp);
     const int m2 = __popc(m2mask);
     if (kp) {
       const int b = __popc(m2mask & ((1u << lane) - 1u));
       kidx2[b] = lane;
       sg[b] = 1.0 / sqrt(B[lane * m + lane].x);
     }
-    __syncwarp();
-    for (int e = lane; e < m * m2; e += 32) {  // X (m x m2) into B
+    g.sync();
+    for (int e = lane; e < m * m2; e += G) {  // X (m x m2) into B
       const int i = e / m2, b = e - (e / m2) * m2;
       B[e] = cscale(V[i * m + kidx2[b]], sg[b]);
     }
-    __syncwarp();
-    for (int e = lane; e < m * m2; e += 32) {  // W = H~ X (m x m2) into V
+    g.sync();
+    for (int e = lane; e < m * m2; e += G) {  // W = H~ X (m x m2) into V
       const int i = e / m2, b = e - (e / m2) * m2;
       double2 acc = make_double2(0.0, 0.0);
       for (int k = 0; k < m; ++k) {
@@ -682,8 +722,8 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       }
       V[e] = acc;
     }
-    __syncwarp();
-    for (int e = lane; e < m2 * m2; e += 32) {  // C = X^H W (m2 x m2) into A
+    g.sync();
+    for (int e = lane; e < m2 * m2; e += G) {  // C = X^H W (m2 x m2) into A
       const int a = e / m2, b = e - (e / m2) * m2;
       double2 acc = make_double2(0.0, 0.0);
       for (int k = 0; k < m; ++k) {
@@ -693,9 +733,9 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       }
       A[e] = acc;
     }
-    __syncwarp();
+    g.sync();
     m = m2;
-    hermitian_part(A, m, lane);
+    hermitian_part(A, m, g);
   }
 
   bool tri = s.tri != nullptr;
@@ -705,8 +745,8 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     // singular overlaps, nearly cancelled Bloch functions with large scaled entries), so such
     // k-points stay on Jacobi: tridiagonal only if ||C||_F <= 2 ||H~||_F
     double cf2 = 0.0;
-    for (int e = lane; e < m * m; e += 32) cf2 += A[e].x * A[e].x + A[e].y * A[e].y;
-    for (int o = 16; o > 0; o >>= 1) cf2 += __shfl_xor_sync(0xffffffffu, cf2, o);
+    for (int e = lane; e < m * m; e += G) cf2 += A[e].x * A[e].x + A[e].y * A[e].y;
+    for (int o = G / 2; o > 0; o >>= 1) cf2 += __shfl_xor_sync(g.mask, cf2, o);
     // and only if its absolute error stays below half the 1e-10 Ha floor: m eps ||C||_F <= 5e-11
     const double cmax = 5e-11 / (m * 2.220446049250313e-16);
     if (!(cf2 <= 4.0 * hf2) || !(cf2 <= cmax * cmax)) {
@@ -719,7 +759,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     //     k_tridiag_eig (one thread per matrix); slot widx = [m | d[m0] | e[m0]]
     double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
     if (ok && m > 0)
-      householder_tridiag(A, m, lane, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+      householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
                           slot + 1 + m0);
     if (lane == 0) {
       slot[0] = ok ? (double)m : -1.0;
@@ -745,13 +785,13 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     // 3. cyclic Jacobi on C (with the eigenvectors of C accumulated in V when requested: V is
     //    free on both routes once C is formed)
     if (s.vecs) {
-      for (int e = lane; e < m * m; e += 32) {
+      for (int e = lane; e < m * m; e += G) {
         const int i = e / m, j = e - (e / m) * m;
         V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
       }
-      __syncwarp();
+      g.sync();
     }
-    sweeps += jacobi_herm(A, s.vecs ? V : nullptr, m, lane, R);
+    sweeps += jacobi_herm(A, s.vecs ? V : nullptr, m, g, R);
     if (lane == 0 && counters) {
       if (!s.tri) atomicAdd(counters, (unsigned long long)sweeps);  // tridiagonal mode counts QR rotations
       atomicAdd(counters + 1, 1ull);
@@ -763,10 +803,10 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   //    column of each eigenvalue (ties keep the lower column first)
   double v = (ok && lane < m) ? A[lane * m + lane].x : INFINITY;
   int vid = lane;
-  for (int k = 2; k <= 32; k <<= 1)
+  for (int k = 2; k <= G; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      const double o = __shfl_xor_sync(0xffffffffu, v, j);
-      const int oid = __shfl_xor_sync(0xffffffffu, vid, j);
+      const double o = __shfl_xor_sync(g.mask, v, j);
+      const int oid = __shfl_xor_sync(g.mask, vid, j);
       const bool up = (lane & k) == 0, lower = (lane & j) == 0;
       const bool o_less = o < v || (o == v && oid < vid);
       if ((lower == up) == o_less) {
@@ -775,7 +815,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       }
     }
   if (!ok) v = NAN;
-  if (s.vecs) bloch_vectors(s, kap, mk, ok, chol, m, mkept, lane, vid, A, B, V, sg, dsc, kidx);
+  if (s.vecs) bloch_vectors(s, kap, mk, ok, chol, m, mkept, g, vid, A, B, V, sg, dsc, kidx);
   if (lane < m0) {
     s.eig[(int64_t)kap * m0 + lane] = v;
     s.eig[(int64_t)mk * m0 + lane] = v;
@@ -1043,26 +1083,38 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Lanes per matrix: half a warp when every order fits (m0 <= 16), else a whole warp.
+static inline int eig_group(int max_m0) { return max_m0 <= 16 ? 16 : 32; }
+
 int eig_max_warps(int max_m0) {
+  const int per_warp = 32 / eig_group(max_m0);
   int w = kEigMaxWarps;
-  while (w > 1 && (size_t)w * eig_warp_bytes(max_m0) > 227 * 1024) --w;
+  while (w > 1 && (size_t)w * per_warp * eig_warp_bytes(max_m0) > 227 * 1024) --w;
   return w;
+}
+
+template <int G>
+static cudaError_t launch_k_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
+                                unsigned long long *counters, cudaStream_t st, int warps) {
+  const int per_cta = warps * (32 / G);
+  const size_t smem = (size_t)per_cta * eig_warp_bytes(max_m0);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_eig<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((max_k + per_cta - 1) / per_cta, nsys);
+  kmark(LHF_K_EIG, 1, st);
+  k_eig<G><<<grid, warps * 32, smem, st>>>(sys, flags, counters, max_m0);
+  kmark(LHF_K_EIG, 0, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                               unsigned long long *counters, cudaStream_t st, int warps) {
   if (max_k <= 0 || nsys <= 0) return cudaSuccess;
-  if (warps < 1 || warps > kEigMaxWarps) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)warps * eig_warp_bytes(max_m0);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 grid((max_k + warps - 1) / warps, nsys);
-  kmark(LHF_K_EIG, 1, st);
-  k_eig<<<grid, warps * 32, smem, st>>>(sys, flags, counters, max_m0);
-  kmark(LHF_K_EIG, 0, st);
-  return cudaGetLastError();
+  if (warps < 1 || warps > eig_max_warps(max_m0)) return cudaErrorInvalidValue;
+  return eig_group(max_m0) == 16 ? launch_k_eig<16>(sys, nsys, max_k, max_m0, flags, counters, st, warps)
+                                 : launch_k_eig<32>(sys, nsys, max_k, max_m0, flags, counters, st, warps);
 }
 
 cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
