@@ -146,13 +146,15 @@ __device__ double gauss_cell_series(double m, double d) {
 }
 
 // Exact integral of exp(-t^2 (x - c)^2) over [lo, hi]  (eq. (3.5) with one term of eq. (3.6)).
-__device__ double gauss_cell_integral(double t, double lo, double hi, double c) {
+// invt = 1 / t (divisions are FP64 instruction sequences on this GPU: the row's reciprocals are
+// formed once).
+__device__ double gauss_cell_integral(double t, double invt, double lo, double hi, double c) {
   const double A = t * (lo - c), B = t * (hi - c);
-  const double f = 0.88622692545275801365 / t;  // sqrt(pi) / (2 t)
+  const double f = 0.88622692545275801365 * invt;  // sqrt(pi) / (2 t)
   if (A < 0.0 && B > 0.0) return f * (erf(B) + erf(-A));
   const double delta = B - A;
   const double m = 0.5 * (A + B);
-  if (delta <= 0.25 && fabs(m) * delta <= 1.0) return gauss_cell_series(m, 0.5 * delta) / t;
+  if (delta <= 0.25 && fabs(m) * delta <= 1.0) return gauss_cell_series(m, 0.5 * delta) * invt;
   if (A >= 0.0) return f * (erfc(A) - erfc(B));
   return f * (erfc(-B) - erfc(-A));
 }
@@ -250,7 +252,7 @@ __device__ double half_sqrtpi_erf_diff(double x, double y) {
   return f * (erf(x) - erf(y));
 }
 
-__device__ double image_sum_em(double t, double xc, double b, const double *bc, int J, const double *C,
+__device__ double image_sum_em(double t, double xc, double b, double invs, const double *bc, int J, const double *C,
                                int klo, int khi, int kmax, bool even) {
   const double s = t * b, m0 = t * xc;
   const double ma = m0 - klo * s, mc = m0 - khi * s;
@@ -268,7 +270,7 @@ __device__ double image_sum_em(double t, double xc, double b, const double *bc, 
     pa *= ma * ma;
     pc *= mc * mc;
   }
-  integ /= s;
+  integ *= invs;
   double ca = C[kEmDeg], cc = C[kEmDeg];
 #pragma unroll
   for (int k = kEmDeg - 1; k >= 0; --k) {
@@ -288,13 +290,13 @@ __device__ double image_sum_em(double t, double xc, double b, const double *bc, 
 // walking outward from the image nearest to the cell and restarted from exp every 8 images, so
 // that the dominant terms come from small exponents and the product's rounding stays within a
 // few tens of ulp.
-__device__ double image_sum_taylor(double t, double xc, double b, const double *bc, int J, int klo, int khi,
-                                   int kmax, bool even) {
+__device__ double image_sum_taylor(double t, double xc, double b, double invb, const double *bc, int J, int klo,
+                                   int khi, int kmax, bool even) {
   if (klo > khi) return 0.0;  // no image within reach
   const double sb = t * b;
   const double Q = exp(-2.0 * sb * sb);
   // the image nearest to the cell, clamped to the window
-  int kc = (int)rint(xc / b);
+  int kc = (int)rint(xc * invb);
   kc = kc < klo ? klo : (kc > khi ? khi : kc);
   double v = 0.0;
   // outward: dir = +1 (k = kc .. khi, m decreasing), dir = -1 (k = kc-1 .. klo, m increasing)
@@ -341,9 +343,9 @@ __device__ double poisson_weight(int n, double s, double h, double b) {
   return g * (2.0 * b / (kPi * n)) * sinpi(n * h / b);
 }
 
-__device__ double image_sum_poisson(double t, double lo, double hi, double c0, double b, const double *pw, int N) {
+__device__ double image_sum_poisson(double pref, double lo, double hi, double c0, double invb, const double *pw, int N) {
   const double h = hi - lo, xm = 0.5 * (lo + hi);
-  const double c1 = cospi(2.0 * (xm - c0) / b);
+  const double c1 = cospi(2.0 * (xm - c0) * invb);
   double acc = h, cm = 1.0, cn = c1;  // cos((n-1) theta), cos(n theta)
   for (int n = 1; n <= N; ++n) {
     acc = fma(pw[n], cn, acc);
@@ -351,7 +353,7 @@ __device__ double image_sum_poisson(double t, double lo, double hi, double c0, d
     cm = cn;
     cn = nx;
   }
-  return 1.7724538509055160273 / (t * b) * acc;  // sqrt(pi) / (t b)
+  return pref * acc;  // pref = sqrt(pi) / (t b)
 }
 
 // One CTA per (system, direction, rank term r = (nucleus nu, sinc node q)): the row constants
@@ -369,7 +371,8 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
   const int nu = r / s.R, q = r - nu * s.R;
   const double t = s.t[q];
   const double c0 = s.a[nu][l];
-  const double reach = 10.0 / t;
+  const double invt = 1.0 / t, invb = 1.0 / D.b, invZ = 1.0 / s.Z[nu];  // the row's reciprocals
+  const double reach = 10.0 * invt;
   const double delta = t * D.h, sb = t * D.b;
   const bool taylor = delta <= kTaylorMaxDelta;
   const int J = taylor ? taylor_degree(0.5 * delta) : 0;
@@ -393,38 +396,38 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
       const double lo = D.cell0 + i * D.h, hi = lo + D.h;
       const int kmax = D.K / 2;
       const bool even = (D.K % 2) == 0;
-      const double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
+      const double klo_f = ceil((lo - reach - c0) * invb), khi_f = floor((hi + reach - c0) * invb);
       const int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
       const int khi = (khi_f > kmax) ? kmax : (int)khi_f;
       const double xc = 0.5 * (lo + hi) - c0;
       if (poisson_row && klo > -kmax && khi < kmax) {
-        v = image_sum_poisson(t, lo, hi, c0, D.b, pw, NP);
+        v = image_sum_poisson(1.7724538509055160273 * invt * invb, lo, hi, c0, invb, pw, NP);
       } else if (em_row && khi - klo >= 16) {
-        v = image_sum_em(t, xc, D.b, bc, J, emc, klo, khi, kmax, even) / t;
+        v = image_sum_em(t, xc, D.b, invt * invb, bc, J, emc, klo, khi, kmax, even) * invt;
       } else if (taylor) {
-        v = image_sum_taylor(t, xc, D.b, bc, J, klo, khi, kmax, even) / t;
+        v = image_sum_taylor(t, xc, D.b, invb, bc, J, klo, khi, kmax, even) * invt;
       } else {
         for (int k = klo; k <= khi; ++k) {
           const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
-          v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+          v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
         }
       }
     } else {
       const double lo = D.x0 + i * D.h, hi = lo + D.h;
       if (D.lattice) {
-        const double klo_f = ceil((lo - reach - c0) / D.b), khi_f = floor((hi + reach - c0) / D.b);
+        const double klo_f = ceil((lo - reach - c0) * invb), khi_f = floor((hi + reach - c0) * invb);
         const int klo = (klo_f < 0.0) ? 0 : (int)klo_f;
         const int khi = (khi_f > D.L - 1) ? D.L - 1 : (int)khi_f;
         for (int k = klo; k <= khi; ++k) {
-          const double wk = s.zcell ? s.zcell[k * s.M0 + nu] / s.Z[nu] : 1.0;
-          v += wk * gauss_cell_integral(t, lo, hi, c0 + k * D.b);
+          const double wk = s.zcell ? s.zcell[k * s.M0 + nu] * invZ : 1.0;
+          v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
         }
       } else if (lo - reach <= c0 && c0 <= hi + reach) {
         if (taylor) {
           const double m = t * (0.5 * (lo + hi) - c0), y = m * m;
-          v = exp(-y) * taylor_S(bc, J, y) / t;
+          v = exp(-y) * taylor_S(bc, J, y) * invt;
         } else {
-          v = gauss_cell_integral(t, lo, hi, c0);
+          v = gauss_cell_integral(t, invt, lo, hi, c0);
         }
       }
     }
