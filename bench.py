@@ -164,7 +164,7 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
         "k_gram_tc": {"bound": "tensor", "work": tc, "algorithmic_flops": gram},
         "k_gram_slice": {"bound": "hbm", "work": slice_bytes},
         "k_ranksum": {"bound": "alu", "work": rank},
-        "k_dft_pass": {"bound": "hbm", "work": dft_bytes, "launches_per_step": max(levels, 1)},
+        "k_dft_pass": {"bound": "hbm", "work": dft_bytes},
         "k_eig": {"bound": "alu", "work": matrices * (28.0 / 3.0 + 16.0 / 3.0) * m ** 3},
         "k_tridiag_eig": {"bound": "alu", "work": passes * 8.0 * m},
     }
@@ -512,8 +512,11 @@ def run_gpu(args):
         if k_n == 0 or k_ms <= 0 or kname not in work:
             continue
         w = work[kname]
-        per_launch_s = k_ms / 1e3 / k_n
-        per_launch_work = w["work"] / w.get("launches_per_step", 1)
+        # total algorithmic work over the kernel's total time (= work per launch / average launch
+        # time when the launches of a step are alike; the Gram kernels run once per direction)
+        step_s = k_ms / 1e3 / max(args.steps, 1)
+        per_launch_s = step_s
+        per_launch_work = w["work"]
         if w["bound"] == "hbm":
             achieved = per_launch_work / per_launch_s / 1e9
             peak, unit = float(peaks.get("hbm_gbs", 6800.0)), "GB/s"
@@ -528,6 +531,7 @@ def run_gpu(args):
             src = "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
         r = {"bound": w["bound"], "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
              "peak_source": src, "launches": k_n, "ms_per_launch": k_ms / k_n}
+        r["launches_per_step"] = k_n / max(args.steps, 1)
         if "algorithmic_flops" in w:
             r["algorithmic_tflops"] = w["algorithmic_flops"] / per_launch_s / 1e12
         rooflines[kname] = r
@@ -535,7 +539,7 @@ def run_gpu(args):
     roof = dict(rooflines.get(dom, {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None}))
     roof["kernel"] = dom
     roof["traffic"] = kernel_traffic(dom, B)
-    roof["algorithmic_per_launch"] = work.get(dom, {}).get("work")
+    roof["algorithmic_per_step"] = work.get(dom, {}).get("work")
     stage_summary = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in stages.items()}
     kernel_summary = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                           "share": v[0] / max(sum(x[0] for x in kernels.values()), 1e-30)}

@@ -33,9 +33,9 @@ struct GramItem {
 };
 
 // CTA b of a system -> (direction, window block, mu) over the contracted blocks jw = cw0 ..
-// cw0 + Jc - 1 of each direction.
-__device__ __forceinline__ bool decode_gram(const SysDev &s, int b, GramItem &it) {
-  for (int l = 0; l < 3; ++l) {
+// cw0 + Jc - 1 of each direction (of direction ldir alone when ldir >= 0).
+__device__ __forceinline__ bool decode_gram(const SysDev &s, int b, GramItem &it, int ldir) {
+  for (int l = ldir < 0 ? 0 : ldir; l < (ldir < 0 ? 3 : ldir + 1); ++l) {
     const int cnt = s.d[l].Jc * s.m0;
     if (b < cnt) {
       it.l = l;
@@ -151,10 +151,10 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
   }
 }
 
-__global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv) {
+__global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   GramItem it;  // open boxes: directions 1, 2 only (direction 0 has no window here)
-  if (!decode_gram(s, blockIdx.x, it)) return;
+  if (!decode_gram(s, blockIdx.x, it, ldir)) return;
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv;
   const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
@@ -247,11 +247,11 @@ __device__ __forceinline__ int scale_exponent_key(unsigned key) {
   return bex ? bex - 1022 : 0;
 }
 
-__global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__restrict__ sysv) {
+__global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   GramItem it;
-  if (!decode_gram(s, blockIdx.x, it)) return;
+  if (!decode_gram(s, blockIdx.x, it, ldir)) return;
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv, Kp = D.Kpad;
   const int ld = nv + 1;
@@ -378,7 +378,7 @@ cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items,
 }
 
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
-                             int max_nv, cudaStream_t st) {
+                             int max_nv, cudaStream_t st, int ldir) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
   if (smem > 48 * 1024) {
@@ -388,13 +388,13 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
   }
   dim3 grid(max_blocks, nsys);
   kmark(LHF_K_GRAM_FP64, 1, st);
-  k_gram_fp64<<<grid, kGramThreads, smem, st>>>(sys);
+  k_gram_fp64<<<grid, kGramThreads, smem, st>>>(sys, ldir);
   kmark(LHF_K_GRAM_FP64, 0, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
-                               int max_rt3, cudaStream_t st) {
+cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
+                               int ldir) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
   if (smem > 48 * 1024) {
@@ -403,10 +403,13 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
     if (e != cudaSuccess) return e;
   }
   kmark(LHF_K_GRAM_SLICE, 1, st);
-  k_gram_slice<<<dim3(max_blocks, nsys), kGramThreads, smem, st>>>(sys);
+  k_gram_slice<<<dim3(max_blocks, nsys), kGramThreads, smem, st>>>(sys, ldir);
   kmark(LHF_K_GRAM_SLICE, 0, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vslices(const SysDev *sys, int nsys, int max_rt3, cudaStream_t st) {
+  if (max_rt3 <= 0 || nsys <= 0) return cudaSuccess;
   kmark(LHF_K_VSLICE, 1, st);
   k_vslice<<<dim3(max_rt3, nsys), kGramThreads, 0, st>>>(sys);
   kmark(LHF_K_VSLICE, 0, st);

@@ -586,20 +586,40 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
   long long mirror = 0;
   if (with_mirror)
     for (const Plan &p : ps) mirror = std::max(mirror, p.mirror_items);
+  // one launch per direction, each sized by that direction's rows (shared memory per CTA holds two
+  // rows of n_v values for each of m0 functions: the short rows of a long periodic direction do
+  // not inherit the transverse directions' footprint)
+  int dir_blocks[3] = {0, 0, 0}, dir_nv[3] = {0, 0, 0};
+  for (const Plan &p : ps)
+    for (int l = 0; l < 3; ++l) {
+      const DirDev &D = p.sd.d[l];
+      if (D.Jc <= 0) continue;
+      dir_blocks[l] = std::max(dir_blocks[l], D.Jc * p.sd.m0);
+      dir_nv[l] = std::max(dir_nv[l], D.nv);
+    }
+  int gram_launches = 0;
+  lhf_status st = LHF_OK;
   if (!ps[0].mixed) {
     c->begin(2);
-    lhf_status st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
-                                                  max_of(ps, &Plan::nv_max), c->stream),
-                            "Gram kernel");
+    for (int l = 0; l < 3 && st == LHF_OK; ++l)
+      if (dir_blocks[l] > 0) {
+        st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, dir_blocks[l], max_m0, dir_nv[l], c->stream, l),
+                     "Gram kernel");
+        ++gram_launches;
+      }
     if (st == LHF_OK) st = c->cuda(lhf::launch_gram_mirror(c->d_sys, nsys, mirror, c->stream), "mirror kernel");
-    c->end(mirror > 0 ? 2 : 1);
+    c->end(gram_launches + (mirror > 0 ? 1 : 0));
     return st;
   }
   c->begin(2);
-  lhf_status st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, max_of(ps, &Plan::gram_blocks), max_m0,
-                                                  max_of(ps, &Plan::nv_max), 3 * max_rt, c->stream),
-                          "digit-plane kernels");
-  c->end(2);
+  for (int l = 0; l < 3 && st == LHF_OK; ++l)
+    if (dir_blocks[l] > 0) {
+      st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, dir_blocks[l], max_m0, dir_nv[l], c->stream, l),
+                   "digit-plane kernel");
+      ++gram_launches;
+    }
+  if (st == LHF_OK) st = c->cuda(lhf::launch_vslices(c->d_sys, nsys, 3 * max_rt, c->stream), "digit-plane kernel");
+  c->end(gram_launches + 1);
   if (st != LHF_OK) return st;
   if (c->graph_tc) {  // capture: the arguments were prepared and copied before the capture
     c->begin(8);

@@ -165,10 +165,15 @@ inline void kmark(int kernel, int begin, cudaStream_t st) {
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 // One CTA per (direction, rank term) row: max_rows = 3 R_tot over the batch.
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
+// Weighted Grams (FP64 route) and the folded products' digit planes (tensor-core route): one CTA
+// per (direction, contracted window block, mu); ldir >= 0 restricts a launch to direction ldir
+// (max_blocks, max_nv then over that direction: the shared memory fits its rows), -1 takes all.
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
-                             int max_nv, cudaStream_t st);
-cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv,
-                               int max_rt3, cudaStream_t st);
+                             int max_nv, cudaStream_t st, int ldir = -1);
+cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
+                               int ldir = -1);
+// Digit planes of the potential factors: one CTA per (direction, rank term), max_rt3 = 3 R_tot.
+cudaError_t launch_vslices(const SysDev *sys, int nsys, int max_rt3, cudaStream_t st);
 // The window blocks outside cw0 .. cw0 + Jc - 1 from their mirrors (thread per element).
 cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items, cudaStream_t st);
 // Tensor-core contraction of the digit planes (tcgen05), one job per (system, direction, 128-row
