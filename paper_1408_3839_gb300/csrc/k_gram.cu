@@ -247,7 +247,7 @@ __device__ __forceinline__ int scale_exponent_key(unsigned key) {
   return bex ? bex - 1022 : 0;
 }
 
-__global__ void __launch_bounds__(kGramThreads) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
+__global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   GramItem it;
