@@ -176,11 +176,10 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
 # kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
 # time; any other hash reports null.
 TRAFFIC = {
-    # ncu --set full of the tube_256 workload at 16 systems (profiles/tube_256_kernels_batch16.md)
-    "k_eig": {"src": "k_eig.cu", "sha": "e3648d26e1bda79e", "bytes_per_system": (17.008896e6 + 0.028160e6) / 16},
-    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "afc3622104ae4eef", "bytes_per_system": (180.74752e6 + 26.00704e6) / 16},
-    "k_gram_slice": {"src": "k_gram.cu", "sha": "41d7660d9b5eb076", "bytes_per_system": (6.277376e6 + 112.187648e6) / 16},
-    "k_ranksum": {"src": "k_ranksum.cu", "sha": "2c6c387596456151", "bytes_per_system": (46.152704e6 + 5.535232e6) / 16},
+    # ncu --set full of the tube_256 workload at 16 systems, the autotuned launch
+    # (profiles/tube_256_kernels_batch16.md)
+    "k_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": (17.01888e6 + 0.024576e6) / 16},
+    "k_potential": {"src": "k_setup.cu", "sha": "24da134a45bc6a94", "bytes_per_system": (0.196608e6 + 0.0) / 16},
 }
 
 
