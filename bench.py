@@ -366,13 +366,31 @@ def _device_time_ms(fn, steps, stream):
 
 
 def run_extras(ctx, lhf, stream, steps: int, warmup: int) -> dict:
-    """The other workloads of the path, each timed on the device (not part of the headline):
-    the heterogeneous batch of 64 tubes and slabs as one captured CUDA graph (mixed route), the
+    """The other workloads of the path, each timed on the device (not part of the headline): the
+    headline workload at batches of 1, 16, 64 and 256 systems, the heterogeneous batch of 64 tubes
+    and slabs as one captured CUDA graph (mixed route), the
     open (64,1,1) box (dense matrices and dense eigensolve, FP64) and the periodic (32,32,32)
     cube (three-level block DFT, 16 385 k-point solves; mixed route)."""
     import torch
 
     out = {}
+    # the headline workload at other batch sizes (mixed route, device-timed)
+    try:
+        sweep = {}
+        for B in (1, 16, 64, 256):
+            cfgs = [W.tube_256(seed) for seed in range(3000, 3000 + B)]
+            ctx.setup(cfgs[0])
+            sz = ctx.query_sizes()
+            eig = torch.empty(B * sz["n_kpoints"] * sz["m0"], dtype=torch.float64, device="cuda")
+            for _ in range(warmup):
+                ctx.bloch_spectra(cfgs, eig, None, lhf.MIXED)
+            nsteps = max(2, steps * 64 // (4 * B)) if B < 64 else steps
+            ms = _device_time_ms(lambda: ctx.bloch_spectra(cfgs, eig, None, lhf.MIXED), nsteps, stream)
+            sweep[str(B)] = {"value": B * nsteps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / nsteps}
+            del eig
+        out["tube_256_batch_sweep"] = sweep
+    except Exception as e:
+        out["tube_256_batch_sweep"] = {"error": str(e)}
     # heterogeneous batch through a graph
     try:
         cfgs = W.hetero_batch()

@@ -323,6 +323,39 @@ __device__ double image_sum_taylor(double t, double xc, double b, double invb, c
   return v;
 }
 
+// The same recurrence over the actual nuclei of an open box, k = klo .. khi, each image weighted
+// by its cell's charge over the row's reference charge (zc[k M0] / Z; weight 1 without zc).
+__device__ __noinline__ double image_sum_taylor_box(double t, double xc, double b, double invb, const double *bc, int J, int klo,
+                                       int khi, const double *zc, int M0, double invZ) {
+  if (klo > khi) return 0.0;  // no nucleus within reach
+  const double sb = t * b;
+  const double Q = exp(-2.0 * sb * sb);
+  int kc = (int)rint(xc * invb);
+  kc = kc < klo ? klo : (kc > khi ? khi : kc);
+  double v = 0.0;
+  for (int dir = 1; dir >= -1; dir -= 2) {
+    const int kbeg = dir > 0 ? kc : kc - 1;
+    const int kend = dir > 0 ? khi + 1 : klo - 1;
+    for (int k0 = kbeg; k0 != kend;) {
+      double m = t * (xc - k0 * b);
+      double e = exp(-m * m);
+      double R = exp(dir * 2.0 * m * sb - sb * sb);
+      const int steps = dir > 0 ? min(8, kend - k0) : min(8, k0 - kend);
+      for (int u = 0; u < steps; ++u) {
+        const int k = k0 + dir * u;
+        const double S = taylor_S(bc, J, m * m);
+        const double w = zc ? e * (zc[(int64_t)k * M0] * invZ) : e;
+        v = fma(w, S, v);
+        e *= R;
+        R *= Q;
+        m -= dir * sb;
+      }
+      k0 += dir * steps;
+    }
+  }
+  return v;
+}
+
 // Image sums whose window holds every image within reach (the images beyond the window lie
 // beyond exp(-100) of the nearest one): the lattice sum of the Gaussian is periodic in x and its
 // Fourier series (Poisson summation) integrates over the cell in closed form,
@@ -365,9 +398,17 @@ constexpr int kPotThreads = 128;
 __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   const int Rt = s.Rt;
-  if ((int)blockIdx.x >= 3 * Rt) return;
-  const int l = blockIdx.x / Rt, r = blockIdx.x - l * Rt;
+  // CTA -> (direction l, rank term r, chunk of cells)
+  int bidx = blockIdx.x, l = 0;
+  for (; l < 3; ++l) {
+    const int cnt = Rt * ((s.d[l].nv + kPotChunk - 1) / kPotChunk);
+    if (bidx < cnt) break;
+    bidx -= cnt;
+  }
+  if (l == 3) return;
   const DirDev &D = s.d[l];
+  const int nch = (D.nv + kPotChunk - 1) / kPotChunk;
+  const int r = bidx / nch, chunk = bidx - r * nch;
   const int nu = r / s.R, q = r - nu * s.R;
   const double t = s.t[q];
   const double c0 = s.a[nu][l];
@@ -390,7 +431,8 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
   __syncthreads();
 
   double *out = s.ws + D.offV + (int64_t)r * D.nv;
-  for (int i = tid; i < D.nv; i += kPotThreads) {
+  const int iend = min(D.nv, (chunk + 1) * kPotChunk);
+  for (int i = chunk * kPotChunk + tid; i < iend; i += kPotThreads) {
     double v = 0.0;
     if (D.periodic) {
       const double lo = D.cell0 + i * D.h, hi = lo + D.h;
@@ -418,9 +460,15 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
         const double klo_f = ceil((lo - reach - c0) * invb), khi_f = floor((hi + reach - c0) * invb);
         const int klo = (klo_f < 0.0) ? 0 : (int)klo_f;
         const int khi = (khi_f > D.L - 1) ? D.L - 1 : (int)khi_f;
-        for (int k = klo; k <= khi; ++k) {
-          const double wk = s.zcell ? s.zcell[k * s.M0 + nu] * invZ : 1.0;
-          v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
+        if (taylor) {
+          v = image_sum_taylor_box(t, 0.5 * (lo + hi) - c0, D.b, invb, bc, J, klo, khi,
+                                   s.zcell ? s.zcell + nu : nullptr, s.M0, invZ) *
+              invt;
+        } else {
+          for (int k = klo; k <= khi; ++k) {
+            const double wk = s.zcell ? s.zcell[k * s.M0 + nu] * invZ : 1.0;
+            v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
+          }
         }
       } else if (lo - reach <= c0 && c0 <= hi + reach) {
         if (taylor) {

@@ -434,7 +434,6 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.mirror_items += (long long)(D.J - D.Jc) * (Rt + 2) * mm;
     if (!(box && l == 0)) sd.nwin *= D.J;
     sd.nblocks *= D.L;
-    P.pot_rows += Rt;  // one CTA per (direction, rank term) row
     P.gram_blocks += D.Jc * m0;
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
@@ -502,6 +501,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
   P.basis_items = lhf::basis_ctas(sd);  // one CTA per (direction, function, chunk of samples)
+  P.pot_rows = lhf::potential_ctas(sd);  // one CTA per (direction, rank term, chunk of cells)
   P.ws = off;
   return LHF_OK;
 }

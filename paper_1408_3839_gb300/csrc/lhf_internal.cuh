@@ -146,6 +146,15 @@ __host__ __device__ inline int basis_ctas(const SysDev &s) {
   return n;
 }
 
+// Potential rows: one CTA per (direction, rank term, chunk of kPotChunk cells); the host sizes
+// the launch with potential_ctas.
+constexpr int kPotChunk = 512;
+__host__ __device__ inline int potential_ctas(const SysDev &s) {
+  int n = 0;
+  for (int l = 0; l < 3; ++l) n += s.Rt * ((s.d[l].nv + kPotChunk - 1) / kPotChunk);
+  return n;
+}
+
 // Per-kernel timing hook: while a context with profiling enabled is launching, kclock.mark is
 // set and every launcher brackets each of its kernel launches with kmark(kernel, 1 / 0, st)
 // (kernel = LHF_K_*).  Unset (the default) the calls do nothing.
@@ -163,7 +172,8 @@ inline void kmark(int kernel, int begin, cudaStream_t st) {
 // batch.  Periodic lattice directions write only the support-cell window of each row (see
 // k_basis).
 cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
-// One CTA per (direction, rank term) row: max_rows = 3 R_tot over the batch.
+// One CTA per (direction, rank term, chunk of kPotChunk cells): max_rows = potential_ctas over
+// the batch.
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st);
 // Weighted Grams (FP64 route) and the folded products' digit planes (tensor-core route): one CTA
 // per (direction, contracted window block, mu); ldir >= 0 restricts a launch to direction ldir
