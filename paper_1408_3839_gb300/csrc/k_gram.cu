@@ -78,6 +78,33 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
   const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
   const int mspan = mhi - mlo;
   const bool periodic = D.periodic != 0;
+  // per column function nu: the cells p of g_nu's support where the shifted row function is
+  // present, as up to two runs of consecutive cells -- [plo, phi] meets the row support
+  // [mlo, mhi] modulo L; unless the row support covers every residue its images [mlo + kL,
+  // mhi + kL] are disjoint, and [plo, phi] (at most L cells) meets at most two of them, k0 (the
+  // first that ends at or after plo) and k0 + 1 -- each run given by its length and the nodes of
+  // its first cell (for c = 0) in g_nu and in the shifted row function; formed once per CTA
+  __shared__ int seg[kMaxM0][2][3];  // [nu][run]: cells, first node of g_nu, first node of the row
+  if (periodic && tid < m0) {
+    const int nu = tid;
+    const int plo = s.cell_lo[it.l][nu];
+    int phi = s.cell_hi[it.l][nu];
+    if (phi > plo + L - 1) phi = plo + L - 1;
+    int seg_lo[2] = {plo, 1}, seg_hi[2] = {phi, 0};
+    if (mspan < L - 1) {
+      const int k0 = floor_div(plo - mhi + L - 1, L);
+      seg_lo[0] = max(plo, mlo + k0 * L);
+      seg_hi[0] = min(phi, mhi + k0 * L);
+      seg_lo[1] = max(plo, mlo + (k0 + 1) * L);
+      seg_hi[1] = min(phi, mhi + (k0 + 1) * L);
+    }
+    for (int sg = 0; sg < 2; ++sg) {
+      seg[nu][sg][0] = seg_hi[sg] >= seg_lo[sg] ? seg_hi[sg] - seg_lo[sg] + 1 : 0;
+      seg[nu][sg][1] = wrap(seg_lo[sg], L) * nc;      // node of g_nu in the run's first cell
+      seg[nu][sg][2] = wrap(seg_lo[sg] - j, L) * nc;  // node of the row function shifted by j
+    }
+  }
+  __syncthreads();
   const int items = m0 * nv;
   for (int p0 = tid; p0 < items; p0 += kGramThreads) {
     const int nu = p0 / nv;
@@ -86,28 +113,13 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
     const double *dg = Dg + (int64_t)nu * n;
     double q = 0.0, e = 0.0;
     if (periodic) {
-      const int plo = s.cell_lo[it.l][nu];
-      int phi = s.cell_hi[it.l][nu];
-      if (phi > plo + L - 1) phi = plo + L - 1;
-      // cells p of g_nu's support where the shifted row function is present: [plo, phi] meets the
-      // row support [mlo, mhi] modulo L.  Unless the row support covers every residue its images
-      // [mlo + kL, mhi + kL] are disjoint, and [plo, phi] (at most L cells) meets at most two of
-      // them, k0 (the first that ends at or after plo) and k0 + 1.  Visited in increasing p.
-      int seg_lo[2] = {plo, 1}, seg_hi[2] = {phi, 0};
-      if (mspan < L - 1) {
-        const int k0 = floor_div(plo - mhi + L - 1, L);
-        seg_lo[0] = max(plo, mlo + k0 * L);
-        seg_hi[0] = min(phi, mhi + k0 * L);
-        seg_lo[1] = max(plo, mlo + (k0 + 1) * L);
-        seg_hi[1] = min(phi, mhi + (k0 + 1) * L);
-      }
+      // visited in increasing p; the indices advance by one cell per p (no division in the loop)
 #pragma unroll
       for (int sg = 0; sg < 2; ++sg) {
-        if (seg_lo[sg] > seg_hi[sg]) continue;
-        // indices advance by one cell per p (no division inside the loop)
-        int iv = wrap(c + seg_lo[sg] * nc, n);  // node of g_nu in cell p
-        int iu = wrap(iv - j * nc, n);          // node of the row function shifted by j
-        for (int p = seg_lo[sg]; p <= seg_hi[sg]; ++p) {
+        const int cnt = seg[nu][sg][0];
+        int iv = seg[nu][sg][1] + c;
+        int iu = seg[nu][sg][2] + c;
+        for (int t = 0; t < cnt; ++t) {
           q += f[iu] * g[iv];
           e += df[iu] * dg[iv];
           iv += nc;
