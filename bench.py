@@ -176,10 +176,14 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
 # kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
 # time; any other hash reports null.
 TRAFFIC = {
-    # ncu --set full of the tube_256 workload at 16 systems, the autotuned launch
-    # (profiles/tube_256_kernels_batch16.md)
-    "k_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": (17.01888e6 + 0.024576e6) / 16},
-    "k_potential": {"src": "k_setup.cu", "sha": "24da134a45bc6a94", "bytes_per_system": (0.196608e6 + 0.0) / 16},
+    # ncu --set full of the tube_256 workload at 16 systems (profiles/tube_256_kernels_batch16.md):
+    # the autotuned k_eig launch and the first launch of the others; bytes read + written / 16.
+    # Only kernels whose traffic grows with the systems of a batch are listed (the 16-system
+    # capture keeps part of the rank sum's and the DFT's outputs in L2, a 64-system step does not)
+    "k_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": (17.019136e6 + 0.037888e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": 0.620288e6 / 16},
+    "k_potential": {"src": "k_setup.cu", "sha": "05fe0693b241f088", "bytes_per_system": (0.196352e6 + 0.000512e6) / 16},
+    "k_basis": {"src": "k_setup.cu", "sha": "05fe0693b241f088", "bytes_per_system": 0.103168e6 / 16},
 }
 
 
@@ -549,6 +553,9 @@ def run_gpu(args):
         r = {"bound": w["bound"], "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
              "peak_source": src, "launches": k_n, "ms_per_launch": k_ms / k_n}
         r["launches_per_step"] = k_n / max(args.steps, 1)
+        tr = kernel_traffic(kname, B)
+        if tr is not None:
+            r["traffic"] = tr
         if "algorithmic_flops" in w:
             r["algorithmic_tflops"] = w["algorithmic_flops"] / per_launch_s / 1e12
         rooflines[kname] = r
