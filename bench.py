@@ -373,8 +373,9 @@ def run_extras(ctx, lhf, stream, steps: int, warmup: int) -> dict:
     """The other workloads of the path, each timed on the device (not part of the headline): the
     headline workload at batches of 1, 16, 64 and 256 systems, the heterogeneous batch of 64 tubes
     and slabs as one captured CUDA graph (mixed route), the
-    open (64,1,1) box (dense matrices and dense eigensolve, FP64) and the periodic (32,32,32)
-    cube (three-level block DFT, 16 385 k-point solves; mixed route)."""
+    open (64,1,1) box (dense matrices and dense eigensolve, FP64), the energy per cell of the
+    lowest band of open and periodic chains against L, and the periodic (32,32,32) cube
+    (three-level block DFT, 16 385 k-point solves; mixed route)."""
     import torch
 
     out = {}
@@ -441,6 +442,42 @@ def run_extras(ctx, lhf, stream, steps: int, warmup: int) -> dict:
             "stages_ms": {k: v[0] / steps for k, v in st.items() if v[1]}}
     except Exception as e:
         out["box_64"] = {"error": str(e)}
+    # energy per cell of the lowest band of a (L,1,1) chain against L, open box and periodic
+    try:
+        Ls_per, Ls_box = (8, 32, 128, 512), (8, 32, 128, 256)
+        cfgs, sizes = [], []
+        for periodic, Ls in ((True, Ls_per), (False, Ls_box)):
+            for L in Ls:
+                cfg = W.chain(L, periodic=periodic)
+                ctx.setup(cfg)
+                sz = ctx.query_sizes()
+                cfgs.append(cfg)
+                sizes.append(sz["n_kpoints"] * sz["m0"] if periodic else sz["n_basis"])
+        off = [int(v) for v in np.cumsum([0] + sizes[:-1])]
+        eig = torch.empty(sum(sizes), dtype=torch.float64, device="cuda")
+        for cfg, o, n in zip(cfgs, off, sizes):
+            ctx.bloch_spectra([cfg], eig[o:o + n])
+        cells = [float(c["L"][0]) for c in cfgs]
+        n_low = [c["L"][0] for c in cfgs]  # the lowest band: one state per cell
+        energy = torch.empty(len(cfgs), dtype=torch.float64, device="cuda")
+        level = torch.empty(len(cfgs), dtype=torch.float64, device="cuda")
+        call = lambda: ctx.cell_energies(eig, off, sizes, n_low, cells, energy, level)
+        for _ in range(warmup):
+            call()
+        ms = _device_time_ms(call, steps, stream)
+        e, lv = energy.cpu().tolist(), level.cpu().tolist()
+        out["chain_cell_energy"] = {
+            "workload": "(L,1,1) chains of identical cells (b = 2.0, one Z = 1 nucleus, m0 = 4 s functions, "
+                        "h = 0.0625, open directions [-8, 8] x 64 nodes), periodic and open box; energy per cell "
+                        "of the lowest band (L lowest states) and the highest of them, by lhf_cell_energies over "
+                        "all chains in one launch",
+            "periodic": {str(L): {"energy_per_cell": e[i], "top_level": lv[i]} for i, L in enumerate(Ls_per)},
+            "box": {str(L): {"energy_per_cell": e[len(Ls_per) + i], "top_level": lv[len(Ls_per) + i]}
+                    for i, L in enumerate(Ls_box)},
+            "eigenvalues": sum(sizes), "ms_per_call": ms / steps,
+            "values_per_s": sum(sizes) * steps / (ms / 1e3)}
+    except Exception as e:
+        out["chain_cell_energy"] = {"error": str(e)}
     # periodic cube (32,32,32)
     try:
         cube = W.cubic_32()

@@ -215,6 +215,22 @@ lhf_status lhf_k_point_eigenvectors(lhf_ctx *ctx, const double *Hbar, const doub
 lhf_status lhf_bloch_orbitals(lhf_ctx *ctx, const int *kappa, int norb, const double *coef, const int *lo,
                               const int *cnt, double *out);
 
+/* Energy per cell of the lowest states (Sec. 5, the average energy per unit cell of a (L,1,1)
+ * chain against L, open and periodic): for each of nseg spectra, held on the device in
+ * eig[off[s] .. off[s] + cnt[s]) -- the eigenvalues of all k-points of one lattice (their union is
+ * the lattice matrix's spectrum, Prop. 6.1) or of one open box -- energy[s] = (sum of the n_low[s]
+ * smallest values) / cells[s], and level[s] = the n_low[s]-th smallest value (the highest
+ * selected state).  Equal values are counted with multiplicity; the selected set and level do not
+ * depend on the order of the values within a segment (the sum's rounding may), and repeated calls
+ * agree bit for bit.  +inf (removed functions, see
+ * lhf_k_point_eigensolve) sorts last: a segment with fewer than n_low[s] finite values gets
+ * energy = level = +inf.  NaN values give an undefined result.
+ * eig, energy, level: device (level may be NULL); off, cnt, n_low, cells: host arrays [nseg] with
+ * off[s] >= 0, 1 <= n_low[s] <= cnt[s], cells[s] > 0 (else LHF_ERR_ARG).  Uses the context's
+ * workspace (nseg records of 24 bytes). */
+lhf_status lhf_cell_energies(lhf_ctx *ctx, int nseg, const double *eig, const long long *off, const int *cnt,
+                             const int *n_low, const double *cells, double *energy, double *level);
+
 /* Generalized symmetric-definite eigenvalues of dense N x N matrices (open box, Table 4.1's
  * full eigensolver): H x = lambda S x.  Device pointers; eig [N] ascending. */
 lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, int N, double *eig);

@@ -206,6 +206,33 @@ def box_64(seed: int = 2, L: int = 64, n_perp: int = 320) -> dict:
         Z_cell=[[z] for z in z_cell])
 
 
+def chain(L: int, seed: int = 6, periodic: bool = True, n_perp: int = 64) -> dict:
+    """A (L,1,1) chain of identical cells, periodic (supercell of L cells, K_sum = L) or an open
+    box, the same cell either way (the paper's box-vs-periodic comparisons): b = 2.0, h = 0.0625
+    (n_cell = 32), one Z = 1 nucleus at a seeded offset, m0 = 4 s-type functions on it (exponents
+    log-uniform in [0.05, 20]), open directions [-8, 8] with n_perp nodes, R = 32.  The open box
+    pads x by ceil(rho_max / h) nodes per end and rounds up to a multiple of 128 nodes."""
+    rng = _rng(seed)
+    b = 2.0
+    h = 0.0625
+    n_c = int(round(b / h))
+    off = rng.uniform(-b / 4.0, b / 4.0, size=3)
+    pos = [[b / 2.0 + off[0], off[1], off[2]]]
+    kinds, alphas, centres = _basis_s_p(rng, 4, 4, 0, 0.05, 20.0, pos)
+    hp = 16.0 / n_perp
+    if periodic:
+        n1, x0 = L * n_c, 0.0
+    else:
+        pad = int(math.ceil(math.sqrt(RHO / min(alphas)) / h))
+        n1 = ((L * n_c + 2 * pad + 127) // 128) * 128
+        x0 = -((n1 - L * n_c) // 2) * h
+    return _system(
+        L=[L, 1, 1], b=[b, 16.0, 16.0], periodic=[1 if periodic else 0, 0, 0], n=[n1, n_perp, n_perp],
+        n_cell=[n_c, n_perp, n_perp], h=[h, hp, hp], x0=[x0, -8.0, -8.0], cell0=[0.0, -8.0, -8.0],
+        K_sum=[L if periodic else 1, 1, 1], Z=[1.0], a=pos, kinds=kinds, alphas=alphas, centres=centres,
+        sinc_key="hetero_32", name=f"chain_{'periodic' if periodic else 'box'}_{L}", seed=seed)
+
+
 def hetero(seed: int) -> dict:
     """One member of the heterogeneous batch: b = 2.0, one Z = 1 nucleus at a seeded offset,
     h drawn from {0.05, 0.0625, 0.08} (n_cell = 40, 32, 25), m0 from {4, 8, 16} (4 s; 4 s + px,

@@ -4,9 +4,10 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.
 this package.  It shares no code with the CUDA library: the arithmetic lives in
 ``lhf_oracle.c`` (compiled with gcc, loaded through ctypes), except for the Bloch eigenvectors
 (``k_point_eigenvectors``, ``lattice_eigenvector``), the Bloch orbitals on the grid
-(``bloch_orbital``, ``p1_mass_matrix``) and the separable k-space route (``kspace_blocks``),
-written here in numpy; the rest of this module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each
-function follows.
+(``bloch_orbital``, ``p1_mass_matrix``), the separable k-space route (``kspace_blocks``) and the
+energy per cell of the lowest states (``cell_energy``), written here in numpy; the rest of this
+module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each function
+follows.
 """
 
 from __future__ import annotations
@@ -416,6 +417,20 @@ def p1_mass_matrix(n: int, h: float, periodic: bool) -> np.ndarray:
     if periodic and n > 2:
         M[0, -1] = M[-1, 0] = 1.0
     return M * (h / 6.0)
+
+
+def cell_energy(eig, n_low: int, cells: float):
+    """Energy per cell of the lowest states (Sec. 5: the average energy per unit cell of a chain
+    against L): the n_low smallest values of the spectrum eig -- any shape; the union of the
+    k-point spectra of a lattice is the lattice matrix's spectrum (Prop. 6.1), an open box's is its
+    dense pencil's; +inf (removed functions) sorts last -- summed in ascending order and divided by
+    cells.  Returns (energy, the n_low-th smallest value)."""
+    v = np.sort(np.ravel(np.asarray(eig, dtype=np.float64)))
+    low = v[:int(n_low)]
+    total = 0.0
+    for x in low:
+        total += float(x)
+    return total / float(cells), float(low[-1])
 
 
 def bloch_spectrum(cfg):

@@ -1573,6 +1573,29 @@ lhf_status lhf_bloch_orbitals(lhf_ctx *c, const int *kappa, int norb, const doub
                  "orbital kernels");
 }
 
+lhf_status lhf_cell_energies(lhf_ctx *c, int nseg, const double *eig, const long long *off, const int *cnt,
+                             const int *n_low, const double *cells, double *energy, double *level) {
+  if (!c) return LHF_ERR_ARG;
+  if (nseg < 1 || !eig || !off || !cnt || !n_low || !cells || !energy)
+    return c->fail(LHF_ERR_ARG, "nseg >= 1, eig, off, cnt, n_low, cells and energy are required");
+  if (nseg > (1 << 30)) return c->fail(LHF_ERR_ARG, "nseg = %d too large", nseg);
+  std::vector<lhf::SpectrumSeg> seg((size_t)nseg);
+  for (int s = 0; s < nseg; ++s) {
+    if (off[s] < 0 || cnt[s] < 1 || n_low[s] < 1 || n_low[s] > cnt[s] || !(cells[s] > 0.0))
+      return c->fail(LHF_ERR_ARG, "spectrum %d: off = %lld, cnt = %d, n_low = %d, cells = %g", s, off[s], cnt[s],
+                     n_low[s], cells[s]);
+    seg[s] = lhf::SpectrumSeg{off[s], cnt[s], n_low[s], cells[s]};
+  }
+  const size_t bytes = seg.size() * sizeof(lhf::SpectrumSeg);
+  lhf_status st = ensure_ws(c, (bytes + sizeof(double) - 1) / sizeof(double));
+  if (st != LHF_OK) return st;
+  auto *d_seg = reinterpret_cast<lhf::SpectrumSeg *>(c->ws);
+  st = c->cuda(cudaMemcpyAsync(d_seg, seg.data(), bytes, cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  if (st != LHF_OK) return st;
+  // a pageable source is staged before the call returns; the stream orders the kernel after it
+  return c->cuda(lhf::launch_cell_energy(eig, d_seg, nseg, energy, level, c->stream), "cell energy kernel");
+}
+
 lhf_status lhf_potential_factors(lhf_ctx *c, int l, double *V) {
   if (!c) return LHF_ERR_ARG;
   if (l < 0 || l > 2 || !V) return c->fail(LHF_ERR_ARG, "direction 0..2 and an output pointer are required");

@@ -232,6 +232,18 @@ cudaError_t launch_kspace(const SysDev *sys, int nsys, int max_factor_ctas, long
 // support windows.  maxL: the largest L_l.
 cudaError_t launch_orbitals(const SysDev *sys, const int *kappa, const int *lo, const int *cnt, int norb,
                             const double *coef, double *B, double *out, int m0, int maxL, cudaStream_t st);
+// One spectrum of lhf_cell_energies: values eig[off .. off + cnt), the n_low smallest selected,
+// their sum divided by cells.
+struct SpectrumSeg {
+  long long off;
+  int cnt;
+  int n_low;
+  double cells;
+};
+// One CTA per spectrum: energy[s] = (sum of the n_low smallest) / cells, level[s] (may be null) =
+// the n_low-th smallest value.  seg: device array [nseg].
+cudaError_t launch_cell_energy(const double *eig, const SpectrumSeg *seg, int nseg, double *energy, double *level,
+                               cudaStream_t st);
 // Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
 // the dense matrices (thread per entry).
 size_t box_gram_smem_bytes(int max_width);

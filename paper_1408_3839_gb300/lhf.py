@@ -102,6 +102,8 @@ def load():
             "lhf_k_point_eigensolve": (st, [ctx] + [ctypes.c_void_p] * 4),
             "lhf_k_point_eigenvectors": (st, [ctx] + [ctypes.c_void_p] * 5),
             "lhf_dense_eigensolve": (st, [ctx, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+            "lhf_cell_energies": (st, [ctx, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), _ip, _ip,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_bloch_spectra": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_bloch_spectra_host": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_basis_factors": (st, [ctx, ctypes.c_int, ctypes.c_void_p]),
@@ -342,6 +344,15 @@ class Context:
 
     def dense_eigensolve(self, H, S, N: int, eig):
         self._check(self.lib.lhf_dense_eigensolve(self._h, _ptr(H), _ptr(S), int(N), _ptr(eig)))
+
+    def cell_energies(self, eig, off, cnt, n_low, cells, energy, level=None):
+        """lhf_cell_energies: eig, energy, level device float64; off, cnt, n_low, cells host sequences."""
+        n = len(cnt)
+        o = (ctypes.c_longlong * n)(*[int(v) for v in off])
+        c = (ctypes.c_int * n)(*[int(v) for v in cnt])
+        k = (ctypes.c_int * n)(*[int(v) for v in n_low])
+        w = (ctypes.c_double * n)(*[float(v) for v in cells])
+        self._check(self.lib.lhf_cell_energies(self._h, n, _ptr(eig), o, c, k, w, _ptr(energy), _ptr(level)))
 
     @staticmethod
     def _systems(cfgs):
