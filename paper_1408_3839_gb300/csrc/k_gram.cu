@@ -19,8 +19,8 @@
 //
 // One CTA per (system, direction, window block, mu): phase 1 forms Q[nu][c] for all nu in
 // shared memory (only the cells where both supports can be nonzero are visited) together with
-// the P1 sums; phase 2 contracts with the R_tot potential rows.  Deterministic (fixed-order
-// reductions, no atomics).
+// the P1 sums; phase 2 contracts with the R_tot potential rows.  Deterministic: fixed-order
+// floating-point reductions, and exact integer sums (whose order does not matter).
 #include "lhf_internal.cuh"
 
 namespace lhf {
@@ -57,13 +57,96 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// Phase 1 for one CTA: Q[nu][c] and the difference products E[nu][c] = sum_p D_i(g_mu,j) D_i(g_nu)
-// in shared memory, their row sums in red[2 nu], and the P1 stiffness/mass slots of C written
-// out.  With D_i(f) = f_i - f_(i+1) (periodic wrap; open: f_(-1) = f_n = 0),
+// ---- exact fixed-point forms of FP64 rows ----------------------------------------------
+//
+// A row x[c] (c < nv) with max|x| = f 2^e, 1/2 <= f < 1, becomes the 62-bit fixed-point integers
+// X[c] = rint(x[c] 2^(62-e)).  X is formed from the bit fields of x with integer arithmetic only
+// (the FP64 pipe of this GPU runs at a small fraction of the integer rate): |x| = M 2^(ex - 1075)
+// with M the 53-bit significand, so X = M 2^(ex - 1013 - e), a left shift by at most 9 bits
+// (|x| < 2^e) or a right shift rounded to nearest, ties to even.
+__device__ __forceinline__ long long fixed62(double x, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int bex = (int)((u >> 52) & 0x7ff);
+  const unsigned long long M = (u & ((1ull << 52) - 1)) | (bex ? (1ull << 52) : 0ull);
+  const int sh = (bex ? bex : 1) - 1013 - e;
+  unsigned long long X;
+  if (sh >= 0) {
+    X = M << sh;
+  } else if (sh > -64) {
+    const int r = -sh;
+    X = M >> r;
+    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (X & 1ull))) ++X;
+  } else {
+    X = 0;
+  }
+  return (u >> 63) ? -(long long)X : (long long)X;
+}
+
+// Magnitude key of x: the high word without the sign.  Keys order like |x| up to the low word,
+// and the largest key of a row carries the largest biased exponent.
+__device__ __forceinline__ unsigned mag_key(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+
+// e with max |x| < 2^e over a row from its largest magnitude key: frexp's exponent of the largest
+// element (f 2^e, 1/2 <= f < 1) when it is normal, 0 when every element is below 2^-1022 (those
+// round to zero).
+__device__ __forceinline__ int scale_exponent_key(unsigned key) {
+  const int bex = (int)(key >> 20);
+  return bex ? bex - 1022 : 0;
+}
+
+// Row sums of Q as exact integer sums: term(c) = round(X[c] / 2^qsh) (X the fixed-point form
+// above), sum = 2^(e + qsh - 62) sum_c term(c) -- each term within 2^(e + qsh - 63) of Q[c], the
+// integer sum exact whatever its order, one rounding on conversion.  qsh >= 10 with nv < 2^qsh
+// keeps |sum_c term| < 2^62 + 2^qsh (no overflow); for nv < 1024 the terms resolve 2^-52 of the
+// row's largest element, the resolution of an FP64 sum.
+__device__ __forceinline__ int row_sum_shift(int nv) {
+  int qsh = 10;
+  while (nv >= (1 << qsh)) ++qsh;
+  return qsh;
+}
+
+__device__ __forceinline__ long long row_sum_term(long long X, int qsh) {
+  return (X + (1ll << (qsh - 1))) >> qsh;
+}
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// rexp[nu]: the scale exponent of row nu of Q (warp per row).
+__device__ __forceinline__ void q_row_exponents(const double *Q, int ld, int m0, int nv, int *rexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
+    unsigned mx = 0;
+    for (int c = lane; c < nv; c += 32) mx = max(mx, mag_key(Q[nu * ld + c]));
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) rexp[nu] = scale_exponent_key(mx);
+  }
+}
+
+// The P1 slots of C for row function mu (thread nu < m0): stiffness (1/h) sum D D and mass
+// h sum f g - (h/6) sum D D, from dq = sum_c Q[nu][c] and de = red[2 nu + 1].
+__device__ __forceinline__ void write_p1_slots(const SysDev &s, const GramItem &it, int nu, double dq, double de) {
+  const DirDev &D = s.d[it.l];
+  const int m0 = s.m0, Rt = s.Rt, mm = m0 * m0;
+  double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + it.mu * m0;
+  Cout[(int64_t)Rt * mm + nu] = de / D.h;
+  Cout[(int64_t)(Rt + 1) * mm + nu] = D.h * dq - de * D.h / 6.0;
+}
+
+// Phase 1 for one CTA: Q[nu][c] in shared memory and red[2 nu + 1] = the sum over all nodes of the
+// difference products D_i(g_mu,j) D_i(g_nu), with D_i(f) = f_i - f_(i+1) (periodic wrap; open:
+// f_(-1) = f_n = 0).  The P1 forms follow from these sums and the row sums of Q:
 //   g^T A f = (1/h) sum_i D_i(f) D_i(g),   g^T S f = h sum_i f_i g_i - (h/6) sum_i D_i(f) D_i(g),
 // the same sums as (1/h) sum (2 f_i g_i - f_i g_(i+1) - f_(i+1) g_i) and (h/6) sum (4 f_i g_i +
 // cross terms) regrouped: no cancellation in the stiffness sum and two products per node.
-__device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, double *E, double *red) {
+// A warp takes one column function nu at a time, its lanes the nodes c = lane + 32 k: the
+// difference products of every node a lane visits accumulate in one register, so only a warp
+// reduction per function is left (two functions per butterfly).
+__device__ __forceinline__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, double *red) {
   const DirDev &D = s.d[it.l];
   const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, L = D.L;
   const int ld = nv + 1;
@@ -73,7 +156,8 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
   const int j = D.jlo + it.jw;
   const double *f = G + (int64_t)mu * n;
   const double *df = Dg + (int64_t)mu * n;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kWarps = kGramThreads / 32;
   // support of the shifted row function (cells), tested modulo L
   const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
   const int mspan = mhi - mlo;
@@ -105,62 +189,55 @@ __device__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, doub
     }
   }
   __syncthreads();
-  const int items = m0 * nv;
-  for (int p0 = tid; p0 < items; p0 += kGramThreads) {
-    const int nu = p0 / nv;
-    const int c = p0 - nu * nv;
-    const double *g = G + (int64_t)nu * n;
-    const double *dg = Dg + (int64_t)nu * n;
-    double q = 0.0, e = 0.0;
-    if (periodic) {
-      // visited in increasing p; the indices advance by one cell per p (no division in the loop)
+  for (int nu0 = warp; nu0 < m0; nu0 += 2 * kWarps) {
+    double es0 = 0.0, es1 = 0.0;
+    for (int h = 0; h < 2; ++h) {
+      const int nu = nu0 + h * kWarps;
+      if (nu >= m0) break;  // warp-uniform
+      const double *g = G + (int64_t)nu * n;
+      const double *dg = Dg + (int64_t)nu * n;
+      double e = 0.0;
+      if (periodic) {
+        for (int c = lane; c < nv; c += 32) {
+          // visited in increasing p; the indices advance by one cell per p (no division in the loop)
+          double q = 0.0;
 #pragma unroll
-      for (int sg = 0; sg < 2; ++sg) {
-        const int cnt = seg[nu][sg][0];
-        int iv = seg[nu][sg][1] + c;
-        int iu = seg[nu][sg][2] + c;
-        for (int t = 0; t < cnt; ++t) {
-          q += f[iu] * g[iv];
-          e += df[iu] * dg[iv];
-          iv += nc;
-          if (iv >= n) iv -= n;
-          iu += nc;
-          if (iu >= n) iu -= n;
+          for (int sg = 0; sg < 2; ++sg) {
+            const int cnt = seg[nu][sg][0];
+            int iv = seg[nu][sg][1] + c;
+            int iu = seg[nu][sg][2] + c;
+            for (int t = 0; t < cnt; ++t) {
+              q = fma(f[iu], g[iv], q);
+              e = fma(df[iu], dg[iv], e);
+              iv += nc;
+              if (iv >= n) iv -= n;
+              iu += nc;
+              if (iu >= n) iu -= n;
+            }
+          }
+          Q[nu * ld + c] = q;
+        }
+      } else {
+        // single open cell: nodes c = 0..n-1, Dirichlet ends (the virtual node -1 adds f_0 g_0)
+        if (lane == 0) e = f[0] * g[0];
+        for (int c = lane; c < nv; c += 32) {
+          Q[nu * ld + c] = f[c] * g[c];
+          e = fma(df[c], dg[c], e);
         }
       }
-    } else {
-      // single open cell: nodes c = 0..n-1, Dirichlet ends (the virtual node -1 adds f_0 g_0)
-      q = f[c] * g[c];
-      e = df[c] * dg[c];
-      if (c == 0) e += f[0] * g[0];
+      if (h == 0) es0 = e;
+      else es1 = e;
     }
-    Q[nu * ld + c] = q;
-    E[nu * ld + c] = e;
+    // lanes 0-15 end with the warp's total for nu0, lanes 16-31 with that for nu0 + kWarps: one
+    // exchanging step (each half keeps one function), then four steps within the halves
+    const bool up = (lane & 16) != 0;
+    double v = (up ? es1 : es0) + __shfl_xor_sync(0xffffffffu, up ? es0 : es1, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[2 * nu0 + 1] = v;
+    if (lane == 16 && nu0 + kWarps < m0) red[2 * (nu0 + kWarps) + 1] = v;
   }
   __syncthreads();
-  // P1 sums per nu: red[2 nu] = sum_c Q[nu][c], red[2 nu + 1] = sum_c E[nu][c], each by a group
-  // of 8 lanes (strided partial sums, then a fixed 3-level shuffle tree)
-  {
-    const int sub = tid & 7, lane = tid & 31;
-    const unsigned gmask = 0xffu << (lane & 24);
-    for (int sidx = tid >> 3; sidx < 2 * m0; sidx += kGramThreads / 8) {
-      const double *row = ((sidx & 1) ? E : Q) + (sidx >> 1) * ld;
-      double acc = 0.0;
-      for (int c = sub; c < nv; c += 8) acc += row[c];
-      acc += __shfl_xor_sync(gmask, acc, 4);
-      acc += __shfl_xor_sync(gmask, acc, 2);
-      acc += __shfl_xor_sync(gmask, acc, 1);
-      if (sub == 0) red[sidx] = acc;
-    }
-  }
-  __syncthreads();
-  const int Rt = s.Rt, mm = m0 * m0;
-  double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
-  if (tid < m0) {
-    const double dq = red[2 * tid], de = red[2 * tid + 1];
-    Cout[(int64_t)Rt * mm + tid] = de / D.h;
-    Cout[(int64_t)(Rt + 1) * mm + tid] = D.h * dq - de * D.h / 6.0;
-  }
 }
 
 __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__restrict__ sysv, int ldir) {
@@ -172,9 +249,24 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
   const int ld = nv + 1;  // padded row stride of Q (bank-conflict-free column reads)
   extern __shared__ double sm[];
   double *Q = sm;               // [m0][ld]
-  double *E = Q + m0 * ld;      // [m0][ld]  difference products per node (P1 forms)
-  double *red = E + m0 * ld;    // [m0][2]   Dsum, Esum per nu
-  gram_phase1(s, it, Q, E, red);
+  double *red = Q + m0 * ld;    // [m0][2]   row sum of Q, sum of the difference products per nu
+  __shared__ int rexp[kMaxM0];
+  gram_phase1(s, it, Q, red);
+  // P1 slots: the row sums of Q as exact fixed-point sums (the same numbers as the tensor-core
+  // route, which forms them from its digit planes)
+  q_row_exponents(Q, ld, m0, nv, rexp);
+  __syncthreads();
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, qsh = row_sum_shift(nv);
+    for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
+      long long acc = 0;
+      for (int c = lane; c < nv; c += 32) acc += row_sum_term(fixed62(Q[nu * ld + c], rexp[nu]), qsh);
+      acc = warp_sum_i64(acc);
+      if (lane == 0) red[2 * nu] = scale_pow2((double)acc, rexp[nu] + qsh - 62);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < m0) write_p1_slots(s, it, threadIdx.x, red[2 * threadIdx.x], red[2 * threadIdx.x + 1]);
 
   // ---- phase 2: C_r[nu] = sum_c V[r][c] Q[nu][c] ------------------------------------------
   const int Rt = s.Rt;
@@ -201,39 +293,13 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
 
 // ---- tensor-core route: exact digit slices of the FP64 operands -------------------------
 //
-// A row x[c] (c < nv) with max|x| = f 2^e, 1/2 <= f < 1, becomes the 62-bit fixed-point integers
-// X[c] = rint(x[c] 2^(62-e)) and then 7 balanced base-2^7 digits
+// The fixed-point integers X[c] of a row (fixed62 above) split into 7 balanced base-2^7 digits
 //   X = a_0 2^55 + a_1 2^48 + ... + a_6 2^13 + r,  a_0 in [-128, 128], a_k in [-64, 64], |r| <= 2^12,
 // so x[c] = 2^e (sum_k a_k 2^(-7(k+1)) + O(2^-50)).  Every digit is an integer of at most 8
 // significant bits, exact in BF16; products of two digits are exact in FP32 and sums of up to
 // 2^24 / 2^14 of them accumulate exactly.  Digit plane k of a row block goes to
 // planes + k * rows * Kpad + row * Kpad + c (BF16, Kpad >= nv, zero padded).
-//
-// X is formed from the bit fields of x with integer arithmetic only (the FP64 pipe of this GPU
-// runs at a small fraction of the integer rate): |x| = M 2^(ex - 1075) with M the 53-bit
-// significand, so X = M 2^(ex - 1013 - e), a left shift by at most 9 bits (|x| < 2^e) or a right
-// shift rounded to nearest, ties to even.
-__device__ __forceinline__ long long fixed62(double x, int e) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int bex = (int)((u >> 52) & 0x7ff);
-  const unsigned long long M = (u & ((1ull << 52) - 1)) | (bex ? (1ull << 52) : 0ull);
-  const int sh = (bex ? bex : 1) - 1013 - e;
-  unsigned long long X;
-  if (sh >= 0) {
-    X = M << sh;
-  } else if (sh > -64) {
-    const int r = -sh;
-    X = M >> r;
-    const unsigned long long rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
-    if (rem > half || (rem == half && (X & 1ull))) ++X;
-  } else {
-    X = 0;
-  }
-  return (u >> 63) ? -(long long)X : (long long)X;
-}
-
-__device__ __forceinline__ void digits7(double x, int e, int *a) {
-  long long X = fixed62(x, e);  // |X| <= 2^62
+__device__ __forceinline__ void digits7(long long X, int *a) {  // |X| <= 2^62
 #pragma unroll
   for (int k = 0; k < kSlices; ++k) {
     const int sh = 55 - 7 * k;
@@ -247,18 +313,6 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v|
   return (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
-// Magnitude key of x: the high word without the sign.  Keys order like |x| up to the low word,
-// and the largest key of a row carries the largest biased exponent.
-__device__ __forceinline__ unsigned mag_key(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
-
-// e with max |x| < 2^e over a row from its largest magnitude key: frexp's exponent of the largest
-// element (f 2^e, 1/2 <= f < 1) when it is normal, 0 when every element is below 2^-1022 (those
-// round to zero digits).
-__device__ __forceinline__ int scale_exponent_key(unsigned key) {
-  const int bex = (int)(key >> 20);
-  return bex ? bex - 1022 : 0;
-}
-
 __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
@@ -269,24 +323,23 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
   const int ld = nv + 1;
   extern __shared__ double sm[];
   double *Q = sm;
-  double *E = Q + m0 * ld;
-  double *red = E + m0 * ld;
+  double *red = Q + m0 * ld;
   __shared__ int rexp[kMaxM0];
-  gram_phase1(s, it, Q, E, red);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int nu = warp; nu < m0; nu += kGramThreads / 32) {
-    unsigned mx = 0;
-    for (int c = lane; c < nv; c += 32) mx = max(mx, mag_key(Q[nu * ld + c]));
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0) rexp[nu] = scale_exponent_key(mx);
-  }
+  __shared__ unsigned long long qsum[kMaxM0];  // exact fixed-point row sums of Q (two's complement)
+  gram_phase1(s, it, Q, red);
+  const int tid = threadIdx.x, lane = tid & 31;
+  q_row_exponents(Q, ld, m0, nv, rexp);
+  if (tid < m0) qsum[tid] = 0ull;
   __syncthreads();
   const int64_t rows = (int64_t)D.Jc * m0 * m0;
   const int64_t row0 = ((int64_t)(it.jw - D.cw0) * m0 + it.mu) * m0;
   unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
   int *rowexp = reinterpret_cast<int *>(s.ws + D.offRE);
   if (tid < m0) rowexp[row0 + tid] = rexp[tid];
-  // two adjacent columns per thread (Kp is even): one 32-bit store per digit plane
+  // two adjacent columns per thread (Kp is even): one 32-bit store per digit plane.  Kp is a
+  // multiple of 64, so the 32 lanes of a warp share nu: the row-sum terms of the fixed-point
+  // values are summed over the warp, then added to the row's exact sum
+  const int qsh = row_sum_shift(nv);
   const int half = Kp >> 1;
   const int items = m0 * half;
   for (int p0 = tid; p0 < items; p0 += kGramThreads) {
@@ -294,14 +347,28 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
     int a[kSlices], b[kSlices];
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0;
-    if (c < nv) digits7(Q[nu * ld + c], rexp[nu], a);
-    if (c + 1 < nv) digits7(Q[nu * ld + c + 1], rexp[nu], b);
+    long long term = 0;
+    if (c < nv) {
+      const long long X = fixed62(Q[nu * ld + c], rexp[nu]);
+      term = row_sum_term(X, qsh);
+      digits7(X, a);
+    }
+    if (c + 1 < nv) {
+      const long long X = fixed62(Q[nu * ld + c + 1], rexp[nu]);
+      term += row_sum_term(X, qsh);
+      digits7(X, b);
+    }
     const int64_t at = (row0 + nu) * Kp + c;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
       *reinterpret_cast<unsigned *>(planes + k * rows * Kp + at) =
           (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
+    term = warp_sum_i64(term);
+    if (lane == 0) atomicAdd(&qsum[nu], (unsigned long long)term);
   }
+  __syncthreads();
+  if (tid < m0)
+    write_p1_slots(s, it, tid, scale_pow2((double)(long long)qsum[tid], rexp[tid] + qsh - 62), red[2 * tid + 1]);
 }
 
 // Digit planes of the potential factors: one CTA per (system, direction, rank term r).
@@ -338,8 +405,8 @@ __global__ void __launch_bounds__(kGramThreads) k_vslice(const SysDev *__restric
     int a[kSlices], b[kSlices];
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0;
-    if (c < nv) digits7(v[c], e, a);
-    if (c + 1 < nv) digits7(v[c + 1], e, b);
+    if (c < nv) digits7(fixed62(v[c], e), a);
+    if (c + 1 < nv) digits7(fixed62(v[c + 1], e), b);
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
       *reinterpret_cast<unsigned *>(planes + ((int64_t)k * Rt + r) * Kp + c) =
@@ -392,7 +459,7 @@ cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items,
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
                              int max_nv, cudaStream_t st, int ldir) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
+  const size_t smem = sizeof(double) * ((size_t)max_m0 * (max_nv + 1) + 2 * max_m0);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -408,7 +475,7 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
                                int ldir) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * ((size_t)2 * max_m0 * (max_nv + 1) + 2 * max_m0);
+  const size_t smem = sizeof(double) * ((size_t)max_m0 * (max_nv + 1) + 2 * max_m0);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
