@@ -14,12 +14,13 @@
 // converted to FP64 once.
 //
 // One CTA of 256 threads per (system, direction, 128-row tile, 64-column tile):
-//   * TMA (cp.async.bulk.tensor.2d, 128-byte swizzle, no multicast) brings, per 64-wide K chunk,
-//     the 7 digit planes of the A tile (7 x 128 x 64 BF16) and of the B tile (7 x 64 x 64) into
-//     shared memory (168 KB, one stage);
+//   * TMA (cp.async.bulk.tensor.2d, 64-byte swizzle, no multicast) brings, per 32-wide K chunk,
+//     the 7 digit planes of the A tile (7 x 128 x 32 BF16) and of the B tile (7 x 64 x 32) into
+//     one of two shared-memory stages (84 KB each): the load of chunk k + 1 runs while the MMAs
+//     of chunk k execute;
 //   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 64, K = 16) for every
 //     pair (a, b) into the TMEM accumulator of its diagonal s = a + b (7 x 64 columns of the
-//     512 allocated), then tcgen05.commit to an mbarrier;
+//     512 allocated), then tcgen05.commit to the stage's mbarrier, which frees the stage;
 //   * the 8 warps read the accumulators back with tcgen05.ld (32x32b; warp w reads TMEM lanes
 //     32 (w % 4) .. + 31, warps w and w + 4 half of the columns each), recombine the 7 diagonals
 //     and store the FP64 results in the layout of the FP64 route.
@@ -39,12 +40,13 @@ namespace {
 constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 read TMEM lane quadrant w % 4, half the columns each
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
-constexpr int kChunkK = 64;  // one 128-byte swizzle atom of BF16
+constexpr int kChunkK = 32;  // one 64-byte swizzle atom of BF16
+constexpr int kStages = 2;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kABytes = kTileM * kChunkK * 2;  // 16 KB per digit plane
-constexpr uint32_t kBBytes = kTileN * kChunkK * 2;  // 8 KB per digit plane
+constexpr uint32_t kABytes = kTileM * kChunkK * 2;  // 8 KB per digit plane
+constexpr uint32_t kBBytes = kTileN * kChunkK * 2;  // 4 KB per digit plane
 constexpr uint32_t kStageBytes = kSlices * (kABytes + kBBytes);
-constexpr size_t kSmemBytes = kStageBytes + 1024;  // + alignment slack for the 1024-byte swizzle base
+constexpr size_t kSmemBytes = kStages * kStageBytes + 1024;  // + alignment slack for the swizzle base
 constexpr long long kWaitCycles = 2000000000ll;    // ~1 s at 2 GHz
 
 struct TcJob {
@@ -80,12 +82,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (start >> 4 in bits 0-13, leading offset 16 B (unused) in 16-29, stride 1024 B
-// in 32-45, descriptor version 1 in 46-48, swizzle mode 2 = 128B in 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor: K-major tile of 64-byte rows, 64-byte swizzle, 8-row groups
+// 512 bytes apart (start >> 4 in bits 0-13, leading offset 16 B (unused) in 16-29, stride 512 B
+// in 32-45, descriptor version 1 in 46-48, swizzle mode 4 = 64B in 61-63).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
@@ -121,12 +123,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restrict__ jobs,
                                                            const TcArgs *__restrict__ args, unsigned *flags) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_free[kStages];
   __shared__ uint32_t tmem_slot;
   __shared__ int ok_sh;
   unsigned char *tiles =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t sA = smem_u32(tiles), sB = sA + kSlices * kABytes;
+  const uint32_t s0 = smem_u32(tiles);
   const TcJob job = jobs[blockIdx.x];
   const TcArgs &P = args[job.sys * 3 + job.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,8 +141,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   if (threadIdx.x == 32) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_load)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)) : "memory");
+    for (int st = 0; st < kStages; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[st])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_free[st])) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ok_sh = 1;
   }
@@ -149,46 +153,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
   const uint32_t tmem = tmem_slot;
 
   if (threadIdx.x == 0) {
-    const uint32_t bl = smem_u32(&bar_load), bm = smem_u32(&bar_mma);
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapB)) : "memory");
     const int nchunks = P.Kpad / kChunkK;
-    uint32_t phase = 0;
-    bool ok = true, mma_pending = false;
+    // chunk ch uses stage ch % 2 for the (ch / 2)-th time: its barriers complete with parity (ch / 2) & 1
+    auto load = [&](int ch) {
+      const int st = ch & 1;
+      const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes, bf = smem_u32(&bar_full[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"(kStageBytes) : "memory");
+      for (int a = 0; a < kSlices; ++a) tma_load_2d(sA + a * kABytes, &P.mapA, ch * kChunkK, a * P.rows + job.row0, bf);
+      for (int b = 0; b < kSlices; ++b) tma_load_2d(sB + b * kBBytes, &P.mapB, ch * kChunkK, b * P.Rt + job.n0, bf);
+    };
+    bool ok = true;
+    int last_commit = -1;  // the last chunk whose MMAs were committed
+    int last_load = 0, last_arrived = -1;  // the last chunk loaded / seen in shared memory
+    load(0);
     for (int ch = 0; ch < nchunks && ok; ++ch) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl), "r"(kStageBytes) : "memory");
-      for (int a = 0; a < kSlices; ++a)
-        tma_load_2d(sA + a * kABytes, &P.mapA, ch * kChunkK, a * P.rows + job.row0, bl);
-      for (int b = 0; b < kSlices; ++b)
-        tma_load_2d(sB + b * kBBytes, &P.mapB, ch * kChunkK, b * P.Rt + job.n0, bl);
-      if (!mbar_wait(bl, phase)) {
+      const int st = ch & 1;
+      if (ch + 1 < nchunks) {
+        // stage (ch + 1) % 2 is free once the MMAs of chunk ch - 1 are done
+        if (ch >= 1 && !mbar_wait(smem_u32(&bar_free[st ^ 1]), ((ch - 1) >> 1) & 1)) {
+          ok = false;
+          break;
+        }
+        load(ch + 1);
+        last_load = ch + 1;
+      }
+      if (!mbar_wait(smem_u32(&bar_full[st]), (ch >> 1) & 1)) {
         ok = false;
         break;
       }
+      last_arrived = ch;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes;
       for (int s = 0; s < kSlices; ++s)
         for (int a = 0; a <= s; ++a) {
           const int b = s - a;
           for (int kk = 0; kk < kChunkK / 16; ++kk) {
-            const uint64_t ad = sw128_desc(sA + a * kABytes + kk * 32);
-            const uint64_t bd = sw128_desc(sB + b * kBBytes + kk * 32);
+            const uint64_t ad = sw64_desc(sA + a * kABytes + kk * 32);
+            const uint64_t bd = sw64_desc(sB + b * kBBytes + kk * 32);
             mma_bf16(tmem + (uint32_t)(s * kTileN), ad, bd, (ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
           }
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bm)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar_free[st]))
                    : "memory");
-      mma_pending = true;
-      if (!mbar_wait(bm, phase)) {
-        ok = false;
-        break;
-      }
-      mma_pending = false;
-      phase ^= 1u;
+      last_commit = ch;
     }
+    // the last commit covers every MMA issued before it (in-order completion)
+    if (last_commit >= 0 &&
+        !mbar_wait(smem_u32(&bar_free[last_commit & 1]), (last_commit >> 1) & 1))
+      ok = false;
     if (!ok) {
       atomicOr(flags, kFlagTimeout);
       ok_sh = 0;
-      if (mma_pending) mbar_wait(bm, phase);  // bounded: give in-flight MMAs a chance to drain
+      // bounded: give the loads still in flight a chance to land before the CTA exits
+      for (int ch = last_arrived + 1; ch <= last_load; ++ch) mbar_wait(smem_u32(&bar_full[ch & 1]), (ch >> 1) & 1);
     }
   }
   __syncthreads();
@@ -263,7 +283,7 @@ bool encode_planes(CUtensorMap *map, void *base, int K, int rows_total, int box_
   const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
