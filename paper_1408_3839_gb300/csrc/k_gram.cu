@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
 //   X = a_0 2^55 + a_1 2^48 + ... + a_6 2^13 + r,  a_0 in [-128, 128], a_k in [-64, 64], |r| <= 2^12,
 // so x[c] = 2^e (sum_k a_k 2^(-7(k+1)) + O(2^-50)).  Every digit is an integer of at most 8
 // significant bits, exact in BF16; products of two digits are exact in FP32 and sums of up to
-// 2^24 / 2^14 of them accumulate exactly.  Digit plane k of a row block goes to
-// planes + k * rows * Kpad + row * Kpad + c (BF16, Kpad >= nv, zero padded).
+// 2^24 / 2^14 of them accumulate exactly.  Digit k of (row, c) goes to
+// planes + ((k * Kpad / 32 + c / 32) * rows + row) * 32 + c % 32 (BF16, Kpad >= nv, zero padded):
+// chunk-major, so that a 32-column tile of consecutive rows is contiguous.
 __device__ __forceinline__ void digits7(long long X, int *a) {  // |X| <= 2^62
 #pragma unroll
   for (int k = 0; k < kSlices; ++k) {
@@ -358,10 +359,12 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
       term += row_sum_term(X, qsh);
       digits7(X, b);
     }
-    const int64_t at = (row0 + nu) * Kp + c;
+    // c and c + 1 share a 32-column chunk
+    const int64_t at = ((int64_t)(c / kPlaneChunk) * rows + row0 + nu) * kPlaneChunk + c % kPlaneChunk;
+    const int64_t plane = (int64_t)(Kp / kPlaneChunk) * rows * kPlaneChunk;  // = rows * Kp
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
-      *reinterpret_cast<unsigned *>(planes + k * rows * Kp + at) =
+      *reinterpret_cast<unsigned *>(planes + k * plane + at) =
           (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
     term = warp_sum_i64(term);
     if (lane == 0) atomicAdd(&qsum[nu], (unsigned long long)term);
@@ -409,7 +412,8 @@ __global__ void __launch_bounds__(kGramThreads) k_vslice(const SysDev *__restric
     if (c + 1 < nv) digits7(fixed62(v[c + 1], e), b);
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
-      *reinterpret_cast<unsigned *>(planes + ((int64_t)k * Rt + r) * Kp + c) =
+      *reinterpret_cast<unsigned *>(
+          planes + (((int64_t)k * (Kp / kPlaneChunk) + c / kPlaneChunk) * Rt + r) * kPlaneChunk + c % kPlaneChunk) =
           (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
   }
 }

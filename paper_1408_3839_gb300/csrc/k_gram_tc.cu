@@ -40,7 +40,7 @@ namespace {
 constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 read TMEM lane quadrant w % 4, half the columns each
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
-constexpr int kChunkK = 32;  // one 64-byte swizzle atom of BF16
+constexpr int kChunkK = kPlaneChunk;  // one 64-byte swizzle atom of BF16
 constexpr int kStages = 2;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kABytes = kTileM * kChunkK * 2;  // 8 KB per digit plane
@@ -161,8 +161,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
       const int st = ch & 1;
       const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes, bf = smem_u32(&bar_full[st]);
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"(kStageBytes) : "memory");
-      for (int a = 0; a < kSlices; ++a) tma_load_2d(sA + a * kABytes, &P.mapA, ch * kChunkK, a * P.rows + job.row0, bf);
-      for (int b = 0; b < kSlices; ++b) tma_load_2d(sB + b * kBBytes, &P.mapB, ch * kChunkK, b * P.Rt + job.n0, bf);
+      // chunk-major planes: rows (k * nchunks + ch) * rows + row0 .. of a 32-wide 2D view
+      for (int a = 0; a < kSlices; ++a)
+        tma_load_2d(sA + a * kABytes, &P.mapA, 0, (a * nchunks + ch) * P.rows + job.row0, bf);
+      for (int b = 0; b < kSlices; ++b)
+        tma_load_2d(sB + b * kBBytes, &P.mapB, 0, (b * nchunks + ch) * P.Rt + job.n0, bf);
     };
     bool ok = true;
     int last_commit = -1;  // the last chunk whose MMAs were committed
@@ -275,11 +278,13 @@ EncodeTiled encode_fn() {
   return fn;
 }
 
-bool encode_planes(CUtensorMap *map, void *base, int K, int rows_total, int box_rows) {
+// The chunk-major planes [kSlices][K / 32][rows][32] as a 2D tensor of 32-wide rows: a box of
+// box_rows rows at y = (k K / 32 + ch) rows + row0 is one contiguous block.
+bool encode_planes(CUtensorMap *map, void *base, int K, int rows, int box_rows) {
   EncodeTiled fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows_total};
-  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint64_t dims[2] = {(cuuint64_t)kPlaneChunk, (cuuint64_t)kSlices * (K / kPlaneChunk) * rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kPlaneChunk * 2};
   const cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -312,8 +317,8 @@ cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, si
       const int rows = D.Jc * s.m0 * s.m0;  // the contracted window blocks cw0 .. cw0 + Jc - 1
       if (D.Kpad % kChunkK != 0 || D.Kpad > 448 || rows < 1) return cudaErrorNotSupported;
       TcArgs &a = args[(size_t)i * 3 + l];
-      if (!encode_planes(&a.mapA, s.ws + D.offA, D.Kpad, kSlices * rows, kTileM) ||
-          !encode_planes(&a.mapB, s.ws + D.offB, D.Kpad, kSlices * s.Rt, kTileN))
+      if (!encode_planes(&a.mapA, s.ws + D.offA, D.Kpad, rows, kTileM) ||
+          !encode_planes(&a.mapB, s.ws + D.offB, D.Kpad, s.Rt, kTileN))
         return cudaErrorInvalidValue;
       a.C = s.ws + D.offC + (size_t)D.cw0 * (s.Rt + 2) * s.m0 * s.m0;
       a.rowexp = reinterpret_cast<const int *>(s.ws + D.offRE);

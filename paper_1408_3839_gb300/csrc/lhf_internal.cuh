@@ -17,6 +17,9 @@ constexpr int kMaxNuc = LHF_MAX_NUCLEI;
 constexpr int kMaxR = LHF_MAX_R;
 constexpr int kMaxRt = kMaxNuc * kMaxR;
 constexpr int kSlices = 7;  // base-2^7 digit slices per FP64 operand on the tensor-core route
+// Digit planes are stored chunk-major, [plane][K / kPlaneChunk][row][kPlaneChunk]: the tile of 128
+// (or 64) rows x kPlaneChunk columns that one tensor-core load takes is one contiguous block.
+constexpr int kPlaneChunk = 32;
 // A Bloch function is numerically absent at a k-point when Re Sbar_ii <= kDropTol * s0_i.
 constexpr double kDropTol = LHF_DROP_TOL;
 // Canonical orthogonalisation drops directions of the scaled overlap below kLindepTol.  The
@@ -50,8 +53,8 @@ struct DirDev {
   // tensor-core route (LHF_MIXED): digit planes and scale exponents
   int Kpad;       // nv rounded up to a multiple of 64
   int pad2_;
-  int64_t offA;   // BF16 [kSlices][Jc m0 m0][Kpad] digit planes of the folded products
-  int64_t offB;   // BF16 [kSlices][Rt][Kpad] digit planes of the potential factors
+  int64_t offA;   // BF16 [kSlices][Kpad / 32][Jc m0 m0][32] digit planes of the folded products
+  int64_t offB;   // BF16 [kSlices][Kpad / 32][Rt][32] digit planes of the potential factors
   int64_t offRE;  // int [Jc m0 m0] row scale exponents
   int64_t offCE;  // int [Rt] potential-row scale exponents
   int64_t offF;   // k-space route: complex [L][Rt+2][m0][m0] 1D DFTs of the factors (0 when unused)
