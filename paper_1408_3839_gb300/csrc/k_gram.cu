@@ -294,20 +294,28 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
 // ---- tensor-core route: exact digit slices of the FP64 operands -------------------------
 //
 // The fixed-point integers X[c] of a row (fixed62 above) split into 7 balanced base-2^7 digits
-//   X = a_0 2^55 + a_1 2^48 + ... + a_6 2^13 + r,  a_0 in [-128, 128], a_k in [-64, 64], |r| <= 2^12,
+//   X = a_0 2^55 + a_1 2^48 + ... + a_6 2^13 + r,  a_0 in [-128, 128], a_k in [-64, 63], -2^12 <= r < 2^12,
 // so x[c] = 2^e (sum_k a_k 2^(-7(k+1)) + O(2^-50)).  Every digit is an integer of at most 8
 // significant bits, exact in BF16; products of two digits are exact in FP32 and sums of up to
 // 2^24 / 2^14 of them accumulate exactly.  Digit k of (row, c) goes to
 // planes + ((k * Kpad / 32 + c / 32) * rows + row) * 32 + c % 32 (BF16, Kpad >= nv, zero padded):
 // chunk-major, so that a 32-column tile of consecutive rows is contiguous.
+// Digits from the least significant end: the 13 remainder bits round half up into digit 6 (a carry
+// when bit 12 is set), then each 7-bit field plus the incoming carry becomes a digit in [-64, 63]
+// and a carry; the top digit takes the bits from 55 up and the last carry.  The digits and the
+// remainder (X mod 2^13, balanced) are those of rounding from the top down, up to the choice
+// between +64 and -64 plus a carry, with one field extract and three integer steps per digit.
 __device__ __forceinline__ void digits7(long long X, int *a) {  // |X| <= 2^62
+  const unsigned long long U = (unsigned long long)X;
+  int carry = (int)((U >> 12) & 1u);
 #pragma unroll
-  for (int k = 0; k < kSlices; ++k) {
+  for (int k = kSlices - 1; k >= 1; --k) {
     const int sh = 55 - 7 * k;
-    const long long d = (X + (1ll << (sh - 1))) >> sh;
-    X -= d << sh;
-    a[k] = (int)d;
+    const int t = (int)((U >> sh) & 0x7fu) + carry;
+    carry = (t + 64) >> 7;
+    a[k] = t - (carry << 7);
   }
+  a[0] = (int)(X >> 55) + carry;
 }
 
 __device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v| <= 256
