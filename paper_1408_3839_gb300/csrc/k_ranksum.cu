@@ -11,7 +11,7 @@
 //
 // A thread takes one entry (mu, nu) of kRankGroup consecutive direction-0 window blocks with the
 // same (j1, j2): the weights w_r = c_r C1_r C2_r are formed once and each block costs one FMA
-// per rank term.  Factor blocks outside the contracted half of a window are read from their
+// per rank term.  The blocks outside the window get one CTA each (block decoded once per CTA).  Factor blocks outside the contracted half of a window are read from their
 // mirrors, C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
 // Consecutive threads take consecutive entries: the factor slots are read coalesced.
 #include "lhf_internal.cuh"
@@ -32,18 +32,19 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
   const int m0 = s.m0, mm = m0 * m0, Rt = s.Rt;
   const DirDev &D0 = s.d[0], &D1 = s.d[1], &D2 = s.d[2];
   if ((int)blockIdx.x >= compute_ctas) {
-    // zeros outside the window (a6): thread per (block, entry)
-    const int64_t item = (int64_t)(blockIdx.x - compute_ctas) * blockDim.x + threadIdx.x;
-    if (item >= (int64_t)s.nblocks * mm) return;
-    const int64_t blk = item / mm;
-    const int jj[3] = {(int)(blk / ((int64_t)D1.L * D2.L)), (int)((blk / D2.L) % D1.L), (int)(blk % D2.L)};
-    for (int l = 0; l < 3; ++l)
-      if (wrap_block(jj[l] - s.d[l].jlo, s.d[l].L) >= s.d[l].J) {
-        s.H[item] = 0.0;
-        s.S[item] = 0.0;
-        return;
-      }
-    return;  // inside the window: written by the compute threads
+    // zeros outside the window (a6): CTA per block, thread per entry
+    const int blk = (int)blockIdx.x - compute_ctas;
+    if (blk >= s.nblocks) return;
+    const int jj[3] = {blk / (D1.L * D2.L), (blk / D2.L) % D1.L, blk % D2.L};
+    bool outside = false;
+    for (int l = 0; l < 3; ++l) outside |= wrap_block(jj[l] - s.d[l].jlo, s.d[l].L) >= s.d[l].J;
+    if (!outside) return;  // inside the window: written by the compute threads
+    double *H = s.H + (int64_t)blk * mm, *S = s.S + (int64_t)blk * mm;
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      H[i] = 0.0;
+      S[i] = 0.0;
+    }
+    return;
   }
   const int groups = (D0.J + kRankGroup - 1) / kRankGroup;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,10 +94,10 @@ int ranksum_compute_items(const SysDev &s) {
   return s.d[1].J * s.d[2].J * groups * s.m0 * s.m0;
 }
 
-cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_items, cudaStream_t st) {
-  if (max_items <= 0 || nsys <= 0) return cudaSuccess;
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, cudaStream_t st) {
+  if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const int compute_ctas = (max_compute_items + 255) / 256;
-  dim3 grid(compute_ctas + (max_items + 255) / 256, nsys);
+  dim3 grid(compute_ctas + max_blocks, nsys);
   kmark(LHF_K_RANKSUM, 1, st);
   k_ranksum<<<grid, 256, 0, st>>>(sys, compute_ctas);
   kmark(LHF_K_RANKSUM, 0, st);

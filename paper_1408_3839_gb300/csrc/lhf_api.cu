@@ -49,7 +49,7 @@ struct Plan {
   size_t s0_off = 0;   // offset of s0 [m0]
   bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
-  int basis_items = 0 /* rows */, pot_rows = 0, gram_blocks = 0, rank_items = 0, rank_compute = 0;
+  int basis_items = 0 /* rows */, pot_rows = 0, gram_blocks = 0, rank_items = 0 /* blocks */, rank_compute = 0;
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
@@ -496,7 +496,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.tri_off = off;  // one slot per k-point bounds the solved ones
     off = align_up(off + (size_t)sd.nblocks * (2 * m0 + 1));
     P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
-    P.rank_items = sd.nblocks * mm;  // zeros outside the window
+    P.rank_items = sd.nblocks;  // zeros outside the window: CTA per block
     P.rank_compute = lhf::ranksum_compute_items(sd);
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
