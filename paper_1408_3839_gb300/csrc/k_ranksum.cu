@@ -19,7 +19,7 @@
 namespace lhf {
 namespace {
 
-constexpr int kRankGroup = 4;
+constexpr int kRankGroup = 2;
 
 __device__ __forceinline__ int wrap_block(int j, int L) {
   j %= L;
