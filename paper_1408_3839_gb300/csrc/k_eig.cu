@@ -839,10 +839,11 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
 //   * Sturm counts: the number of eigenvalues below x is the number of negative pivots of
 //     T - x I = L D L^T, r_0 = d_0 - x, r_j = (d_j - x) - e_(j-1)^2 / r_(j-1) (Sylvester's law of
 //     inertia).  In FP32 the computed count is the exact count of a matrix within
-//     eta ~ 6 eps_32 max|T| < 2^-19 of T (rounding of the recurrence as backward perturbations
+//     eta ~ 6 eps_32 max|T| < 2^-21 of T (rounding of the recurrence as backward perturbations
 //     of the entries), so count32(y) lies between #(lambda < y - eta) and #(lambda < y + eta).
-//   * FP32 bisection: 24 halvings of [lo, hi] give [a, b] with count32(a) <= i < count32(b);
-//     with delta = 2^-17 > eta, count32(a - 2 delta) = i and count32(b + 2 delta) = i + 1 prove
+//   * FP32 quadrisection: 12 steps, each shrinking [lo, hi] by 4 with three counts evaluated
+//     together (24 halvings), give [a, b] with count32(a) <= i < count32(b);
+//     with delta = 2^-19 > 4 eta, count32(a - 2 delta) = i and count32(b + 2 delta) = i + 1 prove
 //     that [A, B] = [a - delta, b + delta] holds lambda_i alone, at least delta - eta from either
 //     end, and that det(T - x I) has the sign (-1)^i at A.
 //   * FP64 Newton's iteration on q_m(x) = det(T - x I) from the leading-minor recurrence
@@ -955,6 +956,31 @@ __device__ int tri_count32(const float *df, const float *e2f, int m, float x) {
   return c;
 }
 
+// The same counts at three points at once: three independent recurrences in one loop, so that
+// each hides the others' latency (the reciprocals dominate a single chain).
+__device__ __forceinline__ void tri_count32x3(const float *df, const float *e2f, int m, float x0, float x1, float x2,
+                                              int &c0, int &c1, int &c2) {
+  float r0 = df[0] - x0, r1 = df[0] - x1, r2 = df[0] - x2;
+  if (r0 == 0.0f) r0 = -1e-30f;
+  if (r1 == 0.0f) r1 = -1e-30f;
+  if (r2 == 0.0f) r2 = -1e-30f;
+  c0 = r0 < 0.0f ? 1 : 0;
+  c1 = r1 < 0.0f ? 1 : 0;
+  c2 = r2 < 0.0f ? 1 : 0;
+  for (int j = 1; j < m; ++j) {
+    const float d = df[j], e = e2f[j - 1];
+    r0 = (d - x0) - __fdividef(e, r0);
+    r1 = (d - x1) - __fdividef(e, r1);
+    r2 = (d - x2) - __fdividef(e, r2);
+    if (r0 == 0.0f) r0 = -1e-30f;
+    if (r1 == 0.0f) r1 = -1e-30f;
+    if (r2 == 0.0f) r2 = -1e-30f;
+    c0 += r0 < 0.0f ? 1 : 0;
+    c1 += r1 < 0.0f ? 1 : 0;
+    c2 += r2 < 0.0f ? 1 : 0;
+  }
+}
+
 template <int G>
 __global__ void __launch_bounds__(kTriMaxThreads) k_tridiag_eig(const SysDev *__restrict__ sysv, unsigned *flags,
                                                               unsigned long long *counters) {
@@ -1003,16 +1029,29 @@ __global__ void __launch_bounds__(kTriMaxThreads) k_tridiag_eig(const SysDev *__
   double x = INFINITY;
   int passes = 0;
   if (i < m) {
-    // FP32 bisection on the pivot counts
+    // FP32 quadrisection on the pivot counts (count(a) <= i < count(b) throughout): three points
+    // per step, the bracket shrinks by 4, 12 steps as 24 of bisection
     float a = (float)lo, b = (float)hi;
-    for (int it = 0; it < 24; ++it) {
-      const float mid = 0.5f * (a + b);
-      if (tri_count32(df, e2f, m, mid) <= i)
-        a = mid;
-      else
-        b = mid;
+    for (int it = 0; it < 12; ++it) {
+      const float w = b - a;
+      const float p1 = a + 0.25f * w, p2 = a + 0.5f * w, p3 = a + 0.75f * w;
+      int c1, c2, c3;
+      tri_count32x3(df, e2f, m, p1, p2, p3, c1, c2, c3);
+      if (c1 > i) {
+        b = p1;
+      } else if (c2 > i) {
+        a = p1;
+        b = p2;
+      } else if (c3 > i) {
+        a = p2;
+        b = p3;
+      } else {
+        a = p3;
+      }
     }
-    const double delta = 0x1p-17;
+    // isolation margin delta = 2^-19 > 4 eta (eta: the FP32 counts' backward error, above);
+    // eigenvalues closer than ~2 delta go to the cluster path below
+    const double delta = 0x1p-19;
     bool done = false;
     if (tri_count32(df, e2f, m, (float)((double)a - 2.0 * delta)) == i &&
         tri_count32(df, e2f, m, (float)((double)b + 2.0 * delta)) == i + 1)
