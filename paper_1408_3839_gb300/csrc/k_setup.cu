@@ -63,11 +63,21 @@ __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
 // periodic lattice direction are spread over several CTAs.  In a periodic lattice direction
 // only the nodes of the support cells cell_lo .. cell_hi of the cell-0 copy (mod L, at most L
 // cells) are written -- the Gram kernels read nothing else, and every node outside them lies
-// beyond the cut (zero sample); other directions write the whole row (basis_row_samples).  The
-// neighbour's sample comes from the next lane, or is evaluated where the next lane holds no
-// node of the window (chunks end on warp boundaries).
-constexpr int kBasisThreads = 256;
-static_assert(kBasisChunk % 32 == 0, "chunks end on warp boundaries");
+// beyond the cut (zero sample); other directions write the whole row (basis_row_samples).
+//
+// A thread takes a run of kBasisRun consecutive samples.  Along a run the distance to the
+// centre advances by h, d_j = d_0 + j h (continuous across the periodic wrap of the node index:
+// the image changes with it), so that
+//   exp(-alpha d_j^2) = exp(-alpha d_0^2) E^j T_j,  E = exp(-2 alpha d_0 h),  T_j = exp(-alpha h^2 j^2)
+// with T from a per-CTA table: two exponentials per run instead of one per sample, within a few
+// ulps of the direct value (the rounding of the direct argument alpha d^2 near the cut is of the
+// same size).  Runs whose ends lie where exp(-alpha d^2) could underflow (alpha d^2 > 600, far
+// beyond the cut), and rows whose support window covers the whole period (several images per
+// node), take the direct per-sample evaluation.  The neighbour of a run's last sample is the
+// next lane's first sample, or is evaluated where the next lane holds none.
+constexpr int kBasisRun = 8;
+constexpr int kBasisThreads = kBasisChunk / kBasisRun;  // one run per thread and chunk
+static_assert(kBasisThreads % 32 == 0, "chunks end on warp boundaries");
 
 __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
@@ -92,24 +102,78 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
     start = (s.cell_lo[l][mu] % D.L) * D.nc;
     if (start < 0) start += D.n;
   }
+  const double al = s.alpha[mu], h = D.h, cut = s.cut[mu], pn = s.pnorm[mu];
+  const bool pdir = (s.kind[mu] == 1 + l);
+  __shared__ double T[kBasisRun];
+  if (threadIdx.x < kBasisRun) {
+    const double u = h * (double)threadIdx.x;
+    T[threadIdx.x] = exp(-al * (u * u));
+  }
+  __syncthreads();
+  // several images per node: direct evaluation (row-uniform)
+  const bool direct_row = D.periodic && s.node_span[l][mu] >= D.n;
   const int lane = threadIdx.x & 31;
   const int kend = min(count, (b + 1) * kBasisChunk);
-  for (int k0 = b * kBasisChunk + (threadIdx.x & ~31); k0 < kend; k0 += kBasisThreads) {
-    const int k = k0 + lane;
-    const bool valid = k < kend;
-    int e = start + k;
-    if (e >= nx) e -= nx;  // periodic wrap (start < n = nx there)
-    const double g = valid ? basis_sample(s, l, mu, e) : 0.0;
-    // the whole warp takes part in the shuffle
-    double gn = __shfl_down_sync(0xffffffffu, g, 1);
-    if (!valid) continue;
-    s.ws[D.offG + (int64_t)mu * nx + e] = g;
+  const int k0 = b * kBasisChunk + (int)threadIdx.x * kBasisRun;
+  const bool has = k0 < kend;
+  int e0 = start + k0;
+  if (e0 >= nx) e0 -= nx;  // periodic wrap (start < n = nx there)
+  double g[kBasisRun];
+  if (has) {
+    // offset of the run's first sample in the support window and its distance to the centre of
+    // the image that holds it (as basis_sample); the recurrence needs the window offset not to
+    // wrap inside the run (the image changes there)
+    int rel = e0 - s.node_lo[l][mu];
+    const int wrapped = (D.periodic && rel < 0) ? 1 : 0;
+    if (wrapped) rel += D.n;
+    double d0 = D.x0 + (e0 - D.gext + 0.5) * h - s.centre[mu][l];
+    if (D.periodic) d0 += (double)(s.node_wrap[l][mu] + wrapped) * (D.L * D.b);
+    const double dl = d0 + (kBasisRun - 1) * h;
+    const bool direct = direct_row || (D.periodic && rel + kBasisRun - 1 >= D.n) || al * (d0 * d0) > 600.0 ||
+                        al * (dl * dl) > 600.0;
+    if (direct) {
+#pragma unroll
+      for (int j = 0; j < kBasisRun; ++j) {
+        int e = e0 + j;
+        if (e >= nx) e -= nx;
+        g[j] = k0 + j < kend ? basis_sample(s, l, mu, e) : 0.0;
+      }
+    } else {
+      const double g0 = exp(-al * (d0 * d0)), E = exp(-2.0 * al * d0 * h);
+      double P = 1.0;
+#pragma unroll
+      for (int j = 0; j < kBasisRun; ++j) {
+        // the widened window (exact zeros outside it) and the cut, as basis_sample
+        const int rj = rel + j;
+        const double dj = d0 + j * h;
+        double v = g0 * P * T[j];
+        if (pdir) v *= pn * dj;
+        g[j] = (k0 + j < kend && rj >= 0 && rj < s.node_span[l][mu] && fabs(dj) <= cut) ? v : 0.0;
+        P *= E;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kBasisRun; ++j) g[j] = 0.0;
+  }
+  // the whole warp takes part in the shuffle: the next run's first sample
+  double gn = __shfl_down_sync(0xffffffffu, g[0], 1);
+  if (!has) return;
+#pragma unroll
+  for (int j = 0; j < kBasisRun; ++j) {
+    if (k0 + j >= kend) break;
+    int e = e0 + j;
+    if (e >= nx) e -= nx;
+    s.ws[D.offG + (int64_t)mu * nx + e] = g[j];
     if (D.offD < 0) continue;
+    double nxt;
     if (e + 1 == D.n)
-      gn = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
-    else if (lane == 31 || k + 1 == kend)
-      gn = basis_sample(s, l, mu, e + 1);
-    s.ws[D.offD + (int64_t)mu * D.n + e] = g - gn;
+      nxt = D.periodic ? basis_sample(s, l, mu, 0) : 0.0;
+    else if (j + 1 < kBasisRun)
+      nxt = k0 + j + 1 < kend ? g[j + 1] : basis_sample(s, l, mu, e + 1);
+    else
+      nxt = (lane == 31 || k0 + kBasisRun >= kend) ? basis_sample(s, l, mu, e + 1) : gn;
+    s.ws[D.offD + (int64_t)mu * D.n + e] = g[j] - nxt;
   }
 }
 
