@@ -458,6 +458,7 @@ __device__ double image_sum_poisson(double pref, double lo, double hi, double c0
 // thread per cell i of the row.  Cells farther than 10 / t from every image within the window
 // get exactly zero (their integrals are below exp(-100) of the nearest image's).
 constexpr int kPotThreads = 128;
+constexpr int kPotRun = 4;  // cells per thread on the single open cell rows
 
 __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
@@ -496,6 +497,34 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
 
   double *out = s.ws + D.offV + (int64_t)r * D.nv;
   const int iend = min(D.nv, (chunk + 1) * kPotChunk);
+  if (!D.periodic && !D.lattice && taylor) {
+    // a single open cell row of narrow cells: exp(-m^2) S(m^2) / t at the cell centres, m_j =
+    // m_0 + j delta along a run of kPotRun cells, exp(-m_j^2) = exp(-m_0^2) E^j U_j with E =
+    // exp(-2 m_0 delta), U_j = exp(-delta^2 j^2) (|m| <= 10 + kPotRun delta within reach: no
+    // underflow); cells beyond reach stay exact zeros
+    __shared__ double U[kPotRun];
+    if (tid < kPotRun) U[tid] = exp(-(delta * tid) * (delta * tid));
+    __syncthreads();
+    for (int i0 = chunk * kPotChunk + kPotRun * tid; i0 < iend; i0 += kPotRun * kPotThreads) {
+      const double m0 = t * (D.x0 + (i0 + 0.5) * D.h - c0);
+      const double g0 = exp(-m0 * m0), E = exp(-2.0 * m0 * delta);
+      double P = 1.0;
+#pragma unroll
+      for (int j = 0; j < kPotRun; ++j) {
+        const int i = i0 + j;
+        if (i >= iend) break;
+        const double lo = D.x0 + i * D.h, hi = lo + D.h;
+        double v = 0.0;
+        if (lo - reach <= c0 && c0 <= hi + reach) {
+          const double m = m0 + j * delta;
+          v = g0 * P * U[j] * taylor_S(bc, J, m * m) * invt;
+        }
+        out[i] = v;
+        P *= E;
+      }
+    }
+    return;
+  }
   for (int i = chunk * kPotChunk + tid; i < iend; i += kPotThreads) {
     double v = 0.0;
     if (D.periodic) {
