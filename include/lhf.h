@@ -307,7 +307,7 @@ lhf_status lhf_stage_times(lhf_ctx *ctx, double *ms, int *launches);
  * string; NULL outside 0 .. LHF_NUM_KERNELS - 1). */
 enum {
     LHF_K_BASIS = 0,         /* a1 basis samples and differences */
-    LHF_K_POTENTIAL = 1,     /* a2 potential factors */
+    LHF_K_POTENTIAL = 1,     /* a2 potential factors (two launches: row constants, rows) */
     LHF_K_GRAM_FP64 = 2,     /* a3-a4 FP64 weighted Grams */
     LHF_K_GRAM_SLICE = 3,    /* a3-a4 folded products and their digit planes (LHF_MIXED) */
     LHF_K_VSLICE = 4,        /* digit planes of the potential factors (LHF_MIXED) */

@@ -451,6 +451,8 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     sd.d[l].offV = (int64_t)off;
     off = align_up(off + (size_t)Rt * sd.d[l].nv);
   }
+  sd.offPC = (int64_t)off;
+  off = align_up(off + (size_t)3 * s.R * lhf::kPotConst);
   for (int l = 0; l < 3; ++l) {
     sd.d[l].offC = (int64_t)off;
     off = align_up(off + (size_t)sd.d[l].J * (Rt + 2) * mm);

@@ -94,6 +94,7 @@ struct SysDev {
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
   int64_t offCb;
+  int64_t offPC;          // potential row constants [3][R][kPotConst] (k_pot_rows, read by k_potential)
   const double *zcell;    // box charges [L0][M0] (device) or null
 };
 
@@ -152,6 +153,9 @@ __host__ __device__ inline int basis_ctas(const SysDev &s) {
 // Potential rows: one CTA per (direction, rank term, chunk of kPotChunk cells); the host sizes
 // the launch with potential_ctas.
 constexpr int kPotChunk = 512;
+// Per (direction, sinc node) constants of a potential row: degree J of the cell series, its
+// coefficients, the Euler-Maclaurin polynomial and the Poisson weights.
+constexpr int kPotConst = 44;
 __host__ __device__ inline int potential_ctas(const SysDev &s) {
   int n = 0;
   for (int l = 0; l < 3; ++l) n += s.Rt * ((s.d[l].nv + kPotChunk - 1) / kPotChunk);

@@ -213,8 +213,9 @@ def test_batch_equals_single_runs_bitwise(ctx):
 
 def test_live_kernel_times_count_every_launch(ctx, lhf):
     """Per-kernel timing brackets each launch of the path: one pass of a 1D tube launches each
-    kernel of its route once (the DFT once per lattice level), and the kernel times fit inside
-    the stage times that bracket them."""
+    kernel of its route once (the DFT once per lattice level, the Grams once per direction, the
+    potential twice: row constants, then rows), and the kernel times fit inside the stage times
+    that bracket them."""
     cfg = CASES["tube_16_m16"]()
     ctx.setup(cfg)
     s = ctx.query_sizes()
@@ -232,8 +233,9 @@ def test_live_kernel_times_count_every_launch(ctx, lhf):
         expect = ["k_basis", "k_potential", "k_ranksum", "k_dft_pass", "k_overlap_norms", "k_eig",
                   "k_tridiag_eig"] + route
         for k, (ms, n) in kt.items():
-            # the Gram kernels run once per direction with a window (three for a tube)
-            want = (3 if k in ("k_gram_fp64", "k_gram_slice") else 1) if k in expect else 0
+            # the Gram kernels run once per direction with a window (three for a tube); the
+            # potential launches its row constants, then the rows
+            want = ({"k_gram_fp64": 3, "k_gram_slice": 3, "k_potential": 2}.get(k, 1)) if k in expect else 0
             assert n == want, (k, n)
             assert ms >= 0.0
         total_k = sum(v[0] for v in kt.values())
