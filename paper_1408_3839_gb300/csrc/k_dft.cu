@@ -160,7 +160,21 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   }
   __syncthreads();
   if (pow2) {
-    for (int hs = 1; hs < Ld; hs <<= 1) {
+    // the twiddles of the first two stages are 1 and -i (omega^(L/4)): no multiplications
+    for (int hs = 1; hs < Ld && hs <= 2; hs <<= 1) {
+      const int nb = (Ld / 2) * TW;
+      for (int k = tid; k < nb; k += kDftThreads) {
+        const int t = k % TW, b = k / TW;
+        const int kk = b % hs;
+        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
+        const double2 u = x[top * TW + t], v = x[bot * TW + t];
+        const double2 wv = kk == 0 ? v : make_double2(v.y, -v.x);  // v or -i v
+        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
+        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
+      }
+      __syncthreads();
+    }
+    for (int hs = 4; hs < Ld; hs <<= 1) {
       const int stride = Ld / (2 * hs);
       const int nb = (Ld / 2) * TW;
       for (int k = tid; k < nb; k += kDftThreads) {
