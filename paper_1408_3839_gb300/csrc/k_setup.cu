@@ -289,34 +289,24 @@ __constant__ double kEmB[kEmP] = {1.0 / 12.0,         -1.0 / 720.0,     1.0 / 30
                                   -1.0 / 1209600.0,   1.0 / 47900160.0, -691.0 / 1307674368000.0,
                                   1.0 / 74724249600.0};
 
-// Coefficients of C (C[k] of m^k, k <= kEmDeg) by one thread: P_0 = S(m^2) from the series
-// coefficients, P_(n+1)[k] = (k + 1) P_n[k + 1] - 2 P_n[k - 1] (the coefficients of P_n' - 2 m P_n),
-// and C accumulates B_2j / (2j)! s^(2j-1) P_(2j-1).
-__device__ void em_poly_thread(const double *bc, int J, double s, double *C) {
-  double P[32], acc[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    P[k] = ((k & 1) == 0 && k / 2 <= J) ? bc[k / 2] : 0.0;
-    acc[k] = 0.0;
-  }
-  double sp = s;  // s^(2j-1)
+// Coefficients of C (C[k] of m^k, k <= kEmDeg) by one warp, lane k holding the coefficient of
+// m^k: P_0 = S(m^2) from the series coefficients, P_(n+1) = P_n' - 2 m P_n (coefficients
+// (k + 1) P_n[k + 1] - 2 P_n[k - 1], neighbours by shuffles), C accumulating
+// B_2j / (2j)! s^(2j-1) P_(2j-1).
+__device__ void em_poly_warp(const double *bc, int J, double s, double *C) {
+  const int k = threadIdx.x & 31;
+  double P = ((k & 1) == 0 && k / 2 <= J) ? bc[k / 2] : 0.0;
+  double acc = 0.0, sp = s;  // s^(2j-1)
   for (int n = 0; n < 2 * kEmP - 1; ++n) {
-    double Pn[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const double up = k < 31 ? P[k + 1] : 0.0, dn = k > 0 ? P[k - 1] : 0.0;
-      Pn[k] = (double)(k + 1) * up - 2.0 * dn;
+    const double up = __shfl_down_sync(0xffffffffu, P, 1);  // coefficient of m^(k+1)
+    const double dn = __shfl_up_sync(0xffffffffu, P, 1);    // coefficient of m^(k-1)
+    P = (double)(k + 1) * (k < 31 ? up : 0.0) - 2.0 * (k > 0 ? dn : 0.0);
+    if (((n + 1) & 1) != 0) {
+      acc = fma(kEmB[n / 2] * sp, P, acc);  // j = (n + 2) / 2
+      sp *= s * s;
     }
-    const bool odd = ((n + 1) & 1) != 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      P[k] = Pn[k];
-      if (odd) acc[k] = fma(kEmB[n / 2] * sp, P[k], acc[k]);
-    }
-    if (odd) sp *= s * s;
   }
-#pragma unroll
-  for (int k = 0; k <= kEmDeg; ++k) C[k] = acc[k];
+  if (k <= kEmDeg) C[k] = acc;
 }
 
 // (sqrt(pi)/2) (erf(x) - erf(y)) for x >= y, without cancellation when both are far out on one
@@ -465,16 +455,17 @@ __device__ double image_sum_poisson(double pref, double lo, double hi, double c0
   return pref * acc;  // pref = sqrt(pi) / (t b)
 }
 
-// Row constants per (system, direction l, sinc node q), one thread each (they depend on t_q, h_l
-// and b_l only, not on the nucleus): PC[0] = J, PC[1 + i] = b_i (i <= J), PC[18 + k] = the
+// Row constants per (system, direction l, sinc node q), a warp each (they depend on t_q, h_l and
+// b_l only, not on the nucleus): PC[0] = J, PC[1 + i] = b_i (i <= J), PC[18 + k] = the
 // Euler-Maclaurin coefficients (k <= kEmDeg), PC[38 + n] = the Poisson weights (n <= NP).
 static_assert(1 + (kTaylorMaxJ + 1) + (kEmDeg + 1) + (kPoissonMaxN + 1) <= kPotConst, "row constants");
 constexpr int kPcBc = 1, kPcEm = kPcBc + kTaylorMaxJ + 1, kPcPw = kPcEm + kEmDeg + 1;
 
 __global__ void __launch_bounds__(64) k_pot_rows(const SysDev *__restrict__ sysv) {
+  // a warp per row (lane i: series coefficient i, Euler-Maclaurin coefficient i, Poisson weight i)
   const SysDev &s = sysv[blockIdx.y];
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 3 * s.R) return;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (idx >= 3 * s.R) return;  // warp-uniform
   const int l = idx / s.R, q = idx - l * s.R;
   const DirDev &D = s.d[l];
   double *pc = s.ws + s.offPC + (int64_t)idx * kPotConst;
@@ -484,17 +475,18 @@ __global__ void __launch_bounds__(64) k_pot_rows(const SysDev *__restrict__ sysv
   const bool em_row = D.periodic && taylor && sb <= kEmMaxS && J <= kEmJ;
   const bool poisson_row = D.periodic && sb < kPoissonMaxS;
   const int NP = poisson_row ? min((int)ceil(2.16 * sb) + 1, kPoissonMaxN) : 0;
-  pc[0] = (double)J;
-  double bc[kTaylorMaxJ + 1];
-  for (int i = 0; i <= kTaylorMaxJ; ++i) bc[i] = (taylor && i <= J) ? taylor_coef(i, J, 0.5 * delta) : 0.0;
-  for (int i = 0; i <= kTaylorMaxJ; ++i) pc[kPcBc + i] = bc[i];
+  __shared__ double bcs[2][kTaylorMaxJ + 1];
+  double *bc = bcs[threadIdx.x >> 5];
+  if (lane <= kTaylorMaxJ) bc[lane] = (taylor && lane <= J) ? taylor_coef(lane, J, 0.5 * delta) : 0.0;
+  __syncwarp();
+  if (lane == 0) pc[0] = (double)J;
+  if (lane <= kTaylorMaxJ) pc[kPcBc + lane] = bc[lane];
   if (em_row) {
-    em_poly_thread(bc, J, sb, pc + kPcEm);
-  } else {
-    for (int k = 0; k <= kEmDeg; ++k) pc[kPcEm + k] = 0.0;
+    em_poly_warp(bc, J, sb, pc + kPcEm);
+  } else if (lane <= kEmDeg) {
+    pc[kPcEm + lane] = 0.0;
   }
-  pc[kPcPw] = 0.0;
-  for (int n = 1; n <= kPoissonMaxN; ++n) pc[kPcPw + n] = n <= NP ? poisson_weight(n, sb, D.h, D.b) : 0.0;
+  if (lane <= kPoissonMaxN) pc[kPcPw + lane] = (lane >= 1 && lane <= NP) ? poisson_weight(lane, sb, D.h, D.b) : 0.0;
 }
 
 // One CTA per (system, direction, rank term r = (nucleus nu, sinc node q)): the row constants
@@ -630,9 +622,9 @@ cudaError_t launch_basis(const SysDev *sys, int nsys, int max_rows, cudaStream_t
 
 cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStream_t st) {
   if (max_rows <= 0 || nsys <= 0) return cudaSuccess;
-  // the row constants (3 R rows per system, a thread each), then the rows
+  // the row constants (3 R rows per system, a warp each), then the rows
   kmark(LHF_K_POTENTIAL, 1, st);
-  k_pot_rows<<<dim3((3 * kMaxR + 63) / 64, nsys), 64, 0, st>>>(sys);
+  k_pot_rows<<<dim3((3 * kMaxR + 1) / 2, nsys), 64, 0, st>>>(sys);
   kmark(LHF_K_POTENTIAL, 0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
