@@ -177,13 +177,18 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
 # time; any other hash reports null.
 TRAFFIC = {
     # ncu --set full of the tube_256 workload at 16 systems (profiles/tube_256_kernels_batch16.md):
-    # the autotuned k_eig launch and the first launch of the others; bytes read + written / 16.
-    # Only kernels whose traffic grows with the systems of a batch are listed (the 16-system
-    # capture keeps part of the rank sum's and the DFT's outputs in L2, a 64-system step does not)
-    "k_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": (17.019136e6 + 0.037888e6) / 16},
-    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "427f05f4f0e8b7ad", "bytes_per_system": 0.620288e6 / 16},
-    "k_potential": {"src": "k_setup.cu", "sha": "05fe0693b241f088", "bytes_per_system": (0.196352e6 + 0.000512e6) / 16},
-    "k_basis": {"src": "k_setup.cu", "sha": "05fe0693b241f088", "bytes_per_system": 0.103168e6 / 16},
+    # the autotuned k_eig / k_tridiag_eig launches and the first launch of the others; bytes read +
+    # written / 16 (k_potential: its two launches, row constants and rows).  Only kernels whose
+    # traffic grows with the systems of a batch are listed (the 16-system capture keeps part of
+    # the rank sum's and the DFT's outputs in L2, a 64-system step does not; the digit slicing
+    # runs once per direction and only direction 0 was captured)
+    "k_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": (17.019136e6 + 0.034048e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": 0.621312e6 / 16},
+    "k_potential": {"src": "k_setup.cu", "sha": "893c2099f4a96658",
+                    "bytes_per_system": (0.060672e6 + 0.742912e6 + 0.002304e6) / 16},
+    "k_basis": {"src": "k_setup.cu", "sha": "893c2099f4a96658", "bytes_per_system": (0.228096e6 + 0.046080e6) / 16},
+    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "70b7c2ac7ec28b1d",
+                  "bytes_per_system": (180.756736e6 + 27.759104e6) / 16},
 }
 
 
