@@ -258,7 +258,7 @@ def cpu_baseline(seed: int, procs: int = 1):
         t0 = time.perf_counter()
         dt, eig, st, mats = _oracle_one(seed, keep=True)
         return {"wall": time.perf_counter() - t0, "systems": 1, "cores": 1, "eig": [eig], "status": [st],
-                "mats": mats}
+                "mats": mats, "per_system_s": [dt]}
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
         pool.map(int, range(procs))  # workers started before the clock
@@ -266,7 +266,7 @@ def cpu_baseline(seed: int, procs: int = 1):
         res = pool.map(_oracle_task, [(seed + i, i == 0) for i in range(procs)])
         wall = time.perf_counter() - t0
     return {"wall": wall, "systems": procs, "cores": procs, "eig": [r[1] for r in res],
-            "status": [r[2] for r in res], "mats": res[0][3]}
+            "status": [r[2] for r in res], "mats": res[0][3], "per_system_s": [r[0] for r in res]}
 
 
 def host_cores() -> int:
@@ -655,10 +655,13 @@ def run_gpu(args):
             "removed_functions": int(cb["status"][0].clip(min=0).sum()),
             "median_abs_ha": float(np.median(np.abs(got[fin] - ref[fin]))),
             "k_status_match": bool(np.array_equal(kst[:ref.shape[0]].cpu().numpy(), cb["status"][0]))}
+        per_sys = float(np.mean(cb["per_system_s"]))
         line["cpu_baseline"] = {"value": cb["systems"] / cb["wall"], "unit": UNIT, "cores": cb["cores"],
                                 "kind": "oracle", "wall_s": cb["wall"],
                                 "sample": f"{cb['systems']} tube_256 systems (seeds 3000..{2999 + cb['systems']}), "
-                                          "one per single-threaded process, all at once"}
+                                          "one per single-threaded process, all at once",
+                                # one core: the mean time of one system inside its own process
+                                "single_thread": {"value": 1.0 / per_sys, "unit": UNIT, "s_per_system": per_sys}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
