@@ -95,6 +95,42 @@ def test_basis_and_potential_factors(ctx, oracle_mod, name):
         assert rel.max() <= 1e-13, (l, rel.max())
 
 
+def seam_and_tail_system():
+    """A (4,1,1) lattice whose functions' support windows fall just short of the period (runs of
+    basis samples straddle the window's seam), and open directions 16 bohr wide with a narrow
+    function (runs far in its tails, where exp(-alpha d^2) could underflow), s and p kinds."""
+    R, u0, du = W.SINC_TABLE["small"]
+    centre = [1.0, 0.1, -0.2]
+    return W.make_system(L=[4, 1, 1], b=[2.0, 16.0, 16.0], periodic=[1, 0, 0], n_cell=[16, 64, 64],
+                         h=[0.125, 0.25, 0.25], x0=[0.0, -8.0, -8.0], cell0=[0.0, -8.0, -8.0], Z=[1.0],
+                         a=[centre], kind=[0, 0, 1, 0, 2, 3], alpha=[2.75, 2.9, 3.05, 3.2, 3.35, 30.0],
+                         centre=[centre] * 6, R=R, u0=u0, du=du, name="seam_and_tail")
+
+
+def test_basis_runs_at_the_window_seam_and_in_the_tails(ctx, oracle_mod):
+    # basis samples are formed in runs along a row; runs that straddle the periodic window's seam
+    # or reach where exp(-alpha d^2) could underflow take the direct evaluation: every sample and
+    # the P1 forms built from the differences across run boundaries agree with the oracle
+    cfg = seam_and_tail_system()
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0, Rt = sz["m0"], sz["rank"]
+    for l in range(3):
+        G = dev((m0, cfg["n"][l]))
+        ctx.basis_factors(l, G)
+        ref = oracle_mod.basis_samples(cfg, l, 0)
+        assert np.abs(G.cpu().numpy() - ref).max() <= 1e-14 * max(1.0, np.abs(ref).max()), l
+        J = sz["window"][l]
+        C = dev((J, Rt + 2, m0, m0))
+        jlo = ctx.gram_factors(l, C)
+        C = C.cpu().numpy()
+        V = oracle_mod.potential_factors(cfg, l)
+        for jw in range(J):
+            _, K, M = oracle_mod.gram_1d(cfg, l, (jlo + jw) % cfg["L"][l], 0, V)
+            assert np.abs(C[jw, Rt] - K).max() <= 1e-12 * max(np.abs(K).max(), 1e-300), (l, jw)
+            assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300), (l, jw)
+
+
 @pytest.mark.parametrize("name", ["periodic_8", "tube_16_m16", "tube_24_windowed", "cubic_3"])
 def test_gram_factors(ctx, oracle_mod, name):
     cfg = CASES[name]()
