@@ -131,6 +131,32 @@ def test_basis_runs_at_the_window_seam_and_in_the_tails(ctx, oracle_mod):
             assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300), (l, jw)
 
 
+def test_p1_row_sums_of_long_rows(ctx, oracle_mod, lhf):
+    # rows of 1200 nodes (open directions): the exact fixed-point row sums of the folded products
+    # take a wider rounding shift (nv >= 1024) so that the integer sum cannot overflow; the P1
+    # forms still agree with the oracle to 1e-12 (FP64 route; the tensor-core route caps rows at
+    # 448 nodes)
+    R, u0, du = W.SINC_TABLE["small"]
+    centre = [1.0, 0.3, -0.4]
+    cfg = W.make_system(L=[4, 1, 1], b=[2.0, 16.0, 16.0], periodic=[1, 0, 0], n_cell=[16, 1200, 1200],
+                        h=[0.125, 16.0 / 1200, 16.0 / 1200], x0=[0.0, -8.0, -8.0], cell0=[0.0, -8.0, -8.0],
+                        Z=[1.0], a=[centre], kind=[0, 0, 2, 3], alpha=[0.3, 1.5, 0.8, 4.0], centre=[centre] * 4,
+                        R=R, u0=u0, du=du, name="long_rows")
+    ctx.setup(cfg)
+    sz = ctx.query_sizes()
+    m0, Rt = sz["m0"], sz["rank"]
+    for l in (1, 2):
+        C = dev((sz["window"][l], Rt + 2, m0, m0))
+        ctx.gram_factors(l, C, lhf.FP64)
+        C = C.cpu().numpy()
+        V = oracle_mod.potential_factors(cfg, l)
+        Cr, K, M = oracle_mod.gram_1d(cfg, l, 0, 0, V)
+        assert np.abs(C[0, Rt] - K).max() <= 1e-12 * np.abs(K).max(), l
+        assert np.abs(C[0, Rt + 1] - M).max() <= 1e-12 * np.abs(M).max(), l
+        for r in range(Rt):
+            assert np.abs(C[0, r] - Cr[r]).max() <= 1e-12 * np.abs(Cr[r]).max() + 1e-40 * np.abs(Cr).max()
+
+
 @pytest.mark.parametrize("name", ["periodic_8", "tube_16_m16", "tube_24_windowed", "cubic_3"])
 def test_gram_factors(ctx, oracle_mod, name):
     cfg = CASES[name]()
