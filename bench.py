@@ -184,9 +184,9 @@ TRAFFIC = {
     # runs once per direction and only direction 0 was captured)
     "k_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": (17.019136e6 + 0.034048e6) / 16},
     "k_tridiag_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": 0.621312e6 / 16},
-    "k_potential": {"src": "k_setup.cu", "sha": "893c2099f4a96658",
+    "k_potential": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83",
                     "bytes_per_system": (0.060672e6 + 0.742912e6 + 0.002304e6) / 16},
-    "k_basis": {"src": "k_setup.cu", "sha": "893c2099f4a96658", "bytes_per_system": (0.228096e6 + 0.046080e6) / 16},
+    "k_basis": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83", "bytes_per_system": (0.228096e6 + 0.046080e6) / 16},
     "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "70b7c2ac7ec28b1d",
                   "bytes_per_system": (180.756736e6 + 27.759104e6) / 16},
 }

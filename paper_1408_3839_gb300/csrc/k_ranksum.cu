@@ -11,8 +11,9 @@
 //
 // A thread takes one entry (mu, nu) of kRankGroup consecutive direction-0 window blocks with the
 // same (j1, j2): the weights w_r = c_r C1_r C2_r are formed once and each block costs one FMA
-// per rank term.  The blocks outside the window get one CTA each (block decoded once per CTA).  Factor blocks outside the contracted half of a window are read from their
-// mirrors, C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
+// per rank term.  The blocks outside the window get one CTA each (block decoded once per CTA).
+// Factor blocks outside the contracted half of a window are read from their mirrors,
+// C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
 // Consecutive threads take consecutive entries: the factor slots are read coalesced.
 #include "lhf_internal.cuh"
 

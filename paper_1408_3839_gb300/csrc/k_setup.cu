@@ -7,8 +7,9 @@
 //    images k of nucleus nu (periodic: window centred on cell 0, evaluated for the cell-0 nodes;
 //    open box: the L actual cells weighted by their charges; single open cell: k = 0).
 //
-// Layout: thread per output element, systems on blockIdx.y, elements flattened over
-// (direction, row, node) so that consecutive threads write consecutive nodes (coalesced).
+// Layout: systems on blockIdx.y; a1 one CTA per chunk of 512 samples of a row (a thread per run of
+// 8 consecutive samples), a2 the row constants once per (direction, sinc node) and then one CTA
+// per chunk of 512 cells of a row (see k_basis, k_pot_rows, k_potential).
 #include <math.h>
 
 #include "lhf_internal.cuh"
