@@ -9,24 +9,26 @@
 // written to block (j0 mod L0, j1 mod L1, j2 mod L2) of the first block column; blocks outside
 // the window are written as exact zeros by the same kernel (step a6).
 //
-// A thread takes one entry (mu, nu) of kRankGroup consecutive direction-0 window blocks with the
+// A thread takes one entry (mu, nu) of GROUP consecutive direction-0 window blocks with the
 // same (j1, j2): the weights w_r = c_r C1_r C2_r are formed once and each block costs one FMA
 // per rank term.  The blocks outside the window get one CTA each (block decoded once per CTA).
 // Factor blocks outside the contracted half of a window are read from their mirrors,
 // C_r[-j][mu][nu] = C_r[j][nu][mu] (the transposed entry of the mirrored block).
-// Consecutive threads take consecutive entries: the factor slots are read coalesced.
+// Consecutive threads take consecutive entries: the factor slots are read coalesced.  GROUP = 2
+// when every system's windows in directions 1 and 2 are single blocks (tubes: more threads for a
+// latency-bound loop), else 4 (fewer redundant weights where the (j1, j2) window is wide).
 #include "lhf_internal.cuh"
 
 namespace lhf {
 namespace {
 
-constexpr int kRankGroup = 2;
 
 __device__ __forceinline__ int wrap_block(int j, int L) {
   j %= L;
   return j < 0 ? j + L : j;
 }
 
+template <int GROUP>
 __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv, int compute_ctas) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
     }
     return;
   }
-  const int groups = (D0.J + kRankGroup - 1) / kRankGroup;
+  const int groups = (D0.J + GROUP - 1) / GROUP;
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= (int64_t)D1.J * D2.J * groups * mm) return;
   const int e = (int)(item % mm);
@@ -58,28 +60,28 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
   const int mu = e / m0, nu = e - mu * m0;
   const double *F1 = factor_entry(s, D1, jw1, mu, nu);
   const double *F2 = factor_entry(s, D2, jw2, mu, nu);
-  const double *F0[kRankGroup];
-  const int jw0_0 = g * kRankGroup;
-  const int nb = min(kRankGroup, D0.J - jw0_0);
+  const double *F0[GROUP];
+  const int jw0_0 = g * GROUP;
+  const int nb = min(GROUP, D0.J - jw0_0);
 #pragma unroll
-  for (int b = 0; b < kRankGroup; ++b) F0[b] = factor_entry(s, D0, jw0_0 + (b < nb ? b : 0), mu, nu);
-  double acc[kRankGroup];
+  for (int b = 0; b < GROUP; ++b) F0[b] = factor_entry(s, D0, jw0_0 + (b < nb ? b : 0), mu, nu);
+  double acc[GROUP];
 #pragma unroll
-  for (int b = 0; b < kRankGroup; ++b) acc[b] = 0.0;
+  for (int b = 0; b < GROUP; ++b) acc[b] = 0.0;
   // unrolled: the loads of four rank terms are in flight together
 #pragma unroll 4
   for (int r = 0; r < Rt; ++r) {
     const int64_t o = (int64_t)r * mm;
     const double w = s.c[r] * F1[o] * F2[o];
 #pragma unroll
-    for (int b = 0; b < kRankGroup; ++b) acc[b] = fma(w, F0[b][o], acc[b]);
+    for (int b = 0; b < GROUP; ++b) acc[b] = fma(w, F0[b][o], acc[b]);
   }
   const int64_t ok = (int64_t)Rt * mm, om = (int64_t)(Rt + 1) * mm;
   const double K1 = F1[ok], K2 = F2[ok], M1 = F1[om], M2 = F2[om];
   const double P = M1 * M2, Q = K1 * M2 + M1 * K2;
   const int64_t col = ((int64_t)wrap_block(D1.jlo + jw1, D1.L)) * D2.L + wrap_block(D2.jlo + jw2, D2.L);
 #pragma unroll
-  for (int b = 0; b < kRankGroup; ++b) {
+  for (int b = 0; b < GROUP; ++b) {
     if (b >= nb) break;
     const double K0 = F0[b][ok], M0 = F0[b][om];
     const int64_t blk = (int64_t)wrap_block(D0.jlo + jw0_0 + b, D0.L) * D1.L * D2.L + col;
@@ -90,17 +92,23 @@ __global__ void __launch_bounds__(256) k_ranksum(const SysDev *__restrict__ sysv
 
 }  // namespace
 
-int ranksum_compute_items(const SysDev &s) {
-  const int groups = (s.d[0].J + kRankGroup - 1) / kRankGroup;
+int ranksum_group(const SysDev &s) { return s.d[1].J * s.d[2].J == 1 ? 2 : 4; }
+
+int ranksum_compute_items(const SysDev &s, int group) {
+  const int groups = (s.d[0].J + group - 1) / group;
   return s.d[1].J * s.d[2].J * groups * s.m0 * s.m0;
 }
 
-cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, cudaStream_t st) {
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, int group,
+                           cudaStream_t st) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const int compute_ctas = (max_compute_items + 255) / 256;
   dim3 grid(compute_ctas + max_blocks, nsys);
   kmark(LHF_K_RANKSUM, 1, st);
-  k_ranksum<<<grid, 256, 0, st>>>(sys, compute_ctas);
+  if (group == 2)
+    k_ranksum<2><<<grid, 256, 0, st>>>(sys, compute_ctas);
+  else
+    k_ranksum<4><<<grid, 256, 0, st>>>(sys, compute_ctas);
   kmark(LHF_K_RANKSUM, 0, st);
   return cudaGetLastError();
 }

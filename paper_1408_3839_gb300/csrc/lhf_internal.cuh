@@ -209,8 +209,11 @@ cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsi
 // Rank sum over the window blocks (max_compute_items = ranksum_compute_items over the batch) and
 // zeros for the blocks outside it (max_blocks = nblocks over the batch).  Reads mirrored window
 // blocks from their contracted partners (no mirror pass needed).
-int ranksum_compute_items(const SysDev &s);
-cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, cudaStream_t st);
+// group: direction-0 window blocks per thread (2 or 4; ranksum_group, the largest over a batch).
+int ranksum_group(const SysDev &s);
+int ranksum_compute_items(const SysDev &s, int group);
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, int group,
+                           cudaStream_t st);
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st);  // *passes += kernel launches (may be null)
 // k-point eigensolves; tri: systems carry a tridiagonal scratch (SysDev::tri), and the
