@@ -423,21 +423,17 @@ __device__ void bloch_vectors(const SysDev &s, int kap, int mk, bool ok, bool ch
 __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict__ sysv) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box || !s.s0) return;
-  __shared__ double part[256];
+  // every diagonal entry at once: a group of P lanes (16, or 8 when m0 > 16) per entry i, each
+  // lane summing every P-th k-point, then a fixed shuffle tree within the group
   const int m = s.m0, K = s.nblocks, tid = threadIdx.x;
+  const int P = m <= 16 ? 16 : 8;
+  const int i = tid / P, sub = tid % P;
   const double2 *Sb = reinterpret_cast<const double2 *>(s.Sbar);
-  for (int i = 0; i < m; ++i) {
-    double acc = 0.0;
-    for (int k = tid; k < K; k += 256) acc += Sb[(int64_t)k * m * m + i * m + i].x;
-    part[tid] = acc;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (tid < w) part[tid] += part[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) s.s0[i] = part[0] / K;
-    __syncthreads();
-  }
+  double acc = 0.0;
+  if (i < m)
+    for (int k = sub; k < K; k += P) acc += Sb[(int64_t)k * m * m + i * m + i].x;
+  for (int o = P / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (i < m && sub == 0) s.s0[i] = acc / K;
 }
 
 template <int G>
