@@ -182,8 +182,8 @@ TRAFFIC = {
     # traffic grows with the systems of a batch are listed (the 16-system capture keeps part of
     # the rank sum's and the DFT's outputs in L2, a 64-system step does not; the digit slicing
     # runs once per direction and only direction 0 was captured)
-    "k_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": (17.019136e6 + 0.034048e6) / 16},
-    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "4e35221459d3b556", "bytes_per_system": 0.621312e6 / 16},
+    "k_eig": {"src": "k_eig.cu", "sha": "f46a43380a8f2edb", "bytes_per_system": (17.018880e6 + 0.044288e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "f46a43380a8f2edb", "bytes_per_system": 0.620288e6 / 16},
     "k_potential": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83",
                     "bytes_per_system": (0.060672e6 + 0.742912e6 + 0.002304e6) / 16},
     "k_basis": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83", "bytes_per_system": (0.228096e6 + 0.046080e6) / 16},
