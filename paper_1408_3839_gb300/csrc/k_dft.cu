@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   extern __shared__ double sm[];
   double2 *x = reinterpret_cast<double2 *>(sm);  // [Ld][TW]
   double2 *tab = x + (size_t)Ld * TW;            // [Ld] omega^m
-  __shared__ double red[2 * (kDftThreads / 32)];
   const int tid = threadIdx.x;
   for (int m = tid; m < Ld; m += kDftThreads) {
     double sn, cs;
@@ -111,36 +110,34 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   const int bits = pow2 ? __ffs(Ld) - 1 : 0;
   int sig_e = 0;  // sigma = 2^sig_e
   if (packed) {
-    double mh = 0.0, ms = 0.0;
+    // the exponents of max |H| and max |S| over the tile, from the largest high words without the
+    // sign (integer operations: they order like the magnitudes up to the low word, and carry the
+    // largest biased exponent; frexp's exponent is that exponent - 1022 for a normal maximum)
+    unsigned kh = 0u, ks = 0u;
     for (int k = tid; k < Ld * TW; k += kDftThreads) {
       const int j = k / TW, t = k - j * TW;
       if (t < tw_valid) {
         const int64_t idx = (o * Ld + j) * inner + off_sh[t];
-        mh = fmax(mh, fabs(s.H[idx]));
-        ms = fmax(ms, fabs(s.S[idx]));
+        kh = max(kh, (unsigned)__double2hiint(s.H[idx]) & 0x7fffffffu);
+        ks = max(ks, (unsigned)__double2hiint(s.S[idx]) & 0x7fffffffu);
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, off));
-      ms = fmax(ms, __shfl_xor_sync(0xffffffffu, ms, off));
-    }
+    kh = __reduce_max_sync(0xffffffffu, kh);
+    ks = __reduce_max_sync(0xffffffffu, ks);
+    __shared__ unsigned redk[2 * (kDftThreads / 32)];
     if ((tid & 31) == 0) {
-      red[2 * (tid >> 5)] = mh;
-      red[2 * (tid >> 5) + 1] = ms;
+      redk[2 * (tid >> 5)] = kh;
+      redk[2 * (tid >> 5) + 1] = ks;
     }
     __syncthreads();
-    mh = red[0];
-    ms = red[1];
+    kh = redk[0];
+    ks = redk[1];
     for (int w = 1; w < kDftThreads / 32; ++w) {
-      mh = fmax(mh, red[2 * w]);
-      ms = fmax(ms, red[2 * w + 1]);
+      kh = max(kh, redk[2 * w]);
+      ks = max(ks, redk[2 * w + 1]);
     }
-    if (mh > 0.0 && ms > 0.0) {
-      int eh = 0, es = 0;
-      frexp(mh, &eh);
-      frexp(ms, &es);
-      sig_e = eh - es;
-    }
+    const int bh = (int)(kh >> 20), bs = (int)(ks >> 20);  // biased exponents (0: zero or subnormal)
+    if (bh > 0 && bs > 0) sig_e = bh - bs;
   }
   const double sig = pow2_scale(sig_e);
   for (int k = tid; k < Ld * TW; k += kDftThreads) {
