@@ -176,7 +176,7 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
 # kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
 # time; any other hash reports null.
 TRAFFIC = {
-    # ncu --set full of the tube_256 workload at 16 systems (profiles/tube_256_kernels_batch16.md):
+    # ncu --set full of the tube_256 workload at 16 systems:
     # the autotuned k_eig / k_tridiag_eig launches and the first launch of the others; bytes read +
     # written / 16 (k_potential: its two launches, row constants and rows).  Only kernels whose
     # traffic grows with the systems of a batch are listed (the 16-system capture keeps part of
@@ -276,6 +276,17 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+WORKLOAD = "tube_256: periodic (256,1,1), b=2.8, M0=2, m0=16, n=32768x256x256, R=32, K_sum=256"
+
+
+def bench_config(batch: int, world: int) -> dict:
+    """The `config` object of both arms' JSON lines (the GPU arm's workload; the reference arm
+    times a bounded sample of it, stated in its cpu_baseline)."""
+    return {"workload": WORKLOAD, "systems_per_step_per_gpu": batch,
+            "l2": "working set per step >> L2 (no flush needed)",
+            "parallelism": f"replicas x{world} (independent systems per GPU)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -295,10 +306,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded tube_256 variants)",
-        "config": {"workload": "tube_256: periodic (256,1,1), m0=16, n=32768x256x256, R=32, K_sum=256",
-                   "systems_per_step": cores},
+        "config": bench_config(args.batch, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{cores} systems per step, one per spawned process"},
+                         "sample": f"{cores} of the workload's systems per step (seeds 3000 + step x {cores} ..), "
+                                   "one per spawned single-threaded process"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -617,9 +628,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "precision": args.precision, "data": "synthetic (seeded tube_256 variants)",
-        "config": {"workload": "tube_256: periodic (256,1,1), b=2.8, M0=2, m0=16, n=32768x256x256, R=32, K_sum=256",
-                   "systems_per_step_per_gpu": B, "l2": "working set per step >> L2 (no flush needed)",
-                   "parallelism": f"replicas x{world} (independent systems per GPU)"},
+        "config": bench_config(B, world),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": B * sizes[0]["desc_bytes"], "d2h_bytes_per_step": B * per_sys * 8 + hk.nbytes},
         "gpu_launches": gpu_launches,

@@ -336,21 +336,22 @@ const char *lhf_kernel_name(int kernel);
 lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned long long *matrices);
 
 /* Allocation-free variant of lhf_k_point_eigensolve (the paper has no counterpart: this is an
- * interface for callers that cannot allocate device memory -- code inside CUDA stream capture,
- * services held to a fixed device-memory budget, hosts whose allocator policy forbids raw CUDA
- * allocations).  It needs no context and calls no cudaMalloc/cudaFree or allocating library
- * routine: its scratch (the kernel's descriptor, a status word and the overlap norms s0) lives
+ * interface for callers that cannot allocate device memory -- services held to a fixed
+ * device-memory budget set at start-up, and hosts whose allocator policy forbids raw CUDA
+ * allocations because another framework owns the device memory).  It needs no context and
+ * calls no cudaMalloc/cudaFree or allocating library routine: its scratch (the kernel's descriptor, a status word and the overlap norms s0) lives
  * in one file-scope device array of LHF_NOALLOC_SCRATCH_BYTES that every GPU loading the
  * library holds until the process exits.
  *   L[3]   host: lattice sizes (each 1..4096); m0: functions per cell, 1..LHF_MAX_M0 (larger m0
  *          returns LHF_ERR_ARG: s0 would not fit the scratch);
  *   Hbar, Sbar, eig, k_status: as for lhf_k_point_eigensolve (caller-owned device memory;
  *          k_status may be NULL); stream: cudaStream_t (NULL = default stream).
- * Asynchronous on the stream.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  All calls share the one array, which keeps the last call's contents: calls whose
- * work may overlap on the GPU (different streams without ordering) race and must be
- * serialised by the caller.  Returns LHF_OK, LHF_ERR_ARG or LHF_ERR_CUDA. */
+ * Asynchronous on the stream; the descriptor is written into the array by a kernel on the same
+ * stream, so no host buffer of the call has to outlive it.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture is active on the calling thread.  All calls share the one
+ * array, which keeps the last call's contents: calls whose work may overlap on the GPU
+ * (different streams without ordering) race and must be serialised by the caller.  Returns LHF_OK, LHF_ERR_ARG or LHF_ERR_CUDA. */
 #define LHF_NOALLOC_SCRATCH_BYTES 16384
 lhf_status lhf_k_point_eigensolve_noalloc(const int *L, int m0, const double *Hbar, const double *Sbar,
                                           double *eig, int *k_status, void *stream);

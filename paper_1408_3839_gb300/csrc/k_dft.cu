@@ -136,8 +136,10 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
       kh = max(kh, redk[2 * w]);
       ks = max(ks, redk[2 * w + 1]);
     }
-    const int bh = (int)(kh >> 20), bs = (int)(ks >> 20);  // biased exponents (0: zero or subnormal)
-    if (bh > 0 && bs > 0) sig_e = bh - bs;
+    // biased exponents (0: zero or subnormal; 2047: an inf or NaN entry, which must not set the
+    // scale of the whole tile -- without balancing, only the transforms it enters go non-finite)
+    const int bh = (int)(kh >> 20), bs = (int)(ks >> 20);
+    if (bh > 0 && bs > 0 && bh < 2047 && bs < 2047) sig_e = bh - bs;
   }
   const double sig = pow2_scale(sig_e);
   for (int k = tid; k < Ld * TW; k += kDftThreads) {

@@ -1,14 +1,15 @@
 // lhf_noalloc.cu -- k-point eigensolve for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside CUDA stream capture (allocation is
-// not allowed there), services that must stay within a fixed device-memory budget set at
-// start-up, and hosts whose allocator policy forbids raw CUDA allocations (another framework
-// owns the memory).  For them lhf_k_point_eigensolve_noalloc runs the same kernels as
+// Some callers cannot call cudaMalloc: services that must stay within a fixed device-memory
+// budget set at start-up (an allocation later could fail or evict another tenant's memory), and
+// hosts whose allocator policy forbids raw CUDA allocations because another framework owns the
+// device memory.  For them lhf_k_point_eigensolve_noalloc runs the same kernels as
 // lhf_k_point_eigensolve without a context: the descriptor and the kernels' scratch (the
 // overlap norms s0 and a status word) live in one file-scope device array, sized once for all,
-// that every GPU loading this library holds until the process exits.
+// that every GPU loading this library holds until the process exits.  The descriptor is written
+// into that array by a one-thread-block kernel that receives its fields as kernel arguments, so
+// no host buffer has to outlive the call.
 #include <mutex>
-#include <string.h>
 
 #include "lhf_internal.cuh"
 
@@ -40,6 +41,37 @@ cudaError_t scratch_address(int device, unsigned char **out) {
   return cudaSuccess;
 }
 
+// The fields of the descriptor that the overlap-norm and k-point kernels read for one system.
+struct NoallocArgs {
+  int L[3];
+  int m0;
+  int nblocks;
+  const double *Hbar, *Sbar;
+  double *eig;
+  int *kstat;
+};
+
+// Writes the descriptor [0, kDescBytes) and the status word of the scratch at base: every byte of
+// the descriptor zero except the fields above, s0 pointing into the scratch.
+__global__ void k_noalloc_setup(NoallocArgs a, unsigned char *base) {
+  unsigned *words = reinterpret_cast<unsigned *>(base);
+  for (size_t i = threadIdx.x; i < kDescBytes / sizeof(unsigned); i += blockDim.x) words[i] = 0u;
+  if (threadIdx.x == 0) *reinterpret_cast<unsigned *>(base + kDescBytes) = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    lhf::SysDev *sd = reinterpret_cast<lhf::SysDev *>(base);
+    for (int l = 0; l < 3; ++l) sd->d[l].L = a.L[l];
+    sd->m0 = a.m0;
+    sd->nblocks = a.nblocks;
+    sd->box = 0;
+    sd->Hbar = const_cast<double *>(a.Hbar);
+    sd->Sbar = const_cast<double *>(a.Sbar);
+    sd->eig = a.eig;
+    sd->kstat = a.kstat;
+    sd->s0 = reinterpret_cast<double *>(base + kDescBytes + 256);
+  }
+}
+
 }  // namespace
 
 extern "C" lhf_status lhf_k_point_eigensolve_noalloc(const int *L, int m0, const double *Hbar,
@@ -64,22 +96,18 @@ extern "C" lhf_status lhf_k_point_eigensolve_noalloc(const int *L, int m0, const
     return LHF_ERR_CUDA;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  lhf::SysDev sd;
-  memset(&sd, 0, sizeof sd);
-  for (int l = 0; l < 3; ++l) sd.d[l].L = L[l];
-  sd.m0 = m0;
-  sd.nblocks = (int)nblocks;
-  sd.box = 0;
-  sd.Hbar = const_cast<double *>(Hbar);
-  sd.Sbar = const_cast<double *>(Sbar);
-  sd.eig = eig;
-  sd.kstat = k_status;
+  NoallocArgs a;
+  for (int l = 0; l < 3; ++l) a.L[l] = L[l];
+  a.m0 = m0;
+  a.nblocks = (int)nblocks;
+  a.Hbar = Hbar;
+  a.Sbar = Sbar;
+  a.eig = eig;
+  a.kstat = k_status;
   unsigned *flags = reinterpret_cast<unsigned *>(base + kDescBytes);
-  sd.s0 = reinterpret_cast<double *>(base + kDescBytes + 256);
   lhf::SysDev *dsys = reinterpret_cast<lhf::SysDev *>(base);
-  // sd is pageable host memory: the copy has been staged when cudaMemcpyAsync returns
-  if (cudaMemcpyAsync(dsys, &sd, sizeof sd, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess ||
+  k_noalloc_setup<<<1, 256, 0, st>>>(a, base);
+  if (cudaGetLastError() != cudaSuccess ||
       lhf::launch_overlap_norms(dsys, 1, st) != cudaSuccess ||
       lhf::launch_eig(dsys, 1, (int)nblocks, m0, flags, nullptr, st, false) != cudaSuccess) {
     cudaGetLastError();

@@ -468,10 +468,16 @@ class Graph:
 
 def k_point_eigensolve_noalloc(L, m0: int, Hbar, Sbar, eig, k_status=None, stream=None):
     """lhf_k_point_eigensolve_noalloc: the k-point eigensolve without a context or any device
-    allocation (its scratch is a static device array inside the library)."""
+    allocation (its scratch is a static device array inside the library).  stream: a torch
+    stream or a raw cudaStream_t; None takes torch's current stream, the one on which the
+    caller's tensors were written."""
     lib = load()
     Larr = (ctypes.c_int * 3)(*[int(v) for v in L])
-    raw = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     st = lib.lhf_k_point_eigensolve_noalloc(Larr, int(m0), _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(k_status), raw)
     if st != LHF_OK:
         raise LhfError(st, "lhf_k_point_eigensolve_noalloc failed")
