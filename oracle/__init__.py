@@ -7,7 +7,8 @@ this package.  It shares no code with the CUDA library: the arithmetic lives in
 (``bloch_orbital``, ``p1_mass_matrix``), the separable k-space route (``kspace_blocks``) and the
 energy per cell of the lowest states (``cell_energy``), written here in numpy; the rest of this
 module only marshals arguments.  See ``lhf_oracle.c`` for the passages of the paper each function
-follows.
+follows.  ``oracle.extended`` compiles the same source with long double arithmetic and solves
+pencils in 50 digits: the exact values against which the FP64 rounding of this oracle is pinned.
 """
 
 from __future__ import annotations

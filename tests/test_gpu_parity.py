@@ -246,6 +246,44 @@ def test_bloch_spectrum_end_to_end(ctx, oracle_mod, name):
     assert ratio <= 1.0, (worst, ratio)
 
 
+def _exact_periodic_8():
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "periodic_8_exact_eigenvalues.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(v) for v in r[1:]] for r in rows])
+
+
+def test_periodic_8_against_the_exact_spectrum(ctx, oracle_mod, lhf):
+    """Both routes against the exact Bloch spectrum of periodic_8 (extended-precision assembly,
+    50-digit pencils; tests/golden).  Where every Bloch function keeps at least 1e-3 of its norm
+    the GPU meets the flat 1e-10 Ha target; at the zone boundary, where the diffuse s function's
+    Bloch sum cancels to 3.5e-5 of its norm, FP64 blocks determine the spectrum only to ~4e-10 Ha
+    (the oracle is 3.7e-10 Ha off there, as is the exact solve of its own blocks): the GPU stays
+    within the first-order perturbation bound of the exact values, like the oracle."""
+    exact = _exact_periodic_8()
+    cfg = W.periodic_8()
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, st = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    d = np.real(np.einsum("kii->ki", Sb.reshape(-1, 4, 4)))
+    well = (d / d.mean(axis=0)).min(axis=1) >= 1e-3
+    assert well.sum() == 7 and not well[4]
+    ctx.setup(cfg)
+    for prec, flat in ((lhf.FP64, 1e-10), (lhf.MIXED, 1e-9)):
+        eig = dev((8, 4))
+        ks = dev((8,), torch.int32)
+        ctx.bloch_spectra([cfg], eig, ks, prec)
+        ctx.sync()
+        got = eig.cpu().numpy()
+        assert np.all(ks.cpu().numpy() == 0)
+        err = np.abs(got - exact).max(axis=1)
+        assert err[well].max() <= flat, (prec, err)
+        worst, ratio = check_eigenvalues(got, exact, Hb, Sb, Hr, Sr, status=st)
+        assert ratio <= 1.0 and worst < 1e-9, (prec, worst, ratio)
+    assert np.abs(ref - exact).max(axis=1)[well].max() <= 1e-10
+
+
 # ---------------------------------------------------------------------------------------------
 # batching, determinism, edge cases and errors
 

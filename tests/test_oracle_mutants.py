@@ -24,6 +24,9 @@ MUTANTS = {
     "embedding_transpose": ("Xe[(size_t)i * n + j + m] = -xi;", "Xe[(size_t)i * n + j + m] = xi;"),
     "lindep_scale": ("X[(size_t)i * nk + a] = V[(size_t)i * n + kept[a]] / sqrt(", "X[(size_t)i * nk + a] = V[(size_t)i * n + kept[a]] * sqrt("),
     "drop_rule": ("if (Sk[2 * ((size_t)i * m + i)] > tau * s0[i]) keep[mr++] = i;", "keep[mr++] = i;"),
+    "drop_threshold_x100": ("> tau * s0[i]) keep[mr++] = i;", "> 100.0 * tau * s0[i]) keep[mr++] = i;"),
+    "drop_threshold_div100": ("> tau * s0[i]) keep[mr++] = i;", "> 0.01 * tau * s0[i]) keep[mr++] = i;"),
+    "s0_from_kappa_0_only": ("s0[i] += Sbar[k * mm2 + 2 * ((size_t)i * m + i)];", "s0[i] += Sbar[2 * ((size_t)i * m + i)];"),
     "first_weight_tail": ("w[0] = w[0] / (1.0 - exp(-du));", "w[0] = w[0];"),
     "cell_shift": ("double A = s->centre[3 * mu + l] + cell * s->b[l];", "double A = s->centre[3 * mu + l] - cell * s->b[l];"),
 }
