@@ -335,6 +335,23 @@ const char *lhf_kernel_name(int kernel);
  * of k-points).  Reset by the call. */
 lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned long long *matrices);
 
+/* Failure detection (no counterpart in the paper: controls of this library's own error paths).
+ * lhf_set_wait_limit: the bound, in SM clock cycles, of every wait at a grid barrier of the dense
+ *   eigensolver (lhf_dense_eigensolve and the open-box path); cycles <= 0 restores the default
+ *   2e9 (about a second).  A wait that runs out sets the context's device error word and makes
+ *   every CTA of that launch return; the next lhf_sync returns LHF_ERR_TIMEOUT, and the context
+ *   stays usable (the outputs of that solve are undefined).
+ * lhf_inject_barrier_stall: the next dense eigensolve of this context runs with grid barriers
+ *   that expect one CTA more than the launch holds, so that their waits run out as above (a test
+ *   of the time-out path that faults nothing; consumed by that solve).
+ * lhf_set_workspace_limit: the most bytes of device workspace the context (and each graph created
+ *   from it) may allocate; a call needing more returns LHF_ERR_NOMEM before any kernel launch.
+ *   0 = no limit (default).  Small fixed buffers (descriptors, status words) are not counted.
+ * Each returns LHF_OK, or LHF_ERR_ARG for a null context. */
+lhf_status lhf_set_wait_limit(lhf_ctx *ctx, long long cycles);
+lhf_status lhf_inject_barrier_stall(lhf_ctx *ctx);
+lhf_status lhf_set_workspace_limit(lhf_ctx *ctx, size_t bytes);
+
 /* Allocation-free variant of lhf_k_point_eigensolve (the paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory -- services held to a fixed
  * device-memory budget set at start-up, and hosts whose allocator policy forbids raw CUDA

@@ -20,8 +20,10 @@
 //      8 lanes evaluate 8 equally spaced sigmas per round, 18 rounds shrink the Gershgorin
 //      interval by 9^18.  Eigenvalues come out ascending by construction.
 // The grid barrier is a counter and a generation word in global memory with a bounded wait: a
-// CTA that waits longer than about a second raises kFlagTimeout and an abort word that makes
-// every CTA return.
+// CTA that waits longer than wait_cycles SM clock cycles (default 2e9, about a second) raises
+// kFlagTimeout and an abort word that makes every CTA return.  The barrier completes when
+// `arrivals` CTAs have arrived: gridDim.x, or one more for the failure-detection test, whose
+// waits then run out.
 #include <math.h>
 
 #include "lhf_internal.cuh"
@@ -41,7 +43,7 @@ struct GridBar {
 };
 
 // Bounded grid-wide barrier; returns false if it (or another CTA's barrier) gave up.
-__device__ bool grid_barrier(GridBar *bar, unsigned nblocks, unsigned *flags, int *ok_sh) {
+__device__ bool grid_barrier(GridBar *bar, unsigned nblocks, unsigned *flags, int *ok_sh, long long wait_cycles) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -58,7 +60,7 @@ __device__ bool grid_barrier(GridBar *bar, unsigned nblocks, unsigned *flags, in
       const volatile unsigned *gen = &bar->gen;
       const volatile unsigned *abort_word = &bar->abort;
       while (*gen == g) {
-        if ((++spins & 255u) == 0 && (clock64() - t0 > 2000000000ll || *abort_word)) {
+        if ((++spins & 255u) == 0 && (clock64() - t0 > wait_cycles || *abort_word)) {
           atomicOr(flags, kFlagTimeout);
           atomicExch(&bar->abort, 1u);
           ok = 0;
@@ -141,7 +143,8 @@ __device__ int sturm_count(const double *td, const double *te2, int N, double si
 __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__restrict__ H,
                                                             const double *__restrict__ S, int N,
                                                             double *eig, double *work, GridBar *bar,
-                                                            unsigned *flags) {
+                                                            unsigned *flags, long long wait_cycles,
+                                                            unsigned arrivals) {
   extern __shared__ double sm[];
   double *vec = sm;      // [N] scales, column of L, Householder vector
   double *wv = sm + N;   // [N] w
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
       Lm[(int64_t)i * N + j] = S[(int64_t)i * N + j] * sc;
       C[(int64_t)i * N + j] = H[(int64_t)i * N + j] * sc;
     }
-  if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+  if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
   bad = __ldcg(&bar->bad) != 0u;
 
   // 1. Cholesky (lower triangle of Lm)
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
       const double li = vec[i];
       for (int k = j + 1 + tid; k <= i; k += kDenseThreads) row[k] -= li * vec[k];
     }
-    if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+    if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
   }
   if (bad) {
     if (blockIdx.x == 0 && tid == 0) atomicOr(flags, kFlagNotSpd);
@@ -206,17 +209,17 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
 
   // 2. Y = H~ L^{-T} on the own rows of C
   rows_times_inv_lt(C, Lm, ld, N, G);
-  if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+  if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
   // 3. own rows of Y^T, times L^{-T}, then C = (X + X^T) / 2 on the own rows
   for (int i = blockIdx.x; i < N; i += G)
     for (int j = tid; j < N; j += kDenseThreads) Yt[(int64_t)i * N + j] = __ldcg(C + (int64_t)j * N + i);
   __syncthreads();
   rows_times_inv_lt(Yt, Lm, ld, N, G);
-  if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+  if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
   for (int i = blockIdx.x; i < N; i += G)
     for (int j = tid; j < N; j += kDenseThreads)
       C[(int64_t)i * N + j] = 0.5 * (Yt[(int64_t)i * N + j] + __ldcg(Yt + (int64_t)j * N + i));
-  if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+  if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
 
   // 4. Householder tridiagonalisation of C
   for (int k = 0; k + 2 < N; ++k) {
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
         if (lane == 0) pv[i] = tau * acc;
       }
     }
-    if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+    if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
     if (tau != 0.0) {
       double pd = 0.0;
       for (int i = k + 1 + tid; i < N; i += kDenseThreads) {
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
         for (int j = k + 1 + tid; j < N; j += kDenseThreads) row[j] -= vi * wv[j] + wi * vec[j];
       }
     }
-    if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+    if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
   }
   if (blockIdx.x == 0 && tid == 0) {
     if (N >= 2) {
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
     td[N - 1] = __ldcg(C + (int64_t)(N - 1) * N + N - 1);
     for (int i = 0; i + 1 < N; ++i) te2[i] = te[i] * te[i];
   }
-  if (!grid_barrier(bar, G, flags, &ok_sh)) return;
+  if (!grid_barrier(bar, arrivals, flags, &ok_sh, wait_cycles)) return;
 
   // 5. multisection on the Sturm count; every CTA forms the Gershgorin interval itself
   double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0;
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_eig(const double *__res
 size_t dense_eig_workspace_doubles(int N) { return (size_t)3 * N * N + 5 * (size_t)N + 64; }
 
 cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *eig, double *work,
-                             unsigned *flags, cudaStream_t st) {
+                             unsigned *flags, cudaStream_t st, long long wait_cycles, int stall) {
   if (N <= 0) return cudaSuccess;
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -360,7 +363,10 @@ cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *ei
   const int G = sms < N ? sms : N;  // one CTA per SM, all resident
   GridBar *bar = reinterpret_cast<GridBar *>(work + 3 * (size_t)N * N + 5 * (size_t)N);
   if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st)) != cudaSuccess) return e;
-  void *args[] = {(void *)&H, (void *)&S, (void *)&N, (void *)&eig, (void *)&work, (void *)&bar, (void *)&flags};
+  if (wait_cycles <= 0) wait_cycles = kDefaultWaitCycles;
+  unsigned arrivals = (unsigned)G + (stall ? 1u : 0u);
+  void *args[] = {(void *)&H,    (void *)&S,     (void *)&N,           (void *)&eig,     (void *)&work,
+                  (void *)&bar,  (void *)&flags, (void *)&wait_cycles, (void *)&arrivals};
   kmark(LHF_K_DENSE_EIG, 1, st);
   e = cudaLaunchCooperativeKernel((const void *)k_dense_eig, dim3(G), dim3(kDenseThreads), args, smem, st);
   kmark(LHF_K_DENSE_EIG, 0, st);

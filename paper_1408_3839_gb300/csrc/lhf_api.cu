@@ -95,6 +95,11 @@ struct lhf_ctx {
   int graph_tc_jobs = 0;
   size_t graph_tc_off = 0;
   std::vector<int> host_L;
+  // failure detection: bound of the dense solver's grid-barrier waits, a one-shot injected
+  // barrier stall (test), and a cap on the workspace bytes (0: none)
+  long long wait_cycles = lhf::kDefaultWaitCycles;
+  bool stall_next = false;
+  size_t ws_limit = 0;
   // solved k-points (one per conjugate pair) per lattice shape, on the device
   std::map<std::array<int, 3>, std::pair<int *, int>> klists;
   // launch-shape autotuner of the k-point eigensolver: per (m0, tridiagonal route, log2 of the
@@ -519,12 +524,16 @@ lhf_status current_plan(lhf_ctx *c, Plan &P, bool mixed = false) {
 
 lhf_status ensure_ws(lhf_ctx *c, size_t doubles) {
   if (doubles <= c->ws_cap) return LHF_OK;
+  if (c->ws_limit && doubles * sizeof(double) > c->ws_limit)
+    return c->fail(LHF_ERR_NOMEM, "workspace of %zu bytes exceeds the context's limit of %zu bytes",
+                   doubles * sizeof(double), c->ws_limit);
   lhf_status st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (st != LHF_OK) return st;
   if (c->ws) cudaFree(c->ws);
   c->ws = nullptr;
   c->ws_cap = 0;
   size_t want = std::max(doubles, c->ws_cap + c->ws_cap / 4);
+  if (c->ws_limit) want = std::min(want, std::max(doubles, c->ws_limit / sizeof(double)));
   cudaError_t e = cudaMalloc(&c->ws, want * sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -753,7 +762,9 @@ lhf_status run_box_assemble(lhf_ctx *c, const std::vector<Plan> &ps) {
 // Dense generalized eigensolve of one pencil with the context's flags word.
 lhf_status run_dense_eig(lhf_ctx *c, const double *H, const double *S, int N, double *eig, double *work) {
   c->begin(5);
-  cudaError_t e = lhf::launch_dense_eig(H, S, N, eig, work, c->d_flags, c->stream);
+  const int stall = c->stall_next ? 1 : 0;
+  c->stall_next = false;
+  cudaError_t e = lhf::launch_dense_eig(H, S, N, eig, work, c->d_flags, c->stream, c->wait_cycles, stall);
   c->end();
   if (e == cudaErrorNotSupported) return c->fail(LHF_ERR_UNSUPPORTED, "cooperative launch not available");
   return c->cuda(e, "dense eigensolver");
@@ -1013,6 +1024,24 @@ lhf_status lhf_launch_shapes(lhf_ctx *c, int *eig_warps, int *tri_threads) {
   if (!c || !eig_warps || !tri_threads) return LHF_ERR_ARG;
   *eig_warps = c->last_eig_warps;
   *tri_threads = c->last_tri_threads;
+  return LHF_OK;
+}
+
+lhf_status lhf_set_wait_limit(lhf_ctx *c, long long cycles) {
+  if (!c) return LHF_ERR_ARG;
+  c->wait_cycles = cycles > 0 ? cycles : lhf::kDefaultWaitCycles;
+  return LHF_OK;
+}
+
+lhf_status lhf_inject_barrier_stall(lhf_ctx *c) {
+  if (!c) return LHF_ERR_ARG;
+  c->stall_next = true;
+  return LHF_OK;
+}
+
+lhf_status lhf_set_workspace_limit(lhf_ctx *c, size_t bytes) {
+  if (!c) return LHF_ERR_ARG;
+  c->ws_limit = bytes;
   return LHF_OK;
 }
 
@@ -1384,6 +1413,9 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
     lhf_graph_destroy(g);
     return s;
   };
+  if (c->ws_limit && total * sizeof(double) > c->ws_limit)
+    return cleanup(c->fail(LHF_ERR_NOMEM, "graph workspace of %zu bytes exceeds the context's limit of %zu bytes",
+                           total * sizeof(double), c->ws_limit));
   if (cudaMalloc(&g->ws, total * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(c->fail(LHF_ERR_NOMEM, "graph workspace of %zu bytes", total * sizeof(double)));

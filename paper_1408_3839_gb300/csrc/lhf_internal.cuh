@@ -261,8 +261,12 @@ cudaError_t launch_box_gram(const SysDev *sys, int nsys, int max_items, int max_
 cudaError_t launch_box_assemble(const SysDev *sys, int nsys, long long max_entries, cudaStream_t st);
 // Dense generalized symmetric-definite eigenvalues (cooperative launch, one CTA per SM).
 // work: dense_eig_workspace_doubles(N) doubles.  cudaErrorNotSupported without cooperative launch.
+// wait_cycles: bound of each grid-barrier wait (<= 0: kDefaultWaitCycles); stall: the barriers
+// expect one CTA more than launched, so that every wait runs out (failure-detection test).
+constexpr long long kDefaultWaitCycles = 2000000000ll;  // about a second at 2 GHz
 cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *eig,
-                             double *work, unsigned *flags, cudaStream_t st);
+                             double *work, unsigned *flags, cudaStream_t st,
+                             long long wait_cycles = kDefaultWaitCycles, int stall = 0);
 size_t dense_eig_workspace_doubles(int N);
 
 }  // namespace lhf

@@ -117,6 +117,9 @@ def load():
             "lhf_kernel_times": (st, [ctx, _dp, _ip]),
             "lhf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
+            "lhf_set_wait_limit": (st, [ctx, ctypes.c_longlong]),
+            "lhf_inject_barrier_stall": (st, [ctx]),
+            "lhf_set_workspace_limit": (st, [ctx, ctypes.c_size_t]),
             "lhf_k_point_eigensolve_noalloc": (st, [ctypes.POINTER(ctypes.c_int), ctypes.c_int] + [ctypes.c_void_p] * 5),
             "lhf_graph_create": (st, [ctx, ctypes.c_int, S, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_void_p)]),
@@ -402,6 +405,18 @@ class Context:
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.lhf_launch_shapes(self._h, ctypes.byref(a), ctypes.byref(b)))
         return {"eig_warps": a.value, "tri_threads": b.value}
+
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM clock cycles) of the dense eigensolver's grid-barrier waits; <= 0: default."""
+        self._check(self.lib.lhf_set_wait_limit(self._h, int(cycles)))
+
+    def inject_barrier_stall(self):
+        """Make the next dense eigensolve's barrier waits run out (failure-detection test)."""
+        self._check(self.lib.lhf_inject_barrier_stall(self._h))
+
+    def set_workspace_limit(self, nbytes: int):
+        """Cap on the context's device workspace in bytes (0: none)."""
+        self._check(self.lib.lhf_set_workspace_limit(self._h, int(nbytes)))
 
     def set_profiling(self, enable: bool):
         self._check(self.lib.lhf_set_profiling(self._h, 1 if enable else 0))
