@@ -42,7 +42,8 @@ typedef enum {
     LHF_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
     LHF_ERR_UNSUPPORTED = -5, /* valid input outside what this build supports */
     LHF_ERR_STATE = -6,       /* call order violated (e.g. assemble before setup) */
-    LHF_ERR_NOMEM = -7        /* workspace allocation failed */
+    LHF_ERR_NOMEM = -7,       /* workspace allocation failed */
+    LHF_ERR_NOT_CONVERGED = -8 /* an iterative solver stopped above its tolerance */
 } lhf_status;
 
 /* Arithmetic of the weighted Gram contractions (steps a3-a4).  Everything else (potential
@@ -235,6 +236,30 @@ lhf_status lhf_cell_energies(lhf_ctx *ctx, int nseg, const double *eig, const lo
  * full eigensolver): H x = lambda S x.  Device pointers; eig [N] ascending. */
 lhf_status lhf_dense_eigensolve(lhf_ctx *ctx, const double *H, const double *S, int N, double *eig);
 
+/* The n_ev lowest eigenvalues of an open (L,1,1) box (Sec. 3.3, eqs. (3.8)-(3.10); the box case of
+ * Table 4.1) without the dense eigensolve, for boxes beyond it (N_b = m0 L up to 4096 cells).
+ * The box's H and S are block-banded -- the block of cells (p, q) vanishes outside the overlap
+ * window (Lemma 3.1) -- and their overlap and kinetic parts are block-Toeplitz; the solver is
+ * block LOBPCG in FP64 on the banded matrices.  Its start block is a seeded block preconditioned
+ * by the block-circulant matrix whose blocks are the band's diagonals averaged over the rows (the
+ * Toeplitz-to-circulant embedding of Remark 2.4, padded to a power of two of at least L + window
+ * cells), which the DFT along the cells block-diagonalises (Lemma 2.2): one m0 x m0 Cholesky
+ * solve per k-point, shifted just below that circulant's spectrum.  The iterations are
+ * preconditioned by (H - sigma S)^{-1} itself, factored exactly as a block-tridiagonal Cholesky
+ * over super-cells that span the band, with sigma below the box's lowest eigenvalue (lowered
+ * until the factorisation succeeds).
+ *   box: one system, open along direction 0 (the lhf_bloch_spectra box layout); n_ev: 1 .. 20
+ *   (at most N_b); tol: convergence when every one of the n_ev residuals ||H x - theta S x|| (x
+ *   S-normalised) is at most tol max(1, |theta|) -- an eigenvalue is then accurate to about
+ *   ||r||^2 / (its gap to the rest of the spectrum); max_iter >= 1.
+ *   eig: device [n_ev], ascending (written also when not converged); iterations, residual: host,
+ *   optional: iterations run and the largest scaled residual at exit.
+ * Synchronising.  Returns LHF_OK, LHF_ERR_NOT_CONVERGED (eig holds the last Ritz values),
+ * LHF_ERR_ARG, LHF_ERR_UNSUPPORTED (a circulant of more than 8192 cells would be needed),
+ * LHF_ERR_NOT_SPD, LHF_ERR_NOMEM or LHF_ERR_CUDA. */
+lhf_status lhf_box_lowest_eigenvalues(lhf_ctx *ctx, const lhf_system_desc *box, int n_ev, double tol, int max_iter,
+                                      double *eig, int *iterations, double *residual);
+
 /* Batched Bloch spectra: for every system s of an array of nsys periodic lattices, the whole
  * path (basis and potential factors, Grams, rank sum, block DFT, k-point eigensolves) in one
  * pass of batched launches.  eig: device, systems concatenated, system s at offset
@@ -323,7 +348,8 @@ enum {
     LHF_K_DENSE_EIG = 14,    /* a9 dense generalized eigensolve */
     LHF_K_FACTOR_DFT = 15,   /* k-space route: 1D DFTs of the per-direction factors */
     LHF_K_KSPACE_BLOCKS = 16, /* k-space route: Hadamard products and rank sum per k-point */
-    LHF_NUM_KERNELS = 17
+    LHF_K_BOX_SOLVE = 17,    /* large box: banded products, preconditioner, Rayleigh-Ritz */
+    LHF_NUM_KERNELS = 18
 };
 lhf_status lhf_kernel_times(lhf_ctx *ctx, double *ms, int *launches);
 const char *lhf_kernel_name(int kernel);

@@ -285,7 +285,7 @@ void copy_grid(HostSystem &s, const lhf_grid_desc *d) {
 }
 
 // Consistency of the three parts; fills the plan (descriptor, window, workspace sizes).
-lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = false) {
+lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = false, bool dense_box = true) {
   SysDev &sd = P.sd;
   memset(&sd, 0, sizeof sd);
   if (s.M0 * s.R > lhf::kMaxRt) return c->fail(LHF_ERR_ARG, "M0 R = %d exceeds %d", s.M0 * s.R, lhf::kMaxRt);
@@ -493,7 +493,10 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     }
   }
   P.mixed = mixed && !box;  // the box's Grams run in FP64 in both modes
-  if (box) {
+  if (box && !dense_box) {  // banded matrices and an iterative solver (lhf_box_lowest_eigenvalues)
+    P.blocks_doubles = 0;
+    P.rank_items = 0;
+  } else if (box) {
     const size_t Nb = (size_t)m0 * s.L[0];
     if (Nb > 8192) return c->fail(LHF_ERR_UNSUPPORTED, "open box: N_b = %zu above 8192", Nb);
     P.dense_off = off;
@@ -1101,7 +1104,7 @@ const char *lhf_kernel_name(int kernel) {
   static const char *const names[LHF_NUM_KERNELS] = {
       "k_basis",   "k_potential",   "k_gram_fp64", "k_gram_slice",   "k_vslice",        "k_gram_tc",
       "k_gram_mirror", "k_ranksum", "k_dft_pass",  "k_overlap_norms", "k_eig",          "k_tridiag_eig",
-      "k_box_gram", "k_box_assemble", "k_dense_eig", "k_factor_dft", "k_kspace_blocks"};
+      "k_box_gram", "k_box_assemble", "k_dense_eig", "k_factor_dft", "k_kspace_blocks", "k_box_solve"};
   return kernel >= 0 && kernel < LHF_NUM_KERNELS ? names[kernel] : nullptr;
 }
 
@@ -1314,6 +1317,229 @@ lhf_status lhf_dense_eigensolve(lhf_ctx *c, const double *H, const double *S, in
   lhf_status st = ensure_ws(c, lhf::dense_eig_workspace_doubles(N));
   if (st != LHF_OK) return st;
   return run_dense_eig(c, H, S, N, eig, c->ws);
+}
+
+lhf_status lhf_box_lowest_eigenvalues(lhf_ctx *c, const lhf_system_desc *box, int n_ev, double tol, int max_iter,
+                                      double *eig, int *iterations, double *residual) {
+  if (!c) return LHF_ERR_ARG;
+  if (!box || !eig) return c->fail(LHF_ERR_ARG, "box and eig are required");
+  if (iterations) *iterations = 0;
+  if (residual) *residual = 0.0;
+  HostSystem hs;
+  lhf_status st = system_from_desc(c, box, hs);
+  if (st != LHF_OK) return st;
+  Plan P;
+  st = make_plan(c, hs, P, false, false);
+  if (st != LHF_OK) return st;
+  if (!P.sd.box) return c->fail(LHF_ERR_ARG, "lhf_box_lowest_eigenvalues needs an open (L,1,1) box");
+  const int L = P.sd.d[0].L, m0 = P.sd.m0, bJ = P.sd.bJ, bjlo = P.sd.bjlo;
+  const long long N = (long long)L * m0;
+  const int kv = std::min(n_ev + std::max(4, n_ev / 4), (int)std::min<long long>(N, 24));
+  if (n_ev < 1 || n_ev > 20 || n_ev > kv) return c->fail(LHF_ERR_ARG, "n_ev = %d outside [1, min(20, N)]", n_ev);
+  if (!(tol > 0.0) || max_iter < 1) return c->fail(LHF_ERR_ARG, "tol > 0 and max_iter >= 1 are required");
+  int M = 1;
+  while (M < L + bJ) M <<= 1;
+  if (M > 8192) return c->fail(LHF_ERR_UNSUPPORTED, "box of %d cells with a window of %d: circulant above 8192 cells", L, bJ);
+  // workspace: factors | band H, S | Z, HZ, SZ [3kv][N] | Z' [2kv][N] | R [kv][N] |
+  // Hk, Sk, Lk [M][m0][m0] complex | Vk [kv][M][m0] complex | GA, GB [72^2] | C [72][kv] |
+  // theta, rnorm [kv] | flags (one double: bad word + info)
+  const size_t band = align_up((size_t)L * bJ * m0 * m0);
+  const size_t vec = (size_t)N;  // vector stride (doubles)
+  const size_t kblk = align_up((size_t)M * m0 * m0 * 2);
+  const int nrr = lhf::rayleigh_ritz_max();
+  size_t off = P.ws;
+  const size_t o_hb = off, o_sb = o_hb + band;
+  off = o_sb + band;
+  const size_t blk3 = align_up(3 * kv * vec), blk2 = align_up(2 * kv * vec);
+  const size_t o_z = off, o_hz = o_z + blk3, o_sz = o_hz + blk3;
+  off = o_sz + blk3;
+  const size_t o_z2 = off;
+  off = o_z2 + blk2;
+  const size_t o_r = off;
+  off += align_up(kv * vec);
+  const size_t o_hk = off, o_sk = o_hk + kblk, o_lk = o_sk + kblk;
+  off = o_lk + kblk;
+  const size_t o_vk = off;
+  off = align_up(off + (size_t)kv * M * m0 * 2);
+  const size_t o_ha = off, o_sa = o_ha + align_up((size_t)bJ * m0 * m0);
+  off = o_sa + align_up((size_t)bJ * m0 * m0);
+  const size_t o_ga = off, o_gb = o_ga + align_up((size_t)nrr * nrr);
+  off = o_gb + align_up((size_t)nrr * nrr);
+  const size_t o_c = off;
+  off = align_up(off + (size_t)nrr * kv);
+  const size_t o_th = off, o_rn = o_th + align_up(kv);
+  off = o_rn + align_up(kv);
+  const size_t o_fl = off;
+  off = align_up(off + 4);
+  // block-tridiagonal factor of H - sigma S: super-cells of g cells (the band's reach)
+  const int g = std::max(1, std::max(-bjlo, bjlo + bJ - 1));
+  const int Bt = g * m0, nbt = (L + g - 1) / g;
+  const size_t o_td = off, o_te = o_td + align_up((size_t)nbt * Bt * Bt);
+  off = o_te + align_up((size_t)nbt * Bt * Bt);
+  const size_t o_tv = off;
+  off = align_up(off + (size_t)kv * nbt * Bt);
+  st = ensure_ws(c, off);
+  if (st != LHF_OK) return st;
+  double *w = c->ws;
+  bind_ws(P, w);
+  double *Hb = w + o_hb, *Sb = w + o_sb, *Z = w + o_z, *HZ = w + o_hz, *SZ = w + o_sz;
+  double *Z2 = w + o_z2, *R = w + o_r;
+  double2 *Hk = reinterpret_cast<double2 *>(w + o_hk), *Sk = reinterpret_cast<double2 *>(w + o_sk);
+  double2 *Lk = reinterpret_cast<double2 *>(w + o_lk), *Vk = reinterpret_cast<double2 *>(w + o_vk);
+  double *Ha = w + o_ha, *Sa = w + o_sa;
+  double *GA = w + o_ga, *GB = w + o_gb, *C = w + o_c, *theta = w + o_th, *rnorm = w + o_rn;
+  double *TD = w + o_td, *TE = w + o_te, *TV = w + o_tv;
+  unsigned *bad = reinterpret_cast<unsigned *>(w + o_fl);
+  int *info = reinterpret_cast<int *>(w + o_fl + 1);
+  std::vector<Plan> one(1, P);
+  st = upload(c, {P.sd});
+  if (st != LHF_OK) return st;
+  st = run_box_factors(c, one);
+  if (st != LHF_OK) return st;
+  auto cu = [&](cudaError_t e, const char *what) { return c->cuda(e, what); };
+  c->begin(5);
+  st = cu(lhf::launch_box_band(c->d_sys, (long long)L * bJ * m0 * m0, Hb, Sb, c->stream), "band kernel");
+  if (st == LHF_OK) st = cu(lhf::launch_band_average(Hb, Sb, L, bJ, bjlo, m0, Ha, Sa, c->stream), "band average");
+  if (st == LHF_OK)
+    st = cu(lhf::launch_prec_blocks(Ha, Sa, 0, bJ, bjlo, m0, M, Hk, Sk, c->stream), "preconditioner blocks");
+  c->end();
+  if (st != LHF_OK) return st;
+  // the preconditioner's shift: Pbar_kappa(sigma) = Hbar_kappa - sigma Sbar_kappa is positive
+  // definite for every kappa exactly when sigma lies below the spectrum of the bulk circulant
+  // (Sylvester's law of inertia per kappa); bisection on that test, then a margin below
+  auto pd = [&](double sigma, bool *ok) -> lhf_status {
+    lhf_status s2 = cu(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream), "cudaMemsetAsync");
+    if (s2 == LHF_OK) s2 = cu(lhf::launch_prec_factor(Hk, Sk, sigma, m0, M, Lk, bad, c->stream), "preconditioner factor");
+    unsigned h = 0;
+    if (s2 == LHF_OK) s2 = cu(cudaMemcpyAsync(&h, bad, sizeof h, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (s2 == LHF_OK) s2 = cu(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    *ok = h == 0;
+    return s2;
+  };
+  double lo = -1.0, hi = 0.0;
+  bool ok = false;
+  for (int t = 0; t < 64; ++t) {
+    if ((st = pd(lo, &ok)) != LHF_OK) return st;
+    if (ok) break;
+    hi = lo;
+    lo = 2.0 * lo - 1.0;
+  }
+  if (!ok) return c->fail(LHF_ERR_NOT_SPD, "no shift makes the bulk circulant positive definite");
+  for (int t = 0; t < 64; ++t) {  // an upper end where the test fails
+    if ((st = pd(hi, &ok)) != LHF_OK) return st;
+    if (!ok) break;
+    const double step = 2.0 * (hi - lo) + 1.0;
+    lo = hi;
+    hi += step;
+  }
+  for (int t = 0; t < 48 && hi - lo > 1e-12 * (1.0 + fabs(lo)); ++t) {
+    const double mid = 0.5 * (lo + hi);
+    if ((st = pd(mid, &ok)) != LHF_OK) return st;
+    (ok ? lo : hi) = mid;
+  }
+  const double sigma = lo - 0.05 * (1.0 + fabs(lo));
+  if ((st = pd(sigma, &ok)) != LHF_OK) return st;
+  if (!ok) return c->fail(LHF_ERR_NOT_SPD, "preconditioner not positive definite at sigma = %g", sigma);
+  const size_t vb = vec * sizeof(double);
+  c->begin(5);
+  // start: preconditioned seeded vectors, their products, Rayleigh-Ritz on X alone
+  st = cu(lhf::launch_start_vectors(R, kv, (long long)vec, 0x5eedull, c->stream), "start vectors");
+  if (st == LHF_OK) st = cu(lhf::launch_prec_apply(Lk, R, Z, Vk, L, m0, M, kv, c->stream), "preconditioner");
+  if (st == LHF_OK) st = cu(lhf::launch_band_mv(Hb, Sb, Z, HZ, SZ, L, bJ, bjlo, m0, kv, c->stream), "band matvec");
+  c->end();
+  if (st != LHF_OK) return st;
+  auto rr = [&](int n, int *kept) -> lhf_status {
+    lhf_status s2 = cu(lhf::launch_gram_vec(Z, HZ, n, N, GA, c->stream), "Gram kernel");
+    if (s2 == LHF_OK) s2 = cu(lhf::launch_gram_vec(Z, SZ, n, N, GB, c->stream), "Gram kernel");
+    if (s2 == LHF_OK) s2 = cu(lhf::launch_rayleigh_ritz(GA, GB, n, kv, 1e-12, theta, C, info, c->stream), "Rayleigh-Ritz kernel");
+    int h = 0;
+    if (s2 == LHF_OK) s2 = cu(cudaMemcpyAsync(&h, info, sizeof h, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (s2 == LHF_OK) s2 = cu(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    *kept = h;
+    return s2;
+  };
+  // X <- Z C (rows 0 .. n), P <- Z[kv..n] C[kv..n] (when with_p), then their products H X, S X,
+  // H P, S P by banded matvecs: updating the products by the same combinations would carry the
+  // rounding of coefficients of nearly dependent directions (up to 1 / sqrt(cut)) into them
+  auto update = [&](int n, bool with_p) -> lhf_status {
+    lhf_status s2 = cu(lhf::launch_lincomb(Z, C, kv, 0, n, kv, N, Z2, c->stream), "linear combination");
+    if (s2 == LHF_OK && with_p)
+      s2 = cu(lhf::launch_lincomb(Z, C, kv, kv, n, kv, N, Z2 + kv * vec, c->stream), "linear combination");
+    if (s2 == LHF_OK) s2 = cu(cudaMemcpyAsync(Z, Z2, kv * vb, cudaMemcpyDeviceToDevice, c->stream), "cudaMemcpyAsync");
+    if (s2 == LHF_OK && with_p)
+      s2 = cu(cudaMemcpyAsync(Z + 2 * kv * vec, Z2 + kv * vec, kv * vb, cudaMemcpyDeviceToDevice, c->stream),
+              "cudaMemcpyAsync");
+    if (s2 == LHF_OK) s2 = cu(lhf::launch_band_mv(Hb, Sb, Z, HZ, SZ, L, bJ, bjlo, m0, kv, c->stream), "band matvec");
+    if (s2 == LHF_OK && with_p)
+      s2 = cu(lhf::launch_band_mv(Hb, Sb, Z + 2 * kv * vec, HZ + 2 * kv * vec, SZ + 2 * kv * vec, L, bJ, bjlo, m0,
+                                  kv, c->stream),
+              "band matvec");
+    return s2;
+  };
+  int kept = 0;
+  if ((st = rr(kv, &kept)) != LHF_OK) return st;
+  if (kept < kv) return c->fail(LHF_ERR_NOT_SPD, "start block of rank %d < %d", kept, kv);
+  if ((st = update(kv, false)) != LHF_OK) return st;
+  std::vector<double> th(kv), rn(kv);
+  // the shift of the exact preconditioner (H - sigma S)^{-1}: below the lowest Ritz value of the
+  // start block by a quarter of its spread; lowered until the block Cholesky succeeds (positive
+  // definite exactly when sigma lies below the box's lowest eigenvalue)
+  st = cu(cudaMemcpyAsync(th.data(), theta, kv * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (st == LHF_OK) st = cu(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  const double spread = std::max(th[kv - 1] - th[0], 0.1);
+  double shift = th[0] - 0.25 * spread;
+  for (int t = 0;; ++t) {
+    lhf_status s2 = cu(cudaMemsetAsync(bad, 0, sizeof(unsigned), c->stream), "cudaMemsetAsync");
+    if (s2 == LHF_OK)
+      s2 = cu(lhf::launch_tri_factor(Hb, Sb, shift, L, bJ, bjlo, m0, g, nbt, TD, TE, bad, c->stream), "band factor");
+    unsigned h = 0;
+    if (s2 == LHF_OK) s2 = cu(cudaMemcpyAsync(&h, bad, sizeof h, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (s2 == LHF_OK) s2 = cu(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (s2 != LHF_OK) return s2;
+    if (h == 0) break;
+    if (t == 30) return c->fail(LHF_ERR_NOT_SPD, "no shift below the box spectrum found (last %g)", shift);
+    shift -= spread * (double)(1 << std::min(t, 20));
+  }
+  bool have_p = false;
+  int it = 0;
+  double worst = 0.0;
+  bool converged = false;
+  for (it = 0; it < max_iter; ++it) {
+    st = cu(lhf::launch_residual(HZ, SZ, theta, kv, N, R, rnorm, c->stream), "residual kernel");
+    if (st == LHF_OK) st = cu(cudaMemcpyAsync(th.data(), theta, kv * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (st == LHF_OK) st = cu(cudaMemcpyAsync(rn.data(), rnorm, kv * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    if (st == LHF_OK) st = cu(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (st != LHF_OK) return st;
+    worst = 0.0;
+    for (int i = 0; i < n_ev; ++i) worst = std::max(worst, rn[i] / std::max(1.0, fabs(th[i])));
+    if (worst <= tol) {
+      converged = true;
+      break;
+    }
+    // W = (H - shift S)^{-1} R into Z[kv .. 2kv), its products
+    st = cu(cudaMemcpyAsync(Z + kv * vec, R, kv * vb, cudaMemcpyDeviceToDevice, c->stream), "cudaMemcpyAsync");
+    if (st == LHF_OK) st = cu(lhf::launch_tri_solve(TD, TE, Bt, nbt, N, kv, Z + kv * vec, TV, c->stream), "band solve");
+    if (st == LHF_OK)
+      st = cu(lhf::launch_band_mv(Hb, Sb, Z + kv * vec, HZ + kv * vec, SZ + kv * vec, L, bJ, bjlo, m0, kv, c->stream),
+              "band matvec");
+    if (st != LHF_OK) return st;
+    int n = have_p ? 3 * kv : 2 * kv;
+    if ((st = rr(n, &kept)) != LHF_OK) return st;
+    if (kept < kv && have_p) {  // the previous directions made the basis degenerate: drop them
+      n = 2 * kv;
+      if ((st = rr(n, &kept)) != LHF_OK) return st;
+    }
+    if (kept < kv) return c->fail(LHF_ERR_NOT_SPD, "LOBPCG basis of rank %d < %d", kept, kv);
+    if ((st = update(n, true)) != LHF_OK) return st;
+    have_p = true;
+  }
+  if (iterations) *iterations = it;
+  if (residual) *residual = worst;
+  st = cu(cudaMemcpyAsync(eig, theta, n_ev * sizeof(double), cudaMemcpyDeviceToDevice, c->stream), "cudaMemcpyAsync");
+  if (st != LHF_OK) return st;
+  if (!converged) return c->fail(LHF_ERR_NOT_CONVERGED, "LOBPCG: residual %.3g above %.3g after %d iterations", worst, tol, it);
+  return LHF_OK;
 }
 
 lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *systems, lhf_precision prec,

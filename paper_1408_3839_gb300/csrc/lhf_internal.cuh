@@ -268,5 +268,39 @@ cudaError_t launch_dense_eig(const double *H, const double *S, int N, double *ei
                              double *work, unsigned *flags, cudaStream_t st,
                              long long wait_cycles = kDefaultWaitCycles, int stall = 0);
 size_t dense_eig_workspace_doubles(int N);
+// Iterative solver of large open boxes (k_lobpcg.cu): band H, S [L][bJ][m0][m0] from the box
+// factors (one system at sys[0]); banded products of kv vectors ([kv][N], N = L m0); the
+// block-circulant preconditioner of M cells (power of two >= L + bJ): the band averaged over the
+// rows [bJ][m0][m0] and its kappa blocks, their Cholesky factors at a shift (bad |= 1 when one is not positive definite), and
+// its application Y = T X (Vk: kv M m0 complex scratch); Gram matrices G = Z^T Y of nz vectors;
+// out = sum_{j0 <= j < j1} C[j][c] Z[j] for c < kv; residuals R = YH - theta YS and their norms;
+// seeded start vectors; the Rayleigh-Ritz step on a pencil of order n <= rayleigh_ritz_max().
+cudaError_t launch_box_band(const SysDev *sys, long long items, double *Hband, double *Sband, cudaStream_t st);
+cudaError_t launch_band_mv(const double *Hb, const double *Sb, const double *X, double *YH, double *YS, int L,
+                           int bJ, int bjlo, int m0, int kv, cudaStream_t st);
+cudaError_t launch_band_average(const double *Hb, const double *Sb, int L, int bJ, int bjlo, int m0, double *Ha,
+                                double *Sa, cudaStream_t st);
+cudaError_t launch_prec_blocks(const double *Hb, const double *Sb, int mid, int bJ, int bjlo, int m0, int M,
+                               double2 *Hk, double2 *Sk, cudaStream_t st);
+cudaError_t launch_prec_factor(const double2 *Hk, const double2 *Sk, double sigma, int m0, int M, double2 *Lk,
+                               unsigned *bad, cudaStream_t st);
+cudaError_t launch_prec_apply(const double2 *Lk, const double *X, double *Y, double2 *Vk, int L, int m0, int M,
+                              int kv, cudaStream_t st);
+// Block-tridiagonal Cholesky of H - sigma S (super-cells of g cells, B = g m0, nb = ceil(L / g)
+// blocks; D, E: nb B^2 doubles each; bad |= 1 when not positive definite) and its solve of kv
+// right-hand sides in place in Y [kv][N] (scratch V: kv nb B doubles).
+cudaError_t launch_tri_factor(const double *Hb, const double *Sb, double sigma, int L, int bJ, int bjlo, int m0,
+                              int g, int nb, double *D, double *E, unsigned *bad, cudaStream_t st);
+cudaError_t launch_tri_solve(const double *D, const double *E, int B, int nb, long long N, int kv, double *Y,
+                             double *V, cudaStream_t st);
+cudaError_t launch_gram_vec(const double *Z, const double *Y, int nz, long long N, double *G, cudaStream_t st);
+cudaError_t launch_lincomb(const double *Z, const double *C, int ldc, int j0, int j1, int kv, long long N,
+                           double *out, cudaStream_t st);
+cudaError_t launch_residual(const double *YH, const double *YS, const double *theta, int kv, long long N,
+                            double *R, double *rnorm, cudaStream_t st);
+cudaError_t launch_start_vectors(double *X, int kv, long long N, unsigned long long seed, cudaStream_t st);
+int rayleigh_ritz_max();
+cudaError_t launch_rayleigh_ritz(const double *A, const double *B, int n, int kv, double cut, double *theta,
+                                 double *C, int *info, cudaStream_t st);
 
 }  // namespace lhf

@@ -23,6 +23,7 @@ LHF_ERR_TIMEOUT = -4
 LHF_ERR_UNSUPPORTED = -5
 LHF_ERR_STATE = -6
 LHF_ERR_NOMEM = -7
+LHF_ERR_NOT_CONVERGED = -8
 
 FP64 = 0
 MIXED = 1
@@ -117,6 +118,8 @@ def load():
             "lhf_kernel_times": (st, [ctx, _dp, _ip]),
             "lhf_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
+            "lhf_box_lowest_eigenvalues": (st, [ctx, S, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
             "lhf_set_wait_limit": (st, [ctx, ctypes.c_longlong]),
             "lhf_inject_barrier_stall": (st, [ctx]),
             "lhf_set_workspace_limit": (st, [ctx, ctypes.c_size_t]),
@@ -353,6 +356,19 @@ class Context:
         self._check(self.lib.lhf_k_point_eigenvectors(self._h, _ptr(Hbar), _ptr(Sbar), _ptr(eig), _ptr(vecs),
                                                       _ptr(k_status)))
 
+    def box_lowest_eigenvalues(self, cfg, n_ev: int, eig, tol: float = 1e-7, max_iter: int = 300,
+                               check: bool = True):
+        """lhf_box_lowest_eigenvalues: the n_ev lowest eigenvalues of an open (L,1,1) box by
+        preconditioned LOBPCG on its banded matrices; returns (status, iterations, residual)."""
+        batch, arr = self._systems([cfg])
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        st = self.lib.lhf_box_lowest_eigenvalues(self._h, arr, int(n_ev), float(tol), int(max_iter), _ptr(eig),
+                                                 ctypes.byref(it), ctypes.byref(res))
+        if check:
+            self._check(st)
+        return st, it.value, res.value
+
     def dense_eigensolve(self, H, S, N: int, eig):
         self._check(self.lib.lhf_dense_eigensolve(self._h, _ptr(H), _ptr(S), int(N), _ptr(eig)))
 
@@ -429,7 +445,7 @@ class Context:
         self._check(self.lib.lhf_stage_times(self._h, ms, cnt))
         return {name: (ms[i], cnt[i]) for i, name in enumerate(self.STAGES)}
 
-    NUM_KERNELS = 17
+    NUM_KERNELS = 18
 
     def kernel_times(self) -> dict:
         """{kernel name: (total ms, launches)} for kernel launches recorded since the previous call."""
