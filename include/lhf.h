@@ -62,7 +62,10 @@ typedef struct lhf_ctx lhf_ctx;
  * direction l (images k = -floor(K/2) .. floor(K/2), weight 1/2 on |k| = K/2 for even K; the sum
  * is evaluated in cell 0 and replicated, eq. (4.1)).  Open directions ignore K_sum.  Z_cell
  * (optional, NULL otherwise) gives per-cell charges Z_cell[k M0 + nu] of an open box whose only
- * lattice direction is l = 0 (eq. (3.8)).  Host pointers; copied during setup. */
+ * lattice direction is l = 0 (eq. (3.8)).  L[l] is 1 .. 4096, except that a one-dimensional
+ * lattice (L[1] = L[2] = 1) may have up to 32768 cells along l = 0 when L[0] splits as A B with
+ * A, B <= 4096 (its block DFT then runs as two passes of such lengths).  Host pointers; copied
+ * during setup. */
 typedef struct {
     int L[3];
     double b[3];

@@ -32,7 +32,7 @@ __device__ inline unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (3
 
 __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restrict__ sysv, int d) {
   const SysDev &s = sysv[blockIdx.y];
-  if (s.box) return;
+  if (s.box || s.d[0].L > kDftTileMax) return;  // long chains take the four-step route
   const int L0 = s.d[0].L, L1 = s.d[1].L, L2 = s.d[2].L;
   const int Ls[3] = {L0, L1, L2};
   const bool all_one = (L0 == 1 && L1 == 1 && L2 == 1);
@@ -238,17 +238,164 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   }
 }
 
+// ---- four-step DFT of long one-dimensional lattices ----------------------------------------
+// For L = A B, j = B j1 + j2 and kappa = kappa1 + A kappa2 (j1, kappa1 < A; j2, kappa2 < B):
+//   Xbar_kappa = sum_j2 omega_B^(j2 kappa2) [omega_L^(j2 kappa1) sum_j1 omega_A^(j1 kappa1) X_(B j1 + j2)]
+// (the factorisation of F_L behind Lemma 2.2's fast transform): pass 1 transforms along j1 for
+// every (j2, entry) and applies the twiddle omega_L^(j2 kappa1), writing Y[kappa1][j2]; pass 2
+// transforms along j2 for every (kappa1, entry) and writes Xbar at kappa1 + A kappa2.  Every entry
+// (mu, nu) of H and S is transformed (blockIdx.z: 0 H, 1 S).  A tile holds TW consecutive entries
+// for all positions of one transform in shared memory: radix-2 when the length is a power of two,
+// the direct sum with a twiddle table otherwise.
+
+// In-place transform of Ld positions x TW columns (x[j * TW + t]); tab[m] = omega^m.  For a power
+// of two the input must have been stored bit-reversed.
+__device__ void tile_transform(double2 *x, int Ld, int TW, int tw_valid, const double2 *tab, bool pow2,
+                               double2 *tmp) {
+  const int tid = threadIdx.x;
+  if (pow2) {
+    for (int hs = 1; hs < Ld; hs <<= 1) {
+      const int stride = Ld / (2 * hs);
+      for (int k = tid; k < (Ld / 2) * TW; k += kDftThreads) {
+        const int t = k % TW, b = k / TW;
+        const int kk = b % hs;
+        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
+        const double2 w = tab[kk * stride];
+        const double2 u = x[top * TW + t], v = x[bot * TW + t];
+        const double2 wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
+        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
+        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // direct sum into tmp, then back
+  for (int k = tid; k < Ld * TW; k += kDftThreads) {
+    const int kap = k / TW, t = k - kap * TW;
+    double re = 0.0, im = 0.0;
+    if (t < tw_valid) {
+      int m = 0;
+      for (int j = 0; j < Ld; ++j) {
+        const double2 w = tab[m], v = x[j * TW + t];
+        re += w.x * v.x - w.y * v.y;
+        im += w.x * v.y + w.y * v.x;
+        m += kap;
+        if (m >= Ld) m -= Ld;
+      }
+    }
+    tmp[k] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int k = tid; k < Ld * TW; k += kDftThreads) x[k] = tmp[k];
+  __syncthreads();
+}
+
+__device__ void twiddle_table(double2 *tab, int Ld) {
+  for (int m = threadIdx.x; m < Ld; m += kDftThreads) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)Ld, &sn, &cs);
+    tab[m] = make_double2(cs, -sn);
+  }
+}
+
+// pass: 1 (along j1, length A, then the twiddle) or 2 (along j2, length B).  Grid x: (pass 1: j2,
+// pass 2: kappa1) x entry tiles; z: H / S.
+__global__ void __launch_bounds__(kDftThreads) k_dft_four_step(const SysDev *__restrict__ sysv, int A, int B,
+                                                               int pass) {
+  const SysDev &s = *sysv;
+  const int m0 = s.m0, mm = m0 * m0, L = A * B;
+  const int Ld = pass == 1 ? A : B;
+  const int TW = tile_width(Ld);
+  const int tiles_e = (mm + TW - 1) / TW;
+  const int line = blockIdx.x / tiles_e, e0 = (blockIdx.x % tiles_e) * TW;
+  const int tw_valid = mm - e0 < TW ? mm - e0 : TW;
+  const bool pow2 = (Ld & (Ld - 1)) == 0;
+  const int bits = pow2 ? __ffs(Ld) - 1 : 0;
+  extern __shared__ double sm[];
+  double2 *x = reinterpret_cast<double2 *>(sm);  // [Ld][TW]
+  double2 *tab = x + (size_t)Ld * TW;            // [Ld]
+  double2 *tmp = tab + Ld;                       // [Ld][TW] (direct sums only)
+  twiddle_table(tab, Ld);
+  double2 *Y = reinterpret_cast<double2 *>(s.dftw) + (size_t)blockIdx.z * L * mm;
+  for (int k = threadIdx.x; k < Ld * TW; k += kDftThreads) {
+    const int j = k / TW, t = k - j * TW;
+    double2 v = make_double2(0.0, 0.0);
+    if (t < tw_valid) {
+      if (pass == 1) {  // X_(B j + j2), real
+        const double *X = blockIdx.z == 0 ? s.H : s.S;
+        v.x = X[((int64_t)B * j + line) * mm + e0 + t];
+      } else {  // Y[kappa1][j]
+        v = Y[((int64_t)line * B + j) * mm + e0 + t];
+      }
+    }
+    const int pos = (pow2 && bits > 0) ? (int)bitrev((unsigned)j, bits) : j;
+    x[pos * TW + t] = v;
+  }
+  __syncthreads();
+  tile_transform(x, Ld, TW, tw_valid, tab, pow2, tmp);
+  for (int k = threadIdx.x; k < Ld * TW; k += kDftThreads) {
+    const int kap = k / TW, t = k - kap * TW;
+    if (t >= tw_valid) continue;
+    double2 v = x[kap * TW + t];
+    if (pass == 1) {
+      // omega_L^(j2 kappa1), the phase reduced mod L in integers
+      const long long ph = ((long long)line * kap) % L;
+      double sn, cs;
+      sincospi(2.0 * (double)ph / (double)L, &sn, &cs);
+      v = make_double2(cs * v.x + sn * v.y, cs * v.y - sn * v.x);  // (cs - i sn) v
+      Y[((int64_t)kap * B + line) * mm + e0 + t] = v;
+    } else {
+      double2 *Xc = reinterpret_cast<double2 *>(blockIdx.z == 0 ? s.Hbar : s.Sbar);
+      Xc[((int64_t)line + (int64_t)A * kap) * mm + e0 + t] = v;
+    }
+  }
+}
+
 }  // namespace
+
+bool dft_four_step_split(int L, int *A, int *B) {
+  // the most balanced split L = A B with B <= A <= kDftTileMax
+  int best = 0;
+  for (int b = 1; (long long)b * b <= L; ++b)
+    if (L % b == 0 && L / b <= kDftTileMax) best = b;
+  if (!best) return false;
+  *A = L / best;
+  *B = best;
+  return true;
+}
 
 // host_L: [nsys][3] lattice sizes (host copy) used to size the grid of each pass.
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st) {
   if (nsys <= 0) return cudaSuccess;
+  for (int s = 0; s < nsys; ++s) {
+    const int *L = host_L + 4 * s;
+    if (L[0] <= kDftTileMax) continue;
+    int A = 0, B = 0;
+    if (L[1] != 1 || L[2] != 1 || !dft_four_step_split(L[0], &A, &B)) return cudaErrorInvalidValue;
+    const int m0 = L[3], mm = m0 * m0;
+    for (int pass = 1; pass <= 2; ++pass) {
+      const int Ld = pass == 1 ? A : B, lines = pass == 1 ? B : A;
+      const int TW = tile_width(Ld);
+      const bool pow2 = (Ld & (Ld - 1)) == 0;
+      const size_t smem = sizeof(double2) * ((size_t)Ld * TW * (pow2 ? 1 : 2) + Ld);
+      cudaError_t e = cudaFuncSetAttribute(k_dft_four_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      dim3 grid((unsigned)(lines * ((mm + TW - 1) / TW)), 1, 2);
+      kmark(LHF_K_DFT, 1, st);
+      k_dft_four_step<<<grid, kDftThreads, smem, st>>>(sys + s, A, B, pass);
+      kmark(LHF_K_DFT, 0, st);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (passes) ++*passes;
+    }
+  }
   for (int d = 2; d >= 0; --d) {
     int64_t max_tiles = 0;
     int max_Ld = 0;
     for (int s = 0; s < nsys; ++s) {
       const int *L = host_L + 4 * s;  // L0, L1, L2, m0
+      if (L[0] > kDftTileMax) continue;  // four-step route above
       const bool all_one = (L[0] == 1 && L[1] == 1 && L[2] == 1);
       if (!(L[d] > 1 || (d == 0 && all_one))) continue;
       int last = 0;
@@ -271,6 +418,7 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
     size_t smem = 0;
     for (int s = 0; s < nsys; ++s) {
       const int *L = host_L + 4 * s;
+      if (L[0] > kDftTileMax) continue;
       const int Ld = L[d];
       const size_t need = sizeof(double2) * ((size_t)Ld * tile_width(Ld) + Ld);
       if (need > smem) smem = need;

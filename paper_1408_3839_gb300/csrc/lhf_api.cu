@@ -57,6 +57,7 @@ struct Plan {
   long long mirror_items = 0;  // window-block elements filled from their mirrors
   size_t zcell_off = 0, dense_off = 0;
   size_t tri_off = 0;  // tridiagonal scratch of the k-point solves (periodic)
+  size_t dft_off = 0;  // four-step DFT scratch of a long chain (0: none)
   std::vector<double> zcell;  // host copy of the per-cell charges (box)
 };
 
@@ -198,7 +199,9 @@ namespace {
 lhf_status check_lattice(lhf_ctx *c, const lhf_lattice_desc *d) {
   if (!d) return c->fail(LHF_ERR_ARG, "lattice descriptor is NULL");
   for (int l = 0; l < 3; ++l) {
-    if (d->L[l] < 1 || d->L[l] > 4096) return c->fail(LHF_ERR_ARG, "L[%d] = %d outside [1, 4096]", l, d->L[l]);
+    // up to kDftTileMax per direction; a one-dimensional lattice up to kDftMaxL1 cells
+    const int lmax = (l == 0 && d->L[1] == 1 && d->L[2] == 1) ? lhf::kDftMaxL1 : lhf::kDftTileMax;
+    if (d->L[l] < 1 || d->L[l] > lmax) return c->fail(LHF_ERR_ARG, "L[%d] = %d outside [1, %d]", l, d->L[l], lmax);
     if (!(d->b[l] > 0) || !finite(d->b[l])) return c->fail(LHF_ERR_ARG, "b[%d] must be positive", l);
     if (d->periodic[l] != 0 && d->periodic[l] != 1) return c->fail(LHF_ERR_ARG, "periodic[%d] must be 0 or 1", l);
     if (d->periodic[l] && (d->K_sum[l] < 1 || d->K_sum[l] > 1 << 20))
@@ -506,6 +509,13 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
   } else {
     P.tri_off = off;  // one slot per k-point bounds the solved ones
     off = align_up(off + (size_t)sd.nblocks * (2 * m0 + 1));
+    if (s.L[0] > lhf::kDftTileMax) {  // scratch of the four-step DFT
+      int A = 0, B = 0;
+      if (!lhf::dft_four_step_split(s.L[0], &A, &B))
+        return c->fail(LHF_ERR_UNSUPPORTED, "L = %d has no split A B with A, B <= %d for the DFT", s.L[0], lhf::kDftTileMax);
+      P.dft_off = off;
+      off = align_up(off + (size_t)4 * s.L[0] * mm);
+    }
     P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
     P.rank_items = sd.nblocks;  // zeros outside the window: CTA per block
     P.rank_group = lhf::ranksum_group(sd);
@@ -924,6 +934,7 @@ void bind_ws(Plan &p, double *base) {
   p.sd.s0 = base + p.s0_off;
   p.sd.zcell = (p.sd.box && !p.zcell.empty()) ? base + p.zcell_off : nullptr;
   p.sd.tri = p.sd.box ? nullptr : base + p.tri_off;
+  p.sd.dftw = p.dft_off ? base + p.dft_off : nullptr;
 }
 
 // Plan one system with workspace at ws_base and internal H, S, Hbar, Sbar after its factors.
@@ -1256,6 +1267,9 @@ lhf_status lhf_circulant_fft(lhf_ctx *c, const double *H, const double *S, doubl
   lhf_status st = current_plan(c, ps[0]);
   if (st != LHF_OK) return st;
   if (ps[0].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "the block DFT needs a periodic lattice");
+  st = ensure_ws(c, ps[0].ws);  // the four-step route of long chains uses the plan's scratch
+  if (st != LHF_OK) return st;
+  bind_ws(ps[0], c->ws);
   ps[0].sd.H = const_cast<double *>(H);
   ps[0].sd.S = const_cast<double *>(S);
   ps[0].sd.Hbar = Hbar;

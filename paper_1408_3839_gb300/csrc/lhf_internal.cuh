@@ -90,6 +90,7 @@ struct SysDev {
   const int *klist;       // [nkhalf] k-points solved (one per conjugate pair), or null
   double *tri;            // [nkhalf][2 m0 + 1] tridiagonal of each solved k-point, or null (Jacobi)
   double *vecs;           // complex [nblocks][m0][m0] Bloch eigenvectors (rows), or null
+  double *dftw;           // complex [2][L0][m0][m0] scratch of the four-step DFT (L0 > kDftTileMax), or null
   // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
@@ -214,6 +215,12 @@ int ranksum_group(const SysDev &s);
 int ranksum_compute_items(const SysDev &s, int group);
 cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, int group,
                            cudaStream_t st);
+// A lattice dimension of at most kDftTileMax positions is transformed in one shared-memory tile
+// per pass; a one-dimensional lattice of up to kDftMaxL1 cells with L0 > kDftTileMax takes the
+// four-step route (L0 = A B, A, B <= kDftTileMax) through the scratch SysDev::dftw.
+constexpr int kDftTileMax = 4096;
+constexpr int kDftMaxL1 = 32768;
+bool dft_four_step_split(int L, int *A, int *B);  // a split with A, B <= kDftTileMax, A >= B
 cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *passes,
                        cudaStream_t st);  // *passes += kernel launches (may be null)
 // k-point eigensolves; tri: systems carry a tridiagonal scratch (SysDev::tri), and the
