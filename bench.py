@@ -617,6 +617,38 @@ def run_extras(ctx, lhf, stream, steps: int, warmup: int) -> dict:
             "rows": rows}
     except Exception as e:
         out["box_lowest_16"] = {"error": str(e)}
+    # rank reduction of the direction-0 potential (FP64 route), tube_256 batch of 64
+    try:
+        cfgs = [W.tube_256(seed) for seed in range(3000, 3064)]
+        ctx.setup(cfgs[0])
+        sz = ctx.query_sizes()
+        eig = torch.empty(64 * sz["n_kpoints"] * sz["m0"], dtype=torch.float64, device="cuda")
+        ref = torch.empty_like(eig)
+        ctx.bloch_spectra(cfgs, ref, None, lhf.FP64)
+        for _ in range(warmup):
+            ctx.bloch_spectra(cfgs, ref, None, lhf.FP64)
+        ms_full = _device_time_ms(lambda: ctx.bloch_spectra(cfgs, ref, None, lhf.FP64), steps, stream) / steps
+        rows = {}
+        for eps in (1e-12, 1e-8):
+            ctx.set_rank_reduction(eps)
+            ctx.setup(cfgs[0])
+            info = ctx.rank_reduction_info()
+            for _ in range(warmup):
+                ctx.bloch_spectra(cfgs, eig, None, lhf.FP64)
+            ms = _device_time_ms(lambda: ctx.bloch_spectra(cfgs, eig, None, lhf.FP64), steps, stream) / steps
+            fin = torch.isfinite(ref) & torch.isfinite(eig)
+            rows[str(eps)] = {"rank_in": info["rank_in"], "rank_out": info["rank_out"],
+                              "dropped_over_largest": info["dropped"] / info["largest"], "ms_per_step": ms,
+                              "value": 64 / (ms / 1e3),
+                              "max_abs_diff_vs_unreduced_ha": float((eig - ref)[fin].abs().max().item())}
+        ctx.set_rank_reduction(0.0)
+        out["rank_reduction_fp64"] = {
+            "workload": "tube_256 batch of 64 (seeds 3000..3063), FP64 route, direction-0 potential rank reduced "
+                        "by a truncated SVD (one CTA per system)", "unreduced_ms_per_step": ms_full,
+            "unreduced_value": 64 / (ms_full / 1e3), "rows": rows}
+    except Exception as e:
+        ctx.set_rank_reduction(0.0)
+        out["rank_reduction_fp64"] = {"error": str(e)}
     # periodic (8,1,1), FP64
     try:
         p8 = W.periodic_8()

@@ -364,6 +364,23 @@ const char *lhf_kernel_name(int kernel);
  * of k-points).  Reset by the call. */
 lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned long long *matrices);
 
+/* Rank reduction of the lattice-summed potential (the rank optimisation of Sec. 3.2) for periodic
+ * (L,1,1) lattices on the FP64 route.  The nuclear part of a block is a sum over R_tot = M0 R rank
+ * terms, V_j = sum_r <Q_j, v_r> T_r (v_r the direction-0 factor over one cell, Q_j the cell fold of
+ * the product row, T_r = c_r C1_r (.) C2_r the single-cell transverse factors).  With weights
+ * w_r = max |T_r|, the truncated SVD of the weighted factor rows, v_r w_r = sum_a Y_ra s_a u_a,
+ * keeps the s_a > eps s_0 and replaces the sum by r1 terms, V_j ~ sum_a <Q_j, u_a> D_a with
+ * D_a = s_a sum_r Y_ra T_r / w_r; every entry of V_j then moves by at most
+ * s_r1 ||Q_j,mu,nu||_2 ||(T_r[mu][nu] / w_r)_r||_2 <= s_r1 ||Q_j,mu,nu||_2 sqrt(R_tot), s_r1 the
+ * largest dropped singular value.  The direction-0 Gram and the rank sum then run over r1 terms.
+ * lhf_set_rank_reduction: eps in (0, 1) turns it on for the context's later FP64 assemblies and
+ * spectra of such lattices with R_tot <= 64 (other systems, the mixed route and graphs are
+ * unaffected); 0 turns it off.  lhf_rank_reduction_info: for the current setup system (reduction
+ * on), runs the factor stages and returns R_tot, r1, s_r1 and s_0 (host outputs, each optional;
+ * synchronising). */
+lhf_status lhf_set_rank_reduction(lhf_ctx *ctx, double eps);
+lhf_status lhf_rank_reduction_info(lhf_ctx *ctx, int *rank_in, int *rank_out, double *dropped, double *largest);
+
 /* Failure detection (no counterpart in the paper: controls of this library's own error paths).
  * lhf_set_wait_limit: the bound, in SM clock cycles, of every wait at a grid barrier of the dense
  *   eigensolver (lhf_dense_eigensolve and the open-box path); cycles <= 0 restores the default

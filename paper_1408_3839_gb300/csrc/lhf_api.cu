@@ -58,6 +58,7 @@ struct Plan {
   size_t zcell_off = 0, dense_off = 0;
   size_t tri_off = 0;  // tridiagonal scratch of the k-point solves (periodic)
   size_t dft_off = 0;  // four-step DFT scratch of a long chain (0: none)
+  size_t rank_smem = 0;  // shared memory of the rank reduction (0: not reduced)
   std::vector<double> zcell;  // host copy of the per-cell charges (box)
 };
 
@@ -98,6 +99,7 @@ struct lhf_ctx {
   std::vector<int> host_L;
   // failure detection: bound of the dense solver's grid-barrier waits, a one-shot injected
   // barrier stall (test), and a cap on the workspace bytes (0: none)
+  double rank_eps = 0.0;  // rank reduction of one-dimensional lattices (FP64 route); 0: off
   long long wait_cycles = lhf::kDefaultWaitCycles;
   bool stall_next = false;
   size_t ws_limit = 0;
@@ -523,6 +525,16 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     P.rank_compute4 = lhf::ranksum_compute_items(sd, 4);
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
+  // rank reduction: periodic (L,1,1) lattices with open single-cell transverse directions, FP64
+  sd.rank_eps = 0.0;
+  sd.offRR = 0;
+  if (c->rank_eps > 0.0 && !box && !mixed && s.periodic[0] && !s.periodic[1] && !s.periodic[2] && s.L[1] == 1 &&
+      s.L[2] == 1 && Rt <= lhf::kRankReduceMaxRt && lhf::rank_reduce_smem_bytes(Rt, sd.d[0].nv) <= 200 * 1024) {
+    sd.rank_eps = c->rank_eps;
+    sd.offRR = (int64_t)off;
+    off = align_up(off + 8 + (size_t)(Rt + 4) * mm);
+    P.rank_smem = lhf::rank_reduce_smem_bytes(Rt, sd.d[0].nv);
+  }
   P.basis_items = lhf::basis_ctas(sd);  // one CTA per (direction, function, chunk of samples)
   P.pot_rows = lhf::potential_ctas(sd);  // one CTA per (direction, rank term, chunk of cells)
   P.ws = off;
@@ -627,13 +639,25 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
   int gram_launches = 0;
   lhf_status st = LHF_OK;
   if (!ps[0].mixed) {
+    // with a rank reduction, the transverse directions first, then the reduction (which rewrites
+    // the direction-0 potential rows and the transverse factors), then direction 0
+    size_t rsmem = 0;
+    for (const Plan &p : ps) rsmem = std::max(rsmem, p.rank_smem);
+    const int order[3] = {rsmem ? 1 : 0, rsmem ? 2 : 1, rsmem ? 0 : 2};
     c->begin(2);
-    for (int l = 0; l < 3 && st == LHF_OK; ++l)
+    for (int o = 0; o < 3 && st == LHF_OK; ++o) {
+      const int l = order[o];
+      if (rsmem && l == 0) {
+        st = c->cuda(lhf::launch_rank_reduce(c->d_sys, nsys, rsmem, c->stream), "rank-reduction kernel");
+        ++gram_launches;
+        if (st != LHF_OK) break;
+      }
       if (dir_blocks[l] > 0) {
         st = c->cuda(lhf::launch_gram_fp64(c->d_sys, nsys, dir_blocks[l], max_m0, dir_nv[l], c->stream, l),
                      "Gram kernel");
         ++gram_launches;
       }
+    }
     if (st == LHF_OK) st = c->cuda(lhf::launch_gram_mirror(c->d_sys, nsys, mirror, c->stream), "mirror kernel");
     c->end(gram_launches + (mirror > 0 ? 1 : 0));
     return st;
@@ -694,6 +718,20 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
 }
 
 // Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
+// a1, a2 and the Gram factors (with the rank reduction when planned), without the rank sum.
+lhf_status run_assembly_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
+  const int nsys = (int)ps.size();
+  c->begin(0);
+  lhf_status st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  c->begin(1);
+  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
+  c->end();
+  if (st != LHF_OK) return st;
+  return run_gram(c, ps, false);
+}
+
 lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
   lhf_status st;  // (a6, the zero blocks outside the window, is written by the rank-sum kernel)
@@ -1038,6 +1076,39 @@ lhf_status lhf_launch_shapes(lhf_ctx *c, int *eig_warps, int *tri_threads) {
   if (!c || !eig_warps || !tri_threads) return LHF_ERR_ARG;
   *eig_warps = c->last_eig_warps;
   *tri_threads = c->last_tri_threads;
+  return LHF_OK;
+}
+
+lhf_status lhf_set_rank_reduction(lhf_ctx *c, double eps) {
+  if (!c) return LHF_ERR_ARG;
+  if (!(eps >= 0.0) || eps >= 1.0) return c->fail(LHF_ERR_ARG, "eps = %g outside [0, 1)", eps);
+  c->rank_eps = eps;
+  return LHF_OK;
+}
+
+lhf_status lhf_rank_reduction_info(lhf_ctx *c, int *rank_in, int *rank_out, double *dropped, double *largest) {
+  if (!c) return LHF_ERR_ARG;
+  if (!(c->rank_eps > 0.0)) return c->fail(LHF_ERR_STATE, "rank reduction is off");
+  Plan P;
+  lhf_status st = current_plan(c, P);
+  if (st != LHF_OK) return st;
+  if (!P.rank_smem) return c->fail(LHF_ERR_UNSUPPORTED, "the current system takes no rank reduction");
+  st = ensure_ws(c, P.ws);
+  if (st != LHF_OK) return st;
+  bind_ws(P, c->ws);
+  st = upload(c, {P.sd});
+  if (st != LHF_OK) return st;
+  std::vector<Plan> one(1, P);
+  st = run_assembly_factors(c, one);
+  if (st != LHF_OK) return st;
+  double h[4] = {0, 0, 0, 0};
+  st = c->cuda(cudaMemcpyAsync(h, P.sd.ws + P.sd.offRR, sizeof h, cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+  if (st == LHF_OK) st = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (st != LHF_OK) return st;
+  if (rank_in) *rank_in = (int)h[0];
+  if (rank_out) *rank_out = (int)h[1];
+  if (dropped) *dropped = h[2];
+  if (largest) *largest = h[3];
   return LHF_OK;
 }
 
@@ -1642,6 +1713,10 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
     st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
     st = make_plan(c, hs, ps[i], prec == LHF_MIXED);
+    if (ps[i].rank_smem) {  // a replay would read the descriptor the reduction rewrote
+      ps[i].sd.rank_eps = 0.0;
+      ps[i].rank_smem = 0;
+    }
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
     if (ps[i].sd.box) return c->fail(LHF_ERR_UNSUPPORTED, "system %d: open boxes are not captured in graphs", i);
     total += internal_doubles(ps[i]);

@@ -91,6 +91,10 @@ struct SysDev {
   double *tri;            // [nkhalf][2 m0 + 1] tridiagonal of each solved k-point, or null (Jacobi)
   double *vecs;           // complex [nblocks][m0][m0] Bloch eigenvectors (rows), or null
   double *dftw;           // complex [2][L0][m0][m0] scratch of the four-step DFT (L0 > kDftTileMax), or null
+  // rank reduction of the direction-0 potential factors (one-dimensional lattices, FP64 route):
+  // singular values below rank_eps of the largest dropped (0: off); scratch at ws + offRR
+  double rank_eps;
+  int64_t offRR;
   // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
@@ -192,6 +196,13 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
                                int ldir = -1);
 // Digit planes of the potential factors: one CTA per (direction, rank term), max_rt3 = 3 R_tot.
 cudaError_t launch_vslices(const SysDev *sys, int nsys, int max_rt3, cudaStream_t st);
+// Rank reduction (k_rank.cu), one CTA per system with rank_eps > 0, after the transverse Grams
+// and before the direction-0 Gram: rewrites the direction-0 potential rows, the transverse
+// factors, the rank coefficients and Rt of the device descriptor.  Its scratch header holds
+// [R_tot, r1, s_r1 (largest dropped singular value), s_0].  R_tot <= kRankReduceMaxRt.
+constexpr int kRankReduceMaxRt = 64;
+size_t rank_reduce_smem_bytes(int R, int nv);
+cudaError_t launch_rank_reduce(SysDev *sys, int nsys, size_t smem, cudaStream_t st);
 // The window blocks outside cw0 .. cw0 + Jc - 1 from their mirrors (thread per element).
 cudaError_t launch_gram_mirror(const SysDev *sys, int nsys, long long max_items, cudaStream_t st);
 // Tensor-core contraction of the digit planes (tcgen05), one job per (system, direction, 128-row

@@ -120,6 +120,9 @@ def load():
             "lhf_eig_counters": (st, [ctx, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
             "lhf_box_lowest_eigenvalues": (st, [ctx, S, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+            "lhf_set_rank_reduction": (st, [ctx, ctypes.c_double]),
+            "lhf_rank_reduction_info": (st, [ctx, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "lhf_set_wait_limit": (st, [ctx, ctypes.c_longlong]),
             "lhf_inject_barrier_stall": (st, [ctx]),
             "lhf_set_workspace_limit": (st, [ctx, ctypes.c_size_t]),
@@ -421,6 +424,19 @@ class Context:
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(self.lib.lhf_launch_shapes(self._h, ctypes.byref(a), ctypes.byref(b)))
         return {"eig_warps": a.value, "tri_threads": b.value}
+
+    def set_rank_reduction(self, eps: float):
+        """Rank reduction of the direction-0 potential of (L,1,1) lattices (FP64 route); 0: off."""
+        self._check(self.lib.lhf_set_rank_reduction(self._h, float(eps)))
+
+    def rank_reduction_info(self) -> dict:
+        """R_tot, the reduced rank r1, the largest dropped and the largest singular value for the
+        current setup system."""
+        ri, ro = ctypes.c_int(0), ctypes.c_int(0)
+        dr, lg = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        self._check(self.lib.lhf_rank_reduction_info(self._h, ctypes.byref(ri), ctypes.byref(ro), ctypes.byref(dr),
+                                                     ctypes.byref(lg)))
+        return {"rank_in": ri.value, "rank_out": ro.value, "dropped": dr.value, "largest": lg.value}
 
     def set_wait_limit(self, cycles: int):
         """Bound (SM clock cycles) of the dense eigensolver's grid-barrier waits; <= 0: default."""
