@@ -381,6 +381,19 @@ lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned l
 lhf_status lhf_set_rank_reduction(lhf_ctx *ctx, double eps);
 lhf_status lhf_rank_reduction_info(lhf_ctx *ctx, int *rank_in, int *rank_out, double *dropped, double *largest);
 
+/* Extrapolation of the lattice sum to the limit (the regularisation of Sec. 4.1: the nuclear lattice
+ * sum converges only conditionally and is extrapolated over a sequence of lattice parameters).
+ * eig: device [nK][n], the same n spectral values of one lattice computed with nK image windows
+ * K[k] (host [nK], distinct, >= 1; e.g. lhf_bloch_spectra of copies of the system differing only
+ * in K_sum[0]); each value is fitted to lambda(K) = A + B ln K + C / K (least squares; nK = 2
+ * fits A + B ln K).  eig_limit: device [n] the finite parts A; slope: device [n] the coefficients
+ * B (may be NULL).  For an (L,1,1) chain the far images shift every eigenvalue by
+ * -(2 Z_cell / b) sum_k 1/k, so B tends to -2 Z_cell / b (Z_cell the charge per cell) and A is the
+ * regularised eigenvalue.  Non-finite inputs (removed functions) stay non-finite.  2 <= nK <= 8.
+ * Asynchronous on the context stream; uses the first nK doubles of the context workspace. */
+lhf_status lhf_extrapolate_lattice_sum(lhf_ctx *ctx, int nK, const double *K, long long n, const double *eig,
+                                       double *eig_limit, double *slope);
+
 /* Failure detection (no counterpart in the paper: controls of this library's own error paths).
  * lhf_set_wait_limit: the bound, in SM clock cycles, of every wait at a grid barrier of the dense
  *   eigensolver (lhf_dense_eigensolve and the open-box path); cycles <= 0 restores the default

@@ -89,7 +89,62 @@ __global__ void __launch_bounds__(kSelThreads) k_cell_energy(const double *__res
   }
 }
 
+// Extrapolation of the lattice sum to the limit (the regularisation of Sec. 4.1): spectra of one
+// lattice computed with nK image windows K_k, fitted per value to
+//   lambda(K) = A + B ln K + C / K
+// (least squares through the normal equations; two windows fit A + B ln K), thread per value.
+// For a chain the far images add a potential that is constant over the cell, -(2 Z / b) sum 1/k,
+// so B tends to -2 Z_cell / b and A is the finite part.  Non-finite inputs give non-finite output.
+__global__ void k_lattice_extrapolate(const double *__restrict__ eig, const double *__restrict__ K, int nK, int64_t n,
+                                      double *A, double *B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double y[kMaxExtrapolationWindows];
+  bool fin = true;
+  for (int k = 0; k < nK; ++k) {
+    y[k] = eig[(int64_t)k * n + i];
+    if (!isfinite(y[k])) fin = false;
+  }
+  if (!fin) {
+    A[i] = y[0] + y[nK - 1];  // inf or NaN, as the inputs
+    if (B) B[i] = A[i];
+    return;
+  }
+  const int nb = nK >= 3 ? 3 : 2;
+  double M[3][3] = {{0.0}}, r[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < nK; ++k) {
+    const double x[3] = {1.0, log(K[k]), 1.0 / K[k]};
+    for (int a = 0; a < nb; ++a) {
+      r[a] += x[a] * y[k];
+      for (int b = 0; b < nb; ++b) M[a][b] += x[a] * x[b];
+    }
+  }
+  double a0, b0;
+  if (nb == 2) {
+    const double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    a0 = (r[0] * M[1][1] - M[0][1] * r[1]) / det;
+    b0 = (M[0][0] * r[1] - M[1][0] * r[0]) / det;
+  } else {
+    const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                       M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                       M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    a0 = (r[0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (r[1] * M[2][2] - M[1][2] * r[2]) +
+          M[0][2] * (r[1] * M[2][1] - M[1][1] * r[2])) / det;
+    b0 = (M[0][0] * (r[1] * M[2][2] - M[1][2] * r[2]) - r[0] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+          M[0][2] * (M[1][0] * r[2] - r[1] * M[2][0])) / det;
+  }
+  A[i] = a0;
+  if (B) B[i] = b0;
+}
+
 }  // namespace
+
+cudaError_t launch_lattice_extrapolate(const double *eig, const double *K, int nK, long long n, double *A, double *B,
+                                       cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_lattice_extrapolate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(eig, K, nK, n, A, B);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cell_energy(const double *eig, const SpectrumSeg *seg, int nseg, double *energy, double *level,
                                cudaStream_t st) {

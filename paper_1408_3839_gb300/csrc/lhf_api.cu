@@ -1112,6 +1112,25 @@ lhf_status lhf_rank_reduction_info(lhf_ctx *c, int *rank_in, int *rank_out, doub
   return LHF_OK;
 }
 
+lhf_status lhf_extrapolate_lattice_sum(lhf_ctx *c, int nK, const double *K, long long n, const double *eig,
+                                       double *eig_limit, double *slope) {
+  if (!c) return LHF_ERR_ARG;
+  if (nK < 2 || nK > lhf::kMaxExtrapolationWindows || !K || !eig || !eig_limit || n < 0)
+    return c->fail(LHF_ERR_ARG, "nK in [2, %d], K, eig and eig_limit are required", lhf::kMaxExtrapolationWindows);
+  for (int k = 0; k < nK; ++k) {
+    if (!(K[k] >= 1.0) || !std::isfinite(K[k])) return c->fail(LHF_ERR_ARG, "K[%d] = %g must be >= 1", k, K[k]);
+    for (int q = 0; q < k; ++q)
+      if (K[q] == K[k]) return c->fail(LHF_ERR_ARG, "K values must differ");
+  }
+  // the windows into the workspace (pinned staging is not needed for nK doubles: a pageable
+  // source is staged before cudaMemcpyAsync returns)
+  lhf_status st = ensure_ws(c, 32);
+  if (st != LHF_OK) return st;
+  st = c->cuda(cudaMemcpyAsync(c->ws, K, nK * sizeof(double), cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync");
+  if (st != LHF_OK) return st;
+  return c->cuda(lhf::launch_lattice_extrapolate(eig, c->ws, nK, n, eig_limit, slope, c->stream), "extrapolation kernel");
+}
+
 lhf_status lhf_set_wait_limit(lhf_ctx *c, long long cycles) {
   if (!c) return LHF_ERR_ARG;
   c->wait_cycles = cycles > 0 ? cycles : lhf::kDefaultWaitCycles;

@@ -272,6 +272,10 @@ struct SpectrumSeg {
 // the n_low-th smallest value.  seg: device array [nseg].
 cudaError_t launch_cell_energy(const double *eig, const SpectrumSeg *seg, int nseg, double *energy, double *level,
                                cudaStream_t st);
+// Lattice-sum extrapolation: eig [nK][n] (device), K device [nK] (2 <= nK <= 8); A, B [n] (B may be null).
+constexpr int kMaxExtrapolationWindows = 8;
+cudaError_t launch_lattice_extrapolate(const double *eig, const double *K, int nK, long long n, double *A, double *B,
+                                       cudaStream_t st);
 // Open box: direction-0 factors (one CTA per (d, mu, nu), max_width = widest product row) and
 // the dense matrices (thread per entry).
 size_t box_gram_smem_bytes(int max_width);

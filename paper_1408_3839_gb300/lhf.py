@@ -123,6 +123,8 @@ def load():
             "lhf_set_rank_reduction": (st, [ctx, ctypes.c_double]),
             "lhf_rank_reduction_info": (st, [ctx, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+            "lhf_extrapolate_lattice_sum": (st, [ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_longlong,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
             "lhf_set_wait_limit": (st, [ctx, ctypes.c_longlong]),
             "lhf_inject_barrier_stall": (st, [ctx]),
             "lhf_set_workspace_limit": (st, [ctx, ctypes.c_size_t]),
@@ -437,6 +439,13 @@ class Context:
         self._check(self.lib.lhf_rank_reduction_info(self._h, ctypes.byref(ri), ctypes.byref(ro), ctypes.byref(dr),
                                                      ctypes.byref(lg)))
         return {"rank_in": ri.value, "rank_out": ro.value, "dropped": dr.value, "largest": lg.value}
+
+    def extrapolate_lattice_sum(self, K, eig, eig_limit, slope=None):
+        """lhf_extrapolate_lattice_sum: eig device [len(K)][n] -> eig_limit (and slope) device [n]."""
+        Karr = (ctypes.c_double * len(K))(*[float(v) for v in K])
+        n = eig_limit.numel() if hasattr(eig_limit, "numel") else int(eig_limit)
+        self._check(self.lib.lhf_extrapolate_lattice_sum(self._h, len(K), Karr, int(n), _ptr(eig), _ptr(eig_limit),
+                                                         _ptr(slope)))
 
     def set_wait_limit(self, cycles: int):
         """Bound (SM clock cycles) of the dense eigensolver's grid-barrier waits; <= 0: default."""
