@@ -7,9 +7,10 @@ sinc terms, K_sum = 256 images), each taken through the whole path in one batche
 basis samples -> potential factors -> weighted 1D Grams -> rank sum -> block DFT -> k-point
 eigensolves.  One Bloch spectrum = all 256 x 16 = 4096 eigenvalues of one system.
 
-value: systems/s with the system descriptors on the host and every intermediate on the device
-       (device-timed with CUDA events on the launching stream; the per-step working set,
-       ~13 MB per system, is far larger than L2), for --precision (default mixed: the Gram
+value: systems/s with every input and intermediate on the device, the whole path captured once
+       in a CUDA graph and replayed every step (device-timed with CUDA events on the launching
+       stream; the per-step working set, ~13 MB per system, is far larger than L2; the direct
+       lhf_bloch_spectra calls are timed beside it), for --precision (default mixed: the Gram
        contractions on tensor cores through exact BF16 digit slices); the other route (FP64
        CUDA-core Grams) is timed beside it and reported with the ratio of the two.
 e2e:   the same through lhf_bloch_spectra_host: descriptor upload and the copy of all
@@ -385,7 +386,7 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
-def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None, profile=False):
+def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None, profile=False, graph=None):
     """Device time (ms, max over ranks) of `steps` batched passes.  With profile, every stage and
     every kernel launch is also bracketed by CUDA events on the launching stream (live stage and
     kernel times; the extra event records cost a few percent of the step, so the headline
@@ -407,7 +408,10 @@ def timed_steps(ctx, cfgs, eig, kst, precision, steps, stream, dist, clocks=None
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(steps):
-        ctx.bloch_spectra(cfgs, eig, kst, precision)
+        if graph is not None:
+            graph.launch()
+        else:
+            ctx.bloch_spectra(cfgs, eig, kst, precision)
     t_end.record(stream)
     torch.cuda.synchronize()
     if clocks:
@@ -722,8 +726,14 @@ def run_gpu(args):
     ms_other, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
     _, stages_other, kernels_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist,
                                                           profile=True)
+    # the headline: the whole path captured once in a CUDA graph and replayed every step (each replay
+    # recomputes every stage of every system); the direct calls are timed beside it
+    ms_direct, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist)
+    graph = ctx.graph_create(cfgs, eig, kst, precision)
+    for _ in range(max(args.warmup, 0)):
+        graph.launch()
     clocks = ClockSampler(local)
-    ms, _, _, _, _, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks)
+    ms, _, _, _, _, ck = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist, clocks, graph=graph)
     # the same steps again with live stage and kernel timing (the rooflines' denominators)
     ms_prof, stages, kernels, passes, mats, _ = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream,
                                                             dist, profile=True)
@@ -809,6 +819,9 @@ def run_gpu(args):
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                         for k, v in kernels_other.items() if v[1]}},
         "mixed_over_fp64": (value / value_other) if precision == lhf.MIXED else (value_other / value),
+        "direct_calls": {"value": total_systems / (ms_direct / 1e3), "unit": UNIT,
+                         "ms_per_step": ms_direct / args.steps,
+                         "note": "the same steps through lhf_bloch_spectra calls instead of graph replays"},
         "stages": stage_summary,
         "profiled_ms_per_step": ms_prof / args.steps,
         "eig_tridiag_passes_per_matrix": passes / max(mats, 1),
@@ -840,6 +853,7 @@ def run_gpu(args):
                                 "single_thread": {"value": 1.0 / per_sys, "unit": UNIT, "s_per_system": per_sys}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    graph.close()
     ctx.close()
     if dist:
         dist.destroy_process_group()

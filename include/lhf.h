@@ -276,8 +276,10 @@ lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *syst
  * lhf_graph_launch on the context stream (one graph launch instead of a dozen kernel launches
  * and no host work per replay).  The graph owns its workspace and descriptors; every replay
  * recomputes the same systems into the same eig / k_status device buffers (which must outlive
- * the graph).  Periodic lattices only (LHF_ERR_UNSUPPORTED for open boxes).  The graph must be
- * destroyed before its context; lhf_graph_destroy waits for the context stream. */
+ * the graph).  Periodic lattices only (LHF_ERR_UNSUPPORTED for open boxes).  Destroy the graph
+ * before its context when possible (lhf_graph_destroy then waits for the context stream); a
+ * context destroyed first detaches its graphs: lhf_graph_launch on them returns LHF_ERR_STATE and
+ * lhf_graph_destroy still frees them (after a device-wide synchronisation). */
 typedef struct lhf_graph lhf_graph;
 lhf_status lhf_graph_create(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems, lhf_precision precision,
                             double *eig, int *k_status, lhf_graph **out);
@@ -368,16 +370,16 @@ lhf_status lhf_eig_counters(lhf_ctx *ctx, unsigned long long *passes, unsigned l
  * (L,1,1) lattices on the FP64 route.  The nuclear part of a block is a sum over R_tot = M0 R rank
  * terms, V_j = sum_r <Q_j, v_r> T_r (v_r the direction-0 factor over one cell, Q_j the cell fold of
  * the product row, T_r = c_r C1_r (.) C2_r the single-cell transverse factors).  With weights
- * w_r = max |T_r|, the truncated SVD of the weighted factor rows, v_r w_r = sum_a Y_ra s_a u_a,
- * keeps the s_a > eps s_0 and replaces the sum by r1 terms, V_j ~ sum_a <Q_j, u_a> D_a with
- * D_a = s_a sum_r Y_ra T_r / w_r; every entry of V_j then moves by at most
- * s_r1 ||Q_j,mu,nu||_2 ||(T_r[mu][nu] / w_r)_r||_2 <= s_r1 ||Q_j,mu,nu||_2 sqrt(R_tot), s_r1 the
- * largest dropped singular value.  The direction-0 Gram and the rank sum then run over r1 terms.
- * lhf_set_rank_reduction: eps in (0, 1) turns it on for the context's later FP64 assemblies and
+ * w_r = max |T_r|, a rank-revealing (pivoted, reorthogonalised) Gram-Schmidt of the weighted
+ * factor rows a_r = v_r w_r stops once every residual row is at most eps times the first pivot,
+ * a_r = sum_k R_rk q_k + res_r with ||res_r|| <= rho, and the sum becomes r1 terms,
+ * V_j ~ sum_k <Q_j, q_k> D_k with D_k = sum_r R_rk T_r / w_r; every entry of V_j then moves by at
+ * most rho ||Q_j,mu,nu||_2 R_tot.  The direction-0 Gram and the rank sum then run over r1 terms.
+ * lhf_set_rank_reduction: eps in [1e-14, 1) turns it on for the context's later FP64 assemblies and
  * spectra of such lattices with R_tot <= 64 (other systems, the mixed route and graphs are
  * unaffected); 0 turns it off.  lhf_rank_reduction_info: for the current setup system (reduction
- * on), runs the factor stages and returns R_tot, r1, s_r1 and s_0 (host outputs, each optional;
- * synchronising). */
+ * on), runs the factor stages and returns R_tot, r1, rho and the first pivot (host outputs, each optional;
+ * synchronising): "dropped" is rho, "largest" the first pivot's norm. */
 lhf_status lhf_set_rank_reduction(lhf_ctx *ctx, double eps);
 lhf_status lhf_rank_reduction_info(lhf_ctx *ctx, int *rank_in, int *rank_out, double *dropped, double *largest);
 

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -97,6 +98,8 @@ struct lhf_ctx {
   int graph_tc_jobs = 0;
   size_t graph_tc_off = 0;
   std::vector<int> host_L;
+  // graphs created from this context (detached, not freed, when the context is destroyed first)
+  std::set<lhf_graph *> graphs;
   // failure detection: bound of the dense solver's grid-barrier waits, a one-shot injected
   // barrier stall (test), and a cap on the workspace bytes (0: none)
   double rank_eps = 0.0;  // rank reduction of one-dimensional lattices (FP64 route); 0: off
@@ -1029,6 +1032,7 @@ void lhf_destroy(lhf_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (lhf_graph *g : c->graphs) g->ctx = nullptr;  // their owners still free them
   if (c->ws) cudaFree(c->ws);
   if (c->d_sys) cudaFree(c->d_sys);
   if (c->h_sys) cudaFreeHost(c->h_sys);
@@ -1081,7 +1085,7 @@ lhf_status lhf_launch_shapes(lhf_ctx *c, int *eig_warps, int *tri_threads) {
 
 lhf_status lhf_set_rank_reduction(lhf_ctx *c, double eps) {
   if (!c) return LHF_ERR_ARG;
-  if (!(eps >= 0.0) || eps >= 1.0) return c->fail(LHF_ERR_ARG, "eps = %g outside [0, 1)", eps);
+  if (!(eps == 0.0 || (eps >= 1e-14 && eps < 1.0))) return c->fail(LHF_ERR_ARG, "eps = %g: 0 or in [1e-14, 1)", eps);
   c->rank_eps = eps;
   return LHF_OK;
 }
@@ -1743,6 +1747,7 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
   lhf_graph *g = new (std::nothrow) lhf_graph();
   if (!g) return c->fail(LHF_ERR_NOMEM, "graph");
   g->ctx = c;
+  c->graphs.insert(g);
   auto cleanup = [&](lhf_status s) {
     lhf_graph_destroy(g);
     return s;
@@ -1824,12 +1829,18 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
 
 lhf_status lhf_graph_launch(lhf_graph *g) {
   if (!g || !g->exec) return LHF_ERR_ARG;
+  if (!g->ctx) return LHF_ERR_STATE;  // its context was destroyed
   return g->ctx->cuda(cudaGraphLaunch(g->exec, g->ctx->stream), "cudaGraphLaunch");
 }
 
 void lhf_graph_destroy(lhf_graph *g) {
   if (!g) return;
-  if (g->ctx) cudaStreamSynchronize(g->ctx->stream);
+  if (g->ctx) {
+    cudaStreamSynchronize(g->ctx->stream);
+    g->ctx->graphs.erase(g);
+  } else {
+    cudaDeviceSynchronize();  // detached: its context (and stream) are gone
+  }
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->tc_dev) cudaFree(g->tc_dev);

@@ -199,7 +199,8 @@ cudaError_t launch_vslices(const SysDev *sys, int nsys, int max_rt3, cudaStream_
 // Rank reduction (k_rank.cu), one CTA per system with rank_eps > 0, after the transverse Grams
 // and before the direction-0 Gram: rewrites the direction-0 potential rows, the transverse
 // factors, the rank coefficients and Rt of the device descriptor.  Its scratch header holds
-// [R_tot, r1, s_r1 (largest dropped singular value), s_0].  R_tot <= kRankReduceMaxRt.
+// [R_tot, r1, rho (largest residual row norm left out), the first pivot's norm].
+// R_tot <= kRankReduceMaxRt.
 constexpr int kRankReduceMaxRt = 64;
 size_t rank_reduce_smem_bytes(int R, int nv);
 cudaError_t launch_rank_reduce(SysDev *sys, int nsys, size_t smem, cudaStream_t st);

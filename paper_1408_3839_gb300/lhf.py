@@ -508,7 +508,10 @@ class Graph:
         self._keep = keep  # the output buffers the graph writes
 
     def launch(self):
-        self._ctx._check(self._ctx.lib.lhf_graph_launch(self._h))
+        st = self._ctx.lib.lhf_graph_launch(self._h)
+        if st != LHF_OK and not self._ctx._h:
+            raise LhfError(st, "the graph's context was destroyed")
+        self._ctx._check(st)
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -148,3 +148,22 @@ def test_full_hetero_batch_runs_and_matches_single_runs_on_samples(ctx):
         assert np.array_equal(g_eig.cpu().numpy(), got)
     finally:
         g.close()
+
+
+def test_graph_outliving_its_context(lhf):
+    # a context destroyed before its graph detaches it: the graph refuses to launch (no stream to
+    # launch on) and is still freed cleanly
+    c = lhf.Context(0)
+    cfg = W.periodic_8()
+    c.setup(cfg)
+    sz = c.query_sizes()
+    eig = torch.empty((sz["n_kpoints"], sz["m0"]), dtype=torch.float64, device="cuda")
+    g = c.graph_create([cfg], eig, None, lhf.FP64)
+    g.launch()
+    c.sync()
+    c.close()
+    with pytest.raises(lhf.LhfError) as ei:
+        g.launch()
+    assert ei.value.status == lhf.LHF_ERR_STATE
+    g.close()
+    torch.cuda.synchronize()

@@ -1,7 +1,8 @@
 """Rank reduction of the lattice-summed potential (lhf_set_rank_reduction, FP64 route, (L,1,1)
 lattices): the reduced blocks against the oracle's unreduced blocks within the stated per-entry
-bound s_r1 ||Q_j,mu,nu||_2 sqrt(R_tot) (s_r1 the largest dropped singular value, Q the cell fold
-of the product row, computed here from the oracle's basis samples) plus FP64 rounding; overlap
+bound rho ||Q_j,mu,nu||_2 R_tot (rho the largest residual row norm the pivoted Gram-Schmidt
+leaves out, Q the cell fold of the product row, computed here from the oracle's basis samples)
+plus FP64 rounding; overlap
 blocks unchanged; the reduced rank reported; spectra of the full-size tube; the mixed route and
 graphs unaffected."""
 
@@ -84,7 +85,7 @@ def test_reduced_blocks_within_the_stated_bound(lhf, oracle_mod, name, eps):
     assert 1 <= info["rank_out"] < info["rank_in"]
     assert info["dropped"] <= eps * info["largest"]
     assert block_rel_err(S, Sr, m0) <= 1e-12  # the overlap does not involve the potential
-    bound = info["dropped"] * _fold_norms(oracle_mod, cfg) * np.sqrt(info["rank_in"])
+    bound = info["dropped"] * _fold_norms(oracle_mod, cfg) * info["rank_in"]
     noise = 1e-12 * np.abs(Hr).reshape(len(Hr), -1).max(axis=1)[:, None, None]
     err = np.abs(H - Hr)
     assert np.all(err <= bound + noise), float((err - bound - noise).max())
