@@ -610,3 +610,23 @@ def test_mixed_gram_factors_full_size_tube_256(ctx, lhf):
     ctx.sync()
     assert block_rel_err(Hmx.cpu().numpy(), H64.cpu().numpy(), m0) <= 1e-12
     assert np.array_equal(Smx.cpu().numpy(), S64.cpu().numpy())
+
+
+@pytest.mark.slow
+def test_mixed_route_full_size_tube_256_spectrum_against_oracle(ctx, oracle_mod, lhf):
+    """The benchmark system on the benchmark route (tensor-core Grams through the exact digit
+    split) end to end against the oracle: the same removed functions and every eigenvalue within
+    the perturbation bound (the mixed route's target is 1e-6 Ha; its split is exact to 2^-46)."""
+    cfg = W.tube_256(3000)
+    ctx.setup(cfg)
+    eig = dev((256, 16))
+    ks = dev((256,), torch.int32)
+    ctx.bloch_spectra([cfg], eig, ks, lhf.MIXED)
+    ctx.sync()
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    Hb, Sb = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, st = oracle_mod.k_point_eigenvalues(Hb, Sb)
+    assert np.array_equal(ks.cpu().numpy(), st)
+    got = eig.cpu().numpy()
+    worst, ratio = check_eigenvalues(got, ref, Hb, Sb, Hr, Sr, status=st)
+    assert ratio <= 1.0 and worst <= 1e-6, (worst, ratio)
