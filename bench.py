@@ -719,13 +719,16 @@ def run_gpu(args):
     # FP64 route beside the mixed one (the metric compares the two); the main line is
     # args.precision, timed last
     other = lhf.FP64 if precision == lhf.MIXED else lhf.MIXED
-    for prec in (other, precision):
+    for prec in ((precision,) if args.only_main else (other, precision)):
         for _ in range(max(args.warmup, 0)):
             ctx.bloch_spectra(cfgs, eig, kst, prec)
     torch.cuda.synchronize()
-    ms_other, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
-    _, stages_other, kernels_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist,
-                                                          profile=True)
+    if args.only_main:  # profiling runs: the main route alone
+        ms_other, stages_other, kernels_other = float("nan"), {}, {}
+    else:
+        ms_other, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist)
+        _, stages_other, kernels_other, _, _, _ = timed_steps(ctx, cfgs, eig, kst, other, args.steps, stream, dist,
+                                                              profile=True)
     # the headline: the whole path captured once in a CUDA graph and replayed every step (each replay
     # recomputes every stage of every system); the direct calls are timed beside it
     ms_direct, _, _, _, _, _ = timed_steps(ctx, cfgs, eig, kst, precision, args.steps, stream, dist)
@@ -871,6 +874,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads (box, cube, batch)")
     ap.add_argument("--oracle-table", action="store_true", help="time the CPU oracle per workload and exit")
+    ap.add_argument("--only-main", action="store_true",
+                    help="skip the other Gram route timed beside the main one (for profiling captures)")
     args = ap.parse_args()
     if args.oracle_table:
         return oracle_table(args)

@@ -46,11 +46,15 @@ typedef enum {
     LHF_ERR_NOT_CONVERGED = -8 /* an iterative solver stopped above its tolerance */
 } lhf_status;
 
-/* Arithmetic of the weighted Gram contractions (steps a3-a4).  Everything else (potential
- * factors, rank sum, DFT, eigensolves) is FP64 in both modes.
- *   LHF_FP64:   FP64 CUDA-core contraction.
- *   LHF_MIXED:  tensor-core contraction (tcgen05) on BF16 slices of the FP64 operands with
- *               exact FP32 accumulation per slice pair, recombined in FP64. */
+/* Arithmetic route.  Potential factors, rank sum and DFT are FP64 in both modes.
+ *   LHF_FP64:   FP64 CUDA-core Gram contraction; FP64 k-point reduction.
+ *   LHF_MIXED:  tensor-core Gram contraction (tcgen05) on BF16 slices of the FP64 operands with
+ *               exact FP32 accumulation per slice pair, recombined in FP64; the k-point
+ *               reduction of the Cholesky route (Cholesky, triangular solves, Householder) in
+ *               compensated pairs of FP32 words (48 significant bits, compensated dot products),
+ *               the canonical route, Jacobi and the tridiagonal eigenvalues in FP64.  Target:
+ *               eigenvalues within 1e-6 Ha of the FP64 ones (measured: within the FP64 route's
+ *               perturbation bound, 3.5e-11 Ha on the benchmark system). */
 typedef enum { LHF_FP64 = 0, LHF_MIXED = 1 } lhf_precision;
 
 typedef struct lhf_ctx lhf_ctx;

@@ -333,6 +333,322 @@ __device__ void hermitian_part(double2 *A, int m, const Grp<G> &g) {
   g.sync();
 }
 
+// ---- compensated FP32 pairs for the mixed route's reduction ---------------------------------
+// GB300 runs FP64 at 1/64 of the FP32 rate and charges the FP64 unit per warp instruction, so
+// the mixed route (whose eigenvalue target is 1e-6 Ha) takes the Cholesky-route reduction --
+// Cholesky, the two triangular solves, Householder -- in pairs of FP32 words: a real value is
+// h + l with |l| <= ulp(h) / 2 (48 significant bits), a complex entry a float4 {re_h, re_l, im_h,
+// im_l} in the 16 bytes of the double2 it replaces.  Sums of products are compensated dot
+// products (Ogita, Rump and Oishi 2005): each product's rounding error comes from an FMA, each
+// sum's from Knuth's TwoSum, and both are gathered in a second FP32 word, so that a sum of n
+// products is as accurate as if computed with twice the FP32 precision.  Square roots and
+// reciprocals take the FP32 approximation and one Newton step in pair arithmetic.  __fadd_rn and
+// __fmul_rn keep the compiler from contracting the error-free transforms into FMAs.
+struct Cacc {
+  float rs, rc, is, ic;  // real part rs + rc, imaginary part is + ic
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float v = __fadd_rn(s, -a);
+  e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -v)), __fadd_rn(b, -v));
+}
+// s + c += (xh + xl)(yh + yl)
+__device__ __forceinline__ void acc_prod(float &s, float &c, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float q = fmaf(xh, yh, -p);
+  q = fmaf(xh, yl, q);
+  q = fmaf(xl, yh, q);
+  float t, e;
+  two_sum(s, p, t, e);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, q));
+}
+// s + c += xh + xl
+__device__ __forceinline__ void acc_add(float &s, float &c, float xh, float xl) {
+  float t, e;
+  two_sum(s, xh, t, e);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, xl));
+}
+__device__ __forceinline__ float2 df_norm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  return make_float2(h, __fadd_rn(c, -__fadd_rn(h, -s)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float q = fmaf(a.x, b.x, -p);
+  q = fmaf(a.x, b.y, q);
+  q = fmaf(a.y, b.x, q);
+  return df_norm(p, q);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// 1 / a, 1 / sqrt(a), sqrt(a): the FP32 value and one Newton step in pair arithmetic
+__device__ __forceinline__ float2 df_recip(float2 a) {
+  const float h = __frcp_rn(a.x);
+  const float2 e = df_add(make_float2(1.0f, 0.0f), df_mul(make_float2(-h, 0.0f), a));  // 1 - h a
+  return df_norm(h, __fmul_rn(h, e.x));
+}
+__device__ __forceinline__ float2 df_rsqrt(float2 a) {
+  const float h = rsqrtf(a.x);
+  const float2 e = df_add(make_float2(1.0f, 0.0f), df_neg(df_mul(a, df_mul(make_float2(h, 0.0f), make_float2(h, 0.0f)))));
+  return df_norm(h, __fmul_rn(0.5f * h, e.x));  // h (1 + (1 - a h^2) / 2)
+}
+__device__ __forceinline__ float2 df_sqrt(float2 a) {
+  if (!(a.x > 0.0f)) return make_float2(0.0f, 0.0f);
+  const float h = __fsqrt_rn(a.x);
+  const float2 r = df_add(a, df_neg(df_mul(make_float2(h, 0.0f), make_float2(h, 0.0f))));  // a - h^2
+  return df_norm(h, __fdiv_rn(r.x, 2.0f * h));
+}
+__device__ __forceinline__ float4 df_from(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+__device__ __forceinline__ double2 df_to(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+__device__ __forceinline__ float2 df_real(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+// A += a b and A -= a conj(b) (complex)
+__device__ __forceinline__ void cacc_mad(Cacc &A, float4 a, float4 b) {
+  acc_prod(A.rs, A.rc, a.x, a.y, b.x, b.y);
+  acc_prod(A.rs, A.rc, -a.z, -a.w, b.z, b.w);
+  acc_prod(A.is, A.ic, a.x, a.y, b.z, b.w);
+  acc_prod(A.is, A.ic, a.z, a.w, b.x, b.y);
+}
+__device__ __forceinline__ void cacc_msub_conj(Cacc &A, float4 a, float4 b) {
+  acc_prod(A.rs, A.rc, -a.x, -a.y, b.x, b.y);
+  acc_prod(A.rs, A.rc, -a.z, -a.w, b.z, b.w);
+  acc_prod(A.is, A.ic, -a.z, -a.w, b.x, b.y);
+  acc_prod(A.is, A.ic, a.x, a.y, b.z, b.w);
+}
+__device__ __forceinline__ Cacc cacc_from(float4 v) { return Cacc{v.x, v.y, v.z, v.w}; }
+__device__ __forceinline__ float4 cacc_value(const Cacc &A) {
+  const float2 r = df_norm(A.rs, A.rc), i = df_norm(A.is, A.ic);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 df_cscale(float4 v, float2 t) {
+  const float2 r = df_mul(make_float2(v.x, v.y), t), i = df_mul(make_float2(v.z, v.w), t);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 df_conj(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+__device__ __forceinline__ float2 df_abs2(float4 v) {  // |v|^2
+  float s = 0.0f, c = 0.0f;
+  acc_prod(s, c, v.x, v.y, v.x, v.y);
+  acc_prod(s, c, v.z, v.w, v.z, v.w);
+  return df_norm(s, c);
+}
+// sum of a pair over the group's lanes (pairwise compensated)
+template <int G>
+__device__ __forceinline__ float2 df_group_sum(float2 v, const Grp<G> &g) {
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(g.mask, v.x, o), l = __shfl_xor_sync(g.mask, v.y, o);
+    v = df_add(v, make_float2(h, l));
+  }
+  return v;
+}
+
+// Hermitian part (X + X^H) / 2 in pairs.
+template <int G>
+__device__ void df_hermitian_part(float4 *A, int m, const Grp<G> &g) {
+  for (int e = g.lane; e < m * m; e += G) {
+    const int i = e / m, j = e - (e / m) * m;
+    if (i < j) {
+      const float4 x = A[i * m + j], y = A[j * m + i];
+      const float2 re = df_add(make_float2(x.x, x.y), make_float2(y.x, y.y));
+      const float2 im = df_add(make_float2(x.z, x.w), make_float2(-y.z, -y.w));
+      const float4 a = make_float4(0.5f * re.x, 0.5f * re.y, 0.5f * im.x, 0.5f * im.y);
+      A[i * m + j] = a;
+      A[j * m + i] = df_conj(a);
+    } else if (i == j) {
+      A[e].z = 0.0f;
+      A[e].w = 0.0f;
+    }
+  }
+  g.sync();
+}
+
+// Cholesky of the scaled overlap in pairs, as the FP64 loop of k_eig: the FP32 copy L32 (1 / L_jj
+// on its diagonal) and the inverse pivots sgf (pairs) for the triangular solves.  False when a
+// scaled pivot falls below kCholTol.
+template <int G>
+__device__ bool df_cholesky(float4 *B, int m, const Grp<G> &g, float2 *L32, float2 *sgf) {
+  const int lane = g.lane;
+  for (int j = 0; j < m; ++j) {
+    const float2 d = make_float2(B[j * m + j].x, B[j * m + j].y);
+    if (!(d.x + d.y >= (float)kCholTol)) return false;  // group-uniform
+    const float2 inv = df_rsqrt(d), ljj = df_mul(d, inv);
+    g.sync();
+    for (int i = j + 1 + lane; i < m; i += G) {
+      const float4 lij = df_cscale(B[i * m + j], inv);
+      B[i * m + j] = lij;
+      L32[i * m + j] = make_float2(lij.x, lij.z);
+    }
+    g.sync();
+    if (lane == 0) {
+      B[j * m + j] = make_float4(ljj.x, ljj.y, 0.0f, 0.0f);
+      sgf[j] = inv;
+      L32[j * m + j] = make_float2(inv.x, 0.0f);
+    }
+    const int n = m - j - 1;
+    for (int t = lane; t < n * (n + 1) / 2; t += G) {
+      int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int k = t - i * (i + 1) / 2;
+      const int ri = j + 1 + i, rk = j + 1 + k;
+      Cacc acc = cacc_from(B[ri * m + rk]);
+      cacc_msub_conj(acc, B[ri * m + j], B[rk * m + j]);
+      B[ri * m + rk] = cacc_value(acc);
+    }
+    g.sync();
+  }
+  return true;
+}
+
+// Forward substitution in pairs, as the FP64 pass of k_eig: columns cc < ncol of X (A for cc < m,
+// V for the identity columns m .. 2m - 1) become L^{-1} X, lanes over columns (two lanes per
+// column when 16 columns or fewer fill a whole warp).
+template <int G>
+__device__ void df_forward(float4 *A, float4 *V, const float4 *B, const float2 *sgf, int m, int ncol, const Grp<G> &g) {
+  const int lane = g.lane;
+  const int q = (G == 32 && ncol <= 16) ? 2 : 1;
+  for (int cc0 = 0; cc0 < ncol; cc0 += G / q) {
+    const int cc = cc0 + lane / q, part = lane % q;
+    const bool act = cc < ncol;
+    float4 *X = cc < m ? A : V;
+    const int c = act ? (cc < m ? cc : cc - m) : 0;
+    float4 z[kMaxM0];
+    for (int i = 0; i < m; ++i) {
+      Cacc acc{0.0f, 0.0f, 0.0f, 0.0f};
+      if (act)
+        for (int k = part; k < i; k += q) cacc_mad(acc, B[i * m + k], z[k]);
+      if (q == 2) {
+        const float rs = __shfl_xor_sync(g.mask, acc.rs, 1), rc = __shfl_xor_sync(g.mask, acc.rc, 1);
+        const float is = __shfl_xor_sync(g.mask, acc.is, 1), ic = __shfl_xor_sync(g.mask, acc.ic, 1);
+        acc_add(acc.rs, acc.rc, rs, rc);
+        acc_add(acc.is, acc.ic, is, ic);
+      }
+      const float4 xi = act ? X[i * m + c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      Cacc d = cacc_from(xi);
+      acc_add(d.rs, d.rc, -acc.rs, -acc.rc);
+      acc_add(d.is, d.ic, -acc.is, -acc.ic);
+      z[i] = df_cscale(cacc_value(d), sgf[i]);
+      if (act && part == 0) X[i * m + c] = z[i];
+    }
+  }
+  g.sync();
+}
+
+// Householder reduction to real tridiagonal form in pairs, as householder_tridiag (same steps and
+// lane layout); td, te receive the diagonal and off-diagonal in FP64.  vw: 2 x 32 pair scratch.
+template <int G>
+__device__ void df_householder_tridiag(float4 *A, int m, const Grp<G> &g, float4 *vw, double *td, double *te) {
+  const int lane = g.lane;
+  float4 *vec = vw, *wv = vw + 32;
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n = m - k - 1;
+    float4 xi = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lane < n) xi = A[(k + 1 + lane) * m + k];
+    const float2 sig = df_group_sum(df_abs2(xi), g);
+    const float4 x0 = A[(k + 1) * m + k];
+    const float2 akk = make_float2(A[k * m + k].x, A[k * m + k].y);
+    if (!(sig.x > 0.0f)) {  // column already reduced
+      if (lane == 0) {
+        td[k] = (double)akk.x + (double)akk.y;
+        te[k] = 0.0;
+      }
+      continue;
+    }
+    const float2 nrm = df_sqrt(sig);
+    const float2 a2 = df_abs2(x0);
+    const bool nz = a2.x > 0.0f;
+    const float2 ra = nz ? df_rsqrt(a2) : make_float2(0.0f, 0.0f), ax0 = df_mul(a2, ra);
+    const float2 phr = nz ? df_mul(make_float2(x0.x, x0.y), ra) : make_float2(1.0f, 0.0f);
+    const float2 phi = nz ? df_mul(make_float2(x0.z, x0.w), ra) : make_float2(0.0f, 0.0f);
+    const float2 tau = df_recip(df_add(df_mul(nrm, ax0), sig));
+    if (lane < n) {
+      if (lane == 0) {
+        const float2 r = df_add(make_float2(x0.x, x0.y), df_mul(phr, nrm));
+        const float2 i = df_add(make_float2(x0.z, x0.w), df_mul(phi, nrm));
+        vec[0] = make_float4(r.x, r.y, i.x, i.y);
+      } else {
+        vec[lane] = xi;
+      }
+    }
+    g.sync();
+    constexpr int RL = G / 16;
+    const float4 *Bt = A + (k + 1) * m + (k + 1);
+    float kps = 0.0f, kpc = 0.0f;
+    for (int r0 = 0; r0 < n; r0 += 16) {
+      const int r = r0 + lane / RL;
+      Cacc pi{0.0f, 0.0f, 0.0f, 0.0f};
+      if (r < n) {
+        for (int j = lane % RL; j < n; j += RL) {
+          const float4 b = j <= r ? Bt[r * m + j] : df_conj(Bt[j * m + r]);
+          cacc_mad(pi, b, vec[j]);
+        }
+      }
+      if (RL == 2) {
+        const float rs = __shfl_xor_sync(g.mask, pi.rs, 1), rc = __shfl_xor_sync(g.mask, pi.rc, 1);
+        const float is = __shfl_xor_sync(g.mask, pi.is, 1), ic = __shfl_xor_sync(g.mask, pi.ic, 1);
+        acc_add(pi.rs, pi.rc, rs, rc);
+        acc_add(pi.is, pi.ic, is, ic);
+      }
+      if (r < n && lane % RL == 0) {
+        const float4 p = df_cscale(cacc_value(pi), tau);
+        wv[r] = p;
+        const float4 v = vec[r];  // Re(conj(v_r) p_r)
+        acc_prod(kps, kpc, v.x, v.y, p.x, p.y);
+        acc_prod(kps, kpc, v.z, v.w, p.z, p.w);
+      }
+    }
+    const float2 kp = df_group_sum(df_norm(kps, kpc), g);
+    const float2 Kf = df_mul(make_float2(0.5f * tau.x, 0.5f * tau.y), kp);  // (tau / 2) Re(v^H p)
+    g.sync();
+    if (lane < n) {
+      const float4 v = vec[lane], w = wv[lane];
+      Cacc acc = cacc_from(w);
+      acc_prod(acc.rs, acc.rc, -Kf.x, -Kf.y, v.x, v.y);
+      acc_prod(acc.is, acc.ic, -Kf.x, -Kf.y, v.z, v.w);
+      wv[lane] = cacc_value(acc);
+    }
+    g.sync();
+    for (int t = lane; t < n * (n + 1) / 2; t += G) {
+      int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int j = t - i * (i + 1) / 2;
+      float4 &a = A[(k + 1 + i) * m + (k + 1 + j)];
+      Cacc acc = cacc_from(a);
+      cacc_msub_conj(acc, vec[i], wv[j]);
+      cacc_msub_conj(acc, wv[i], vec[j]);
+      a = cacc_value(acc);
+    }
+    if (lane == 0) {
+      td[k] = (double)akk.x + (double)akk.y;
+      te[k] = (double)nrm.x + (double)nrm.y;
+    }
+    g.sync();
+  }
+  if (lane == 0) {
+    if (m >= 2) {
+      td[m - 2] = (double)A[(m - 2) * m + (m - 2)].x + (double)A[(m - 2) * m + (m - 2)].y;
+      const double2 b = df_to(A[(m - 1) * m + (m - 2)]);
+      te[m - 2] = hypot(b.x, b.y);
+    }
+    td[m - 1] = (double)A[(m - 1) * m + (m - 1)].x + (double)A[(m - 1) * m + (m - 1)].y;
+  }
+  g.sync();
+}
+
 // Eigenvectors of the pencil at k-point kap (and, conjugated, at its partner mk) from the
 // eigenvectors W of C (columns of V after Jacobi, sorted order given by vid per lane):
 //   Cholesky route:  y = L^{-H} w (back substitution, lanes over columns), S~-orthonormal;
@@ -528,15 +844,33 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   }
   for (int o = G / 2; o > 0; o >>= 1) hf2 += __shfl_xor_sync(g.mask, hf2, o);
   g.sync();
+  // mixed route, eigenvalues only: the Cholesky-route reduction in compensated FP32 pairs (A, B
+  // and V then hold float4 pairs in the same bytes); the canonical route and Jacobi stay FP64
+  const bool dfp = s.eig_df != 0 && s.tri != nullptr && s.vecs == nullptr;
+  float4 *Af = reinterpret_cast<float4 *>(A), *Bf = reinterpret_cast<float4 *>(B), *Vf = reinterpret_cast<float4 *>(V);
+  float2 *sgf = reinterpret_cast<float2 *>(sg);  // inverse pivots as pairs (in sg's doubles)
+  bool a_df = false;                            // A holds pairs
   // the blocks are Hermitian up to the rounding of the transform: solve their Hermitian parts
-  hermitian_part(A, m, g);
-  hermitian_part(B, m, g);
+  if (dfp) {
+    for (int e = lane; e < m * m; e += G) {
+      Af[e] = df_from(A[e]);
+      Bf[e] = df_from(B[e]);
+    }
+    g.sync();
+    df_hermitian_part(Af, m, g);
+    df_hermitian_part(Bf, m, g);
+    a_df = true;
+  } else {
+    hermitian_part(A, m, g);
+    hermitian_part(B, m, g);
+  }
 
   // 1. Cholesky of the scaled overlap (lower triangle, in place in B), right-looking: column j
   //    is scaled by its pivot, then the trailing lower triangle is updated by every lane (no
   //    serial sums); a pivot below kCholTol sends the k-point to canonical orthogonalisation
   bool chol = ok;
-  for (int j = 0; chol && j < m; ++j) {
+  if (dfp && chol) chol = df_cholesky(Bf, m, g, L32, sgf);
+  for (int j = 0; !dfp && chol && j < m; ++j) {
     const double d = B[j * m + j].x;
     if (!(d >= kCholTol)) {  // warp-uniform: every lane reads the same pivot
       chol = false;
@@ -611,7 +945,53 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     }
     g.sync();
   }
-  if (ok && chol) {
+  if (ok && chol && dfp) {
+    // 2 (pairs).  The same two passes as below: W = L^{-1} H (with the identity columns m .. 2m - 1
+    // when the trace test is open), A <- W^H, C = L^{-1} A, its Hermitian part
+    if (need64)
+      for (int e = lane; e < m * m; e += G) {
+        const int i = e / m, j = e - (e / m) * m;
+        Vf[e] = make_float4(i == j ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    g.sync();
+    df_forward(Af, Vf, Bf, sgf, m, need64 ? 2 * m : m, g);
+    if (need64) {
+      double tr = 0.0;
+      for (int e = lane; e < m * m; e += G) {
+        const double2 v = df_to(Vf[e]);
+        tr += v.x * v.x + v.y * v.y;
+      }
+      for (int o = G / 2; o > 0; o >>= 1) tr += __shfl_xor_sync(g.mask, tr, o);
+      if (!(tr * kLindepTol <= 1.0)) chol = false;  // a direction may lie below kLindepTol
+    }
+    if (chol) {
+      for (int e = lane; e < m * m; e += G) {  // A <- A^H
+        const int i = e / m, j = e - (e / m) * m;
+        if (i < j) {
+          const float4 x = Af[i * m + j], y = Af[j * m + i];
+          Af[i * m + j] = df_conj(y);
+          Af[j * m + i] = df_conj(x);
+        } else if (i == j) {
+          Af[e] = df_conj(Af[e]);
+        }
+      }
+      g.sync();
+      df_forward(Af, Vf, Bf, sgf, m, m, g);
+      df_hermitian_part(Af, m, g);
+    }
+  }
+  if (ok && !chol && a_df) {
+    // the pairs' Cholesky or trace test sent the k-point to the canonical route: the scaled H
+    // again in FP64 (the canonical route gathers the overlap itself)
+    for (int e = lane; e < m * m; e += G) {
+      const int a = e / m, b = e - (e / m) * m;
+      A[e] = cscale(Hb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
+    }
+    g.sync();
+    hermitian_part(A, m, g);
+    a_df = false;
+  }
+  if (ok && chol && !dfp) {
     // 2. C = L^{-1} H L^{-H}.  When the FP32 estimate left the decision open, the first pass also
     //    solves L Z = I in FP64 in the columns m .. 2m-1 and ||Z||_F^2 decides: 1 / ||Z||_F^2 >=
     //    kLindepTol keeps the Cholesky route, otherwise the k-point goes to the canonical route.
@@ -741,7 +1121,13 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     // singular overlaps, nearly cancelled Bloch functions with large scaled entries), so such
     // k-points stay on Jacobi: tridiagonal only if ||C||_F <= 2 ||H~||_F
     double cf2 = 0.0;
-    for (int e = lane; e < m * m; e += G) cf2 += A[e].x * A[e].x + A[e].y * A[e].y;
+    if (a_df) {
+      float c2 = 0.0f;
+      for (int e = lane; e < m * m; e += G) c2 = fmaf(Af[e].x, Af[e].x, fmaf(Af[e].z, Af[e].z, c2));
+      cf2 = (double)c2;
+    } else {
+      for (int e = lane; e < m * m; e += G) cf2 += A[e].x * A[e].x + A[e].y * A[e].y;
+    }
     for (int o = G / 2; o > 0; o >>= 1) cf2 += __shfl_xor_sync(g.mask, cf2, o);
     // and only if its absolute error stays below half the 1e-10 Ha floor: m eps ||C||_F <= 5e-11
     const double cmax = 5e-11 / (m * 2.220446049250313e-16);
@@ -750,13 +1136,23 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       if (lane == 0) s.tri[(int64_t)widx * (2 * m0 + 1)] = -2.0;  // solved here
     }
   }
+  if (a_df && !tri) {  // Jacobi runs in FP64: C back from its pairs
+    for (int e = lane; e < m * m; e += G) A[e] = df_to(Af[e]);
+    g.sync();
+    a_df = false;
+  }
   if (tri) {
     // 3'. tridiagonal route: Householder reduction here, the tridiagonal eigenvalues by
     //     k_tridiag_eig (one thread per matrix); slot widx = [m | d[m0] | e[m0]]
     double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
-    if (ok && m > 0)
-      householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
-                          slot + 1 + m0);
+    if (ok && m > 0) {
+      if (a_df)
+        df_householder_tridiag(Af, m, g, reinterpret_cast<float4 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+                               slot + 1 + m0);
+      else
+        householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+                            slot + 1 + m0);
+    }
     if (lane == 0) {
       slot[0] = ok ? (double)m : -1.0;
       if (counters && ok) {

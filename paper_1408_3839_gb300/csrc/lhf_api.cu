@@ -501,6 +501,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     }
   }
   P.mixed = mixed && !box;  // the box's Grams run in FP64 in both modes
+  sd.eig_df = P.mixed ? 1 : 0;
   if (box && !dense_box) {  // banded matrices and an iterative solver (lhf_box_lowest_eigenvalues)
     P.blocks_doubles = 0;
     P.rank_items = 0;

@@ -95,6 +95,9 @@ struct SysDev {
   // singular values below rank_eps of the largest dropped (0: off); scratch at ws + offRR
   double rank_eps;
   int64_t offRR;
+  // k-point reduction (Cholesky route, then Householder) in compensated FP32 pairs instead of
+  // FP64: set for the mixed route (LHF_MIXED), whose eigenvalue target is 1e-6 Ha
+  int eig_df;
   // open box (direction 0 an open lattice): factors between cells p and p + d, d = bjlo ..
   // bjlo + bJ - 1, at ws + offCb, layout [L0][bJ][Rt+2][m0][m0]
   int bJ, bjlo;
