@@ -1515,10 +1515,14 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
 }
 
 // Lanes per matrix: half a warp when every order fits (m0 <= 16), else a whole warp.
-static inline int eig_group(int max_m0) { return max_m0 <= 16 ? 16 : 32; }
+// Lanes per matrix: half a warp up to order 16 (the FP64 scalar steps then cost one warp
+// instruction per two matrices), a whole warp otherwise or when `full` (the pair arithmetic of the
+// mixed route, whose scalar steps are FP32: a warp per matrix halves the shared memory per warp and
+// gives two lanes to each column of the triangular solves).
+static inline int eig_group(int max_m0, bool full) { return (max_m0 <= 16 && !full) ? 16 : 32; }
 
-int eig_max_warps(int max_m0) {
-  const int per_warp = 32 / eig_group(max_m0);
+int eig_max_warps(int max_m0, bool full) {
+  const int per_warp = 32 / eig_group(max_m0, full);
   int w = kEigMaxWarps;
   while (w > 1 && (size_t)w * per_warp * eig_warp_bytes(max_m0) > 227 * 1024) --w;
   return w;
@@ -1541,10 +1545,10 @@ static cudaError_t launch_k_eig(const SysDev *sys, int nsys, int max_k, int max_
 }
 
 cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                              unsigned long long *counters, cudaStream_t st, int warps) {
+                              unsigned long long *counters, cudaStream_t st, int warps, bool full) {
   if (max_k <= 0 || nsys <= 0) return cudaSuccess;
-  if (warps < 1 || warps > eig_max_warps(max_m0)) return cudaErrorInvalidValue;
-  return eig_group(max_m0) == 16 ? launch_k_eig<16>(sys, nsys, max_k, max_m0, flags, counters, st, warps)
+  if (warps < 1 || warps > eig_max_warps(max_m0, full)) return cudaErrorInvalidValue;
+  return eig_group(max_m0, full) == 16 ? launch_k_eig<16>(sys, nsys, max_k, max_m0, flags, counters, st, warps)
                                  : launch_k_eig<32>(sys, nsys, max_k, max_m0, flags, counters, st, warps);
 }
 
@@ -1565,8 +1569,9 @@ cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, u
 }
 
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                       unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps, int tri_threads) {
-  cudaError_t e = launch_eig_reduce(sys, nsys, max_k, max_m0, flags, counters, st, eig_warps);
+                       unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps, int tri_threads,
+                       bool full) {
+  cudaError_t e = launch_eig_reduce(sys, nsys, max_k, max_m0, flags, counters, st, eig_warps, full);
   if (e != cudaSuccess || !tri) return e;
   return launch_tridiag(sys, nsys, max_k, max_m0, flags, counters, st, tri_threads);
 }

@@ -876,7 +876,7 @@ lhf_status set_klist(lhf_ctx *c, SysDev &sd) {
 // k_tridiag_eig (threads per CTA) once on the uploaded batch (the overlap norms already
 // launched); both kernels rewrite the same outputs, so the trial runs leave no trace beyond
 // the time they take.  Returns the fastest pair.
-lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, std::array<int, 2> *best) {
+lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, bool full, std::array<int, 2> *best) {
   cudaEvent_t a = nullptr, b = nullptr;
   lhf_status st = c->cuda(cudaEventCreate(&a), "cudaEventCreate");
   if (st == LHF_OK) st = c->cuda(cudaEventCreate(&b), "cudaEventCreate");
@@ -891,15 +891,16 @@ lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, std::
   (*best)[0] = 4;
   (*best)[1] = 128;
   float tbest = 1e30f, t = 0.f;
-  const int wmax = lhf::eig_max_warps(max_m0);
+  const int wmax = lhf::eig_max_warps(max_m0, full);
   // a first run at the default shape warms the caches (and its output feeds the tridiagonal trials)
   if (st == LHF_OK)
     st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream,
-                                                   std::min(4, wmax)); },
+                                                   std::min(4, wmax), full); },
                &t);
   for (int w : {1, 2, 4, 8}) {
     if (st != LHF_OK || w > wmax) break;
-    st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream, w); },
+    st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream, w,
+                                                   full); },
                &t);
     if (st == LHF_OK && t < tbest) {
       tbest = t;
@@ -928,30 +929,32 @@ lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, std::
 lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps, bool tri = true) {
   int max_k = 0, max_m0 = 0;
   long long total = 0;
+  bool full = tri;  // every system on the mixed route's pair arithmetic: a warp per matrix
   for (const Plan &p : ps) {
     const int k = p.sd.klist ? p.sd.nkhalf : p.sd.nblocks;
     max_k = std::max(max_k, k);
     max_m0 = std::max(max_m0, p.sd.m0);
     total += k;
+    full = full && p.sd.eig_df != 0 && p.sd.vecs == nullptr;
   }
   int lg = 0;
   while ((1ll << (lg + 1)) <= total) ++lg;
-  const std::array<int, 3> key{max_m0, tri ? 1 : 0, lg};
-  std::array<int, 2> shape{std::min(4, lhf::eig_max_warps(max_m0)), 128};
+  const std::array<int, 3> key{max_m0, (tri ? 1 : 0) | (full ? 2 : 0), lg};
+  std::array<int, 2> shape{std::min(4, lhf::eig_max_warps(max_m0, full)), 128};
   c->begin(5);
   lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
   auto it = c->eig_tune.find(key);
   if (it != c->eig_tune.end()) {
     shape = it->second;
   } else if (st == LHF_OK && c->autotune && !c->capturing) {
-    st = tune_eig(c, (int)ps.size(), max_k, max_m0, tri, &shape);
+    st = tune_eig(c, (int)ps.size(), max_k, max_m0, tri, full, &shape);
     if (st == LHF_OK) c->eig_tune[key] = shape;
   }
   c->last_eig_warps = shape[0];
   c->last_tri_threads = shape[1];
   if (st == LHF_OK)
     st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream,
-                                 tri, shape[0], shape[1]),
+                                 tri, shape[0], shape[1], full),
                  "eigen kernel");
   c->end(tri ? 3 : 2);
   return st;

@@ -243,12 +243,13 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
 // eig_warps: k-points (warps) per CTA of k_eig, 1 .. 8; tri_threads: threads per CTA of the
 // tridiagonal kernel (a multiple of its 16 or 32 lanes per matrix, at most 256).  The two
 // kernels alone (launch_eig_reduce, launch_tridiag) serve the launch-shape autotuner.
+// full: a whole warp per matrix even up to order 16 (the mixed route's pair arithmetic).
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps = 4,
-                       int tri_threads = 128);
+                       int tri_threads = 128, bool full = false);
 cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                              unsigned long long *counters, cudaStream_t st, int warps);
-int eig_max_warps(int max_m0);  // most k_eig warps per CTA whose shared memory fits an SM
+                              unsigned long long *counters, cudaStream_t st, int warps, bool full = false);
+int eig_max_warps(int max_m0, bool full = false);  // most k_eig warps per CTA whose shared memory fits an SM
 cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                            unsigned long long *counters, cudaStream_t st, int threads);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
