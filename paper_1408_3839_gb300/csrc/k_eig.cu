@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include "lhf_internal.cuh"
+#include "lhf_pairs.cuh"
 
 namespace lhf {
 namespace {
@@ -32,9 +33,6 @@ constexpr int kEigMaxWarps = 8;  // warps (k-points) per CTA: blockDim.x / 32, s
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
-  return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) {
   return make_double2(a.x - b.x, a.y - b.y);
@@ -348,46 +346,6 @@ struct Cacc {
   float rs, rc, is, ic;  // real part rs + rc, imaginary part is + ic
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float v = __fadd_rn(s, -a);
-  e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -v)), __fadd_rn(b, -v));
-}
-// s + c += (xh + xl)(yh + yl)
-__device__ __forceinline__ void acc_prod(float &s, float &c, float xh, float xl, float yh, float yl) {
-  const float p = __fmul_rn(xh, yh);
-  float q = fmaf(xh, yh, -p);
-  q = fmaf(xh, yl, q);
-  q = fmaf(xl, yh, q);
-  float t, e;
-  two_sum(s, p, t, e);
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(e, q));
-}
-// s + c += xh + xl
-__device__ __forceinline__ void acc_add(float &s, float &c, float xh, float xl) {
-  float t, e;
-  two_sum(s, xh, t, e);
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(e, xl));
-}
-__device__ __forceinline__ float2 df_norm(float s, float c) {
-  const float h = __fadd_rn(s, c);
-  return make_float2(h, __fadd_rn(c, -__fadd_rn(h, -s)));
-}
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  float s, e;
-  two_sum(a.x, b.x, s, e);
-  return df_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
-}
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float q = fmaf(a.x, b.x, -p);
-  q = fmaf(a.x, b.y, q);
-  q = fmaf(a.y, b.x, q);
-  return df_norm(p, q);
-}
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
 // 1 / a, 1 / sqrt(a), sqrt(a): the FP32 value and one Newton step in pair arithmetic
 __device__ __forceinline__ float2 df_recip(float2 a) {
   const float h = __frcp_rn(a.x);
@@ -411,10 +369,6 @@ __device__ __forceinline__ float4 df_from(double2 v) {
 }
 __device__ __forceinline__ double2 df_to(float4 v) {
   return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
-}
-__device__ __forceinline__ float2 df_real(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - (double)h));
 }
 // A += a b and A -= a conj(b) (complex)
 __device__ __forceinline__ void cacc_mad(Cacc &A, float4 a, float4 b) {

@@ -22,6 +22,7 @@
 // the P1 sums; phase 2 contracts with the R_tot potential rows.  Deterministic: fixed-order
 // floating-point reductions, and exact integer sums (whose order does not matter).
 #include "lhf_internal.cuh"
+#include "lhf_pairs.cuh"
 
 namespace lhf {
 namespace {
@@ -137,6 +138,37 @@ __device__ __forceinline__ void write_p1_slots(const SysDev &s, const GramItem &
   Cout[(int64_t)(Rt + 1) * mm + nu] = D.h * dq - de * D.h / 6.0;
 }
 
+// Per column function nu (thread nu < m0 of a periodic direction): the cells p of g_nu's support
+// where the row function shifted by j is present, as up to two runs of consecutive cells --
+// [plo, phi] meets the row support [mlo, mhi] modulo L; unless the row support covers every
+// residue its images [mlo + kL, mhi + kL] are disjoint, and [plo, phi] (at most L cells) meets at
+// most two of them, k0 (the first that ends at or after plo) and k0 + 1 -- each run given by its
+// length and the nodes of its first cell (for c = 0) in g_nu and in the shifted row function.
+__device__ __forceinline__ void gram_runs(const SysDev &s, const GramItem &it, int (*seg)[2][3]) {
+  const DirDev &D = s.d[it.l];
+  const int m0 = s.m0, nc = D.nc, L = D.L, mu = it.mu, j = D.jlo + it.jw;
+  const int tid = threadIdx.x;
+  if (!D.periodic || tid >= m0) return;
+  const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
+  const int nu = tid;
+  const int plo = s.cell_lo[it.l][nu];
+  int phi = s.cell_hi[it.l][nu];
+  if (phi > plo + L - 1) phi = plo + L - 1;
+  int seg_lo[2] = {plo, 1}, seg_hi[2] = {phi, 0};
+  if (mhi - mlo < L - 1) {
+    const int k0 = floor_div(plo - mhi + L - 1, L);
+    seg_lo[0] = max(plo, mlo + k0 * L);
+    seg_hi[0] = min(phi, mhi + k0 * L);
+    seg_lo[1] = max(plo, mlo + (k0 + 1) * L);
+    seg_hi[1] = min(phi, mhi + (k0 + 1) * L);
+  }
+  for (int sg = 0; sg < 2; ++sg) {
+    seg[nu][sg][0] = seg_hi[sg] >= seg_lo[sg] ? seg_hi[sg] - seg_lo[sg] + 1 : 0;
+    seg[nu][sg][1] = wrap(seg_lo[sg], L) * nc;      // node of g_nu in the run's first cell
+    seg[nu][sg][2] = wrap(seg_lo[sg] - j, L) * nc;  // node of the row function shifted by j
+  }
+}
+
 // Phase 1 for one CTA: Q[nu][c] in shared memory and red[2 nu + 1] = the sum over all nodes of the
 // difference products D_i(g_mu,j) D_i(g_nu), with D_i(f) = f_i - f_(i+1) (periodic wrap; open:
 // f_(-1) = f_n = 0).  The P1 forms follow from these sums and the row sums of Q:
@@ -148,46 +180,18 @@ __device__ __forceinline__ void write_p1_slots(const SysDev &s, const GramItem &
 // reduction per function is left (two functions per butterfly).
 __device__ __forceinline__ void gram_phase1(const SysDev &s, const GramItem &it, double *Q, double *red) {
   const DirDev &D = s.d[it.l];
-  const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, L = D.L;
+  const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc;
   const int ld = nv + 1;
   const double *G = s.ws + D.offG;
   const double *Dg = s.ws + D.offD;
   const int mu = it.mu;
-  const int j = D.jlo + it.jw;
   const double *f = G + (int64_t)mu * n;
   const double *df = Dg + (int64_t)mu * n;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int kWarps = kGramThreads / 32;
-  // support of the shifted row function (cells), tested modulo L
-  const int mlo = s.cell_lo[it.l][mu] + j, mhi = s.cell_hi[it.l][mu] + j;
-  const int mspan = mhi - mlo;
   const bool periodic = D.periodic != 0;
-  // per column function nu: the cells p of g_nu's support where the shifted row function is
-  // present, as up to two runs of consecutive cells -- [plo, phi] meets the row support
-  // [mlo, mhi] modulo L; unless the row support covers every residue its images [mlo + kL,
-  // mhi + kL] are disjoint, and [plo, phi] (at most L cells) meets at most two of them, k0 (the
-  // first that ends at or after plo) and k0 + 1 -- each run given by its length and the nodes of
-  // its first cell (for c = 0) in g_nu and in the shifted row function; formed once per CTA
   __shared__ int seg[kMaxM0][2][3];  // [nu][run]: cells, first node of g_nu, first node of the row
-  if (periodic && tid < m0) {
-    const int nu = tid;
-    const int plo = s.cell_lo[it.l][nu];
-    int phi = s.cell_hi[it.l][nu];
-    if (phi > plo + L - 1) phi = plo + L - 1;
-    int seg_lo[2] = {plo, 1}, seg_hi[2] = {phi, 0};
-    if (mspan < L - 1) {
-      const int k0 = floor_div(plo - mhi + L - 1, L);
-      seg_lo[0] = max(plo, mlo + k0 * L);
-      seg_hi[0] = min(phi, mhi + k0 * L);
-      seg_lo[1] = max(plo, mlo + (k0 + 1) * L);
-      seg_hi[1] = min(phi, mhi + (k0 + 1) * L);
-    }
-    for (int sg = 0; sg < 2; ++sg) {
-      seg[nu][sg][0] = seg_hi[sg] >= seg_lo[sg] ? seg_hi[sg] - seg_lo[sg] + 1 : 0;
-      seg[nu][sg][1] = wrap(seg_lo[sg], L) * nc;      // node of g_nu in the run's first cell
-      seg[nu][sg][2] = wrap(seg_lo[sg] - j, L) * nc;  // node of the row function shifted by j
-    }
-  }
+  gram_runs(s, it, seg);
   __syncthreads();
   for (int nu0 = warp; nu0 < m0; nu0 += 2 * kWarps) {
     double es0 = 0.0, es1 = 0.0;
@@ -322,64 +326,162 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v|
   return (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
+// Nearest integer of |t| < 2^22 (the addition of 1.5 2^23 rounds to an integer).
+__device__ __forceinline__ float round_small(float t) {
+  const float m = 12582912.0f;
+  return __fadd_rn(__fadd_rn(t, m), -m);
+}
+
+// The 7 digits of x = h + l (a pair, |x| < 1) as integer-valued floats, x = sum_k a_k 2^(-7(k+1))
+// + O(2^-50): each digit the nearest integer to 128 times the remainder, decided by the
+// remainder's leading word; TwoSum folds the trailing word in before digits 2, 4 and 6 (before
+// it can reach 2^-11 of the remainder), so a_0 is in [-128, 128] and |a_k| <= 64 after it, the
+// bounds of digits7.  Every step is exact.
+__device__ __forceinline__ void digits7f(float h, float l, float *a) {
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) {
+    if (k == 2 || k == 4 || k == 6) {
+      float t, e;
+      two_sum(h, l, t, e);
+      h = t;
+      l = e;
+    }
+    const float t = __fmul_rn(h, 128.0f);
+    const float d = round_small(t);
+    a[k] = d;
+    h = __fadd_rn(t, -d);
+    l = __fmul_rn(l, 128.0f);
+  }
+}
+
+// The folded products in compensated FP32 pairs and their digit planes (tensor-core route), one
+// CTA per (system, direction, window block, mu).  GB300 issues FP64 at 1/64 of the FP32 rate, so
+// the fold runs on the pairs h + l of the samples and differences written by k_basis: each
+// product exact as a pair (an FMA gives its rounding error), the sums compensated (TwoSum), a
+// relative error of a few units of 2^-48 of sum |g_mu,j g_nu| per folded value.  Per row nu:
+//   * Q[nu][c] (pairs) in shared memory, a warp per nu, lanes over the nodes c;
+//   * the row scale e with max_c |Q| < 2^e (frexp's exponent of the largest |h| + |l|);
+//   * the P1 slots from the compensated sums over the nodes of Q and of the difference products:
+//     stiffness (1/h) sum D D and mass h sum f g - (h/6) sum D D, in pairs (the factors 1/h, h,
+//     h/6 as pairs from the host), converted to FP64 once;
+//   * the 7 digit planes of Q 2^-e (digits7f), two adjacent nodes per thread and store, in the
+//     chunk-major layout of digits7 (c >= n_v: zero).
 __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   GramItem it;
   if (!decode_gram(s, blockIdx.x, it, ldir)) return;
   const DirDev &D = s.d[it.l];
-  const int m0 = s.m0, nv = D.nv, Kp = D.Kpad;
+  const int m0 = s.m0, nv = D.nv, n = D.n, nc = D.nc, Kp = D.Kpad, Rt = s.Rt, mm = m0 * m0;
   const int ld = nv + 1;
-  extern __shared__ double sm[];
-  double *Q = sm;
-  double *red = Q + m0 * ld;
+  const bool periodic = D.periodic != 0;
+  extern __shared__ float2 Qp[];  // [m0][ld] folded products as pairs
+  __shared__ int seg[kMaxM0][2][3];
   __shared__ int rexp[kMaxM0];
-  __shared__ unsigned long long qsum[kMaxM0];  // exact fixed-point row sums of Q (two's complement)
-  gram_phase1(s, it, Q, red);
-  const int tid = threadIdx.x, lane = tid & 31;
-  q_row_exponents(Q, ld, m0, nv, rexp);
-  if (tid < m0) qsum[tid] = 0ull;
+  __shared__ float2 qsum[kMaxM0], esum[kMaxM0];
+  gram_runs(s, it, seg);
   __syncthreads();
-  const int64_t rows = (int64_t)D.Jc * m0 * m0;
-  const int64_t row0 = ((int64_t)(it.jw - D.cw0) * m0 + it.mu) * m0;
-  unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
-  int *rowexp = reinterpret_cast<int *>(s.ws + D.offRE);
-  if (tid < m0) rowexp[row0 + tid] = rexp[tid];
-  // two adjacent columns per thread (Kp is even): one 32-bit store per digit plane.  Kp is a
-  // multiple of 64, so the 32 lanes of a warp share nu: the row-sum terms of the fixed-point
-  // values are summed over the warp, then added to the row's exact sum
-  const int qsh = row_sum_shift(nv);
-  const int half = Kp >> 1;
-  const int items = m0 * half;
-  for (int p0 = tid; p0 < items; p0 += kGramThreads) {
-    const int nu = p0 / half, c = 2 * (p0 - nu * half);
-    int a[kSlices], b[kSlices];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kWarps = kGramThreads / 32;
+  const float2 *Gp = reinterpret_cast<const float2 *>(s.ws + D.offGp);
+  const float2 *Dp = reinterpret_cast<const float2 *>(s.ws + D.offDp);
+  const float2 *f = Gp + (int64_t)it.mu * n, *df = Dp + (int64_t)it.mu * n;
+  for (int nu = warp; nu < m0; nu += kWarps) {
+    const float2 *g = Gp + (int64_t)nu * n, *dg = Dp + (int64_t)nu * n;
+    float q0 = 0.0f, q1 = 0.0f, e0 = 0.0f, e1 = 0.0f, mx = 0.0f;
+    if (!periodic && lane == 0) {
+      // single open cell, Dirichlet ends: the virtual node -1 adds f_0 g_0 to the difference sum
+      const float2 a = __ldg(&f[0]), b = __ldg(&g[0]);
+      acc_prod(e0, e1, a.x, a.y, b.x, b.y);
+    }
+    for (int c = lane; c < nv; c += 32) {
+      float qs = 0.0f, qc = 0.0f;
+      if (periodic) {
+        // visited in increasing p; the indices advance by one cell per p
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0;
-    long long term = 0;
+        for (int sg = 0; sg < 2; ++sg) {
+          const int cnt = seg[nu][sg][0];
+          int iv = seg[nu][sg][1] + c, iu = seg[nu][sg][2] + c;
+#pragma unroll 2
+          for (int t = 0; t < cnt; ++t) {
+            const float2 a = __ldg(&f[iu]), b = __ldg(&g[iv]);
+            const float2 da = __ldg(&df[iu]), db = __ldg(&dg[iv]);
+            acc_prod(qs, qc, a.x, a.y, b.x, b.y);
+            acc_prod(e0, e1, da.x, da.y, db.x, db.y);
+            iv += nc;
+            if (iv >= n) iv -= n;
+            iu += nc;
+            if (iu >= n) iu -= n;
+          }
+        }
+      } else {
+        const float2 a = __ldg(&f[c]), b = __ldg(&g[c]);
+        const float2 da = __ldg(&df[c]), db = __ldg(&dg[c]);
+        acc_prod(qs, qc, a.x, a.y, b.x, b.y);
+        acc_prod(e0, e1, da.x, da.y, db.x, db.y);
+      }
+      float2 q;
+      two_sum(qs, qc, q.x, q.y);
+      Qp[nu * ld + c] = q;
+      mx = fmaxf(mx, fabsf(q.x) + fabsf(q.y));
+      acc_add(q0, q1, q.x, q.y);
+    }
+    const unsigned key = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));  // mx >= 0: bits order as values
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a0 = __shfl_xor_sync(0xffffffffu, q0, o), a1 = __shfl_xor_sync(0xffffffffu, q1, o);
+      const float b0 = __shfl_xor_sync(0xffffffffu, e0, o), b1 = __shfl_xor_sync(0xffffffffu, e1, o);
+      acc_add(q0, q1, a0, a1);
+      acc_add(e0, e1, b0, b1);
+    }
+    if (lane == 0) {
+      // |Q| <= |h| + |l| < 2^e (frexp's exponent; the e of a denormal maximum is -126)
+      const int be = (int)(key >> 23);
+      rexp[nu] = key == 0u ? 0 : (be == 0 ? -126 : min(be - 126, 126));
+      qsum[nu] = df_norm(q0, q1);
+      esum[nu] = df_norm(e0, e1);
+    }
+  }
+  __syncthreads();
+  const int64_t rows = (int64_t)D.Jc * mm;
+  const int64_t row0 = ((int64_t)(it.jw - D.cw0) * m0 + it.mu) * m0;
+  if (tid < m0) {
+    reinterpret_cast<int *>(s.ws + D.offRE)[row0 + tid] = rexp[tid];
+    // P1 slots in pairs, converted once (m0 threads of one warp: one FP64 pass)
+    const float2 invh = make_float2(D.p1h[0], D.p1h[1]), h1 = make_float2(D.p1h[2], D.p1h[3]);
+    const float2 h6 = make_float2(D.p1h[4], D.p1h[5]);
+    const float2 stiff = df_mul(esum[tid], invh);
+    const float2 mass = df_add(df_mul(qsum[tid], h1), df_neg(df_mul(esum[tid], h6)));
+    double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + it.mu * m0;
+    Cout[(int64_t)Rt * mm + tid] = (double)stiff.x + (double)stiff.y;
+    Cout[(int64_t)(Rt + 1) * mm + tid] = (double)mass.x + (double)mass.y;
+  }
+  // digit planes: two adjacent columns per thread (Kp is a multiple of 64, so c and c + 1 share a
+  // 32-column chunk), one 32-bit store per plane
+  unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
+  const int half = Kp >> 1;
+  const int64_t plane = (int64_t)(Kp / kPlaneChunk) * rows * kPlaneChunk;  // = rows * Kp
+  for (int p0 = tid; p0 < m0 * half; p0 += kGramThreads) {
+    const int nu = p0 / half, c = 2 * (p0 - nu * half);
+    const float sc = __int_as_float((127 - rexp[nu]) << 23);  // 2^-e, e in [-126, 126]
+    float a[kSlices], b[kSlices];
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k) a[k] = b[k] = 0.0f;
     if (c < nv) {
-      const long long X = fixed62(Q[nu * ld + c], rexp[nu]);
-      term = row_sum_term(X, qsh);
-      digits7(X, a);
+      const float2 q = Qp[nu * ld + c];
+      digits7f(__fmul_rn(q.x, sc), __fmul_rn(q.y, sc), a);
     }
     if (c + 1 < nv) {
-      const long long X = fixed62(Q[nu * ld + c + 1], rexp[nu]);
-      term += row_sum_term(X, qsh);
-      digits7(X, b);
+      const float2 q = Qp[nu * ld + c + 1];
+      digits7f(__fmul_rn(q.x, sc), __fmul_rn(q.y, sc), b);
     }
-    // c and c + 1 share a 32-column chunk
     const int64_t at = ((int64_t)(c / kPlaneChunk) * rows + row0 + nu) * kPlaneChunk + c % kPlaneChunk;
-    const int64_t plane = (int64_t)(Kp / kPlaneChunk) * rows * kPlaneChunk;  // = rows * Kp
+    // BF16 of an integer-valued float of at most 8 significant bits: its upper half, exact
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
       *reinterpret_cast<unsigned *>(planes + k * plane + at) =
-          (unsigned)bf16_of_int(a[k]) | ((unsigned)bf16_of_int(b[k]) << 16);
-    term = warp_sum_i64(term);
-    if (lane == 0) atomicAdd(&qsum[nu], (unsigned long long)term);
+          (__float_as_uint(a[k]) >> 16) | (__float_as_uint(b[k]) & 0xffff0000u);
   }
-  __syncthreads();
-  if (tid < m0)
-    write_p1_slots(s, it, tid, scale_pow2((double)(long long)qsum[tid], rexp[tid] + qsh - 62), red[2 * tid + 1]);
 }
 
 // Digit planes of the potential factors: one CTA per (system, direction, rank term r).
@@ -487,7 +589,7 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
                                int ldir) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * ((size_t)max_m0 * (max_nv + 1) + 2 * max_m0);
+  const size_t smem = sizeof(float2) * (size_t)max_m0 * (max_nv + 1);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_gram_slice, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

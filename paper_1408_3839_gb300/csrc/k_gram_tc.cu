@@ -18,9 +18,11 @@
 //     the 7 digit planes of the A tile (7 x 128 x 32 BF16) and of the B tile (7 x 64 x 32) into
 //     one of two shared-memory stages (84 KB each): the load of chunk k + 1 runs while the MMAs
 //     of chunk k execute;
-//   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 64, K = 16) for every
-//     pair (a, b) into the TMEM accumulator of its diagonal s = a + b (7 x 64 columns of the
-//     512 allocated), then tcgen05.commit to the stage's mbarrier, which frees the stage;
+//   * one thread issues tcgen05.mma.cta_group::1.kind::f16 (M = 128, K = 16) for every pair
+//     (a, b) into the TMEM accumulator of its diagonal s = a + b (7 x 64 columns of the 512
+//     allocated) -- the B planes of consecutive b side by side in shared memory, so that one MMA
+//     of N = 64 nb takes plane a against nb of them -- then tcgen05.commit to the stage's
+//     mbarrier, which frees the stage;
 //   * the 8 warps read the accumulators back with tcgen05.ld (32x32b; warp w reads TMEM lanes
 //     32 (w % 4) .. + 31, warps w and w + 4 half of the columns each), recombine the 7 diagonals
 //     and store the FP64 results in the layout of the FP64 route.
@@ -92,16 +94,42 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
 // both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
+}
+
+// x 2^e for an integer x, |x| < 2^63: x rounded to 53 bits (to nearest, ties to even) and scaled,
+// the value of scale_pow2((double)x, e), formed with integer operations (on this GPU an FP64
+// instruction costs a warp 16 cycles of the FP64 unit, whatever its active lanes); results outside
+// the normal range take scale_pow2 itself.
+__device__ __forceinline__ double int_times_pow2(long long x, int e) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = x < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long u = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int lz = __clzll(u);
+  const unsigned long long m = u << lz;  // leading bit at 63
+  unsigned long long mant = m >> 11;     // 53 bits
+  const unsigned long long rem = m & 0x7ffull;
+  int top = 63 - lz;  // exponent of the leading bit of x
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++top;
+    }
+  }
+  const int be = top + e + 1023;
+  if (be < 1 || be > 2046) return scale_pow2((double)x, e);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1))));
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -188,16 +216,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
       }
       last_arrived = ch;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // digit plane a of A against the B planes b0 .. b0 + nb - 1 (consecutive 64-row tiles in
+      // shared memory: one B operand of N = 64 nb rows) lands in the accumulators of the
+      // diagonals a + b0 .. a + b0 + nb - 1 (consecutive 64-column TMEM ranges): the 28 pairs
+      // a + b <= 6 as 10 MMAs of N <= 256 per K step (a = 0 first: it initialises every
+      // diagonal)
       const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes;
-      for (int s = 0; s < kSlices; ++s)
-        for (int a = 0; a <= s; ++a) {
-          const int b = s - a;
-          for (int kk = 0; kk < kChunkK / 16; ++kk) {
+      for (int kk = 0; kk < kChunkK / 16; ++kk)
+        for (int a = 0; a < kSlices; ++a)
+          for (int b0 = 0; b0 < kSlices - a; b0 += 4) {
+            const int nb = min(4, kSlices - a - b0);
             const uint64_t ad = sw64_desc(sA + a * kABytes + kk * 32);
-            const uint64_t bd = sw64_desc(sB + b * kBBytes + kk * 32);
-            mma_bf16(tmem + (uint32_t)(s * kTileN), ad, bd, (ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
+            const uint64_t bd = sw64_desc(sB + b0 * kBBytes + kk * 32);
+            mma_bf16(tmem + (uint32_t)((a + b0) * kTileN), ad, bd, idesc_n(nb * kTileN),
+                     (ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
           }
-        }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&bar_free[st]))
                    : "memory");
@@ -245,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
           const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
           const long long T = (hi << 24) + ((lo + 8) >> 4);
           const int E = er + P.colexp[n];
-          Crow[(int64_t)n * mm] = scale_pow2((double)T, E - 52);
+          Crow[(int64_t)n * mm] = int_times_pow2(T, E - 52);
         }
       }
     }

@@ -586,7 +586,6 @@ __global__ void __launch_bounds__(256) k_rayleigh_ritz(const double *__restrict_
   double *X = V + kRRMax * kRRMax;  // [kRRMax][kRRMax]
   __shared__ double dsc[kRRMax], sg[kRRMax], rc[kRRMax / 2], rs[kRRMax / 2];
   __shared__ int rp[kRRMax / 2], rq[kRRMax / 2], kept[kRRMax], nk_sh;
-  __shared__ double bmax;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double b = Bg[i * n + i];
     dsc[i] = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
@@ -602,7 +601,6 @@ __global__ void __launch_bounds__(256) k_rayleigh_ritz(const double *__restrict_
   if (threadIdx.x == 0) {
     double mx = 0.0;
     for (int i = 0; i < n; ++i) mx = fmax(mx, A[i * kRRMax + i]);
-    bmax = mx;
     int nk = 0;
     for (int i = 0; i < n; ++i)
       if (A[i * kRRMax + i] > cut * mx) {
@@ -663,7 +661,6 @@ __global__ void __launch_bounds__(256) k_rayleigh_ritz(const double *__restrict_
     }
   }
   if (threadIdx.x == 0) info[0] = nk;
-  (void)bmax;
 }
 
 }  // namespace

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include "lhf_internal.cuh"
+#include "lhf_pairs.cuh"
 
 namespace lhf {
 namespace {
@@ -59,7 +60,8 @@ __device__ double basis_sample(const SysDev &s, int l, int mu, int e) {
 }
 
 // Samples and their forward differences D_e = g_e - g_(e+1) (periodic directions wrap; open
-// ones take g_n = 0; not formed for the extended samples of an open box): one CTA per (system,
+// ones take g_n = 0; not formed for the extended samples of an open box), and on the mixed route
+// both also as FP32 pairs: one CTA per (system,
 // direction, function mu, chunk of kBasisChunk samples of the row), so that the long rows of a
 // periodic lattice direction are spread over several CTAs.  In a periodic lattice direction
 // only the nodes of the support cells cell_lo .. cell_hi of the cell-0 copy (mod L, at most L
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
     int e = e0 + j;
     if (e >= nx) e -= nx;
     s.ws[D.offG + (int64_t)mu * nx + e] = g[j];
+    if (D.offGp >= 0) reinterpret_cast<float2 *>(s.ws + D.offGp)[(int64_t)mu * D.n + e] = fp32_pair(g[j]);
     if (D.offD < 0) continue;
     double nxt;
     if (e + 1 == D.n)
@@ -174,7 +177,9 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
       nxt = k0 + j + 1 < kend ? g[j + 1] : basis_sample(s, l, mu, e + 1);
     else
       nxt = (lane == 31 || k0 + kBasisRun >= kend) ? basis_sample(s, l, mu, e + 1) : gn;
-    s.ws[D.offD + (int64_t)mu * D.n + e] = g[j] - nxt;
+    const double dif = g[j] - nxt;
+    s.ws[D.offD + (int64_t)mu * D.n + e] = dif;
+    if (D.offDp >= 0) reinterpret_cast<float2 *>(s.ws + D.offDp)[(int64_t)mu * D.n + e] = fp32_pair(dif);
   }
 }
 

@@ -362,6 +362,14 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     D.nv = D.periodic ? D.nc : D.n;
     D.K = s.K[l];
     D.h = s.h[l];
+    {
+      const double hv[3] = {1.0 / D.h, D.h, D.h / 6.0};
+      for (int k = 0; k < 3; ++k) {
+        const float hi = (float)hv[k];
+        D.p1h[2 * k] = hi;
+        D.p1h[2 * k + 1] = (float)(hv[k] - (double)hi);
+      }
+    }
     D.x0 = s.x0[l];
     D.cell0 = s.cell0[l];
     D.b = s.b[l];
@@ -452,6 +460,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
   for (int l = 0; l < 3; ++l) {
+    sd.d[l].offGp = sd.d[l].offDp = -1;
     sd.d[l].offG = (int64_t)off;
     off = align_up(off + (size_t)m0 * (sd.d[l].n + sd.d[l].gext));
     if (sd.d[l].gext == 0 && sd.d[l].J > 0) {  // differences for the P1 forms of the Gram kernels
@@ -489,6 +498,13 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     D.Kpad = (D.nv + 63) / 64 * 64;
     if (mixed && !box) {
       const size_t rows = (size_t)D.Jc * mm;
+      if (D.J > 0 && D.offD >= 0) {
+        // the samples and differences as FP32 pairs (8 bytes each: one double per value)
+        D.offGp = (int64_t)off;
+        off = align_up(off + (size_t)m0 * D.n);
+        D.offDp = (int64_t)off;
+        off = align_up(off + (size_t)m0 * D.n);
+      }
       D.offA = (int64_t)off;
       off = align_up(off + (lhf::kSlices * rows * D.Kpad * 2 + 7) / 8);
       D.offB = (int64_t)off;

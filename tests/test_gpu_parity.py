@@ -594,10 +594,13 @@ def test_mixed_gram_factors_full_size_tube_256(ctx, lhf):
         ctx.gram_factors(l, Cmx, lhf.MIXED)
         ctx.sync()
         a, b = C64.cpu().numpy(), Cmx.cpu().numpy()
-        # P1 slots are FP64 on both routes; rank slots within 1e-11 of their own scale or, for
-        # tail slots (digit truncation is relative to the row's scale), 1e-14 of the block's
-        # largest slot
-        assert np.array_equal(a[:, Rt:], b[:, Rt:])
+        # P1 slots: compensated FP32-pair sums on the mixed route (a few 2^-48 of the sums of
+        # magnitudes), within 1e-13 of each slot's largest entry; rank slots within 1e-11 of
+        # their own scale or, for tail slots (digit truncation is relative to the row's scale),
+        # 1e-14 of the block's largest slot
+        p1 = np.abs(a[:, Rt:]).max(axis=(0, 2, 3), keepdims=True)
+        d1 = np.abs(a[:, Rt:] - b[:, Rt:])
+        assert np.all(d1 <= 1e-13 * p1), (d1 / p1).max()
         scale = np.abs(a[:, :Rt]).max(axis=(2, 3), keepdims=True)
         block = np.abs(a[:, :Rt]).max(axis=(1, 2, 3), keepdims=True)
         assert np.all(np.abs(a[:, :Rt] - b[:, :Rt]) <= 1e-11 * scale + 1e-14 * block)
@@ -609,7 +612,7 @@ def test_mixed_gram_factors_full_size_tube_256(ctx, lhf):
     ctx.assemble_core_hamiltonian(Hmx, Smx, lhf.MIXED)
     ctx.sync()
     assert block_rel_err(Hmx.cpu().numpy(), H64.cpu().numpy(), m0) <= 1e-12
-    assert np.array_equal(Smx.cpu().numpy(), S64.cpu().numpy())
+    assert block_rel_err(Smx.cpu().numpy(), S64.cpu().numpy(), m0) <= 1e-13
 
 
 @pytest.mark.slow
