@@ -326,37 +326,33 @@ __device__ __forceinline__ unsigned short bf16_of_int(int v) {  // exact for |v|
   return (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
-// Nearest integer of |t| < 2^22 (the addition of 1.5 2^23 rounds to an integer).
-__device__ __forceinline__ float round_small(float t) {
-  const float m = 12582912.0f;
-  return __fadd_rn(__fadd_rn(t, m), -m);
-}
-
 // The 7 digits of x = h + l (a pair, |x| < 1) as integer-valued floats, x = sum_k a_k 2^(-7(k+1))
 // + O(2^-50): each digit the nearest integer to 128 times the remainder, decided by the
 // remainder's leading word; TwoSum folds the trailing word in before digits 2, 4 and 6 (before
 // it can reach 2^-11 of the remainder), so a_0 is in [-128, 128] and |a_k| <= 64 after it, the
-// bounds of digits7.  Every step is exact.
+// bounds of digits7.  A digit takes three exact steps: t = 128 h + 1.5 2^23 (rounds 128 h to an
+// integer), d = t - 1.5 2^23, h <- 128 h - d (one FMA: the difference is representable); the
+// trailing word is scaled only when folded in (by 2^14, for the two digits since the last fold).
 __device__ __forceinline__ void digits7f(float h, float l, float *a) {
+  const float m = 12582912.0f;
 #pragma unroll
   for (int k = 0; k < kSlices; ++k) {
     if (k == 2 || k == 4 || k == 6) {
       float t, e;
-      two_sum(h, l, t, e);
+      two_sum(h, __fmul_rn(l, 16384.0f), t, e);
       h = t;
       l = e;
     }
-    const float t = __fmul_rn(h, 128.0f);
-    const float d = round_small(t);
+    const float d = __fadd_rn(__fmaf_rn(h, 128.0f, m), -m);
     a[k] = d;
-    h = __fadd_rn(t, -d);
-    l = __fmul_rn(l, 128.0f);
+    h = __fmaf_rn(h, 128.0f, -d);
   }
 }
 
 // The folded products in compensated FP32 pairs and their digit planes (tensor-core route), one
 // CTA per (system, direction, window block, mu).  GB300 issues FP64 at 1/64 of the FP32 rate, so
-// the fold runs on the pairs h + l of the samples and differences written by k_basis: each
+// the fold runs on the pairs h + l of the samples and differences written by k_basis (one 16-byte
+// load per node and function gives both): each
 // product exact as a pair (an FMA gives its rounding error), the sums compensated (TwoSum), a
 // relative error of a few units of 2^-48 of sum |g_mu,j g_nu| per folded value.  Per row nu:
 //   * Q[nu][c] (pairs) in shared memory, a warp per nu, lanes over the nodes c;
@@ -366,7 +362,7 @@ __device__ __forceinline__ void digits7f(float h, float l, float *a) {
 //     h/6 as pairs from the host), converted to FP64 once;
 //   * the 7 digit planes of Q 2^-e (digits7f), two adjacent nodes per thread and store, in the
 //     chunk-major layout of digits7 (c >= n_v: zero).
-__global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
+__global__ void __launch_bounds__(kGramThreads, 4) k_gram_slice(const SysDev *__restrict__ sysv, int ldir) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   GramItem it;
@@ -383,15 +379,14 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
   __syncthreads();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int kWarps = kGramThreads / 32;
-  const float2 *Gp = reinterpret_cast<const float2 *>(s.ws + D.offGp);
-  const float2 *Dp = reinterpret_cast<const float2 *>(s.ws + D.offDp);
-  const float2 *f = Gp + (int64_t)it.mu * n, *df = Dp + (int64_t)it.mu * n;
+  const float4 *GD = reinterpret_cast<const float4 *>(s.ws + D.offGD);  // {sample, difference} pairs
+  const float4 *f = GD + (int64_t)it.mu * n;
   for (int nu = warp; nu < m0; nu += kWarps) {
-    const float2 *g = Gp + (int64_t)nu * n, *dg = Dp + (int64_t)nu * n;
+    const float4 *g = GD + (int64_t)nu * n;
     float q0 = 0.0f, q1 = 0.0f, e0 = 0.0f, e1 = 0.0f, mx = 0.0f;
     if (!periodic && lane == 0) {
       // single open cell, Dirichlet ends: the virtual node -1 adds f_0 g_0 to the difference sum
-      const float2 a = __ldg(&f[0]), b = __ldg(&g[0]);
+      const float4 a = __ldg(&f[0]), b = __ldg(&g[0]);
       acc_prod(e0, e1, a.x, a.y, b.x, b.y);
     }
     for (int c = lane; c < nv; c += 32) {
@@ -404,10 +399,9 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
           int iv = seg[nu][sg][1] + c, iu = seg[nu][sg][2] + c;
 #pragma unroll 2
           for (int t = 0; t < cnt; ++t) {
-            const float2 a = __ldg(&f[iu]), b = __ldg(&g[iv]);
-            const float2 da = __ldg(&df[iu]), db = __ldg(&dg[iv]);
+            const float4 a = __ldg(&f[iu]), b = __ldg(&g[iv]);
             acc_prod(qs, qc, a.x, a.y, b.x, b.y);
-            acc_prod(e0, e1, da.x, da.y, db.x, db.y);
+            acc_prod(e0, e1, a.z, a.w, b.z, b.w);
             iv += nc;
             if (iv >= n) iv -= n;
             iu += nc;
@@ -415,10 +409,9 @@ __global__ void __launch_bounds__(kGramThreads, 5) k_gram_slice(const SysDev *__
           }
         }
       } else {
-        const float2 a = __ldg(&f[c]), b = __ldg(&g[c]);
-        const float2 da = __ldg(&df[c]), db = __ldg(&dg[c]);
+        const float4 a = __ldg(&f[c]), b = __ldg(&g[c]);
         acc_prod(qs, qc, a.x, a.y, b.x, b.y);
-        acc_prod(e0, e1, da.x, da.y, db.x, db.y);
+        acc_prod(e0, e1, a.z, a.w, b.z, b.w);
       }
       float2 q;
       two_sum(qs, qc, q.x, q.y);

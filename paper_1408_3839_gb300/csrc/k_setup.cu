@@ -168,7 +168,6 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
     int e = e0 + j;
     if (e >= nx) e -= nx;
     s.ws[D.offG + (int64_t)mu * nx + e] = g[j];
-    if (D.offGp >= 0) reinterpret_cast<float2 *>(s.ws + D.offGp)[(int64_t)mu * D.n + e] = fp32_pair(g[j]);
     if (D.offD < 0) continue;
     double nxt;
     if (e + 1 == D.n)
@@ -179,7 +178,10 @@ __global__ void __launch_bounds__(kBasisThreads) k_basis(const SysDev *__restric
       nxt = (lane == 31 || k0 + kBasisRun >= kend) ? basis_sample(s, l, mu, e + 1) : gn;
     const double dif = g[j] - nxt;
     s.ws[D.offD + (int64_t)mu * D.n + e] = dif;
-    if (D.offDp >= 0) reinterpret_cast<float2 *>(s.ws + D.offDp)[(int64_t)mu * D.n + e] = fp32_pair(dif);
+    if (D.offGD >= 0) {
+      const float2 gp = fp32_pair(g[j]), dp = fp32_pair(dif);
+      reinterpret_cast<float4 *>(s.ws + D.offGD)[(int64_t)mu * D.n + e] = make_float4(gp.x, gp.y, dp.x, dp.y);
+    }
   }
 }
 

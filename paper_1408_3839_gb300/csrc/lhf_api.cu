@@ -460,7 +460,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
   for (int l = 0; l < 3; ++l) {
-    sd.d[l].offGp = sd.d[l].offDp = -1;
+    sd.d[l].offGD = -1;
     sd.d[l].offG = (int64_t)off;
     off = align_up(off + (size_t)m0 * (sd.d[l].n + sd.d[l].gext));
     if (sd.d[l].gext == 0 && sd.d[l].J > 0) {  // differences for the P1 forms of the Gram kernels
@@ -499,11 +499,9 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if (mixed && !box) {
       const size_t rows = (size_t)D.Jc * mm;
       if (D.J > 0 && D.offD >= 0) {
-        // the samples and differences as FP32 pairs (8 bytes each: one double per value)
-        D.offGp = (int64_t)off;
-        off = align_up(off + (size_t)m0 * D.n);
-        D.offDp = (int64_t)off;
-        off = align_up(off + (size_t)m0 * D.n);
+        // the samples and differences as FP32 pairs, interleaved (16 bytes a node: two doubles)
+        D.offGD = (int64_t)off;
+        off = align_up(off + (size_t)2 * m0 * D.n);
       }
       D.offA = (int64_t)off;
       off = align_up(off + (lhf::kSlices * rows * D.Kpad * 2 + 7) / 8);

@@ -54,8 +54,8 @@ struct DirDev {
   int Kpad;       // nv rounded up to a multiple of 64
   int pad2_;
   float p1h[6];   // 1 / h, h, h / 6 as FP32 pairs (hi, lo): the P1 factors of the mixed route
-  int64_t offGp;  // float2 [m0][n] basis samples as FP32 pairs h + l (written with offG), or -1
-  int64_t offDp;  // float2 [m0][n] differences as FP32 pairs (written with offD), or -1
+  int64_t offGD;  // float4 [m0][n] {sample, difference} as FP32 pairs h + l (written with offG and
+                  // offD on the mixed route), or -1
   int64_t offA;   // BF16 [kSlices][Kpad / 32][Jc m0 m0][32] digit planes of the folded products
   int64_t offB;   // BF16 [kSlices][Kpad / 32][Rt][32] digit planes of the potential factors
   int64_t offRE;  // int [Jc m0 m0] row scale exponents
