@@ -13,7 +13,9 @@
 // (its one rounding, 2^-53 of the scale, is far below the truncation of the dropped pairs) and is
 // converted to FP64 once.
 //
-// One CTA of 256 threads per (system, direction, 128-row tile, 64-column tile):
+// Jobs are (system, direction, 128-row tile, 64-column tile); a persistent grid of one CTA per SM
+// takes every gridDim.x-th job, warp 0 running the loads and MMAs one chunk ahead across its tiles
+// while warps 1 .. 8 drain the previous tile's accumulators (mbarriers tmem_full / tmem_empty):
 //   * TMA (cp.async.bulk.tensor.2d, 64-byte swizzle, no multicast) brings, per 32-wide K chunk,
 //     the 7 digit planes of the A tile (7 x 128 x 32 BF16) and of the B tile (7 x 64 x 32) into
 //     one of two shared-memory stages (84 KB each): the load of chunk k + 1 runs while the MMAs
@@ -23,12 +25,13 @@
 //     allocated) -- the B planes of consecutive b side by side in shared memory, so that one MMA
 //     of N = 64 nb takes plane a against nb of them -- then tcgen05.commit to the stage's
 //     mbarrier, which frees the stage;
-//   * the 8 warps read the accumulators back with tcgen05.ld (32x32b; warp w reads TMEM lanes
-//     32 (w % 4) .. + 31, warps w and w + 4 half of the columns each), recombine the 7 diagonals
-//     and store the FP64 results in the layout of the FP64 route.
+//   * warps 1 .. 8 read the accumulators back with tcgen05.ld (32x32b; warp w reads TMEM lanes
+//     32 (w % 4) .. + 31, half of the columns each), release them, recombine the 7 diagonals and
+//     store the FP64 results in the layout of the FP64 route.
 // Every mbarrier wait is bounded (~1 s of clock cycles); on time-out the CTA sets kFlagTimeout,
 // waits (bounded) for its outstanding operations, frees its TMEM and returns.
 #include <cuda.h>
+#include <algorithm>
 #include <mutex>
 #include <string.h>
 
@@ -39,7 +42,8 @@
 namespace lhf {
 namespace {
 
-constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 read TMEM lane quadrant w % 4, half the columns each
+constexpr int kEpiWarps = 8;  // warps 1 .. 8 read TMEM lane quadrant w % 4, half the columns each
+constexpr int kTcThreads = 32 * (1 + kEpiWarps);
 constexpr int kTileM = 128;
 constexpr int kTileN = 64;
 constexpr int kChunkK = kPlaneChunk;  // one 64-byte swizzle atom of BF16
@@ -68,9 +72,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; also gives up once *ok (if given) drops to 0.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int *ok) {
   const long long t0 = clock64();
-  while (true) {
+  for (unsigned spin = 0;; ++spin) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -80,6 +85,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((spin & 15u) == 15u && ok && *(volatile const int *)ok == 0) return false;
     if (clock64() - t0 > kWaitCycles) return false;
   }
 }
@@ -148,17 +154,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restrict__ jobs,
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restrict__ jobs, int njobs,
                                                            const TcArgs *__restrict__ args, unsigned *flags) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar_full[kStages], bar_free[kStages];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_free[kStages], tmem_full, tmem_empty;
   __shared__ uint32_t tmem_slot;
   __shared__ int ok_sh;
   unsigned char *tiles =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t s0 = smem_u32(tiles);
-  const TcJob job = jobs[blockIdx.x];
-  const TcArgs &P = args[job.sys * 3 + job.l];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) {
@@ -173,6 +177,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[st])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_free[st])) : "memory");
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tmem_full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tmem_empty)), "r"(kEpiWarps) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ok_sh = 1;
   }
@@ -180,105 +186,147 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (threadIdx.x == 0) {
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapB)) : "memory");
-    const int nchunks = P.Kpad / kChunkK;
-    // chunk ch uses stage ch % 2 for the (ch / 2)-th time: its barriers complete with parity (ch / 2) & 1
-    auto load = [&](int ch) {
-      const int st = ch & 1;
-      const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes, bf = smem_u32(&bar_full[st]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"(kStageBytes) : "memory");
-      // chunk-major planes: rows (k * nchunks + ch) * rows + row0 .. of a 32-wide 2D view
-      for (int a = 0; a < kSlices; ++a)
-        tma_load_2d(sA + a * kABytes, &P.mapA, 0, (a * nchunks + ch) * P.rows + job.row0, bf);
-      for (int b = 0; b < kSlices; ++b)
-        tma_load_2d(sB + b * kBBytes, &P.mapB, 0, (b * nchunks + ch) * P.Rt + job.n0, bf);
-    };
-    bool ok = true;
-    int last_commit = -1;  // the last chunk whose MMAs were committed
-    int last_load = 0, last_arrived = -1;  // the last chunk loaded / seen in shared memory
-    load(0);
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-      const int st = ch & 1;
-      if (ch + 1 < nchunks) {
-        // stage (ch + 1) % 2 is free once the MMAs of chunk ch - 1 are done
-        if (ch >= 1 && !mbar_wait(smem_u32(&bar_free[st ^ 1]), ((ch - 1) >> 1) & 1)) {
+  if (warp == 0) {
+    // ---- control (one thread): the loads run one chunk ahead of the MMAs, across tiles -------
+    if (lane == 0) {
+      // chunk cursor over this CTA's tiles (jobs blockIdx.x, blockIdx.x + gridDim.x, ..)
+      struct Cur {
+        int job, ch, nch;
+      };
+      auto first = [&](int job) {
+        return Cur{job, 0, job < njobs ? args[jobs[job].sys * 3 + jobs[job].l].Kpad / kChunkK : 0};
+      };
+      auto next = [&](Cur c) { return ++c.ch < c.nch ? c : first(c.job + (int)gridDim.x); };
+      // global chunk g uses stage g % 2 for the (g / 2)-th time: its barriers complete with parity
+      // (g / 2) & 1
+      auto load = [&](const Cur &c, int g) {
+        const TcJob jb = jobs[c.job];
+        const TcArgs &P = args[jb.sys * 3 + jb.l];
+        if (c.ch == 0) {
+          asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapA)) : "memory");
+          asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mapB)) : "memory");
+        }
+        const int st = g & 1;
+        const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes, bf = smem_u32(&bar_full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bf), "r"(kStageBytes) : "memory");
+        // chunk-major planes: rows (k * nchunks + ch) * rows + row0 .. of a 32-wide 2D view
+        for (int a = 0; a < kSlices; ++a)
+          tma_load_2d(sA + a * kABytes, &P.mapA, 0, (a * c.nch + c.ch) * P.rows + jb.row0, bf);
+        for (int b = 0; b < kSlices; ++b)
+          tma_load_2d(sB + b * kBBytes, &P.mapB, 0, (b * c.nch + c.ch) * P.Rt + jb.n0, bf);
+      };
+      bool ok = true;
+      int last_commit = -1, last_load = -1, last_arrived = -1, ntile = 0;
+      Cur cur = first(blockIdx.x), ahead = cur;
+      if (cur.nch > 0) {
+        load(cur, 0);
+        last_load = 0;
+      }
+      for (int g = 0; cur.nch > 0 && ok; ++g) {
+        const int st = g & 1;
+        ahead = next(ahead);
+        if (ahead.nch > 0) {
+          // stage (g + 1) % 2 is free once the MMAs of chunk g - 1 are done
+          if (g >= 1 && !mbar_wait(smem_u32(&bar_free[st ^ 1]), ((g - 1) >> 1) & 1, &ok_sh)) {
+            ok = false;
+            break;
+          }
+          load(ahead, g + 1);
+          last_load = g + 1;
+        }
+        if (!mbar_wait(smem_u32(&bar_full[st]), (g >> 1) & 1, &ok_sh)) {
           ok = false;
           break;
         }
-        load(ch + 1);
-        last_load = ch + 1;
+        last_arrived = g;
+        // a tile's first MMAs overwrite the accumulators: the previous tile's epilogue must be done
+        if (cur.ch == 0 && ntile > 0 && !mbar_wait(smem_u32(&tmem_empty), (ntile - 1) & 1, &ok_sh)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // digit plane a of A against the B planes b0 .. b0 + nb - 1 (consecutive 64-row tiles in
+        // shared memory: one B operand of N = 64 nb rows) lands in the accumulators of the
+        // diagonals a + b0 .. a + b0 + nb - 1 (consecutive 64-column TMEM ranges): the 28 pairs
+        // a + b <= 6 as 10 MMAs of N <= 256 per K step (a = 0 first: it initialises every
+        // diagonal)
+        const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes;
+        for (int kk = 0; kk < kChunkK / 16; ++kk)
+          for (int a = 0; a < kSlices; ++a)
+            for (int b0 = 0; b0 < kSlices - a; b0 += 4) {
+              const int nb = min(4, kSlices - a - b0);
+              const uint64_t ad = sw64_desc(sA + a * kABytes + kk * 32);
+              const uint64_t bd = sw64_desc(sB + b0 * kBBytes + kk * 32);
+              mma_bf16(tmem + (uint32_t)((a + b0) * kTileN), ad, bd, idesc_n(nb * kTileN),
+                       (cur.ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar_free[st]))
+                     : "memory");
+        last_commit = g;
+        if (cur.ch == cur.nch - 1) {
+          // the tile's accumulators are complete once these MMAs are
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&tmem_full))
+                       : "memory");
+          ++ntile;
+        }
+        cur = next(cur);
       }
-      if (!mbar_wait(smem_u32(&bar_full[st]), (ch >> 1) & 1)) {
-        ok = false;
-        break;
+      if (!ok) {
+        atomicOr(flags, kFlagTimeout);
+        ok_sh = 0;
+        // bounded: the MMAs and loads still in flight complete before the CTA exits
+        if (last_commit >= 0) mbar_wait(smem_u32(&bar_free[last_commit & 1]), (last_commit >> 1) & 1, nullptr);
+        for (int g = last_arrived + 1; g <= last_load; ++g)
+          mbar_wait(smem_u32(&bar_full[g & 1]), (g >> 1) & 1, nullptr);
       }
-      last_arrived = ch;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // digit plane a of A against the B planes b0 .. b0 + nb - 1 (consecutive 64-row tiles in
-      // shared memory: one B operand of N = 64 nb rows) lands in the accumulators of the
-      // diagonals a + b0 .. a + b0 + nb - 1 (consecutive 64-column TMEM ranges): the 28 pairs
-      // a + b <= 6 as 10 MMAs of N <= 256 per K step (a = 0 first: it initialises every
-      // diagonal)
-      const uint32_t sA = s0 + st * kStageBytes, sB = sA + kSlices * kABytes;
-      for (int kk = 0; kk < kChunkK / 16; ++kk)
-        for (int a = 0; a < kSlices; ++a)
-          for (int b0 = 0; b0 < kSlices - a; b0 += 4) {
-            const int nb = min(4, kSlices - a - b0);
-            const uint64_t ad = sw64_desc(sA + a * kABytes + kk * 32);
-            const uint64_t bd = sw64_desc(sB + b0 * kBBytes + kk * 32);
-            mma_bf16(tmem + (uint32_t)((a + b0) * kTileN), ad, bd, idesc_n(nb * kTileN),
-                     (ch > 0 || a > 0 || kk > 0) ? 1u : 0u);
-          }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bar_free[st]))
-                   : "memory");
-      last_commit = ch;
     }
-    // the last commit covers every MMA issued before it (in-order completion)
-    if (last_commit >= 0 &&
-        !mbar_wait(smem_u32(&bar_free[last_commit & 1]), (last_commit >> 1) & 1))
-      ok = false;
-    if (!ok) {
-      atomicOr(flags, kFlagTimeout);
-      ok_sh = 0;
-      // bounded: give the loads still in flight a chance to land before the CTA exits
-      for (int ch = last_arrived + 1; ch <= last_load; ++ch) mbar_wait(smem_u32(&bar_full[ch & 1]), (ch >> 1) & 1);
-    }
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (ok_sh) {
-    const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad .. 32 quad + 31; column half
-    const int row = job.row0 + quad * 32 + lane;
-    const int mm = P.m0 * P.m0;
+  } else {
+    // ---- epilogue warps 1 .. 8: TMEM lanes 32 quad .. 32 quad + 31, one half of the columns ----
+    const int quad = warp & 3, half = (warp - 1) >> 2;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    const int er = row < P.rows ? P.rowexp[row] : 0;
-    double *Crow = P.C + (int64_t)(row / mm) * (P.Rt + 2) * mm + (row % mm);
-    for (int cc = half * (kTileN / 32); cc < (half + 1) * (kTileN / 32); ++cc) {
-      uint32_t v[kSlices][16];
+    int ntile = 0;
+    for (int job = blockIdx.x; job < njobs; job += gridDim.x, ++ntile) {
+      bool ready = false;
+      if (lane == 0) ready = mbar_wait(smem_u32(&tmem_full), ntile & 1, &ok_sh);
+      if (!__shfl_sync(0xffffffffu, ready ? 1 : 0, 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const TcJob jb = jobs[job];
+      const TcArgs &P = args[jb.sys * 3 + jb.l];
+      const int row = jb.row0 + quad * 32 + lane;
+      const int mm = P.m0 * P.m0;
+      const int er = row < P.rows ? P.rowexp[row] : 0;
+      double *Crow = P.C + (int64_t)(row / mm) * (P.Rt + 2) * mm + (row % mm);
+      for (int cc = half * (kTileN / 32); cc < (half + 1) * (kTileN / 32); ++cc) {
+        uint32_t v[kSlices][16];
 #pragma unroll
-      for (int s = 0; s < kSlices; ++s) tmem_ld16(tmem + lane_base + (uint32_t)(s * kTileN + cc * 16), v[s]);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < P.rows) {
+        for (int s = 0; s < kSlices; ++s) tmem_ld16(tmem + lane_base + (uint32_t)(s * kTileN + cc * 16), v[s]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (cc == (half + 1) * (kTileN / 32) - 1) {
+          // every read of this warp's accumulators is done: the next tile's MMAs may start
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_empty)) : "memory");
+        }
+        if (row < P.rows) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int n = job.n0 + cc * 16 + t;
-          if (n >= P.Rt) continue;
-          // D_s are integers below 2^24 held exactly in FP32: converted to int32 and combined in
-          // 64-bit integers, hi < 2^39 (weights 2^-14 .. 2^-28) and lo < 2^46 (2^-35 .. 2^-56),
-          // then T = hi 2^24 + round(lo / 16) (< 2^63; the rounding, 2^-53 of the scale 2^E, is far
-          // below the 2^-48 truncation of the dropped digit pairs) converted and scaled once
-          long long d[kSlices];
+          for (int t = 0; t < 16; ++t) {
+            const int n = jb.n0 + cc * 16 + t;
+            if (n >= P.Rt) continue;
+            // D_s are integers below 2^24 held exactly in FP32: converted to int32 and combined in
+            // 64-bit integers, hi < 2^39 (weights 2^-14 .. 2^-28) and lo < 2^46 (2^-35 .. 2^-56),
+            // then T = hi 2^24 + round(lo / 16) (< 2^63; the rounding, 2^-53 of the scale 2^E, is
+            // far below the 2^-48 truncation of the dropped digit pairs) converted and scaled once
+            long long d[kSlices];
 #pragma unroll
-          for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2int_rn(__uint_as_float(v[s][t]));
-          const long long hi = (d[0] << 14) + (d[1] << 7) + d[2];
-          const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
-          const long long T = (hi << 24) + ((lo + 8) >> 4);
-          const int E = er + P.colexp[n];
-          Crow[(int64_t)n * mm] = int_times_pow2(T, E - 52);
+            for (int s = 0; s < kSlices; ++s) d[s] = (long long)__float2int_rn(__uint_as_float(v[s][t]));
+            const long long hi = (d[0] << 14) + (d[1] << 7) + d[2];
+            const long long lo = (d[3] << 21) + (d[4] << 14) + (d[5] << 7) + d[6];
+            const long long T = (hi << 24) + ((lo + 8) >> 4);
+            const int E = er + P.colexp[n];
+            Crow[(int64_t)n * mm] = int_times_pow2(T, E - 52);
+          }
         }
       }
     }
@@ -379,10 +427,17 @@ cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsi
   if (njobs <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
+  // persistent: one CTA per SM (shared memory and TMEM admit one), each taking every
+  // gridDim.x-th job
+  int dev = 0, nsm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(njobs, nsm));
   const unsigned char *d = static_cast<const unsigned char *>(dev_buf);
   kmark(LHF_K_GRAM_TC, 1, st);
-  k_gram_tc<<<(unsigned)njobs, kTcThreads, kSmemBytes, st>>>(reinterpret_cast<const TcJob *>(d + jobs_off),
-                                                             reinterpret_cast<const TcArgs *>(d), flags);
+  k_gram_tc<<<(unsigned)grid, kTcThreads, kSmemBytes, st>>>(reinterpret_cast<const TcJob *>(d + jobs_off), njobs,
+                                                            reinterpret_cast<const TcArgs *>(d), flags);
   kmark(LHF_K_GRAM_TC, 0, st);
   return cudaGetLastError();
 }
