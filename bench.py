@@ -129,7 +129,7 @@ def _jc(s: dict, l: int) -> int:
     return L // 2 + 1 if J == L else (J + 1) // 2
 
 
-def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
+def kernel_work(sizes: list[dict], passes: float, matrices: float, pairs: bool = False) -> dict:
     """Algorithmic work of one step (a batch of systems) per kernel: the roofline numerators.
 
     k_gram_fp64: 2 R_tot m0^2 n_v per contracted window block (blocks j >= 0; the j < 0 blocks are
@@ -143,7 +143,13 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
     per column a Hermitian matrix-vector product and a rank-2 update of the lower triangle, 2 n^2
     complex multiply-adds for a trailing block of order n).  k_tridiag_eig: 8 m flops per FP64
     characteristic-polynomial pass (the minors and their derivatives; its FP32 bisection is not
-    counted).  `passes` and `matrices` are per step."""
+    counted).  `passes` and `matrices` are per step.
+
+    pairs (the mixed route): k_eig's reduction runs in compensated FP32 pairs, a complex
+    multiply-add (8 FP64 flops) as four compensated products of 12 FP32 operations each, so its
+    work is counted as 6 FP32 operations per FP64-equivalent flop against the FP32 issue rate
+    ("alu32"; "algorithmic_flops" keeps the FP64-equivalent count).  k_gram_slice's fold is FP32
+    pairs too; it is rated by the digit-plane bytes it writes."""
     gram = tc = tc_alg = slice_bytes = rank = dft_bytes = 0.0
     levels = 0
     for s in sizes:
@@ -160,13 +166,15 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
         dft_bytes += s["n_blocks"] * m0 * m0 * (2 * 8 + 2 * 16)
         levels = max(levels, sum(1 for l in range(3) if s["L"][l] > 1))
     m = sizes[0]["m0"] if sizes else 0
+    eig_flops = matrices * (28.0 / 3.0 + 16.0 / 3.0) * m ** 3
     return {
         "k_gram_fp64": {"bound": "alu", "work": gram},
         "k_gram_tc": {"bound": "tensor", "work": tc, "algorithmic_flops": gram},
         "k_gram_slice": {"bound": "hbm", "work": slice_bytes},
         "k_ranksum": {"bound": "alu", "work": rank},
         "k_dft_pass": {"bound": "hbm", "work": dft_bytes},
-        "k_eig": {"bound": "alu", "work": matrices * (28.0 / 3.0 + 16.0 / 3.0) * m ** 3},
+        "k_eig": ({"bound": "alu32", "work": 6.0 * eig_flops, "algorithmic_flops": eig_flops} if pairs
+                  else {"bound": "alu", "work": eig_flops}),
         "k_tridiag_eig": {"bound": "alu", "work": passes * 8.0 * m},
     }
 
@@ -177,19 +185,20 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float) -> dict:
 # kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
 # time; any other hash reports null.
 TRAFFIC = {
-    # ncu --set full of the tube_256 workload at 16 systems:
-    # the autotuned k_eig / k_tridiag_eig launches and the first launch of the others; bytes read +
-    # written / 16 (k_potential: its two launches, row constants and rows).  Only kernels whose
-    # traffic grows with the systems of a batch are listed (the 16-system capture keeps part of
-    # the rank sum's and the DFT's outputs in L2, a 64-system step does not; the digit slicing
-    # runs once per direction and only direction 0 was captured)
-    "k_eig": {"src": "k_eig.cu", "sha": "f46a43380a8f2edb", "bytes_per_system": (17.018880e6 + 0.044288e6) / 16},
-    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "f46a43380a8f2edb", "bytes_per_system": 0.620288e6 / 16},
-    "k_potential": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83",
-                    "bytes_per_system": (0.060672e6 + 0.742912e6 + 0.002304e6) / 16},
-    "k_basis": {"src": "k_setup.cu", "sha": "c58f415a6dcc6d83", "bytes_per_system": (0.228096e6 + 0.046080e6) / 16},
-    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "70b7c2ac7ec28b1d",
-                  "bytes_per_system": (180.756736e6 + 27.759104e6) / 16},
+    # ncu --set full of the tube_256 workload at 16 systems, one kernel per capture: the autotuned
+    # k_eig / k_tridiag_eig launches and the first launch of the others; bytes read + written / 16
+    # (k_potential: its row launch plus the row-constant launch k_pot_rows of the capture before,
+    # whose code is unchanged).  Only kernels whose traffic grows with the systems of a batch are
+    # listed (the 16-system capture keeps part of the rank sum's and the DFT's outputs in L2, a
+    # 64-system step does not; the digit slicing runs once per direction and only direction 0 was
+    # captured)
+    "k_eig": {"src": "k_eig.cu", "sha": "cb92bc0544d011c7", "bytes_per_system": (17.025280e6 + 0.193280e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "cb92bc0544d011c7", "bytes_per_system": 0.621056e6 / 16},
+    "k_potential": {"src": "k_setup.cu", "sha": "6739f7ff09425235",
+                    "bytes_per_system": (0.060672e6 + 0.741632e6 + 0.000768e6) / 16},
+    "k_basis": {"src": "k_setup.cu", "sha": "6739f7ff09425235", "bytes_per_system": (0.287744e6 + 0.110592e6) / 16},
+    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "5ea77bf3011af230",
+                  "bytes_per_system": (180.771072e6 + 22.735616e6) / 16},
 }
 
 
@@ -208,6 +217,11 @@ def kernel_traffic(kernel: str, systems: int):
     if not t or _src_sha(t["src"]) != t["sha"]:
         return None
     return t["bytes_per_system"] * systems
+
+
+def fp32_op_peak_tops() -> float:
+    # 152 SMs x 128 FP32 lanes x 2.07 GHz: FP32 operations (an FMA counted once) per second
+    return 152 * 128 * 2.07e9 / 1e12
 
 
 def fp64_peak_tflops() -> float:
@@ -758,7 +772,7 @@ def run_gpu(args):
     e2e_value = total_systems / e2e_s
 
     # rooflines per kernel, and of the dominant kernel (the most device time in the timed region)
-    work = kernel_work(all_sizes, passes / max(args.steps, 1), mats / max(args.steps, 1))
+    work = kernel_work(all_sizes, passes / max(args.steps, 1), mats / max(args.steps, 1), precision == lhf.MIXED)
     peaks = measured_peaks()
     fp64_peak = fp64_peak_tflops()
     rooflines = {}
@@ -779,11 +793,15 @@ def run_gpu(args):
             achieved = per_launch_work / per_launch_s / 1e12
             peak, unit = float(peaks.get("bf16_tflops_sustained", 1700.0)), "TFLOP/s"
             src = "measured bf16_tflops_sustained" if "bf16_tflops_sustained" in peaks else "fallback"
+        elif w["bound"] == "alu32":
+            achieved = per_launch_work / per_launch_s / 1e12
+            peak, unit = fp32_op_peak_tops(), "Top/s"
+            src = "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz"
         else:
             achieved = per_launch_work / per_launch_s / 1e12
             peak, unit = fp64_peak, "TFLOP/s"
             src = "FP64: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
-        r = {"bound": w["bound"], "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+        r = {"bound": "alu" if w["bound"] == "alu32" else w["bound"], "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
              "peak_source": src, "launches": k_n, "ms_per_launch": k_ms / k_n}
         r["launches_per_step"] = k_n / max(args.steps, 1)
         tr = kernel_traffic(kname, B)
