@@ -501,6 +501,156 @@ __device__ void df_forward(float4 *A, float4 *V, const float4 *B, const float2 *
   g.sync();
 }
 
+// A += c x (c a real pair, x a complex pair)
+__device__ __forceinline__ void cacc_rmad(Cacc &A, float2 c, float4 x) {
+  acc_prod(A.rs, A.rc, c.x, c.y, x.x, x.y);
+  acc_prod(A.is, A.ic, c.x, c.y, x.z, x.w);
+}
+
+// Cyclic Jacobi in pairs, as jacobi_herm (same ordering, rotations and block updates; the
+// rotation table's c, s_r, s_i hold pairs in their doubles' bytes): the rotation from
+// u = 2 sign(d) / (|d| + sqrt(d^2 + 4 |A_pq|^2)) with the square root and the reciprocals in
+// pair arithmetic, the 2 x 2 block updates as compensated sums.  Pairs resolve about 2^-46 of
+// an entry, so the sweeps stop once the off-diagonal Frobenius norm falls below 2^-42 of the
+// total (squared: 2^-84), a margin above the rounding noise of the updates; the off-diagonal
+// left moves an eigenvalue by its square over the gap.  Returns the sweeps.
+template <int G>
+__device__ int df_jacobi_herm(float4 *A, float4 *V, int m, const Grp<G> &g, const RotTab &R) {
+  const int lane = g.lane;
+  const int mm = m * m, mp = m + (m & 1), npair = mp / 2;
+  const int nblk = npair * (npair - 1) / 2;
+  float2 *Rc = reinterpret_cast<float2 *>(R.c), *Rr = reinterpret_cast<float2 *>(R.sr);
+  float2 *Ri = reinterpret_cast<float2 *>(R.si);
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    float off = 0.0f, tot = 0.0f;
+    for (int e = lane; e < mm; e += G) {
+      const float v = fmaf(A[e].x, A[e].x, A[e].z * A[e].z);
+      tot += v;
+      if (e / m != e - (e / m) * m) off += v;
+    }
+    for (int o = G / 2; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(g.mask, off, o);
+      tot += __shfl_xor_sync(g.mask, tot, o);
+    }
+    if (off <= 0x1p-84f * tot) break;
+    for (int step = 0; step < mp - 1; ++step) {
+      if (lane < npair) {
+        const int pa = lane, pb = mp - 1 - lane;
+        int p = pa == 0 ? 0 : ((pa - 1 + step) % (mp - 1)) + 1;
+        int q = pb == 0 ? 0 : ((pb - 1 + step) % (mp - 1)) + 1;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        float2 c = make_float2(1.0f, 0.0f), sr = make_float2(0.0f, 0.0f), si = make_float2(0.0f, 0.0f);
+        if (q < m) {
+          const float4 gq = A[p * m + q];
+          const float2 a = make_float2(A[p * m + p].x, A[p * m + p].y), b = make_float2(A[q * m + q].x, A[q * m + q].y);
+          const float2 ag2 = df_abs2(gq);
+          if (ag2.x > 1e-37f && ag2.x > 1e-30f * fabsf(a.x * b.x)) {
+            const float2 d = df_add(b, df_neg(a));
+            const float2 r = df_sqrt(df_add(df_mul(d, d), df_mul(make_float2(4.0f, 0.0f), ag2)));
+            const float2 ad = d.x < 0.0f ? df_neg(d) : d;
+            float2 u = df_recip(df_add(ad, r));
+            u = make_float2(2.0f * (d.x < 0.0f ? -u.x : u.x), 2.0f * (d.x < 0.0f ? -u.y : u.y));
+            const float2 tg = df_mul(u, ag2);  // t |A_pq|
+            c = df_rsqrt(df_add(make_float2(1.0f, 0.0f), df_mul(tg, u)));  // 1 / sqrt(1 + t^2)
+            const float2 uc = df_mul(u, c);
+            sr = df_mul(uc, make_float2(gq.x, gq.y));
+            si = df_mul(uc, make_float2(gq.z, gq.w));
+            const float2 na = df_add(a, df_neg(tg)), nb = df_add(b, tg);
+            A[p * m + p] = make_float4(na.x, na.y, 0.0f, 0.0f);
+            A[q * m + q] = make_float4(nb.x, nb.y, 0.0f, 0.0f);
+            A[p * m + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            A[q * m + p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
+        }
+        R.p[lane] = p;
+        R.q[lane] = q;
+        Rc[lane] = c;
+        Rr[lane] = sr;
+        Ri[lane] = si;
+      }
+      g.sync();
+      for (int bi = lane; bi < nblk; bi += G) {
+        const int k1 = R.blk[2 * bi], k2 = R.blk[2 * bi + 1];
+        const bool r1 = !(Rr[k1].x == 0.0f && Ri[k1].x == 0.0f), r2 = !(Rr[k2].x == 0.0f && Ri[k2].x == 0.0f);
+        if (!r1 && !r2) continue;
+        const int p1 = R.p[k1], q1 = R.q[k1], p2 = R.p[k2], q2 = R.q[k2];
+        const bool v1 = q1 < m, v2 = q2 < m;  // q = m is the dummy of an odd order
+        const float2 c1 = Rc[k1], c2 = Rc[k2];
+        const float4 s1 = make_float4(Rr[k1].x, Rr[k1].y, Ri[k1].x, Ri[k1].y);
+        const float4 s2 = make_float4(Rr[k2].x, Rr[k2].y, Ri[k2].x, Ri[k2].y);
+        const float4 ms2c = make_float4(-s2.x, -s2.y, s2.z, s2.w);  // -conj(s2)
+        const float4 ms1 = make_float4(-s1.x, -s1.y, -s1.z, -s1.w);  // -s1
+        const float4 s1c = df_conj(s1);
+        const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float4 x11 = A[p1 * m + p2], x12 = v2 ? A[p1 * m + q2] : z;
+        const float4 x21 = v1 ? A[q1 * m + p2] : z, x22 = (v1 && v2) ? A[q1 * m + q2] : z;
+        // Y = X R2: Y[:,0] = c2 X[:,0] - conj(s2) X[:,1], Y[:,1] = s2 X[:,0] + c2 X[:,1]
+        Cacc t11{}, t21{}, t12{}, t22{};
+        cacc_rmad(t11, c2, x11);
+        cacc_mad(t11, ms2c, x12);
+        cacc_rmad(t21, c2, x21);
+        cacc_mad(t21, ms2c, x22);
+        cacc_mad(t12, s2, x11);
+        cacc_rmad(t12, c2, x12);
+        cacc_mad(t22, s2, x21);
+        cacc_rmad(t22, c2, x22);
+        const float4 y11 = cacc_value(t11), y21 = cacc_value(t21), y12 = cacc_value(t12), y22 = cacc_value(t22);
+        // X' = R1^H Y: row 0 = c1 Y0 - s1 Y1, row 1 = conj(s1) Y0 + c1 Y1
+        Cacc u11{}, u12{}, u21{}, u22{};
+        cacc_rmad(u11, c1, y11);
+        cacc_mad(u11, ms1, y21);
+        cacc_rmad(u12, c1, y12);
+        cacc_mad(u12, ms1, y22);
+        cacc_mad(u21, s1c, y11);
+        cacc_rmad(u21, c1, y21);
+        cacc_mad(u22, s1c, y12);
+        cacc_rmad(u22, c1, y22);
+        const float4 n11 = cacc_value(u11), n12 = cacc_value(u12), n21 = cacc_value(u21), n22 = cacc_value(u22);
+        A[p1 * m + p2] = n11;
+        A[p2 * m + p1] = df_conj(n11);
+        if (v2) {
+          A[p1 * m + q2] = n12;
+          A[q2 * m + p1] = df_conj(n12);
+        }
+        if (v1) {
+          A[q1 * m + p2] = n21;
+          A[p2 * m + q1] = df_conj(n21);
+        }
+        if (v1 && v2) {
+          A[q1 * m + q2] = n22;
+          A[q2 * m + q1] = df_conj(n22);
+        }
+      }
+      if (V) {
+        const int work = npair * m;
+        for (int it = lane; it < work; it += G) {  // V <- V J
+          const int k = it / m, r = it - (it / m) * m;
+          const int p = R.p[k], q = R.q[k];
+          if (q >= m || (Rr[k].x == 0.0f && Ri[k].x == 0.0f)) continue;
+          const float2 c = Rc[k];
+          const float4 se = make_float4(Rr[k].x, Rr[k].y, Ri[k].x, Ri[k].y);
+          const float4 mse = make_float4(-se.x, -se.y, se.z, se.w);  // -conj(se)
+          const float4 x = V[r * m + p], y = V[r * m + q];
+          Cacc a{}, b{};
+          cacc_rmad(a, c, x);
+          cacc_mad(a, mse, y);
+          cacc_mad(b, se, x);
+          cacc_rmad(b, c, y);
+          V[r * m + p] = cacc_value(a);
+          V[r * m + q] = cacc_value(b);
+        }
+      }
+      g.sync();
+    }
+  }
+  return sweep;
+}
+
 // Householder reduction to real tridiagonal form in pairs, as householder_tridiag (same steps and
 // lane layout); td, te receive the diagonal and off-diagonal in FP64.  vw: 2 x 32 pair scratch.
 template <int G>
@@ -707,7 +857,7 @@ __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict_
 }
 
 template <int G>
-__global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restrict__ sysv,
+__global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
                                                         unsigned *flags, unsigned long long *counters,
                                                         int max_m0) {
   const SysDev &s = sysv[blockIdx.y];
@@ -798,8 +948,8 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
   }
   for (int o = G / 2; o > 0; o >>= 1) hf2 += __shfl_xor_sync(g.mask, hf2, o);
   g.sync();
-  // mixed route, eigenvalues only: the Cholesky-route reduction in compensated FP32 pairs (A, B
-  // and V then hold float4 pairs in the same bytes); the canonical route and Jacobi stay FP64
+  // mixed route, eigenvalues only: the reduction in compensated FP32 pairs (A, B and V then hold
+  // float4 pairs in the same bytes): Cholesky route, canonical route and Jacobi
   const bool dfp = s.eig_df != 0 && s.tri != nullptr && s.vecs == nullptr;
   float4 *Af = reinterpret_cast<float4 *>(A), *Bf = reinterpret_cast<float4 *>(B), *Vf = reinterpret_cast<float4 *>(V);
   float2 *sgf = reinterpret_cast<float2 *>(sg);  // inverse pivots as pairs (in sg's doubles)
@@ -934,17 +1084,6 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       df_hermitian_part(Af, m, g);
     }
   }
-  if (ok && !chol && a_df) {
-    // the pairs' Cholesky or trace test sent the k-point to the canonical route: the scaled H
-    // again in FP64 (the canonical route gathers the overlap itself)
-    for (int e = lane; e < m * m; e += G) {
-      const int a = e / m, b = e - (e / m) * m;
-      A[e] = cscale(Hb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
-    }
-    g.sync();
-    hermitian_part(A, m, g);
-    a_df = false;
-  }
   if (ok && chol && !dfp) {
     // 2. C = L^{-1} H L^{-H}.  When the FP32 estimate left the decision open, the first pass also
     //    solves L Z = I in FP64 in the columns m .. 2m-1 and ||Z||_F^2 decides: 1 / ||Z||_F^2 >=
@@ -1017,7 +1156,70 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
     }
   }
   const int mkept = m;  // kept functions (rows of the back-transformation)
-  if (ok && !chol) {
+  bool canon64 = ok && !chol;  // canonical route in FP64
+  if (ok && !chol && dfp) {
+    // 2' (pairs).  Canonical orthogonalisation as below, in compensated FP32 pairs: the scaled
+    //     pencil again from the FP64 blocks (the Cholesky attempt overwrote B, the solves A),
+    //     the overlap's eigen-decomposition by Jacobi, X = V_kept diag(sigma)^{-1/2},
+    //     C = X^H H~ X.  An eigenvalue sigma within 1e-3 of kLindepTol leaves the decision to
+    //     the FP64 route, whose rounding is 2^-7 of the pairs'.
+    for (int e = lane; e < m * m; e += G) {
+      const int a = e / m, b = e - (e / m) * m;
+      const double sc = dsc[a] * dsc[b];
+      Af[e] = df_from(cscale(Hb[kidx[a] * m0 + kidx[b]], sc));
+      Bf[e] = df_from(cscale(Sb[kidx[a] * m0 + kidx[b]], sc));
+      Vf[e] = make_float4(a == b ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    g.sync();
+    df_hermitian_part(Af, m, g);
+    df_hermitian_part(Bf, m, g);
+    sweeps += df_jacobi_herm(Bf, Vf, m, g, R);
+    double sig = 0.0;
+    if (lane < m) sig = (double)Bf[lane * m + lane].x + (double)Bf[lane * m + lane].y;
+    const bool near = lane < m && fabs(sig - kLindepTol) < 1e-3 * kLindepTol;
+    if (!g.ballot(near)) {
+      canon64 = false;
+      const bool kp = lane < m && sig >= kLindepTol;
+      const unsigned m2mask = g.ballot(kp);
+      const int m2 = __popc(m2mask);
+      if (kp) {
+        const int b = __popc(m2mask & ((1u << lane) - 1u));
+        kidx2[b] = lane;
+        sgf[b] = df_rsqrt(make_float2(Bf[lane * m + lane].x, Bf[lane * m + lane].y));
+      }
+      g.sync();
+      for (int e = lane; e < m * m2; e += G) {  // X (m x m2) into B
+        const int i = e / m2, b = e - (e / m2) * m2;
+        Bf[e] = df_cscale(Vf[i * m + kidx2[b]], sgf[b]);
+      }
+      g.sync();
+      for (int e = lane; e < m * m2; e += G) {  // W = H~ X (m x m2) into V
+        const int i = e / m2, b = e - (e / m2) * m2;
+        Cacc acc{};
+        for (int k = 0; k < m; ++k) cacc_mad(acc, Af[i * m + k], Bf[k * m2 + b]);
+        Vf[e] = cacc_value(acc);
+      }
+      g.sync();
+      for (int e = lane; e < m2 * m2; e += G) {  // C = X^H W (m2 x m2) into A
+        const int a = e / m2, b = e - (e / m2) * m2;
+        Cacc acc{};
+        for (int k = 0; k < m; ++k) cacc_mad(acc, df_conj(Bf[k * m2 + a]), Vf[k * m2 + b]);
+        Af[e] = cacc_value(acc);
+      }
+      g.sync();
+      m = m2;
+      df_hermitian_part(Af, m, g);
+    } else {
+      a_df = false;
+      for (int e = lane; e < m * m; e += G) {  // the scaled H again in FP64
+        const int a = e / m, b = e - (e / m) * m;
+        A[e] = cscale(Hb[kidx[a] * m0 + kidx[b]], dsc[a] * dsc[b]);
+      }
+      g.sync();
+      hermitian_part(A, m, g);
+    }
+  }
+  if (canon64) {
     // 2'. canonical orthogonalisation: S~ = V diag(sigma) V^H, keep sigma >= kLindepTol,
     //     X = V_kept diag(sigma)^{-1/2}, C = X^H H~ X
     for (int e = lane; e < m * m; e += G) {
@@ -1090,10 +1292,16 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       if (lane == 0) s.tri[(int64_t)widx * (2 * m0 + 1)] = -2.0;  // solved here
     }
   }
-  if (a_df && !tri) {  // Jacobi runs in FP64: C back from its pairs
-    for (int e = lane; e < m * m; e += G) A[e] = df_to(Af[e]);
+  bool jac_done = false;
+  if (a_df && !tri) {  // Jacobi in pairs; the eigenvalues (C's diagonal) back to FP64
+    sweeps += df_jacobi_herm(Af, nullptr, m, g, R);
+    for (int e = lane; e < m; e += G) {
+      const float4 d = Af[e * m + e];
+      A[e * m + e] = make_double2((double)d.x + (double)d.y, 0.0);
+    }
     g.sync();
     a_df = false;
+    jac_done = true;
   }
   if (tri) {
     // 3'. tridiagonal route: Householder reduction here, the tridiagonal eigenvalues by
@@ -1137,7 +1345,7 @@ __global__ void __launch_bounds__(kEigMaxWarps * 32) k_eig(const SysDev *__restr
       }
       g.sync();
     }
-    sweeps += jacobi_herm(A, s.vecs ? V : nullptr, m, g, R);
+    if (!jac_done) sweeps += jacobi_herm(A, s.vecs ? V : nullptr, m, g, R);
     if (lane == 0 && counters) {
       if (!s.tri) atomicAdd(counters, (unsigned long long)sweeps);  // tridiagonal mode counts QR rotations
       atomicAdd(counters + 1, 1ull);
