@@ -13,7 +13,8 @@
 // for S): the last pass transforms only the entries mu <= nu and writes the others as their
 // conjugates (earlier passes of a multi-dimensional lattice still relate entries of different
 // outer indices and transform every entry).  The tile is transformed in shared memory: an iterative radix-2 FFT when
-// L_d is a power of two, otherwise the direct O(L_d^2) sum.  Twiddles come from a per-CTA table
+// L_d is a power of two, Bluestein's chirp transform through radix-2 FFTs of length M >= 2 L_d - 1
+// otherwise (64 <= L_d <= 1024), the direct O(L_d^2) sum for the other lengths.  Twiddles come from a per-CTA table
 // built with sincospi (correctly-rounded arguments).
 #include "lhf_internal.cuh"
 
@@ -29,6 +30,65 @@ __host__ __device__ inline int tile_width(int Ld) {
 }
 
 __device__ inline unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+
+// Bluestein's transform for a length L that is not a power of two: with w_n = exp(-pi i n^2 / L),
+// omega^(j k) = w_j w_k conj(w_(k-j)) (since 2 j k = j^2 + k^2 - (k - j)^2), so
+//   Xbar_k = w_k sum_j (x_j w_j) conj(w_(k-j)),
+// a cyclic convolution of length M (the power of two >= 2 L - 1) taken by radix-2 FFTs:
+// A = F_M(x w) (zero-padded), B = F_M(b) with b_n = conj(w_|n|) at n mod M for |n| < L (the
+// same for every column: once per CTA), Xbar_k = w_k conj(F_M(conj(A B)))_k / M.  O(M log M) per
+// column instead of the direct sum's L^2.  For kBluesteinMinL <= L <= kBluesteinMaxL (M <=
+// 2048; shorter lengths keep the direct sum, as cheap there); the chirp arguments n^2 / L are
+// reduced modulo 2 exactly in integers.
+constexpr int kBluesteinMinL = 64, kBluesteinMaxL = 1024;
+
+__host__ __device__ inline int bluestein_m(int Ld) {
+  if ((Ld & (Ld - 1)) == 0 || Ld < kBluesteinMinL || Ld > kBluesteinMaxL) return 0;
+  int M = 1;
+  while (M < 2 * Ld - 1) M <<= 1;
+  return M;
+}
+
+// Tile width of a transform pass: the columns of one CTA, so that the transformed length (Ld, or
+// Bluestein's M) times the width fits 128 KB of complex values.
+__host__ __device__ inline int pass_tile_width(int Ld) {
+  const int M = bluestein_m(Ld);
+  const int len = M ? M : Ld;
+  int tw = 16;
+  while (tw > 1 && (size_t)len * tw * 2 > 8192) tw >>= 1;
+  return tw;
+}
+
+// Shared memory of a transform pass of length Ld (the tile, the twiddle table; Bluestein: the
+// length-M table, the filter's transform and the chirp).
+__host__ __device__ inline size_t pass_smem_bytes(int Ld) {
+  const int M = bluestein_m(Ld), TW = pass_tile_width(Ld);
+  return sizeof(double2) * (M ? (size_t)M * TW + 2 * (size_t)M + Ld : (size_t)Ld * TW + Ld);
+}
+
+// In-place radix-2 FFT of M positions x TW columns stored bit-reversed (x[j * TW + t]), output in
+// natural order; tab[m] = omega_M^m.  The first two stages' twiddles are 1 and -i.
+__device__ void radix2_columns(double2 *x, int M, int TW, const double2 *tab) {
+  for (int hs = 1; hs < M; hs <<= 1) {
+    const int stride = M / (2 * hs);
+    for (int k = threadIdx.x; k < (M / 2) * TW; k += blockDim.x) {
+      const int t = k % TW, b = k / TW;
+      const int kk = b % hs;
+      const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
+      const double2 u = x[top * TW + t], v = x[bot * TW + t];
+      double2 wv;
+      if (hs <= 2) {
+        wv = kk == 0 ? v : make_double2(v.y, -v.x);  // v or -i v
+      } else {
+        const double2 w = tab[kk * stride];
+        wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
+      }
+      x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
+      x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
+    }
+    __syncthreads();
+  }
+}
 
 __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restrict__ sysv, int d) {
   const SysDev &s = sysv[blockIdx.y];
@@ -60,7 +120,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   const int64_t items = nlat * nup;      // inner items transformed
   int64_t outer = 1;
   for (int q = 0; q < d; ++q) outer *= Ls[q];
-  const int TW = tile_width(Ld);
+  const int TW = pass_tile_width(Ld);
   const int64_t tiles_inner = (items + TW - 1) / TW;
   const int64_t tile = blockIdx.x;
   if (tile >= outer * tiles_inner) return;
@@ -88,6 +148,73 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
     offT_sh[t] = (upper && mu != nu) ? lat * mm + nu * m0 + mu : -1;
   }
   __syncthreads();
+
+  const int Mb = bluestein_m(Ld);
+  if (Mb > 0) {
+    // Bluestein (see bluestein_m): H and S in separate transforms (blockIdx.z)
+    const double *Xr = blockIdx.z == 0 ? s.H : s.S;
+    double *Xc = blockIdx.z == 0 ? s.Hbar : s.Sbar;
+    extern __shared__ double smb[];
+    double2 *x = reinterpret_cast<double2 *>(smb);  // [Mb][TW]
+    double2 *tab = x + (size_t)Mb * TW;             // [Mb] omega_M^m
+    double2 *Bf = tab + Mb;                         // [Mb] F_M(b)
+    double2 *wch = Bf + Mb;                         // [Ld] w_n
+    const int tid = threadIdx.x, bitsM = __ffs(Mb) - 1;
+    for (int m = tid; m < Mb; m += kDftThreads) {
+      double sn, cs;
+      sincospi(2.0 * (double)m / (double)Mb, &sn, &cs);
+      tab[m] = make_double2(cs, -sn);
+    }
+    for (int n = tid; n < Ld; n += kDftThreads) {
+      const long long r = ((long long)n * n) % (2ll * Ld);  // n^2 mod 2L: exp(-pi i n^2 / L) exactly periodic
+      double sn, cs;
+      sincospi((double)r / (double)Ld, &sn, &cs);
+      wch[n] = make_double2(cs, -sn);
+    }
+    __syncthreads();
+    for (int p = tid; p < Mb; p += kDftThreads) {  // b, bit-reversed
+      const int n = p < Ld ? p : (p > Mb - Ld ? Mb - p : -1);
+      Bf[bitrev((unsigned)p, bitsM)] = n >= 0 ? make_double2(wch[n].x, -wch[n].y) : make_double2(0.0, 0.0);
+    }
+    for (int k = tid; k < Mb * TW; k += kDftThreads) {  // a = x w, zero-padded, bit-reversed
+      const int j = k / TW, t = k - j * TW;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < Ld && t < tw_valid) {
+        const int64_t idx = (o * Ld + j) * inner + off_sh[t];
+        const double2 xv = real_in ? make_double2(Xr[idx], 0.0) : reinterpret_cast<const double2 *>(Xc)[idx];
+        const double2 w = wch[j];
+        v = make_double2(xv.x * w.x - xv.y * w.y, xv.x * w.y + xv.y * w.x);
+      }
+      x[bitrev((unsigned)j, bitsM) * TW + t] = v;
+    }
+    __syncthreads();
+    radix2_columns(Bf, Mb, 1, tab);
+    radix2_columns(x, Mb, TW, tab);
+    // conj(A B), moved to bit-reversed order for the second transform (pairs of swapped slots)
+    for (int k = tid; k < Mb * TW; k += kDftThreads) {
+      const int j = k / TW, t = k - j * TW;
+      const int jr = (int)bitrev((unsigned)j, bitsM);
+      if (jr < j) continue;
+      const double2 a = x[j * TW + t], b = Bf[j], a2 = x[jr * TW + t], b2 = Bf[jr];
+      const double2 u = make_double2(a.x * b.x - a.y * b.y, -(a.x * b.y + a.y * b.x));
+      const double2 u2 = make_double2(a2.x * b2.x - a2.y * b2.y, -(a2.x * b2.y + a2.y * b2.x));
+      x[jr * TW + t] = u;
+      x[j * TW + t] = u2;
+    }
+    __syncthreads();
+    radix2_columns(x, Mb, TW, tab);
+    const double invM = 1.0 / (double)Mb;  // a power of two: exact
+    for (int k = tid; k < Ld * TW; k += kDftThreads) {
+      const int kap = k / TW, t = k - kap * TW;
+      if (t >= tw_valid) continue;
+      const double2 z = x[kap * TW + t], w = wch[kap];  // Xbar = w conj(z) / M
+      const double re = invM * (w.x * z.x + w.y * z.y), im = invM * (w.y * z.x - w.x * z.y);
+      const int64_t base = (o * Ld + kap) * inner;
+      reinterpret_cast<double2 *>(Xc)[base + off_sh[t]] = make_double2(re, im);
+      if (offT_sh[t] >= 0) reinterpret_cast<double2 *>(Xc)[base + offT_sh[t]] = make_double2(re, -im);
+    }
+    return;
+  }
 
   const bool pow2 = (Ld & (Ld - 1)) == 0;
   // real first pass of a power-of-two length: H and S in one complex transform of
@@ -408,7 +535,7 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
       for (int q = d + 1; q < 3; ++q) items *= L[q];
       int64_t outer = 1;
       for (int q = 0; q < d; ++q) outer *= L[q];
-      const int TW = tile_width(L[d]);
+      const int TW = pass_tile_width(L[d]);
       const int64_t tiles = outer * ((items + TW - 1) / TW);
       if (tiles > max_tiles) max_tiles = tiles;
       if (L[d] > max_Ld) max_Ld = L[d];
@@ -419,8 +546,8 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
     for (int s = 0; s < nsys; ++s) {
       const int *L = host_L + 4 * s;
       if (L[0] > kDftTileMax) continue;
-      const int Ld = L[d];
-      const size_t need = sizeof(double2) * ((size_t)Ld * tile_width(Ld) + Ld);
+      if (!(L[d] > 1 || (d == 0 && L[0] == 1 && L[1] == 1 && L[2] == 1))) continue;
+      const size_t need = pass_smem_bytes(L[d]);
       if (need > smem) smem = need;
     }
     if (smem > 48 * 1024) {

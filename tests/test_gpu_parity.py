@@ -183,6 +183,42 @@ def test_gram_factors(ctx, oracle_mod, name):
             assert np.abs(C[jw, Rt + 1] - M).max() <= 1e-12 * max(np.abs(M).max(), 1e-300)
 
 
+@pytest.mark.parametrize("L", [75, 97, 130])
+def test_block_dft_bluestein_lengths(ctx, oracle_mod, lhf, L):
+    """Lattice lengths that are not powers of two (75 = 3 5^2, the prime 97, 130 = 2 5 13) take
+    Bluestein's chirp transform through radix-2 FFTs: against the oracle's direct DFT of the same
+    GPU blocks, entry by entry, and Hermitian at every k-point; the whole path's spectra against
+    the oracle's solve of the oracle's transform on the mixed route."""
+    cfg = small_tube(L, seed=20 + L, n_c=16, n_perp=32, m0_s=2, m0_pshell=1)
+    H, S = gpu_blocks(ctx, cfg)
+    m0 = H.shape[-1]
+    Hb = dev(H.shape + (2,))
+    Sb = dev(S.shape + (2,))
+    ctx.circulant_fft(torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda(), Hb, Sb)
+    ctx.sync()
+    Hbg = Hb.cpu().numpy()
+    Sbg = Sb.cpu().numpy()
+    Hbg = Hbg[..., 0] + 1j * Hbg[..., 1]
+    Sbg = Sbg[..., 0] + 1j * Sbg[..., 1]
+    Hb_ref, Sb_ref = oracle_mod.block_dft(H), oracle_mod.block_dft(S)
+    # a transform of L terms of size <= max |X| rounds each output by a few ulps of L max |X|
+    assert np.abs(Hbg - Hb_ref).max() <= 1e-13 * L * np.abs(H).max()
+    assert np.abs(Sbg - Sb_ref).max() <= 1e-13 * L * np.abs(S).max()
+    off = ~np.eye(m0, dtype=bool)  # mirrored entries exactly; the diagonal's imaginary part rounds
+    assert np.array_equal(Hbg[..., off], np.conj(np.swapaxes(Hbg, -1, -2))[..., off])
+    assert np.array_equal(Sbg[..., off], np.conj(np.swapaxes(Sbg, -1, -2))[..., off])
+    eig = dev((L * m0,))
+    ks = dev((L,), torch.int32)
+    ctx.bloch_spectra([cfg], eig, ks, lhf.MIXED)
+    ctx.sync()
+    Hr, Sr = oracle_mod.core_blocks(cfg)
+    Hbr, Sbr = oracle_mod.block_dft(Hr), oracle_mod.block_dft(Sr)
+    ref, st = oracle_mod.k_point_eigenvalues(Hbr, Sbr)
+    assert np.array_equal(ks.cpu().numpy(), st)
+    worst, ratio = check_eigenvalues(eig.cpu().numpy().reshape(L, m0), ref, Hbr, Sbr, Hr, Sr, status=st)
+    assert ratio <= 1.0, (worst, ratio)
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_core_hamiltonian_blocks(ctx, oracle_mod, name):
     cfg = CASES[name]()
