@@ -436,10 +436,21 @@ __global__ void __launch_bounds__(kGramThreads, 4) k_gram_slice(const SysDev *__
     }
   }
   __syncthreads();
-  const int64_t rows = (int64_t)D.Jc * mm;
+  // rows with overlap only (compact index from k_gram_rowmap); the others' rank slots are zeros
+  const int64_t rows = D.rows_c;
   const int64_t row0 = ((int64_t)(it.jw - D.cw0) * m0 + it.mu) * m0;
+  const int *f2c = reinterpret_cast<const int *>(s.ws + D.offRM);
+  __shared__ int crow[kMaxM0];
+  if (tid < m0) crow[tid] = f2c[row0 + tid];
+  {
+    double *Cz = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + it.mu * m0;
+    for (int e = tid; e < Rt * m0; e += kGramThreads) {
+      const int r = e / m0, nu = e - r * m0;
+      if (f2c[row0 + nu] < 0) Cz[(int64_t)r * mm + nu] = 0.0;
+    }
+  }
   if (tid < m0) {
-    reinterpret_cast<int *>(s.ws + D.offRE)[row0 + tid] = rexp[tid];
+    if (crow[tid] >= 0) reinterpret_cast<int *>(s.ws + D.offRE)[crow[tid]] = rexp[tid];
     // P1 slots in pairs, converted once (m0 threads of one warp: one FP64 pass)
     const float2 invh = make_float2(D.p1h[0], D.p1h[1]), h1 = make_float2(D.p1h[2], D.p1h[3]);
     const float2 h6 = make_float2(D.p1h[4], D.p1h[5]);
@@ -454,8 +465,10 @@ __global__ void __launch_bounds__(kGramThreads, 4) k_gram_slice(const SysDev *__
   unsigned short *planes = reinterpret_cast<unsigned short *>(s.ws + D.offA);
   const int half = Kp >> 1;
   const int64_t plane = (int64_t)(Kp / kPlaneChunk) * rows * kPlaneChunk;  // = rows * Kp
+  __syncthreads();  // crow
   for (int p0 = tid; p0 < m0 * half; p0 += kGramThreads) {
     const int nu = p0 / half, c = 2 * (p0 - nu * half);
+    if (crow[nu] < 0) continue;  // warp-uniform: a warp's 64 columns share nu
     const float sc = __int_as_float((127 - rexp[nu]) << 23);  // 2^-e, e in [-126, 126]
     float a[kSlices], b[kSlices];
 #pragma unroll
@@ -468,12 +481,53 @@ __global__ void __launch_bounds__(kGramThreads, 4) k_gram_slice(const SysDev *__
       const float2 q = Qp[nu * ld + c + 1];
       digits7f(__fmul_rn(q.x, sc), __fmul_rn(q.y, sc), b);
     }
-    const int64_t at = ((int64_t)(c / kPlaneChunk) * rows + row0 + nu) * kPlaneChunk + c % kPlaneChunk;
+    const int64_t at = ((int64_t)(c / kPlaneChunk) * rows + crow[nu]) * kPlaneChunk + c % kPlaneChunk;
     // BF16 of an integer-valued float of at most 8 significant bits: its upper half, exact
 #pragma unroll
     for (int k = 0; k < kSlices; ++k)
       *reinterpret_cast<unsigned *>(planes + k * plane + at) =
           (__float_as_uint(a[k]) >> 16) | (__float_as_uint(b[k]) & 0xffff0000u);
+  }
+}
+
+// The rows with overlap (gram_row_cells > 0) of one direction's contracted window, in row order:
+// full -> compact index (-1 for a row whose folded products vanish identically), compact -> full.
+// One CTA per (system, direction), rows in rounds of the block: a ballot per warp, the warps'
+// counts prefixed through shared memory.
+__global__ void __launch_bounds__(kGramThreads) k_gram_rowmap(const SysDev *__restrict__ sysv) {
+  const SysDev &s = sysv[blockIdx.y];
+  const int l = blockIdx.x;
+  if (s.box || l > 2) return;
+  const DirDev &D = s.d[l];
+  if (D.Jc <= 0 || D.offRM < 0) return;
+  const int m0 = s.m0, mm = m0 * m0, rows = D.Jc * mm;
+  int *f2c = reinterpret_cast<int *>(s.ws + D.offRM), *c2f = f2c + rows;
+  __shared__ int wcount[kGramThreads / 32];
+  __shared__ int base_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) base_sh = 0;
+  __syncthreads();
+  for (int r0 = 0; r0 < rows; r0 += kGramThreads) {
+    const int row = r0 + tid;
+    bool nz = false;
+    if (row < rows) {
+      const int jc = row / mm, mu = (row / m0) % m0, nu = row % m0;
+      nz = gram_row_cells(s, l, D.jlo + D.cw0 + jc, mu, nu) > 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int before = base_sh;
+    for (int w = 0; w < warp; ++w) before += wcount[w];
+    const int k = before + __popc(bal & ((1u << lane) - 1u));
+    if (row < rows) {
+      f2c[row] = nz ? k : -1;
+      if (nz) c2f[k] = row;
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 0; w < kGramThreads / 32; ++w) base_sh += wcount[w];
+    __syncthreads();
   }
 }
 
@@ -580,7 +634,7 @@ cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int ma
 }
 
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
-                               int ldir) {
+                               int ldir, bool rowmap) {
   if (max_blocks <= 0 || nsys <= 0) return cudaSuccess;
   const size_t smem = sizeof(float2) * (size_t)max_m0 * (max_nv + 1);
   if (smem > 48 * 1024) {
@@ -589,6 +643,8 @@ cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int 
     if (e != cudaSuccess) return e;
   }
   kmark(LHF_K_GRAM_SLICE, 1, st);
+  // the row map, once, inside the first slicing launch's bracket (it precedes every slicing launch)
+  if (rowmap) k_gram_rowmap<<<dim3(3, nsys), kGramThreads, 0, st>>>(sys);
   k_gram_slice<<<dim3(max_blocks, nsys), kGramThreads, smem, st>>>(sys, ldir);
   kmark(LHF_K_GRAM_SLICE, 0, st);
   return cudaGetLastError();

@@ -1,7 +1,9 @@
 // k_gram_tc.cu -- step a3 on the tensor cores (LHF_MIXED): the weighted 1D Gram contraction
 // C_r[row] = sum_c V_r(c) Q_row(c) of the folded products Q (rows = (window block, mu, nu))
 // with the potential factors V, from the exact base-2^7 digit planes written by k_gram_slice /
-// k_vslice (k_gram.cu).
+// k_vslice (k_gram.cu).  Only the rows whose functions overlap somewhere (gram_row_cells > 0;
+// 41% of tube_256's direction-0 rows) are contracted, in the compact order of k_gram_rowmap; the
+// results go to their rows through its map, the other rows' factors are zeros.
 //
 // With row = 2^e_row sum_a alpha_a 2^(-7(a+1)) and V_r = 2^e_r sum_b beta_b 2^(-7(b+1)) (digits
 // alpha, beta integers with |.| <= 128), the contraction is
@@ -65,6 +67,8 @@ struct TcArgs {  // per (system, direction)
   double *C;
   const int *rowexp;
   const int *colexp;
+  const int *c2f;   // compact row -> row of the contracted window (rows with overlap only)
+  int rows_full;    // rows of the contracted window, Jc m0^2
   int rows, Kpad, Rt, m0;
 };
 
@@ -294,10 +298,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const TcJob jb = jobs[job];
       const TcArgs &P = args[jb.sys * 3 + jb.l];
-      const int row = jb.row0 + quad * 32 + lane;
+      const int row = jb.row0 + quad * 32 + lane;  // compact row
       const int mm = P.m0 * P.m0;
       const int er = row < P.rows ? P.rowexp[row] : 0;
-      double *Crow = P.C + (int64_t)(row / mm) * (P.Rt + 2) * mm + (row % mm);
+      int frow = row < P.rows ? P.c2f[row] : -1;
+      if (frow < 0 || frow >= P.rows_full) frow = -1;  // (a map entry out of range writes nothing)
+      double *Crow = P.C + (int64_t)(frow < 0 ? 0 : frow / mm) * (P.Rt + 2) * mm + (frow < 0 ? 0 : frow % mm);
       for (int cc = half * (kTileN / 32); cc < (half + 1) * (kTileN / 32); ++cc) {
         uint32_t v[kSlices][16];
 #pragma unroll
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const TcJob *__restri
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tmem_empty)) : "memory");
         }
-        if (row < P.rows) {
+        if (frow >= 0) {
 #pragma unroll
           for (int t = 0; t < 16; ++t) {
             const int n = jb.n0 + cc * 16 + t;
@@ -380,7 +386,7 @@ size_t gram_tc_args_bytes(const SysDev *host_sys, int nsys) {
   for (int i = 0; i < nsys; ++i)
     for (int l = 0; l < 3; ++l) {
       const DirDev &D = host_sys[i].d[l];
-      const size_t rows = (size_t)D.Jc * host_sys[i].m0 * host_sys[i].m0;
+      const size_t rows = (size_t)D.rows_c;
       jobs += ((rows + kTileM - 1) / kTileM) * ((host_sys[i].Rt + kTileN - 1) / kTileN);
     }
   return (size_t)nsys * 3 * sizeof(TcArgs) + jobs * sizeof(TcJob) + 256;
@@ -395,8 +401,12 @@ cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, si
     const SysDev &s = host_sys[i];
     for (int l = 0; l < 3; ++l) {
       const DirDev &D = s.d[l];
-      const int rows = D.Jc * s.m0 * s.m0;  // the contracted window blocks cw0 .. cw0 + Jc - 1
-      if (D.Kpad % kChunkK != 0 || D.Kpad > 448 || rows < 1) return cudaErrorNotSupported;
+      // the rows with overlap of the contracted window blocks cw0 .. cw0 + Jc - 1 (the others'
+      // factors are zeros, written by k_gram_slice)
+      const int rows = D.rows_c;
+      if (D.Jc < 1) return cudaErrorNotSupported;
+      if (rows < 1) continue;
+      if (D.Kpad % kChunkK != 0 || D.Kpad > 448) return cudaErrorNotSupported;
       TcArgs &a = args[(size_t)i * 3 + l];
       if (!encode_planes(&a.mapA, s.ws + D.offA, D.Kpad, rows, kTileM) ||
           !encode_planes(&a.mapB, s.ws + D.offB, D.Kpad, s.Rt, kTileN))
@@ -404,6 +414,8 @@ cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, si
       a.C = s.ws + D.offC + (size_t)D.cw0 * (s.Rt + 2) * s.m0 * s.m0;
       a.rowexp = reinterpret_cast<const int *>(s.ws + D.offRE);
       a.colexp = reinterpret_cast<const int *>(s.ws + D.offCE);
+      a.c2f = reinterpret_cast<const int *>(s.ws + D.offRM) + (size_t)D.Jc * s.m0 * s.m0;
+      a.rows_full = D.Jc * s.m0 * s.m0;
       a.rows = rows;
       a.Kpad = D.Kpad;
       a.Rt = s.Rt;

@@ -460,7 +460,8 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     if (D.J > 0) P.nv_max = std::max(P.nv_max, D.nv);  // rows contracted by the Gram kernels
   }
   for (int l = 0; l < 3; ++l) {
-    sd.d[l].offGD = -1;
+    sd.d[l].offGD = sd.d[l].offRM = -1;
+    sd.d[l].rows_c = 0;
     sd.d[l].offG = (int64_t)off;
     off = align_up(off + (size_t)m0 * (sd.d[l].n + sd.d[l].gext));
     if (sd.d[l].gext == 0 && sd.d[l].J > 0) {  // differences for the P1 forms of the Gram kernels
@@ -509,6 +510,12 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
       off = align_up(off + (lhf::kSlices * (size_t)Rt * D.Kpad * 2 + 7) / 8);
       D.offRE = (int64_t)off;
       off = align_up(off + (rows * 4 + 7) / 8);
+      D.offRM = (int64_t)off;
+      off = align_up(off + (2 * rows * 4 + 7) / 8);
+      D.rows_c = 0;
+      for (int jc = 0; jc < D.Jc; ++jc)
+        for (int mu = 0; mu < m0; ++mu)
+          for (int nu = 0; nu < m0; ++nu) D.rows_c += lhf::gram_row_cells(sd, l, D.jlo + D.cw0 + jc, mu, nu) > 0;
       D.offCE = (int64_t)off;
       off = align_up(off + ((size_t)Rt * 4 + 7) / 8);
       if (D.Kpad > 448) return c->fail(LHF_ERR_UNSUPPORTED, "mixed precision: direction %d has %d nodes per contraction (limit 448)", l, D.nv);
@@ -683,7 +690,8 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
   c->begin(2);
   for (int l = 0; l < 3 && st == LHF_OK; ++l)
     if (dir_blocks[l] > 0) {
-      st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, dir_blocks[l], max_m0, dir_nv[l], c->stream, l),
+      st = c->cuda(lhf::launch_gram_slices(c->d_sys, nsys, dir_blocks[l], max_m0, dir_nv[l], c->stream, l,
+                                           gram_launches == 0),
                    "digit-plane kernel");
       ++gram_launches;
     }

@@ -59,6 +59,9 @@ struct DirDev {
   int64_t offA;   // BF16 [kSlices][Kpad / 32][Jc m0 m0][32] digit planes of the folded products
   int64_t offB;   // BF16 [kSlices][Kpad / 32][Rt][32] digit planes of the potential factors
   int64_t offRE;  // int [Jc m0 m0] row scale exponents
+  int64_t offRM;  // int [2][Jc m0 m0] rows with overlap: full -> compact index (-1: none), compact -> full
+  int rows_c;     // rows (window block, mu, nu) whose functions overlap: the tensor-core route's rows
+  int pad3_;
   int64_t offCE;  // int [Rt] potential-row scale exponents
   int64_t offF;   // k-space route: complex [L][Rt+2][m0][m0] 1D DFTs of the factors (0 when unused)
 };
@@ -108,6 +111,29 @@ struct SysDev {
   int64_t offPC;          // potential row constants [3][R][kPotConst] (k_pot_rows, read by k_potential)
   const double *zcell;    // box charges [L0][M0] (device) or null
 };
+
+// Cells p where the copy of mu shifted by the window displacement j and nu overlap (the runs of
+// the Gram's fold): [plo, phi] (nu's support, at most L cells) against the images of [mlo, mhi]
+// modulo L; a single open cell overlaps itself.  The same integers on host and device.
+__host__ __device__ inline int gram_row_cells(const SysDev &s, int l, int j, int mu, int nu) {
+  const DirDev &D = s.d[l];
+  if (!D.periodic) return 1;
+  const int L = D.L;
+  const int mlo = s.cell_lo[l][mu] + j, mhi = s.cell_hi[l][mu] + j;
+  const int plo = s.cell_lo[l][nu];
+  int phi = s.cell_hi[l][nu];
+  if (phi > plo + L - 1) phi = plo + L - 1;
+  if (mhi - mlo >= L - 1) return phi - plo + 1;
+  const int a = plo - mhi + L - 1;
+  const int k0 = a >= 0 ? a / L : -((-a + L - 1) / L);
+  int cells = 0;
+  for (int k = k0; k <= k0 + 1; ++k) {
+    const int lo = plo > mlo + k * L ? plo : mlo + k * L;
+    const int hi = phi < mhi + k * L ? phi : mhi + k * L;
+    if (hi >= lo) cells += hi - lo + 1;
+  }
+  return cells;
+}
 
 // 2^e as a double from its exponent field (normal range), else by ldexp.
 __device__ __forceinline__ double pow2(int e) {
@@ -198,8 +224,10 @@ cudaError_t launch_potential(const SysDev *sys, int nsys, int max_rows, cudaStre
 // (max_blocks, max_nv then over that direction: the shared memory fits its rows), -1 takes all.
 cudaError_t launch_gram_fp64(const SysDev *sys, int nsys, int max_blocks, int max_m0,
                              int max_nv, cudaStream_t st, int ldir = -1);
+// With rowmap, the launch first maps the rows with overlap of every direction (k_gram_rowmap: the
+// tensor-core route contracts only those); the first slicing launch of a step takes it.
 cudaError_t launch_gram_slices(const SysDev *sys, int nsys, int max_blocks, int max_m0, int max_nv, cudaStream_t st,
-                               int ldir = -1);
+                               int ldir, bool rowmap);
 // Digit planes of the potential factors: one CTA per (direction, rank term), max_rt3 = 3 R_tot.
 cudaError_t launch_vslices(const SysDev *sys, int nsys, int max_rt3, cudaStream_t st);
 // Rank reduction (k_rank.cu), one CTA per system with rank_eps > 0, after the transverse Grams
