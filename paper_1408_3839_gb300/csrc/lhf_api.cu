@@ -83,6 +83,11 @@ struct lhf_ctx {
   SysDev *h_sys = nullptr;  // pinned staging
   size_t h_sys_cap = 0;
   cudaEvent_t upload_done = nullptr;
+  // the mixed route's potential runs on a side stream, beside the basis samples and the fold
+  // (they do not depend on it): forked after the upload, joined before its digit planes
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool join_pending = false;
   unsigned *d_flags = nullptr;
   unsigned long long *d_counters = nullptr;  // [0] Jacobi sweeps, [1] matrices, [2] canonical route
   double *d_zcell = nullptr;
@@ -154,16 +159,16 @@ struct lhf_ctx {
     }
     return e;
   }
-  void begin(int stage) {
+  void begin(int stage, cudaStream_t st = nullptr) {
     if (!prof) return;
     open_mark = {stage, take_event(), take_event(), 0};
-    if (open_mark.a) cudaEventRecord(open_mark.a, stream);
+    if (open_mark.a) cudaEventRecord(open_mark.a, st ? st : stream);
     lhf::kclock = {this, &lhf_ctx::kernel_mark};
   }
-  void end(int kernels = 1) {
+  void end(int kernels = 1, cudaStream_t st = nullptr) {
     lhf::kclock = {nullptr, nullptr};
     if (!prof || open_mark.stage < 0) return;
-    if (open_mark.b) cudaEventRecord(open_mark.b, stream);
+    if (open_mark.b) cudaEventRecord(open_mark.b, st ? st : stream);
     open_mark.kernels = kernels;
     if (open_mark.a && open_mark.b) marks.push_back(open_mark);
     open_mark = {-1, nullptr, nullptr, 0};
@@ -181,6 +186,12 @@ struct lhf_ctx {
   lhf_status cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return LHF_OK;
     return fail(LHF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+  // the main stream waits for the side stream's work (a no-op when nothing was forked)
+  lhf_status join() {
+    if (!join_pending) return LHF_OK;
+    join_pending = false;
+    return cuda(cudaStreamWaitEvent(stream, join_ev, 0), "cudaStreamWaitEvent");
   }
 };
 
@@ -695,6 +706,8 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
                    "digit-plane kernel");
       ++gram_launches;
     }
+  const lhf_status sj = c->join();  // the potential rows, for their digit planes
+  if (st == LHF_OK) st = sj;
   if (st == LHF_OK) st = c->cuda(lhf::launch_vslices(c->d_sys, nsys, 3 * max_rt, c->stream), "digit-plane kernel");
   c->end(gram_launches + 1);
   if (st != LHF_OK) return st;
@@ -745,31 +758,49 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
 
 // Launch a1..a5 for the uploaded systems (H, S already set in the descriptors).
 // a1, a2 and the Gram factors (with the rank reduction when planned), without the rank sum.
-lhf_status run_assembly_factors(lhf_ctx *c, const std::vector<Plan> &ps) {
+// a1, a2 and the Gram factors.  On the mixed route the potential rows (FP64-bound) run on the
+// side stream beside the basis samples and the fold into digit planes (FP32- and ALU-bound),
+// which do not read them; the main stream waits for them before their own digit planes.  A CUDA
+// graph captured over this records the two as parallel branches.
+lhf_status run_factors_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
-  c->begin(0);
-  lhf_status st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
-  c->end();
-  if (st != LHF_OK) return st;
-  c->begin(1);
-  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
-  c->end();
-  if (st != LHF_OK) return st;
-  return run_gram(c, ps, false);
-}
-
-lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
-  const int nsys = (int)ps.size();
-  lhf_status st;  // (a6, the zero blocks outside the window, is written by the rank-sum kernel)
+  const bool fork = ps[0].mixed && c->side;
+  lhf_status st = LHF_OK;
+  if (fork) {
+    st = c->cuda(cudaEventRecord(c->fork_ev, c->stream), "cudaEventRecord");
+    if (st == LHF_OK) st = c->cuda(cudaStreamWaitEvent(c->side, c->fork_ev, 0), "cudaStreamWaitEvent");
+    if (st != LHF_OK) return st;
+    c->begin(1, c->side);
+    st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->side), "potential kernel");
+    c->end(1, c->side);
+    // the join is recorded whatever the launch returned: the main stream never runs ahead of it
+    const lhf_status sr = c->cuda(cudaEventRecord(c->join_ev, c->side), "cudaEventRecord");
+    if (sr != LHF_OK) return sr;
+    c->join_pending = true;
+    if (st != LHF_OK) {
+      c->join();
+      return st;
+    }
+  }
   c->begin(0);
   st = c->cuda(lhf::launch_basis(c->d_sys, nsys, max_of(ps, &Plan::basis_items), c->stream), "basis kernel");
   c->end();
-  if (st != LHF_OK) return st;
-  c->begin(1);
-  st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
-  c->end();
-  if (st != LHF_OK) return st;
-  st = run_gram(c, ps, false);
+  if (st == LHF_OK && !fork) {
+    c->begin(1);
+    st = c->cuda(lhf::launch_potential(c->d_sys, nsys, max_of(ps, &Plan::pot_rows), c->stream), "potential kernel");
+    c->end();
+  }
+  if (st == LHF_OK) st = run_gram(c, ps, false);
+  const lhf_status sj = c->join();
+  return st != LHF_OK ? st : sj;
+}
+
+lhf_status run_assembly_factors(lhf_ctx *c, const std::vector<Plan> &ps) { return run_factors_gram(c, ps); }
+
+lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
+  const int nsys = (int)ps.size();
+  // (a6, the zero blocks outside the window, is written by the rank-sum kernel)
+  lhf_status st = run_factors_gram(c, ps);
   if (st != LHF_OK) return st;
   c->begin(3);
   const int rgroup = max_of(ps, &Plan::rank_group);
@@ -1038,6 +1069,9 @@ lhf_status lhf_create(lhf_ctx **out, int device, void *stream) {
   c->stream = (cudaStream_t)stream;
   if (cudaSetDevice(device) != cudaSuccess || cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->tc_copied, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&c->d_flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->d_flags, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_counters, 3 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -1045,6 +1079,9 @@ lhf_status lhf_create(lhf_ctx **out, int device, void *stream) {
     cudaGetLastError();
     if (c->upload_done) cudaEventDestroy(c->upload_done);
     if (c->tc_copied) cudaEventDestroy(c->tc_copied);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->d_flags) cudaFree(c->d_flags);
     if (c->d_counters) cudaFree(c->d_counters);
     delete c;
@@ -1070,6 +1107,9 @@ void lhf_destroy(lhf_ctx *c) {
   if (c->tc_host) cudaFreeHost(c->tc_host);
   if (c->upload_done) cudaEventDestroy(c->upload_done);
   if (c->tc_copied) cudaEventDestroy(c->tc_copied);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   for (auto &m : c->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
