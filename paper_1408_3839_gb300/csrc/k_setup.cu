@@ -450,9 +450,8 @@ __device__ double poisson_weight(int n, double s, double h, double b) {
   return g * (2.0 * b / (kPi * n)) * sinpi(n * h / b);
 }
 
-__device__ double image_sum_poisson(double pref, double lo, double hi, double c0, double invb, const double *pw, int N) {
-  const double h = hi - lo, xm = 0.5 * (lo + hi);
-  const double c1 = cospi(2.0 * (xm - c0) * invb);
+__device__ double image_sum_poisson(double pref, double h, double xc, double invb, const double *pw, int N) {
+  const double c1 = cospi(2.0 * xc * invb);  // xc: cell midpoint minus c0
   double acc = h, cm = 1.0, cn = c1;  // cos((n-1) theta), cos(n theta)
   for (int n = 1; n <= N; ++n) {
     acc = fma(pw[n], cn, acc);
@@ -465,9 +464,21 @@ __device__ double image_sum_poisson(double pref, double lo, double hi, double c0
 
 // Row constants per (system, direction l, sinc node q), a warp each (they depend on t_q, h_l and
 // b_l only, not on the nucleus): PC[0] = J, PC[1 + i] = b_i (i <= J), PC[18 + k] = the
-// Euler-Maclaurin coefficients (k <= kEmDeg), PC[38 + n] = the Poisson weights (n <= NP).
-static_assert(1 + (kTaylorMaxJ + 1) + (kEmDeg + 1) + (kPoissonMaxN + 1) <= kPotConst, "row constants");
+// Euler-Maclaurin coefficients (k <= kEmDeg), PC[38 + n] = the Poisson weights (n <= NP), then
+// the row's scalars (t, 1/t, the reach 10/t, delta = t h, s = t b, 1/b, 1/h, 1/(t b), the
+// Poisson prefactor sqrt(pi)/(t b)) and its branch flags as an integer bit pattern: formed once
+// here instead of by every thread of every row of k_potential (an FP64 division is a sequence of
+// FP64 instructions, and this GPU charges each per warp).
 constexpr int kPcBc = 1, kPcEm = kPcBc + kTaylorMaxJ + 1, kPcPw = kPcEm + kEmDeg + 1;
+constexpr int kPcT = kPcPw + kPoissonMaxN + 1, kPcInvT = kPcT + 1, kPcReach = kPcT + 2, kPcDelta = kPcT + 3,
+              kPcSb = kPcT + 4, kPcInvB = kPcT + 5, kPcInvH = kPcT + 6, kPcInvS = kPcT + 7, kPcPref = kPcT + 8,
+              kPcFlags = kPcT + 9;
+static_assert(kPcFlags < kPotConst, "row constants");
+// flags: bit 0 Taylor cells, bit 1 Euler-Maclaurin row, bit 2 Poisson row, bits 8.. NP, bits 16.. J
+__device__ __forceinline__ double pot_flags(bool taylor, bool em_row, bool poisson_row, int NP, int J) {
+  return __longlong_as_double((long long)taylor | ((long long)em_row << 1) | ((long long)poisson_row << 2) |
+                              ((long long)NP << 8) | ((long long)J << 16));
+}
 
 __global__ void __launch_bounds__(64) k_pot_rows(const SysDev *__restrict__ sysv) {
   // a warp per row (lane i: series coefficient i, Euler-Maclaurin coefficient i, Poisson weight i)
@@ -487,7 +498,20 @@ __global__ void __launch_bounds__(64) k_pot_rows(const SysDev *__restrict__ sysv
   double *bc = bcs[threadIdx.x >> 5];
   if (lane <= kTaylorMaxJ) bc[lane] = (taylor && lane <= J) ? taylor_coef(lane, J, 0.5 * delta) : 0.0;
   __syncwarp();
-  if (lane == 0) pc[0] = (double)J;
+  if (lane == 0) {
+    pc[0] = (double)J;
+    const double invt = 1.0 / t, invb = 1.0 / D.b;
+    pc[kPcT] = t;
+    pc[kPcInvT] = invt;
+    pc[kPcReach] = 10.0 * invt;
+    pc[kPcDelta] = delta;
+    pc[kPcSb] = sb;
+    pc[kPcInvB] = invb;
+    pc[kPcInvH] = 1.0 / D.h;
+    pc[kPcInvS] = invt * invb;
+    pc[kPcPref] = 1.7724538509055160273 * invt * invb;
+    pc[kPcFlags] = pot_flags(taylor, em_row, poisson_row, NP, J);
+  }
   if (lane <= kTaylorMaxJ) pc[kPcBc + lane] = bc[lane];
   if (em_row) {
     em_poly_warp(bc, J, sb, pc + kPcEm);
@@ -519,97 +543,117 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const SysDev *__restr
   const int nch = (D.nv + kPotChunk - 1) / kPotChunk;
   const int r = bidx / nch, chunk = bidx - r * nch;
   const int nu = r / s.R, q = r - nu * s.R;
-  const double t = s.t[q];
   const double c0 = s.a[nu][l];
-  const double invt = 1.0 / t, invb = 1.0 / D.b, invZ = 1.0 / s.Z[nu];  // the row's reciprocals
-  const double reach = 10.0 * invt;
-  const double delta = t * D.h, sb = t * D.b;
-  const bool taylor = delta <= kTaylorMaxDelta;
   const double *pc = s.ws + s.offPC + (int64_t)(l * s.R + q) * kPotConst;
-  const int J = (int)pc[0];
-  const bool em_row = D.periodic && taylor && sb <= kEmMaxS && J <= kEmJ;
-  const bool poisson_row = D.periodic && sb < kPoissonMaxS;
-  const int NP = poisson_row ? min((int)ceil(2.16 * sb) + 1, kPoissonMaxN) : 0;
-  __shared__ double rowc[kPotConst];
-  const double *bc = rowc + kPcBc, *emc = rowc + kPcEm, *pw = rowc + kPcPw;
   const int tid = threadIdx.x;
+  const int ibeg = chunk * kPotChunk, iend = min(D.nv, ibeg + kPotChunk);
+  const double base = D.periodic ? D.cell0 : D.x0;  // left edge of cell 0
+  // Per-row scalars in shared memory.  Thread 0 forms the few that depend on the nucleus, in
+  // FP64 once per CTA: the cell midpoints relative to c0, xc_i = xc0 + i h; the image range of
+  // cell i (images k with c0 + k b within the reach of the cell) as FP32 affine functions of i,
+  // k in [ceil(flo + i fst), floor(fhi + i fst)] -- an image whose distance rounds across the
+  // reach lies exp(-100) below the nearest one, so its inclusion does not matter; a single open
+  // cell row's cells within reach of c0, ilo .. ihi.  Threads 1 .. kPotRun form the run table of
+  // the single open cell rows, U_j = exp(-(delta j)^2).
+  __shared__ double rowc[kPotConst];
+  __shared__ double xc0_sh, invZ_sh, U[kPotRun];
+  __shared__ float flo_sh, fhi_sh, fst_sh;
+  __shared__ int ilo_sh, ihi_sh;
   if (tid < kPotConst) rowc[tid] = pc[tid];
+  if (tid == 0) {
+    const double reach = pc[kPcReach], invb = pc[kPcInvB], invh = pc[kPcInvH];
+    xc0_sh = (base - c0) + 0.5 * D.h;
+    flo_sh = (float)((base - reach - c0) * invb);
+    fhi_sh = (float)((base + D.h + reach - c0) * invb);
+    fst_sh = (float)(D.h * invb);
+    // cell i within reach: base + i h - reach <= c0 <= base + (i + 1) h + reach
+    const double lo_f = ceil((c0 - reach - base) * invh - 1.0), hi_f = floor((c0 + reach - base) * invh);
+    ilo_sh = lo_f < (double)ibeg ? ibeg : (lo_f > (double)iend ? iend : (int)lo_f);
+    ihi_sh = hi_f >= (double)iend ? iend - 1 : (hi_f < (double)ibeg - 1.0 ? ibeg - 1 : (int)hi_f);
+    invZ_sh = D.lattice ? 1.0 / s.Z[nu] : 1.0;
+  } else if (tid <= kPotRun && !D.periodic && !D.lattice) {
+    const double dj = pc[kPcDelta] * (tid - 1);
+    U[tid - 1] = exp(-dj * dj);
+  }
   __syncthreads();
+  const double *bc = rowc + kPcBc, *emc = rowc + kPcEm, *pw = rowc + kPcPw;
+  const double t = rowc[kPcT], invt = rowc[kPcInvT], invb = rowc[kPcInvB];
+  const long long fl = __double_as_longlong(rowc[kPcFlags]);
+  const bool taylor = (fl & 1) != 0, em_row = (fl & 2) != 0, poisson_row = (fl & 4) != 0;
+  const int NP = (int)((fl >> 8) & 0xff), J = (int)((fl >> 16) & 0xff);
+  const int ilo = ilo_sh, ihi = ihi_sh;
+  const double xc0 = xc0_sh;
+  const float flo = flo_sh, fhi = fhi_sh, fst = fst_sh;
 
   double *out = s.ws + D.offV + (int64_t)r * D.nv;
-  const int iend = min(D.nv, (chunk + 1) * kPotChunk);
-  if (!D.periodic && !D.lattice && taylor) {
-    // a single open cell row of narrow cells: exp(-m^2) S(m^2) / t at the cell centres, m_j =
-    // m_0 + j delta along a run of kPotRun cells, exp(-m_j^2) = exp(-m_0^2) E^j U_j with E =
-    // exp(-2 m_0 delta), U_j = exp(-delta^2 j^2) (|m| <= 10 + kPotRun delta within reach: no
-    // underflow); cells beyond reach stay exact zeros
-    __shared__ double U[kPotRun];
-    if (tid < kPotRun) U[tid] = exp(-(delta * tid) * (delta * tid));
-    __syncthreads();
-    for (int i0 = chunk * kPotChunk + kPotRun * tid; i0 < iend; i0 += kPotRun * kPotThreads) {
-      const double m0 = t * (D.x0 + (i0 + 0.5) * D.h - c0);
+  if (!D.periodic && !D.lattice) {
+    // a single open cell row: cells ilo .. ihi within reach, exact zeros elsewhere
+    for (int i = ibeg + tid; i < iend; i += kPotThreads)
+      if (i < ilo || i > ihi) out[i] = 0.0;
+    if (!taylor) {
+      for (int i = ilo + tid; i <= ihi; i += kPotThreads) {
+        const double lo = D.x0 + i * D.h;
+        out[i] = gauss_cell_integral(t, invt, lo, lo + D.h, c0);
+      }
+      return;
+    }
+    // narrow cells: exp(-m^2) S(m^2) / t at the cell centres, m_j = m_0 + j delta along a run of
+    // kPotRun cells, exp(-m_j^2) = exp(-m_0^2) E^j U_j with E = exp(-2 m_0 delta) (|m| <= 10 +
+    // kPotRun delta within reach: no underflow)
+    const double delta = rowc[kPcDelta];
+    for (int i0 = ilo + kPotRun * tid; i0 <= ihi; i0 += kPotRun * kPotThreads) {
+      const double m0 = t * (xc0 + i0 * D.h);
       const double g0 = exp(-m0 * m0), E = exp(-2.0 * m0 * delta);
+      const double gt = g0 * invt;
       double P = 1.0;
 #pragma unroll
       for (int j = 0; j < kPotRun; ++j) {
         const int i = i0 + j;
-        if (i >= iend) break;
-        const double lo = D.x0 + i * D.h, hi = lo + D.h;
-        double v = 0.0;
-        if (lo - reach <= c0 && c0 <= hi + reach) {
-          const double m = m0 + j * delta;
-          v = g0 * P * U[j] * taylor_S(bc, J, m * m) * invt;
-        }
-        out[i] = v;
+        if (i > ihi) break;
+        const double m = fma((double)j, delta, m0);
+        out[i] = gt * P * U[j] * taylor_S(bc, J, m * m);
         P *= E;
       }
     }
     return;
   }
-  for (int i = chunk * kPotChunk + tid; i < iend; i += kPotThreads) {
+  for (int i = ibeg + tid; i < iend; i += kPotThreads) {
     double v = 0.0;
+    const double xc = fma((double)i, D.h, xc0);  // cell midpoint - c0
+    const float fi = (float)i;
+    const float kf_lo = ceilf(fmaf(fi, fst, flo)), kf_hi = floorf(fmaf(fi, fst, fhi));
     if (D.periodic) {
-      const double lo = D.cell0 + i * D.h, hi = lo + D.h;
       const int kmax = D.K / 2;
       const bool even = (D.K % 2) == 0;
-      const double klo_f = ceil((lo - reach - c0) * invb), khi_f = floor((hi + reach - c0) * invb);
-      const int klo = (klo_f < -kmax) ? -kmax : (int)klo_f;
-      const int khi = (khi_f > kmax) ? kmax : (int)khi_f;
-      const double xc = 0.5 * (lo + hi) - c0;
+      // (clamped on both sides before the conversion: an empty range stays empty)
+      const int klo = kf_lo < (float)-kmax ? -kmax : (kf_lo > (float)(kmax + 1) ? kmax + 1 : (int)kf_lo);
+      const int khi = kf_hi > (float)kmax ? kmax : (kf_hi < (float)(-kmax - 1) ? -kmax - 1 : (int)kf_hi);
       if (poisson_row && klo > -kmax && khi < kmax) {
-        v = image_sum_poisson(1.7724538509055160273 * invt * invb, lo, hi, c0, invb, pw, NP);
+        v = image_sum_poisson(rowc[kPcPref], D.h, xc, invb, pw, NP);
       } else if (em_row && khi - klo >= 16) {
-        v = image_sum_em(t, xc, D.b, invt * invb, bc, J, emc, klo, khi, kmax, even) * invt;
+        v = image_sum_em(t, xc, D.b, rowc[kPcInvS], bc, J, emc, klo, khi, kmax, even) * invt;
       } else if (taylor) {
         v = image_sum_taylor(t, xc, D.b, invb, bc, J, klo, khi, kmax, even) * invt;
       } else {
+        const double lo = D.cell0 + i * D.h, hi = lo + D.h;
         for (int k = klo; k <= khi; ++k) {
           const double wk = (even && (k == kmax || k == -kmax)) ? 0.5 : 1.0;
           v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
         }
       }
     } else {
-      const double lo = D.x0 + i * D.h, hi = lo + D.h;
-      if (D.lattice) {
-        const double klo_f = ceil((lo - reach - c0) * invb), khi_f = floor((hi + reach - c0) * invb);
-        const int klo = (klo_f < 0.0) ? 0 : (int)klo_f;
-        const int khi = (khi_f > D.L - 1) ? D.L - 1 : (int)khi_f;
-        if (taylor) {
-          v = image_sum_taylor_box(t, 0.5 * (lo + hi) - c0, D.b, invb, bc, J, klo, khi,
-                                   s.zcell ? s.zcell + nu : nullptr, s.M0, invZ) *
-              invt;
-        } else {
-          for (int k = klo; k <= khi; ++k) {
-            const double wk = s.zcell ? s.zcell[k * s.M0 + nu] * invZ : 1.0;
-            v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
-          }
-        }
-      } else if (lo - reach <= c0 && c0 <= hi + reach) {
-        if (taylor) {
-          const double m = t * (0.5 * (lo + hi) - c0), y = m * m;
-          v = exp(-y) * taylor_S(bc, J, y) * invt;
-        } else {
-          v = gauss_cell_integral(t, invt, lo, hi, c0);
+      // open box: the L actual cells, weighted by their charges
+      const int klo = kf_lo < 0.0f ? 0 : (kf_lo > (float)D.L ? D.L : (int)kf_lo);
+      const int khi = kf_hi > (float)(D.L - 1) ? D.L - 1 : (kf_hi < -1.0f ? -1 : (int)kf_hi);
+      const double invZ = invZ_sh;
+      if (taylor) {
+        v = image_sum_taylor_box(t, xc, D.b, invb, bc, J, klo, khi, s.zcell ? s.zcell + nu : nullptr, s.M0, invZ) *
+            invt;
+      } else {
+        const double lo = D.x0 + i * D.h, hi = lo + D.h;
+        for (int k = klo; k <= khi; ++k) {
+          const double wk = s.zcell ? s.zcell[k * s.M0 + nu] * invZ : 1.0;
+          v += wk * gauss_cell_integral(t, invt, lo, hi, c0 + k * D.b);
         }
       }
     }

@@ -191,8 +191,8 @@ __host__ __device__ inline int basis_ctas(const SysDev &s) {
 // the launch with potential_ctas.
 constexpr int kPotChunk = 512;
 // Per (direction, sinc node) constants of a potential row: degree J of the cell series, its
-// coefficients, the Euler-Maclaurin polynomial and the Poisson weights.
-constexpr int kPotConst = 44;
+// coefficients, the Euler-Maclaurin polynomial, the Poisson weights, the row's scalars and flags.
+constexpr int kPotConst = 54;
 __host__ __device__ inline int potential_ctas(const SysDev &s) {
   int n = 0;
   for (int l = 0; l < 3; ++l) n += s.Rt * ((s.d[l].nv + kPotChunk - 1) / kPotChunk);
