@@ -79,15 +79,19 @@ struct Grp {
   __device__ __forceinline__ unsigned ballot(bool p) const { return __ballot_sync(mask, p) >> base; }
 };
 
-// per warp: A, B, V (m^2 complex each), rotation table (16 x {c, sr, si, p, q}), kept index
-// map, scales and overlap eigenvalues (32 each), the (k1 < k2) pair-block table (120 x 2) and the
-// Householder vectors (2 x 32 complex)
-__host__ __device__ inline size_t eig_warp_core_bytes(int m) {
-  return (size_t)3 * m * m * sizeof(double2) + 16 * (3 * sizeof(double) + 2 * sizeof(int)) +
+// per warp: A, B, V (m^2 complex each; V in the system's per-k-point scratch SysDev::evs instead
+// when vglob), rotation table (16 x {c, sr, si, p, q}), kept index map, scales and overlap
+// eigenvalues (32 each), the (k1 < k2) pair-block table (120 x 2) and the Householder vectors
+// (2 x 32 complex).  V is touched only by the canonical route, the FP64 trace test and the
+// eigenvector path: out of shared memory it leaves room for a third more resident matrices.
+__host__ __device__ inline size_t eig_warp_core_bytes(int m, bool vglob) {
+  return (size_t)(vglob ? 2 : 3) * m * m * sizeof(double2) + 16 * (3 * sizeof(double) + 2 * sizeof(int)) +
          32 * (2 * sizeof(double) + 2 * sizeof(int)) + 288;
 }
 // + 64 complex of Householder scratch (v and w)
-__host__ __device__ inline size_t eig_warp_bytes(int m) { return eig_warp_core_bytes(m) + 64 * sizeof(double2); }
+__host__ __device__ inline size_t eig_warp_bytes(int m, bool vglob) {
+  return eig_warp_core_bytes(m, vglob) + 64 * sizeof(double2);
+}
 
 struct RotTab {
   double *c, *sr, *si;
@@ -859,7 +863,7 @@ __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict_
 template <int G>
 __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
                                                         unsigned *flags, unsigned long long *counters,
-                                                        int max_m0) {
+                                                        int max_m0, int vglob) {
   const SysDev &s = sysv[blockIdx.y];
   if (s.box) return;
   const Grp<G> g;
@@ -884,11 +888,11 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
   if (!s.klist && mk < kap) return;  // the conjugate partner solves this pair
   const int m0 = s.m0;
   extern __shared__ unsigned char smraw[];
-  unsigned char *base = smraw + (size_t)slotm * eig_warp_bytes(max_m0);
+  unsigned char *base = smraw + (size_t)slotm * eig_warp_bytes(max_m0, vglob != 0);
   double2 *A = reinterpret_cast<double2 *>(base);
   double2 *B = A + max_m0 * max_m0;
-  double2 *V = B + max_m0 * max_m0;
-  double *rc = reinterpret_cast<double *>(V + max_m0 * max_m0);
+  double2 *V = vglob ? reinterpret_cast<double2 *>(s.evs) + (int64_t)widx * m0 * m0 : B + max_m0 * max_m0;
+  double *rc = reinterpret_cast<double *>(B + (vglob ? 1 : 2) * max_m0 * max_m0);
   double *rsr = rc + 16, *rsi = rsr + 16;
   double *dsc = rsi + 16;   // [32] scale of kept function a
   double *sg = dsc + 32;    // [32] eigenvalues of the scaled overlap (canonical path)
@@ -1309,10 +1313,10 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
     double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
     if (ok && m > 0) {
       if (a_df)
-        df_householder_tridiag(Af, m, g, reinterpret_cast<float4 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+        df_householder_tridiag(Af, m, g, reinterpret_cast<float4 *>(base + eig_warp_core_bytes(max_m0, vglob != 0)), slot + 1,
                                slot + 1 + m0);
       else
-        householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0)), slot + 1,
+        householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0, vglob != 0)), slot + 1,
                             slot + 1 + m0);
     }
     if (lane == 0) {
@@ -1683,35 +1687,35 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
 // gives two lanes to each column of the triangular solves).
 static inline int eig_group(int max_m0, bool full) { return (max_m0 <= 16 && !full) ? 16 : 32; }
 
-int eig_max_warps(int max_m0, bool full) {
+int eig_max_warps(int max_m0, bool full, bool vglob) {
   const int per_warp = 32 / eig_group(max_m0, full);
   int w = kEigMaxWarps;
-  while (w > 1 && (size_t)w * per_warp * eig_warp_bytes(max_m0) > 227 * 1024) --w;
+  while (w > 1 && (size_t)w * per_warp * eig_warp_bytes(max_m0, vglob) > 227 * 1024) --w;
   return w;
 }
 
 template <int G>
 static cudaError_t launch_k_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                                unsigned long long *counters, cudaStream_t st, int warps) {
+                                unsigned long long *counters, cudaStream_t st, int warps, bool vglob) {
   const int per_cta = warps * (32 / G);
-  const size_t smem = (size_t)per_cta * eig_warp_bytes(max_m0);
+  const size_t smem = (size_t)per_cta * eig_warp_bytes(max_m0, vglob);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_eig<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((max_k + per_cta - 1) / per_cta, nsys);
   kmark(LHF_K_EIG, 1, st);
-  k_eig<G><<<grid, warps * 32, smem, st>>>(sys, flags, counters, max_m0);
+  k_eig<G><<<grid, warps * 32, smem, st>>>(sys, flags, counters, max_m0, vglob ? 1 : 0);
   kmark(LHF_K_EIG, 0, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                              unsigned long long *counters, cudaStream_t st, int warps, bool full) {
+                              unsigned long long *counters, cudaStream_t st, int warps, bool full, bool vglob) {
   if (max_k <= 0 || nsys <= 0) return cudaSuccess;
-  if (warps < 1 || warps > eig_max_warps(max_m0, full)) return cudaErrorInvalidValue;
-  return eig_group(max_m0, full) == 16 ? launch_k_eig<16>(sys, nsys, max_k, max_m0, flags, counters, st, warps)
-                                 : launch_k_eig<32>(sys, nsys, max_k, max_m0, flags, counters, st, warps);
+  if (warps < 1 || warps > eig_max_warps(max_m0, full, vglob)) return cudaErrorInvalidValue;
+  return eig_group(max_m0, full) == 16 ? launch_k_eig<16>(sys, nsys, max_k, max_m0, flags, counters, st, warps, vglob)
+                                       : launch_k_eig<32>(sys, nsys, max_k, max_m0, flags, counters, st, warps, vglob);
 }
 
 cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
@@ -1732,8 +1736,8 @@ cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, u
 
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps, int tri_threads,
-                       bool full) {
-  cudaError_t e = launch_eig_reduce(sys, nsys, max_k, max_m0, flags, counters, st, eig_warps, full);
+                       bool full, bool vglob) {
+  cudaError_t e = launch_eig_reduce(sys, nsys, max_k, max_m0, flags, counters, st, eig_warps, full, vglob);
   if (e != cudaSuccess || !tri) return e;
   return launch_tridiag(sys, nsys, max_k, max_m0, flags, counters, st, tri_threads);
 }

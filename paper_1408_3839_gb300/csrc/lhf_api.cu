@@ -58,6 +58,7 @@ struct Plan {
   long long mirror_items = 0;  // window-block elements filled from their mirrors
   size_t zcell_off = 0, dense_off = 0;
   size_t tri_off = 0;  // tridiagonal scratch of the k-point solves (periodic)
+  size_t evs_off = 0;  // per-k-point matrix scratch of the k-point solves (periodic)
   size_t dft_off = 0;  // four-step DFT scratch of a long chain (0: none)
   size_t rank_smem = 0;  // shared memory of the rank reduction (0: not reduced)
   std::vector<double> zcell;  // host copy of the per-cell charges (box)
@@ -547,6 +548,8 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
   } else {
     P.tri_off = off;  // one slot per k-point bounds the solved ones
     off = align_up(off + (size_t)sd.nblocks * (2 * m0 + 1));
+    P.evs_off = off;
+    off = align_up(off + (size_t)sd.nblocks * 2 * mm);
     if (s.L[0] > lhf::kDftTileMax) {  // scratch of the four-step DFT
       int A = 0, B = 0;
       if (!lhf::dft_four_step_split(s.L[0], &A, &B))
@@ -929,7 +932,8 @@ lhf_status set_klist(lhf_ctx *c, SysDev &sd) {
 // k_tridiag_eig (threads per CTA) once on the uploaded batch (the overlap norms already
 // launched); both kernels rewrite the same outputs, so the trial runs leave no trace beyond
 // the time they take.  Returns the fastest pair.
-lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, bool full, std::array<int, 2> *best) {
+lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, bool full, bool vglob,
+                    std::array<int, 2> *best) {
   cudaEvent_t a = nullptr, b = nullptr;
   lhf_status st = c->cuda(cudaEventCreate(&a), "cudaEventCreate");
   if (st == LHF_OK) st = c->cuda(cudaEventCreate(&b), "cudaEventCreate");
@@ -944,16 +948,16 @@ lhf_status tune_eig(lhf_ctx *c, int nsys, int max_k, int max_m0, bool tri, bool 
   (*best)[0] = 4;
   (*best)[1] = 128;
   float tbest = 1e30f, t = 0.f;
-  const int wmax = lhf::eig_max_warps(max_m0, full);
+  const int wmax = lhf::eig_max_warps(max_m0, full, vglob);
   // a first run at the default shape warms the caches (and its output feeds the tridiagonal trials)
   if (st == LHF_OK)
     st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream,
-                                                   std::min(4, wmax), full); },
+                                                   std::min(4, wmax), full, vglob); },
                &t);
   for (int w : {1, 2, 4, 8}) {
     if (st != LHF_OK || w > wmax) break;
     st = timed([&] { return lhf::launch_eig_reduce(c->d_sys, nsys, max_k, max_m0, c->d_flags, nullptr, c->stream, w,
-                                                   full); },
+                                                   full, vglob); },
                &t);
     if (st == LHF_OK && t < tbest) {
       tbest = t;
@@ -983,7 +987,9 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps, bool tri = true) {
   int max_k = 0, max_m0 = 0;
   long long total = 0;
   bool full = tri;  // every system on the mixed route's pair arithmetic: a warp per matrix
+  bool vglob = true;  // every system has the per-k-point matrix scratch
   for (const Plan &p : ps) {
+    vglob = vglob && p.sd.evs != nullptr;
     const int k = p.sd.klist ? p.sd.nkhalf : p.sd.nblocks;
     max_k = std::max(max_k, k);
     max_m0 = std::max(max_m0, p.sd.m0);
@@ -992,22 +998,22 @@ lhf_status run_eig(lhf_ctx *c, const std::vector<Plan> &ps, bool tri = true) {
   }
   int lg = 0;
   while ((1ll << (lg + 1)) <= total) ++lg;
-  const std::array<int, 3> key{max_m0, (tri ? 1 : 0) | (full ? 2 : 0), lg};
-  std::array<int, 2> shape{std::min(4, lhf::eig_max_warps(max_m0, full)), 128};
+  const std::array<int, 3> key{max_m0, (tri ? 1 : 0) | (full ? 2 : 0) | (vglob ? 4 : 0), lg};
+  std::array<int, 2> shape{std::min(4, lhf::eig_max_warps(max_m0, full, vglob)), 128};
   c->begin(5);
   lhf_status st = c->cuda(lhf::launch_overlap_norms(c->d_sys, (int)ps.size(), c->stream), "overlap-norm kernel");
   auto it = c->eig_tune.find(key);
   if (it != c->eig_tune.end()) {
     shape = it->second;
   } else if (st == LHF_OK && c->autotune && !c->capturing) {
-    st = tune_eig(c, (int)ps.size(), max_k, max_m0, tri, full, &shape);
+    st = tune_eig(c, (int)ps.size(), max_k, max_m0, tri, full, vglob, &shape);
     if (st == LHF_OK) c->eig_tune[key] = shape;
   }
   c->last_eig_warps = shape[0];
   c->last_tri_threads = shape[1];
   if (st == LHF_OK)
     st = c->cuda(lhf::launch_eig(c->d_sys, (int)ps.size(), max_k, max_m0, c->d_flags, c->d_counters, c->stream,
-                                 tri, shape[0], shape[1], full),
+                                 tri, shape[0], shape[1], full, vglob),
                  "eigen kernel");
   c->end(tri ? 3 : 2);
   return st;
@@ -1032,6 +1038,7 @@ void bind_ws(Plan &p, double *base) {
   p.sd.s0 = base + p.s0_off;
   p.sd.zcell = (p.sd.box && !p.zcell.empty()) ? base + p.zcell_off : nullptr;
   p.sd.tri = p.sd.box ? nullptr : base + p.tri_off;
+  p.sd.evs = p.sd.box ? nullptr : base + p.evs_off;
   p.sd.dftw = p.dft_off ? base + p.dft_off : nullptr;
 }
 

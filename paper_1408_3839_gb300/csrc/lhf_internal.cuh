@@ -95,6 +95,7 @@ struct SysDev {
   double *s0;             // [m0] mean over k-points of Re Sbar_ii (cell-periodic norms)
   const int *klist;       // [nkhalf] k-points solved (one per conjugate pair), or null
   double *tri;            // [nkhalf][2 m0 + 1] tridiagonal of each solved k-point, or null (Jacobi)
+  double *evs;            // complex [nblocks][m0][m0] scratch of the k-point solves, or null
   double *vecs;           // complex [nblocks][m0][m0] Bloch eigenvectors (rows), or null
   double *dftw;           // complex [2][L0][m0][m0] scratch of the four-step DFT (L0 > kDftTileMax), or null
   // rank reduction of the direction-0 potential factors (one-dimensional lattices, FP64 route):
@@ -275,12 +276,16 @@ cudaError_t launch_dft(const SysDev *sys, int nsys, const int *host_L, int *pass
 // tridiagonal kernel (a multiple of its 16 or 32 lanes per matrix, at most 256).  The two
 // kernels alone (launch_eig_reduce, launch_tridiag) serve the launch-shape autotuner.
 // full: a whole warp per matrix even up to order 16 (the mixed route's pair arithmetic).
+// vglob: every system carries the per-k-point scratch SysDev::evs, which then holds each
+// solve's third matrix instead of shared memory (more resident solves per SM).
 cudaError_t launch_eig(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                        unsigned long long *counters, cudaStream_t st, bool tri, int eig_warps = 4,
-                       int tri_threads = 128, bool full = false);
+                       int tri_threads = 128, bool full = false, bool vglob = false);
 cudaError_t launch_eig_reduce(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
-                              unsigned long long *counters, cudaStream_t st, int warps, bool full = false);
-int eig_max_warps(int max_m0, bool full = false);  // most k_eig warps per CTA whose shared memory fits an SM
+                              unsigned long long *counters, cudaStream_t st, int warps, bool full = false,
+                              bool vglob = false);
+// most k_eig warps per CTA whose shared memory fits an SM
+int eig_max_warps(int max_m0, bool full = false, bool vglob = false);
 cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, unsigned *flags,
                            unsigned long long *counters, cudaStream_t st, int threads);
 cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st);
