@@ -433,11 +433,18 @@ __device__ void df_hermitian_part(float4 *A, int m, const Grp<G> &g) {
   g.sync();
 }
 
-// Cholesky of the scaled overlap in pairs, as the FP64 loop of k_eig: the FP32 copy L32 (1 / L_jj
-// on its diagonal) and the inverse pivots sgf (pairs) for the triangular solves.  False when a
-// scaled pivot falls below kCholTol.
+// FP32 copy of the Cholesky factor's entry (i, j), i > j, for the trace estimate: stored in the
+// first 8 bytes of the (16-byte) element (j, i) of the factorised matrix, whose strict upper
+// triangle neither the factorisation nor the triangular solves read.
+__device__ __forceinline__ float2 *l32_at(void *B, int m, int i, int j) {
+  return reinterpret_cast<float2 *>(static_cast<unsigned char *>(B) + (size_t)(j * m + i) * 16);
+}
+
+// Cholesky of the scaled overlap in pairs, as the FP64 loop of k_eig: the FP32 copy of the
+// off-diagonal factor in the free strict upper triangle of B (l32_at) and the inverse pivots sgf
+// (pairs) for the triangular solves.  False when a scaled pivot falls below kCholTol.
 template <int G>
-__device__ bool df_cholesky(float4 *B, int m, const Grp<G> &g, float2 *L32, float2 *sgf) {
+__device__ bool df_cholesky(float4 *B, int m, const Grp<G> &g, float2 *sgf) {
   const int lane = g.lane;
   for (int j = 0; j < m; ++j) {
     const float2 d = make_float2(B[j * m + j].x, B[j * m + j].y);
@@ -447,13 +454,12 @@ __device__ bool df_cholesky(float4 *B, int m, const Grp<G> &g, float2 *L32, floa
     for (int i = j + 1 + lane; i < m; i += G) {
       const float4 lij = df_cscale(B[i * m + j], inv);
       B[i * m + j] = lij;
-      L32[i * m + j] = make_float2(lij.x, lij.z);
+      *l32_at(B, m, i, j) = make_float2(lij.x, lij.z);
     }
     g.sync();
     if (lane == 0) {
       B[j * m + j] = make_float4(ljj.x, ljj.y, 0.0f, 0.0f);
       sgf[j] = inv;
-      L32[j * m + j] = make_float2(inv.x, 0.0f);
     }
     const int n = m - j - 1;
     for (int t = lane; t < n * (n + 1) / 2; t += G) {
@@ -915,9 +921,6 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
     g.sync();
   }
   const RotTab R{rc, rsr, rsi, rp, rq, blk};
-  // FP32 copy of the Cholesky factor (off-diagonal entries, 1 / L_jj on the diagonal), kept in
-  // V's space, which the Cholesky route needs only after the FP32 trace estimate
-  float2 *L32 = reinterpret_cast<float2 *>(V);
 
   const double2 *Hb = reinterpret_cast<const double2 *>(s.Hbar) + (int64_t)kap * m0 * m0;
   const double2 *Sb = reinterpret_cast<const double2 *>(s.Sbar) + (int64_t)kap * m0 * m0;
@@ -977,7 +980,7 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
   //    is scaled by its pivot, then the trailing lower triangle is updated by every lane (no
   //    serial sums); a pivot below kCholTol sends the k-point to canonical orthogonalisation
   bool chol = ok;
-  if (dfp && chol) chol = df_cholesky(Bf, m, g, L32, sgf);
+  if (dfp && chol) chol = df_cholesky(Bf, m, g, sgf);
   for (int j = 0; !dfp && chol && j < m; ++j) {
     const double d = B[j * m + j].x;
     if (!(d >= kCholTol)) {  // warp-uniform: every lane reads the same pivot
@@ -989,13 +992,12 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
     for (int i = j + 1 + lane; i < m; i += G) {
       const double2 lij = cscale(B[i * m + j], inv);
       B[i * m + j] = lij;
-      L32[i * m + j] = make_float2((float)lij.x, (float)lij.y);
+      *l32_at(B, m, i, j) = make_float2((float)lij.x, (float)lij.y);
     }
     g.sync();
     if (lane == 0) {
       B[j * m + j] = make_double2(ljj, 0.0);
       sg[j] = inv;
-      L32[j * m + j] = make_float2((float)inv, 0.0f);  // the diagonal holds 1 / L_jj
     }
     // B[i][k] -= L[i][j] conj(L[k][j]) for j < k <= i < m: the n (n + 1) / 2 entries of the
     // trailing lower triangle, n = m - j - 1, row by row
@@ -1030,7 +1032,7 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
       float2 acc = make_float2(0.0f, 0.0f);
       if (act)
         for (int k = part; k < i; k += q) {
-          const float2 l = L32[i * m + k];
+          const float2 l = *l32_at(B, m, i, k);
           acc.x = fmaf(l.x, z[k].x, acc.x);
           acc.x = fmaf(-l.y, z[k].y, acc.x);
           acc.y = fmaf(l.x, z[k].y, acc.y);
@@ -1040,7 +1042,7 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
         acc.x += __shfl_xor_sync(g.mask, acc.x, 1);
         acc.y += __shfl_xor_sync(g.mask, acc.y, 1);
       }
-      const float di = L32[i * m + i].x;
+      const float di = dfp ? sgf[i].x : (float)sg[i];  // 1 / L_ii
       z[i] = make_float2(((i == cc ? 1.0f : 0.0f) - acc.x) * di, -acc.y * di);
       if (act && part == 0) tr = fmaf(z[i].x, z[i].x, fmaf(z[i].y, z[i].y, tr));
     }
