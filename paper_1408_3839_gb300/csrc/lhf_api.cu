@@ -50,8 +50,7 @@ struct Plan {
   size_t s0_off = 0;   // offset of s0 [m0]
   bool mixed = false;  // digit planes for the tensor-core route allocated
   size_t blocks_doubles = 0;  // nblocks * m0^2
-  int basis_items = 0 /* rows */, pot_rows = 0, gram_blocks = 0, rank_items = 0 /* blocks */, rank_compute2 = 0,
-      rank_compute4 = 0, rank_group = 2;
+  int basis_items = 0 /* rows */, pot_rows = 0, gram_blocks = 0, rank_items = 0 /* blocks */, rank_ctas = 0;
   int nv_max = 0;
   // open box: direction-0 factor rows, widest product row, zcell and dense-solver regions
   int box_items = 0, box_width = 0;
@@ -559,9 +558,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
     }
     P.blocks_doubles = align_up((size_t)sd.nblocks * mm);
     P.rank_items = sd.nblocks;  // zeros outside the window: CTA per block
-    P.rank_group = lhf::ranksum_group(sd);
-    P.rank_compute2 = lhf::ranksum_compute_items(sd, 2);
-    P.rank_compute4 = lhf::ranksum_compute_items(sd, 4);
+    P.rank_ctas = lhf::ranksum_ctas(sd);
     if ((size_t)sd.nblocks * mm > (size_t)1 << 31) return c->fail(LHF_ERR_UNSUPPORTED, "too many block entries");
   }
   // rank reduction: periodic (L,1,1) lattices with open single-cell transverse directions, FP64
@@ -806,9 +803,10 @@ lhf_status run_assembly(lhf_ctx *c, const std::vector<Plan> &ps) {
   lhf_status st = run_factors_gram(c, ps);
   if (st != LHF_OK) return st;
   c->begin(3);
-  const int rgroup = max_of(ps, &Plan::rank_group);
-  st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, rgroup == 2 ? &Plan::rank_compute2 : &Plan::rank_compute4),
-                                   max_of(ps, &Plan::rank_items), rgroup, c->stream),
+  int max_rt = 0;
+  for (const Plan &p : ps) max_rt = std::max(max_rt, p.sd.Rt);
+  st = c->cuda(lhf::launch_ranksum(c->d_sys, nsys, max_of(ps, &Plan::rank_ctas), max_of(ps, &Plan::rank_items),
+                                   max_rt, c->stream),
                "rank-sum kernel");
   c->end();
   return st;

@@ -254,13 +254,12 @@ cudaError_t launch_gram_tc_impl(const SysDev *host_sys, int nsys, void *dev_buf,
 cudaError_t gram_tc_prepare(const SysDev *host_sys, int nsys, void *host_buf, size_t host_bytes, int *njobs,
                             size_t *jobs_off);
 cudaError_t gram_tc_launch(const void *dev_buf, int njobs, size_t jobs_off, unsigned *flags, cudaStream_t st);
-// Rank sum over the window blocks (max_compute_items = ranksum_compute_items over the batch) and
-// zeros for the blocks outside it (max_blocks = nblocks over the batch).  Reads mirrored window
-// blocks from their contracted partners (no mirror pass needed).
-// group: direction-0 window blocks per thread (2 or 4; ranksum_group, the largest over a batch).
-int ranksum_group(const SysDev &s);
-int ranksum_compute_items(const SysDev &s, int group);
-cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_items, int max_blocks, int group,
+// Rank sum over the window blocks (max_compute_ctas = ranksum_ctas over the batch) and zeros for
+// the blocks outside it (max_blocks = nblocks over the batch); max_rt: the largest R_tot of the
+// batch (shared memory of the rank weights).  Reads mirrored window blocks from their contracted
+// partners (no mirror pass needed).
+int ranksum_ctas(const SysDev &s);
+cudaError_t launch_ranksum(const SysDev *sys, int nsys, int max_compute_ctas, int max_blocks, int max_rt,
                            cudaStream_t st);
 // A lattice dimension of at most kDftTileMax positions is transformed in one shared-memory tile
 // per pass; a one-dimensional lattice of up to kDftMaxL1 cells with L0 > kDftTileMax takes the
