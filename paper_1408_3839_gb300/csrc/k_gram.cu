@@ -382,6 +382,15 @@ __global__ void __launch_bounds__(kGramThreads, 4) k_gram_slice(const SysDev *__
   const float4 *GD = reinterpret_cast<const float4 *>(s.ws + D.offGD);  // {sample, difference} pairs
   const float4 *f = GD + (int64_t)it.mu * n;
   for (int nu = warp; nu < m0; nu += kWarps) {
+    if (periodic && seg[nu][0][0] == 0 && seg[nu][1][0] == 0) {
+      // no cell where both functions live: every folded value and sum is an exact zero
+      for (int c = lane; c < nv; c += 32) Qp[nu * ld + c] = make_float2(0.0f, 0.0f);
+      if (lane == 0) {
+        rexp[nu] = 0;
+        qsum[nu] = esum[nu] = make_float2(0.0f, 0.0f);
+      }
+      continue;  // warp-uniform
+    }
     const float4 *g = GD + (int64_t)nu * n;
     float q0 = 0.0f, q1 = 0.0f, e0 = 0.0f, e1 = 0.0f, mx = 0.0f;
     if (!periodic && lane == 0) {
