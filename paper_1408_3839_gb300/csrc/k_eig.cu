@@ -367,6 +367,25 @@ __device__ __forceinline__ float2 df_sqrt(float2 a) {
   const float2 r = df_add(a, df_neg(df_mul(make_float2(h, 0.0f), make_float2(h, 0.0f))));  // a - h^2
   return df_norm(h, __fdiv_rn(r.x, 2.0f * h));
 }
+// x as a pair from its bits, without FP64 instructions (this GPU issues them at 1/64 of the FP32
+// rate): h = the leading 24 significant bits, l = the remaining 29 bits rounded to 24, then
+// renormalised (|x - (h + l)| <= 2^-48 |x|).  Zero and subnormal x give 0; an exponent outside
+// h's and l's normal range (|x| < 2^-74, |x| >= 2^128, inf, NaN) takes the FP64 conversion.
+__device__ __forceinline__ float2 pair_from_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ffu);
+  if (E == 0) return make_float2(0.0f, 0.0f);
+  const int fe = E - 896;  // h's biased FP32 exponent (E - 1023 + 127)
+  if (fe < 53 || fe > 254) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float h = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+  // x - h = +-(low 29 bits) 2^(E - 1075), the power of two an FP32 normal (fe - 52 >= 1)
+  const float lm = __fmul_rn((float)(unsigned)(b & 0x1fffffffu), __uint_as_float((unsigned)(fe - 52) << 23));
+  return df_norm(h, sign ? -lm : lm);
+}
 __device__ __forceinline__ float4 df_from(double2 v) {
   const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
   return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
@@ -938,36 +957,54 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
   ok = __all_sync(g.mask, ok);
   const unsigned kmask = g.ballot(keep);
   int m = __popc(kmask);
-  if (keep) {
-    const int a = __popc(kmask & ((1u << lane) - 1u));
-    kidx[a] = lane;
-    dsc[a] = 1.0 / sqrt(dii);
-  }
-  g.sync();
-  double hf2 = 0.0;  // ||H~||_F^2
-  for (int e = lane; e < m * m; e += G) {
-    const int a = e / m, b = e - (e / m) * m;
-    const int ia = kidx[a], ib = kidx[b];
-    const double sc = dsc[a] * dsc[b];
-    A[e] = cscale(Hb[ia * m0 + ib], sc);
-    B[e] = cscale(Sb[ia * m0 + ib], sc);
-    hf2 += A[e].x * A[e].x + A[e].y * A[e].y;
-  }
-  for (int o = G / 2; o > 0; o >>= 1) hf2 += __shfl_xor_sync(g.mask, hf2, o);
-  g.sync();
   // mixed route, eigenvalues only: the reduction in compensated FP32 pairs (A, B and V then hold
   // float4 pairs in the same bytes): Cholesky route, canonical route and Jacobi
   const bool dfp = s.eig_df != 0 && s.tri != nullptr && s.vecs == nullptr;
   float4 *Af = reinterpret_cast<float4 *>(A), *Bf = reinterpret_cast<float4 *>(B), *Vf = reinterpret_cast<float4 *>(V);
   float2 *sgf = reinterpret_cast<float2 *>(sg);  // inverse pivots as pairs (in sg's doubles)
+  float2 *dscf = reinterpret_cast<float2 *>(rc);  // the scales as pairs (rotation-table space, free until Jacobi)
   bool a_df = false;                            // A holds pairs
+  if (keep) {
+    const int a = __popc(kmask & ((1u << lane) - 1u));
+    kidx[a] = lane;
+    dsc[a] = 1.0 / sqrt(dii);
+    if (dfp) dscf[a] = fp32_pair(dsc[a]);
+  }
+  g.sync();
+  double hf2 = 0.0;  // ||H~||_F^2
+  if (dfp) {
+    // the pair route gathers straight from the FP64 blocks: the entries split into pairs by their
+    // bits and scaled in pairs (no FP64 instruction per entry); ||H~||_F^2 in FP32 (it only
+    // chooses between the tridiagonal and the Jacobi route, by a factor of 4)
+    float hf = 0.0f;
+    for (int e = lane; e < m * m; e += G) {
+      const int a = e / m, b = e - (e / m) * m;
+      const int ia = kidx[a], ib = kidx[b];
+      const float2 sc = df_mul(dscf[a], dscf[b]);
+      const double2 hv = Hb[ia * m0 + ib], sv = Sb[ia * m0 + ib];
+      const float2 hr = pair_from_bits(hv.x), hi = pair_from_bits(hv.y);
+      const float2 sr = pair_from_bits(sv.x), si = pair_from_bits(sv.y);
+      const float4 x = df_cscale(make_float4(hr.x, hr.y, hi.x, hi.y), sc);
+      Af[e] = x;
+      Bf[e] = df_cscale(make_float4(sr.x, sr.y, si.x, si.y), sc);
+      hf = fmaf(x.x, x.x, fmaf(x.z, x.z, hf));
+    }
+    for (int o = G / 2; o > 0; o >>= 1) hf += __shfl_xor_sync(g.mask, hf, o);
+    hf2 = (double)hf;
+  } else {
+    for (int e = lane; e < m * m; e += G) {
+      const int a = e / m, b = e - (e / m) * m;
+      const int ia = kidx[a], ib = kidx[b];
+      const double sc = dsc[a] * dsc[b];
+      A[e] = cscale(Hb[ia * m0 + ib], sc);
+      B[e] = cscale(Sb[ia * m0 + ib], sc);
+      hf2 += A[e].x * A[e].x + A[e].y * A[e].y;
+    }
+    for (int o = G / 2; o > 0; o >>= 1) hf2 += __shfl_xor_sync(g.mask, hf2, o);
+  }
+  g.sync();
   // the blocks are Hermitian up to the rounding of the transform: solve their Hermitian parts
   if (dfp) {
-    for (int e = lane; e < m * m; e += G) {
-      Af[e] = df_from(A[e]);
-      Bf[e] = df_from(B[e]);
-    }
-    g.sync();
     df_hermitian_part(Af, m, g);
     df_hermitian_part(Bf, m, g);
     a_df = true;
