@@ -88,9 +88,11 @@ __host__ __device__ inline size_t eig_warp_core_bytes(int m, bool vglob) {
   return (size_t)(vglob ? 2 : 3) * m * m * sizeof(double2) + 16 * (3 * sizeof(double) + 2 * sizeof(int)) +
          32 * (2 * sizeof(double) + 2 * sizeof(int)) + 288;
 }
-// + 64 complex of Householder scratch (v and w)
+// + 64 complex of Householder scratch (v and w), except with vglob from order 8 on: then the
+// vectors take B's space, free once C is formed on the tridiagonal route
+__host__ __device__ inline bool eig_hh_in_b(int m, bool vglob) { return vglob && m >= 8; }
 __host__ __device__ inline size_t eig_warp_bytes(int m, bool vglob) {
-  return eig_warp_core_bytes(m, vglob) + 64 * sizeof(double2);
+  return eig_warp_core_bytes(m, vglob) + (eig_hh_in_b(m, vglob) ? 0 : 64 * sizeof(double2));
 }
 
 struct RotTab {
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(256) k_overlap_norms(const SysDev *__restrict_
 }
 
 template <int G>
-__global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
+__global__ void __maxnreg__(80) k_eig(const SysDev *__restrict__ sysv,
                                                         unsigned *flags, unsigned long long *counters,
                                                         int max_m0, int vglob) {
   const SysDev &s = sysv[blockIdx.y];
@@ -1350,12 +1352,14 @@ __global__ void __maxnreg__(96) k_eig(const SysDev *__restrict__ sysv,
     // 3'. tridiagonal route: Householder reduction here, the tridiagonal eigenvalues by
     //     k_tridiag_eig (one thread per matrix); slot widx = [m | d[m0] | e[m0]]
     double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
+    unsigned char *hh = eig_hh_in_b(max_m0, vglob != 0) ? reinterpret_cast<unsigned char *>(B)
+                                                         : base + eig_warp_core_bytes(max_m0, vglob != 0);
     if (ok && m > 0) {
       if (a_df)
-        df_householder_tridiag(Af, m, g, reinterpret_cast<float4 *>(base + eig_warp_core_bytes(max_m0, vglob != 0)), slot + 1,
+        df_householder_tridiag(Af, m, g, reinterpret_cast<float4 *>(hh), slot + 1,
                                slot + 1 + m0);
       else
-        householder_tridiag(A, m, g, reinterpret_cast<double2 *>(base + eig_warp_core_bytes(max_m0, vglob != 0)), slot + 1,
+        householder_tridiag(A, m, g, reinterpret_cast<double2 *>(hh), slot + 1,
                             slot + 1 + m0);
     }
     if (lane == 0) {
@@ -1592,10 +1596,13 @@ __global__ void __launch_bounds__(kTriMaxThreads) k_tridiag_eig(const SysDev *__
   const double *slot = s.tri + (int64_t)widx * (2 * m0 + 1);
   const int m = (int)slot[0];
   if (m < 0) return;  // -1: not positive definite (NaN written by k_eig); -2: solved by k_eig
-  __shared__ double dsh[kTriMaxThreads / G][kTriMax], esh[kTriMaxThreads / G][kTriMax];
-  __shared__ float dfs[kTriMaxThreads / G][kTriMax], efs[kTriMaxThreads / G][kTriMax];
-  double *dn = dsh[gi], *e2 = esh[gi];
-  float *df = dfs[gi], *e2f = efs[gi];
+  // per matrix of the CTA: d and e^2 in FP64 and FP32 (shared memory sized by the launch, so
+  // that small CTAs keep many matrices resident: the kernel is bound by its dependent chains)
+  extern __shared__ double trsm[];
+  const int groups = (int)(blockDim.x / G);
+  double *dn = trsm + (size_t)gi * kTriMax, *e2 = trsm + (size_t)(groups + gi) * kTriMax;
+  float *df = reinterpret_cast<float *>(trsm + (size_t)2 * groups * kTriMax) + (size_t)gi * kTriMax;
+  float *e2f = reinterpret_cast<float *>(trsm + (size_t)2 * groups * kTriMax) + (size_t)(groups + gi) * kTriMax;
   // scale 2^ex >= max |entries|
   const double di = i < m ? slot[1 + i] : 0.0;
   const double ei = i + 1 < m ? slot[1 + m0 + i] : 0.0;
@@ -1764,11 +1771,12 @@ cudaError_t launch_tridiag(const SysDev *sys, int nsys, int max_k, int max_m0, u
   const int G = max_m0 <= 16 ? 16 : 32;
   if (threads < G || threads > kTriMaxThreads || threads % G != 0) return cudaErrorInvalidValue;
   const int per = threads / G;
+  const size_t smem = (size_t)per * kTriMax * (2 * sizeof(double) + 2 * sizeof(float));  // <= 6 KB
   kmark(LHF_K_TRIDIAG_EIG, 1, st);
   if (G == 16)
-    k_tridiag_eig<16><<<dim3((max_k + per - 1) / per, nsys), threads, 0, st>>>(sys, flags, counters);
+    k_tridiag_eig<16><<<dim3((max_k + per - 1) / per, nsys), threads, smem, st>>>(sys, flags, counters);
   else
-    k_tridiag_eig<32><<<dim3((max_k + per - 1) / per, nsys), threads, 0, st>>>(sys, flags, counters);
+    k_tridiag_eig<32><<<dim3((max_k + per - 1) / per, nsys), threads, smem, st>>>(sys, flags, counters);
   kmark(LHF_K_TRIDIAG_EIG, 0, st);
   return cudaGetLastError();
 }

@@ -761,10 +761,11 @@ lhf_status run_gram(lhf_ctx *c, const std::vector<Plan> &ps, bool with_mirror) {
 // a1, a2 and the Gram factors.  On the mixed route the potential rows (FP64-bound) run on the
 // side stream beside the basis samples and the fold into digit planes (FP32- and ALU-bound),
 // which do not read them; the main stream waits for them before their own digit planes.  A CUDA
-// graph captured over this records the two as parallel branches.
+// graph captured over this records the two as parallel branches.  With per-kernel timing on, the
+// potential stays on the main stream, so that every bracketed kernel runs alone.
 lhf_status run_factors_gram(lhf_ctx *c, const std::vector<Plan> &ps) {
   const int nsys = (int)ps.size();
-  const bool fork = ps[0].mixed && c->side;
+  const bool fork = ps[0].mixed && c->side && !c->prof;
   lhf_status st = LHF_OK;
   if (fork) {
     st = c->cuda(cudaEventRecord(c->fork_ev, c->stream), "cudaEventRecord");
