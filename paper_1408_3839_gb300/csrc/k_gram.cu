@@ -273,15 +273,37 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_fp64(const SysDev *__rest
   if (threadIdx.x < m0) write_p1_slots(s, it, threadIdx.x, red[2 * threadIdx.x], red[2 * threadIdx.x + 1]);
 
   // ---- phase 2: C_r[nu] = sum_c V[r][c] Q[nu][c] ------------------------------------------
+  // over the rows whose functions share a cell (listed first, so that every thread's dot product
+  // is one that can be nonzero); the others' slots are exact zeros
   const int Rt = s.Rt;
   const int mm = m0 * m0;
   const int mu = it.mu;
   double *Cout = s.ws + D.offC + (int64_t)it.jw * (Rt + 2) * mm + mu * m0;
   const double *V = s.ws + D.offV;
-  const int outs = Rt * m0;
+  __shared__ int nzl[kMaxM0], nnz_sh;
+  __shared__ unsigned zmask_sh;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    unsigned zm = 0u;
+    for (int nu = 0; nu < m0; ++nu) {
+      if (D.periodic && gram_row_cells(s, it.l, D.jlo + it.jw, mu, nu) == 0)
+        zm |= 1u << nu;
+      else
+        nzl[k++] = nu;
+    }
+    nnz_sh = k;
+    zmask_sh = zm;
+  }
+  __syncthreads();
+  const int nnz = nnz_sh;
+  const unsigned zmask = zmask_sh;
+  if (zmask)
+    for (int o = threadIdx.x; o < Rt * m0; o += kGramThreads)
+      if ((zmask >> (o % m0)) & 1u) Cout[(int64_t)(o / m0) * mm + o % m0] = 0.0;
+  const int outs = Rt * nnz;
   for (int o = threadIdx.x; o < outs; o += kGramThreads) {
-    const int r = o / m0;
-    const int nu = o - r * m0;
+    const int r = o / nnz;
+    const int nu = nzl[o - r * nnz];
     const double *vr = V + (int64_t)r * nv;
     const double *qn = Q + nu * ld;
     double acc0 = 0.0, acc1 = 0.0;
