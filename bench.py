@@ -185,20 +185,20 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float, pairs: bool =
 # kernel's source file is unchanged: "sha" is the first 16 hex digits of its SHA-256 at capture
 # time; any other hash reports null.
 TRAFFIC = {
-    # ncu --set full of the tube_256 workload at 16 systems, one kernel per capture: the autotuned
-    # k_eig / k_tridiag_eig launches and the first launch of the others; bytes read + written / 16
-    # (k_potential: its row launch plus the row-constant launch k_pot_rows of the capture before,
-    # whose code is unchanged).  Only kernels whose traffic grows with the systems of a batch are
+    # ncu --set full of the tube_256 workload at 16 systems (mixed route alone, --only-main), one
+    # kernel per capture: the autotuned k_eig / k_tridiag_eig launches and the first launch of the
+    # others; bytes read + written / 16
+    # (k_potential: its row launch plus its row-constant launch k_pot_rows, captured separately
+    # from the same command).  Only kernels whose traffic grows with the systems of a batch are
     # listed (the 16-system capture keeps part of the rank sum's and the DFT's outputs in L2, a
     # 64-system step does not; the digit slicing runs once per direction and only direction 0 was
     # captured)
-    "k_eig": {"src": "k_eig.cu", "sha": "cb92bc0544d011c7", "bytes_per_system": (17.025280e6 + 0.193280e6) / 16},
-    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "cb92bc0544d011c7", "bytes_per_system": 0.621056e6 / 16},
-    "k_potential": {"src": "k_setup.cu", "sha": "6739f7ff09425235",
-                    "bytes_per_system": (0.060672e6 + 0.741632e6 + 0.000768e6) / 16},
-    "k_basis": {"src": "k_setup.cu", "sha": "6739f7ff09425235", "bytes_per_system": (0.287744e6 + 0.110592e6) / 16},
-    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "5ea77bf3011af230",
-                  "bytes_per_system": (180.771072e6 + 22.735616e6) / 16},
+    "k_eig": {"src": "k_eig.cu", "sha": "0d945c0bded8c328", "bytes_per_system": (17.022e6 + 0.320e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "0d945c0bded8c328", "bytes_per_system": 0.620e6 / 16},
+    "k_potential": {"src": "k_setup.cu", "sha": "a1cd64a6af8541fc",
+                    "bytes_per_system": (0.064e6 + 0.840e6 + 0.000e6) / 16},
+    "k_basis": {"src": "k_setup.cu", "sha": "a1cd64a6af8541fc", "bytes_per_system": (0.765e6 + 0.593e6) / 16},
+    "k_gram_tc": {"src": "k_gram_tc.cu", "sha": "b36c4f676234f152", "bytes_per_system": (98.173e6 + 4.870e6) / 16},
 }
 
 
