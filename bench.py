@@ -132,12 +132,15 @@ def _jc(s: dict, l: int) -> int:
 def kernel_work(sizes: list[dict], passes: float, matrices: float, pairs: bool = False) -> dict:
     """Algorithmic work of one step (a batch of systems) per kernel: the roofline numerators.
 
-    k_gram_fp64: 2 R_tot m0^2 n_v per contracted window block (blocks j >= 0; the j < 0 blocks are
-    mirrors), per direction.  k_gram_tc: the same contraction issued as 28 BF16 digit-pair
-    products per FP64 product (7 digits per operand, pairs a + b <= 6), over K padded to a
-    multiple of 64 (tensor-pipe work; "algorithmic_flops" keeps the FP64 count).  k_gram_slice:
-    bytes of the digit planes and exponents it writes.  k_ranksum: (4 R_tot + 12) per window
-    entry.  k_dft_pass: read 2 real blocks, write 2 complex blocks per lattice block, per level.
+    k_gram_fp64: 2 R_tot n_v per contracted row (window block j >= 0, mu, nu) whose two functions
+    share a cell (the sizes query's overlap_rows; the other rows are exact zeros, and the j < 0
+    blocks are mirrors), per direction.  k_gram_tc: the same contraction issued as 28 BF16
+    digit-pair products per FP64 product (7 digits per operand, pairs a + b <= 6), over K padded
+    to a multiple of 64 (tensor-pipe work; "algorithmic_flops" keeps the FP64 count).
+    k_gram_slice: the bytes it writes: the digit planes and scale exponents of those rows, the
+    zero rank slots of the other rows, the two P1 slots of every row.  k_ranksum: one FMA per
+    rank term per window entry plus 12 flops of the P1 terms, and the rank weights c_r C1_r C2_r
+    (two multiplications per term) once per transverse block pair and entry.  k_dft_pass: read 2 real blocks, write 2 complex blocks per lattice block, per level.
     k_eig: per solved matrix 9.33 m^3 (Cholesky m^3/6 and two triangular solves m^3/2 each, in
     complex multiply-adds of 8 flops) + 5.33 m^3 (Householder reduction to real tridiagonal form:
     per column a Hermitian matrix-vector product and a rank-2 update of the lower triangle, 2 n^2
@@ -156,13 +159,14 @@ def kernel_work(sizes: list[dict], passes: float, matrices: float, pairs: bool =
         m0, Rt = s["m0"], s["rank"]
         for l in range(3):
             jc = _jc(s, l)
+            rows = s["overlap_rows"][l]
             nv = s["n_potential"][l]
             kpad = (nv + 63) // 64 * 64
-            gram += 2.0 * Rt * jc * m0 * m0 * nv
-            tc += 28.0 * 2.0 * Rt * jc * m0 * m0 * kpad
-            slice_bytes += 7 * 2.0 * jc * m0 * m0 * kpad + 4.0 * jc * m0 * m0
+            gram += 2.0 * Rt * rows * nv
+            tc += 28.0 * 2.0 * Rt * rows * kpad
+            slice_bytes += (7 * 2.0 * kpad + 4.0) * rows + 8.0 * Rt * (jc * m0 * m0 - rows) + 16.0 * jc * m0 * m0
         nwin = s["window"][0] * s["window"][1] * s["window"][2]
-        rank += nwin * m0 * m0 * (4.0 * Rt + 12.0)
+        rank += nwin * m0 * m0 * (2.0 * Rt + 12.0) + s["window"][1] * s["window"][2] * m0 * m0 * 2.0 * Rt
         dft_bytes += s["n_blocks"] * m0 * m0 * (2 * 8 + 2 * 16)
         levels = max(levels, sum(1 for l in range(3) if s["L"][l] > 1))
     m = sizes[0]["m0"] if sizes else 0

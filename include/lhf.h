@@ -130,6 +130,9 @@ typedef struct {
     int n_potential[3]; /* length of each direction's potential factor (n_cell periodic, else n) */
     int periodic;       /* 1 if every direction with L > 1 is periodic */
     int desc_bytes;     /* bytes of the device descriptor copied host -> device per system and call */
+    int overlap_rows[3]; /* rows (contracted window block j >= 0, mu, nu) of each direction's weighted
+                            Gram whose two functions share a cell; the other rows' factors are exact
+                            zeros and are not contracted (0 where the direction has no such Gram) */
 } lhf_sizes;
 
 /* Context creation.  device: CUDA ordinal; stream: a cudaStream_t (NULL = default stream).

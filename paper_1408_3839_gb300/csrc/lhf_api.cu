@@ -1352,6 +1352,12 @@ lhf_status lhf_query_sizes(lhf_ctx *c, lhf_sizes *out) {
   for (int l = 0; l < 3; ++l) {
     out->window[l] = (P.sd.box && l == 0) ? P.sd.bJ : P.sd.d[l].J;
     out->n_potential[l] = P.sd.d[l].nv;
+    const DirDev &D = P.sd.d[l];
+    if (P.sd.box && l == 0) continue;  // the box's cell-pair factors (no window Gram)
+    for (int jc = 0; jc < D.Jc; ++jc)
+      for (int mu = 0; mu < P.sd.m0; ++mu)
+        for (int nu = 0; nu < P.sd.m0; ++nu)
+          out->overlap_rows[l] += lhf::gram_row_cells(P.sd, l, D.jlo + D.cw0 + jc, mu, nu) > 0;
   }
   return LHF_OK;
 }

@@ -56,7 +56,8 @@ class lhf_system_desc(ctypes.Structure):
 class lhf_sizes(ctypes.Structure):
     _fields_ = [("m0", ctypes.c_int), ("n_blocks", ctypes.c_int), ("n_kpoints", ctypes.c_int),
                 ("n_basis", ctypes.c_int), ("rank", ctypes.c_int), ("window", ctypes.c_int * 3),
-                ("n_potential", ctypes.c_int * 3), ("periodic", ctypes.c_int), ("desc_bytes", ctypes.c_int)]
+                ("n_potential", ctypes.c_int * 3), ("periodic", ctypes.c_int), ("desc_bytes", ctypes.c_int),
+                ("overlap_rows", ctypes.c_int * 3)]
 
 
 class LhfError(RuntimeError):
@@ -331,7 +332,7 @@ class Context:
         return {"m0": out.m0, "n_blocks": out.n_blocks, "n_kpoints": out.n_kpoints,
                 "n_basis": out.n_basis, "rank": out.rank, "window": list(out.window),
                 "n_potential": list(out.n_potential), "periodic": out.periodic,
-                "desc_bytes": out.desc_bytes}
+                "desc_bytes": out.desc_bytes, "overlap_rows": list(out.overlap_rows)}
 
     def sync(self):
         self._check(self.lib.lhf_sync(self._h))

@@ -81,3 +81,33 @@ def test_batched_descriptors_match_single_descriptors():
         else:
             n = len(cfg["Z_cell"]) * M0
             assert [got.lattice.Z_cell[i] for i in range(n)] == list(np.ravel(cfg["Z_cell"]))
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every descriptor struct of the binding has the size and field offsets of include/lhf.h
+    (compiled here by the host C compiler): a field added on one side only fails on the CPU."""
+    import shutil
+    import subprocess
+
+    import paper_1408_3839_gb300.lhf as B
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = ["lhf_lattice_desc", "lhf_basis_desc", "lhf_grid_desc", "lhf_system_desc", "lhf_sizes"]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lhf.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for name, _ in getattr(B, st)._fields_:
+            lines.append(f'  printf("{st} {name} %zu\\n", offsetof({st}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for row in filter(None, out):
+        st, field, value = row.split()
+        cls = getattr(B, st)
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (st, field, got, value)
