@@ -12,10 +12,11 @@
 // transformed block is Hermitian, Hbar_kappa[nu][mu] = conj(Hbar_kappa[mu][nu]) (the same holds
 // for S): the last pass transforms only the entries mu <= nu and writes the others as their
 // conjugates (earlier passes of a multi-dimensional lattice still relate entries of different
-// outer indices and transform every entry).  The tile is transformed in shared memory: an iterative radix-2 FFT when
-// L_d is a power of two, Bluestein's chirp transform through radix-2 FFTs of length M >= 2 L_d - 1
-// otherwise (64 <= L_d <= 1024), the direct O(L_d^2) sum for the other lengths.  Twiddles come from a per-CTA table
-// built with sincospi (correctly-rounded arguments).
+// outer indices and transform every entry).  The tile is transformed in shared memory: an
+// iterative radix-4 FFT (fft_columns) when L_d is a power of two, Bluestein's chirp transform
+// through such FFTs of length M >= 2 L_d - 1 otherwise (64 <= L_d <= 1024), the direct O(L_d^2)
+// sum for the other lengths.  Twiddles come from a per-CTA table built with sincospi
+// (correctly-rounded arguments).
 #include "lhf_internal.cuh"
 
 namespace lhf {
@@ -34,7 +35,7 @@ __device__ inline unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (3
 // Bluestein's transform for a length L that is not a power of two: with w_n = exp(-pi i n^2 / L),
 // omega^(j k) = w_j w_k conj(w_(k-j)) (since 2 j k = j^2 + k^2 - (k - j)^2), so
 //   Xbar_k = w_k sum_j (x_j w_j) conj(w_(k-j)),
-// a cyclic convolution of length M (the power of two >= 2 L - 1) taken by radix-2 FFTs:
+// a cyclic convolution of length M (the power of two >= 2 L - 1) taken by power-of-two FFTs:
 // A = F_M(x w) (zero-padded), B = F_M(b) with b_n = conj(w_|n|) at n mod M for |n| < L (the
 // same for every column: once per CTA), Xbar_k = w_k conj(F_M(conj(A B)))_k / M.  O(M log M) per
 // column instead of the direct sum's L^2.  For kBluesteinMinL <= L <= kBluesteinMaxL (M <=
@@ -66,25 +67,46 @@ __host__ __device__ inline size_t pass_smem_bytes(int Ld) {
   return sizeof(double2) * (M ? (size_t)M * TW + 2 * (size_t)M + Ld : (size_t)Ld * TW + Ld);
 }
 
-// In-place radix-2 FFT of M positions x TW columns stored bit-reversed (x[j * TW + t]), output in
-// natural order; tab[m] = omega_M^m.  The first two stages' twiddles are 1 and -i.
-__device__ void radix2_columns(double2 *x, int M, int TW, const double2 *tab) {
-  for (int hs = 1; hs < M; hs <<= 1) {
-    const int stride = M / (2 * hs);
+// In-place FFT of M (a power of two) positions x TW columns stored bit-reversed (x[j * TW + t]),
+// output in natural order; tab[m] = omega_M^m.  Decimation in time, two levels (spans hs and
+// 2 hs) per pass (radix 4): with w2 = omega_(4 hs)^kk, the level-hs twiddle is w1 = w2^2 and the
+// two level-2hs twiddles are w2 and -i w2, so the outputs at positions p + {0, 1, 2, 3} hs are
+//   A + C, B - i D, A - C, B + i D,   A, B = x0 +- w1 x1,   C, D = w2 x2 +- w3 x3,   w3 = w2^3:
+// three complex multiplications per four points where two radix-2 levels take four, and one
+// shared-memory round trip and barrier per two levels.  An odd number of levels starts with one
+// radix-2 level (twiddle 1); the first pass (hs = 1) needs no multiplication.
+__device__ void fft_columns(double2 *x, int M, int TW, const double2 *tab) {
+  const int bits = __ffs(M) - 1;
+  int hs = 1;
+  if (bits & 1) {
     for (int k = threadIdx.x; k < (M / 2) * TW; k += blockDim.x) {
-      const int t = k % TW, b = k / TW;
-      const int kk = b % hs;
-      const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
-      const double2 u = x[top * TW + t], v = x[bot * TW + t];
-      double2 wv;
-      if (hs <= 2) {
-        wv = kk == 0 ? v : make_double2(v.y, -v.x);  // v or -i v
-      } else {
-        const double2 w = tab[kk * stride];
-        wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
+      const int t = k % TW, top = 2 * (k / TW);
+      const double2 u = x[top * TW + t], v = x[(top + 1) * TW + t];
+      x[top * TW + t] = make_double2(u.x + v.x, u.y + v.y);
+      x[(top + 1) * TW + t] = make_double2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+    hs = 2;
+  }
+  for (; hs < M; hs <<= 2) {
+    const int s4 = M / (4 * hs);  // table stride of omega_(4 hs)
+    for (int k = threadIdx.x; k < (M / 4) * TW; k += blockDim.x) {
+      const int t = k % TW, gq = k / TW;
+      const int kk = gq % hs, p0 = (gq / hs) * 4 * hs + kk;
+      double2 x0 = x[p0 * TW + t], x1 = x[(p0 + hs) * TW + t];
+      double2 x2 = x[(p0 + 2 * hs) * TW + t], x3 = x[(p0 + 3 * hs) * TW + t];
+      if (kk != 0) {
+        const double2 w1 = tab[2 * kk * s4], w2 = tab[kk * s4], w3 = tab[3 * kk * s4];
+        x1 = make_double2(w1.x * x1.x - w1.y * x1.y, w1.x * x1.y + w1.y * x1.x);
+        x2 = make_double2(w2.x * x2.x - w2.y * x2.y, w2.x * x2.y + w2.y * x2.x);
+        x3 = make_double2(w3.x * x3.x - w3.y * x3.y, w3.x * x3.y + w3.y * x3.x);
       }
-      x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
-      x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
+      const double2 A = make_double2(x0.x + x1.x, x0.y + x1.y), B = make_double2(x0.x - x1.x, x0.y - x1.y);
+      const double2 C = make_double2(x2.x + x3.x, x2.y + x3.y), D = make_double2(x2.x - x3.x, x2.y - x3.y);
+      x[p0 * TW + t] = make_double2(A.x + C.x, A.y + C.y);
+      x[(p0 + hs) * TW + t] = make_double2(B.x + D.y, B.y - D.x);  // B - i D
+      x[(p0 + 2 * hs) * TW + t] = make_double2(A.x - C.x, A.y - C.y);
+      x[(p0 + 3 * hs) * TW + t] = make_double2(B.x - D.y, B.y + D.x);  // B + i D
     }
     __syncthreads();
   }
@@ -188,8 +210,8 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
       x[bitrev((unsigned)j, bitsM) * TW + t] = v;
     }
     __syncthreads();
-    radix2_columns(Bf, Mb, 1, tab);
-    radix2_columns(x, Mb, TW, tab);
+    fft_columns(Bf, Mb, 1, tab);
+    fft_columns(x, Mb, TW, tab);
     // conj(A B), moved to bit-reversed order for the second transform (pairs of swapped slots)
     for (int k = tid; k < Mb * TW; k += kDftThreads) {
       const int j = k / TW, t = k - j * TW;
@@ -202,7 +224,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
       x[j * TW + t] = u2;
     }
     __syncthreads();
-    radix2_columns(x, Mb, TW, tab);
+    fft_columns(x, Mb, TW, tab);
     const double invM = 1.0 / (double)Mb;  // a power of two: exact
     for (int k = tid; k < Ld * TW; k += kDftThreads) {
       const int kap = k / TW, t = k - kap * TW;
@@ -286,35 +308,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
   }
   __syncthreads();
   if (pow2) {
-    // the twiddles of the first two stages are 1 and -i (omega^(L/4)): no multiplications
-    for (int hs = 1; hs < Ld && hs <= 2; hs <<= 1) {
-      const int nb = (Ld / 2) * TW;
-      for (int k = tid; k < nb; k += kDftThreads) {
-        const int t = k % TW, b = k / TW;
-        const int kk = b % hs;
-        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
-        const double2 u = x[top * TW + t], v = x[bot * TW + t];
-        const double2 wv = kk == 0 ? v : make_double2(v.y, -v.x);  // v or -i v
-        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
-        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
-      }
-      __syncthreads();
-    }
-    for (int hs = 4; hs < Ld; hs <<= 1) {
-      const int stride = Ld / (2 * hs);
-      const int nb = (Ld / 2) * TW;
-      for (int k = tid; k < nb; k += kDftThreads) {
-        const int t = k % TW, b = k / TW;
-        const int kk = b % hs;
-        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
-        const double2 w = tab[kk * stride];
-        const double2 u = x[top * TW + t], v = x[bot * TW + t];
-        const double2 wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
-        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
-        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
-      }
-      __syncthreads();
-    }
+    fft_columns(x, Ld, TW, tab);
     if (packed) {
       const double hs2 = 0.5 / sig;
       for (int k = tid; k < Ld * TW; k += kDftThreads) {
@@ -372,8 +366,8 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_pass(const SysDev *__restri
 // every (j2, entry) and applies the twiddle omega_L^(j2 kappa1), writing Y[kappa1][j2]; pass 2
 // transforms along j2 for every (kappa1, entry) and writes Xbar at kappa1 + A kappa2.  Every entry
 // (mu, nu) of H and S is transformed (blockIdx.z: 0 H, 1 S).  A tile holds TW consecutive entries
-// for all positions of one transform in shared memory: radix-2 when the length is a power of two,
-// the direct sum with a twiddle table otherwise.
+// for all positions of one transform in shared memory: the radix-4 FFT (fft_columns) when the
+// length is a power of two, the direct sum with a twiddle table otherwise.
 
 // In-place transform of Ld positions x TW columns (x[j * TW + t]); tab[m] = omega^m.  For a power
 // of two the input must have been stored bit-reversed.
@@ -381,20 +375,7 @@ __device__ void tile_transform(double2 *x, int Ld, int TW, int tw_valid, const d
                                double2 *tmp) {
   const int tid = threadIdx.x;
   if (pow2) {
-    for (int hs = 1; hs < Ld; hs <<= 1) {
-      const int stride = Ld / (2 * hs);
-      for (int k = tid; k < (Ld / 2) * TW; k += kDftThreads) {
-        const int t = k % TW, b = k / TW;
-        const int kk = b % hs;
-        const int top = (b / hs) * 2 * hs + kk, bot = top + hs;
-        const double2 w = tab[kk * stride];
-        const double2 u = x[top * TW + t], v = x[bot * TW + t];
-        const double2 wv = make_double2(w.x * v.x - w.y * v.y, w.x * v.y + w.y * v.x);
-        x[top * TW + t] = make_double2(u.x + wv.x, u.y + wv.y);
-        x[bot * TW + t] = make_double2(u.x - wv.x, u.y - wv.y);
-      }
-      __syncthreads();
-    }
+    fft_columns(x, Ld, TW, tab);
     return;
   }
   // direct sum into tmp, then back
