@@ -14,7 +14,7 @@ value: systems/s with every input and intermediate on the device, the whole path
        contractions on tensor cores through exact BF16 digit slices); the other route (FP64
        CUDA-core Grams) is timed beside it and reported with the ratio of the two.
 e2e:   the same through lhf_bloch_spectra_host: descriptor upload and the copy of all
-       eigenvalues back to host memory inside the timed region (wall clock, synchronised).
+       eigenvalues back to pinned host memory inside the timed region (wall clock, synchronised).
 --impl reference: the CPU oracle as it stands (the plain FP64 C reference), on this host's
        cores, one system per core per step.
 """
@@ -764,8 +764,10 @@ def run_gpu(args):
     bad_k = int((kst < 0).sum().item())
 
     # end to end through the host entry point
-    host = np.empty(B * per_sys)
-    hk = np.empty(B * sizes[0]["n_kpoints"], dtype=np.int32)
+    # pinned host buffers for the step's results (the inputs are the descriptors, staged by the
+    # library in its own pinned buffer)
+    host = torch.empty(B * per_sys, dtype=torch.float64, pin_memory=True).numpy()
+    hk = torch.empty(B * sizes[0]["n_kpoints"], dtype=torch.int32, pin_memory=True).numpy()
     ctx.bloch_spectra_host(cfgs, host, hk, precision)
     if dist:
         dist.barrier()

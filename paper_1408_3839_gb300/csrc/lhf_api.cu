@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <unordered_map>
 #include <set>
 #include <string>
 #include <vector>
@@ -113,6 +114,8 @@ struct lhf_ctx {
   size_t ws_limit = 0;
   // solved k-points (one per conjugate pair) per lattice shape, on the device
   std::map<std::array<int, 3>, std::pair<int *, int>> klists;
+  // plans of the batched entry points by descriptor content (cached_plan)
+  std::unordered_map<std::string, Plan> plan_cache;
   // launch-shape autotuner of the k-point eigensolver: per (m0, tridiagonal route, log2 of the
   // solved matrices) the fastest k_eig warps per CTA and tridiagonal threads per CTA, timed on
   // the first batch of that class (outside graph capture); results do not depend on the shape
@@ -574,6 +577,60 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
   P.basis_items = lhf::basis_ctas(sd);  // one CTA per (direction, function, chunk of samples)
   P.pot_rows = lhf::potential_ctas(sd);  // one CTA per (direction, rank term, chunk of cells)
   P.ws = off;
+  return LHF_OK;
+}
+
+// The batched entry points' plans, memoized by the validated descriptor's content with the
+// precision and the context's rank-reduction setting (make_plan reads nothing else): building a
+// plan (overlap windows, workspace layout, the count of overlapping Gram rows) costs ~13 us per
+// tube_256 system, the largest host share of a 64-system call, and repeats identically for
+// repeated lattices.  Bounded: the cache is cleared when it reaches 4096 plans.
+std::string plan_key(const HostSystem &s, bool mixed, double rank_eps) {
+  std::string k;
+  auto put = [&k](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
+  auto putv = [&put](const auto &v) {
+    const size_t n = v.size();
+    put(&n, sizeof n);
+    if (n) put(v.data(), n * sizeof(v[0]));
+  };
+  put(s.L, sizeof s.L);
+  put(s.b, sizeof s.b);
+  put(s.periodic, sizeof s.periodic);
+  put(s.K, sizeof s.K);
+  put(&s.M0, sizeof s.M0);
+  putv(s.Z);
+  putv(s.a);
+  putv(s.zcell);
+  put(&s.m0, sizeof s.m0);
+  putv(s.kind);
+  putv(s.alpha);
+  putv(s.centre);
+  put(&s.rho, sizeof s.rho);
+  put(s.n, sizeof s.n);
+  put(s.nc, sizeof s.nc);
+  put(s.h, sizeof s.h);
+  put(s.x0, sizeof s.x0);
+  put(s.cell0, sizeof s.cell0);
+  put(&s.R, sizeof s.R);
+  put(&s.u0, sizeof s.u0);
+  put(&s.du, sizeof s.du);
+  const char m = mixed ? 1 : 0;
+  put(&m, 1);
+  put(&rank_eps, sizeof rank_eps);
+  return k;
+}
+
+lhf_status cached_plan(lhf_ctx *c, const HostSystem &hs, Plan &P, bool mixed) {
+  std::string key = plan_key(hs, mixed, c->rank_eps);
+  const auto it = c->plan_cache.find(key);
+  if (it != c->plan_cache.end()) {
+    P = it->second;
+    return LHF_OK;
+  }
+  const lhf_status st = make_plan(c, hs, P, mixed);
+  if (st != LHF_OK) return st;
+  if (c->plan_cache.size() >= 4096) c->plan_cache.clear();
+  c->plan_cache.emplace(std::move(key), P);
   return LHF_OK;
 }
 
@@ -1740,7 +1797,7 @@ lhf_status lhf_bloch_spectra(lhf_ctx *c, int nsys, const lhf_system_desc *system
     HostSystem hs;
     st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
-    st = make_plan(c, hs, all[i], prec == LHF_MIXED);
+    st = cached_plan(c, hs, all[i], prec == LHF_MIXED);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
     total += internal_doubles(all[i]);
   }
@@ -1813,7 +1870,7 @@ lhf_status lhf_graph_create(lhf_ctx *c, int nsys, const lhf_system_desc *systems
     HostSystem hs;
     st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return c->fail(st, "system %d: %s", i, c->err.c_str());
-    st = make_plan(c, hs, ps[i], prec == LHF_MIXED);
+    st = cached_plan(c, hs, ps[i], prec == LHF_MIXED);
     if (ps[i].rank_smem) {  // a replay would read the descriptor the reduction rewrote
       ps[i].sd.rank_eps = 0.0;
       ps[i].rank_smem = 0;
@@ -1932,17 +1989,16 @@ lhf_status lhf_bloch_spectra_host(lhf_ctx *c, int nsys, const lhf_system_desc *s
                                   double *eig_host, int *kstat_host) {
   if (!c) return LHF_ERR_ARG;
   if (nsys < 1 || !systems || !eig_host) return c->fail(LHF_ERR_ARG, "nsys >= 1, systems and eig_host are required");
-  // count outputs first
+  // count outputs first (from the validated descriptors: L0 L1 L2 blocks or k-points and m0
+  // values each, periodic or box; the plans are made once, by lhf_bloch_spectra)
   size_t neig = 0, nk = 0;
   for (int i = 0; i < nsys; ++i) {
     HostSystem hs;
     lhf_status st = system_from_desc(c, &systems[i], hs);
     if (st != LHF_OK) return st;
-    Plan p;
-    st = make_plan(c, hs, p);
-    if (st != LHF_OK) return st;
-    neig += (size_t)p.sd.nblocks * p.sd.m0;
-    nk += p.sd.nblocks;
+    const size_t nb = (size_t)hs.L[0] * hs.L[1] * hs.L[2];
+    neig += nb * hs.m0;
+    nk += nb;
   }
   const size_t need = align_up(neig) + (nk + 1) / 2 + 1;
   if (need > c->out_cap) {
