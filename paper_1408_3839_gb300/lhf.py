@@ -388,9 +388,17 @@ class Context:
         self._check(self.lib.lhf_cell_energies(self._h, n, _ptr(eig), o, c, k, w, _ptr(energy), _ptr(level)))
 
     @staticmethod
+    def prepare(cfgs) -> "_Batch":
+        """The lhf_system_desc array of a list of workload dictionaries, marshalled once: every
+        batched call below accepts it in place of the list (the array and the host arrays it
+        points to live as long as the returned object)."""
+        return _Batch(cfgs)
+
+    @staticmethod
     def _systems(cfgs):
-        """(keep-alive object, pointer to the lhf_system_desc array) for a list of workloads."""
-        batch = _Batch(cfgs)
+        """(keep-alive object, pointer to the lhf_system_desc array) for a list of workloads or a
+        prepared batch."""
+        batch = cfgs if isinstance(cfgs, _Batch) else _Batch(cfgs)
         return batch, batch.ptr()
 
     def bloch_spectra(self, cfgs, eig, k_status=None, precision: int = FP64):

@@ -74,3 +74,27 @@ def test_one_field_variants_get_their_own_plans(lhf, precision):
             assert not np.array_equal(got[np.isfinite(got)], spectrum(warm, base, precision)[np.isfinite(got)]), name
     finally:
         warm.close()
+
+
+def test_prepared_batch_equals_the_dictionaries(lhf):
+    """Context.prepare marshals the descriptor array once; the batched calls give the same
+    spectra from it as from the list of workload dictionaries (device and host outputs)."""
+    base, vs = variants()
+    cfgs = [base] + [v for _, v in vs]
+    ctx = lhf.Context(0)
+    try:
+        ctx.setup(base)
+        sz = ctx.query_sizes()
+        n = sum(c["L"][0] * c["L"][1] * c["L"][2] for c in cfgs) * sz["m0"]
+        a = torch.empty(n, dtype=torch.float64, device="cuda")
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        ctx.bloch_spectra(cfgs, a, None, 1)
+        prepared = ctx.prepare(cfgs)
+        ctx.bloch_spectra(prepared, b, None, 1)
+        host = np.empty(n)
+        ctx.bloch_spectra_host(prepared, host, None, 1)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+        assert np.array_equal(a.cpu().numpy(), host)
+    finally:
+        ctx.close()
