@@ -275,7 +275,10 @@ lhf_status lhf_box_lowest_eigenvalues(lhf_ctx *ctx, const lhf_system_desc *box, 
  * pass of batched launches.  eig: device, systems concatenated, system s at offset
  * sum_{t<s} n_kpoints(t) m0(t), conventions of lhf_k_point_eigensolve.  k_status: device (may
  * be NULL), concatenated likewise.
- * Scratch memory is the context's workspace (grown on demand). */
+ * Scratch memory is the context's workspace (grown on demand).  The context keeps each system's
+ * plan (its layout and launch extents, a pure function of the descriptor's content, the
+ * precision and the rank-reduction setting) and reuses it when a later call passes the same
+ * content; at most 4096 plans are kept. */
 lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
                              lhf_precision precision, double *eig, int *k_status);
 

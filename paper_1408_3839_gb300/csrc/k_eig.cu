@@ -1726,7 +1726,6 @@ cudaError_t launch_overlap_norms(const SysDev *sys, int nsys, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Lanes per matrix: half a warp when every order fits (m0 <= 16), else a whole warp.
 // Lanes per matrix: half a warp up to order 16 (the FP64 scalar steps then cost one warp
 // instruction per two matrices), a whole warp otherwise or when `full` (the pair arithmetic of the
 // mixed route, whose scalar steps are FP32: a warp per matrix halves the shared memory per warp and
