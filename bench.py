@@ -198,8 +198,8 @@ TRAFFIC = {
     # listed (the 16-system capture keeps part of the rank sum's and the DFT's outputs in L2, a
     # 64-system step does not; the digit slicing runs once per direction and only direction 0 was
     # captured)
-    "k_eig": {"src": "k_eig.cu", "sha": "0d945c0bded8c328", "bytes_per_system": (17.022e6 + 0.320e6) / 16},
-    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "0d945c0bded8c328", "bytes_per_system": 0.620e6 / 16},
+    "k_eig": {"src": "k_eig.cu", "sha": "2c23fa5145f826fe", "bytes_per_system": (17.022e6 + 0.320e6) / 16},
+    "k_tridiag_eig": {"src": "k_eig.cu", "sha": "2c23fa5145f826fe", "bytes_per_system": 0.620e6 / 16},
     "k_potential": {"src": "k_setup.cu", "sha": "a1cd64a6af8541fc",
                     "bytes_per_system": (0.064e6 + 0.840e6 + 0.000e6) / 16},
     "k_basis": {"src": "k_setup.cu", "sha": "a1cd64a6af8541fc", "bytes_per_system": (0.765e6 + 0.593e6) / 16},
