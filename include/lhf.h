@@ -278,7 +278,7 @@ lhf_status lhf_box_lowest_eigenvalues(lhf_ctx *ctx, const lhf_system_desc *box, 
  * Scratch memory is the context's workspace (grown on demand).  The context keeps each system's
  * plan (its layout and launch extents, a pure function of the descriptor's content, the
  * precision and the rank-reduction setting) and reuses it when a later call passes the same
- * content; at most 4096 plans are kept. */
+ * content; at most 1024 plans are kept. */
 lhf_status lhf_bloch_spectra(lhf_ctx *ctx, int nsys, const lhf_system_desc *systems,
                              lhf_precision precision, double *eig, int *k_status);
 

@@ -584,7 +584,7 @@ lhf_status make_plan(lhf_ctx *c, const HostSystem &s, Plan &P, bool mixed = fals
 // precision and the context's rank-reduction setting (make_plan reads nothing else): building a
 // plan (overlap windows, workspace layout, the count of overlapping Gram rows) costs ~13 us per
 // tube_256 system, the largest host share of a 64-system call, and repeats identically for
-// repeated lattices.  Bounded: the cache is cleared when it reaches 4096 plans.
+// repeated lattices.  Bounded (a plan is ~10 KB): the cache is cleared when it reaches 1024 plans.
 std::string plan_key(const HostSystem &s, bool mixed, double rank_eps) {
   std::string k;
   auto put = [&k](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
@@ -629,7 +629,7 @@ lhf_status cached_plan(lhf_ctx *c, const HostSystem &hs, Plan &P, bool mixed) {
   }
   const lhf_status st = make_plan(c, hs, P, mixed);
   if (st != LHF_OK) return st;
-  if (c->plan_cache.size() >= 4096) c->plan_cache.clear();
+  if (c->plan_cache.size() >= 1024) c->plan_cache.clear();
   c->plan_cache.emplace(std::move(key), P);
   return LHF_OK;
 }
